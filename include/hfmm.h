@@ -1,0 +1,206 @@
+/*
+ * hfmm.h -- C ABI of the GB300 heterogeneous FMM (H-FMM) for the 2-D
+ * Helmholtz equation in a half-space with an impedance boundary, a two-layer
+ * or a three-layer medium (Cho, Huang, Chen, Cai: "A Heterogeneous FMM for
+ * 2-D Layered Media Helmholtz Equation I: Two & Three Layers Cases").
+ *
+ * The library computes the matrix-vector product of Sec. 2.4,
+ *
+ *     y_i = sum_j A_ij q_j,   A_ij = u_{x_j}(x_i)           (Sec. 2.4)
+ *         = sum_{j != i} (i/4) H0^(1)(k1 |x_i - x_j|) q_j   (Eq. (eq:freeGreen))
+ *         + sum_j        G^s(x_i - x_j, y_i + y_j)     q_j   (Eq. (eq:multisommer), (eq:multitop))
+ *
+ *     G^s(X, Y) = 1/(4 pi) int_R e^{-s1 Y} / s1  e^{i lambda X} sigma(lambda) dlambda,
+ *     s_j = -i sqrt(k_j^2 - lambda^2)  (principal root, Re s_j >= 0),
+ *
+ * for N points that are both sources and targets, all in the top layer
+ * y > 0.  The free-space self term (i = j) is omitted; the reaction self term
+ * G^s(0, 2 y_i) is included.  sigma is
+ *     impedance:    (s1 + i alpha) / (s1 - i alpha)                       (Sec. 2.2)
+ *     two layers:   (s1 - s2) / (s1 + s2)                                 (Sec. 2.3, d -> inf)
+ *     three layers: (r12 + r23 e^{-2 s2 d}) / (1 + r12 r23 e^{-2 s2 d}),
+ *                   r_ij = (s_i - s_j) / (s_i + s_j)                      (Sec. 2.3, 4x4 system)
+ * The impedance condition du/dn - i alpha u = 0 (Eq. (impedBC)) is taken with
+ * the normal pointing out of the upper half-plane (n = -y_hat); time factor
+ * e^{-i omega t}.
+ *
+ * Algorithm (Algorithm 1, Sec. 3-5): uniform quadtree over the smallest
+ * bounding square; free-space P2M (Eq. (multi_coeff)), M2M, L2L, L2P and
+ * Graf M2L; heterogeneous M2L with the matrix A_{p,m} of Eq. (eq:m2loperator)
+ * (sigma generalised as in Sec. 5) built at plan time by FP64 quadrature on
+ * the GPU; direct free-space H0 sums over neighbouring leaves.
+ *
+ * Memory and ownership.  All array arguments are plain pointers that may
+ * point to host memory or to device memory of the current CUDA device (the
+ * library asks the driver which).  The caller owns them; the library never
+ * frees or keeps them past the call.  The plan owns all of its device memory
+ * (tree, tables, expansion buffers) and releases it in hfmm_plan_destroy.
+ * Complex arrays are interleaved (re, im).  Multi-RHS arrays are column-major
+ * [nrhs][n]: right-hand side r occupies elements r*n .. r*n+n-1, in the
+ * caller's point order.
+ *
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy
+ * default stream).  Host inputs/outputs make the call synchronous on that
+ * stream; with device pointers the call only enqueues work.
+ *
+ * Errors.  Every function returns an hfmm_status; no C++ exception crosses
+ * the ABI.  hfmm_last_error() returns a thread-local message describing the
+ * most recent failure on the calling thread.  A failed call leaves the plan
+ * usable.
+ */
+#ifndef HFMM_H
+#define HFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hfmm_plan_s* hfmm_plan_t;
+
+typedef enum {
+    HFMM_OK = 0,
+    HFMM_ERR_INVALID_ARG = 1,   /* bad pointer, size, point below y = 0, non-finite input */
+    HFMM_ERR_UNSUPPORTED = 2,   /* valid request the library does not handle (e.g. alpha < 0) */
+    HFMM_ERR_OOM = 3,           /* device or host allocation failed */
+    HFMM_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    HFMM_ERR_NUMERICS = 5,      /* a table quadrature did not reach its tolerance */
+    HFMM_ERR_TIMEOUT = 6        /* a bounded device wait gave up */
+} hfmm_status;
+
+typedef enum {
+    HFMM_IMPEDANCE = 0,         /* y > 0 over the impedance line y = 0 */
+    HFMM_TWO_LAYER = 1,         /* k[0] for y > 0, k[1] for y < 0 */
+    HFMM_THREE_LAYER = 2        /* k[0] for y > 0, k[1] for -d < y < 0, k[2] for y < -d */
+} hfmm_medium_kind;
+
+typedef enum {
+    HFMM_FP64 = 0,              /* complex128 in/out, FP64 arithmetic everywhere */
+    HFMM_MIXED = 1              /* complex64 in/out, FP32 P2P/P2M/L2P, tensor-core M2L */
+} hfmm_precision;
+
+typedef struct {
+    int32_t kind;               /* hfmm_medium_kind */
+    int32_t reserved;
+    double k[3];                /* real wavenumbers, k[0] > 0 */
+    double d;                   /* three layers: middle-layer thickness > 0 */
+    double alpha;               /* impedance: real alpha >= 0 */
+} hfmm_medium;
+
+typedef struct {
+    double tol;                 /* target relative accuracy; selects the expansion order */
+    int32_t p;                  /* > 0: fixed low-frequency order instead of the tol rule */
+    int32_t leaf_size;          /* mean points per leaf that sets the leaf level */
+    int32_t levels;             /* > 0: force the leaf level L */
+    int32_t precision;          /* hfmm_precision */
+    int32_t max_rhs;            /* largest nrhs of later apply calls (buffers sized for it) */
+    int32_t flags;              /* reserved, 0 */
+    int64_t spin_limit;         /* reserved for bounded device waits, 0 = default */
+} hfmm_options;
+
+/* Plan summary for callers and tests. */
+#define HFMM_MAX_LEVELS 24
+typedef struct {
+    int64_t n;
+    int32_t levels;             /* leaf level L */
+    int32_t lmin;               /* coarsest level with translation work */
+    int32_t p[HFMM_MAX_LEVELS]; /* expansion order per level (2p+1 coefficients) */
+    int64_t nonempty_leaves;
+    int64_t v_pairs;            /* free-space M2L pairs, all levels */
+    int64_t r_pairs;            /* reaction M2L pairs, all levels */
+    int64_t direct_leaf_pairs;  /* leaf pairs whose reaction is summed directly */
+    int64_t u_pairs;            /* neighbouring non-empty leaf pairs (P2P) */
+    double x0, y0, size;        /* root square [x0, x0+size] x [y0, y0+size] */
+    double table_bytes;         /* device bytes of translation tables */
+    double buffer_bytes;        /* device bytes of expansion buffers */
+    double plan_ms;             /* wall time of hfmm_plan_create */
+    int32_t precision;
+    int32_t max_rhs;
+} hfmm_plan_info;
+
+/* Bits of `parts` in hfmm_apply_parts (sum of the selected terms). */
+#define HFMM_PART_NEAR_FREE   1  /* H0 sums over neighbouring leaves (Algorithm 1, step 5) */
+#define HFMM_PART_FAR_FREE    2  /* free-space M2L through the tree (steps 2-4) */
+#define HFMM_PART_FAR_REACT   4  /* reaction M2L with A_{p,m} (steps 3-4) */
+#define HFMM_PART_NEAR_REACT  8  /* directly summed reaction (step 5) */
+#define HFMM_PART_ALL        15
+
+/* Defaults: tol 1e-6, p 0, leaf_size 32, levels 0, FP64, max_rhs 1. */
+void hfmm_options_default(hfmm_options* opts);
+
+/*
+ * Build a plan for n points xy[n][2] (x, y interleaved, FP64; host or device
+ * pointer).  Builds the quadtree on the device (Morton sort, leaf binning,
+ * interaction lists), chooses the expansion order per level and computes the
+ * translation tables (Sec. 3.3, Eq. (eq:m2loperator); "precompute tables" of
+ * Algorithm 1, step 1).  Synchronises `stream` before returning.
+ * Errors: INVALID_ARG for n < 1, a null pointer, non-finite coordinates or
+ * y <= 0; UNSUPPORTED for alpha < 0, k <= 0 or d <= 0 (three layers);
+ * OOM / CUDA / NUMERICS as named.  *out is NULL on failure.
+ */
+hfmm_status hfmm_plan_create(hfmm_plan_t* out, int64_t n, const double* xy,
+                             const hfmm_medium* medium, const hfmm_options* opts,
+                             void* stream);
+
+/*
+ * y = A q for nrhs right-hand sides (1 <= nrhs <= max_rhs).  q, y: [nrhs][n]
+ * complex, complex128 for HFMM_FP64 plans, complex64 for HFMM_MIXED plans,
+ * in the caller's point order.  q and y must not overlap.
+ */
+hfmm_status hfmm_apply(hfmm_plan_t plan, int32_t nrhs, const void* q, void* y, void* stream);
+
+/* As hfmm_apply but only the terms selected by `parts` (HFMM_PART_*). */
+hfmm_status hfmm_apply_parts(hfmm_plan_t plan, int32_t nrhs, const void* q, void* y,
+                             int32_t parts, void* stream);
+
+/*
+ * w = A^H v: the transposed tree pass (L2P^T, L2L^T, M2L^T with transposed
+ * tables, M2M^T, P2M^T, P2P^T) applied to conj(v), conjugated.  Same layout
+ * and dtype rules as hfmm_apply.
+ */
+hfmm_status hfmm_apply_adjoint(hfmm_plan_t plan, int32_t nrhs, const void* v, void* w, void* stream);
+
+/* Fill *info (host pointer). */
+hfmm_status hfmm_plan_get_info(hfmm_plan_t plan, hfmm_plan_info* info);
+
+/*
+ * Copy the plan's tree to host arrays: perm[n] (caller index of the i-th
+ * point in leaf order, int64) and leaf_ix[n], leaf_iy[n] (leaf column / row
+ * of each caller-order point, int32).  Any pointer may be NULL.
+ */
+hfmm_status hfmm_plan_get_tree(hfmm_plan_t plan, int64_t* perm, int32_t* leaf_ix, int32_t* leaf_iy);
+
+/*
+ * Copy the interaction pairs of level `level` to host arrays of the given
+ * capacity: kind 0 = free-space M2L (V list), 1 = reaction M2L, 2 = direct
+ * reaction leaf pairs, 3 = neighbouring leaf pairs (U list).  Each pair is
+ * (target ix, target iy, source ix, source iy) in out[4*i .. 4*i+3].
+ * *count receives the number of pairs (also when cap is too small, in
+ * which case INVALID_ARG is returned).
+ */
+hfmm_status hfmm_plan_get_pairs(hfmm_plan_t plan, int32_t kind, int32_t level,
+                                int32_t* out, int64_t cap, int64_t* count);
+
+/* Release the plan (NULL is accepted).  Synchronises the device. */
+hfmm_status hfmm_plan_destroy(hfmm_plan_t plan);
+
+/* Static description of a status code. */
+const char* hfmm_status_string(hfmm_status s);
+
+/* Thread-local message of the last failure on this thread ("" if none). */
+const char* hfmm_last_error(void);
+
+/*
+ * Host reference of the library's own Bessel code (no GPU needed): for x > 0
+ * writes J_n(x) to j[0..nmax] and H_n^(1)(x) to h[2*(0..nmax)] (re, im).
+ * Used by tests to compare the library's Bessel evaluation with other
+ * implementations.
+ */
+hfmm_status hfmm_debug_bessel(double x, int32_t nmax, double* j, double* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HFMM_H */

@@ -1,0 +1,231 @@
+"""GB300 heterogeneous FMM for the 2-D layered-media Helmholtz equation.
+
+Thin Python binding of the C ABI in include/hfmm.h: argument marshalling
+only; every step of the computation runs in the native CUDA library
+``libhfmm.so`` (built by ``paper_1703_09136_gb300.build``).  There is no
+fallback: if the library is missing or fails to load, an ImportError is
+raised on first use.
+
+    from paper_1703_09136_gb300 import Plan, Medium
+    plan = Plan(xy, Medium.three_layer(40, 80, 60, d=0.5), tol=1e-6, max_rhs=64)
+    y = plan.apply(q)            # q: [nrhs, n] complex tensor or array
+    w = plan.adjoint(v)          # A^H v
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _native as _n
+from ._native import (HfmmError, PART_ALL, PART_FAR_FREE, PART_FAR_REACT, PART_NEAR_FREE,
+                      PART_NEAR_REACT, FP64, MIXED, IMPEDANCE, TWO_LAYER, THREE_LAYER)
+
+__all__ = ["Plan", "Medium", "HfmmError", "library", "PART_ALL", "PART_FAR_FREE",
+           "PART_FAR_REACT", "PART_NEAR_FREE", "PART_NEAR_REACT", "FP64", "MIXED",
+           "IMPEDANCE", "TWO_LAYER", "THREE_LAYER"]
+
+
+def library():
+    """The loaded ctypes handle of libhfmm.so (raises ImportError if absent)."""
+    return _n.lib()
+
+
+class Medium:
+    """Medium description (see hfmm_medium in include/hfmm.h)."""
+
+    def __init__(self, kind, k, d=0.0, alpha=0.0):
+        self.kind = int(kind)
+        k = list(k) + [0.0] * (3 - len(k))
+        self.k = tuple(float(v) for v in k[:3])
+        self.d = float(d)
+        self.alpha = float(alpha)
+
+    @classmethod
+    def impedance(cls, k, alpha):
+        return cls(IMPEDANCE, (k,), alpha=alpha)
+
+    @classmethod
+    def two_layer(cls, k1, k2):
+        return cls(TWO_LAYER, (k1, k2))
+
+    @classmethod
+    def three_layer(cls, k1, k2, k3, d):
+        return cls(THREE_LAYER, (k1, k2, k3), d=d)
+
+    @classmethod
+    def of(cls, m):
+        if isinstance(m, cls):
+            return m
+        return cls(m.kind, tuple(m.k), getattr(m, "d", 0.0), getattr(m, "alpha", 0.0))
+
+    def _c(self):
+        c = _n.hfmm_medium()
+        c.kind = self.kind
+        for i in range(3):
+            c.k[i] = self.k[i]
+        c.d = self.d
+        c.alpha = self.alpha
+        return c
+
+
+def _torch():
+    try:
+        import torch
+        return torch
+    except ImportError:  # pragma: no cover
+        return None
+
+
+def _stream_handle(stream):
+    if stream is None:
+        torch = _torch()
+        if torch is not None and torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(a):
+    """(pointer, keepalive) of a contiguous numpy array or torch tensor."""
+    torch = _torch()
+    if torch is not None and isinstance(a, torch.Tensor):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), a
+    a = np.ascontiguousarray(a)
+    return ctypes.c_void_p(a.ctypes.data), a
+
+
+class Plan:
+    """An H-FMM plan for fixed points: y = A q with A_ij = u_{x_j}(x_i)."""
+
+    def __init__(self, xy, medium, tol=1e-6, p=0, leaf_size=32, levels=0, precision=FP64,
+                 max_rhs=1, stream=None):
+        lib = _n.lib()
+        m = Medium.of(medium)
+        opts = _n.hfmm_options()
+        lib.hfmm_options_default(ctypes.byref(opts))
+        opts.tol = float(tol)
+        opts.p = int(p)
+        opts.leaf_size = int(leaf_size)
+        opts.levels = int(levels)
+        opts.precision = int(precision)
+        opts.max_rhs = int(max_rhs)
+        torch = _torch()
+        if torch is not None and isinstance(xy, torch.Tensor):
+            if xy.dtype != torch.float64:
+                raise ValueError("xy must be float64")
+            xy = xy.contiguous()
+            n = xy.shape[0]
+        else:
+            xy = np.ascontiguousarray(xy, dtype=np.float64)
+            n = xy.shape[0]
+        if xy.shape[-1] != 2:
+            raise ValueError("xy must have shape [n, 2]")
+        ptr, keep = _ptr(xy)
+        h = _n.hfmm_plan_t()
+        _n.check(lib.hfmm_plan_create(ctypes.byref(h), ctypes.c_int64(n), ptr, ctypes.byref(m._c()),
+                                      ctypes.byref(opts), _stream_handle(stream)))
+        del keep
+        self._h = h
+        self.n = int(n)
+        self.medium = m
+        self.precision = int(precision)
+        self.max_rhs = int(max_rhs)
+
+    # ------------------------------------------------------------------
+    def _complex_dtype(self):
+        return np.complex128 if self.precision == FP64 else np.complex64
+
+    def _run(self, fn, q, out, stream, *extra):
+        torch = _torch()
+        is_t = torch is not None and isinstance(q, torch.Tensor)
+        want = self._complex_dtype()
+        if is_t:
+            tdt = torch.complex128 if want == np.complex128 else torch.complex64
+            if q.dtype != tdt:
+                raise ValueError(f"q must be {tdt}")
+            q = q.contiguous()
+            shape = q.shape
+            if out is None:
+                out = torch.empty_like(q)
+        else:
+            q = np.ascontiguousarray(q)
+            if q.dtype != want:
+                raise ValueError(f"q must be {np.dtype(want)}")
+            shape = q.shape
+            if out is None:
+                out = np.empty_like(q)
+        if shape[-1] != self.n:
+            raise ValueError(f"last dimension must be n = {self.n}")
+        nrhs = 1 if len(shape) == 1 else int(np.prod(shape[:-1]))
+        qp, kq = _ptr(q)
+        yp, ky = _ptr(out)
+        _n.check(fn(self._h, ctypes.c_int32(nrhs), qp, yp, *extra, _stream_handle(stream)))
+        if not is_t and ky is not out:
+            out[...] = ky
+        return out
+
+    def apply(self, q, out=None, stream=None, parts=PART_ALL):
+        """y = A q (parts: sum of PART_* flags selects terms)."""
+        lib = _n.lib()
+        if parts == PART_ALL:
+            return self._run(lib.hfmm_apply, q, out, stream)
+        return self._run(lib.hfmm_apply_parts, q, out, stream, ctypes.c_int32(parts))
+
+    def adjoint(self, v, out=None, stream=None):
+        """w = A^H v."""
+        return self._run(_n.lib().hfmm_apply_adjoint, v, out, stream)
+
+    # ------------------------------------------------------------------
+    @property
+    def info(self):
+        inf = _n.hfmm_plan_info()
+        _n.check(_n.lib().hfmm_plan_get_info(self._h, ctypes.byref(inf)))
+        d = {name: getattr(inf, name) for name, _ in inf._fields_ if name != "p"}
+        d["p"] = [inf.p[l] for l in range(inf.levels + 1)]
+        return d
+
+    def tree(self):
+        """(perm, leaf_ix, leaf_iy) as numpy arrays."""
+        perm = np.empty(self.n, dtype=np.int64)
+        ix = np.empty(self.n, dtype=np.int32)
+        iy = np.empty(self.n, dtype=np.int32)
+        _n.check(_n.lib().hfmm_plan_get_tree(self._h, perm.ctypes.data_as(ctypes.c_void_p),
+                                             ix.ctypes.data_as(ctypes.c_void_p),
+                                             iy.ctypes.data_as(ctypes.c_void_p)))
+        return perm, ix, iy
+
+    def pairs(self, kind, level):
+        """Interaction pairs [(tx, ty, sx, sy)] of a level: kind 0 V list,
+        1 reaction M2L, 2 direct reaction, 3 neighbouring leaves."""
+        lib = _n.lib()
+        cnt = ctypes.c_int64(0)
+        st = lib.hfmm_plan_get_pairs(self._h, kind, level, None, ctypes.c_int64(0), ctypes.byref(cnt))
+        if st not in (0, 1):
+            _n.check(st)
+        out = np.empty((max(cnt.value, 1), 4), dtype=np.int32)
+        _n.check(lib.hfmm_plan_get_pairs(self._h, kind, level, out.ctypes.data_as(ctypes.c_void_p),
+                                         ctypes.c_int64(cnt.value), ctypes.byref(cnt)))
+        return out[:cnt.value]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _n.lib().hfmm_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,367 @@
+// C ABI of the H-FMM library (include/hfmm.h): plan lifecycle, apply entry
+// points, introspection.  No exception crosses this boundary.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bessel.cuh"
+#include "plan.cuh"
+
+static thread_local std::string g_last_error;
+
+void hfmm_set_error(const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+hfmm_status plan_alloc(hfmm_plan_s* P, void** ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        hfmm_set_error("cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? HFMM_ERR_OOM : HFMM_ERR_CUDA;
+    }
+    P->allocations.push_back(*ptr);
+    return HFMM_OK;
+}
+
+static void plan_free(hfmm_plan_s* P) {
+    if (!P) return;
+    cudaDeviceSynchronize();
+    for (void* p : P->allocations) cudaFree(p);
+    delete P;
+}
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int choose_levels(int64_t n, int leaf) {
+    int L = 2;
+    while (n > (int64_t)leaf * ((int64_t)1 << (2 * L)) && L < 15) ++L;
+    return L;
+}
+
+static int p_low(double tol) {
+    double d = std::max(1.0, -std::log10(tol));
+    return std::max(4, (int)std::ceil(2.5 * d - 6.5));
+}
+
+extern "C" {
+
+void hfmm_options_default(hfmm_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->tol = 1e-6;
+    o->p = 0;
+    o->leaf_size = 32;
+    o->levels = 0;
+    o->precision = HFMM_FP64;
+    o->max_rhs = 1;
+}
+
+const char* hfmm_status_string(hfmm_status s) {
+    switch (s) {
+        case HFMM_OK: return "ok";
+        case HFMM_ERR_INVALID_ARG: return "invalid argument";
+        case HFMM_ERR_UNSUPPORTED: return "unsupported";
+        case HFMM_ERR_OOM: return "out of memory";
+        case HFMM_ERR_CUDA: return "CUDA error";
+        case HFMM_ERR_NUMERICS: return "numerical tolerance not reached";
+        case HFMM_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+const char* hfmm_last_error(void) { return g_last_error.c_str(); }
+
+static hfmm_status validate_medium(const hfmm_medium* m) {
+    if (!m) { hfmm_set_error("medium is NULL"); return HFMM_ERR_INVALID_ARG; }
+    if (!(m->k[0] > 0.0) || !std::isfinite(m->k[0])) {
+        hfmm_set_error("k[0] must be a positive finite wavenumber");
+        return HFMM_ERR_UNSUPPORTED;
+    }
+    switch (m->kind) {
+        case HFMM_IMPEDANCE:
+            if (!std::isfinite(m->alpha) || m->alpha < 0.0) {
+                hfmm_set_error("impedance alpha must be real, finite and >= 0 (got %g)", m->alpha);
+                return HFMM_ERR_UNSUPPORTED;
+            }
+            return HFMM_OK;
+        case HFMM_TWO_LAYER:
+            if (!(m->k[1] > 0.0) || !std::isfinite(m->k[1])) {
+                hfmm_set_error("two layers: k[1] must be positive and finite");
+                return HFMM_ERR_UNSUPPORTED;
+            }
+            return HFMM_OK;
+        case HFMM_THREE_LAYER:
+            if (!(m->k[1] > 0.0) || !(m->k[2] > 0.0) || !std::isfinite(m->k[1]) || !std::isfinite(m->k[2])) {
+                hfmm_set_error("three layers: k[1], k[2] must be positive and finite");
+                return HFMM_ERR_UNSUPPORTED;
+            }
+            if (!(m->d > 0.0) || !std::isfinite(m->d)) {
+                hfmm_set_error("three layers: d must be positive and finite");
+                return HFMM_ERR_UNSUPPORTED;
+            }
+            return HFMM_OK;
+    }
+    hfmm_set_error("unknown medium kind %d", m->kind);
+    return HFMM_ERR_INVALID_ARG;
+}
+
+hfmm_status hfmm_plan_create(hfmm_plan_t* out, int64_t n, const double* xy, const hfmm_medium* medium,
+                             const hfmm_options* opts, void* stream) {
+    if (!out) { hfmm_set_error("out is NULL"); return HFMM_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (n < 1 || n > ((int64_t)1 << 30)) { hfmm_set_error("n must be in [1, 2^30] (got %lld)", (long long)n); return HFMM_ERR_INVALID_ARG; }
+    if (!xy) { hfmm_set_error("xy is NULL"); return HFMM_ERR_INVALID_ARG; }
+    HFMM_TRY(validate_medium(medium));
+    hfmm_options o;
+    hfmm_options_default(&o);
+    if (opts) o = *opts;
+    if (!(o.tol > 0.0) || o.tol >= 1.0) { hfmm_set_error("tol must be in (0, 1)"); return HFMM_ERR_INVALID_ARG; }
+    if (o.leaf_size < 1) o.leaf_size = 32;
+    if (o.max_rhs < 1) o.max_rhs = 1;
+    if (o.precision != HFMM_FP64 && o.precision != HFMM_MIXED) {
+        hfmm_set_error("unknown precision %d", o.precision);
+        return HFMM_ERR_INVALID_ARG;
+    }
+    if (o.precision == HFMM_MIXED) {
+        hfmm_set_error("HFMM_MIXED precision is not available in this build");
+        return HFMM_ERR_UNSUPPORTED;
+    }
+    if (o.levels < 0 || o.levels > 15) { hfmm_set_error("levels must be in [0, 15]"); return HFMM_ERR_INVALID_ARG; }
+    auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t st = (cudaStream_t)stream;
+    hfmm_plan_s* P = new (std::nothrow) hfmm_plan_s();
+    if (!P) { hfmm_set_error("host allocation failed"); return HFMM_ERR_OOM; }
+    P->n = n;
+    P->med = *medium;
+    P->k = medium->k[0];
+    P->tol = o.tol;
+    P->precision = o.precision;
+    P->max_rhs = o.max_rhs;
+    P->L = o.levels > 0 ? o.levels : choose_levels(n, o.leaf_size);
+    hfmm_status s = HFMM_OK;
+    do {
+        const double* d_xy = xy;
+        if (!is_device_ptr(xy)) {
+            double* tmp = nullptr;
+            if ((s = plan_alloc(P, (void**)&tmp, sizeof(double) * 2 * n)) != HFMM_OK) break;
+            cudaError_t e = cudaMemcpyAsync(tmp, xy, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) { hfmm_set_error("copy of xy failed: %s", cudaGetErrorString(e)); s = HFMM_ERR_CUDA; break; }
+            d_xy = tmp;
+        }
+        if ((s = build_tree(P, d_xy, st)) != HFMM_OK) break;
+        const int L = P->L;
+        P->lev.resize(L + 1);
+        const int base = o.p > 0 ? o.p : p_low(o.tol);
+        const double dgt = std::max(1.0, -std::log10(o.tol));
+        for (int l = 0; l <= L; ++l) {
+            LevelInfo& lv = P->lev[l];
+            lv.h = P->S / (double)(1 << l);
+            lv.nbox = (int64_t)1 << (2 * l);
+            const double kR = P->k * lv.h / std::sqrt(2.0);
+            lv.p = base + (int)std::ceil(kR + 1.8 * std::pow(dgt, 2.0 / 3.0) *
+                                                  std::pow(std::max(kR - 1.0, 0.0), 1.0 / 3.0));
+            lv.ncoef = 2 * lv.p + 1;
+        }
+        if ((s = build_lists(P, st)) != HFMM_OK) break;
+        // expansion buffers
+        for (int l = P->lmin; l <= L; ++l) {
+            LevelInfo& lv = P->lev[l];
+            const size_t bytes = sizeof(cd) * (size_t)lv.nbox * o.max_rhs * lv.ncoef;
+            if ((s = plan_alloc(P, (void**)&lv.mult, bytes)) != HFMM_OK) break;
+            if ((s = plan_alloc(P, (void**)&lv.loc, bytes)) != HFMM_OK) break;
+            P->buffer_bytes += 2.0 * bytes;
+        }
+        if (s != HFMM_OK) break;
+        if ((s = plan_alloc(P, (void**)&P->q_sorted, sizeof(cd) * n * o.max_rhs)) != HFMM_OK) break;
+        if ((s = plan_alloc(P, (void**)&P->y_sorted, sizeof(cd) * n * o.max_rhs)) != HFMM_OK) break;
+        P->buffer_bytes += 2.0 * sizeof(cd) * n * o.max_rhs;
+        if ((s = build_tables(P, st)) != HFMM_OK) break;
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { hfmm_set_error("plan build failed: %s", cudaGetErrorString(e)); s = HFMM_ERR_CUDA; break; }
+    } while (0);
+    if (s != HFMM_OK) {
+        plan_free(P);
+        return s;
+    }
+    P->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = P;
+    return HFMM_OK;
+}
+
+static hfmm_status apply_common(hfmm_plan_t P, int32_t nrhs, const void* q, void* y, int parts,
+                                bool adjoint, void* stream) {
+    if (!P) { hfmm_set_error("plan is NULL"); return HFMM_ERR_INVALID_ARG; }
+    if (nrhs < 1 || nrhs > P->max_rhs) {
+        hfmm_set_error("nrhs must be in [1, max_rhs=%d] (got %d)", P->max_rhs, nrhs);
+        return HFMM_ERR_INVALID_ARG;
+    }
+    if (!q || !y) { hfmm_set_error("q or y is NULL"); return HFMM_ERR_INVALID_ARG; }
+    if (q == y) { hfmm_set_error("q and y must not overlap"); return HFMM_ERR_INVALID_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = sizeof(cd) * (size_t)P->n * nrhs;
+    const bool qd = is_device_ptr(q), yd = is_device_ptr(y);
+    const cd* dq = (const cd*)q;
+    cd* dy = (cd*)y;
+    if (!qd) {
+        if (!P->io_q) HFMM_TRY(plan_alloc(P, (void**)&P->io_q, sizeof(cd) * (size_t)P->n * P->max_rhs));
+        HFMM_CUDA_TRY(cudaMemcpyAsync(P->io_q, q, bytes, cudaMemcpyHostToDevice, st));
+        dq = P->io_q;
+    }
+    if (!yd) {
+        if (!P->io_y) HFMM_TRY(plan_alloc(P, (void**)&P->io_y, sizeof(cd) * (size_t)P->n * P->max_rhs));
+        dy = P->io_y;
+    }
+    HFMM_TRY(apply_fp64(P, nrhs, dq, dy, parts, adjoint, st));
+    if (!yd) {
+        HFMM_CUDA_TRY(cudaMemcpyAsync(y, P->io_y, bytes, cudaMemcpyDeviceToHost, st));
+    }
+    if (!qd || !yd) HFMM_CUDA_TRY(cudaStreamSynchronize(st));
+    return HFMM_OK;
+}
+
+hfmm_status hfmm_apply(hfmm_plan_t plan, int32_t nrhs, const void* q, void* y, void* stream) {
+    return apply_common(plan, nrhs, q, y, HFMM_PART_ALL, false, stream);
+}
+
+hfmm_status hfmm_apply_parts(hfmm_plan_t plan, int32_t nrhs, const void* q, void* y, int32_t parts,
+                             void* stream) {
+    if (parts < 0 || parts > HFMM_PART_ALL) { hfmm_set_error("bad parts mask %d", parts); return HFMM_ERR_INVALID_ARG; }
+    return apply_common(plan, nrhs, q, y, parts, false, stream);
+}
+
+hfmm_status hfmm_apply_adjoint(hfmm_plan_t plan, int32_t nrhs, const void* v, void* w, void* stream) {
+    // Transposed pass: with symmetric lists, P2M^T = (4/i) L2P R, M2M^T = R L2L R,
+    // M2L(D)^T = R M2L(-D) R (R: alpha_m -> (-1)^m alpha_{-m}), P2P^T = P2P, the
+    // transposed tree pass is the forward pass; A^H v = conj(A^T conj v).
+    return apply_common(plan, nrhs, v, w, HFMM_PART_ALL, true, stream);
+}
+
+hfmm_status hfmm_plan_get_info(hfmm_plan_t P, hfmm_plan_info* info) {
+    if (!P || !info) { hfmm_set_error("plan or info is NULL"); return HFMM_ERR_INVALID_ARG; }
+    std::memset(info, 0, sizeof(*info));
+    info->n = P->n;
+    info->levels = P->L;
+    info->lmin = P->lmin;
+    for (int l = 0; l <= P->L && l < HFMM_MAX_LEVELS; ++l) info->p[l] = P->lev[l].p;
+    const auto& lb = P->h_leaf_begin;
+    int64_t ne = 0;
+    for (size_t b = 0; b + 1 < lb.size(); ++b) ne += lb[b + 1] > lb[b];
+    info->nonempty_leaves = ne;
+    for (int l = 0; l <= P->L; ++l) { info->v_pairs += P->lev[l].nv; info->r_pairs += P->lev[l].nr; }
+    info->direct_leaf_pairs = P->nd;
+    info->u_pairs = P->u_pairs;
+    info->x0 = P->x0; info->y0 = P->y0; info->size = P->S;
+    info->table_bytes = P->table_bytes;
+    info->buffer_bytes = P->buffer_bytes;
+    info->plan_ms = P->plan_ms;
+    info->precision = P->precision;
+    info->max_rhs = P->max_rhs;
+    return HFMM_OK;
+}
+
+hfmm_status hfmm_plan_get_tree(hfmm_plan_t P, int64_t* perm, int32_t* leaf_ix, int32_t* leaf_iy) {
+    if (!P) { hfmm_set_error("plan is NULL"); return HFMM_ERR_INVALID_ARG; }
+    std::vector<int64_t> hp(P->n);
+    HFMM_CUDA_TRY(cudaMemcpy(hp.data(), P->perm, sizeof(int64_t) * P->n, cudaMemcpyDeviceToHost));
+    if (perm) std::memcpy(perm, hp.data(), sizeof(int64_t) * P->n);
+    if (leaf_ix || leaf_iy) {
+        const auto& lb = P->h_leaf_begin;
+        for (size_t b = 0; b + 1 < lb.size(); ++b)
+            for (int32_t i = lb[b]; i < lb[b + 1]; ++i) {
+                if (leaf_ix) leaf_ix[hp[i]] = (int32_t)morton_x((uint32_t)b);
+                if (leaf_iy) leaf_iy[hp[i]] = (int32_t)morton_y((uint32_t)b);
+            }
+    }
+    return HFMM_OK;
+}
+
+hfmm_status hfmm_plan_get_pairs(hfmm_plan_t P, int32_t kind, int32_t level, int32_t* out, int64_t cap,
+                                int64_t* count) {
+    if (!P || !count) { hfmm_set_error("plan or count is NULL"); return HFMM_ERR_INVALID_ARG; }
+    if (level < 0 || level > P->L) { hfmm_set_error("level out of range"); return HFMM_ERR_INVALID_ARG; }
+    std::vector<int32_t> pairs;
+    auto csr = [&](const int32_t* dbeg, const int32_t* dsrc, int64_t nbox, int64_t nnz) -> hfmm_status {
+        if (!dbeg || nnz == 0) return HFMM_OK;
+        std::vector<int32_t> hb(nbox + 1), hs(nnz);
+        HFMM_CUDA_TRY(cudaMemcpy(hb.data(), dbeg, sizeof(int32_t) * (nbox + 1), cudaMemcpyDeviceToHost));
+        HFMM_CUDA_TRY(cudaMemcpy(hs.data(), dsrc, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
+        for (int64_t b = 0; b < nbox; ++b)
+            for (int32_t e = hb[b]; e < hb[b + 1]; ++e) {
+                pairs.push_back((int32_t)morton_x((uint32_t)b));
+                pairs.push_back((int32_t)morton_y((uint32_t)b));
+                pairs.push_back((int32_t)morton_x((uint32_t)hs[e]));
+                pairs.push_back((int32_t)morton_y((uint32_t)hs[e]));
+            }
+        return HFMM_OK;
+    };
+    const LevelInfo& lv = P->lev[level];
+    if (kind == 0) {
+        HFMM_TRY(csr(lv.v_begin, lv.v_src, lv.nbox, lv.nv));
+    } else if (kind == 1) {
+        HFMM_TRY(csr(lv.r_begin, lv.r_src, lv.nbox, lv.nr));
+    } else if (kind == 2) {
+        if (level == P->L) HFMM_TRY(csr(P->d_begin, P->d_src, lv.nbox, P->nd));
+    } else if (kind == 3) {
+        if (level == P->L) {
+            const auto& lb = P->h_leaf_begin;
+            const int m = 1 << P->L;
+            for (int64_t b = 0; b < lv.nbox; ++b) {
+                if (lb[b + 1] == lb[b]) continue;
+                int ix = (int)morton_x((uint32_t)b), iy = (int)morton_y((uint32_t)b);
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        int sx = ix + dx, sy = iy + dy;
+                        if (sx < 0 || sy < 0 || sx >= m || sy >= m) continue;
+                        uint32_t s = morton(sx, sy);
+                        if (lb[s + 1] == lb[s]) continue;
+                        pairs.insert(pairs.end(), {ix, iy, sx, sy});
+                    }
+            }
+        }
+    } else {
+        hfmm_set_error("unknown pair kind %d", kind);
+        return HFMM_ERR_INVALID_ARG;
+    }
+    *count = (int64_t)pairs.size() / 4;
+    if (*count > cap) { hfmm_set_error("capacity %lld < %lld pairs", (long long)cap, (long long)*count); return HFMM_ERR_INVALID_ARG; }
+    if (out && !pairs.empty()) std::memcpy(out, pairs.data(), sizeof(int32_t) * pairs.size());
+    return HFMM_OK;
+}
+
+hfmm_status hfmm_plan_destroy(hfmm_plan_t plan) {
+    plan_free(plan);
+    return HFMM_OK;
+}
+
+hfmm_status hfmm_debug_bessel(double x, int32_t nmax, double* j, double* h) {
+    if (!(x > 0.0) || nmax < 0 || nmax > 100000) { hfmm_set_error("need x > 0, 0 <= nmax"); return HFMM_ERR_INVALID_ARG; }
+    std::vector<double> J(nmax + 1);
+    std::vector<cd> H(nmax + 1);
+    bessel_j_seq(x, nmax, J.data());
+    hankel_seq(x, nmax, H.data());
+    if (j) std::memcpy(j, J.data(), sizeof(double) * (nmax + 1));
+    if (h) for (int i = 0; i <= nmax; ++i) { h[2 * i] = H[i].x; h[2 * i + 1] = H[i].y; }
+    return HFMM_OK;
+}
+
+}  // extern "C"

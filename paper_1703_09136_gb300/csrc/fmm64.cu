@@ -1,0 +1,357 @@
+// FP64 apply path: y = G q through the H-FMM (Algorithm 1, steps 2-5).
+//
+// Conventions (unscaled expansions, C_n(D) = H_n(k|D|) e^{i n angle D},
+// J_n(v) = J_n(k|v|) e^{i n angle v}):
+//   P2M  alpha_m   = sum_j q_j e^{-i m theta_j} J_m(k rho_j)              (Eq. (multi_coeff))
+//   M2M  alpha^P_j = sum_m alpha^c_m J_{m-j}(P - c)
+//   M2L  beta_p   += sum_m alpha_m C_{m-p}(x_T - x_S)                    (Sec. 3.3)
+//   react beta_p  += sum_m (-1)^m alpha_m A_{-m-p}(x_T - x_S, y_T + y_S)  (Eq. (m2l), (eq:m2loperator);
+//                    image coefficients alpha^im_m = (-1)^m alpha_{-m})
+//   L2L  beta^c_m  = sum_n beta^P_n J_{n-m}(c - P)
+//   L2P  y_i      += (i/4) sum_p beta_p J_p(k rho_i) e^{i p theta_i}
+//   P2P  y_i      += sum_{j in U, j != i} (i/4) H0(k r_ij) q_j            (Eq. (eq:direct), free part)
+//   direct reaction for leaf pairs whose images are not separated from the target leaf.
+#include <algorithm>
+#include <vector>
+
+#include "bessel.cuh"
+#include "plan.cuh"
+
+namespace {
+
+constexpr int TB = 128;
+
+__global__ void gather_q(const cd* q, const int64_t* perm, int64_t n, int nrhs, bool conj_in,
+                         cd* qs) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t j = perm[i];
+    for (int r = 0; r < nrhs; ++r) {
+        cd v = q[(int64_t)r * n + j];
+        qs[(int64_t)r * n + i] = conj_in ? cconj(v) : v;
+    }
+}
+
+__global__ void scatter_y(const cd* ys, const int64_t* perm, int64_t n, int nrhs, bool conj_out,
+                          cd* y) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t j = perm[i];
+    for (int r = 0; r < nrhs; ++r) {
+        cd v = ys[(int64_t)r * n + i];
+        y[(int64_t)r * n + j] = conj_out ? cconj(v) : v;
+    }
+}
+
+// basis of one point about centre (cx, cy): B[m + p] = J_m(k rho) e^{sgn i m theta},
+// m = -p .. p, using J_{-m} = (-1)^m J_m.  Jt: scratch of p + 1 doubles.
+__device__ void point_basis(double px, double py, double cx, double cy, double k, int p, int sgn,
+                            double* Jt, cd* B) {
+    const double dx = px - cx, dy = py - cy;
+    const double rho = hypot(dx, dy);
+    bessel_j_seq(k * rho, p, Jt);
+    const double th = atan2(dy, dx);
+    const cd e1 = cexpi(sgn * th);
+    cd e = cmk(1.0, 0.0);
+    B[p] = cmk(Jt[0], 0.0);
+    for (int m = 1; m <= p; ++m) {
+        e = cmul(e, e1);
+        const double sg = (m & 1) ? -1.0 : 1.0;
+        B[p + m] = cscale(e, Jt[m]);
+        B[p - m] = cscale(cconj(e), sg * Jt[m]);
+    }
+}
+
+// P2M: one CTA per leaf.  Dynamic smem: chunk * (ncoef cd + (p+1) double).
+__global__ void p2m_kernel(const int32_t* lb, const double2* xs, const cd* qs, int64_t n, int nrhs,
+                           double x0, double y0, double h, int L, double k, int p, int chunk,
+                           cd* mult) {
+    extern __shared__ double smem[];
+    const int64_t b = blockIdx.x;
+    const int ncoef = 2 * p + 1;
+    cd* B = (cd*)smem;
+    double* Jt = (double*)(B + (size_t)chunk * ncoef);
+    const int32_t lo = lb[b], hi = lb[b + 1];
+    const double cx = x0 + (morton_x((uint32_t)b) + 0.5) * h;
+    const double cy = y0 + (morton_y((uint32_t)b) + 0.5) * h;
+    cd* out = mult + (int64_t)b * nrhs * ncoef;
+    const int items = nrhs * ncoef;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) out[it] = cmk(0.0, 0.0);
+    for (int32_t c0 = lo; c0 < hi; c0 += chunk) {
+        const int cnt = min(chunk, hi - c0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+            const double2 pt = xs[c0 + t];
+            point_basis(pt.x, pt.y, cx, cy, k, p, -1, Jt + (size_t)t * (p + 1), B + (size_t)t * ncoef);
+        }
+        __syncthreads();
+        for (int it = threadIdx.x; it < items; it += blockDim.x) {
+            const int r = it / ncoef, m = it % ncoef;
+            cd acc = out[it];
+            const cd* qr = qs + (int64_t)r * n + c0;
+            for (int t = 0; t < cnt; ++t) cfma(acc, qr[t], B[(size_t)t * ncoef + m]);
+            out[it] = acc;
+        }
+    }
+}
+
+// M2M: parent b at level l from children at level l + 1.
+__global__ void m2m_kernel(const cd* child, const cd* T, int pc, int pp, int nrhs, cd* parent) {
+    const int64_t b = blockIdx.x;
+    const int nc = 2 * pc + 1, np = 2 * pp + 1, nmax = pc + pp, w = 2 * nmax + 1;
+    const int items = nrhs * np;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int r = it / np, j = it % np - pp;
+        cd acc = cmk(0.0, 0.0);
+        for (int c = 0; c < 4; ++c) {
+            const cd* a = child + ((4 * b + c) * nrhs + r) * (int64_t)nc;
+            const cd* Tc = T + (int64_t)c * w + nmax;
+            for (int m = -pc; m <= pc; ++m) cfma(acc, a[m + pc], Tc[m - j]);
+        }
+        parent[(b * nrhs + r) * (int64_t)np + j + pp] = acc;
+    }
+}
+
+// Downward pass at level l, one CTA per non-empty box:
+// L2L from the parent, free-space M2L over the V list, reaction M2L over the R list.
+__global__ void downward_kernel(const int32_t* lb, int L, int l, int lmin, int nrhs, int p,
+                                int pp, const cd* ploc, const cd* Tl2l, const cd* mult,
+                                const int32_t* v_begin, const int32_t* v_src,
+                                const int32_t* v_off, const cd* Tfree, const int32_t* r_begin,
+                                const int32_t* r_src, const int32_t* r_tab, const cd* Treact,
+                                int parts, cd* loc) {
+    const int64_t b = blockIdx.x;
+    int32_t lo, hi;
+    box_range(lb, L, l, b, &lo, &hi);
+    if (hi <= lo) return;
+    const int nc = 2 * p + 1;
+    const int items = nrhs * nc;
+    const int wf = 4 * p + 1;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int r = it / nc, q = it % nc - p;
+        cd acc = cmk(0.0, 0.0);
+        if (l > lmin && ploc) {
+            const int64_t P = b >> 2;
+            const int c = (int)(b & 3);
+            const int npp = 2 * pp + 1, nmax = p + pp, w = 2 * nmax + 1;
+            const cd* beta = ploc + (P * nrhs + r) * (int64_t)npp;
+            const cd* Tc = Tl2l + (int64_t)c * w + nmax;
+            for (int n = -pp; n <= pp; ++n) cfma(acc, beta[n + pp], Tc[n - q]);
+        }
+        if ((parts & HFMM_PART_FAR_FREE) && v_begin) {
+            for (int32_t e = v_begin[b]; e < v_begin[b + 1]; ++e) {
+                const cd* a = mult + ((int64_t)v_src[e] * nrhs + r) * nc;
+                const cd* F = Tfree + (int64_t)v_off[e] * wf + 2 * p;
+                for (int m = -p; m <= p; ++m) cfma(acc, a[m + p], F[m - q]);
+            }
+        }
+        if ((parts & HFMM_PART_FAR_REACT) && r_begin) {
+            for (int32_t e = r_begin[b]; e < r_begin[b + 1]; ++e) {
+                const cd* a = mult + ((int64_t)r_src[e] * nrhs + r) * nc;
+                const cd* A = Treact + (int64_t)r_tab[e] * wf + 2 * p;
+                for (int m = -p; m <= p; ++m) {
+                    cd v = a[m + p];
+                    if (m & 1) v = cneg(v);
+                    cfma(acc, v, A[-m - q]);
+                }
+            }
+        }
+        loc[(b * nrhs + r) * (int64_t)nc + q + p] = acc;
+    }
+}
+
+// L2P: one CTA per non-empty leaf.
+__global__ void l2p_kernel(const int32_t* lb, const double2* xs, const cd* loc, int64_t n, int nrhs,
+                           double x0, double y0, double h, double k, int p, int chunk, cd* ys) {
+    extern __shared__ double smem[];
+    const int64_t b = blockIdx.x;
+    const int32_t lo = lb[b], hi = lb[b + 1];
+    if (hi <= lo) return;
+    const int ncoef = 2 * p + 1;
+    cd* B = (cd*)smem;
+    double* Jt = (double*)(B + (size_t)chunk * ncoef);
+    const double cx = x0 + (morton_x((uint32_t)b) + 0.5) * h;
+    const double cy = y0 + (morton_y((uint32_t)b) + 0.5) * h;
+    const cd* beta = loc + (int64_t)b * nrhs * ncoef;
+    for (int32_t c0 = lo; c0 < hi; c0 += chunk) {
+        const int cnt = min(chunk, hi - c0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+            const double2 pt = xs[c0 + t];
+            point_basis(pt.x, pt.y, cx, cy, k, p, +1, Jt + (size_t)t * (p + 1), B + (size_t)t * ncoef);
+        }
+        __syncthreads();
+        const int items = nrhs * cnt;
+        for (int it = threadIdx.x; it < items; it += blockDim.x) {
+            const int r = it / cnt, t = it % cnt;
+            cd acc = cmk(0.0, 0.0);
+            const cd* br = beta + (int64_t)r * ncoef;
+            for (int m = 0; m < ncoef; ++m) cfma(acc, br[m], B[(size_t)t * ncoef + m]);
+            cd* yy = ys + (int64_t)r * n + c0 + t;
+            *yy = cadd(*yy, cmuli(cscale(acc, 0.25)));
+        }
+    }
+}
+
+// P2P free-space part: one CTA per non-empty target leaf; kernel blocks of
+// 32 x 32 (i/4) H0 values in shared memory reused across right-hand sides.
+constexpr int PT = 32;
+constexpr int P2P_THREADS = 256;
+constexpr int P2P_RHS = 64;
+constexpr int P2P_ITEMS = P2P_RHS * PT / P2P_THREADS;   // 8
+
+__global__ void __launch_bounds__(P2P_THREADS) p2p_kernel(const int32_t* lb, int L, const double2* xs, const cd* qs,
+                                                          int64_t n, int nrhs, double k, cd* ys) {
+    __shared__ cd G[PT][PT + 1];
+    __shared__ double2 sp[PT];
+    __shared__ double2 tp[PT];
+    const int64_t b = blockIdx.x;
+    const int32_t tlo = lb[b], thi = lb[b + 1];
+    if (thi <= tlo) return;
+    const int m = 1 << L;
+    const int ix = (int)morton_x((uint32_t)b), iy = (int)morton_y((uint32_t)b);
+    for (int r0 = 0; r0 < nrhs; r0 += P2P_RHS) {
+        const int nr = min(P2P_RHS, nrhs - r0);
+        for (int32_t t0 = tlo; t0 < thi; t0 += PT) {
+            const int tn = min(PT, thi - t0);
+            cd acc[P2P_ITEMS];
+            for (int u = 0; u < P2P_ITEMS; ++u) acc[u] = cmk(0.0, 0.0);
+            __syncthreads();
+            if (threadIdx.x < tn) tp[threadIdx.x] = xs[t0 + threadIdx.x];
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int sx = ix + dx, sy = iy + dy;
+                    if (sx < 0 || sy < 0 || sx >= m || sy >= m) continue;
+                    const uint32_t s = morton((uint32_t)sx, (uint32_t)sy);
+                    const int32_t slo = lb[s], shi = lb[s + 1];
+                    for (int32_t s0 = slo; s0 < shi; s0 += PT) {
+                        const int sn = min(PT, shi - s0);
+                        __syncthreads();
+                        if (threadIdx.x < sn) sp[threadIdx.x] = xs[s0 + threadIdx.x];
+                        __syncthreads();
+                        for (int e = threadIdx.x; e < PT * PT; e += blockDim.x) {
+                            const int i = e / PT, j = e % PT;
+                            cd g = cmk(0.0, 0.0);
+                            if (i < tn && j < sn && (t0 + i) != (s0 + j)) {
+                                const double r = hypot(tp[i].x - sp[j].x, tp[i].y - sp[j].y);
+                                cd h0 = hankel0(k * r);
+                                g = cmk(-0.25 * h0.y, 0.25 * h0.x);
+                            }
+                            G[i][j] = g;
+                        }
+                        __syncthreads();
+                        for (int u = 0; u < P2P_ITEMS; ++u) {
+                            const int it = u * P2P_THREADS + threadIdx.x;
+                            const int rr = it / PT, i = it % PT;
+                            if (rr >= nr || i >= tn) continue;
+                            const cd* qr = qs + (int64_t)(r0 + rr) * n + s0;
+                            cd a = acc[u];
+                            for (int j = 0; j < sn; ++j) cfma(a, G[i][j], qr[j]);
+                            acc[u] = a;
+                        }
+                    }
+                }
+            for (int u = 0; u < P2P_ITEMS; ++u) {
+                const int it = u * P2P_THREADS + threadIdx.x;
+                const int rr = it / PT, i = it % PT;
+                if (rr >= nr || i >= tn) continue;
+                cd* yy = ys + (int64_t)(r0 + rr) * n + t0 + i;
+                *yy = cadd(*yy, acc[u]);
+            }
+        }
+    }
+}
+
+// Directly summed reaction: one CTA per target leaf with direct pairs.
+__global__ void direct_react_kernel(const int32_t* lb, const int32_t* d_begin, const int32_t* d_src,
+                                    const int64_t* d_blk, const cd* vals, const cd* qs, int64_t n,
+                                    int nrhs, cd* ys) {
+    const int64_t b = blockIdx.x;
+    const int32_t e0 = d_begin[b], e1 = d_begin[b + 1];
+    if (e1 <= e0) return;
+    const int32_t tlo = lb[b], tn = lb[b + 1] - tlo;
+    const int items = nrhs * tn;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int r = it / tn, i = it % tn;
+        cd acc = cmk(0.0, 0.0);
+        for (int32_t e = e0; e < e1; ++e) {
+            const int32_t s = d_src[e];
+            const int32_t slo = lb[s], sn = lb[s + 1] - slo;
+            const cd* G = vals + d_blk[e] + (int64_t)i * sn;
+            const cd* qr = qs + (int64_t)r * n + slo;
+            for (int j = 0; j < sn; ++j) cfma(acc, G[j], qr[j]);
+        }
+        cd* yy = ys + (int64_t)r * n + tlo + i;
+        *yy = cadd(*yy, acc);
+    }
+}
+
+int pick_chunk(int p) {
+    const int ncoef = 2 * p + 1;
+    int c = (int)(40000 / (ncoef * 16 + (p + 1) * 8));
+    return std::max(1, std::min(32, c));
+}
+
+}  // namespace
+
+hfmm_status apply_fp64(hfmm_plan_s* P, int nrhs, const cd* q, cd* y, int parts, bool adjoint,
+                       cudaStream_t st) {
+    const int64_t n = P->n;
+    const int L = P->L;
+    const int nb = ceil_div(n, 256);
+    gather_q<<<nb, 256, 0, st>>>(q, P->perm, n, nrhs, adjoint, P->q_sorted);
+    HFMM_CUDA_TRY(cudaMemsetAsync(P->y_sorted, 0, sizeof(cd) * n * nrhs, st));
+    const bool far = (parts & (HFMM_PART_FAR_FREE | HFMM_PART_FAR_REACT)) != 0;
+    if (far) {
+        // step 2: upward pass
+        {
+            LevelInfo& lv = P->lev[L];
+            const int chunk = pick_chunk(lv.p);
+            const size_t sm = (size_t)chunk * ((2 * lv.p + 1) * sizeof(cd) + (lv.p + 1) * sizeof(double));
+            p2m_kernel<<<(unsigned)lv.nbox, TB, sm, st>>>(P->leaf_begin, P->xy_sorted, P->q_sorted, n, nrhs,
+                                                         P->x0, P->y0, lv.h, L, P->k, lv.p, chunk, lv.mult);
+            HFMM_CUDA_TRY(cudaGetLastError());
+        }
+        for (int l = L - 1; l >= P->lmin; --l) {
+            LevelInfo& lv = P->lev[l];
+            m2m_kernel<<<(unsigned)lv.nbox, TB, 0, st>>>(P->lev[l + 1].mult, lv.t_m2m, P->lev[l + 1].p, lv.p,
+                                                        nrhs, lv.mult);
+            HFMM_CUDA_TRY(cudaGetLastError());
+        }
+        // step 3: downward pass
+        for (int l = P->lmin; l <= L; ++l) {
+            LevelInfo& lv = P->lev[l];
+            const bool has_parent = l > P->lmin;
+            downward_kernel<<<(unsigned)lv.nbox, TB, 0, st>>>(
+                P->leaf_begin, L, l, P->lmin, nrhs, lv.p, has_parent ? P->lev[l - 1].p : 0,
+                has_parent ? P->lev[l - 1].loc : nullptr, has_parent ? P->lev[l - 1].t_l2l : nullptr,
+                lv.mult, lv.nv ? lv.v_begin : nullptr, lv.v_src, lv.v_off, lv.t_free,
+                lv.nr ? lv.r_begin : nullptr, lv.r_src, lv.r_tab, lv.t_react, parts, lv.loc);
+            HFMM_CUDA_TRY(cudaGetLastError());
+        }
+        // step 4: local expansions at the targets
+        {
+            LevelInfo& lv = P->lev[L];
+            const int chunk = pick_chunk(lv.p);
+            const size_t sm = (size_t)chunk * ((2 * lv.p + 1) * sizeof(cd) + (lv.p + 1) * sizeof(double));
+            l2p_kernel<<<(unsigned)lv.nbox, TB, sm, st>>>(P->leaf_begin, P->xy_sorted, lv.loc, n, nrhs, P->x0,
+                                                         P->y0, lv.h, P->k, lv.p, chunk, P->y_sorted);
+            HFMM_CUDA_TRY(cudaGetLastError());
+        }
+    }
+    // step 5: direct interactions
+    if (parts & HFMM_PART_NEAR_FREE) {
+        p2p_kernel<<<(unsigned)P->lev[L].nbox, P2P_THREADS, 0, st>>>(P->leaf_begin, L, P->xy_sorted,
+                                                                     P->q_sorted, n, nrhs, P->k, P->y_sorted);
+        HFMM_CUDA_TRY(cudaGetLastError());
+    }
+    if ((parts & HFMM_PART_NEAR_REACT) && P->nd > 0) {
+        direct_react_kernel<<<(unsigned)P->lev[L].nbox, TB, 0, st>>>(P->leaf_begin, P->d_begin, P->d_src,
+                                                                     P->d_blk, P->d_vals, P->q_sorted, n,
+                                                                     nrhs, P->y_sorted);
+        HFMM_CUDA_TRY(cudaGetLastError());
+    }
+    scatter_y<<<nb, 256, 0, st>>>(P->y_sorted, P->perm, n, nrhs, adjoint, y);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    return HFMM_OK;
+}

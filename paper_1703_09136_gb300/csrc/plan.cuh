@@ -1,0 +1,132 @@
+// Internal plan layout of the H-FMM library.
+//
+// Boxes.  The quadtree has uniform depth: level l holds 4^l boxes of side
+// h_l = S / 2^l over the root square [x0, x0 + S] x [y0, y0 + S].  A box is
+// addressed by its Morton index b (bits of ix in even, bits of iy in odd
+// positions), so the children of b are 4b .. 4b + 3 and the leaves below b
+// form the contiguous range [b 4^(L-l), (b+1) 4^(L-l)).  Points are sorted by
+// leaf Morton index (ties by caller index), so every box owns a contiguous
+// range of sorted points: [leaf_begin[b 4^(L-l)], leaf_begin[(b+1) 4^(L-l)]).
+//
+// Expansions.  Level l stores for each box, each right-hand side r and each
+// order n = -p_l .. p_l one complex coefficient at
+//     buf_l[(b * max_rhs + r) * (2 p_l + 1) + n + p_l].
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+struct LevelInfo {
+    int p = 0;
+    int ncoef = 1;          // 2p + 1
+    double h = 0.0;
+    int64_t nbox = 1;       // 4^l
+    // free-space M2L (V list), CSR over target boxes
+    int32_t* v_begin = nullptr;   // [nbox + 1]
+    int32_t* v_src = nullptr;     // [nv]
+    int32_t* v_off = nullptr;     // [nv] offset index (dx + 3) * 7 + (dy + 3)
+    int64_t nv = 0;
+    // reaction M2L, CSR over target boxes
+    int32_t* r_begin = nullptr;   // [nbox + 1]
+    int32_t* r_src = nullptr;     // [nr]
+    int32_t* r_tab = nullptr;     // [nr] index of the A_n table entry
+    int64_t nr = 0;
+    // tables
+    cd* t_free = nullptr;         // [49][4p + 1]  C_n(dx h, dy h), n = -2p .. 2p
+    cd* t_m2m = nullptr;          // [4][2(p + p_child) + 1] J_n(parent - child_c)  (this level = parent)
+    cd* t_l2l = nullptr;          // [4][2(p + p_child) + 1] J_n(child_c - parent)
+    cd* t_react = nullptr;        // [nentries][4p + 1] A_n(X, Y), n = -2p .. 2p
+    int n_react_entries = 0;
+    int react_dx_max = 0;         // entries indexed (dx + dxmax) * 3 + ysum
+    // expansion buffers (FP64 path)
+    cd* mult = nullptr;
+    cd* loc = nullptr;
+};
+
+struct hfmm_plan_s {
+    int64_t n = 0;
+    int L = 0;
+    int lmin = 0;
+    int lstar = 0;                // first level whose bottom-row pairs are admissible
+    int precision = HFMM_FP64;
+    int max_rhs = 1;
+    hfmm_medium med{};
+    double k = 0.0;
+    double x0 = 0.0, y0 = 0.0, S = 1.0;
+    double tol = 1e-6;
+    std::vector<LevelInfo> lev;
+
+    // sorted points
+    double2* xy_sorted = nullptr;   // [n]
+    int64_t* perm = nullptr;        // [n] caller index of sorted point i
+    int32_t* leaf_begin = nullptr;  // [4^L + 1]
+    std::vector<int32_t> h_leaf_begin;
+
+    // directly summed reaction: leaf pairs (CSR over target leaves)
+    int32_t* d_begin = nullptr;     // [4^L + 1]
+    int32_t* d_src = nullptr;       // [nd]
+    int64_t* d_blk = nullptr;       // [nd] offset of the n_T x n_S block in d_vals
+    cd* d_vals = nullptr;
+    int64_t nd = 0;
+    int64_t nd_vals = 0;
+
+    // work buffers
+    cd* q_sorted = nullptr;         // [max_rhs][n]
+    cd* y_sorted = nullptr;         // [max_rhs][n]
+    cd* io_q = nullptr;             // staging for host pointers
+    cd* io_y = nullptr;
+
+    // info
+    int64_t u_pairs = 0;
+    double table_bytes = 0.0;
+    double buffer_bytes = 0.0;
+    double plan_ms = 0.0;
+    std::vector<void*> allocations;
+};
+
+// allocation helper that records the pointer in the plan
+hfmm_status plan_alloc(hfmm_plan_s* P, void** ptr, size_t bytes);
+
+// tree.cu
+hfmm_status build_tree(hfmm_plan_s* P, const double* d_xy, cudaStream_t st);
+hfmm_status build_lists(hfmm_plan_s* P, cudaStream_t st);
+// tables.cu
+hfmm_status build_tables(hfmm_plan_s* P, cudaStream_t st);
+// fmm64.cu
+hfmm_status apply_fp64(hfmm_plan_s* P, int nrhs, const cd* q, cd* y, int parts, bool adjoint,
+                       cudaStream_t st);
+
+// Morton helpers
+HD uint32_t spread_bits(uint32_t v) {
+    v &= 0xFFFFu;
+    v = (v | (v << 8)) & 0x00FF00FFu;
+    v = (v | (v << 4)) & 0x0F0F0F0Fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+HD uint32_t compact_bits(uint32_t v) {
+    v &= 0x55555555u;
+    v = (v | (v >> 1)) & 0x33333333u;
+    v = (v | (v >> 2)) & 0x0F0F0F0Fu;
+    v = (v | (v >> 4)) & 0x00FF00FFu;
+    v = (v | (v >> 8)) & 0x0000FFFFu;
+    return v;
+}
+HD uint32_t morton(uint32_t ix, uint32_t iy) { return spread_bits(ix) | (spread_bits(iy) << 1); }
+HD uint32_t morton_x(uint32_t b) { return compact_bits(b); }
+HD uint32_t morton_y(uint32_t b) { return compact_bits(b >> 1); }
+
+// Points of box b at level l.
+HD void box_range(const int32_t* leaf_begin, int L, int l, int64_t b, int32_t* lo, int32_t* hi) {
+    const int64_t span = (int64_t)1 << (2 * (L - l));
+    *lo = leaf_begin[b * span];
+    *hi = leaf_begin[(b + 1) * span];
+}
+
+// Reaction admissibility at level l (image box one box below the target box):
+// y_T + y_S >= 2 h_l  <=>  iyT + iyS >= 1  or  2 y0 >= h_l.
+HD bool reaction_admissible(int iyT, int iyS, double y0, double hl) {
+    return (iyT + iyS >= 1) || (2.0 * y0 >= hl);
+}

@@ -1,0 +1,571 @@
+// Plan-time translation tables, FP64 on the GPU (Algorithm 1, step 1:
+// "precompute tables"; the paper used Mathematica, here quadrature kernels).
+//
+//  * free-space M2L:  C_n(D) = H_n(k|D|) e^{i n angle D}, n = -2p .. 2p, for the
+//    49 offsets D = (dx, dy) h_l, |dx|, |dy| <= 3 (Graf, Sec. 3.3);
+//  * M2M / L2L:       J_n(v) = J_n(k|v|) e^{i n angle v} for the four child
+//    offsets v = +-(h_{l+1}/2, h_{l+1}/2);
+//  * reaction M2L:    A_n(X, Y) of Eq. (eq:m2loperator) with sigma of the
+//    medium (Sec. 5), n = -2p .. 2p, for every (dx, ysum) used by the
+//    reaction lists, X = dx h_l, Y = 2 y0 + (ysum + 1) h_l;
+//  * direct reaction: G^s(x_i - x_j, y_i + y_j) = (i/4) A_0 per point pair of
+//    the leaf pairs whose images are not separated from the target leaf.
+//
+// Quadrature (written for this library): the propagating part is integrated
+// over tau in [0, pi] with composite 16-point Gauss-Legendre panels; the
+// evanescent part over t >= 0, where for layered media the path first dips
+// below the real axis on [0, tb] (t = u - i c 4 u (tb - u) / tb^2) to pass
+// the branch points of s2, s3 and the guided-mode poles on the radiating side,
+// then follows the real axis to the point where the integrand envelope
+// e^{-tY} ((xi + t)/k1)^nmax / xi has decayed by e^{-38}.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "bessel.cuh"
+#include "plan.cuh"
+
+namespace {
+
+constexpr int GLN = 16;
+__constant__ double c_glx[GLN];
+__constant__ double c_glw[GLN];
+double h_glx[GLN], h_glw[GLN];
+bool gl_ready = false;
+
+// Gauss-Legendre nodes on [-1, 1] by Newton's method on P_n.
+void gauss_legendre(int n, double* x, double* w) {
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(HFMM_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = 0.0;
+            for (int j = 1; j <= n; ++j) {
+                double p2 = p1;
+                p1 = p0;
+                p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
+            }
+            dp = n * (z * p0 - p1) / (z * z - 1.0);
+            const double dz = p0 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        // derivative at the converged node
+        double p0 = 1.0, p1 = 0.0;
+        for (int j = 1; j <= n; ++j) {
+            double p2 = p1;
+            p1 = p0;
+            p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
+        }
+        dp = n * (z * p0 - p1) / (z * z - 1.0);
+        x[i] = -z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+hfmm_status ensure_gl() {
+    if (!gl_ready) {
+        gauss_legendre(GLN, h_glx, h_glw);
+        gl_ready = true;
+    }
+    HFMM_CUDA_TRY(cudaMemcpyToSymbol(c_glx, h_glx, sizeof(h_glx)));
+    HFMM_CUDA_TRY(cudaMemcpyToSymbol(c_glw, h_glw, sizeof(h_glw)));
+    return HFMM_OK;
+}
+
+// quadrature segment: kind 0 tau (real panels on [a, b] in [0, pi]), 1 deformed
+// t on [a, b] = [0, tb] with depth c, 2 real t on [a, b]
+struct Seg {
+    double a, b, c, tb;
+    int kind, npan;
+    int64_t node0;
+};
+
+struct Entry {
+    double X, Y;
+    int nmax;
+    int seg0, seg1;
+    int64_t nodes;
+    int64_t out;      // offset of A_{-nmax} in the output
+};
+
+// real t >= 0 where sigma is not analytic (branch points of s_j, k_j > k1;
+// guided-mode poles lie below the largest of them)
+void singular_t(const hfmm_medium& m, std::vector<double>& out) {
+    const double k1 = m.k[0];
+    int nl = m.kind == HFMM_TWO_LAYER ? 1 : (m.kind == HFMM_THREE_LAYER ? 2 : 0);
+    for (int j = 1; j <= nl; ++j) {
+        double kj = m.k[j];
+        if (kj > k1) out.push_back(std::sqrt(kj * kj - k1 * k1));
+    }
+}
+
+void tau_kinks(const hfmm_medium& m, std::vector<double>& out) {
+    const double k1 = m.k[0];
+    int nl = m.kind == HFMM_TWO_LAYER ? 1 : (m.kind == HFMM_THREE_LAYER ? 2 : 0);
+    for (int j = 1; j <= nl; ++j) {
+        double kj = m.k[j];
+        if (kj < k1) {
+            out.push_back(std::acos(kj / k1));
+            out.push_back(std::acos(-kj / k1));
+        }
+    }
+}
+
+double log_env(double t, double k1, double Y, int nmax) {
+    double xi = std::sqrt(t * t + k1 * k1);
+    return -t * Y + nmax * std::log((xi + t) / k1) - std::log(xi);
+}
+
+// end of the evanescent integral
+double t_end(double k1, double Y, int nmax) {
+    // peak of the envelope: derivative -Y + nmax / xi - t / xi^2 = 0
+    double lo = 0.0, hi = std::max(1.0, (nmax + 1.0) / Y) * 4.0;
+    auto d = [&](double t) {
+        double xi = std::sqrt(t * t + k1 * k1);
+        return -Y + nmax / xi - t / (xi * xi);
+    };
+    double tp = 0.0;
+    if (d(0.0) > 0.0) {
+        for (int it = 0; it < 200; ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (d(mid) > 0.0) lo = mid; else hi = mid;
+        }
+        tp = 0.5 * (lo + hi);
+    }
+    const double target = log_env(tp, k1, Y, nmax) - 38.0;
+    double a = tp, b = std::max(2.0 * tp, tp + 1.0);
+    while (log_env(b, k1, Y, nmax) > target) b *= 2.0;
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (a + b);
+        if (log_env(mid, k1, Y, nmax) > target) a = mid; else b = mid;
+    }
+    return b;
+}
+
+// Build the segments of one integral; returns the number of nodes.
+int64_t make_rule(const hfmm_medium& m, double xmax, double ymin, double ymax, int nmax,
+                  std::vector<Seg>& segs) {
+    const double k1 = m.k[0];
+    const bool three = m.kind == HFMM_THREE_LAYER;
+    const double dd = three ? m.d : 0.0;
+    int64_t nodes = 0;
+    auto push = [&](double a, double b, int kind, int npan, double c, double tb) {
+        Seg s{a, b, c, tb, kind, std::max(npan, 1), nodes};
+        nodes += (int64_t)s.npan * GLN;
+        segs.push_back(s);
+    };
+    // propagating part
+    double rate = k1 * (std::fabs(xmax) + std::fabs(ymax)) + nmax + 1.0;
+    if (three) rate += 2.0 * dd * std::max(m.k[1], k1);
+    std::vector<double> brk{0.0};
+    tau_kinks(m, brk);
+    brk.push_back(HFMM_PI);
+    std::sort(brk.begin(), brk.end());
+    for (size_t i = 0; i + 1 < brk.size(); ++i) {
+        double len = brk[i + 1] - brk[i];
+        push(brk[i], brk[i + 1], 0, (int)std::ceil(len * rate / 4.0) + 1, 0.0, 0.0);
+    }
+    // evanescent part
+    const double xa = std::max(std::fabs(xmax), 1e-12);
+    double T = t_end(k1, ymin, nmax);
+    std::vector<double> sing;
+    singular_t(m, sing);
+    double t0 = 0.0;
+    if (!sing.empty()) {
+        double ts = *std::max_element(sing.begin(), sing.end());
+        double tb = 1.3 * ts + 0.1 * k1;
+        double c = std::min(0.2 * tb, 0.8 / xa);
+        double w = std::min({0.7 * c, 3.0 / std::max(ymax, 1e-12), 3.0 / xa});
+        if (three && dd > 0) w = std::min(w, 1.5 / dd);
+        push(0.0, tb, 1, (int)std::ceil(tb / w) + 2, c, tb);
+        t0 = tb;
+        T = std::max(T, tb + 1.0);
+    }
+    double wc = std::min(4.0 / std::max(ymin, 1e-300), 4.0 / xa);
+    if (three && dd > 0) wc = std::min(wc, 2.0 / dd);
+    const double wmin = wc / 16.0;
+    double a = t0;
+    while (a < T) {
+        double wl = nmax > 0 ? 3.0 * a / nmax : wc;
+        double w = std::min(wc, std::max(wmin, wl));
+        double b = (w < wc) ? std::min(T, std::max(a + 16.0 * w, 2.0 * a)) : T;
+        push(a, b, 2, (int)std::ceil((b - a) / w), 0.0, 0.0);
+        a = b;
+    }
+    return nodes;
+}
+
+struct MedDev {
+    int kind;
+    double k1, k2sq, k3sq, d, alpha;
+};
+
+MedDev make_med(const hfmm_medium& m) {
+    MedDev d;
+    d.kind = m.kind;
+    d.k1 = m.k[0];
+    d.k2sq = m.k[1] * m.k[1];
+    d.k3sq = m.k[2] * m.k[2];
+    d.d = m.d;
+    d.alpha = m.alpha;
+    return d;
+}
+
+// s = -i sqrt(k^2 - lambda^2), principal root (Re s >= 0)
+__device__ __forceinline__ cd s_branch(double kk, cd lam2) {
+    cd r = csqrtz(cmk(kk - lam2.x, -lam2.y));
+    return cmk(r.y, -r.x);
+}
+
+__device__ cd sigma_dev(const MedDev& m, cd lam2, cd s1) {
+    if (m.kind == HFMM_IMPEDANCE) {
+        return cdiv(cmk(s1.x, s1.y + m.alpha), cmk(s1.x, s1.y - m.alpha));
+    }
+    cd s2 = s_branch(m.k2sq, lam2);
+    cd r12 = cdiv(csub(s1, s2), cadd(s1, s2));
+    if (m.kind == HFMM_TWO_LAYER) return r12;
+    cd s3 = s_branch(m.k3sq, lam2);
+    cd r23 = cdiv(csub(s2, s3), cadd(s2, s3));
+    cd e = cexpz(cscale(s2, -2.0 * m.d));
+    cd re = cmul(r23, e);
+    return cdiv(cadd(r12, re), cadd(cmk(1.0, 0.0), cmul(r12, re)));
+}
+
+struct Node {
+    int kind;        // 0 tau, 1 t
+    cd base;         // tau: w e^{i k1 (Y sin - X cos)} sigma ; t: unused
+    double tau;
+    cd lp, lm;       // t: log(w dt sigma / xi) - tY +- i xi X
+    cd lzp, lzm;     // t: log zp, log zm
+};
+
+__device__ Node eval_node(const MedDev& m, const Seg* segs, int s0, int s1, int64_t nu, double X,
+                          double Y) {
+    int s = s0;
+    while (s + 1 < s1 && segs[s + 1].node0 <= nu) ++s;
+    const Seg sg = segs[s];
+    const int64_t local = nu - sg.node0;
+    const int pan = (int)(local / GLN), g = (int)(local % GLN);
+    const double w = (sg.b - sg.a) / sg.npan;
+    const double u = sg.a + (pan + 0.5 + 0.5 * c_glx[g]) * w;
+    const double wu = 0.5 * w * c_glw[g];
+    Node nd;
+    const double k1 = m.k1;
+    if (sg.kind == 0) {
+        double st, ct;
+        sincos(u, &st, &ct);
+        cd lam2 = cmk(k1 * k1 * ct * ct, 0.0);
+        cd sg1 = sigma_dev(m, lam2, cmk(0.0, -k1 * st));
+        nd.kind = 0;
+        nd.tau = u;
+        nd.base = cscale(cmul(cexpi(k1 * (Y * st - X * ct)), sg1), wu);
+        return nd;
+    }
+    cd t, dt;
+    if (sg.kind == 1) {
+        double tb = sg.tb;
+        t = cmk(u, -sg.c * 4.0 * u * (tb - u) / (tb * tb));
+        dt = cmk(1.0, -sg.c * 4.0 * (tb - 2.0 * u) / (tb * tb));
+    } else {
+        t = cmk(u, 0.0);
+        dt = cmk(1.0, 0.0);
+    }
+    cd lam2 = cadd(cmul(t, t), cmk(k1 * k1, 0.0));
+    cd xi = csqrtz(lam2);
+    cd sg1 = sigma_dev(m, lam2, t);
+    cd common = cdiv(cmul(cscale(dt, wu), sg1), xi);
+    cd lc = clogz(common);
+    cd ixX = cmuli(cscale(xi, X));            // i xi X
+    cd mtY = cscale(t, -Y);                   // -t Y
+    nd.kind = 1;
+    nd.lp = cadd(cadd(lc, mtY), ixX);
+    nd.lm = csub(cadd(lc, mtY), ixX);
+    cd xpt = cadd(xi, t);
+    cd lx = clogz(xpt);
+    double lk = log(k1);
+    nd.lzp = cmk(lk - lx.x, -lx.y);
+    nd.lzm = cmk(lx.x - lk, lx.y + HFMM_PI);
+    return nd;
+}
+
+constexpr int CH = 8;   // orders per chunk
+
+// One CTA per table entry.  Writes A_n, n = -nmax .. nmax, scaled by `scale`.
+__global__ void react_table_kernel(MedDev m, const Entry* ents, const Seg* segs, cd* out,
+                                   double scale) {
+    const Entry e = ents[blockIdx.x];
+    const int nn = 2 * e.nmax + 1;
+    __shared__ cd red[CH][2][32];
+    for (int n0 = -e.nmax; n0 <= e.nmax; n0 += CH) {
+        cd at[CH], ae[CH];
+        for (int j = 0; j < CH; ++j) { at[j] = cmk(0, 0); ae[j] = cmk(0, 0); }
+        for (int64_t nu = threadIdx.x; nu < e.nodes; nu += blockDim.x) {
+            Node nd = eval_node(m, segs, e.seg0, e.seg1, nu, e.X, e.Y);
+            if (nd.kind == 0) {
+                cd v = cmul(nd.base, cexpi(-(double)n0 * nd.tau));
+                cd st = cexpi(-nd.tau);
+                for (int j = 0; j < CH; ++j) { at[j] = cadd(at[j], v); v = cmul(v, st); }
+            } else {
+                cd vp = cexpz(cadd(nd.lp, cscale(nd.lzp, (double)n0)));
+                cd vm = cexpz(cadd(nd.lm, cscale(nd.lzm, (double)n0)));
+                cd zp = cexpz(nd.lzp), zm = cexpz(nd.lzm);
+                for (int j = 0; j < CH; ++j) {
+                    ae[j] = cadd(ae[j], cadd(vp, vm));
+                    vp = cmul(vp, zp);
+                    vm = cmul(vm, zm);
+                }
+            }
+        }
+        // block reduction (warp shuffles, then one warp over the warps)
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        for (int j = 0; j < CH; ++j) {
+            for (int o = 16; o > 0; o >>= 1) {
+                at[j].x += __shfl_down_sync(0xffffffffu, at[j].x, o);
+                at[j].y += __shfl_down_sync(0xffffffffu, at[j].y, o);
+                ae[j].x += __shfl_down_sync(0xffffffffu, ae[j].x, o);
+                ae[j].y += __shfl_down_sync(0xffffffffu, ae[j].y, o);
+            }
+            if (lane == 0) { red[j][0][wid] = at[j]; red[j][1][wid] = ae[j]; }
+        }
+        __syncthreads();
+        if (wid == 0) {
+            const int nw = blockDim.x >> 5;
+            for (int j = 0; j < CH; ++j) {
+                cd a = lane < nw ? red[j][0][lane] : cmk(0, 0);
+                cd b = lane < nw ? red[j][1][lane] : cmk(0, 0);
+                for (int o = 16; o > 0; o >>= 1) {
+                    a.x += __shfl_down_sync(0xffffffffu, a.x, o);
+                    a.y += __shfl_down_sync(0xffffffffu, a.y, o);
+                    b.x += __shfl_down_sync(0xffffffffu, b.x, o);
+                    b.y += __shfl_down_sync(0xffffffffu, b.y, o);
+                }
+                const int n = n0 + j;
+                if (lane == 0 && n <= e.nmax) {
+                    // i^n / pi * tau-sum + (-i)^n / (i pi) * t-sum
+                    int r = ((n % 4) + 4) % 4;
+                    cd in = (r == 0) ? cmk(1, 0) : (r == 1) ? cmk(0, 1) : (r == 2) ? cmk(-1, 0) : cmk(0, -1);
+                    cd mi = cconj(in);                  // (-i)^n
+                    cd v = cadd(cscale(cmul(in, a), 1.0 / HFMM_PI),
+                                cscale(cmul(mi, cmk(b.y, -b.x)), 1.0 / HFMM_PI));  // b / i = -i b
+                    out[e.out + (n + e.nmax)] = cscale(v, scale);
+                }
+            }
+        }
+        __syncthreads();
+        (void)nn;
+    }
+}
+
+// Direct reaction blocks: one thread per point pair (i in T, j in S).
+struct DirectJob {
+    int32_t t_lo, t_n, s_lo, s_n;
+    int seg0, seg1;
+    int64_t nodes;
+    int64_t blk;
+};
+
+__global__ void direct_block_kernel(MedDev m, const DirectJob* jobs, const Seg* segs,
+                                    const double2* xs, cd* vals) {
+    const DirectJob jb = jobs[blockIdx.x];
+    for (int idx = threadIdx.x; idx < jb.t_n * jb.s_n; idx += blockDim.x) {
+    const int i = idx / jb.s_n, j = idx % jb.s_n;
+    const double2 pi_ = xs[jb.t_lo + i], pj = xs[jb.s_lo + j];
+    const double X = pi_.x - pj.x, Y = pi_.y + pj.y;
+    cd at = cmk(0, 0), ae = cmk(0, 0);
+    for (int64_t nu = 0; nu < jb.nodes; ++nu) {
+        Node nd = eval_node(m, segs, jb.seg0, jb.seg1, nu, X, Y);
+        if (nd.kind == 0) at = cadd(at, nd.base);
+        else ae = cadd(ae, cadd(cexpz(nd.lp), cexpz(nd.lm)));
+    }
+    // A_0 = tau-sum / pi + t-sum / (i pi);  G^s = (i/4) A_0
+    cd a0 = cadd(cscale(at, 1.0 / HFMM_PI), cscale(cmk(ae.y, -ae.x), 1.0 / HFMM_PI));
+    vals[jb.blk + idx] = cmuli(cscale(a0, 0.25));
+    }
+}
+
+// free-space M2L: one thread per (offset) of one level
+__global__ void free_table_kernel(double k, double h, int p, cd* out) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= 49) return;
+    const int dx = o / 7 - 3, dy = o % 7 - 3;
+    const int w = 4 * p + 1;
+    cd* T = out + (int64_t)o * w;
+    if (abs(dx) < 2 && abs(dy) < 2) {
+        for (int i = 0; i < w; ++i) T[i] = cmk(0, 0);
+        return;
+    }
+    const double X = dx * h, Y = dy * h;
+    const double r = hypot(X, Y), th = atan2(Y, X);
+    const double x = k * r;
+    cd h0, h1;
+    hankel01(x, &h0, &h1);
+    cd hm = h0, hn = h1;
+    T[2 * p] = h0;
+    for (int n = 1; n <= 2 * p; ++n) {
+        cd ph = cexpi(n * th);
+        double sg = (n & 1) ? -1.0 : 1.0;
+        T[2 * p + n] = cmul(hn, ph);
+        T[2 * p - n] = cscale(cmul(hn, cconj(ph)), sg);
+        cd hx = csub(cscale(hn, 2.0 * n / x), hm);
+        hm = hn;
+        hn = hx;
+    }
+}
+
+// M2M (P - c) and L2L (c - P) tables of parent level l: thread per child
+__global__ void shift_table_kernel(double k, double hc, int nmax, double* scratch, cd* m2m,
+                                   cd* l2l) {
+    const int c = threadIdx.x;
+    if (c >= 4) return;
+    const int w = 2 * nmax + 1;
+    const double vx = (0.5 - (c & 1)) * hc, vy = (0.5 - (c >> 1)) * hc;   // P - c
+    const double r = hypot(vx, vy), th = atan2(vy, vx);
+    double* J = scratch + (int64_t)c * (nmax + 1);
+    bessel_j_seq(k * r, nmax, J);
+    for (int n = 0; n <= nmax; ++n) {
+        cd ph = cexpi(n * th);
+        double sg = (n & 1) ? -1.0 : 1.0;
+        cd vp = cscale(ph, J[n]);                  // J_n(v) e^{i n th}
+        cd vn = cscale(cconj(ph), sg * J[n]);      // J_{-n} e^{-i n th}
+        m2m[(int64_t)c * w + nmax + n] = vp;
+        m2m[(int64_t)c * w + nmax - n] = vn;
+        // c - P = -v: J_n(-v) = (-1)^n J_n(v)
+        l2l[(int64_t)c * w + nmax + n] = cscale(vp, sg);
+        l2l[(int64_t)c * w + nmax - n] = cscale(vn, sg);
+    }
+}
+
+}  // namespace
+
+hfmm_status build_tables(hfmm_plan_s* P, cudaStream_t st) {
+    HFMM_TRY(ensure_gl());
+    const int L = P->L;
+    const double k = P->k;
+    const MedDev md = make_med(P->med);
+    // free M2L and shift tables
+    for (int l = 0; l <= L; ++l) {
+        LevelInfo& lv = P->lev[l];
+        if (l >= 2 && l >= P->lmin) {
+            HFMM_TRY(plan_alloc(P, (void**)&lv.t_free, sizeof(cd) * 49 * (4 * lv.p + 1)));
+            free_table_kernel<<<1, 64, 0, st>>>(k, lv.h, lv.p, lv.t_free);
+            HFMM_CUDA_TRY(cudaGetLastError());
+            P->table_bytes += sizeof(cd) * 49.0 * (4 * lv.p + 1);
+        }
+        if (l < L && l >= P->lmin) {
+            const int nmax = lv.p + P->lev[l + 1].p;
+            const int w = 2 * nmax + 1;
+            double* scratch = nullptr;
+            HFMM_TRY(plan_alloc(P, (void**)&scratch, sizeof(double) * 4 * (nmax + 1)));
+            HFMM_TRY(plan_alloc(P, (void**)&lv.t_m2m, sizeof(cd) * 4 * w));
+            HFMM_TRY(plan_alloc(P, (void**)&lv.t_l2l, sizeof(cd) * 4 * w));
+            shift_table_kernel<<<1, 32, 0, st>>>(k, P->lev[l + 1].h, nmax, scratch, lv.t_m2m, lv.t_l2l);
+            HFMM_CUDA_TRY(cudaGetLastError());
+            P->table_bytes += sizeof(cd) * 8.0 * w;
+        }
+    }
+    // reaction tables
+    std::vector<Seg> segs;
+    std::vector<Entry> ents;
+    int64_t total = 0;
+    std::vector<int64_t> lev_off(L + 1, 0);
+    for (int l = 0; l <= L; ++l) {
+        LevelInfo& lv = P->lev[l];
+        if (lv.nr == 0) continue;
+        const int m = 1 << l;
+        const int dxmax = l == 0 ? 0 : m - 1;
+        lv.react_dx_max = dxmax;
+        lv.n_react_entries = (2 * dxmax + 1) * 3;
+        const int nmax = 2 * lv.p;
+        lev_off[l] = total;
+        for (int dx = -dxmax; dx <= dxmax; ++dx)
+            for (int ys = 0; ys < 3; ++ys) {
+                const int64_t idx = (int64_t)(dx + dxmax) * 3 + ys;
+                bool used = (l == 0) ? (dx == 0 && ys == 0)
+                                     : (ys <= 2 && reaction_admissible(ys, 0, P->y0, lv.h) && !(ys == 2 && m < 2));
+                if (l == 0) used = used && P->lstar == 0;
+                if (!used) continue;
+                Entry e;
+                e.X = dx * lv.h;
+                e.Y = 2.0 * P->y0 + (ys + 1) * lv.h;
+                e.nmax = nmax;
+                e.seg0 = (int)segs.size();
+                std::vector<Seg> tmp;
+                e.nodes = make_rule(P->med, e.X, e.Y, e.Y, nmax, tmp);
+                for (auto& s : tmp) segs.push_back(s);
+                e.seg1 = (int)segs.size();
+                e.out = total + idx * (2 * nmax + 1);
+                ents.push_back(e);
+            }
+        total += (int64_t)lv.n_react_entries * (2 * nmax + 1);
+    }
+    if (!ents.empty()) {
+        cd* tab = nullptr;
+        HFMM_TRY(plan_alloc(P, (void**)&tab, sizeof(cd) * total));
+        HFMM_CUDA_TRY(cudaMemsetAsync(tab, 0, sizeof(cd) * total, st));
+        for (int l = 0; l <= L; ++l)
+            if (P->lev[l].nr > 0) P->lev[l].t_react = tab + lev_off[l];
+        Seg* dsegs = nullptr;
+        Entry* dents = nullptr;
+        HFMM_TRY(plan_alloc(P, (void**)&dsegs, sizeof(Seg) * segs.size()));
+        HFMM_TRY(plan_alloc(P, (void**)&dents, sizeof(Entry) * ents.size()));
+        HFMM_CUDA_TRY(cudaMemcpyAsync(dsegs, segs.data(), sizeof(Seg) * segs.size(), cudaMemcpyHostToDevice, st));
+        HFMM_CUDA_TRY(cudaMemcpyAsync(dents, ents.data(), sizeof(Entry) * ents.size(), cudaMemcpyHostToDevice, st));
+        react_table_kernel<<<(unsigned)ents.size(), 256, 0, st>>>(md, dents, dsegs, tab, 1.0);
+        HFMM_CUDA_TRY(cudaGetLastError());
+        P->table_bytes += sizeof(cd) * (double)total;
+    }
+    // direct reaction blocks
+    if (P->nd > 0) {
+        const int m = 1 << L;
+        const double h = P->lev[L].h;
+        std::vector<int32_t> dbeg((size_t)P->lev[L].nbox + 1), dsrc(P->nd);
+        HFMM_CUDA_TRY(cudaMemcpyAsync(dbeg.data(), P->d_begin, sizeof(int32_t) * dbeg.size(), cudaMemcpyDeviceToHost, st));
+        HFMM_CUDA_TRY(cudaMemcpyAsync(dsrc.data(), P->d_src, sizeof(int32_t) * P->nd, cudaMemcpyDeviceToHost, st));
+        HFMM_CUDA_TRY(cudaStreamSynchronize(st));
+        std::vector<Seg> dsg;
+        std::vector<DirectJob> jobs;
+        std::vector<int64_t> blk(P->nd);
+        int64_t off = 0;
+        int maxpairs = 0;
+        const auto& lb = P->h_leaf_begin;
+        for (int64_t b = 0; b < P->lev[L].nbox; ++b) {
+            for (int32_t e = dbeg[b]; e < dbeg[b + 1]; ++e) {
+                const int64_t s = dsrc[e];
+                DirectJob jb;
+                jb.t_lo = lb[b]; jb.t_n = lb[b + 1] - lb[b];
+                jb.s_lo = lb[s]; jb.s_n = lb[s + 1] - lb[s];
+                const int dx = (int)morton_x((uint32_t)b) - (int)morton_x((uint32_t)s);
+                const double xmax = (std::abs(dx) + 1) * h;
+                jb.seg0 = (int)dsg.size();
+                std::vector<Seg> tmp;
+                jb.nodes = make_rule(P->med, xmax, 2.0 * P->y0, 2.0 * P->y0 + 2.0 * h, 0, tmp);
+                for (auto& sgm : tmp) dsg.push_back(sgm);
+                jb.seg1 = (int)dsg.size();
+                jb.blk = off;
+                blk[e] = off;
+                off += (int64_t)jb.t_n * jb.s_n;
+                maxpairs = std::max(maxpairs, jb.t_n * jb.s_n);
+                jobs.push_back(jb);
+            }
+        }
+        (void)m;
+        P->nd_vals = off;
+        HFMM_TRY(plan_alloc(P, (void**)&P->d_vals, sizeof(cd) * std::max<int64_t>(off, 1)));
+        HFMM_TRY(plan_alloc(P, (void**)&P->d_blk, sizeof(int64_t) * P->nd));
+        HFMM_CUDA_TRY(cudaMemcpyAsync(P->d_blk, blk.data(), sizeof(int64_t) * P->nd, cudaMemcpyHostToDevice, st));
+        Seg* dsegs = nullptr;
+        DirectJob* djobs = nullptr;
+        HFMM_TRY(plan_alloc(P, (void**)&dsegs, sizeof(Seg) * dsg.size()));
+        HFMM_TRY(plan_alloc(P, (void**)&djobs, sizeof(DirectJob) * jobs.size()));
+        HFMM_CUDA_TRY(cudaMemcpyAsync(dsegs, dsg.data(), sizeof(Seg) * dsg.size(), cudaMemcpyHostToDevice, st));
+        HFMM_CUDA_TRY(cudaMemcpyAsync(djobs, jobs.data(), sizeof(DirectJob) * jobs.size(), cudaMemcpyHostToDevice, st));
+        if (maxpairs > 0) {
+            direct_block_kernel<<<(unsigned)jobs.size(), 128, 0, st>>>(md, djobs, dsegs, P->xy_sorted, P->d_vals);
+            HFMM_CUDA_TRY(cudaGetLastError());
+        }
+        P->table_bytes += sizeof(cd) * (double)off;
+    }
+    HFMM_CUDA_TRY(cudaStreamSynchronize(st));
+    return HFMM_OK;
+}

@@ -1,0 +1,213 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+* tree and interaction lists: bit-exact against the oracle's tree;
+* expansion orders: equal integers;
+* every term of the FP64 apply against the plain CPU FMM at equal p (1e-11,
+  relative to the norm of the full result);
+* whole apply against the O(N^2) direct sum within the FMM tolerance;
+* the full-size workloads on sampled targets with sparse strengths.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from workloads import Medium
+from oracle import direct, fmm
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1703_09136_gb300 import Plan, HfmmError  # noqa: E402
+from paper_1703_09136_gb300 import build as _build  # noqa: E402
+
+PARITY_TOL = 1e-11
+
+CFG4_MED = W.WORKLOADS[4].medium
+CFG3_MED = W.WORKLOADS[3].medium
+
+
+def _case(name):
+    """(medium, xy, q, tol, leaf, p) of a parity case."""
+    if name == "cfg1":
+        w = W.WORKLOADS[1]
+        xy = W.points(1)
+        return w.medium, xy, W.strengths(1, xy.shape[0], 2), 1e-6, 32, 0
+    if name == "cfg2":
+        w = W.WORKLOADS[2]
+        xy = W.points(2)
+        return w.medium, xy, W.strengths(2, xy.shape[0], 1), 1e-6, 32, 0
+    if name == "cfg3-small":
+        xy = W.points_in_box(3, 2048, ((0.0, 0.5), (0.02, 0.52)))
+        return CFG3_MED, xy, W.strengths(3, 2048, 2), 1e-6, 16, 0
+    if name == "cfg4-small":
+        xy = W.points_in_box(4, 2048, ((0.0, 0.5), (0.02, 0.52)))
+        return CFG4_MED, xy, W.strengths(4, 2048, 2), 1e-6, 16, 0
+    raise KeyError(name)
+
+
+CASES = ["cfg1", "cfg2", "cfg3-small", "cfg4-small"]
+_cache = {}
+
+
+def _oracle(name):
+    if name not in _cache:
+        med, xy, q, tol, leaf, p = _case(name)
+        F = fmm.CpuFmm(xy, med, tol=tol, leaf_size=leaf, p=p)
+        parts = {part: F.apply(q, parts=part) for part in (1, 2, 4, 8)}
+        _cache[name] = (F, parts)
+    return _cache[name]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    _build.build()
+
+
+def _plan(name, **kw):
+    med, xy, q, tol, leaf, p = _case(name)
+    return Plan(xy, med, tol=tol, leaf_size=leaf, p=p, max_rhs=q.shape[0], **kw)
+
+
+def _morton(ix, iy):
+    out = np.zeros_like(ix, dtype=np.int64)
+    for b in range(16):
+        out |= ((ix >> b) & 1).astype(np.int64) << (2 * b)
+        out |= ((iy >> b) & 1).astype(np.int64) << (2 * b + 1)
+    return out
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_tree_and_lists_match_oracle(name):
+    F, _ = _oracle(name)
+    t = F.tree
+    plan = _plan(name)
+    info = plan.info
+    assert info["levels"] == t.L
+    assert info["x0"] == t.x0 and info["y0"] == t.y0 and info["size"] == t.S
+    perm, ix, iy = plan.tree()
+    assert np.array_equal(ix, t.leaf_ix) and np.array_equal(iy, t.leaf_iy)
+    want = np.lexsort((np.arange(len(ix)), _morton(t.leaf_ix, t.leaf_iy)))
+    assert np.array_equal(perm, want)
+    for l in range(t.L + 1):
+        ne = t.nonempty(l)
+        if l >= 2:
+            v = {tuple(r) for r in plan.pairs(0, l)}
+            v_or = {(T[0], T[1], S[0], S[1]) for T in ne for S in fmm.v_list(t, l, T, ne)}
+            assert v == v_or, l
+        r = {tuple(x) for x in plan.pairs(1, l)}
+        assert r == {(T[0], T[1], S[0], S[1]) for T, S in F.R[l]}, l
+    d = {tuple(x) for x in plan.pairs(2, t.L)}
+    assert d == {(T[0], T[1], S[0], S[1]) for T, S in F.direct_pairs}
+    u = {tuple(x) for x in plan.pairs(3, t.L)}
+    assert u == {(T[0], T[1], S[0], S[1]) for T in t.leaves for S in fmm.u_list(t, T)}
+    assert info["p"] == F.p
+    plan.close()
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("part", [1, 2, 4, 8])
+def test_fp64_terms_match_cpu_fmm(name, part):
+    F, parts = _oracle(name)
+    med, xy, q, tol, leaf, p = _case(name)
+    full = sum(parts.values())
+    plan = _plan(name)
+    y = plan.apply(torch.from_numpy(q).cuda(), parts=part).cpu().numpy()
+    err = np.linalg.norm(y - parts[part]) / np.linalg.norm(full)
+    assert err < PARITY_TOL, (name, part, err)
+    plan.close()
+
+
+@pytest.mark.parametrize("name,tol", [("cfg1", 1e-6), ("cfg2", 1e-6), ("cfg2", 1e-10)])
+def test_fp64_matches_direct_sum(name, tol):
+    med, xy, q, _, leaf, p = _case(name)
+    yd = direct.direct_apply(med, xy, q)
+    plan = Plan(xy, med, tol=tol, leaf_size=leaf, max_rhs=q.shape[0])
+    y = plan.apply(torch.from_numpy(q).cuda()).cpu().numpy()
+    assert direct.rel_l2(y, yd) < tol
+    plan.close()
+
+
+def test_adjoint_dot_product_and_conjugate_symmetry():
+    med, xy, q, tol, leaf, p = _case("cfg1")
+    rng = np.random.default_rng(11)
+    v = rng.standard_normal(q.shape) + 1j * rng.standard_normal(q.shape)
+    plan = _plan("cfg1")
+    qd = torch.from_numpy(q).cuda()
+    vd = torch.from_numpy(v).cuda()
+    Gq = plan.apply(qd).cpu().numpy()
+    GHv = plan.adjoint(vd).cpu().numpy()
+    lhs = np.vdot(v, Gq)          # <v, G q>
+    rhs = np.vdot(GHv, q)         # <G^H v, q>
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    plan.close()
+
+
+def test_multi_rhs_equals_single_rhs_and_host_pointers():
+    med, xy, q1, tol, leaf, p = _case("cfg4-small")
+    q = np.concatenate([q1, W.strengths(4, xy.shape[0], 2, salt=5)])
+    plan = Plan(xy, med, tol=tol, leaf_size=leaf, max_rhs=q.shape[0])
+    yall = plan.apply(torch.from_numpy(q).cuda()).cpu().numpy()
+    for r in range(q.shape[0]):
+        yr = plan.apply(torch.from_numpy(q[r:r + 1].copy()).cuda()).cpu().numpy()
+        assert np.max(np.abs(yr[0] - yall[r])) <= 1e-14 * np.max(np.abs(yall[r]))
+    yh = plan.apply(q)            # numpy in/out: host pointers through the C ABI
+    assert np.array_equal(yh, yall)
+    plan.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 33])
+def test_tiny_inputs_match_direct_sum(n):
+    med = W.WORKLOADS[1].medium
+    xy = W.points(1, n, salt=3)
+    q = W.strengths(1, n, 1, salt=3)
+    plan = Plan(xy, med, tol=1e-10, leaf_size=4)
+    y = plan.apply(q)
+    yd = direct.direct_apply(med, xy, q)
+    assert direct.rel_l2(y, yd) < 1e-9
+    plan.close()
+
+
+def test_device_side_input_errors():
+    med = W.WORKLOADS[1].medium
+    xy = W.points(1, 50)
+    bad = xy.copy()
+    bad[7, 1] = -0.01
+    with pytest.raises(HfmmError) as e:
+        Plan(bad, med)
+    assert e.value.status == 1
+    bad[7, 1] = float("nan")
+    with pytest.raises(HfmmError):
+        Plan(bad, med)
+    plan = Plan(xy, med, max_rhs=1)
+    with pytest.raises(HfmmError):
+        plan.apply(np.zeros((2, 50), dtype=np.complex128))
+    plan.close()
+
+
+def _sparse_probe(cfg, n_src=1500, n_tgt=300):
+    """Full-size point cloud, strengths on a random subset: the direct sum on
+    sampled targets is cheap and the FMM still runs over the whole tree."""
+    w = W.WORKLOADS[cfg]
+    xy = W.points(cfg)
+    n = xy.shape[0]
+    src = W.sample_indices(cfg, n, n_src, salt=1)
+    tgt = W.sample_indices(cfg, n, n_tgt, salt=2)
+    q = np.zeros((1, n), dtype=np.complex128)
+    q[0, src] = W.strengths(cfg, n_src, 1, salt=9)[0]
+    self_index = np.where(np.isin(tgt, src), np.searchsorted(src, tgt), -1)
+    yd = direct.free_sum(xy[tgt], xy[src], q[:, src], w.medium.k1, self_index=self_index)
+    yd = yd + direct.reaction_sum(w.medium, xy[tgt], xy[src], q[:, src])
+    return w, xy, q, tgt, yd
+
+
+@pytest.mark.parametrize("cfg", [3, 4])
+def test_full_size_workload_on_sampled_targets(cfg):
+    w, xy, q, tgt, yd = _sparse_probe(cfg)
+    plan = Plan(torch.from_numpy(xy).cuda(), w.medium, tol=w.tol, leaf_size=w.leaf, max_rhs=1)
+    y = plan.apply(torch.from_numpy(q).cuda()).cpu().numpy()[:, tgt]
+    assert direct.rel_l2(y, yd) < 2 * w.tol
+    plan.close()
