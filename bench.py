@@ -1,0 +1,305 @@
+"""H-FMM matvec benchmark: Mtargets/s of y = G q on one GB300.
+
+Workload (default): three-layer medium k = 40 / 80 / 60, middle layer
+0.5 thick, N = 1,048,576 points uniform in [0, 8] x [0.02, 8.02] (top layer),
+64 complex right-hand sides with N(0,1) parts, tolerance 1e-6.  A step is one
+apply (P2M, M2M, L2L + free-space and reaction M2L, L2P, P2P and the directly
+summed reaction) over all right-hand sides; the plan (tree, lists, tables) is
+built once before timing, as the paper precomputes its tables.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  value = N * nrhs / time per step / 1e6 over all ranks
+(independent replicas, one per GPU).  e2e = the same through the C ABI with
+pinned host buffers (copies inside the timed region).  cpu_baseline / the
+reference arm = the CPU oracle (plain NumPy/SciPy H-FMM) on a bounded sample
+of the same workload: the points of a 1 x 1 corner of the domain
+(same density, same distance to the interface), 64 right-hand sides.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 rate (no measured FP64 figure exists)
+SAMPLE_BOX = ((0.0, 1.0), (0.02, 1.02))
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=4)
+    ap.add_argument("--n", type=int, default=0, help="override the number of points")
+    ap.add_argument("--nrhs", type=int, default=0, help="override the number of right-hand sides")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-n", type=int, default=0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (runs in a child process with one thread)
+# ---------------------------------------------------------------------------
+_CPU_CHILD = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import workloads as W
+from oracle import fmm
+w = W.WORKLOADS[{cfg}]
+(x0, x1), (y0, y1) = {box!r}
+n = {n}
+xy = W.points_in_box({cfg}, n, ((x0, x1), (y0, y1)))
+q = W.strengths({cfg}, n, {nrhs})
+t0 = time.perf_counter()
+F = fmm.CpuFmm(xy, w.medium, tol=w.tol, leaf_size=16)
+plan_s = time.perf_counter() - t0
+times = []
+for _ in range({reps}):
+    t0 = time.perf_counter()
+    F.apply(q)
+    times.append(time.perf_counter() - t0)
+print(json.dumps({{"n": n, "nrhs": {nrhs}, "plan_s": plan_s, "apply_s": times}}))
+"""
+
+
+def cpu_oracle_sample(cfg, nrhs, reps=1, n=0):
+    w_density = 1048576 / 64.0                     # points per unit area of the 8 x 8 workload
+    (x0, x1), (y0, y1) = SAMPLE_BOX
+    n = n or int(round(w_density * (x1 - x0) * (y1 - y0)))
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    code = _CPU_CHILD.format(root=ROOT, cfg=cfg, box=SAMPLE_BOX, n=n, nrhs=nrhs, reps=reps)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    return out
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5], parts[6], parts[7], parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[2 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_1703_09136_gb300 import Plan, FP64, MIXED
+    from paper_1703_09136_gb300 import build as _build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        _build.build()
+    if world > 1:
+        torch.distributed.barrier()
+
+    cfg = args.config
+    w = W.WORKLOADS[cfg]
+    n = args.n or w.n
+    nrhs = args.nrhs or w.nrhs
+    prec = FP64 if args.precision == "fp64" else MIXED
+    cdt = torch.complex128 if prec == FP64 else torch.complex64
+    xy_h = W.points(cfg, n)
+    q_h = W.strengths(cfg, n, nrhs)
+    dev = torch.device("cuda", local)
+    xy = torch.from_numpy(xy_h).to(dev)
+    q = torch.from_numpy(q_h).to(dev, cdt)
+    t0 = time.perf_counter()
+    plan = Plan(xy, w.medium, tol=w.tol, leaf_size=w.leaf, precision=prec, max_rhs=nrhs, profile=True)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    y = torch.empty_like(q)
+    for _ in range(args.warmup):
+        plan.apply(q, out=y)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    stage_ms = {}
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.apply(q, out=y)
+        for k, v in plan.stage_times().items():
+            stage_ms[k] = stage_ms.get(k, 0.0) + v
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    total_ms = ev0.elapsed_time(ev1)
+    ck = clocks.stop()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = world * n * nrhs / (ms_per_step * 1e-3) / 1e6
+    info = plan.info
+    launches = int(info["launches_last_apply"]) * args.steps
+    # roofline of the dominant stage
+    avg = {k: v / args.steps for k, v in stage_ms.items()}
+    dom = max(avg, key=avg.get)
+    flops = info["flops_last_apply"][dom]
+    roof = {"kernel": dom, "bound": "alu", "achieved": flops / (avg[dom] * 1e-3) / 1e12,
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": None,
+            "peak_source": "nominal GB300 FP64 rate (MEASURED_PEAKS.json has no FP64 figure)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    # end to end through the C ABI with pinned host buffers
+    qh = torch.from_numpy(q_h).to(cdt).pin_memory()
+    yh = torch.empty_like(qh).pin_memory()
+    e2e_t = []
+    for _ in range(args.e2e_steps):
+        t1 = time.perf_counter()
+        plan._run(plan_lib_apply(), qh, yh, None)
+        e2e_t.append(time.perf_counter() - t1)
+    e2e_s = statistics.median(e2e_t)
+    cbytes = 16 if prec == FP64 else 8
+    e2e = {"value": world * n * nrhs / e2e_s / 1e6, "unit": "Mtargets/s",
+           "h2d_bytes_per_step": cbytes * n * nrhs, "d2h_bytes_per_step": cbytes * n * nrhs}
+    out = {
+        "metric": "H-FMM matvec throughput (targets x RHS per second), three-layer medium, N=1M, 64 RHS",
+        "value": value, "unit": "Mtargets/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == FP64 else "mixed-f32", "data": "synthetic",
+        "config": {"workload": w.name, "n": n, "nrhs": nrhs, "medium": "three-layer k=40/80/60 d=0.5",
+                   "tol": w.tol, "levels": info["levels"], "p": info["p"], "plan_s": plan_s,
+                   "l2": "inputs larger than L2 (q, y and expansions are GBs)",
+                   "parallelism": f"replicas{world}"},
+        "stage_ms": avg, "adjoint_ms": None, "gpu_launches": launches, "e2e": e2e, "roofline": roof,
+        "clocks": ck,
+    }
+    # adjoint time
+    ev0.record(stream)
+    plan.adjoint(q, out=y)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    out["adjoint_ms"] = ev0.elapsed_time(ev1)
+    if rank == 0 and not args.no_cpu_baseline:
+        s = cpu_oracle_sample(cfg, nrhs, reps=2, n=args.cpu_sample_n)
+        t_apply = min(s["apply_s"])
+        out["cpu_baseline"] = {"value": s["n"] * s["nrhs"] / t_apply / 1e6, "unit": "Mtargets/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"CPU oracle H-FMM on the {s['n']} points of the {SAMPLE_BOX} corner "
+                                         f"of the workload (same density and medium), {s['nrhs']} RHS; "
+                                         f"apply {t_apply:.2f} s, plan {s['plan_s']:.2f} s, 1 thread"}
+    plan.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def plan_lib_apply():
+    from paper_1703_09136_gb300 import library
+    return library().hfmm_apply
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import workloads as W
+    cfg = args.config
+    w = W.WORKLOADS[cfg]
+    nrhs = args.nrhs or w.nrhs
+    s = cpu_oracle_sample(cfg, nrhs, reps=args.warmup + args.steps, n=args.cpu_sample_n)
+    times = s["apply_s"][args.warmup:]
+    t = sum(times) / len(times)
+    value = s["n"] * s["nrhs"] / t / 1e6
+    sample = (f"CPU oracle H-FMM on the {s['n']} points of the {SAMPLE_BOX} corner of the workload, "
+              f"{s['nrhs']} RHS, 1 thread")
+    out = {"impl": "reference", "metric": "H-FMM matvec throughput (targets x RHS per second), "
+                                          "three-layer medium, N=1M, 64 RHS",
+           "value": value, "unit": "Mtargets/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name, "sample_n": s["n"], "nrhs": s["nrhs"]},
+           "cpu_baseline": {"value": value, "unit": "Mtargets/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "Mtargets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -95,9 +95,23 @@ typedef struct {
     int32_t levels;             /* > 0: force the leaf level L */
     int32_t precision;          /* hfmm_precision */
     int32_t max_rhs;            /* largest nrhs of later apply calls (buffers sized for it) */
-    int32_t flags;              /* reserved, 0 */
+    int32_t flags;              /* HFMM_FLAG_* bits, 0 = none */
     int64_t spin_limit;         /* reserved for bounded device waits, 0 = default */
 } hfmm_options;
+
+/* Option flags. */
+#define HFMM_FLAG_PROFILE 1     /* record CUDA events around every stage of each apply */
+
+/* Stages reported by hfmm_plan_get_stage_times (milliseconds of the last apply). */
+#define HFMM_STAGE_GATHER   0   /* caller order -> leaf order */
+#define HFMM_STAGE_P2M      1
+#define HFMM_STAGE_M2M      2
+#define HFMM_STAGE_DOWN     3   /* L2L + free-space M2L + reaction M2L, all levels */
+#define HFMM_STAGE_L2P      4
+#define HFMM_STAGE_P2P      5
+#define HFMM_STAGE_DIRECT   6   /* directly summed reaction */
+#define HFMM_STAGE_SCATTER  7
+#define HFMM_NUM_STAGES     8
 
 /* Plan summary for callers and tests. */
 #define HFMM_MAX_LEVELS 24
@@ -117,6 +131,9 @@ typedef struct {
     double plan_ms;             /* wall time of hfmm_plan_create */
     int32_t precision;
     int32_t max_rhs;
+    int64_t launches_last_apply;  /* kernels launched by the last apply call */
+    double flops_last_apply[HFMM_NUM_STAGES];  /* algorithmic real flops per stage, last apply */
+    double bytes_last_apply[HFMM_NUM_STAGES];  /* algorithmic DRAM bytes per stage, last apply */
 } hfmm_plan_info;
 
 /* Bits of `parts` in hfmm_apply_parts (sum of the selected terms). */
@@ -181,6 +198,14 @@ hfmm_status hfmm_plan_get_tree(hfmm_plan_t plan, int64_t* perm, int32_t* leaf_ix
  */
 hfmm_status hfmm_plan_get_pairs(hfmm_plan_t plan, int32_t kind, int32_t level,
                                 int32_t* out, int64_t cap, int64_t* count);
+
+/*
+ * Stage times of the last apply of a plan created with HFMM_FLAG_PROFILE:
+ * ms[HFMM_NUM_STAGES] (host array), measured with CUDA events recorded on
+ * the apply's stream around each stage.  Synchronises that stream.
+ * INVALID_ARG if the plan was created without the flag.
+ */
+hfmm_status hfmm_plan_get_stage_times(hfmm_plan_t plan, double* ms);
 
 /* Release the plan (NULL is accepted).  Synchronises the device. */
 hfmm_status hfmm_plan_destroy(hfmm_plan_t plan);

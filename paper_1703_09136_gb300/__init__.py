@@ -104,7 +104,7 @@ class Plan:
     """An H-FMM plan for fixed points: y = A q with A_ij = u_{x_j}(x_i)."""
 
     def __init__(self, xy, medium, tol=1e-6, p=0, leaf_size=32, levels=0, precision=FP64,
-                 max_rhs=1, stream=None):
+                 max_rhs=1, stream=None, profile=False):
         lib = _n.lib()
         m = Medium.of(medium)
         opts = _n.hfmm_options()
@@ -115,6 +115,7 @@ class Plan:
         opts.levels = int(levels)
         opts.precision = int(precision)
         opts.max_rhs = int(max_rhs)
+        opts.flags = _n.FLAG_PROFILE if profile else 0
         torch = _torch()
         if torch is not None and isinstance(xy, torch.Tensor):
             if xy.dtype != torch.float64:
@@ -186,9 +187,18 @@ class Plan:
     def info(self):
         inf = _n.hfmm_plan_info()
         _n.check(_n.lib().hfmm_plan_get_info(self._h, ctypes.byref(inf)))
-        d = {name: getattr(inf, name) for name, _ in inf._fields_ if name != "p"}
+        d = {name: getattr(inf, name) for name, _ in inf._fields_
+             if name not in ("p", "flops_last_apply", "bytes_last_apply")}
         d["p"] = [inf.p[l] for l in range(inf.levels + 1)]
+        d["flops_last_apply"] = dict(zip(_n.STAGES, list(inf.flops_last_apply)))
+        d["bytes_last_apply"] = dict(zip(_n.STAGES, list(inf.bytes_last_apply)))
         return d
+
+    def stage_times(self):
+        """Per-stage milliseconds of the last apply (plan built with profile=True)."""
+        ms = (ctypes.c_double * _n.NUM_STAGES)()
+        _n.check(_n.lib().hfmm_plan_get_stage_times(self._h, ms))
+        return dict(zip(_n.STAGES, list(ms)))
 
     def tree(self):
         """(perm, leaf_ix, leaf_iy) as numpy arrays."""

@@ -19,7 +19,10 @@ STATUS = {0: "HFMM_OK", 1: "HFMM_ERR_INVALID_ARG", 2: "HFMM_ERR_UNSUPPORTED", 3:
 EXPORTS = ["hfmm_options_default", "hfmm_plan_create", "hfmm_apply", "hfmm_apply_parts",
            "hfmm_apply_adjoint", "hfmm_plan_get_info", "hfmm_plan_get_tree",
            "hfmm_plan_get_pairs", "hfmm_plan_destroy", "hfmm_status_string", "hfmm_last_error",
-           "hfmm_debug_bessel"]
+           "hfmm_debug_bessel", "hfmm_plan_get_stage_times"]
+NUM_STAGES = 8
+STAGES = ["gather", "p2m", "m2m", "down", "l2p", "p2p", "direct", "scatter"]
+FLAG_PROFILE = 1
 
 
 class HfmmError(RuntimeError):
@@ -47,7 +50,8 @@ class hfmm_plan_info(ctypes.Structure):
                 ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("size", ctypes.c_double),
                 ("table_bytes", ctypes.c_double), ("buffer_bytes", ctypes.c_double),
                 ("plan_ms", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("max_rhs", ctypes.c_int32)]
+                ("max_rhs", ctypes.c_int32), ("launches_last_apply", ctypes.c_int64),
+                ("flops_last_apply", ctypes.c_double * 8), ("bytes_last_apply", ctypes.c_double * 8)]
 
 
 hfmm_plan_t = ctypes.c_void_p
@@ -76,9 +80,10 @@ def lib():
         L.hfmm_last_error.argtypes = []
         L.hfmm_last_error.restype = ctypes.c_char_p
         L.hfmm_debug_bessel.argtypes = [dbl, i32, vp, vp]
+        L.hfmm_plan_get_stage_times.argtypes = [hfmm_plan_t, vp]
         for name in ("hfmm_plan_create", "hfmm_apply", "hfmm_apply_parts", "hfmm_apply_adjoint",
                      "hfmm_plan_get_info", "hfmm_plan_get_tree", "hfmm_plan_get_pairs",
-                     "hfmm_plan_destroy", "hfmm_debug_bessel"):
+                     "hfmm_plan_destroy", "hfmm_debug_bessel", "hfmm_plan_get_stage_times"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib

@@ -39,6 +39,8 @@ hfmm_status plan_alloc(hfmm_plan_s* P, void** ptr, size_t bytes) {
 static void plan_free(hfmm_plan_s* P) {
     if (!P) return;
     cudaDeviceSynchronize();
+    if (P->events_ready)
+        for (int s = 0; s < HFMM_NUM_STAGES; ++s) { cudaEventDestroy(P->ev[s][0]); cudaEventDestroy(P->ev[s][1]); }
     for (void* p : P->allocations) cudaFree(p);
     delete P;
 }
@@ -157,6 +159,7 @@ hfmm_status hfmm_plan_create(hfmm_plan_t* out, int64_t n, const double* xy, cons
     P->tol = o.tol;
     P->precision = o.precision;
     P->max_rhs = o.max_rhs;
+    P->flags = o.flags;
     P->L = o.levels > 0 ? o.levels : choose_levels(n, o.leaf_size);
     hfmm_status s = HFMM_OK;
     do {
@@ -196,6 +199,16 @@ hfmm_status hfmm_plan_create(hfmm_plan_t* out, int64_t n, const double* xy, cons
         if ((s = plan_alloc(P, (void**)&P->y_sorted, sizeof(cd) * n * o.max_rhs)) != HFMM_OK) break;
         P->buffer_bytes += 2.0 * sizeof(cd) * n * o.max_rhs;
         if ((s = build_tables(P, st)) != HFMM_OK) break;
+        if (P->flags & HFMM_FLAG_PROFILE) {
+            for (int sg = 0; sg < HFMM_NUM_STAGES && s == HFMM_OK; ++sg)
+                for (int k2 = 0; k2 < 2; ++k2)
+                    if (cudaEventCreate(&P->ev[sg][k2]) != cudaSuccess) {
+                        hfmm_set_error("cudaEventCreate failed");
+                        s = HFMM_ERR_CUDA;
+                    }
+            if (s != HFMM_OK) break;
+            P->events_ready = true;
+        }
         cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) { hfmm_set_error("plan build failed: %s", cudaGetErrorString(e)); s = HFMM_ERR_CUDA; break; }
     } while (0);
@@ -276,6 +289,25 @@ hfmm_status hfmm_plan_get_info(hfmm_plan_t P, hfmm_plan_info* info) {
     info->plan_ms = P->plan_ms;
     info->precision = P->precision;
     info->max_rhs = P->max_rhs;
+    info->launches_last_apply = P->launches;
+    for (int s = 0; s < HFMM_NUM_STAGES; ++s) {
+        info->flops_last_apply[s] = P->st_flops[s];
+        info->bytes_last_apply[s] = P->st_bytes[s];
+    }
+    return HFMM_OK;
+}
+
+hfmm_status hfmm_plan_get_stage_times(hfmm_plan_t P, double* ms) {
+    if (!P || !ms) { hfmm_set_error("plan or ms is NULL"); return HFMM_ERR_INVALID_ARG; }
+    if (!P->events_ready) { hfmm_set_error("plan was created without HFMM_FLAG_PROFILE"); return HFMM_ERR_INVALID_ARG; }
+    HFMM_CUDA_TRY(cudaStreamSynchronize(P->last_stream));
+    for (int s = 0; s < HFMM_NUM_STAGES; ++s) {
+        ms[s] = 0.0;
+        if (!P->ev_used[s]) continue;
+        float t = 0.0f;
+        HFMM_CUDA_TRY(cudaEventElapsedTime(&t, P->ev[s][0], P->ev[s][1]));
+        ms[s] = t;
+    }
     return HFMM_OK;
 }
 

@@ -82,7 +82,30 @@ struct hfmm_plan_s {
     double table_bytes = 0.0;
     double buffer_bytes = 0.0;
     double plan_ms = 0.0;
+    int64_t p2p_point_pairs = 0;    // sum over leaves T of n_T * sum_{S in U(T)} n_S
     std::vector<void*> allocations;
+
+    // profiling (HFMM_FLAG_PROFILE)
+    int flags = 0;
+    bool events_ready = false;
+    cudaEvent_t ev[HFMM_NUM_STAGES][2];
+    bool ev_used[HFMM_NUM_STAGES] = {};
+    cudaStream_t last_stream = nullptr;
+    int64_t launches = 0;
+    double st_flops[HFMM_NUM_STAGES] = {};
+    double st_bytes[HFMM_NUM_STAGES] = {};
+};
+
+// Stage timing helper: records events on the apply stream when profiling.
+struct StageTimer {
+    hfmm_plan_s* P;
+    cudaStream_t st;
+    void begin(int s) {
+        if (P->events_ready) { cudaEventRecord(P->ev[s][0], st); P->ev_used[s] = true; }
+    }
+    void end(int s) {
+        if (P->events_ready) cudaEventRecord(P->ev[s][1], st);
+    }
 };
 
 // allocation helper that records the pointer in the plan

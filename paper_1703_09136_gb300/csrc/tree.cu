@@ -405,7 +405,7 @@ hfmm_status build_lists(hfmm_plan_s* P, cudaStream_t st) {
     // neighbour pairs (count only, host)
     const int m = 1 << L;
     const std::vector<int32_t>& lb = P->h_leaf_begin;
-    int64_t up = 0;
+    int64_t up = 0, pp = 0;
     for (int iy = 0; iy < m; ++iy)
         for (int ix = 0; ix < m; ++ix) {
             uint32_t b = morton(ix, iy);
@@ -415,10 +415,14 @@ hfmm_status build_lists(hfmm_plan_s* P, cudaStream_t st) {
                     int sx = ix + dx, sy = iy + dy;
                     if (sx < 0 || sy < 0 || sx >= m || sy >= m) continue;
                     uint32_t s = morton(sx, sy);
-                    if (lb[s + 1] > lb[s]) ++up;
+                    if (lb[s + 1] > lb[s]) {
+                        ++up;
+                        pp += (int64_t)(lb[b + 1] - lb[b]) * (lb[s + 1] - lb[s]);
+                    }
                 }
         }
     P->u_pairs = up;
+    P->p2p_point_pairs = pp;
     HFMM_CUDA_TRY(cudaStreamSynchronize(st));
     return HFMM_OK;
 }
