@@ -224,6 +224,14 @@ const char* hfmm_last_error(void);
  */
 hfmm_status hfmm_debug_bessel(double x, int32_t nmax, double* j, double* h);
 
+/*
+ * Host copy of the FP32 free-space kernel used by the HFMM_MIXED near field:
+ * g[2i], g[2i+1] = (i/4) H0^(1)(z[i]) (re, im) evaluated in single precision
+ * from the library's piecewise polynomial tables of J0 and of the smooth part
+ * Y0 - (2/pi) ln(z/2) J0, for 0 < z < 16 (NaN outside).  No GPU needed.
+ */
+hfmm_status hfmm_debug_green_f32(int32_t n, const double* z, float* g);
+
 #ifdef __cplusplus
 }
 #endif

@@ -144,10 +144,6 @@ hfmm_status hfmm_plan_create(hfmm_plan_t* out, int64_t n, const double* xy, cons
         hfmm_set_error("unknown precision %d", o.precision);
         return HFMM_ERR_INVALID_ARG;
     }
-    if (o.precision == HFMM_MIXED) {
-        hfmm_set_error("HFMM_MIXED precision is not available in this build");
-        return HFMM_ERR_UNSUPPORTED;
-    }
     if (o.levels < 0 || o.levels > 15) { hfmm_set_error("levels must be in [0, 15]"); return HFMM_ERR_INVALID_ARG; }
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t st = (cudaStream_t)stream;
@@ -187,18 +183,24 @@ hfmm_status hfmm_plan_create(hfmm_plan_t* out, int64_t n, const double* xy, cons
         }
         if ((s = build_lists(P, st)) != HFMM_OK) break;
         // expansion buffers
+        const bool mixed = o.precision == HFMM_MIXED;
+        const size_t esz = mixed ? sizeof(cf) : sizeof(cd);
         for (int l = P->lmin; l <= L; ++l) {
             LevelInfo& lv = P->lev[l];
-            const size_t bytes = sizeof(cd) * (size_t)lv.nbox * o.max_rhs * lv.ncoef;
-            if ((s = plan_alloc(P, (void**)&lv.mult, bytes)) != HFMM_OK) break;
-            if ((s = plan_alloc(P, (void**)&lv.loc, bytes)) != HFMM_OK) break;
+            const size_t bytes = esz * (size_t)lv.nbox * o.max_rhs * lv.ncoef;
+            if ((s = plan_alloc(P, mixed ? (void**)&lv.mult32 : (void**)&lv.mult, bytes)) != HFMM_OK) break;
+            if ((s = plan_alloc(P, mixed ? (void**)&lv.loc32 : (void**)&lv.loc, bytes)) != HFMM_OK) break;
             P->buffer_bytes += 2.0 * bytes;
         }
         if (s != HFMM_OK) break;
-        if ((s = plan_alloc(P, (void**)&P->q_sorted, sizeof(cd) * n * o.max_rhs)) != HFMM_OK) break;
-        if ((s = plan_alloc(P, (void**)&P->y_sorted, sizeof(cd) * n * o.max_rhs)) != HFMM_OK) break;
-        P->buffer_bytes += 2.0 * sizeof(cd) * n * o.max_rhs;
+        if ((s = plan_alloc(P, mixed ? (void**)&P->q32 : (void**)&P->q_sorted, esz * n * o.max_rhs)) != HFMM_OK) break;
+        if ((s = plan_alloc(P, mixed ? (void**)&P->y32 : (void**)&P->y_sorted, esz * n * o.max_rhs)) != HFMM_OK) break;
+        P->buffer_bytes += 2.0 * esz * n * o.max_rhs;
         if ((s = build_tables(P, st)) != HFMM_OK) break;
+        if (mixed) {
+            if ((s = build_tables32(P, st)) != HFMM_OK) break;
+            if ((s = init_h0_table(st)) != HFMM_OK) break;
+        }
         if (P->flags & HFMM_FLAG_PROFILE) {
             for (int sg = 0; sg < HFMM_NUM_STAGES && s == HFMM_OK; ++sg)
                 for (int k2 = 0; k2 < 2; ++k2)
@@ -231,7 +233,8 @@ static hfmm_status apply_common(hfmm_plan_t P, int32_t nrhs, const void* q, void
     if (!q || !y) { hfmm_set_error("q or y is NULL"); return HFMM_ERR_INVALID_ARG; }
     if (q == y) { hfmm_set_error("q and y must not overlap"); return HFMM_ERR_INVALID_ARG; }
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t bytes = sizeof(cd) * (size_t)P->n * nrhs;
+    const bool mixed = P->precision == HFMM_MIXED;
+    const size_t bytes = (mixed ? sizeof(cf) : sizeof(cd)) * (size_t)P->n * nrhs;
     const bool qd = is_device_ptr(q), yd = is_device_ptr(y);
     const cd* dq = (const cd*)q;
     cd* dy = (cd*)y;
@@ -244,7 +247,11 @@ static hfmm_status apply_common(hfmm_plan_t P, int32_t nrhs, const void* q, void
         if (!P->io_y) HFMM_TRY(plan_alloc(P, (void**)&P->io_y, sizeof(cd) * (size_t)P->n * P->max_rhs));
         dy = P->io_y;
     }
-    HFMM_TRY(apply_fp64(P, nrhs, dq, dy, parts, adjoint, st));
+    if (mixed) {
+        HFMM_TRY(apply_mixed(P, nrhs, (const cf*)dq, (cf*)dy, parts, adjoint, st));
+    } else {
+        HFMM_TRY(apply_fp64(P, nrhs, dq, dy, parts, adjoint, st));
+    }
     if (!yd) {
         HFMM_CUDA_TRY(cudaMemcpyAsync(y, P->io_y, bytes, cudaMemcpyDeviceToHost, st));
     }

@@ -42,6 +42,17 @@ struct LevelInfo {
     // expansion buffers (FP64 path)
     cd* mult = nullptr;
     cd* loc = nullptr;
+    // mixed path: scaled expansions a~_n = a_n / s(|n|), b~_n = b_n s(|n|) with
+    // s(n) = min(1, (k R_l / 2)^n / n!), R_l = h_l / sqrt(2) (|J_n(k rho)| <= s(n) for
+    // rho <= R_l), and full scaled translation matrices in FP32
+    std::vector<double> log_s;    // log s(n), n = 0 .. p
+    cf* mult32 = nullptr;
+    cf* loc32 = nullptr;
+    cf* t_free32 = nullptr;       // [49][m][p] (input coefficient m outer)
+    cf* t_react32 = nullptr;      // [nentries][m][p] (image reflection folded in)
+    cf* t_m2m32 = nullptr;        // [4][m child][j parent]   (this level = parent)
+    cf* t_l2l32 = nullptr;        // [4][n parent][m child]   (this level = parent)
+    double* d_log_s = nullptr;    // [p + 1] log s(n) on the device
 };
 
 struct hfmm_plan_s {
@@ -76,6 +87,10 @@ struct hfmm_plan_s {
     cd* y_sorted = nullptr;         // [max_rhs][n]
     cd* io_q = nullptr;             // staging for host pointers
     cd* io_y = nullptr;
+    // mixed path
+    cf* q32 = nullptr;              // [max_rhs][n]
+    cf* y32 = nullptr;
+    cf* d_vals32 = nullptr;
 
     // info
     int64_t u_pairs = 0;
@@ -116,9 +131,14 @@ hfmm_status build_tree(hfmm_plan_s* P, const double* d_xy, cudaStream_t st);
 hfmm_status build_lists(hfmm_plan_s* P, cudaStream_t st);
 // tables.cu
 hfmm_status build_tables(hfmm_plan_s* P, cudaStream_t st);
+hfmm_status build_tables32(hfmm_plan_s* P, cudaStream_t st);
 // fmm64.cu
 hfmm_status apply_fp64(hfmm_plan_s* P, int nrhs, const cd* q, cd* y, int parts, bool adjoint,
                        cudaStream_t st);
+// fmm32.cu
+hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts, bool adjoint,
+                        cudaStream_t st);
+hfmm_status init_h0_table(cudaStream_t st);
 
 // Morton helpers
 HD uint32_t spread_bits(uint32_t v) {

@@ -569,3 +569,125 @@ hfmm_status build_tables(hfmm_plan_s* P, cudaStream_t st) {
     HFMM_CUDA_TRY(cudaStreamSynchronize(st));
     return HFMM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Mixed path: scaled FP32 translation matrices from the FP64 tables.
+//   a~_n = a_n / s_l(|n|), b~_n = b_n s_l(|n|),  s_l(n) = min(1, (k R_l / 2)^n / n!)
+// so that every stored matrix entry is O(1) or smaller (FP32 range).
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ cf to_cf(cd v) { return cfmk((float)v.x, (float)v.y); }
+
+// Matrices are stored column-major (input coefficient outer, output inner),
+// so that threads over output coefficients read consecutive entries.
+// free-space M2L: F~[off][m][p] = s(p) s(m) C_{m-p}(off)
+__global__ void free32_kernel(const cd* T, const double* ls, int p, cf* out) {
+    const int nc = 2 * p + 1, w = 4 * p + 1;
+    const int64_t total = (int64_t)49 * nc * nc;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int off = (int)(e / (nc * nc));
+        const int r = (int)(e % (nc * nc));
+        const int pp = r / nc - p, m = r % nc - p;
+        const double sc = exp(ls[abs(pp)] + ls[abs(m)]);
+        out[(int64_t)off * nc * nc + (int64_t)(m + p) * nc + (pp + p)] =
+            to_cf(cscale(T[(int64_t)off * w + (m - pp) + 2 * p], sc));
+    }
+}
+
+// reaction M2L on a (not a^im): H~[e][m][p] = s(p) s(m) (-1)^m A_{-m-p}
+__global__ void react32_kernel(const cd* T, int nent, const double* ls, int p, cf* out) {
+    const int nc = 2 * p + 1, w = 4 * p + 1;
+    const int64_t total = (int64_t)nent * nc * nc;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int ent = (int)(e / (nc * nc));
+        const int r = (int)(e % (nc * nc));
+        const int pp = r / nc - p, m = r % nc - p;
+        double sc = exp(ls[abs(pp)] + ls[abs(m)]);
+        if (m & 1) sc = -sc;
+        out[(int64_t)ent * nc * nc + (int64_t)(m + p) * nc + (pp + p)] =
+            to_cf(cscale(T[(int64_t)ent * w + (-m - pp) + 2 * p], sc));
+    }
+}
+
+// M2M child (level l+1, order pc) -> parent (level l, order pp):
+//   T~[c][m][j] = J_{m-j}(P - c) s_{l+1}(m) / s_l(j)
+// L2L parent -> child: L~[c][n][m] = J_{n-m}(c - P) s_{l+1}(m) / s_l(n)
+__global__ void shift32_kernel(const cd* m2m, const cd* l2l, const double* lsp, const double* lsc,
+                               int pp, int pc, cf* om2m, cf* ol2l) {
+    const int np = 2 * pp + 1, nc = 2 * pc + 1, nmax = pp + pc, w = 2 * nmax + 1;
+    const int64_t total = (int64_t)4 * np * nc;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / (np * nc));
+        const int r = (int)(e % (np * nc));
+        // M2M: row j (parent), column m (child)
+        {
+            const int j = r / nc - pp, m = r % nc - pc;
+            const double sc = exp(lsc[abs(m)] - lsp[abs(j)]);
+            om2m[(int64_t)c * np * nc + (int64_t)(m + pc) * np + (j + pp)] =
+                to_cf(cscale(m2m[(int64_t)c * w + nmax + (m - j)], sc));
+        }
+        // L2L: row m (child), column n (parent)
+        {
+            const int m = r / np - pc, n = r % np - pp;
+            const double sc = exp(lsc[abs(m)] - lsp[abs(n)]);
+            ol2l[(int64_t)c * np * nc + (int64_t)(n + pp) * nc + (m + pc)] =
+                to_cf(cscale(l2l[(int64_t)c * w + nmax + (n - m)], sc));
+        }
+    }
+}
+
+__global__ void vals32_kernel(const cd* v, int64_t n, cf* out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = to_cf(v[e]);
+}
+
+}  // namespace
+
+hfmm_status build_tables32(hfmm_plan_s* P, cudaStream_t st) {
+    const int L = P->L;
+    const int grid = 4 * 152, tb = 256;
+    for (int l = P->lmin; l <= L; ++l) {
+        LevelInfo& lv = P->lev[l];
+        const double kR = P->k * lv.h / std::sqrt(2.0);
+        lv.log_s.assign(lv.p + 1, 0.0);
+        for (int n = 0; n <= lv.p; ++n) {
+            double v = n * std::log(0.5 * kR) - std::lgamma(n + 1.0);
+            lv.log_s[n] = std::max(-690.0, std::min(0.0, v));
+        }
+        HFMM_TRY(plan_alloc(P, (void**)&lv.d_log_s, sizeof(double) * (lv.p + 1)));
+        HFMM_CUDA_TRY(cudaMemcpyAsync(lv.d_log_s, lv.log_s.data(), sizeof(double) * (lv.p + 1), cudaMemcpyHostToDevice, st));
+    }
+    for (int l = P->lmin; l <= L; ++l) {
+        LevelInfo& lv = P->lev[l];
+        const int nc = lv.ncoef;
+        if (lv.t_free) {
+            HFMM_TRY(plan_alloc(P, (void**)&lv.t_free32, sizeof(cf) * 49 * nc * nc));
+            free32_kernel<<<grid, tb, 0, st>>>(lv.t_free, lv.d_log_s, lv.p, lv.t_free32);
+            HFMM_CUDA_TRY(cudaGetLastError());
+            P->table_bytes += sizeof(cf) * 49.0 * nc * nc;
+        }
+        if (lv.t_react && lv.n_react_entries > 0) {
+            HFMM_TRY(plan_alloc(P, (void**)&lv.t_react32, sizeof(cf) * (size_t)lv.n_react_entries * nc * nc));
+            react32_kernel<<<grid, tb, 0, st>>>(lv.t_react, lv.n_react_entries, lv.d_log_s, lv.p, lv.t_react32);
+            HFMM_CUDA_TRY(cudaGetLastError());
+            P->table_bytes += sizeof(cf) * (double)lv.n_react_entries * nc * nc;
+        }
+        if (l < L && lv.t_m2m) {
+            const int ncc = P->lev[l + 1].ncoef;
+            HFMM_TRY(plan_alloc(P, (void**)&lv.t_m2m32, sizeof(cf) * 4 * nc * ncc));
+            HFMM_TRY(plan_alloc(P, (void**)&lv.t_l2l32, sizeof(cf) * 4 * nc * ncc));
+            shift32_kernel<<<grid, tb, 0, st>>>(lv.t_m2m, lv.t_l2l, lv.d_log_s, P->lev[l + 1].d_log_s, lv.p,
+                                                P->lev[l + 1].p, lv.t_m2m32, lv.t_l2l32);
+            HFMM_CUDA_TRY(cudaGetLastError());
+            P->table_bytes += sizeof(cf) * 8.0 * nc * ncc;
+        }
+    }
+    if (P->nd_vals > 0) {
+        HFMM_TRY(plan_alloc(P, (void**)&P->d_vals32, sizeof(cf) * P->nd_vals));
+        vals32_kernel<<<grid, tb, 0, st>>>(P->d_vals, P->nd_vals, P->d_vals32);
+        HFMM_CUDA_TRY(cudaGetLastError());
+    }
+    HFMM_CUDA_TRY(cudaStreamSynchronize(st));
+    return HFMM_OK;
+}

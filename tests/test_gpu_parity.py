@@ -211,3 +211,47 @@ def test_full_size_workload_on_sampled_targets(cfg):
     y = plan.apply(torch.from_numpy(q).cuda()).cpu().numpy()[:, tgt]
     assert direct.rel_l2(y, yd) < 2 * w.tol
     plan.close()
+
+
+# --- mixed precision ------------------------------------------------------------
+
+MIXED_TOL = 1e-5
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_mixed_matches_fp64_and_oracle(name):
+    """FP32 expansions / near field with scaled FP32 translation matrices:
+    rel-l2 against the FP64 GPU path and against the CPU FMM <= 1e-5."""
+    from paper_1703_09136_gb300 import MIXED
+    F, parts = _oracle(name)
+    med, xy, q, tol, leaf, p = _case(name)
+    full = sum(parts.values())
+    plan = Plan(xy, med, tol=tol, leaf_size=leaf, p=p, max_rhs=q.shape[0], precision=MIXED)
+    y32 = plan.apply(torch.from_numpy(q.astype(np.complex64)).cuda()).cpu().numpy()
+    plan.close()
+    assert direct.rel_l2(y32, full) < MIXED_TOL, direct.rel_l2(y32, full)
+    for part in (1, 2, 4, 8):
+        plan = Plan(xy, med, tol=tol, leaf_size=leaf, p=p, max_rhs=q.shape[0], precision=MIXED)
+        yp = plan.apply(torch.from_numpy(q.astype(np.complex64)).cuda(), parts=part).cpu().numpy()
+        plan.close()
+        err = np.linalg.norm(yp - parts[part]) / np.linalg.norm(full)
+        assert err < MIXED_TOL, (part, err)
+
+
+def test_mixed_many_rhs_and_adjoint():
+    from paper_1703_09136_gb300 import MIXED
+    med, xy, q1, tol, leaf, p = _case("cfg4-small")
+    nrhs = 70                      # more than one 64-wide right-hand-side pass
+    q = W.strengths(4, xy.shape[0], nrhs, salt=8)
+    plan64 = Plan(xy, med, tol=tol, leaf_size=leaf, max_rhs=nrhs)
+    plan32 = Plan(xy, med, tol=tol, leaf_size=leaf, max_rhs=nrhs, precision=MIXED)
+    y64 = plan64.apply(torch.from_numpy(q).cuda()).cpu().numpy()
+    y32 = plan32.apply(torch.from_numpy(q.astype(np.complex64)).cuda()).cpu().numpy()
+    assert direct.rel_l2(y32, y64) < MIXED_TOL
+    v = W.strengths(4, xy.shape[0], nrhs, salt=9).astype(np.complex64)
+    w32 = plan32.adjoint(torch.from_numpy(v).cuda()).cpu().numpy()
+    lhs = np.vdot(v.astype(np.complex128), y32.astype(np.complex128))
+    rhs = np.vdot(w32.astype(np.complex128), q)
+    assert abs(lhs - rhs) < 1e-5 * abs(lhs)
+    plan64.close()
+    plan32.close()
