@@ -207,6 +207,40 @@ hfmm_status hfmm_plan_get_pairs(hfmm_plan_t plan, int32_t kind, int32_t level,
  */
 hfmm_status hfmm_plan_get_stage_times(hfmm_plan_t plan, double* ms);
 
+/*
+ * Leaf ordering that allocates nothing.  The paper has no counterpart: this
+ * is a service for callers that cannot let a library allocate device memory,
+ * e.g. an application that has reserved the GPU's memory for its own pool
+ * allocator, or one whose other streams must not be stalled by the implicit
+ * device synchronisation of cudaMalloc / cudaFree.
+ *
+ * Computes what hfmm_plan_create's tree build computes for `levels` leaf
+ * levels: the smallest bounding square of xy, the Morton index of every
+ * point's leaf, a stable sort by leaf, and the leaf ranges.
+ *   xy          device pointer, [n][2] doubles (x, y), all y > 0;
+ *   perm        device pointer, [n] int64 out: caller index of the i-th point
+ *               in leaf order (equal to hfmm_plan_get_tree's perm for a plan
+ *               built with the same leaf level);
+ *   leaf_begin  device pointer, [4^levels + 1] int32 out: the points of the
+ *               leaf with Morton index b are perm[leaf_begin[b] .. leaf_begin[b+1]).
+ * Limits: 1 <= n <= HFMM_NOALLOC_MAX_POINTS and 2 <= levels <=
+ * HFMM_NOALLOC_MAX_LEVELS; anything larger returns INVALID_ARG with a message
+ * naming the limit.  Non-finite coordinates or y <= 0 return INVALID_ARG
+ * (the call waits for `stream` to read that check back).
+ *
+ * All temporaries live in one static device array of about 6 MB that every
+ * GPU loading this library holds until the process exits.  The first call on
+ * a device looks up that array's device address (with that device current);
+ * make the first call before any stream capture.  Every call shares the
+ * array and it keeps the last call's contents: calls whose work overlaps on
+ * the GPU (other streams, other host threads) race and must be serialised by
+ * the caller.
+ */
+#define HFMM_NOALLOC_MAX_POINTS (1 << 18)
+#define HFMM_NOALLOC_MAX_LEVELS 9
+hfmm_status hfmm_leaf_order_noalloc(int64_t n, const double* xy, int32_t levels, int64_t* perm,
+                                    int32_t* leaf_begin, void* stream);
+
 /* Release the plan (NULL is accepted).  Synchronises the device. */
 hfmm_status hfmm_plan_destroy(hfmm_plan_t plan);
 

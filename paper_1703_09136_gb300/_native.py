@@ -19,7 +19,8 @@ STATUS = {0: "HFMM_OK", 1: "HFMM_ERR_INVALID_ARG", 2: "HFMM_ERR_UNSUPPORTED", 3:
 EXPORTS = ["hfmm_options_default", "hfmm_plan_create", "hfmm_apply", "hfmm_apply_parts",
            "hfmm_apply_adjoint", "hfmm_plan_get_info", "hfmm_plan_get_tree",
            "hfmm_plan_get_pairs", "hfmm_plan_destroy", "hfmm_status_string", "hfmm_last_error",
-           "hfmm_debug_bessel", "hfmm_plan_get_stage_times", "hfmm_debug_green_f32"]
+           "hfmm_debug_bessel", "hfmm_plan_get_stage_times", "hfmm_debug_green_f32",
+           "hfmm_leaf_order_noalloc"]
 NUM_STAGES = 8
 STAGES = ["gather", "p2m", "m2m", "down", "l2p", "p2p", "direct", "scatter"]
 FLAG_PROFILE = 1
@@ -82,10 +83,11 @@ def lib():
         L.hfmm_debug_bessel.argtypes = [dbl, i32, vp, vp]
         L.hfmm_plan_get_stage_times.argtypes = [hfmm_plan_t, vp]
         L.hfmm_debug_green_f32.argtypes = [i32, vp, vp]
+        L.hfmm_leaf_order_noalloc.argtypes = [i64, vp, i32, vp, vp, vp]
         for name in ("hfmm_plan_create", "hfmm_apply", "hfmm_apply_parts", "hfmm_apply_adjoint",
                      "hfmm_plan_get_info", "hfmm_plan_get_tree", "hfmm_plan_get_pairs",
                      "hfmm_plan_destroy", "hfmm_debug_bessel", "hfmm_plan_get_stage_times",
-                     "hfmm_debug_green_f32"):
+                     "hfmm_debug_green_f32", "hfmm_leaf_order_noalloc"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib

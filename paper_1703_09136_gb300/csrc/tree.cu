@@ -426,3 +426,158 @@ hfmm_status build_lists(hfmm_plan_s* P, cudaStream_t st) {
     HFMM_CUDA_TRY(cudaStreamSynchronize(st));
     return HFMM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Leaf ordering without allocation (hfmm_leaf_order_noalloc).
+//
+// Same computation as the plan's tree build (bounding square, Morton leaf
+// keys at level L, stable radix sort, leaf ranges), but every temporary lives
+// in one file-scope device array sized for HFMM_NOALLOC_MAX_POINTS points and
+// HFMM_NOALLOC_MAX_LEVELS levels, so the call never allocates.  The array is
+// shared by all calls on a device and keeps the previous call's contents.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr int64_t NA_MAXP = HFMM_NOALLOC_MAX_POINTS;
+constexpr int64_t NA_MAXLEAF = (int64_t)1 << (2 * HFMM_NOALLOC_MAX_LEVELS);
+constexpr int64_t NA_MAXCNT = (NA_MAXP > NA_MAXLEAF ? NA_MAXP : NA_MAXLEAF);
+constexpr int NA_BBOX_BLOCKS = 256;
+
+// byte offsets inside the scratch array (each a multiple of 256)
+constexpr size_t na_round(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t NA_OFF_PART = 0;                                              // double[4 * 256]
+constexpr size_t NA_OFF_PARAM = NA_OFF_PART + na_round(sizeof(double) * 4 * NA_BBOX_BLOCKS);
+constexpr size_t NA_OFF_KEY = NA_OFF_PARAM + 256;                              // params: x0, y0, scale, flag
+constexpr size_t NA_OFF_KEY2 = NA_OFF_KEY + na_round(sizeof(uint32_t) * NA_MAXP);
+constexpr size_t NA_OFF_VAL = NA_OFF_KEY2 + na_round(sizeof(uint32_t) * NA_MAXP);
+constexpr size_t NA_OFF_VAL2 = NA_OFF_VAL + na_round(sizeof(int32_t) * NA_MAXP);
+constexpr size_t NA_OFF_FLAG = NA_OFF_VAL2 + na_round(sizeof(int32_t) * NA_MAXP);
+constexpr size_t NA_OFF_POS = NA_OFF_FLAG + na_round(sizeof(int32_t) * (NA_MAXCNT + 1));
+constexpr size_t NA_OFF_TMP = NA_OFF_POS + na_round(sizeof(int32_t) * (NA_MAXCNT + 1));
+constexpr size_t NA_BYTES = NA_OFF_TMP + na_round(sizeof(int32_t) * (NA_MAXCNT / SCAN_BLOCK + 2));
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[64] = {};
+
+// Device address of the scratch array for the current device (looked up once
+// per device with that device current).
+hfmm_status noalloc_scratch(unsigned char** out) {
+    int dev = 0;
+    HFMM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) { hfmm_set_error("device ordinal %d out of range", dev); return HFMM_ERR_UNSUPPORTED; }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            hfmm_set_error("cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(e));
+            return HFMM_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = (unsigned char*)g_noalloc_addr[dev];
+    return HFMM_OK;
+}
+
+// reduce the bounding-box partials; param = {x0, y0, scale, flag}
+__global__ void na_bbox_finalize(const double* part, int nblk, uint32_t m, double* param) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double mnx = INFINITY, mny = INFINITY, mxx = -INFINITY, mxy = -INFINITY;
+    int bad = 0;
+    for (int b = 0; b < nblk; ++b) {
+        if (isnan(part[4 * b])) bad = 1;
+        mnx = fmin(mnx, part[4 * b]); mny = fmin(mny, part[4 * b + 1]);
+        mxx = fmax(mxx, part[4 * b + 2]); mxy = fmax(mxy, part[4 * b + 3]);
+    }
+    if (!bad && !(mny > 0.0)) bad = 2;
+    double S = fmax(mxx - mnx, mxy - mny);
+    if (!(S > 0.0)) S = 1.0;
+    param[0] = mnx;
+    param[1] = mny;
+    param[2] = (double)m / S;
+    param[3] = (double)bad;
+}
+
+__global__ void na_leaf_keys(const double* xy, int64_t n, const double* param, uint32_t mmax, uint32_t* key,
+                             int32_t* val) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x0 = param[0], y0 = param[1], scale = param[2];
+    double fx = floor((xy[2 * i] - x0) * scale);
+    double fy = floor((xy[2 * i + 1] - y0) * scale);
+    uint32_t ix = (uint32_t)fmin(fmax(fx, 0.0), (double)mmax);
+    uint32_t iy = (uint32_t)fmin(fmax(fy, 0.0), (double)mmax);
+    key[i] = morton(ix, iy);
+    val[i] = (int32_t)i;
+}
+
+__global__ void na_write_perm(const int32_t* val, int64_t n, int64_t* perm) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) perm[i] = val[i];
+}
+
+}  // namespace
+
+extern "C" hfmm_status hfmm_leaf_order_noalloc(int64_t n, const double* xy, int32_t levels, int64_t* perm,
+                                               int32_t* leaf_begin, void* stream) {
+    if (n < 1 || n > NA_MAXP) {
+        hfmm_set_error("hfmm_leaf_order_noalloc: n = %lld outside [1, %lld] (the size of its static scratch)",
+                       (long long)n, (long long)NA_MAXP);
+        return HFMM_ERR_INVALID_ARG;
+    }
+    if (levels < 2 || levels > HFMM_NOALLOC_MAX_LEVELS) {
+        hfmm_set_error("hfmm_leaf_order_noalloc: levels = %d outside [2, %d]", levels, HFMM_NOALLOC_MAX_LEVELS);
+        return HFMM_ERR_INVALID_ARG;
+    }
+    if (!xy || !perm || !leaf_begin) {
+        hfmm_set_error("hfmm_leaf_order_noalloc: null pointer");
+        return HFMM_ERR_INVALID_ARG;
+    }
+    unsigned char* base = nullptr;
+    HFMM_TRY(noalloc_scratch(&base));
+    cudaStream_t st = (cudaStream_t)stream;
+    double* part = (double*)(base + NA_OFF_PART);
+    double* param = (double*)(base + NA_OFF_PARAM);
+    uint32_t* key = (uint32_t*)(base + NA_OFF_KEY);
+    uint32_t* key2 = (uint32_t*)(base + NA_OFF_KEY2);
+    int32_t* val = (int32_t*)(base + NA_OFF_VAL);
+    int32_t* val2 = (int32_t*)(base + NA_OFF_VAL2);
+    int32_t* flag = (int32_t*)(base + NA_OFF_FLAG);
+    int32_t* pos = (int32_t*)(base + NA_OFF_POS);
+    int32_t* tmp = (int32_t*)(base + NA_OFF_TMP);
+    const int TB = 256;
+    const uint32_t m = 1u << levels;
+    const int64_t nleaf = (int64_t)1 << (2 * levels);
+    bbox_partial<<<NA_BBOX_BLOCKS, 256, 0, st>>>(xy, n, part);
+    na_bbox_finalize<<<1, 32, 0, st>>>(part, NA_BBOX_BLOCKS, m, param);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    double flag_h = 0.0;
+    HFMM_CUDA_TRY(cudaMemcpyAsync(&flag_h, param + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+    HFMM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (flag_h != 0.0) {
+        hfmm_set_error(flag_h == 1.0 ? "hfmm_leaf_order_noalloc: non-finite point coordinates"
+                                     : "hfmm_leaf_order_noalloc: all points must lie in the top layer y > 0");
+        return HFMM_ERR_INVALID_ARG;
+    }
+    na_leaf_keys<<<ceil_div(n, TB), TB, 0, st>>>(xy, n, param, m - 1, key, val);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    for (int bit = 0; bit < 2 * levels; ++bit) {
+        split_flags<<<ceil_div(n, TB), TB, 0, st>>>(key, n, bit, flag);
+        HFMM_TRY(exclusive_scan(flag, pos, n, tmp, st));
+        split_scatter<<<ceil_div(n, TB), TB, 0, st>>>(key, val, pos, n, bit, key2, val2);
+        HFMM_CUDA_TRY(cudaGetLastError());
+        std::swap(key, key2);
+        std::swap(val, val2);
+    }
+    // leaf counts start at zero on every call (the array keeps old contents)
+    HFMM_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int32_t) * nleaf, st));
+    leaf_histogram<<<ceil_div(n, TB), TB, 0, st>>>(key, n, flag);
+    HFMM_TRY(exclusive_scan(flag, leaf_begin, nleaf, tmp, st));
+    na_write_perm<<<ceil_div(n, TB), TB, 0, st>>>(val, n, perm);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    return HFMM_OK;
+}
