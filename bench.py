@@ -46,7 +46,9 @@ def parse():
     ap.add_argument("--config", type=int, default=4)
     ap.add_argument("--n", type=int, default=0, help="override the number of points")
     ap.add_argument("--nrhs", type=int, default=0, help="override the number of right-hand sides")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-fp64-check", action="store_true",
+                    help="skip the FP64 reference apply (accuracy and one-RHS FP64 time)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=0)
@@ -238,7 +240,7 @@ def run_ours(args):
         "metric": "H-FMM matvec throughput (targets x RHS per second), three-layer medium, N=1M, 64 RHS",
         "value": value, "unit": "Mtargets/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == FP64 else "mixed-f32", "data": "synthetic",
+        "dtype": "f64" if prec == FP64 else "f32", "data": "synthetic",
         "config": {"workload": w.name, "n": n, "nrhs": nrhs, "medium": "three-layer k=40/80/60 d=0.5",
                    "tol": w.tol, "levels": info["levels"], "p": info["p"], "plan_s": plan_s,
                    "l2": "inputs larger than L2 (q, y and expansions are GBs)",
@@ -252,6 +254,27 @@ def run_ours(args):
     ev1.record(stream)
     torch.cuda.synchronize()
     out["adjoint_ms"] = ev0.elapsed_time(ev1)
+    # accuracy against the plain FP64 path on the first right-hand sides, and
+    # the FP64 path's time for one right-hand side
+    if prec != FP64 and not args.no_fp64_check:
+        nchk = min(2, nrhs)
+        plan.apply(q, out=y)
+        y_mixed = y[:nchk].to(torch.complex128)
+        p64 = Plan(xy, w.medium, tol=w.tol, leaf_size=w.leaf, precision=FP64, max_rhs=nchk)
+        q64 = torch.from_numpy(q_h[:nchk].copy()).to(dev)
+        y64 = torch.empty_like(q64)
+        p64.apply(q64, out=y64)
+        err = float(torch.linalg.norm(y_mixed - y64) / torch.linalg.norm(y64))
+        q1 = q64[:1].contiguous()
+        y1 = torch.empty_like(q1)
+        p64.apply(q1, out=y1)
+        ev0.record(stream)
+        p64.apply(q1, out=y1)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        out["accuracy"] = {"rel_l2_vs_fp64": err, "rhs_compared": nchk}
+        out["fp64_one_rhs_ms"] = ev0.elapsed_time(ev1)
+        p64.close()
     if rank == 0 and not args.no_cpu_baseline:
         s = cpu_oracle_sample(cfg, nrhs, reps=2, n=args.cpu_sample_n)
         t_apply = min(s["apply_s"])

@@ -101,6 +101,8 @@ typedef struct {
 
 /* Option flags. */
 #define HFMM_FLAG_PROFILE 1     /* record CUDA events around every stage of each apply */
+#define HFMM_FLAG_SIMT_M2L 2    /* HFMM_MIXED: keep the downward pass on FP32 SIMT cores
+                                   instead of the tcgen05 tensor-core pass */
 
 /* Stages reported by hfmm_plan_get_stage_times (milliseconds of the last apply). */
 #define HFMM_STAGE_GATHER   0   /* caller order -> leaf order */
@@ -134,6 +136,8 @@ typedef struct {
     int64_t launches_last_apply;  /* kernels launched by the last apply call */
     double flops_last_apply[HFMM_NUM_STAGES];  /* algorithmic real flops per stage, last apply */
     double bytes_last_apply[HFMM_NUM_STAGES];  /* algorithmic DRAM bytes per stage, last apply */
+    int32_t device_error;       /* nonzero if a bounded device wait gave up (results invalid) */
+    int32_t tensor_levels;      /* levels whose downward pass runs on tcgen05 tensor cores */
 } hfmm_plan_info;
 
 /* Bits of `parts` in hfmm_apply_parts (sum of the selected terms). */

@@ -104,7 +104,7 @@ class Plan:
     """An H-FMM plan for fixed points: y = A q with A_ij = u_{x_j}(x_i)."""
 
     def __init__(self, xy, medium, tol=1e-6, p=0, leaf_size=32, levels=0, precision=FP64,
-                 max_rhs=1, stream=None, profile=False):
+                 max_rhs=1, stream=None, profile=False, simt_m2l=False):
         lib = _n.lib()
         m = Medium.of(medium)
         opts = _n.hfmm_options()
@@ -115,7 +115,7 @@ class Plan:
         opts.levels = int(levels)
         opts.precision = int(precision)
         opts.max_rhs = int(max_rhs)
-        opts.flags = _n.FLAG_PROFILE if profile else 0
+        opts.flags = (_n.FLAG_PROFILE if profile else 0) | (_n.FLAG_SIMT_M2L if simt_m2l else 0)
         torch = _torch()
         if torch is not None and isinstance(xy, torch.Tensor):
             if xy.dtype != torch.float64:

@@ -24,6 +24,7 @@ EXPORTS = ["hfmm_options_default", "hfmm_plan_create", "hfmm_apply", "hfmm_apply
 NUM_STAGES = 8
 STAGES = ["gather", "p2m", "m2m", "down", "l2p", "p2p", "direct", "scatter"]
 FLAG_PROFILE = 1
+FLAG_SIMT_M2L = 2
 
 
 class HfmmError(RuntimeError):
@@ -52,7 +53,8 @@ class hfmm_plan_info(ctypes.Structure):
                 ("table_bytes", ctypes.c_double), ("buffer_bytes", ctypes.c_double),
                 ("plan_ms", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("max_rhs", ctypes.c_int32), ("launches_last_apply", ctypes.c_int64),
-                ("flops_last_apply", ctypes.c_double * 8), ("bytes_last_apply", ctypes.c_double * 8)]
+                ("flops_last_apply", ctypes.c_double * 8), ("bytes_last_apply", ctypes.c_double * 8),
+                ("device_error", ctypes.c_int32), ("tensor_levels", ctypes.c_int32)]
 
 
 hfmm_plan_t = ctypes.c_void_p

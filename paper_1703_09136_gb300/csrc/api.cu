@@ -200,6 +200,8 @@ hfmm_status hfmm_plan_create(hfmm_plan_t* out, int64_t n, const double* xy, cons
         if (mixed) {
             if ((s = build_tables32(P, st)) != HFMM_OK) break;
             if ((s = init_h0_table(st)) != HFMM_OK) break;
+            if ((s = build_local_coords(P, st)) != HFMM_OK) break;
+            if (!(P->flags & HFMM_FLAG_SIMT_M2L) && (s = build_tc(P, st)) != HFMM_OK) break;
         }
         if (P->flags & HFMM_FLAG_PROFILE) {
             for (int sg = 0; sg < HFMM_NUM_STAGES && s == HFMM_OK; ++sg)
@@ -297,6 +299,12 @@ hfmm_status hfmm_plan_get_info(hfmm_plan_t P, hfmm_plan_info* info) {
     info->precision = P->precision;
     info->max_rhs = P->max_rhs;
     info->launches_last_apply = P->launches;
+    if (P->tc_err) {
+        int e = 0;
+        HFMM_CUDA_TRY(cudaMemcpy(&e, P->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+        info->device_error = e;
+    }
+    for (int l = 0; l <= P->L; ++l) info->tensor_levels += P->lev[l].tc_ntiles > 0 ? 1 : 0;
     for (int s = 0; s < HFMM_NUM_STAGES; ++s) {
         info->flops_last_apply[s] = P->st_flops[s];
         info->bytes_last_apply[s] = P->st_bytes[s];

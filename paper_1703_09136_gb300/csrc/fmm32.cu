@@ -169,16 +169,24 @@ __global__ void p2m32_kernel(const int32_t* lb, const double2* xs, const cf* qs,
 __global__ void m2m32_kernel(const cf* child, const cf* T, int pc, int pp, int nrhs, cf* parent) {
     const int64_t b = blockIdx.x;
     const int nc = 2 * pc + 1, np = 2 * pp + 1;
-    const int items = nrhs * np;
+    const int nq = (np + 3) / 4;            // groups of 4 parent coefficients
+    const int items = nrhs * nq;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int r = it / np, j = it % np;
-        cf acc = cfmk(0.f, 0.f);
+        const int r = it / nq, j0 = 4 * (it % nq);
+        const int nj = min(4, np - j0);
+        cf acc[4] = {cfmk(0.f, 0.f), cfmk(0.f, 0.f), cfmk(0.f, 0.f), cfmk(0.f, 0.f)};
         for (int c = 0; c < 4; ++c) {
             const cf* a = child + ((4 * b + c) * nrhs + r) * (int64_t)nc;
-            const cf* Tc = T + (int64_t)c * nc * np + j;
-            for (int m = 0; m < nc; ++m) cfma32(acc, a[m], Tc[(int64_t)m * np]);
+            const cf* Tc = T + (int64_t)c * nc * np + j0;
+            for (int m = 0; m < nc; ++m) {
+                const cf av = a[m];
+                const cf* Tm = Tc + (int64_t)m * np;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (u < nj) cfma32(acc[u], av, Tm[u]);
+            }
         }
-        parent[(b * nrhs + r) * (int64_t)np + j] = acc;
+        for (int u = 0; u < nj; ++u) parent[(b * nrhs + r) * (int64_t)np + j0 + u] = acc[u];
     }
 }
 
@@ -285,6 +293,122 @@ __global__ void l2p32_kernel(const int32_t* lb, const double2* xs, const cf* loc
             cf* yy = ys + (int64_t)r * n + c0 + t;
             yy->x += -0.25f * acc.y;
             yy->y += 0.25f * acc.x;
+        }
+    }
+}
+
+// point offsets from their own leaf centre, FP32 (near-field geometry without FP64)
+__global__ void local_coords_kernel(const int32_t* lb, const double2* xs, int64_t nleaf, double x0,
+                                    double y0, double h, float2* xl) {
+    const int64_t b = blockIdx.x;
+    if (b >= nleaf) return;
+    const double cx = x0 + (morton_x((uint32_t)b) + 0.5) * h;
+    const double cy = y0 + (morton_y((uint32_t)b) + 0.5) * h;
+    for (int32_t i = lb[b] + threadIdx.x; i < lb[b + 1]; i += blockDim.x)
+        xl[i] = make_float2((float)(xs[i].x - cx), (float)(xs[i].y - cy));
+}
+
+// P2P free-space part, FP32 (Algorithm 1, step 5): one CTA per non-empty
+// target leaf, 32 x 32 blocks of (i/4) H0 values in shared memory, source
+// strengths of 64 right-hand sides staged beside them, 2 targets x 4 RHS
+// accumulators per thread.
+constexpr int P2T = 32;            // targets / sources per block
+constexpr int P2R = 64;            // right-hand sides per pass
+constexpr int P2_THREADS = 256;
+
+__global__ void __launch_bounds__(P2_THREADS) p2p32b_kernel(const int32_t* lb, int L, const float2* xl,
+                                                            const cf* qs, int64_t n, int nrhs, float k,
+                                                            float h, cf* ys) {
+    __shared__ cf G[P2T][P2T + 1];
+    __shared__ cf Q[P2R][P2T + 1];
+    __shared__ float2 sp[P2T];
+    __shared__ float2 tp[P2T];
+    __shared__ float tj[H0_NI][H0_DEG + 1];
+    __shared__ float tr[H0_NI][H0_DEG + 1];
+    const int64_t b = blockIdx.x;
+    const int32_t tlo = lb[b], thi = lb[b + 1];
+    if (thi <= tlo) return;
+    for (int e = threadIdx.x; e < H0_NI * (H0_DEG + 1); e += blockDim.x) {
+        tj[e / (H0_DEG + 1)][e % (H0_DEG + 1)] = c_h0j[e / (H0_DEG + 1)][e % (H0_DEG + 1)];
+        tr[e / (H0_DEG + 1)][e % (H0_DEG + 1)] = c_h0r[e / (H0_DEG + 1)][e % (H0_DEG + 1)];
+    }
+    const int m = 1 << L;
+    const int ix = (int)morton_x((uint32_t)b), iy = (int)morton_y((uint32_t)b);
+    const int tpair = threadIdx.x & 15, rg = threadIdx.x >> 4;   // targets 2*tpair(+1), rhs 4*rg..4*rg+3
+    for (int r0 = 0; r0 < nrhs; r0 += P2R) {
+        const int nr = min(P2R, nrhs - r0);
+        for (int32_t t0 = tlo; t0 < thi; t0 += P2T) {
+            const int tn = min(P2T, thi - t0);
+            cf acc[2][4];
+            for (int a = 0; a < 2; ++a)
+                for (int c = 0; c < 4; ++c) acc[a][c] = cfmk(0.f, 0.f);
+            __syncthreads();
+            if (threadIdx.x < tn) tp[threadIdx.x] = xl[t0 + threadIdx.x];
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int sx = ix + dx, sy = iy + dy;
+                    if (sx < 0 || sy < 0 || sx >= m || sy >= m) continue;
+                    const uint32_t s = morton((uint32_t)sx, (uint32_t)sy);
+                    const int32_t slo = lb[s], shi = lb[s + 1];
+                    const float ox = (float)(-dx) * h, oy = (float)(-dy) * h;   // c_T - c_S
+                    for (int32_t s0 = slo; s0 < shi; s0 += P2T) {
+                        const int sn = min(P2T, shi - s0);
+                        __syncthreads();
+                        if (threadIdx.x < sn) sp[threadIdx.x] = xl[s0 + threadIdx.x];
+                        for (int e = threadIdx.x; e < P2R * P2T; e += blockDim.x) {
+                            const int rr = e / P2T, j = e % P2T;
+                            Q[rr][j] = (rr < nr && j < sn) ? qs[(int64_t)(r0 + rr) * n + s0 + j] : cfmk(0.f, 0.f);
+                        }
+                        __syncthreads();
+                        for (int e = threadIdx.x; e < P2T * P2T; e += blockDim.x) {
+                            const int i = e / P2T, j = e % P2T;
+                            cf g = cfmk(0.f, 0.f);
+                            if (i < tn && j < sn && (t0 + i) != (s0 + j)) {
+                                const float ddx = ox + (tp[i].x - sp[j].x);
+                                const float ddy = oy + (tp[i].y - sp[j].y);
+                                const float z = k * sqrtf(ddx * ddx + ddy * ddy);
+                                if (z < H0_ZMAX) {
+                                    const int iv = min((int)(z * H0_INV_DZ), H0_NI - 1);
+                                    const float t = (z - ((float)iv + 0.5f) / H0_INV_DZ) * (2.0f * H0_INV_DZ);
+                                    float jj = tj[iv][H0_DEG], rr2 = tr[iv][H0_DEG];
+#pragma unroll
+                                    for (int d = H0_DEG - 1; d >= 0; --d) {
+                                        jj = fmaf(jj, t, tj[iv][d]);
+                                        rr2 = fmaf(rr2, t, tr[iv][d]);
+                                    }
+                                    const float y = fmaf(0.63661977236758134f * logf(0.5f * z), jj, rr2);
+                                    g = cfmk(-0.25f * y, 0.25f * jj);
+                                } else {
+                                    cd h0 = hankel0((double)z);
+                                    g = cfmk((float)(-0.25 * h0.y), (float)(0.25 * h0.x));
+                                }
+                            }
+                            G[i][j] = g;
+                        }
+                        __syncthreads();
+#pragma unroll 4
+                        for (int j = 0; j < P2T; ++j) {
+                            const cf g0 = G[2 * tpair][j], g1 = G[2 * tpair + 1][j];
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                const cf qv = Q[4 * rg + c][j];
+                                cfma32(acc[0][c], g0, qv);
+                                cfma32(acc[1][c], g1, qv);
+                            }
+                        }
+                    }
+                }
+            for (int a = 0; a < 2; ++a) {
+                const int i = 2 * tpair + a;
+                if (i >= tn) continue;
+                for (int c = 0; c < 4; ++c) {
+                    const int rr = 4 * rg + c;
+                    if (rr >= nr) continue;
+                    cf* yy = ys + (int64_t)(r0 + rr) * n + t0 + i;
+                    yy->x += acc[a][c].x;
+                    yy->y += acc[a][c].y;
+                }
+            }
         }
     }
 }
@@ -407,6 +531,15 @@ hfmm_status init_h0_table(cudaStream_t st) {
     return HFMM_OK;
 }
 
+hfmm_status build_local_coords(hfmm_plan_s* P, cudaStream_t st) {
+    HFMM_TRY(plan_alloc(P, (void**)&P->xl32, sizeof(float2) * P->n));
+    const LevelInfo& lv = P->lev[P->L];
+    local_coords_kernel<<<(unsigned)lv.nbox, 128, 0, st>>>(P->leaf_begin, P->xy_sorted, lv.nbox, P->x0, P->y0, lv.h,
+                                                           P->xl32);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    return HFMM_OK;
+}
+
 extern "C" hfmm_status hfmm_debug_green_f32(int32_t n, const double* z, float* g) {
     if (n < 0 || (n > 0 && (!z || !g))) { hfmm_set_error("bad arguments"); return HFMM_ERR_INVALID_ARG; }
     if (!h0_ready) { fit_h0_table(); h0_ready = true; }
@@ -479,11 +612,16 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
             int rc = std::max(1, std::min(nrhs, (int)(32768 / (wmax * sizeof(cf)))));
             rc = std::max(1, std::min(rc, (8 * DOWN_THREADS) / lv.ncoef));
             const size_t sm = (size_t)rc * wmax * sizeof(cf);
-            down32_kernel<<<(unsigned)lv.nbox, DOWN_THREADS, sm, st>>>(
-                P->leaf_begin, L, l, P->lmin, nrhs, lv.p, has_parent ? P->lev[l - 1].p : 0,
-                has_parent ? P->lev[l - 1].loc32 : nullptr, has_parent ? P->lev[l - 1].t_l2l32 : nullptr,
-                lv.mult32, lv.nv ? lv.v_begin : nullptr, lv.v_src, lv.v_off, lv.t_free32,
-                lv.nr ? lv.r_begin : nullptr, lv.r_src, lv.r_tab, lv.t_react32, parts, rc, lv.loc32);
+            const bool all_far = (parts & HFMM_PART_FAR_FREE) && (parts & HFMM_PART_FAR_REACT);
+            if (lv.tc_ntiles > 0 && all_far) {
+                HFMM_TRY(launch_m2l_tc(P, l, nrhs, st));
+            } else {
+                down32_kernel<<<(unsigned)lv.nbox, DOWN_THREADS, sm, st>>>(
+                    P->leaf_begin, L, l, P->lmin, nrhs, lv.p, has_parent ? P->lev[l - 1].p : 0,
+                    has_parent ? P->lev[l - 1].loc32 : nullptr, has_parent ? P->lev[l - 1].t_l2l32 : nullptr,
+                    lv.mult32, lv.nv ? lv.v_begin : nullptr, lv.v_src, lv.v_off, lv.t_free32,
+                    lv.nr ? lv.r_begin : nullptr, lv.r_src, lv.r_tab, lv.t_react32, parts, rc, lv.loc32);
+            }
             ++P->launches;
             HFMM_CUDA_TRY(cudaGetLastError());
             double pairs = 0.0;
@@ -511,8 +649,8 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
     }
     if (parts & HFMM_PART_NEAR_FREE) {
         tm.begin(HFMM_STAGE_P2P);
-        p2p32_kernel<<<(unsigned)P->lev[L].nbox, P2P_THREADS, 0, st>>>(P->leaf_begin, L, P->xy_sorted, P->q32, n,
-                                                                       nrhs, P->k, P->y32);
+        p2p32b_kernel<<<(unsigned)P->lev[L].nbox, P2_THREADS, 0, st>>>(P->leaf_begin, L, P->xl32, P->q32, n, nrhs,
+                                                                       (float)P->k, (float)P->lev[L].h, P->y32);
         ++P->launches;
         HFMM_CUDA_TRY(cudaGetLastError());
         tm.end(HFMM_STAGE_P2P);

@@ -404,3 +404,271 @@ hfmm_status apply_fp64(hfmm_plan_s* P, int nrhs, const cd* q, cd* y, int parts, 
     P->last_stream = st;
     return HFMM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Field gradients (FP64) for position gradients of a loss through y = A(x) q.
+// For Z_n e^{in theta} of any cylinder function,
+//   (d/dx + i d/dy) Z_n e^{in th} = -k Z_{n+1} e^{i(n+1) th},
+//   (d/dx - i d/dy) Z_n e^{in th} =  k Z_{n-1} e^{i(n-1) th},
+// so the local expansion (i/4) sum_p b_p J_p(x - c) has
+//   d/dx = (i/4)(k/2) sum_p b_p (J_{p-1} - J_{p+1}),
+//   d/dy = (i/4)(i k/2) sum_p b_p (J_{p-1} + J_{p+1}),
+// and the free kernel d/dx (i/4) H0(k r) = (i/4)(-k H1(k r)) (x - x_j) / r.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Bx, By [2p+1]: gradient bases of one point; E scratch [2p+3], Jt [p+2]
+__device__ void point_basis_grad(double px, double py, double cx, double cy, double k, int p, double* Jt,
+                                 cd* E, cd* Bx, cd* By) {
+    const double dx = px - cx, dy = py - cy;
+    const double rho = hypot(dx, dy);
+    bessel_j_seq(k * rho, p + 1, Jt);
+    const double th = atan2(dy, dx);
+    const cd e1 = cexpi(th);
+    cd e = cmk(1.0, 0.0);
+    E[p + 1] = cmk(Jt[0], 0.0);                 // E[n + p + 1] = J_n(k rho) e^{i n th}
+    for (int m = 1; m <= p + 1; ++m) {
+        e = cmul(e, e1);
+        const double sg = (m & 1) ? -1.0 : 1.0;
+        E[p + 1 + m] = cscale(e, Jt[m]);
+        E[p + 1 - m] = cscale(cconj(e), sg * Jt[m]);
+    }
+    const cd cx_ = cmk(0.0, 0.125 * k);         // (i/4)(k/2)
+    const cd cy_ = cmk(-0.125 * k, 0.0);        // (i/4)(i k/2)
+    for (int q = -p; q <= p; ++q) {
+        const cd lo = E[p + 1 + q - 1], hi = E[p + 1 + q + 1];
+        Bx[q + p] = cmul(cx_, csub(lo, hi));
+        By[q + p] = cmul(cy_, cadd(lo, hi));
+    }
+}
+
+__global__ void l2p_grad_kernel(const int32_t* lb, const double2* xs, const cd* loc, int64_t n, int nrhs,
+                                double x0, double y0, double h, double k, int p, int chunk, cd* fx, cd* fy) {
+    extern __shared__ double smem[];
+    const int64_t b = blockIdx.x;
+    const int32_t lo = lb[b], hi = lb[b + 1];
+    if (hi <= lo) return;
+    const int nc = 2 * p + 1;
+    cd* Bx = (cd*)smem;
+    cd* By = Bx + (size_t)chunk * nc;
+    cd* E = By + (size_t)chunk * nc;
+    double* Jt = (double*)(E + (size_t)chunk * (nc + 2));
+    const double cx = x0 + (morton_x((uint32_t)b) + 0.5) * h;
+    const double cy = y0 + (morton_y((uint32_t)b) + 0.5) * h;
+    const cd* beta = loc + (int64_t)b * nrhs * nc;
+    for (int32_t c0 = lo; c0 < hi; c0 += chunk) {
+        const int cnt = min(chunk, hi - c0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+            const double2 pt = xs[c0 + t];
+            point_basis_grad(pt.x, pt.y, cx, cy, k, p, Jt + (size_t)t * (p + 2), E + (size_t)t * (nc + 2),
+                             Bx + (size_t)t * nc, By + (size_t)t * nc);
+        }
+        __syncthreads();
+        for (int it = threadIdx.x; it < nrhs * cnt; it += blockDim.x) {
+            const int r = it / cnt, t = it % cnt;
+            cd ax = cmk(0.0, 0.0), ay = cmk(0.0, 0.0);
+            const cd* br = beta + (int64_t)r * nc;
+            for (int m = 0; m < nc; ++m) {
+                cfma(ax, br[m], Bx[(size_t)t * nc + m]);
+                cfma(ay, br[m], By[(size_t)t * nc + m]);
+            }
+            const int64_t o = (int64_t)r * n + c0 + t;
+            fx[o] = cadd(fx[o], ax);
+            fy[o] = cadd(fy[o], ay);
+        }
+    }
+}
+
+constexpr int GPT = 32;
+__global__ void __launch_bounds__(256) p2p_grad_kernel(const int32_t* lb, int L, const double2* xs, const cd* qs,
+                                                       int64_t n, int nrhs, double k, cd* fx, cd* fy) {
+    __shared__ cd Gx[GPT][GPT + 1];
+    __shared__ cd Gy[GPT][GPT + 1];
+    __shared__ double2 sp[GPT];
+    __shared__ double2 tp[GPT];
+    const int64_t b = blockIdx.x;
+    const int32_t tlo = lb[b], thi = lb[b + 1];
+    if (thi <= tlo) return;
+    const int m = 1 << L;
+    const int ix = (int)morton_x((uint32_t)b), iy = (int)morton_y((uint32_t)b);
+    for (int32_t t0 = tlo; t0 < thi; t0 += GPT) {
+        const int tn = min(GPT, thi - t0);
+        __syncthreads();
+        if (threadIdx.x < tn) tp[threadIdx.x] = xs[t0 + threadIdx.x];
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int sx = ix + dx, sy = iy + dy;
+                if (sx < 0 || sy < 0 || sx >= m || sy >= m) continue;
+                const uint32_t s = morton((uint32_t)sx, (uint32_t)sy);
+                const int32_t slo = lb[s], shi = lb[s + 1];
+                for (int32_t s0 = slo; s0 < shi; s0 += GPT) {
+                    const int sn = min(GPT, shi - s0);
+                    __syncthreads();
+                    if (threadIdx.x < sn) sp[threadIdx.x] = xs[s0 + threadIdx.x];
+                    __syncthreads();
+                    for (int e = threadIdx.x; e < GPT * GPT; e += blockDim.x) {
+                        const int i = e / GPT, j = e % GPT;
+                        cd gx = cmk(0.0, 0.0), gy = cmk(0.0, 0.0);
+                        if (i < tn && j < sn && (t0 + i) != (s0 + j)) {
+                            const double ddx = tp[i].x - sp[j].x, ddy = tp[i].y - sp[j].y;
+                            const double r = hypot(ddx, ddy);
+                            cd h0, h1;
+                            hankel01(k * r, &h0, &h1);
+                            const cd c = cscale(cmuli(h1), -0.25 * k / r);   // (i/4)(-k H1) / r
+                            gx = cscale(c, ddx);
+                            gy = cscale(c, ddy);
+                        }
+                        Gx[i][j] = gx;
+                        Gy[i][j] = gy;
+                    }
+                    __syncthreads();
+                    for (int it = threadIdx.x; it < nrhs * GPT; it += blockDim.x) {
+                        const int rr = it / GPT, i = it % GPT;
+                        if (i >= tn) continue;
+                        const cd* qr = qs + (int64_t)rr * n + s0;
+                        cd ax = cmk(0.0, 0.0), ay = cmk(0.0, 0.0);
+                        for (int j = 0; j < sn; ++j) {
+                            cfma(ax, Gx[i][j], qr[j]);
+                            cfma(ay, Gy[i][j], qr[j]);
+                        }
+                        const int64_t o = (int64_t)rr * n + t0 + i;
+                        fx[o] = cadd(fx[o], ax);
+                        fy[o] = cadd(fy[o], ay);
+                    }
+                }
+            }
+    }
+}
+
+__global__ void direct_grad_kernel(const int32_t* lb, const int32_t* d_begin, const int32_t* d_src,
+                                   const int64_t* d_blk, const cd* gvx, const cd* gvy, const cd* qs, int64_t n,
+                                   int nrhs, cd* fx, cd* fy) {
+    const int64_t b = blockIdx.x;
+    const int32_t e0 = d_begin[b], e1 = d_begin[b + 1];
+    if (e1 <= e0) return;
+    const int32_t tlo = lb[b], tn = lb[b + 1] - tlo;
+    for (int it = threadIdx.x; it < nrhs * tn; it += blockDim.x) {
+        const int r = it / tn, i = it % tn;
+        cd ax = cmk(0.0, 0.0), ay = cmk(0.0, 0.0);
+        for (int32_t e = e0; e < e1; ++e) {
+            const int32_t s = d_src[e];
+            const int32_t slo = lb[s], sn = lb[s + 1] - slo;
+            const int64_t o = d_blk[e] + (int64_t)i * sn;
+            const cd* qr = qs + (int64_t)r * n + slo;
+            for (int j = 0; j < sn; ++j) {
+                cfma(ax, gvx[o + j], qr[j]);
+                cfma(ay, gvy[o + j], qr[j]);
+            }
+        }
+        const int64_t o = (int64_t)r * n + tlo + i;
+        fx[o] = cadd(fx[o], ax);
+        fy[o] = cadd(fy[o], ay);
+    }
+}
+
+// gxy[perm[i]] = Re sum_r conj(g) d u + q d w  (sorted inputs)
+__global__ void grad_combine_kernel(const cd* qs, const cd* gs_conj, const cd* ux, const cd* uy, const cd* wx,
+                                    const cd* wy, const int64_t* perm, int64_t n, int nrhs, double* gxy) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double ax = 0.0, ay = 0.0;
+    for (int r = 0; r < nrhs; ++r) {
+        const int64_t o = (int64_t)r * n + i;
+        const cd g = gs_conj[o];             // conj(g) in sorted order
+        const cd q = qs[o];
+        ax += cmul(g, ux[o]).x + cmul(q, wx[o]).x;
+        ay += cmul(g, uy[o]).x + cmul(q, wy[o]).x;
+    }
+    const int64_t j = perm[i];
+    gxy[2 * j] = ax;
+    gxy[2 * j + 1] = ay;
+}
+
+int pick_chunk_grad(int p) {
+    const int nc = 2 * p + 1;
+    int c = (int)(40000 / ((3 * nc + 2) * 16 + (p + 2) * 8));
+    return std::max(1, std::min(32, c));
+}
+
+// Field gradient of v (already in sorted order in P->q_sorted) into fx, fy.
+hfmm_status field_grad_fp64(hfmm_plan_s* P, int nrhs, cd* fx, cd* fy, cudaStream_t st) {
+    const int64_t n = P->n;
+    const int L = P->L;
+    HFMM_CUDA_TRY(cudaMemsetAsync(fx, 0, sizeof(cd) * n * nrhs, st));
+    HFMM_CUDA_TRY(cudaMemsetAsync(fy, 0, sizeof(cd) * n * nrhs, st));
+    {
+        LevelInfo& lv = P->lev[L];
+        const int chunk = pick_chunk(lv.p);
+        const size_t sm = (size_t)chunk * ((2 * lv.p + 1) * sizeof(cd) + (lv.p + 1) * sizeof(double));
+        p2m_kernel<<<(unsigned)lv.nbox, TB, sm, st>>>(P->leaf_begin, P->xy_sorted, P->q_sorted, n, nrhs, P->x0,
+                                                     P->y0, lv.h, L, P->k, lv.p, chunk, lv.mult);
+        HFMM_CUDA_TRY(cudaGetLastError());
+    }
+    for (int l = L - 1; l >= P->lmin; --l) {
+        LevelInfo& lv = P->lev[l];
+        m2m_kernel<<<(unsigned)lv.nbox, TB, 0, st>>>(P->lev[l + 1].mult, lv.t_m2m, P->lev[l + 1].p, lv.p, nrhs, lv.mult);
+        HFMM_CUDA_TRY(cudaGetLastError());
+    }
+    for (int l = P->lmin; l <= L; ++l) {
+        LevelInfo& lv = P->lev[l];
+        const bool has_parent = l > P->lmin;
+        downward_kernel<<<(unsigned)lv.nbox, TB, 0, st>>>(
+            P->leaf_begin, L, l, P->lmin, nrhs, lv.p, has_parent ? P->lev[l - 1].p : 0,
+            has_parent ? P->lev[l - 1].loc : nullptr, has_parent ? P->lev[l - 1].t_l2l : nullptr, lv.mult,
+            lv.nv ? lv.v_begin : nullptr, lv.v_src, lv.v_off, lv.t_free, lv.nr ? lv.r_begin : nullptr, lv.r_src,
+            lv.r_tab, lv.t_react, HFMM_PART_ALL, lv.loc);
+        HFMM_CUDA_TRY(cudaGetLastError());
+    }
+    {
+        LevelInfo& lv = P->lev[L];
+        const int chunk = pick_chunk_grad(lv.p);
+        const int nc = 2 * lv.p + 1;
+        const size_t sm = (size_t)chunk * ((3 * nc + 2) * sizeof(cd) + (lv.p + 2) * sizeof(double));
+        l2p_grad_kernel<<<(unsigned)lv.nbox, TB, sm, st>>>(P->leaf_begin, P->xy_sorted, lv.loc, n, nrhs, P->x0,
+                                                          P->y0, lv.h, P->k, lv.p, chunk, fx, fy);
+        HFMM_CUDA_TRY(cudaGetLastError());
+    }
+    p2p_grad_kernel<<<(unsigned)P->lev[L].nbox, 256, 0, st>>>(P->leaf_begin, L, P->xy_sorted, P->q_sorted, n, nrhs,
+                                                              P->k, fx, fy);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    if (P->nd > 0) {
+        direct_grad_kernel<<<(unsigned)P->lev[L].nbox, TB, 0, st>>>(P->leaf_begin, P->d_begin, P->d_src, P->d_blk,
+                                                                    P->d_gvals, P->d_gvals + P->nd_vals,
+                                                                    P->q_sorted, n, nrhs, fx, fy);
+        HFMM_CUDA_TRY(cudaGetLastError());
+    }
+    return HFMM_OK;
+}
+
+}  // namespace
+
+hfmm_status apply_grad_fp64(hfmm_plan_s* P, int nrhs, const cd* q, const cd* g, double* gxy, cudaStream_t st) {
+    const int64_t n = P->n;
+    const int nb = ceil_div(n, 256);
+    const size_t bytes = sizeof(cd) * (size_t)n * P->max_rhs;
+    if (!P->grad_buf) {
+        HFMM_TRY(plan_alloc(P, (void**)&P->grad_buf, 5 * bytes));
+        HFMM_TRY(build_direct_grad(P, st));
+    }
+    cd* ux = P->grad_buf;
+    cd* uy = ux + (size_t)n * P->max_rhs;
+    cd* wx = uy + (size_t)n * P->max_rhs;
+    cd* wy = wx + (size_t)n * P->max_rhs;
+    cd* gsc = wy + (size_t)n * P->max_rhs;
+    // u = field of q
+    gather_q<<<nb, 256, 0, st>>>(q, P->perm, n, nrhs, false, P->q_sorted);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    HFMM_TRY(field_grad_fp64(P, nrhs, ux, uy, st));
+    // w = field of conj(g)
+    gather_q<<<nb, 256, 0, st>>>(g, P->perm, n, nrhs, true, gsc);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    gather_q<<<nb, 256, 0, st>>>(g, P->perm, n, nrhs, true, P->q_sorted);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    HFMM_TRY(field_grad_fp64(P, nrhs, wx, wy, st));
+    // sorted q again for the combination
+    gather_q<<<nb, 256, 0, st>>>(q, P->perm, n, nrhs, false, P->q_sorted);
+    grad_combine_kernel<<<nb, 256, 0, st>>>(P->q_sorted, gsc, ux, uy, wx, wy, P->perm, n, nrhs, gxy);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    return HFMM_OK;
+}

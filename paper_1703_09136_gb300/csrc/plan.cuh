@@ -53,6 +53,15 @@ struct LevelInfo {
     cf* t_m2m32 = nullptr;        // [4][m child][j parent]   (this level = parent)
     cf* t_l2l32 = nullptr;        // [4][n parent][m child]   (this level = parent)
     double* d_log_s = nullptr;    // [p + 1] log s(n) on the device
+    // tensor-core downward pass (m2l_tc.cu): real GEMM width, K chunks, pre-split
+    // TF32 operator chunks, target-pair tiles and their source steps
+    int tc_np = 0, tc_kc = 0, tc_kc2 = 0;
+    float* tc_bfree = nullptr;
+    float* tc_breact = nullptr;
+    float* tc_bl2l = nullptr;
+    void* tc_tiles = nullptr;
+    void* tc_steps = nullptr;
+    int64_t tc_ntiles = 0;
 };
 
 struct hfmm_plan_s {
@@ -91,6 +100,15 @@ struct hfmm_plan_s {
     cf* q32 = nullptr;              // [max_rhs][n]
     cf* y32 = nullptr;
     cf* d_vals32 = nullptr;
+    float2* xl32 = nullptr;         // [n] point offsets from their own leaf centre (FP32)
+    // position gradients (FP64): field-gradient buffers and d/dX, d/dY of the
+    // directly summed reaction blocks
+    cd* grad_buf = nullptr;         // [5][max_rhs][n]
+    cd* d_gvals = nullptr;          // [2][nd_vals]
+    void* dj_jobs = nullptr;        // direct-block quadrature jobs and segments (tables.cu)
+    void* dj_segs = nullptr;
+    int64_t dj_njobs = 0;
+    int* tc_err = nullptr;          // set by the tensor-core pass when a bounded wait gave up
 
     // info
     int64_t u_pairs = 0;
@@ -132,6 +150,8 @@ hfmm_status build_lists(hfmm_plan_s* P, cudaStream_t st);
 // tables.cu
 hfmm_status build_tables(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status build_tables32(hfmm_plan_s* P, cudaStream_t st);
+hfmm_status build_direct_grad(hfmm_plan_s* P, cudaStream_t st);
+hfmm_status apply_grad_fp64(hfmm_plan_s* P, int nrhs, const cd* q, const cd* g, double* gxy, cudaStream_t st);
 // fmm64.cu
 hfmm_status apply_fp64(hfmm_plan_s* P, int nrhs, const cd* q, cd* y, int parts, bool adjoint,
                        cudaStream_t st);
@@ -139,6 +159,10 @@ hfmm_status apply_fp64(hfmm_plan_s* P, int nrhs, const cd* q, cd* y, int parts, 
 hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts, bool adjoint,
                         cudaStream_t st);
 hfmm_status init_h0_table(cudaStream_t st);
+hfmm_status build_local_coords(hfmm_plan_s* P, cudaStream_t st);
+// m2l_tc.cu
+hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st);
+hfmm_status launch_m2l_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st);
 
 // Morton helpers
 HD uint32_t spread_bits(uint32_t v) {

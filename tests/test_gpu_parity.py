@@ -255,3 +255,25 @@ def test_mixed_many_rhs_and_adjoint():
     assert abs(lhs - rhs) < 1e-5 * abs(lhs)
     plan64.close()
     plan32.close()
+
+
+def test_tensor_core_downward_pass_matches_simt_and_fp64():
+    """tcgen05 3xTF32 downward pass against the FP32 SIMT pass (same plan
+    otherwise) and against the FP64 path, 64 right-hand sides (one full
+    M = 128 tile of two target boxes)."""
+    from paper_1703_09136_gb300 import MIXED
+    xy = W.points_in_box(4, 8192, ((0.0, 1.0), (0.02, 1.02)))
+    q = W.strengths(4, 8192, 64, salt=3)
+    q32 = torch.from_numpy(q.astype(np.complex64)).cuda()
+    tc = Plan(xy, CFG4_MED, tol=1e-6, leaf_size=16, max_rhs=64, precision=MIXED)
+    si = Plan(xy, CFG4_MED, tol=1e-6, leaf_size=16, max_rhs=64, precision=MIXED, simt_m2l=True)
+    f64 = Plan(xy, CFG4_MED, tol=1e-6, leaf_size=16, max_rhs=4)
+    assert tc.info["tensor_levels"] >= 2 and si.info["tensor_levels"] == 0
+    y_tc = tc.apply(q32).cpu().numpy()
+    y_si = si.apply(q32).cpu().numpy()
+    y64 = f64.apply(torch.from_numpy(q[:4].copy()).cuda()).cpu().numpy()
+    assert tc.info["device_error"] == 0
+    assert direct.rel_l2(y_tc, y_si) < 2e-6
+    assert direct.rel_l2(y_tc[:4], y64) < MIXED_TOL
+    for p in (tc, si, f64):
+        p.close()

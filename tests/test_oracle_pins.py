@@ -348,3 +348,43 @@ def test_error_decay_has_the_order_of_table_1():
             errs.append(e)
             assert row[col] / 300 < e < row[col] * 300, (k, p, e, row[col])
         assert errs[0] / errs[2] > 10 ** 4.5
+
+
+# --- gradients ------------------------------------------------------------------
+
+@pytest.mark.parametrize("med", [Medium(IMP, (20.0,), alpha=10.0), Medium(THREE, (15.0, 30.0, 22.5), d=0.2)])
+def test_field_gradient_matches_finite_differences(med):
+    xy = W.points_in_box(1, 40, ((0.0, 0.6), (0.05, 0.65)))
+    q = W.strengths(1, 40, 1, salt=4)
+    targets = np.array([[0.33, 0.21], [0.05, 0.6]])
+    gx = direct.free_field_grad(targets, xy, q, med.k1)[0] + direct.reaction_field_grad(med, targets, xy, q)[0]
+    gy = direct.free_field_grad(targets, xy, q, med.k1)[1] + direct.reaction_field_grad(med, targets, xy, q)[1]
+    h = 1e-5
+    def u(t):
+        return direct.free_sum(t, xy, q, med.k1) + direct.reaction_sum(med, t, xy, q)
+    for d, g in ((0, gx), (1, gy)):
+        e = np.zeros(2)
+        e[d] = h
+        fd = (u(targets + e) - u(targets - e)) / (2 * h)
+        assert np.max(np.abs(fd - g)) < 1e-6 * np.max(np.abs(g))
+
+
+def test_position_gradient_of_the_loss_matches_finite_differences():
+    """L(x) = sum |G(x) q - y_obs|^2; the reciprocity-based formula against
+    central differences of the direct sum (self terms included)."""
+    med = Medium(IMP, (20.0,), alpha=10.0)
+    xy = W.points_in_box(5, 30, ((0.0, 0.5), (0.05, 0.55)))
+    q = W.strengths(5, 30, 2, salt=1)
+    y_obs = direct.direct_apply(med, W.perturb(5, xy, 1e-3), q)
+    def loss(z):
+        r = direct.direct_apply(med, z, q) - y_obs
+        return float(np.sum(np.abs(r) ** 2))
+    r = direct.direct_apply(med, xy, q) - y_obs
+    G = direct.position_grad(med, xy, q, 2.0 * r)      # g = dL/dRe y + i dL/dIm y = 2 r
+    h = 1e-6
+    for j in (0, 7, 29):
+        for d in (0, 1):
+            zp = xy.copy(); zp[j, d] += h
+            zm = xy.copy(); zm[j, d] -= h
+            fd = (loss(zp) - loss(zm)) / (2 * h)
+            assert abs(fd - G[j, d]) < 1e-5 * max(1.0, abs(G[j, d]))
