@@ -182,6 +182,24 @@ hfmm_status hfmm_apply_parts(hfmm_plan_t plan, int32_t nrhs, const void* q, void
  */
 hfmm_status hfmm_apply_adjoint(hfmm_plan_t plan, int32_t nrhs, const void* v, void* w, void* stream);
 
+/*
+ * Position gradient of a real loss L(y), y = A(x) q, through the matrix of
+ * Sec. 2.4 (A_ij = u_{x_j}(x_i)).  Given g = dL/dRe(y) + i dL/dIm(y)
+ * ([nrhs][n] complex, caller order) writes gxy[2j], gxy[2j+1] = dL/dx_j, dL/dy_j:
+ *     dL/dx_j = Re sum_r [ conj(g_rj) grad u_r(x_j) + q_rj grad w_r(x_j) ],
+ *     u_r = sum_k G(., x_k) q_rk,   w_r = sum_k G(., x_k) conj(g_rk),
+ * which uses the reciprocity G(a, b) = G(b, a) of the domain Green's function.
+ * Field gradients come from the derivative of the local expansion
+ * ((d/dx +- i d/dy) J_p e^{ip theta} = -+k J_{p+-1} e^{i(p+-1) theta}), of the
+ * free-space kernel ((i/4)(-k H1(kr)) (x - x_j)/r) and of the Sommerfeld
+ * integrand (factors i lambda and -s1) for directly summed reaction pairs.
+ * Strength gradients are hfmm_apply_adjoint(g).  q, g: complex128; gxy: [n][2]
+ * doubles; host or device pointers.  HFMM_FP64 plans only (UNSUPPORTED for
+ * HFMM_MIXED).
+ */
+hfmm_status hfmm_apply_grad(hfmm_plan_t plan, int32_t nrhs, const void* q, const void* g, double* gxy,
+                            void* stream);
+
 /* Fill *info (host pointer). */
 hfmm_status hfmm_plan_get_info(hfmm_plan_t plan, hfmm_plan_info* info);
 

@@ -182,6 +182,28 @@ class Plan:
         """w = A^H v."""
         return self._run(_n.lib().hfmm_apply_adjoint, v, out, stream)
 
+    def grad(self, q, g, out=None, stream=None):
+        """dL/dx_j, dL/dy_j ([n, 2] float64) of a real loss of y = A q, given
+        g = dL/dRe(y) + i dL/dIm(y) (hfmm_apply_grad)."""
+        torch = _torch()
+        is_t = torch is not None and isinstance(q, torch.Tensor)
+        if is_t:
+            q = q.contiguous()
+            g = g.contiguous().to(q.dtype)
+            if out is None:
+                out = torch.empty((self.n, 2), dtype=torch.float64, device=q.device)
+        else:
+            q = np.ascontiguousarray(q, dtype=np.complex128)
+            g = np.ascontiguousarray(g, dtype=np.complex128)
+            if out is None:
+                out = np.empty((self.n, 2), dtype=np.float64)
+        nrhs = 1 if q.ndim == 1 else int(np.prod(q.shape[:-1]))
+        qp, kq = _ptr(q)
+        gp, kg = _ptr(g)
+        op, ko = _ptr(out)
+        _n.check(_n.lib().hfmm_apply_grad(self._h, ctypes.c_int32(nrhs), qp, gp, op, _stream_handle(stream)))
+        return out
+
     # ------------------------------------------------------------------
     @property
     def info(self):
@@ -239,3 +261,44 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+def matvec(xy, q, medium, **plan_options):
+    """Differentiable y = A(xy) q (torch tensors on one CUDA device).
+
+    Builds a plan for the positions, applies it, and in backward returns
+    A^H g for q (hfmm_apply_adjoint) and the position gradient of
+    hfmm_apply_grad for xy.  FP64 plans (complex128 q) support both
+    gradients; plan_options are passed to Plan (tol, leaf_size, ...)."""
+    return _MatvecFn.apply(xy, q, medium, plan_options)
+
+
+def _make_fn():
+    torch = _torch()
+    if torch is None:  # pragma: no cover
+        return None
+
+    class MatvecFn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, xy, q, medium, opts):
+            nrhs = 1 if q.dim() == 1 else int(np.prod(q.shape[:-1]))
+            plan = Plan(xy.detach().contiguous(), medium, max_rhs=max(nrhs, 1), **opts)
+            y = plan.apply(q.detach().contiguous())
+            ctx.plan = plan
+            ctx.save_for_backward(q.detach())
+            return y
+
+        @staticmethod
+        def backward(ctx, gy):
+            (q,) = ctx.saved_tensors
+            plan = ctx.plan
+            gy = gy.contiguous()
+            gq = plan.adjoint(gy) if ctx.needs_input_grad[1] else None
+            gxy = plan.grad(q, gy) if ctx.needs_input_grad[0] else None
+            plan.close()
+            return gxy, gq, None, None
+
+    return MatvecFn
+
+
+_MatvecFn = _make_fn()

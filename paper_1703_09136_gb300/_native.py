@@ -20,7 +20,7 @@ EXPORTS = ["hfmm_options_default", "hfmm_plan_create", "hfmm_apply", "hfmm_apply
            "hfmm_apply_adjoint", "hfmm_plan_get_info", "hfmm_plan_get_tree",
            "hfmm_plan_get_pairs", "hfmm_plan_destroy", "hfmm_status_string", "hfmm_last_error",
            "hfmm_debug_bessel", "hfmm_plan_get_stage_times", "hfmm_debug_green_f32",
-           "hfmm_leaf_order_noalloc"]
+           "hfmm_leaf_order_noalloc", "hfmm_apply_grad"]
 NUM_STAGES = 8
 STAGES = ["gather", "p2m", "m2m", "down", "l2p", "p2p", "direct", "scatter"]
 FLAG_PROFILE = 1
@@ -86,10 +86,11 @@ def lib():
         L.hfmm_plan_get_stage_times.argtypes = [hfmm_plan_t, vp]
         L.hfmm_debug_green_f32.argtypes = [i32, vp, vp]
         L.hfmm_leaf_order_noalloc.argtypes = [i64, vp, i32, vp, vp, vp]
+        L.hfmm_apply_grad.argtypes = [hfmm_plan_t, i32, vp, vp, vp, vp]
         for name in ("hfmm_plan_create", "hfmm_apply", "hfmm_apply_parts", "hfmm_apply_adjoint",
                      "hfmm_plan_get_info", "hfmm_plan_get_tree", "hfmm_plan_get_pairs",
                      "hfmm_plan_destroy", "hfmm_debug_bessel", "hfmm_plan_get_stage_times",
-                     "hfmm_debug_green_f32", "hfmm_leaf_order_noalloc"):
+                     "hfmm_debug_green_f32", "hfmm_leaf_order_noalloc", "hfmm_apply_grad"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib

@@ -278,6 +278,44 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t plan, int32_t nrhs, const void* v, vo
     return apply_common(plan, nrhs, v, w, HFMM_PART_ALL, true, stream);
 }
 
+hfmm_status hfmm_apply_grad(hfmm_plan_t P, int32_t nrhs, const void* q, const void* g, double* gxy,
+                            void* stream) {
+    if (!P) { hfmm_set_error("plan is NULL"); return HFMM_ERR_INVALID_ARG; }
+    if (P->precision != HFMM_FP64) {
+        hfmm_set_error("hfmm_apply_grad needs an HFMM_FP64 plan");
+        return HFMM_ERR_UNSUPPORTED;
+    }
+    if (nrhs < 1 || nrhs > P->max_rhs) {
+        hfmm_set_error("nrhs must be in [1, max_rhs=%d] (got %d)", P->max_rhs, nrhs);
+        return HFMM_ERR_INVALID_ARG;
+    }
+    if (!q || !g || !gxy) { hfmm_set_error("q, g or gxy is NULL"); return HFMM_ERR_INVALID_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = sizeof(cd) * (size_t)P->n * nrhs;
+    const bool qd = is_device_ptr(q), gd = is_device_ptr(g), od = is_device_ptr(gxy);
+    const cd* dq = (const cd*)q;
+    const cd* dg = (const cd*)g;
+    double* dout = gxy;
+    if (!qd) {
+        if (!P->io_q) HFMM_TRY(plan_alloc(P, (void**)&P->io_q, sizeof(cd) * (size_t)P->n * P->max_rhs));
+        HFMM_CUDA_TRY(cudaMemcpyAsync(P->io_q, q, bytes, cudaMemcpyHostToDevice, st));
+        dq = P->io_q;
+    }
+    if (!gd) {
+        if (!P->io_y) HFMM_TRY(plan_alloc(P, (void**)&P->io_y, sizeof(cd) * (size_t)P->n * P->max_rhs));
+        HFMM_CUDA_TRY(cudaMemcpyAsync(P->io_y, g, bytes, cudaMemcpyHostToDevice, st));
+        dg = P->io_y;
+    }
+    if (!od) {
+        if (!P->io_gxy) HFMM_TRY(plan_alloc(P, (void**)&P->io_gxy, sizeof(double) * 2 * (size_t)P->n));
+        dout = P->io_gxy;
+    }
+    HFMM_TRY(apply_grad_fp64(P, nrhs, dq, dg, dout, st));
+    if (!od) HFMM_CUDA_TRY(cudaMemcpyAsync(gxy, dout, sizeof(double) * 2 * (size_t)P->n, cudaMemcpyDeviceToHost, st));
+    if (!qd || !gd || !od) HFMM_CUDA_TRY(cudaStreamSynchronize(st));
+    return HFMM_OK;
+}
+
 hfmm_status hfmm_plan_get_info(hfmm_plan_t P, hfmm_plan_info* info) {
     if (!P || !info) { hfmm_set_error("plan or info is NULL"); return HFMM_ERR_INVALID_ARG; }
     std::memset(info, 0, sizeof(*info));

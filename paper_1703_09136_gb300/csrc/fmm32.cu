@@ -603,6 +603,10 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
         }
         tm.end(HFMM_STAGE_M2M);
         tm.begin(HFMM_STAGE_DOWN);
+        const bool all_far = (parts & HFMM_PART_FAR_FREE) && (parts & HFMM_PART_FAR_REACT);
+        if (all_far)
+            for (int l = P->lmin; l <= L; ++l)
+                if (P->lev[l].tc_ntiles > 0) { HFMM_TRY(split_mult_tc(P, l, nrhs, st)); ++P->launches; }
         for (int l = P->lmin; l <= L; ++l) {
             LevelInfo& lv = P->lev[l];
             const bool has_parent = l > P->lmin;
@@ -612,7 +616,6 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
             int rc = std::max(1, std::min(nrhs, (int)(32768 / (wmax * sizeof(cf)))));
             rc = std::max(1, std::min(rc, (8 * DOWN_THREADS) / lv.ncoef));
             const size_t sm = (size_t)rc * wmax * sizeof(cf);
-            const bool all_far = (parts & HFMM_PART_FAR_FREE) && (parts & HFMM_PART_FAR_REACT);
             if (lv.tc_ntiles > 0 && all_far) {
                 HFMM_TRY(launch_m2l_tc(P, l, nrhs, st));
             } else {

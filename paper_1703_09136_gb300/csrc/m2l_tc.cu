@@ -13,12 +13,17 @@
 // B = [[Re M, -Im M], [Im M, Re M]] blocks.  FP32 accuracy comes from three
 // TF32 products per term (hi*hi + hi*lo + lo*hi, x = hi + lo).
 //
-// Pipeline (one CTA = one target pair x 64 right-hand sides): warps 0-3 gather
-// and split A chunks (16 values of K per row) into shared memory; thread 0
-// also bulk-copies (cp.async.bulk) the matching pre-split B chunk; warp 4
-// issues tcgen05.mma into a TMEM accumulator and releases stages with
-// tcgen05.commit; warps 0-3 read the result with tcgen05.ld.  Every mbarrier
-// wait is bounded; a timeout sets an error flag instead of hanging.
+// Operands are stored MMA-ready (pre-split TF32 hi / lo, core-matrix layout):
+// the multipoles of the level and the parent's local expansions are copied
+// into that form after they are produced, the operators at plan time.
+// Pipeline (one CTA = one target pair x 64 right-hand sides): warp 4 streams
+// every K chunk with cp.async.bulk (two 64-row A halves per part plus the
+// operator chunk) into a 4-stage shared-memory ring; warp 5 issues
+// tcgen05.mma into one of two TMEM buffers per source step; warps 0-3 drain
+// each finished step with tcgen05.ld into round-to-nearest FP32 registers
+// (tensor-core accumulation truncates, so long chains in TMEM lose accuracy)
+// and write the local coefficients.  Every mbarrier wait is bounded; a
+// timeout sets an error flag instead of hanging.
 #include <algorithm>
 #include <map>
 #include <vector>
@@ -28,8 +33,7 @@
 namespace {
 
 constexpr int TC_STAGES = 4;
-constexpr int TC_THREADS = 160;
-constexpr int TC_MAX_NP = 112;         // N (and K) of the real GEMM handled here
+constexpr int TC_MAX_NP = 128;         // N of the real GEMM (one 128-column TMEM buffer)
 constexpr long TC_SPIN = 20000000;     // bounded mbarrier polls
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -115,26 +119,65 @@ __global__ void tc_btable_kernel(const cf* M, int nmat, int nin, int nout, int N
     }
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1) m2l_tc_kernel(
+// MMA-ready copy of expansions: per box, per 64-row right-hand-side chunk rc,
+// per K chunk c (16 real values: Re a_0..a_{nin-1} then Im), hi and lo TF32
+// parts, each 64 rows x 16 floats in the no-swizzle core-matrix layout:
+//   float offset (((box * nrc + rc) * kc + c) * 2 + part) * 1024
+//                + ((r / 8) * 4 + kk / 4) * 32 + (r % 8) * 4 + kk % 4.
+__global__ void split_rows_kernel(const cf* __restrict__ src, int64_t nbox, int nrhs, int nin, int kc, int nrc,
+                                  float* __restrict__ dst) {
+    const int64_t total = nbox * nrc * 64;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t box = e / (nrc * 64);
+        const int rc = (int)((e / 64) % nrc);
+        const int r = (int)(e % 64);
+        const int rhs = rc * 64 + r;
+        const cf* row = (rhs < nrhs) ? src + ((int64_t)box * nrhs + rhs) * nin : nullptr;
+        for (int c = 0; c < kc; ++c) {
+            float hv[16], lv[16];
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk) {
+                const int k = 16 * c + kk;
+                float v = 0.0f;
+                if (row && k < 2 * nin) v = (k < nin) ? row[k].x : row[k - nin].y;
+                const float h = __uint_as_float(tf32_rna(v));
+                hv[kk] = h;
+                lv[kk] = __uint_as_float(tf32_rna(v - h));
+            }
+            float* base = dst + (((box * nrc + rc) * kc + c) * 2) * 1024;
+#pragma unroll
+            for (int kb = 0; kb < 4; ++kb) {
+                const int off = ((r >> 3) * 4 + kb) * 32 + (r & 7) * 4;
+                *(float4*)(base + off) = make_float4(hv[4 * kb], hv[4 * kb + 1], hv[4 * kb + 2], hv[4 * kb + 3]);
+                *(float4*)(base + 1024 + off) = make_float4(lv[4 * kb], lv[4 * kb + 1], lv[4 * kb + 2], lv[4 * kb + 3]);
+            }
+        }
+    }
+}
+
+constexpr int TC2_THREADS = 192;   // warps 0-3 drain, warp 4 TMA, warp 5 MMA
+
+template <int NP>
+__global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
     const TcTile* __restrict__ tiles, const TcStep* __restrict__ steps, const float* __restrict__ Bfree,
-    const float* __restrict__ Breact, const float* __restrict__ Bl2l, const cf* __restrict__ mult,
-    const cf* __restrict__ ploc, cf* __restrict__ loc, int nrhs, int nc, int npp, int Np, int kc, int kc2,
-    int* err) {
+    const float* __restrict__ Breact, const float* __restrict__ Bl2l, const float* __restrict__ amma,
+    const float* __restrict__ pmma, const float* __restrict__ zero4k, cf* __restrict__ loc, int nrhs, int nc,
+    int kc, int kc2, int nrc, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int stage_bytes = 16384 + Np * 128;
+    constexpr int stage_bytes = 16384 + NP * 128;
     uint64_t* full = (uint64_t*)(smem + TC_STAGES * stage_bytes);
     uint64_t* empty = full + TC_STAGES;
-    uint64_t* dfull = empty + TC_STAGES;     // [2] accumulator buffer b holds a finished step
-    uint64_t* dfree = dfull + 2;             // [2] accumulator buffer b has been drained
+    uint64_t* dfull = empty + TC_STAGES;
+    uint64_t* dfree = dfull + 2;
     uint32_t* tslot = (uint32_t*)(dfree + 2);
     const TcTile tile = tiles[blockIdx.x];
-    const int r0 = blockIdx.y * 64;
-    const uint32_t ncols = 256;              // two accumulator buffers of 128 columns
+    const int rc = blockIdx.y;
+    const uint32_t ncols = 256;
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(&full[s])), "r"(128));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(&full[s])), "r"(1));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(&empty[s])), "r"(1));
         }
         for (int b = 0; b < 2; ++b) {
@@ -155,89 +198,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1) m2l_tc_kernel(
     const uint32_t taddr = *tslot;
     const int nsteps = tile.s1 - tile.s0;
     if (warp < 4) {
-        // ------- producers (one A row each) and accumulators (their TMEM lane) -------
-        const int row = tid, tgt = row >> 6, r = r0 + (row & 63);
-        const int mb = row >> 3, rr = row & 7;
-        float acc[TC_MAX_NP];
+        // ---------------- drain: FP32 round-to-nearest accumulation ----------------
+        const int row = tid, tgt = row >> 6, r = rc * 64 + (row & 63);
+        float acc[NP];
 #pragma unroll
-        for (int j = 0; j < TC_MAX_NP; ++j) acc[j] = 0.0f;
+        for (int j = 0; j < NP; ++j) acc[j] = 0.0f;
         bool ok = true;
-        // add the finished step s of buffer s & 1 to the FP32 accumulators (round to nearest)
-        auto drain = [&](int s) {
+        for (int s = 0; s < nsteps && ok; ++s) {
             const int b = s & 1;
-            bool good = ok && !s_abort;
-            if (good) good = mbar_wait(&dfull[b], (uint32_t)((s >> 1) & 1));
-            good = __all_sync(0xffffffffu, good);      // keep the warp's .sync.aligned loads uniform
-            if (!good) { ok = false; s_abort = 1; return; }
+            bool good = !s_abort && mbar_wait(&dfull[b], (uint32_t)((s >> 1) & 1));
+            good = __all_sync(0xffffffffu, good);
+            if (!good) { ok = false; s_abort = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t tb = taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 128);
 #pragma unroll
-            for (int c0 = 0; c0 < TC_MAX_NP; c0 += 16) {
-                if (c0 < Np) {
-                    uint32_t v[16];
-                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                                   "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                                   "=r"(v[14]), "=r"(v[15])
-                                 : "r"(tb + (uint32_t)c0));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            for (int c0 = 0; c0 < NP; c0 += 16) {
+                uint32_t v[16];
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                               "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                               "=r"(v[14]), "=r"(v[15])
+                             : "r"(tb + (uint32_t)c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) acc[c0 + j] += __uint_as_float(v[j]);
-                }
+                for (int j = 0; j < 16; ++j) acc[c0 + j] += __uint_as_float(v[j]);
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(&dfree[b]);
-        };
-        int i = 0;
-        for (int s = 0; s < nsteps && ok; ++s) {
-            const TcStep st = steps[tile.s0 + s];
-            const int src = tgt ? st.src1 : st.src0;
-            const bool l2l = st.kind == 2;
-            const int nin = l2l ? npp : nc;
-            const int nk = l2l ? kc2 : kc;
-            const cf* rowp = nullptr;
-            if (src >= 0 && r < nrhs) rowp = l2l ? ploc + ((int64_t)src * nrhs + r) * npp : mult + ((int64_t)src * nrhs + r) * nc;
-            const float* Bm = st.kind == 0 ? Bfree + (int64_t)st.idx * nk * 32 * Np
-                            : st.kind == 1 ? Breact + (int64_t)st.idx * nk * 32 * Np
-                                           : Bl2l + (int64_t)st.idx * nk * 32 * Np;
-            for (int c = 0; c < nk; ++c, ++i) {
-                const int stg = i % TC_STAGES;
-                const uint32_t ph = (uint32_t)((i / TC_STAGES) & 1);
-                bool good = !s_abort && mbar_wait(&empty[stg], ph ^ 1u);
-                good = __all_sync(0xffffffffu, good);
-                if (!good) { ok = false; s_abort = 1; break; }
-                unsigned char* sbase = smem + stg * stage_bytes;
-                float* Ahi = (float*)sbase;
-                float* Alo = (float*)(sbase + 8192);
-                float* Bs = (float*)(sbase + 16384);
-                float hv[16], lv[16];
-#pragma unroll
-                for (int kk = 0; kk < 16; ++kk) {
-                    const int k = 16 * c + kk;
-                    float v = 0.0f;
-                    if (rowp && k < 2 * nin) v = (k < nin) ? rowp[k].x : rowp[k - nin].y;
-                    const float h = __uint_as_float(tf32_rna(v));
-                    hv[kk] = h;
-                    lv[kk] = __uint_as_float(tf32_rna(v - h));
-                }
-#pragma unroll
-                for (int kb = 0; kb < 4; ++kb) {
-                    const int off = (mb * 4 + kb) * 32 + rr * 4;
-                    *(float4*)(Ahi + off) = make_float4(hv[4 * kb], hv[4 * kb + 1], hv[4 * kb + 2], hv[4 * kb + 3]);
-                    *(float4*)(Alo + off) = make_float4(lv[4 * kb], lv[4 * kb + 1], lv[4 * kb + 2], lv[4 * kb + 3]);
-                }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                if (tid == 0) {
-                    const uint32_t bytes = (uint32_t)Np * 128u;
-                    mbar_arrive_tx(&full[stg], bytes);
-                    bulk_g2s(Bs, Bm + (int64_t)c * 32 * Np, bytes, &full[stg]);
-                } else {
-                    mbar_arrive(&full[stg]);
-                }
-            }
-            if (s >= 1 && ok) drain(s - 1);
         }
-        if (nsteps > 0 && ok) drain(nsteps - 1);
         if (!ok || s_abort) {
             if (lane == 0) atomicExch(err, 1);
         } else {
@@ -245,15 +233,47 @@ __global__ void __launch_bounds__(TC_THREADS, 1) m2l_tc_kernel(
             if (box >= 0 && r < nrhs) {
                 float* out = (float*)(loc + ((int64_t)box * nrhs + r) * nc);
 #pragma unroll
-                for (int j = 0; j < TC_MAX_NP; ++j) {
+                for (int j = 0; j < NP; ++j) {
                     if (j < nc) out[2 * j] = acc[j];
                     else if (j < 2 * nc) out[2 * (j - nc) + 1] = acc[j];
                 }
             }
         }
     } else if (warp == 4 && lane == 0) {
+        // ---------------- TMA: A halves (two source boxes) and the operator chunk ----------------
+        int i = 0;
+        for (int s = 0; s < nsteps; ++s) {
+            const TcStep st = steps[tile.s0 + s];
+            const bool l2l = st.kind == 2;
+            const int nk = l2l ? kc2 : kc;
+            const float* base = l2l ? pmma : amma;
+            const float* Bm = st.kind == 0 ? Bfree + (int64_t)st.idx * nk * 32 * NP
+                            : st.kind == 1 ? Breact + (int64_t)st.idx * nk * 32 * NP
+                                           : Bl2l + (int64_t)st.idx * nk * 32 * NP;
+            bool stop = false;
+            for (int c = 0; c < nk; ++c, ++i) {
+                const int stg = i % TC_STAGES;
+                const uint32_t ph = (uint32_t)((i / TC_STAGES) & 1);
+                if (s_abort || !mbar_wait(&empty[stg], ph ^ 1u)) { s_abort = 1; stop = true; break; }
+                unsigned char* sb = smem + stg * stage_bytes;
+                mbar_arrive_tx(&full[stg], (uint32_t)stage_bytes);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int src = h ? st.src1 : st.src0;
+#pragma unroll
+                    for (int part = 0; part < 2; ++part) {
+                        const float* g = (src >= 0) ? base + ((((int64_t)src * nrc + rc) * nk + c) * 2 + part) * 1024
+                                                    : zero4k;
+                        bulk_g2s(sb + part * 8192 + h * 4096, g, 4096u, &full[stg]);
+                    }
+                }
+                bulk_g2s(sb + 16384, Bm + (int64_t)c * 32 * NP, (uint32_t)(NP * 128), &full[stg]);
+            }
+            if (stop) break;
+        }
+    } else if (warp == 5 && lane == 0) {
         // ---------------- MMA issuer: one TMEM buffer per source step ----------------
-        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(Np >> 3) << 17) | ((128u >> 4) << 24);
+        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NP >> 3) << 17) | ((128u >> 4) << 24);
         int i = 0;
         bool ok = true;
         for (int s = 0; s < nsteps && ok; ++s) {
@@ -272,7 +292,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) m2l_tc_kernel(
 #pragma unroll
                 for (int ks = 0; ks < 2; ++ks) {
                     const uint64_t ah = sdesc(sb + ks * 256), al = sdesc(sb + 8192 + ks * 256);
-                    const uint64_t bh = sdesc(sb + 16384 + ks * 256), bl = sdesc(sb + 16384 + Np * 64 + ks * 256);
+                    const uint64_t bh = sdesc(sb + 16384 + ks * 256), bl = sdesc(sb + 16384 + NP * 64 + ks * 256);
                     mma_tf32(dt, ah, bh, idesc, accf);
                     accf = 1;
                     mma_tf32(dt, ah, bl, idesc, 1);
@@ -293,20 +313,30 @@ inline int round16(int x) { return (x + 15) / 16 * 16; }
 }  // namespace
 
 // Plan-time preparation of the tensor-core downward pass for every level
-// whose real GEMM fits (2 nc <= TC_MAX_NP, parent 2 np <= TC_MAX_NP).
+// whose real GEMM width fits one TMEM buffer (2 nc <= 128); K (including the
+// parent's width for L2L) is streamed in chunks of 16.
 hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
     const int L = P->L;
     const int grid = 4 * 152, tb = 256;
+    const int nrc = (P->max_rhs + 63) / 64;
     for (int l = std::max(2, P->lmin); l <= L; ++l) {
         LevelInfo& lv = P->lev[l];
         const int Np = round16(2 * lv.ncoef);
         const bool has_parent = l > P->lmin;
         const int npp = has_parent ? P->lev[l - 1].ncoef : 0;
-        if (Np > TC_MAX_NP || (has_parent && round16(2 * npp) > TC_MAX_NP)) continue;
+        if (Np > TC_MAX_NP) continue;
         if (lv.nbox < 8) continue;
         lv.tc_np = Np;
         lv.tc_kc = Np / 16;
         lv.tc_kc2 = has_parent ? round16(2 * npp) / 16 : 0;
+        // MMA-ready copies: this level's multipoles and the parent's locals
+        HFMM_TRY(plan_alloc(P, (void**)&lv.tc_amma, sizeof(float) * (size_t)lv.nbox * nrc * lv.tc_kc * 2048));
+        P->buffer_bytes += sizeof(float) * (double)lv.nbox * nrc * lv.tc_kc * 2048;
+        if (has_parent) {
+            const size_t pb = sizeof(float) * (size_t)P->lev[l - 1].nbox * nrc * lv.tc_kc2 * 2048;
+            HFMM_TRY(plan_alloc(P, (void**)&lv.tc_pmma, pb));
+            P->buffer_bytes += (double)pb;
+        }
         const size_t mat_f = (size_t)lv.tc_kc * 32 * Np;      // floats per V / reaction matrix
         HFMM_TRY(plan_alloc(P, (void**)&lv.tc_bfree, sizeof(float) * 49 * mat_f));
         tc_btable_kernel<<<grid, tb, 0, st>>>(lv.t_free32, 49, lv.ncoef, lv.ncoef, Np, lv.tc_kc, lv.tc_bfree);
@@ -392,7 +422,36 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
     }
     HFMM_TRY(plan_alloc(P, (void**)&P->tc_err, sizeof(int)));
     HFMM_CUDA_TRY(cudaMemsetAsync(P->tc_err, 0, sizeof(int), st));
+    HFMM_TRY(plan_alloc(P, (void**)&P->tc_zero, 4096));
+    HFMM_CUDA_TRY(cudaMemsetAsync(P->tc_zero, 0, 4096, st));
     HFMM_CUDA_TRY(cudaStreamSynchronize(st));
+    return HFMM_OK;
+}
+
+// MMA-ready copy of the multipoles of a tensor-core level (after the upward pass).
+hfmm_status split_mult_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st) {
+    LevelInfo& lv = P->lev[l];
+    if (lv.tc_ntiles == 0) return HFMM_OK;
+    const int nrc = (P->max_rhs + 63) / 64;
+    split_rows_kernel<<<4 * 152, 128, 0, st>>>(lv.mult32, lv.nbox, nrhs, lv.ncoef, lv.tc_kc, nrc, lv.tc_amma);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    return HFMM_OK;
+}
+
+template <int NP>
+static hfmm_status launch_np(hfmm_plan_s* P, LevelInfo& lv, const float* pmma, int nrhs, cudaStream_t st) {
+    const size_t smem = (size_t)TC_STAGES * (16384 + NP * 128) + 256;
+    static bool attr_set = false;
+    if (!attr_set) {
+        HFMM_CUDA_TRY(cudaFuncSetAttribute(m2l_tc_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    const int nrc = (P->max_rhs + 63) / 64;
+    dim3 grid((unsigned)lv.tc_ntiles, (unsigned)((nrhs + 63) / 64));
+    m2l_tc_kernel<NP><<<grid, TC2_THREADS, smem, st>>>(
+        (const TcTile*)lv.tc_tiles, (const TcStep*)lv.tc_steps, lv.tc_bfree, lv.tc_breact, lv.tc_bl2l, lv.tc_amma,
+        pmma, P->tc_zero, lv.loc32, nrhs, lv.ncoef, lv.tc_kc, lv.tc_kc2, nrc, P->tc_err);
+    HFMM_CUDA_TRY(cudaGetLastError());
     return HFMM_OK;
 }
 
@@ -400,20 +459,24 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
 hfmm_status launch_m2l_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st) {
     LevelInfo& lv = P->lev[l];
     if (lv.tc_ntiles == 0) return HFMM_OK;
-    const int Np = lv.tc_np;
-    const size_t smem = (size_t)TC_STAGES * (16384 + Np * 128) + 256;
-    static bool attr_set = false;
-    if (!attr_set) {
-        HFMM_CUDA_TRY(cudaFuncSetAttribute(m2l_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)((size_t)TC_STAGES * (16384 + TC_MAX_NP * 128) + 256)));
-        attr_set = true;
-    }
     const bool has_parent = l > P->lmin;
-    dim3 grid((unsigned)lv.tc_ntiles, (unsigned)((nrhs + 63) / 64));
-    m2l_tc_kernel<<<grid, TC_THREADS, smem, st>>>(
-        (const TcTile*)lv.tc_tiles, (const TcStep*)lv.tc_steps, lv.tc_bfree, lv.tc_breact, lv.tc_bl2l, lv.mult32,
-        has_parent ? P->lev[l - 1].loc32 : nullptr, lv.loc32, nrhs, lv.ncoef, has_parent ? P->lev[l - 1].ncoef : 0, Np,
-        lv.tc_kc, lv.tc_kc2, P->tc_err);
-    HFMM_CUDA_TRY(cudaGetLastError());
-    return HFMM_OK;
+    const int nrc = (P->max_rhs + 63) / 64;
+    if (has_parent) {
+        const LevelInfo& pl = P->lev[l - 1];
+        split_rows_kernel<<<4 * 152, 128, 0, st>>>(pl.loc32, pl.nbox, nrhs, pl.ncoef, lv.tc_kc2, nrc, lv.tc_pmma);
+        HFMM_CUDA_TRY(cudaGetLastError());
+    }
+    const float* pm = has_parent ? lv.tc_pmma : nullptr;
+    switch (lv.tc_np) {
+        case 16: return launch_np<16>(P, lv, pm, nrhs, st);
+        case 32: return launch_np<32>(P, lv, pm, nrhs, st);
+        case 48: return launch_np<48>(P, lv, pm, nrhs, st);
+        case 64: return launch_np<64>(P, lv, pm, nrhs, st);
+        case 80: return launch_np<80>(P, lv, pm, nrhs, st);
+        case 96: return launch_np<96>(P, lv, pm, nrhs, st);
+        case 112: return launch_np<112>(P, lv, pm, nrhs, st);
+        case 128: return launch_np<128>(P, lv, pm, nrhs, st);
+    }
+    hfmm_set_error("tensor-core pass: unsupported width %d", lv.tc_np);
+    return HFMM_ERR_UNSUPPORTED;
 }

@@ -62,6 +62,8 @@ struct LevelInfo {
     void* tc_tiles = nullptr;
     void* tc_steps = nullptr;
     int64_t tc_ntiles = 0;
+    float* tc_amma = nullptr;     // MMA-ready multipoles of this level
+    float* tc_pmma = nullptr;     // MMA-ready local expansions of the parent level
 };
 
 struct hfmm_plan_s {
@@ -96,6 +98,7 @@ struct hfmm_plan_s {
     cd* y_sorted = nullptr;         // [max_rhs][n]
     cd* io_q = nullptr;             // staging for host pointers
     cd* io_y = nullptr;
+    double* io_gxy = nullptr;
     // mixed path
     cf* q32 = nullptr;              // [max_rhs][n]
     cf* y32 = nullptr;
@@ -109,6 +112,7 @@ struct hfmm_plan_s {
     void* dj_segs = nullptr;
     int64_t dj_njobs = 0;
     int* tc_err = nullptr;          // set by the tensor-core pass when a bounded wait gave up
+    float* tc_zero = nullptr;       // 4 KB of zeros: the A half of a missing source box
 
     // info
     int64_t u_pairs = 0;
@@ -163,6 +167,7 @@ hfmm_status build_local_coords(hfmm_plan_s* P, cudaStream_t st);
 // m2l_tc.cu
 hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status launch_m2l_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st);
+hfmm_status split_mult_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st);
 
 // Morton helpers
 HD uint32_t spread_bits(uint32_t v) {

@@ -238,6 +238,7 @@ struct Node {
     double tau;
     cd lp, lm;       // t: log(w dt sigma / xi) - tY +- i xi X
     cd lzp, lzm;     // t: log zp, log zm
+    cd xi, t;        // t: xi = sqrt(t^2 + k1^2) and t
 };
 
 __device__ Node eval_node(const MedDev& m, const Seg* segs, int s0, int s1, int64_t nu, double X,
@@ -279,6 +280,8 @@ __device__ Node eval_node(const MedDev& m, const Seg* segs, int s0, int s1, int6
     cd ixX = cmuli(cscale(xi, X));            // i xi X
     cd mtY = cscale(t, -Y);                   // -t Y
     nd.kind = 1;
+    nd.xi = xi;
+    nd.t = t;
     nd.lp = cadd(cadd(lc, mtY), ixX);
     nd.lm = csub(cadd(lc, mtY), ixX);
     cd xpt = cadd(xi, t);
@@ -381,6 +384,39 @@ __global__ void direct_block_kernel(MedDev m, const DirectJob* jobs, const Seg* 
     // A_0 = tau-sum / pi + t-sum / (i pi);  G^s = (i/4) A_0
     cd a0 = cadd(cscale(at, 1.0 / HFMM_PI), cscale(cmk(ae.y, -ae.x), 1.0 / HFMM_PI));
     vals[jb.blk + idx] = cmuli(cscale(a0, 0.25));
+    }
+}
+
+// d/dX and d/dY (target point) of the directly summed reaction blocks: the
+// target factor e^{-s1 Y + i lambda X} of the integrand contributes i lambda
+// and -s1 (tau part: lambda = -k1 cos tau, s1 = -i k1 sin tau; t part:
+// lambda = +-xi, s1 = t).
+__global__ void direct_grad_block_kernel(MedDev m, const DirectJob* jobs, const Seg* segs, const double2* xs,
+                                         cd* gx, cd* gy) {
+    const DirectJob jb = jobs[blockIdx.x];
+    for (int idx = threadIdx.x; idx < jb.t_n * jb.s_n; idx += blockDim.x) {
+        const int i = idx / jb.s_n, j = idx % jb.s_n;
+        const double2 pi_ = xs[jb.t_lo + i], pj = xs[jb.s_lo + j];
+        const double X = pi_.x - pj.x, Y = pi_.y + pj.y;
+        cd tx = cmk(0, 0), ty = cmk(0, 0), ex = cmk(0, 0), ey = cmk(0, 0);
+        for (int64_t nu = 0; nu < jb.nodes; ++nu) {
+            Node nd = eval_node(m, segs, jb.seg0, jb.seg1, nu, X, Y);
+            if (nd.kind == 0) {
+                double s_, c_;
+                sincos(nd.tau, &s_, &c_);
+                tx = cadd(tx, cmul(nd.base, cmk(0.0, -m.k1 * c_)));
+                ty = cadd(ty, cmul(nd.base, cmk(0.0, m.k1 * s_)));
+            } else {
+                const cd vp = cexpz(nd.lp), vm = cexpz(nd.lm);
+                ex = cadd(ex, cmul(cmuli(nd.xi), csub(vp, vm)));
+                ey = cadd(ey, cmul(cneg(nd.t), cadd(vp, vm)));
+            }
+        }
+        // A = tau-sum / pi + t-sum / (i pi); G^s derivatives = (i/4) A
+        const cd ax = cadd(cscale(tx, 1.0 / HFMM_PI), cscale(cmk(ex.y, -ex.x), 1.0 / HFMM_PI));
+        const cd ay = cadd(cscale(ty, 1.0 / HFMM_PI), cscale(cmk(ey.y, -ey.x), 1.0 / HFMM_PI));
+        gx[jb.blk + idx] = cmuli(cscale(ax, 0.25));
+        gy[jb.blk + idx] = cmuli(cscale(ay, 0.25));
     }
 }
 
@@ -564,6 +600,9 @@ hfmm_status build_tables(hfmm_plan_s* P, cudaStream_t st) {
             direct_block_kernel<<<(unsigned)jobs.size(), 128, 0, st>>>(md, djobs, dsegs, P->xy_sorted, P->d_vals);
             HFMM_CUDA_TRY(cudaGetLastError());
         }
+        P->dj_jobs = djobs;
+        P->dj_segs = dsegs;
+        P->dj_njobs = (int64_t)jobs.size();
         P->table_bytes += sizeof(cd) * (double)off;
     }
     HFMM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -689,5 +728,19 @@ hfmm_status build_tables32(hfmm_plan_s* P, cudaStream_t st) {
         HFMM_CUDA_TRY(cudaGetLastError());
     }
     HFMM_CUDA_TRY(cudaStreamSynchronize(st));
+    return HFMM_OK;
+}
+
+// Gradient blocks of the directly summed reaction (built on the first
+// position-gradient request).
+hfmm_status build_direct_grad(hfmm_plan_s* P, cudaStream_t st) {
+    if (P->nd == 0 || P->nd_vals == 0) return HFMM_OK;
+    HFMM_TRY(ensure_gl());
+    HFMM_TRY(plan_alloc(P, (void**)&P->d_gvals, sizeof(cd) * 2 * P->nd_vals));
+    const MedDev md = make_med(P->med);
+    direct_grad_block_kernel<<<(unsigned)P->dj_njobs, 128, 0, st>>>(md, (const DirectJob*)P->dj_jobs,
+                                                                     (const Seg*)P->dj_segs, P->xy_sorted,
+                                                                     P->d_gvals, P->d_gvals + P->nd_vals);
+    HFMM_CUDA_TRY(cudaGetLastError());
     return HFMM_OK;
 }

@@ -277,3 +277,51 @@ def test_tensor_core_downward_pass_matches_simt_and_fp64():
     assert direct.rel_l2(y_tc[:4], y64) < MIXED_TOL
     for p in (tc, si, f64):
         p.close()
+
+
+# --- gradients ---------------------------------------------------------------------
+
+def test_position_gradient_matches_oracle_direct_sum_gradient():
+    med = W.WORKLOADS[1].medium
+    xy = W.points(1, 400)
+    q = W.strengths(1, 400, 2, salt=1)
+    y_obs = direct.direct_apply(med, W.perturb(1, xy), q)
+    plan = Plan(xy, med, tol=1e-10, leaf_size=16, max_rhs=2)
+    y = plan.apply(q)
+    g = 2.0 * (y - y_obs)
+    got = plan.grad(q, g)
+    want = direct.position_grad(med, xy, q, g)
+    assert np.linalg.norm(got - want) < 1e-8 * np.linalg.norm(want)
+    plan.close()
+
+
+def test_autograd_gradients_match_finite_differences():
+    """torch.autograd through the C ABI (adjoint for strengths, field
+    gradients for positions) against central differences, h = 1e-6."""
+    from paper_1703_09136_gb300 import matvec
+    med = W.WORKLOADS[5].medium
+    xy0 = W.points(5, 300)
+    q0 = W.strengths(5, 300, 1, salt=2)
+    y_obs = torch.from_numpy(direct.direct_apply(med, W.perturb(5, xy0), q0)).cuda()
+    xy = torch.from_numpy(xy0).cuda().requires_grad_(True)
+    q = torch.from_numpy(q0).cuda().requires_grad_(True)
+    opts = dict(tol=1e-12, leaf_size=16)
+    loss = (matvec(xy, q, med, **opts) - y_obs).abs().pow(2).sum()
+    loss.backward()
+    def L(z, qq):
+        with torch.no_grad():
+            return float((matvec(z, qq, med, **opts) - y_obs).abs().pow(2).sum())
+    h = 1e-6
+    for j, d in ((3, 0), (3, 1), (150, 0), (299, 1)):
+        zp = xy.detach().clone(); zp[j, d] += h
+        zm = xy.detach().clone(); zm[j, d] -= h
+        fd = (L(zp, q.detach()) - L(zm, q.detach())) / (2 * h)
+        assert abs(fd - float(xy.grad[j, d])) < 1e-5 * max(1.0, abs(fd))
+    for j in (0, 77):
+        for part in (1.0, 1j):
+            qp = q.detach().clone(); qp[0, j] += h * part
+            qm = q.detach().clone(); qm[0, j] -= h * part
+            fd = (L(xy.detach(), qp) - L(xy.detach(), qm)) / (2 * h)
+            g = q.grad[0, j]
+            want = float(g.real) if part == 1.0 else float(g.imag)
+            assert abs(fd - want) < 1e-5 * max(1.0, abs(fd))
