@@ -35,6 +35,16 @@ FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 rate (no measured FP64 figure 
 # FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz (max SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 SAMPLE_BOX = ((0.0, 1.0), (0.02, 1.02))
+FALLBACK_BF16_TFLOPS = 1900.0  # used only when MEASURED_PEAKS.json is absent
+
+
+def _measured_bf16():
+    """Dense bf16 burst TFLOP/s measured on this GPU type, and its source."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_BF16_TFLOPS, "fallback"
 
 
 def parse():
@@ -217,11 +227,19 @@ def run_ours(args):
     avg = {k: v / args.steps for k, v in stage_ms.items()}
     dom = max(avg, key=avg.get)
     flops = info["flops_last_apply"][dom]
+    bound = "alu"
     if prec == FP64:
         peak, src = FP64_PEAK_TFLOPS, "nominal GB300 FP64 rate (MEASURED_PEAKS.json has no FP64 figure)"
+    elif dom in ("m2m", "down") and info["tensor_levels"] > 0:
+        # FP32 terms as three TF32 tensor-core products (3xTF32): the measured
+        # bf16 burst peak x the nominal TF32 / BF16 dense ratio (1.1 / 2.25) / 3
+        bf16, how = _measured_bf16()
+        peak = bf16 * (1.1 / 2.25) / 3.0
+        src = f"derived 3xTF32 peak: {how} bf16 {bf16:.1f} TFLOP/s x (1.1 / 2.25) / 3"
+        bound = "tensor"
     else:
         peak, src = FP32_PEAK_TFLOPS, "derived FP32 SIMT peak: 152 SMs x 128 lanes x 2 x 2.07 GHz"
-    roof = {"kernel": dom, "bound": "alu", "achieved": flops / (avg[dom] * 1e-3) / 1e12,
+    roof = {"kernel": dom, "bound": bound, "achieved": flops / (avg[dom] * 1e-3) / 1e12,
             "peak": peak, "unit": "TFLOP/s", "traffic": None, "peak_source": src}
     roof["frac"] = roof["achieved"] / roof["peak"]
     # end to end through the C ABI with pinned host buffers

@@ -103,6 +103,9 @@ typedef struct {
 #define HFMM_FLAG_PROFILE 1     /* record CUDA events around every stage of each apply */
 #define HFMM_FLAG_SIMT_M2L 2    /* HFMM_MIXED: keep the downward pass on FP32 SIMT cores
                                    instead of the tcgen05 tensor-core pass */
+#define HFMM_FLAG_AUTOTUNE 4    /* build the plan at the leaf levels L-1, L, L+1 around the
+                                   leaf_size choice, time max_rhs-wide applies on the device
+                                   and keep the fastest (hfmm_plan_info.tune_*) */
 
 /* Stages reported by hfmm_plan_get_stage_times (milliseconds of the last apply). */
 #define HFMM_STAGE_GATHER   0   /* caller order -> leaf order */
@@ -138,6 +141,8 @@ typedef struct {
     double bytes_last_apply[HFMM_NUM_STAGES];  /* algorithmic DRAM bytes per stage, last apply */
     int32_t device_error;       /* nonzero if a bounded device wait gave up (results invalid) */
     int32_t tensor_levels;      /* levels whose downward pass runs on tcgen05 tensor cores */
+    int32_t tune_levels[3];     /* HFMM_FLAG_AUTOTUNE: leaf levels tried (0 = not tried) */
+    double tune_ms[3];          /* and the apply time measured for each */
 } hfmm_plan_info;
 
 /* Bits of `parts` in hfmm_apply_parts (sum of the selected terms). */
@@ -199,6 +204,30 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t plan, int32_t nrhs, const void* v, vo
  */
 hfmm_status hfmm_apply_grad(hfmm_plan_t plan, int32_t nrhs, const void* q, const void* g, double* gxy,
                             void* stream);
+
+/*
+ * Batches of independent problems of uneven sizes (same medium and options),
+ * e.g. many scatterers or many inverse-problem instances.  One plan per
+ * instance; hfmm_batch_apply applies all of them: the first call with a given
+ * set of buffers runs them once eagerly on `stream` (lazily initialised
+ * state is set up outside capture; `stream` is synchronised), then records
+ * all instances' applies into one CUDA graph on a private stream of the
+ * batch (one branch per instance) and launches it on `stream`; later calls
+ * with the same buffers only launch the graph.  q[i], y[i]: device buffers
+ * [nrhs][n_i] of instance i (dtype as for hfmm_apply); adjoint != 0 applies
+ * A_i^H instead.  Changing any buffer pointer, nrhs or adjoint re-records the
+ * graph.  Errors: HFMM_ERR_INVALID_ARG for host buffers or nrhs outside
+ * 1..max_rhs, HFMM_ERR_CUDA if capture or instantiation fails.  The batch
+ * owns its plans; calls on one batch must not overlap.
+ */
+typedef struct hfmm_batch_s* hfmm_batch_t;
+hfmm_status hfmm_batch_create(hfmm_batch_t* out, int32_t ninst, const int64_t* n, const double* const* xy,
+                              const hfmm_medium* medium, const hfmm_options* opts, void* stream);
+hfmm_status hfmm_batch_apply(hfmm_batch_t batch, int32_t nrhs, const void* const* q, void* const* y,
+                             int32_t adjoint, void* stream);
+/* Plan of instance i (owned by the batch; for introspection and single applies). */
+hfmm_status hfmm_batch_get_plan(hfmm_batch_t batch, int32_t i, hfmm_plan_t* plan);
+hfmm_status hfmm_batch_destroy(hfmm_batch_t batch);
 
 /* Fill *info (host pointer). */
 hfmm_status hfmm_plan_get_info(hfmm_plan_t plan, hfmm_plan_info* info);

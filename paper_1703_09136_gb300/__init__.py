@@ -104,7 +104,7 @@ class Plan:
     """An H-FMM plan for fixed points: y = A q with A_ij = u_{x_j}(x_i)."""
 
     def __init__(self, xy, medium, tol=1e-6, p=0, leaf_size=32, levels=0, precision=FP64,
-                 max_rhs=1, stream=None, profile=False, simt_m2l=False):
+                 max_rhs=1, stream=None, profile=False, simt_m2l=False, autotune=False):
         lib = _n.lib()
         m = Medium.of(medium)
         opts = _n.hfmm_options()
@@ -115,7 +115,8 @@ class Plan:
         opts.levels = int(levels)
         opts.precision = int(precision)
         opts.max_rhs = int(max_rhs)
-        opts.flags = (_n.FLAG_PROFILE if profile else 0) | (_n.FLAG_SIMT_M2L if simt_m2l else 0)
+        opts.flags = ((_n.FLAG_PROFILE if profile else 0) | (_n.FLAG_SIMT_M2L if simt_m2l else 0) |
+                      (_n.FLAG_AUTOTUNE if autotune else 0))
         torch = _torch()
         if torch is not None and isinstance(xy, torch.Tensor):
             if xy.dtype != torch.float64:
@@ -210,7 +211,8 @@ class Plan:
         inf = _n.hfmm_plan_info()
         _n.check(_n.lib().hfmm_plan_get_info(self._h, ctypes.byref(inf)))
         d = {name: getattr(inf, name) for name, _ in inf._fields_
-             if name not in ("p", "flops_last_apply", "bytes_last_apply")}
+             if name not in ("p", "flops_last_apply", "bytes_last_apply", "tune_levels", "tune_ms")}
+        d["tune"] = {int(inf.tune_levels[c]): float(inf.tune_ms[c]) for c in range(3) if inf.tune_levels[c]}
         d["p"] = [inf.p[l] for l in range(inf.levels + 1)]
         d["flops_last_apply"] = dict(zip(_n.STAGES, list(inf.flops_last_apply)))
         d["bytes_last_apply"] = dict(zip(_n.STAGES, list(inf.bytes_last_apply)))
@@ -261,6 +263,51 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Batch:
+    """Independent problems of uneven sizes applied through one CUDA graph
+    (hfmm_batch_*).  xys: list of [n_i, 2] float64 arrays / tensors."""
+
+    def __init__(self, xys, medium, tol=1e-6, p=0, leaf_size=32, levels=0, precision=FP64, max_rhs=1,
+                 stream=None):
+        lib = _n.lib()
+        m = Medium.of(medium)
+        opts = _n.hfmm_options()
+        lib.hfmm_options_default(ctypes.byref(opts))
+        opts.tol, opts.p, opts.leaf_size, opts.levels = float(tol), int(p), int(leaf_size), int(levels)
+        opts.precision, opts.max_rhs = int(precision), int(max_rhs)
+        keep = [_ptr(np.ascontiguousarray(x, dtype=np.float64) if not hasattr(x, "data_ptr") else x.contiguous())
+                for x in xys]
+        ns = (ctypes.c_int64 * len(xys))(*[int(x.shape[0]) for x in xys])
+        ptrs = (ctypes.c_void_p * len(xys))(*[k[0].value for k in keep])
+        h = ctypes.c_void_p()
+        _n.check(lib.hfmm_batch_create(ctypes.byref(h), len(xys), ns, ptrs, ctypes.byref(m._c()),
+                                       ctypes.byref(opts), _stream_handle(stream)))
+        self._h = h
+        self.sizes = [int(x.shape[0]) for x in xys]
+        self.precision = int(precision)
+
+    def apply(self, qs, ys=None, adjoint=False, stream=None):
+        """ys[i] = A_i qs[i] (device tensors [nrhs, n_i]); returns ys."""
+        if ys is None:
+            ys = [q.new_empty(q.shape) for q in qs]
+        nrhs = 1 if qs[0].dim() == 1 else int(qs[0].shape[0])
+        qp = (ctypes.c_void_p * len(qs))(*[q.data_ptr() for q in qs])
+        yp = (ctypes.c_void_p * len(ys))(*[y.data_ptr() for y in ys])
+        _n.check(_n.lib().hfmm_batch_apply(self._h, nrhs, qp, yp, 1 if adjoint else 0, _stream_handle(stream)))
+        return ys
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _n.lib().hfmm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def matvec(xy, q, medium, **plan_options):

@@ -20,11 +20,13 @@ EXPORTS = ["hfmm_options_default", "hfmm_plan_create", "hfmm_apply", "hfmm_apply
            "hfmm_apply_adjoint", "hfmm_plan_get_info", "hfmm_plan_get_tree",
            "hfmm_plan_get_pairs", "hfmm_plan_destroy", "hfmm_status_string", "hfmm_last_error",
            "hfmm_debug_bessel", "hfmm_plan_get_stage_times", "hfmm_debug_green_f32",
-           "hfmm_leaf_order_noalloc", "hfmm_apply_grad"]
+           "hfmm_leaf_order_noalloc", "hfmm_apply_grad", "hfmm_batch_create", "hfmm_batch_apply",
+           "hfmm_batch_get_plan", "hfmm_batch_destroy"]
 NUM_STAGES = 8
 STAGES = ["gather", "p2m", "m2m", "down", "l2p", "p2p", "direct", "scatter"]
 FLAG_PROFILE = 1
 FLAG_SIMT_M2L = 2
+FLAG_AUTOTUNE = 4
 
 
 class HfmmError(RuntimeError):
@@ -54,7 +56,8 @@ class hfmm_plan_info(ctypes.Structure):
                 ("plan_ms", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("max_rhs", ctypes.c_int32), ("launches_last_apply", ctypes.c_int64),
                 ("flops_last_apply", ctypes.c_double * 8), ("bytes_last_apply", ctypes.c_double * 8),
-                ("device_error", ctypes.c_int32), ("tensor_levels", ctypes.c_int32)]
+                ("device_error", ctypes.c_int32), ("tensor_levels", ctypes.c_int32),
+                ("tune_levels", ctypes.c_int32 * 3), ("tune_ms", ctypes.c_double * 3)]
 
 
 hfmm_plan_t = ctypes.c_void_p
@@ -87,10 +90,15 @@ def lib():
         L.hfmm_debug_green_f32.argtypes = [i32, vp, vp]
         L.hfmm_leaf_order_noalloc.argtypes = [i64, vp, i32, vp, vp, vp]
         L.hfmm_apply_grad.argtypes = [hfmm_plan_t, i32, vp, vp, vp, vp]
+        L.hfmm_batch_create.argtypes = [ctypes.POINTER(vp), i32, vp, vp, vp, vp, vp]
+        L.hfmm_batch_apply.argtypes = [vp, i32, vp, vp, i32, vp]
+        L.hfmm_batch_get_plan.argtypes = [vp, i32, ctypes.POINTER(hfmm_plan_t)]
+        L.hfmm_batch_destroy.argtypes = [vp]
         for name in ("hfmm_plan_create", "hfmm_apply", "hfmm_apply_parts", "hfmm_apply_adjoint",
                      "hfmm_plan_get_info", "hfmm_plan_get_tree", "hfmm_plan_get_pairs",
                      "hfmm_plan_destroy", "hfmm_debug_bessel", "hfmm_plan_get_stage_times",
-                     "hfmm_debug_green_f32", "hfmm_leaf_order_noalloc", "hfmm_apply_grad"):
+                     "hfmm_debug_green_f32", "hfmm_leaf_order_noalloc", "hfmm_apply_grad",
+                     "hfmm_batch_create", "hfmm_batch_apply", "hfmm_batch_get_plan", "hfmm_batch_destroy"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib

@@ -65,6 +65,12 @@ static int p_low(double tol) {
     return std::max(4, (int)std::ceil(2.5 * d - 6.5));
 }
 
+// Device-pointer apply of one instance, no host synchronisation (batch graphs).
+hfmm_status batch_apply_one(hfmm_plan_t P, int nrhs, const void* q, void* y, bool adjoint, cudaStream_t st) {
+    if (P->precision == HFMM_MIXED) return apply_mixed(P, nrhs, (const cf*)q, (cf*)y, HFMM_PART_ALL, adjoint, st);
+    return apply_fp64(P, nrhs, (const cd*)q, (cd*)y, HFMM_PART_ALL, adjoint, st);
+}
+
 extern "C" {
 
 void hfmm_options_default(hfmm_options* o) {
@@ -127,8 +133,85 @@ static hfmm_status validate_medium(const hfmm_medium* m) {
     return HFMM_ERR_INVALID_ARG;
 }
 
+static hfmm_status plan_create_one(hfmm_plan_t* out, int64_t n, const double* xy, const hfmm_medium* medium,
+                                   const hfmm_options* opts, void* stream);
+
+// Time one max_rhs-wide apply of a plan (device buffers, CUDA events).
+static hfmm_status time_apply(hfmm_plan_t P, cudaStream_t st, double* ms) {
+    const size_t esz = P->precision == HFMM_MIXED ? sizeof(cf) : sizeof(cd);
+    const size_t bytes = esz * (size_t)P->n * P->max_rhs;
+    if (!P->io_q) HFMM_TRY(plan_alloc(P, (void**)&P->io_q, sizeof(cd) * (size_t)P->n * P->max_rhs));
+    if (!P->io_y) HFMM_TRY(plan_alloc(P, (void**)&P->io_y, sizeof(cd) * (size_t)P->n * P->max_rhs));
+    HFMM_CUDA_TRY(cudaMemsetAsync(P->io_q, 0, bytes, st));
+    cudaEvent_t e0, e1;
+    HFMM_CUDA_TRY(cudaEventCreate(&e0));
+    HFMM_CUDA_TRY(cudaEventCreate(&e1));
+    hfmm_status s = HFMM_OK;
+    for (int it = 0; it < 3 && s == HFMM_OK; ++it) {
+        if (it == 1) cudaEventRecord(e0, st);
+        s = P->precision == HFMM_MIXED
+                ? apply_mixed(P, P->max_rhs, (const cf*)P->io_q, (cf*)P->io_y, HFMM_PART_ALL, false, st)
+                : apply_fp64(P, P->max_rhs, P->io_q, P->io_y, HFMM_PART_ALL, false, st);
+    }
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = t / 2.0;
+    return s;
+}
+
 hfmm_status hfmm_plan_create(hfmm_plan_t* out, int64_t n, const double* xy, const hfmm_medium* medium,
                              const hfmm_options* opts, void* stream) {
+    if (!opts || !(opts->flags & HFMM_FLAG_AUTOTUNE)) return plan_create_one(out, n, xy, medium, opts, stream);
+    if (!out) { hfmm_set_error("out is NULL"); return HFMM_ERR_INVALID_ARG; }
+    *out = nullptr;
+    hfmm_options o = *opts;
+    o.flags &= ~HFMM_FLAG_AUTOTUNE;
+    const int L0 = o.levels > 0 ? o.levels : choose_levels(n, o.leaf_size > 0 ? o.leaf_size : 32);
+    hfmm_plan_t best = nullptr;
+    double best_ms = 0.0;
+    int tried[3] = {0, 0, 0};
+    double times[3] = {0.0, 0.0, 0.0};
+    for (int c = 0; c < 3; ++c) {
+        const int L = L0 - 1 + c;
+        if (L < 2 || L > 15) continue;
+        o.levels = L;
+        hfmm_plan_t p = nullptr;
+        hfmm_status s = plan_create_one(&p, n, xy, medium, &o, stream);
+        if (s != HFMM_OK) {
+            if (s == HFMM_ERR_OOM) continue;            // a deeper tree may not fit: skip it
+            if (best) hfmm_plan_destroy(best);
+            return s;
+        }
+        double ms = 0.0;
+        s = time_apply(p, (cudaStream_t)stream, &ms);
+        if (s != HFMM_OK) {
+            hfmm_plan_destroy(p);
+            if (best) hfmm_plan_destroy(best);
+            return s;
+        }
+        tried[c] = L;
+        times[c] = ms;
+        if (!best || ms < best_ms) {
+            if (best) hfmm_plan_destroy(best);
+            best = p;
+            best_ms = ms;
+        } else {
+            hfmm_plan_destroy(p);
+        }
+    }
+    if (!best) { hfmm_set_error("autotune: no candidate plan could be built"); return HFMM_ERR_OOM; }
+    for (int c = 0; c < 3; ++c) { best->tune_levels[c] = tried[c]; best->tune_ms[c] = times[c]; }
+    best->flags |= HFMM_FLAG_AUTOTUNE;
+    *out = best;
+    return HFMM_OK;
+}
+
+static hfmm_status plan_create_one(hfmm_plan_t* out, int64_t n, const double* xy, const hfmm_medium* medium,
+                                   const hfmm_options* opts, void* stream) {
     if (!out) { hfmm_set_error("out is NULL"); return HFMM_ERR_INVALID_ARG; }
     *out = nullptr;
     if (n < 1 || n > ((int64_t)1 << 30)) { hfmm_set_error("n must be in [1, 2^30] (got %lld)", (long long)n); return HFMM_ERR_INVALID_ARG; }
@@ -346,6 +429,10 @@ hfmm_status hfmm_plan_get_info(hfmm_plan_t P, hfmm_plan_info* info) {
     for (int s = 0; s < HFMM_NUM_STAGES; ++s) {
         info->flops_last_apply[s] = P->st_flops[s];
         info->bytes_last_apply[s] = P->st_bytes[s];
+    }
+    for (int c = 0; c < 3; ++c) {
+        info->tune_levels[c] = P->tune_levels[c];
+        info->tune_ms[c] = P->tune_ms[c];
     }
     return HFMM_OK;
 }

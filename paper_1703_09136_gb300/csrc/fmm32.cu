@@ -592,21 +592,27 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
             P->st_bytes[HFMM_STAGE_P2M] = C * n + 16.0 * n + C * lv.nbox * lv.ncoef;
         }
         tm.begin(HFMM_STAGE_M2M);
+        if (P->tc_on) {
+            HFMM_TRY(split_mult_tc(P, L, nrhs, st));
+            ++P->launches;
+        }
         for (int l = L - 1; l >= P->lmin; --l) {
             LevelInfo& lv = P->lev[l];
-            m2m32_kernel<<<(unsigned)lv.nbox, 128, 0, st>>>(P->lev[l + 1].mult32, lv.t_m2m32, P->lev[l + 1].p,
-                                                           lv.p, nrhs, lv.mult32);
+            if (P->tc_on) {
+                HFMM_TRY(launch_m2m_tc(P, l, nrhs, st));
+            } else {
+                m2m32_kernel<<<(unsigned)lv.nbox, 128, 0, st>>>(P->lev[l + 1].mult32, lv.t_m2m32, P->lev[l + 1].p,
+                                                               lv.p, nrhs, lv.mult32);
+                HFMM_CUDA_TRY(cudaGetLastError());
+            }
             ++P->launches;
-            HFMM_CUDA_TRY(cudaGetLastError());
             P->st_flops[HFMM_STAGE_M2M] += MAC * 4.0 * lv.nbox * lv.ncoef * P->lev[l + 1].ncoef;
             P->st_bytes[HFMM_STAGE_M2M] += C * (4.0 * lv.nbox * P->lev[l + 1].ncoef + lv.nbox * lv.ncoef);
         }
         tm.end(HFMM_STAGE_M2M);
         tm.begin(HFMM_STAGE_DOWN);
-        const bool all_far = (parts & HFMM_PART_FAR_FREE) && (parts & HFMM_PART_FAR_REACT);
-        if (all_far)
-            for (int l = P->lmin; l <= L; ++l)
-                if (P->lev[l].tc_ntiles > 0) { HFMM_TRY(split_mult_tc(P, l, nrhs, st)); ++P->launches; }
+        // the tensor-core pass fuses both far parts of a level; subsets run on SIMT cores
+        const bool tc_down = P->tc_on && (parts & HFMM_PART_FAR_FREE) && (parts & HFMM_PART_FAR_REACT);
         for (int l = P->lmin; l <= L; ++l) {
             LevelInfo& lv = P->lev[l];
             const bool has_parent = l > P->lmin;
@@ -616,7 +622,7 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
             int rc = std::max(1, std::min(nrhs, (int)(32768 / (wmax * sizeof(cf)))));
             rc = std::max(1, std::min(rc, (8 * DOWN_THREADS) / lv.ncoef));
             const size_t sm = (size_t)rc * wmax * sizeof(cf);
-            if (lv.tc_ntiles > 0 && all_far) {
+            if (tc_down) {
                 HFMM_TRY(launch_m2l_tc(P, l, nrhs, st));
             } else {
                 down32_kernel<<<(unsigned)lv.nbox, DOWN_THREADS, sm, st>>>(

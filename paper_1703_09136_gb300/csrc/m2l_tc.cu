@@ -1,29 +1,33 @@
-// Tensor-core downward pass (mixed path): L2L + free-space M2L + reaction M2L
-// of one level as one accumulation in tensor memory (tcgen05, sm_103a).
+// Tensor-core translation passes of the mixed path (tcgen05, sm_103a): the
+// downward pass of a level (L2L + free-space M2L + reaction M2L) and the M2M
+// of a level, each as one accumulation in tensor memory.
 //
 // For a pair of target boxes T0, T1 with the same child position (Morton
-// b and b + 4), every source step s (the parent's local expansion, each
-// V-list offset, each reaction-table entry) contributes
+// b and b + 4), every source step s contributes
 //     beta~_T[r][p] += sum_m a~_S[r][m] M_s[m][p]
-// to the scaled local coefficients of both targets (right-hand side r).
-// In real arithmetic a complex product is one real GEMM,
+// to the scaled coefficients of both targets (right-hand side r).  Downward
+// steps are the parent's local expansion (L2L), each V-list offset and each
+// reaction-table entry; M2M steps are the four children.  In real
+// arithmetic a complex product is one real GEMM,
 //     D[row][n] += sum_k A[row][k] B_s[n][k],
 // rows = (target, r) (2 x 64 = M 128), k = (Re a_m | Im a_m) (K = 2 nc_in,
-// padded to 16), n = (Re b_p | Im b_p) (N = 2 nc, padded to 16), with
-// B = [[Re M, -Im M], [Im M, Re M]] blocks.  FP32 accuracy comes from three
-// TF32 products per term (hi*hi + hi*lo + lo*hi, x = hi + lo).
+// padded to 16), n = (Re b_p | Im b_p) (N = 2 nc padded into column blocks
+// of at most 128), with B = [[Re M, -Im M], [Im M, Re M]] blocks.  FP32
+// accuracy comes from three TF32 products per term (hi*hi + hi*lo + lo*hi,
+// x = hi + lo).
 //
 // Operands are stored MMA-ready (pre-split TF32 hi / lo, core-matrix layout):
-// the multipoles of the level and the parent's local expansions are copied
-// into that form after they are produced, the operators at plan time.
-// Pipeline (one CTA = one target pair x 64 right-hand sides): warp 4 streams
-// every K chunk with cp.async.bulk (two 64-row A halves per part plus the
-// operator chunk) into a 4-stage shared-memory ring; warp 5 issues
-// tcgen05.mma into one of two TMEM buffers per source step; warps 0-3 drain
-// each finished step with tcgen05.ld into round-to-nearest FP32 registers
-// (tensor-core accumulation truncates, so long chains in TMEM lose accuracy)
-// and write the local coefficients.  Every mbarrier wait is bounded; a
-// timeout sets an error flag instead of hanging.
+// the leaf multipoles are copied into that form after P2M, every other
+// expansion is written in that form by the kernel that produces it, the
+// operators at plan time.  Pipeline (one CTA = one target pair x 64
+// right-hand sides x one column block): warp 4 streams every K chunk with
+// cp.async.bulk (two 64-row A halves per part plus the operator block) into a
+// 4-stage shared-memory ring; warp 5 issues tcgen05.mma into one of two TMEM
+// buffers per source step; warps 0-3 drain each finished step with
+// tcgen05.ld into round-to-nearest FP32 registers (tensor-core accumulation
+// truncates, so long chains in TMEM lose accuracy) and write the result.
+// Every mbarrier wait is bounded; a timeout sets an error flag instead of
+// hanging.
 #include <algorithm>
 #include <map>
 #include <vector>
@@ -33,8 +37,9 @@
 namespace {
 
 constexpr int TC_STAGES = 4;
-constexpr int TC_MAX_NP = 128;         // N of the real GEMM (one 128-column TMEM buffer)
+constexpr int TC_MAX_NP = 128;         // widest column block (one 128-column TMEM buffer)
 constexpr long TC_SPIN = 20000000;     // bounded mbarrier polls
+constexpr int TC_STEP_CHUNKS = 8;      // K chunks accumulated in TMEM before a drain
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -90,7 +95,9 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 }
 
 struct TcTile { int32_t b0, b1, s0, s1; };          // boxes (-1: empty), step range
-struct TcStep { int32_t kind, idx, src0, src1; };  // kind 0 free, 1 reaction, 2 L2L; src -1: none
+// kind 0 free M2L, 1 reaction M2L, 2 secondary source (L2L parent or M2M child);
+// src -1: none; K chunks c0 .. c1 - 1 of the operator
+struct TcStep { int32_t kind, idx, src0, src1, c0, c1; };
 
 // Pre-split B chunks: for matrix index i, chunk c, part (0 hi, 1 lo):
 //   float offset ((i * kc + c) * 2 + part) * (Np * 16) + ((n / 8) * 4 + (k % 16) / 4) * 32 + (n % 8) * 4 + k % 4
@@ -157,16 +164,21 @@ __global__ void split_rows_kernel(const cf* __restrict__ src, int64_t nbox, int 
 
 constexpr int TC2_THREADS = 192;   // warps 0-3 drain, warp 4 TMA, warp 5 MMA
 
-template <int NP>
+// One CTA = one target pair x 64 right-hand sides x one block of NB real
+// output columns (blockIdx.z; columns n0 .. n0 + NB - 1 of the Np-wide GEMM).
+// The result goes to the FP32 coefficients out[box][r][0 .. nc) and, when
+// sdst is given, also in MMA-ready form (kcd K chunks, split_rows_kernel
+// layout) for the next tensor-core consumer of these coefficients.
+template <int NB>
 __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
     const TcTile* __restrict__ tiles, const TcStep* __restrict__ steps, const float* __restrict__ Bfree,
     const float* __restrict__ Breact, const float* __restrict__ Bl2l, const float* __restrict__ amma,
-    const float* __restrict__ pmma, const float* __restrict__ zero4k, cf* __restrict__ loc, int nrhs, int nc,
-    int kc, int kc2, int nrc, int* err) {
+    const float* __restrict__ pmma, const float* __restrict__ zero4k, cf* __restrict__ out, int nrhs, int nc,
+    int kc, int kc2, int nrc, int Np, float* __restrict__ sdst, int kcd, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr int stage_bytes = 16384 + NP * 128;
+    constexpr int stage_bytes = 16384 + NB * 128;
     uint64_t* full = (uint64_t*)(smem + TC_STAGES * stage_bytes);
     uint64_t* empty = full + TC_STAGES;
     uint64_t* dfull = empty + TC_STAGES;
@@ -174,6 +186,7 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
     uint32_t* tslot = (uint32_t*)(dfree + 2);
     const TcTile tile = tiles[blockIdx.x];
     const int rc = blockIdx.y;
+    const int n0 = blockIdx.z * NB;
     const uint32_t ncols = 256;
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
@@ -200,9 +213,9 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
     if (warp < 4) {
         // ---------------- drain: FP32 round-to-nearest accumulation ----------------
         const int row = tid, tgt = row >> 6, r = rc * 64 + (row & 63);
-        float acc[NP];
+        float acc[NB];
 #pragma unroll
-        for (int j = 0; j < NP; ++j) acc[j] = 0.0f;
+        for (int j = 0; j < NB; ++j) acc[j] = 0.0f;
         bool ok = true;
         for (int s = 0; s < nsteps && ok; ++s) {
             const int b = s & 1;
@@ -212,7 +225,7 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t tb = taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 128);
 #pragma unroll
-            for (int c0 = 0; c0 < NP; c0 += 16) {
+            for (int c0 = 0; c0 < NB; c0 += 16) {
                 uint32_t v[16];
                 asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
@@ -230,28 +243,51 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
             if (lane == 0) atomicExch(err, 1);
         } else {
             const int box = tgt ? tile.b1 : tile.b0;
-            if (box >= 0 && r < nrhs) {
-                float* out = (float*)(loc + ((int64_t)box * nrhs + r) * nc);
+            if (box >= 0) {
+                if (r < nrhs) {
+                    float* o = (float*)(out + ((int64_t)box * nrhs + r) * nc);
 #pragma unroll
-                for (int j = 0; j < NP; ++j) {
-                    if (j < nc) out[2 * j] = acc[j];
-                    else if (j < 2 * nc) out[2 * (j - nc) + 1] = acc[j];
+                    for (int j = 0; j < NB; ++j) {
+                        const int g = n0 + j;
+                        if (g < nc) o[2 * g] = acc[j];
+                        else if (g < 2 * nc) o[2 * (g - nc) + 1] = acc[j];
+                    }
+                }
+                if (sdst) {
+                    // every row of the 64-row block, so rows r >= nrhs stay zero
+                    const int rr = row & 63;
+                    float* base = sdst + (((int64_t)box * nrc + rc) * kcd * 2) * 1024 + ((rr >> 3) * 4) * 32 + (rr & 7) * 4;
+#pragma unroll
+                    for (int j = 0; j < NB; j += 4) {
+                        const int g = n0 + j;
+                        if ((g >> 4) < kcd) {
+                            float h[4], lo[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                h[u] = __uint_as_float(tf32_rna(acc[j + u]));
+                                lo[u] = __uint_as_float(tf32_rna(acc[j + u] - h[u]));
+                            }
+                            float* d = base + (int64_t)(g >> 4) * 2048 + ((g & 15) >> 2) * 32;
+                            *(float4*)d = make_float4(h[0], h[1], h[2], h[3]);
+                            *(float4*)(d + 1024) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+                        }
+                    }
                 }
             }
         }
     } else if (warp == 4 && lane == 0) {
-        // ---------------- TMA: A halves (two source boxes) and the operator chunk ----------------
+        // ---------------- TMA: A halves (two source boxes) and the operator block ----------------
         int i = 0;
         for (int s = 0; s < nsteps; ++s) {
             const TcStep st = steps[tile.s0 + s];
-            const bool l2l = st.kind == 2;
-            const int nk = l2l ? kc2 : kc;
-            const float* base = l2l ? pmma : amma;
-            const float* Bm = st.kind == 0 ? Bfree + (int64_t)st.idx * nk * 32 * NP
-                            : st.kind == 1 ? Breact + (int64_t)st.idx * nk * 32 * NP
-                                           : Bl2l + (int64_t)st.idx * nk * 32 * NP;
+            const bool sec = st.kind == 2;
+            const int nk = sec ? kc2 : kc;
+            const float* base = sec ? pmma : amma;
+            const float* Bm = st.kind == 0 ? Bfree + (int64_t)st.idx * nk * 32 * Np
+                            : st.kind == 1 ? Breact + (int64_t)st.idx * nk * 32 * Np
+                                           : Bl2l + (int64_t)st.idx * nk * 32 * Np;
             bool stop = false;
-            for (int c = 0; c < nk; ++c, ++i) {
+            for (int c = st.c0; c < st.c1; ++c, ++i) {
                 const int stg = i % TC_STAGES;
                 const uint32_t ph = (uint32_t)((i / TC_STAGES) & 1);
                 if (s_abort || !mbar_wait(&empty[stg], ph ^ 1u)) { s_abort = 1; stop = true; break; }
@@ -267,13 +303,15 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
                         bulk_g2s(sb + part * 8192 + h * 4096, g, 4096u, &full[stg]);
                     }
                 }
-                bulk_g2s(sb + 16384, Bm + (int64_t)c * 32 * NP, (uint32_t)(NP * 128), &full[stg]);
+                const float* Bc = Bm + (int64_t)c * 32 * Np + (int64_t)n0 * 16;
+                bulk_g2s(sb + 16384, Bc, (uint32_t)(NB * 64), &full[stg]);
+                bulk_g2s(sb + 16384 + NB * 64, Bc + (int64_t)Np * 16, (uint32_t)(NB * 64), &full[stg]);
             }
             if (stop) break;
         }
     } else if (warp == 5 && lane == 0) {
         // ---------------- MMA issuer: one TMEM buffer per source step ----------------
-        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NP >> 3) << 17) | ((128u >> 4) << 24);
+        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NB >> 3) << 17) | ((128u >> 4) << 24);
         int i = 0;
         bool ok = true;
         for (int s = 0; s < nsteps && ok; ++s) {
@@ -281,7 +319,7 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
             if (s_abort || !mbar_wait(&dfree[b], (uint32_t)(((s >> 1) & 1) ^ 1))) { s_abort = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t dt = taddr + (uint32_t)(b * 128);
-            const int nk = steps[tile.s0 + s].kind == 2 ? kc2 : kc;
+            const int nk = steps[tile.s0 + s].c1 - steps[tile.s0 + s].c0;
             uint32_t accf = 0;
             for (int c = 0; c < nk; ++c, ++i) {
                 const int stg = i % TC_STAGES;
@@ -292,7 +330,7 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
 #pragma unroll
                 for (int ks = 0; ks < 2; ++ks) {
                     const uint64_t ah = sdesc(sb + ks * 256), al = sdesc(sb + 8192 + ks * 256);
-                    const uint64_t bh = sdesc(sb + 16384 + ks * 256), bl = sdesc(sb + 16384 + NP * 64 + ks * 256);
+                    const uint64_t bh = sdesc(sb + 16384 + ks * 256), bl = sdesc(sb + 16384 + NB * 64 + ks * 256);
                     mma_tf32(dt, ah, bh, idesc, accf);
                     accf = 1;
                     mma_tf32(dt, ah, bl, idesc, 1);
@@ -310,53 +348,151 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
 
 inline int round16(int x) { return (x + 15) / 16 * 16; }
 
+// Width of a level's real GEMM: 2 nc columns in nb blocks of nbw <= 128
+// (multiples of 16, padding spread over the blocks); K chunks of 16.
+void tc_widths(int ncoef, int* nb, int* nbw, int* np, int* kc) {
+    const int w = 2 * ncoef;
+    *nb = (w + TC_MAX_NP - 1) / TC_MAX_NP;
+    *nbw = round16((w + *nb - 1) / *nb);
+    *np = *nb * *nbw;
+    *kc = round16(w) / 16;
+}
+
+// Target pairs (b, b + 4) with b = 8 j + c (same child position, parents 2j
+// and 2j + 1); a missing or empty box is -1.  add(b0, b1) appends the pair's
+// source steps.
+// Append one source step as sub-steps of at most TC_STEP_CHUNKS K chunks.
+void push_step(std::vector<TcStep>& steps, int kind, int idx, int32_t s0, int32_t s1, int nk) {
+    for (int c0 = 0; c0 < nk; c0 += TC_STEP_CHUNKS)
+        steps.push_back({kind, idx, s0, s1, c0, std::min(nk, c0 + TC_STEP_CHUNKS)});
+}
+
+template <class NonEmpty, class Add>
+void pair_tiles(int64_t nbox, NonEmpty nonempty, Add add, std::vector<TcTile>& tiles, std::vector<TcStep>& steps) {
+    const int64_t ngroups = std::max<int64_t>(1, nbox / 8);
+    for (int64_t j = 0; j < ngroups; ++j)
+        for (int c = 0; c < 4; ++c) {
+            const int64_t b0 = 8 * j + c, b1 = 8 * j + 4 + c;
+            const bool e0 = b0 < nbox && nonempty(b0), e1 = b1 < nbox && nonempty(b1);
+            if (!e0 && !e1) continue;
+            TcTile t;
+            t.b0 = e0 ? (int32_t)b0 : -1;
+            t.b1 = e1 ? (int32_t)b1 : -1;
+            t.s0 = (int32_t)steps.size();
+            add(t.b0, t.b1);
+            t.s1 = (int32_t)steps.size();
+            tiles.push_back(t);   // also without steps: the kernel then writes zeros
+        }
+}
+
+hfmm_status upload_tiles(hfmm_plan_s* P, const std::vector<TcTile>& tiles, const std::vector<TcStep>& steps,
+                         void** dt, void** ds, int64_t* nt) {
+    *nt = (int64_t)tiles.size();
+    HFMM_TRY(plan_alloc(P, dt, sizeof(TcTile) * std::max<size_t>(tiles.size(), 1)));
+    HFMM_TRY(plan_alloc(P, ds, sizeof(TcStep) * std::max<size_t>(steps.size(), 1)));
+    if (!tiles.empty()) {
+        HFMM_CUDA_TRY(cudaMemcpy(*dt, tiles.data(), sizeof(TcTile) * tiles.size(), cudaMemcpyHostToDevice));
+        HFMM_CUDA_TRY(cudaMemcpy(*ds, steps.data(), sizeof(TcStep) * steps.size(), cudaMemcpyHostToDevice));
+    }
+    return HFMM_OK;
+}
+
+hfmm_status btable(hfmm_plan_s* P, const cf* M, int nmat, int nin, int nout, int Np, int kc, float** out,
+                   cudaStream_t st) {
+    const size_t floats = (size_t)nmat * kc * 32 * Np;
+    HFMM_TRY(plan_alloc(P, (void**)out, sizeof(float) * floats));
+    tc_btable_kernel<<<4 * 152, 256, 0, st>>>(M, nmat, nin, nout, Np, kc, *out);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    P->table_bytes += sizeof(float) * (double)floats;
+    return HFMM_OK;
+}
+
+// Arguments of one launch of the tensor-core kernel.
+struct TcLaunch {
+    const void* tiles;
+    const void* steps;
+    int64_t ntiles;
+    const float* Bfree;
+    const float* Breact;
+    const float* Bsec;
+    const float* amma;
+    const float* pmma;
+    cf* out;
+    int nc, kc, kc2, np, nb, nbw;
+    float* sdst;
+    int kcd;
+};
+
+template <int NB>
+hfmm_status launch_nb(hfmm_plan_s* P, const TcLaunch& a, int nrhs, cudaStream_t st) {
+    const size_t smem = (size_t)TC_STAGES * (16384 + NB * 128) + 256;
+    static bool attr_set = false;
+    if (!attr_set) {
+        HFMM_CUDA_TRY(cudaFuncSetAttribute(m2l_tc_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    const int nrc = (P->max_rhs + 63) / 64;
+    dim3 grid((unsigned)a.ntiles, (unsigned)((nrhs + 63) / 64), (unsigned)a.nb);
+    m2l_tc_kernel<NB><<<grid, TC2_THREADS, smem, st>>>(
+        (const TcTile*)a.tiles, (const TcStep*)a.steps, a.Bfree, a.Breact, a.Bsec, a.amma, a.pmma, P->tc_zero, a.out,
+        nrhs, a.nc, a.kc, a.kc2, nrc, a.np, a.sdst, a.kcd, P->tc_err);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    return HFMM_OK;
+}
+
+hfmm_status launch_tc(hfmm_plan_s* P, const TcLaunch& a, int nrhs, cudaStream_t st) {
+    if (a.ntiles == 0) return HFMM_OK;
+    switch (a.nbw) {
+        case 16: return launch_nb<16>(P, a, nrhs, st);
+        case 32: return launch_nb<32>(P, a, nrhs, st);
+        case 48: return launch_nb<48>(P, a, nrhs, st);
+        case 64: return launch_nb<64>(P, a, nrhs, st);
+        case 80: return launch_nb<80>(P, a, nrhs, st);
+        case 96: return launch_nb<96>(P, a, nrhs, st);
+        case 112: return launch_nb<112>(P, a, nrhs, st);
+        case 128: return launch_nb<128>(P, a, nrhs, st);
+    }
+    hfmm_set_error("tensor-core pass: unsupported block width %d", a.nbw);
+    return HFMM_ERR_UNSUPPORTED;
+}
+
 }  // namespace
 
-// Plan-time preparation of the tensor-core downward pass for every level
-// whose real GEMM width fits one TMEM buffer (2 nc <= 128); K (including the
-// parent's width for L2L) is streamed in chunks of 16.
+// Plan-time preparation of the tensor-core upward (M2M) and downward
+// (L2L + M2L) passes of every level lmin .. L.
 hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
     const int L = P->L;
-    const int grid = 4 * 152, tb = 256;
     const int nrc = (P->max_rhs + 63) / 64;
-    for (int l = std::max(2, P->lmin); l <= L; ++l) {
+    const auto& lb = P->h_leaf_begin;
+    for (int l = P->lmin; l <= L; ++l) {
         LevelInfo& lv = P->lev[l];
-        const int Np = round16(2 * lv.ncoef);
+        tc_widths(lv.ncoef, &lv.tc_nb, &lv.tc_nbw, &lv.tc_np, &lv.tc_kc);
         const bool has_parent = l > P->lmin;
         const int npp = has_parent ? P->lev[l - 1].ncoef : 0;
-        if (Np > TC_MAX_NP) continue;
-        if (lv.nbox < 8) continue;
-        lv.tc_np = Np;
-        lv.tc_kc = Np / 16;
-        lv.tc_kc2 = has_parent ? round16(2 * npp) / 16 : 0;
+        lv.tc_kc2 = has_parent ? P->lev[l - 1].tc_kc : 0;
+        const int Np = lv.tc_np;
         // MMA-ready copies: this level's multipoles and the parent's locals
-        HFMM_TRY(plan_alloc(P, (void**)&lv.tc_amma, sizeof(float) * (size_t)lv.nbox * nrc * lv.tc_kc * 2048));
-        P->buffer_bytes += sizeof(float) * (double)lv.nbox * nrc * lv.tc_kc * 2048;
+        const size_t ab = sizeof(float) * (size_t)lv.nbox * nrc * lv.tc_kc * 2048;
+        HFMM_TRY(plan_alloc(P, (void**)&lv.tc_amma, ab));
+        HFMM_CUDA_TRY(cudaMemsetAsync(lv.tc_amma, 0, ab, st));
+        P->buffer_bytes += (double)ab;
         if (has_parent) {
             const size_t pb = sizeof(float) * (size_t)P->lev[l - 1].nbox * nrc * lv.tc_kc2 * 2048;
             HFMM_TRY(plan_alloc(P, (void**)&lv.tc_pmma, pb));
+            HFMM_CUDA_TRY(cudaMemsetAsync(lv.tc_pmma, 0, pb, st));
             P->buffer_bytes += (double)pb;
         }
-        const size_t mat_f = (size_t)lv.tc_kc * 32 * Np;      // floats per V / reaction matrix
-        HFMM_TRY(plan_alloc(P, (void**)&lv.tc_bfree, sizeof(float) * 49 * mat_f));
-        tc_btable_kernel<<<grid, tb, 0, st>>>(lv.t_free32, 49, lv.ncoef, lv.ncoef, Np, lv.tc_kc, lv.tc_bfree);
-        HFMM_CUDA_TRY(cudaGetLastError());
-        P->table_bytes += sizeof(float) * 49.0 * mat_f;
-        if (lv.t_react32 && lv.n_react_entries > 0) {
-            HFMM_TRY(plan_alloc(P, (void**)&lv.tc_breact, sizeof(float) * lv.n_react_entries * mat_f));
-            tc_btable_kernel<<<grid, tb, 0, st>>>(lv.t_react32, lv.n_react_entries, lv.ncoef, lv.ncoef, Np, lv.tc_kc,
-                                                  lv.tc_breact);
-            HFMM_CUDA_TRY(cudaGetLastError());
-            P->table_bytes += sizeof(float) * (double)lv.n_react_entries * mat_f;
+        if (lv.nv > 0) HFMM_TRY(btable(P, lv.t_free32, 49, lv.ncoef, lv.ncoef, Np, lv.tc_kc, &lv.tc_bfree, st));
+        if (lv.nr > 0 && !(lv.t_react32 && lv.n_react_entries > 0)) {
+            hfmm_set_error("tensor-core pass: level %d has reaction pairs but no reaction table", l);
+            return HFMM_ERR_UNSUPPORTED;
         }
-        if (has_parent) {
-            const size_t mat_l = (size_t)lv.tc_kc2 * 32 * Np;
-            HFMM_TRY(plan_alloc(P, (void**)&lv.tc_bl2l, sizeof(float) * 4 * mat_l));
-            tc_btable_kernel<<<grid, tb, 0, st>>>(P->lev[l - 1].t_l2l32, 4, npp, lv.ncoef, Np, lv.tc_kc2, lv.tc_bl2l);
-            HFMM_CUDA_TRY(cudaGetLastError());
-            P->table_bytes += sizeof(float) * 4.0 * mat_l;
-        }
-        // tiles (b, b + 4) with b = 8 j + c, and their source steps
+        if (lv.nr > 0)
+            HFMM_TRY(btable(P, lv.t_react32, lv.n_react_entries, lv.ncoef, lv.ncoef, Np, lv.tc_kc, &lv.tc_breact, st));
+        if (has_parent)
+            HFMM_TRY(btable(P, P->lev[l - 1].t_l2l32, 4, npp, lv.ncoef, Np, lv.tc_kc2, &lv.tc_bl2l, st));
+
+        // downward tiles: L2L from the parent, every V-list offset, every reaction entry
         const int64_t nbox = lv.nbox;
         std::vector<int32_t> vb, vs, vo, rb, rs, rt;
         auto fetch = [&](const int32_t* db, const int32_t* ds, const int32_t* dx, int64_t nnz,
@@ -375,108 +511,89 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
         HFMM_CUDA_TRY(cudaStreamSynchronize(st));
         HFMM_TRY(fetch(lv.nv ? lv.v_begin : nullptr, lv.v_src, lv.v_off, lv.nv, vb, vs, vo));
         HFMM_TRY(fetch(lv.nr ? lv.r_begin : nullptr, lv.r_src, lv.r_tab, lv.nr, rb, rs, rt));
-        const auto& lb = P->h_leaf_begin;
         const int64_t span = (int64_t)1 << (2 * (L - l));
         auto nonempty = [&](int64_t b) { return lb[(b + 1) * span] > lb[b * span]; };
         std::vector<TcTile> tiles;
         std::vector<TcStep> steps;
-        for (int64_t j = 0; j < nbox / 8; ++j)
-            for (int c = 0; c < 4; ++c) {
-                const int64_t b0 = 8 * j + c, b1 = 8 * j + 4 + c;
-                const bool e0 = nonempty(b0), e1 = nonempty(b1);
-                if (!e0 && !e1) continue;
-                TcTile t;
-                t.b0 = e0 ? (int32_t)b0 : -1;
-                t.b1 = e1 ? (int32_t)b1 : -1;
-                t.s0 = (int32_t)steps.size();
-                if (has_parent) steps.push_back({2, c, e0 ? (int32_t)(b0 >> 2) : -1, e1 ? (int32_t)(b1 >> 2) : -1});
-                if (!vb.empty() && lv.nv) {
-                    int32_t s0[49], s1[49];
-                    for (int o = 0; o < 49; ++o) s0[o] = s1[o] = -1;
-                    if (e0) for (int32_t e = vb[b0]; e < vb[b0 + 1]; ++e) s0[vo[e]] = vs[e];
-                    if (e1) for (int32_t e = vb[b1]; e < vb[b1 + 1]; ++e) s1[vo[e]] = vs[e];
-                    for (int o = 0; o < 49; ++o)
-                        if (s0[o] >= 0 || s1[o] >= 0) steps.push_back({0, o, s0[o], s1[o]});
-                }
-                if (lv.nr) {
-                    // merge the two reaction lists by table entry (dx, ysum)
-                    std::map<int32_t, std::pair<int32_t, int32_t>> mm;
-                    if (e0) for (int32_t e = rb[b0]; e < rb[b0 + 1]; ++e) mm[rt[e]] = {rs[e], -1};
-                    if (e1) for (int32_t e = rb[b1]; e < rb[b1 + 1]; ++e) {
-                        auto it = mm.find(rt[e]);
-                        if (it == mm.end()) mm[rt[e]] = {-1, rs[e]};
-                        else it->second.second = rs[e];
-                    }
-                    for (auto& kv : mm) steps.push_back({1, kv.first, kv.second.first, kv.second.second});
-                }
-                t.s1 = (int32_t)steps.size();
-                tiles.push_back(t);
+        pair_tiles(nbox, nonempty, [&](int32_t b0, int32_t b1) {
+            const int c = (int)((b0 >= 0 ? b0 : b1) & 3);
+            if (has_parent) push_step(steps, 2, c, b0 >= 0 ? b0 >> 2 : -1, b1 >= 0 ? b1 >> 2 : -1, lv.tc_kc2);
+            if (lv.nv) {
+                int32_t s0[49], s1[49];
+                for (int o = 0; o < 49; ++o) s0[o] = s1[o] = -1;
+                if (b0 >= 0) for (int32_t e = vb[b0]; e < vb[b0 + 1]; ++e) s0[vo[e]] = vs[e];
+                if (b1 >= 0) for (int32_t e = vb[b1]; e < vb[b1 + 1]; ++e) s1[vo[e]] = vs[e];
+                for (int o = 0; o < 49; ++o)
+                    if (s0[o] >= 0 || s1[o] >= 0) push_step(steps, 0, o, s0[o], s1[o], lv.tc_kc);
             }
-        lv.tc_ntiles = (int64_t)tiles.size();
-        HFMM_TRY(plan_alloc(P, (void**)&lv.tc_tiles, sizeof(TcTile) * std::max<size_t>(tiles.size(), 1)));
-        HFMM_TRY(plan_alloc(P, (void**)&lv.tc_steps, sizeof(TcStep) * std::max<size_t>(steps.size(), 1)));
-        if (!tiles.empty()) {
-            HFMM_CUDA_TRY(cudaMemcpy(lv.tc_tiles, tiles.data(), sizeof(TcTile) * tiles.size(), cudaMemcpyHostToDevice));
-            HFMM_CUDA_TRY(cudaMemcpy(lv.tc_steps, steps.data(), sizeof(TcStep) * steps.size(), cudaMemcpyHostToDevice));
-        }
+            if (lv.nr) {
+                // merge the two reaction lists by table entry (dx, ysum)
+                std::map<int32_t, std::pair<int32_t, int32_t>> mm;
+                if (b0 >= 0) for (int32_t e = rb[b0]; e < rb[b0 + 1]; ++e) mm[rt[e]] = {rs[e], -1};
+                if (b1 >= 0) for (int32_t e = rb[b1]; e < rb[b1 + 1]; ++e) {
+                    auto it = mm.find(rt[e]);
+                    if (it == mm.end()) mm[rt[e]] = {-1, rs[e]};
+                    else it->second.second = rs[e];
+                }
+                for (auto& kv : mm) push_step(steps, 1, kv.first, kv.second.first, kv.second.second, lv.tc_kc);
+            }
+        }, tiles, steps);
+        HFMM_TRY(upload_tiles(P, tiles, steps, &lv.tc_tiles, &lv.tc_steps, &lv.tc_ntiles));
+    }
+    // M2M into level l from its children (level l + 1)
+    for (int l = P->lmin; l < L; ++l) {
+        LevelInfo& lv = P->lev[l];
+        const LevelInfo& ch = P->lev[l + 1];
+        HFMM_TRY(btable(P, lv.t_m2m32, 4, ch.ncoef, lv.ncoef, lv.tc_np, ch.tc_kc, &lv.tc_bm2m, st));
+        const int64_t span = (int64_t)1 << (2 * (L - l)), cspan = span >> 2;
+        auto nonempty = [&](int64_t b) { return lb[(b + 1) * span] > lb[b * span]; };
+        auto cnonempty = [&](int64_t b) { return lb[(b + 1) * cspan] > lb[b * cspan]; };
+        std::vector<TcTile> tiles;
+        std::vector<TcStep> steps;
+        pair_tiles(lv.nbox, nonempty, [&](int32_t b0, int32_t b1) {
+            for (int c = 0; c < 4; ++c) {
+                const int32_t s0 = (b0 >= 0 && cnonempty(4 * (int64_t)b0 + c)) ? 4 * b0 + c : -1;
+                const int32_t s1 = (b1 >= 0 && cnonempty(4 * (int64_t)b1 + c)) ? 4 * b1 + c : -1;
+                if (s0 >= 0 || s1 >= 0) push_step(steps, 2, c, s0, s1, ch.tc_kc);
+            }
+        }, tiles, steps);
+        HFMM_TRY(upload_tiles(P, tiles, steps, &lv.tc_mtiles, &lv.tc_msteps, &lv.tc_nmtiles));
     }
     HFMM_TRY(plan_alloc(P, (void**)&P->tc_err, sizeof(int)));
     HFMM_CUDA_TRY(cudaMemsetAsync(P->tc_err, 0, sizeof(int), st));
     HFMM_TRY(plan_alloc(P, (void**)&P->tc_zero, 4096));
     HFMM_CUDA_TRY(cudaMemsetAsync(P->tc_zero, 0, 4096, st));
     HFMM_CUDA_TRY(cudaStreamSynchronize(st));
+    P->tc_on = true;
     return HFMM_OK;
 }
 
-// MMA-ready copy of the multipoles of a tensor-core level (after the upward pass).
+// MMA-ready copy of the leaf multipoles (after P2M).
 hfmm_status split_mult_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st) {
     LevelInfo& lv = P->lev[l];
-    if (lv.tc_ntiles == 0) return HFMM_OK;
     const int nrc = (P->max_rhs + 63) / 64;
     split_rows_kernel<<<4 * 152, 128, 0, st>>>(lv.mult32, lv.nbox, nrhs, lv.ncoef, lv.tc_kc, nrc, lv.tc_amma);
     HFMM_CUDA_TRY(cudaGetLastError());
     return HFMM_OK;
 }
 
-template <int NP>
-static hfmm_status launch_np(hfmm_plan_s* P, LevelInfo& lv, const float* pmma, int nrhs, cudaStream_t st) {
-    const size_t smem = (size_t)TC_STAGES * (16384 + NP * 128) + 256;
-    static bool attr_set = false;
-    if (!attr_set) {
-        HFMM_CUDA_TRY(cudaFuncSetAttribute(m2l_tc_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
-    }
-    const int nrc = (P->max_rhs + 63) / 64;
-    dim3 grid((unsigned)lv.tc_ntiles, (unsigned)((nrhs + 63) / 64));
-    m2l_tc_kernel<NP><<<grid, TC2_THREADS, smem, st>>>(
-        (const TcTile*)lv.tc_tiles, (const TcStep*)lv.tc_steps, lv.tc_bfree, lv.tc_breact, lv.tc_bl2l, lv.tc_amma,
-        pmma, P->tc_zero, lv.loc32, nrhs, lv.ncoef, lv.tc_kc, lv.tc_kc2, nrc, P->tc_err);
-    HFMM_CUDA_TRY(cudaGetLastError());
-    return HFMM_OK;
+// Tensor-core M2M into level l (children at l + 1 already MMA-ready); writes
+// the FP32 multipoles and their MMA-ready copy.
+hfmm_status launch_m2m_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st) {
+    LevelInfo& lv = P->lev[l];
+    const LevelInfo& ch = P->lev[l + 1];
+    TcLaunch a{lv.tc_mtiles, lv.tc_msteps, lv.tc_nmtiles, nullptr, nullptr, lv.tc_bm2m, nullptr, ch.tc_amma,
+               lv.mult32, lv.ncoef, 0, ch.tc_kc, lv.tc_np, lv.tc_nb, lv.tc_nbw, lv.tc_amma, lv.tc_kc};
+    return launch_tc(P, a, nrhs, st);
 }
 
-// Launch the tensor-core downward pass of level l (nrhs right-hand sides).
+// Tensor-core downward pass of level l; writes the FP32 local expansions and,
+// below the leaves, their MMA-ready copy for the children's L2L.
 hfmm_status launch_m2l_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st) {
     LevelInfo& lv = P->lev[l];
-    if (lv.tc_ntiles == 0) return HFMM_OK;
-    const bool has_parent = l > P->lmin;
-    const int nrc = (P->max_rhs + 63) / 64;
-    if (has_parent) {
-        const LevelInfo& pl = P->lev[l - 1];
-        split_rows_kernel<<<4 * 152, 128, 0, st>>>(pl.loc32, pl.nbox, nrhs, pl.ncoef, lv.tc_kc2, nrc, lv.tc_pmma);
-        HFMM_CUDA_TRY(cudaGetLastError());
-    }
-    const float* pm = has_parent ? lv.tc_pmma : nullptr;
-    switch (lv.tc_np) {
-        case 16: return launch_np<16>(P, lv, pm, nrhs, st);
-        case 32: return launch_np<32>(P, lv, pm, nrhs, st);
-        case 48: return launch_np<48>(P, lv, pm, nrhs, st);
-        case 64: return launch_np<64>(P, lv, pm, nrhs, st);
-        case 80: return launch_np<80>(P, lv, pm, nrhs, st);
-        case 96: return launch_np<96>(P, lv, pm, nrhs, st);
-        case 112: return launch_np<112>(P, lv, pm, nrhs, st);
-        case 128: return launch_np<128>(P, lv, pm, nrhs, st);
-    }
-    hfmm_set_error("tensor-core pass: unsupported width %d", lv.tc_np);
-    return HFMM_ERR_UNSUPPORTED;
+    const bool below = l < P->L;
+    TcLaunch a{lv.tc_tiles, lv.tc_steps, lv.tc_ntiles, lv.tc_bfree, lv.tc_breact, lv.tc_bl2l, lv.tc_amma,
+               lv.tc_pmma, lv.loc32, lv.ncoef, lv.tc_kc, lv.tc_kc2, lv.tc_np, lv.tc_nb, lv.tc_nbw,
+               below ? P->lev[l + 1].tc_pmma : nullptr, below ? P->lev[l + 1].tc_kc2 : 0};
+    return launch_tc(P, a, nrhs, st);
 }

@@ -53,15 +53,21 @@ struct LevelInfo {
     cf* t_m2m32 = nullptr;        // [4][m child][j parent]   (this level = parent)
     cf* t_l2l32 = nullptr;        // [4][n parent][m child]   (this level = parent)
     double* d_log_s = nullptr;    // [p + 1] log s(n) on the device
-    // tensor-core downward pass (m2l_tc.cu): real GEMM width, K chunks, pre-split
-    // TF32 operator chunks, target-pair tiles and their source steps
-    int tc_np = 0, tc_kc = 0, tc_kc2 = 0;
+    // tensor-core passes (m2l_tc.cu): real GEMM width tc_np = tc_nb column blocks
+    // of tc_nbw, K chunks of this level (tc_kc) and of the parent (tc_kc2),
+    // pre-split TF32 operator chunks, target-pair tiles and their source steps
+    // for the downward pass (L2L + M2L) and for M2M into this level
+    int tc_np = 0, tc_nb = 0, tc_nbw = 0, tc_kc = 0, tc_kc2 = 0;
     float* tc_bfree = nullptr;
     float* tc_breact = nullptr;
     float* tc_bl2l = nullptr;
+    float* tc_bm2m = nullptr;
     void* tc_tiles = nullptr;
     void* tc_steps = nullptr;
     int64_t tc_ntiles = 0;
+    void* tc_mtiles = nullptr;
+    void* tc_msteps = nullptr;
+    int64_t tc_nmtiles = 0;
     float* tc_amma = nullptr;     // MMA-ready multipoles of this level
     float* tc_pmma = nullptr;     // MMA-ready local expansions of the parent level
 };
@@ -111,6 +117,7 @@ struct hfmm_plan_s {
     void* dj_jobs = nullptr;        // direct-block quadrature jobs and segments (tables.cu)
     void* dj_segs = nullptr;
     int64_t dj_njobs = 0;
+    bool tc_on = false;             // every level lmin..L has tensor-core M2M / downward state
     int* tc_err = nullptr;          // set by the tensor-core pass when a bounded wait gave up
     float* tc_zero = nullptr;       // 4 KB of zeros: the A half of a missing source box
 
@@ -121,6 +128,10 @@ struct hfmm_plan_s {
     double plan_ms = 0.0;
     int64_t p2p_point_pairs = 0;    // sum over leaves T of n_T * sum_{S in U(T)} n_S
     std::vector<void*> allocations;
+
+    // autotuning record (HFMM_FLAG_AUTOTUNE)
+    int tune_levels[3] = {0, 0, 0};
+    double tune_ms[3] = {0.0, 0.0, 0.0};
 
     // profiling (HFMM_FLAG_PROFILE)
     int flags = 0;
@@ -167,6 +178,7 @@ hfmm_status build_local_coords(hfmm_plan_s* P, cudaStream_t st);
 // m2l_tc.cu
 hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status launch_m2l_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st);
+hfmm_status launch_m2m_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st);
 hfmm_status split_mult_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st);
 
 // Morton helpers

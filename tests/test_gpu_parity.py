@@ -258,7 +258,8 @@ def test_mixed_many_rhs_and_adjoint():
 
 
 def test_tensor_core_downward_pass_matches_simt_and_fp64():
-    """tcgen05 3xTF32 downward pass against the FP32 SIMT pass (same plan
+    """tcgen05 3xTF32 M2M and downward passes (every level, wide coarse
+    levels in column blocks) against the FP32 SIMT passes (same plan
     otherwise) and against the FP64 path, 64 right-hand sides (one full
     M = 128 tile of two target boxes)."""
     from paper_1703_09136_gb300 import MIXED
@@ -268,15 +269,61 @@ def test_tensor_core_downward_pass_matches_simt_and_fp64():
     tc = Plan(xy, CFG4_MED, tol=1e-6, leaf_size=16, max_rhs=64, precision=MIXED)
     si = Plan(xy, CFG4_MED, tol=1e-6, leaf_size=16, max_rhs=64, precision=MIXED, simt_m2l=True)
     f64 = Plan(xy, CFG4_MED, tol=1e-6, leaf_size=16, max_rhs=4)
-    assert tc.info["tensor_levels"] >= 2 and si.info["tensor_levels"] == 0
+    assert tc.info["tensor_levels"] == tc.info["levels"] - tc.info["lmin"] + 1
+    assert si.info["tensor_levels"] == 0
     y_tc = tc.apply(q32).cpu().numpy()
     y_si = si.apply(q32).cpu().numpy()
     y64 = f64.apply(torch.from_numpy(q[:4].copy()).cuda()).cpu().numpy()
     assert tc.info["device_error"] == 0
-    assert direct.rel_l2(y_tc, y_si) < 2e-6
-    assert direct.rel_l2(y_tc[:4], y64) < MIXED_TOL
+    e_tc = direct.rel_l2(y_tc[:4], y64)
+    e_si = direct.rel_l2(y_si[:4], y64)
+    assert e_tc < MIXED_TOL and e_si < MIXED_TOL, (e_tc, e_si)
+    # 3xTF32 drops the lo*lo term and truncates inside TMEM between drains:
+    # a little above the SIMT FP32 error, never far above it
+    assert e_tc < 2.5 * e_si, (e_tc, e_si)
+    assert direct.rel_l2(y_tc, y_si) < 2.0 * (e_tc + e_si)
     for p in (tc, si, f64):
         p.close()
+
+
+def test_tensor_core_ragged_rhs_blocks_and_changing_width():
+    """Two 64-row right-hand-side blocks with a ragged second block (70 RHS),
+    then a narrower apply (5 RHS) on the same plan: every column agrees with
+    the FP64 path, so rows beyond nrhs never leak into the next apply."""
+    from paper_1703_09136_gb300 import MIXED
+    xy = W.points_in_box(4, 6000, ((0.0, 1.0), (0.02, 1.02)))
+    tc = Plan(xy, CFG4_MED, tol=1e-6, leaf_size=16, max_rhs=70, precision=MIXED)
+    f64 = Plan(xy, CFG4_MED, tol=1e-6, leaf_size=16, max_rhs=70)
+    assert tc.info["tensor_levels"] == tc.info["levels"] - tc.info["lmin"] + 1
+    for nrhs, salt in ((70, 11), (5, 12), (70, 13)):
+        q = W.strengths(4, 6000, nrhs, salt=salt)
+        y_tc = tc.apply(torch.from_numpy(q.astype(np.complex64)).cuda()).cpu().numpy()
+        y64 = f64.apply(torch.from_numpy(q).cuda()).cpu().numpy()
+        for r in range(nrhs):
+            assert direct.rel_l2(y_tc[r], y64[r]) < MIXED_TOL, (nrhs, r)
+    assert tc.info["device_error"] == 0
+    tc.close()
+    f64.close()
+
+
+def test_autotune_keeps_fastest_depth_and_same_result():
+    """HFMM_FLAG_AUTOTUNE tries the leaf levels around the leaf_size choice,
+    keeps the fastest, and the kept plan gives the result of a plan built
+    with that depth directly."""
+    med = W.WORKLOADS[2].medium
+    xy = W.points(2, 20000)
+    q = torch.from_numpy(W.strengths(2, 20000, 2)).cuda()
+    tuned = Plan(xy, med, tol=1e-6, leaf_size=32, max_rhs=2, autotune=True)
+    inf = tuned.info
+    tried = inf["tune"]
+    assert len(tried) >= 2 and all(ms > 0 for ms in tried.values())
+    assert inf["levels"] == min(tried, key=tried.get)
+    fixed = Plan(xy, med, tol=1e-6, levels=inf["levels"], max_rhs=2)
+    y_t = tuned.apply(q)
+    y_f = fixed.apply(q)
+    assert torch.equal(y_t, y_f)
+    tuned.close()
+    fixed.close()
 
 
 # --- gradients ---------------------------------------------------------------------
@@ -325,3 +372,30 @@ def test_autograd_gradients_match_finite_differences():
             g = q.grad[0, j]
             want = float(g.real) if part == 1.0 else float(g.imag)
             assert abs(fd - want) < 1e-5 * max(1.0, abs(fd))
+
+
+# --- batched uneven instances ------------------------------------------------------
+
+def test_batch_graph_equals_individual_plans():
+    """Uneven instances in one captured CUDA graph give exactly the results of
+    their single-plan applies (FP64 and mixed), on the first (recording) call
+    and on a replay."""
+    from paper_1703_09136_gb300 import Batch, MIXED
+    med = W.WORKLOADS[5].medium
+    sizes = [3000, 700, 12000, 1500, 5000]
+    xys = [W.points(5, n, salt=i) for i, n in enumerate(sizes)]
+    for prec, cdt in ((0, torch.complex128), (MIXED, torch.complex64)):
+        qs = [torch.from_numpy(W.strengths(5, n, 2, salt=i)).cuda().to(cdt) for i, n in enumerate(sizes)]
+        batch = Batch(xys, med, leaf_size=32, precision=prec, max_rhs=2)
+        ys = [torch.empty_like(q) for q in qs]
+        for rep in range(2):
+            for y in ys:
+                y.zero_()
+            batch.apply(qs, ys)
+            torch.cuda.synchronize()
+            for xy, q, y in zip(xys, qs, ys):
+                single = Plan(xy, med, leaf_size=32, precision=prec, max_rhs=2)
+                ref = single.apply(q)
+                single.close()
+                assert torch.equal(ref, y)
+        batch.close()
