@@ -133,37 +133,6 @@ __device__ void point_basis32(double px, double py, double cx, double cy, double
     }
 }
 
-__global__ void p2m32_kernel(const int32_t* lb, const double2* xs, const cf* qs, int64_t n, int nrhs,
-                             double x0, double y0, double h, double k, int p, const double* log_s,
-                             int chunk, cf* mult) {
-    extern __shared__ double smem[];
-    const int64_t b = blockIdx.x;
-    const int ncoef = 2 * p + 1;
-    double* Jt = smem;
-    cf* B = (cf*)(Jt + (size_t)chunk * (p + 1));
-    const int32_t lo = lb[b], hi = lb[b + 1];
-    const double cx = x0 + (morton_x((uint32_t)b) + 0.5) * h;
-    const double cy = y0 + (morton_y((uint32_t)b) + 0.5) * h;
-    cf* out = mult + (int64_t)b * nrhs * ncoef;
-    const int items = nrhs * ncoef;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) out[it] = cfmk(0.f, 0.f);
-    for (int32_t c0 = lo; c0 < hi; c0 += chunk) {
-        const int cnt = min(chunk, hi - c0);
-        __syncthreads();
-        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-            const double2 pt = xs[c0 + t];
-            point_basis32(pt.x, pt.y, cx, cy, k, p, -1, log_s, Jt + (size_t)t * (p + 1), B + (size_t)t * ncoef);
-        }
-        __syncthreads();
-        for (int it = threadIdx.x; it < items; it += blockDim.x) {
-            const int r = it / ncoef, m = it % ncoef;
-            cf acc = out[it];
-            const cf* qr = qs + (int64_t)r * n + c0;
-            for (int t = 0; t < cnt; ++t) cfma32(acc, qr[t], B[(size_t)t * ncoef + m]);
-            out[it] = acc;
-        }
-    }
-}
 
 // M2M (scaled): a~^P[r][j] = sum_c sum_m T~[c][m][j] a~^c[r][m]
 __global__ void m2m32_kernel(const cf* child, const cf* T, int pc, int pp, int nrhs, cf* parent) {
@@ -263,39 +232,6 @@ __global__ void __launch_bounds__(DOWN_THREADS) down32_kernel(
     }
 }
 
-__global__ void l2p32_kernel(const int32_t* lb, const double2* xs, const cf* loc, int64_t n, int nrhs,
-                             double x0, double y0, double h, double k, int p, const double* log_s, int chunk,
-                             cf* ys) {
-    extern __shared__ double smem[];
-    const int64_t b = blockIdx.x;
-    const int32_t lo = lb[b], hi = lb[b + 1];
-    if (hi <= lo) return;
-    const int ncoef = 2 * p + 1;
-    double* Jt = smem;
-    cf* B = (cf*)(Jt + (size_t)chunk * (p + 1));
-    const double cx = x0 + (morton_x((uint32_t)b) + 0.5) * h;
-    const double cy = y0 + (morton_y((uint32_t)b) + 0.5) * h;
-    const cf* beta = loc + (int64_t)b * nrhs * ncoef;
-    for (int32_t c0 = lo; c0 < hi; c0 += chunk) {
-        const int cnt = min(chunk, hi - c0);
-        __syncthreads();
-        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-            const double2 pt = xs[c0 + t];
-            point_basis32(pt.x, pt.y, cx, cy, k, p, +1, log_s, Jt + (size_t)t * (p + 1), B + (size_t)t * ncoef);
-        }
-        __syncthreads();
-        const int items = nrhs * cnt;
-        for (int it = threadIdx.x; it < items; it += blockDim.x) {
-            const int r = it / cnt, t = it % cnt;
-            cf acc = cfmk(0.f, 0.f);
-            const cf* br = beta + (int64_t)r * ncoef;
-            for (int m = 0; m < ncoef; ++m) cfma32(acc, br[m], B[(size_t)t * ncoef + m]);
-            cf* yy = ys + (int64_t)r * n + c0 + t;
-            yy->x += -0.25f * acc.y;
-            yy->y += 0.25f * acc.x;
-        }
-    }
-}
 
 // point offsets from their own leaf centre, FP32 (near-field geometry without FP64)
 __global__ void local_coords_kernel(const int32_t* lb, const double2* xs, int64_t nleaf, double x0,
@@ -308,185 +244,268 @@ __global__ void local_coords_kernel(const int32_t* lb, const double2* xs, int64_
         xl[i] = make_float2((float)(xs[i].x - cx), (float)(xs[i].y - cy));
 }
 
-// P2P free-space part, FP32 (Algorithm 1, step 5): one CTA per non-empty
-// target leaf, 32 x 32 blocks of (i/4) H0 values in shared memory, source
-// strengths of 64 right-hand sides staged beside them, 2 targets x 4 RHS
-// accumulators per thread.
-constexpr int P2T = 32;            // targets / sources per block
-constexpr int P2R = 64;            // right-hand sides per pass
-constexpr int P2_THREADS = 256;
+// P2P free-space part, FP32 (Algorithm 1, step 5), fused with L2P (step 4):
+// one CTA of 128 threads per non-empty target leaf.  Thread (r, half) owns right-hand side r of a
+// 64-wide block and NTH consecutive targets of a pass of up to 32 targets
+// (NTH = 4, 8, 12 or 16 from the pass width, so little padding is computed).
+// Sources are streamed per neighbour leaf in chunks of up to 32 points: their
+// strengths [j][r] and the (i/4) H0 values [j][t] of the chunk are staged in
+// shared memory, and the inner loop runs over the chunk's real length; the G
+// reads are warp-wide broadcasts.  The leaf's local expansion enters the same
+// product as extra chunks.  Results go through shared memory so the
+// read-modify-write of y is coalesced along the points.
+constexpr int PC_THREADS = 128;
+constexpr int PC_SRC = 32;         // sources per chunk
+constexpr int PC_TGT = 32;         // targets per pass
+constexpr int PC_RHS = 64;         // right-hand sides per block
 
-__global__ void __launch_bounds__(P2_THREADS) p2p32b_kernel(const int32_t* lb, int L, const float2* xl,
+struct PcShared {
+    cf q[PC_SRC][PC_RHS + 1];      // strengths of the chunk; reused as y staging [t][r]
+    __align__(16) cf g[PC_SRC][PC_TGT];
+    float2 tp[PC_TGT];
+    float tj[H0_NI][H0_DEG + 1];
+    float tr[H0_NI][H0_DEG + 1];
+};
+
+__device__ __forceinline__ cf green_free_f32_tab(const PcShared& S, float z) {
+    const int iv = min((int)(z * H0_INV_DZ), H0_NI - 1);
+    const float t = (z - ((float)iv + 0.5f) / H0_INV_DZ) * (2.0f * H0_INV_DZ);
+    float jj = S.tj[iv][H0_DEG], rr = S.tr[iv][H0_DEG];
+#pragma unroll
+    for (int d = H0_DEG - 1; d >= 0; --d) {
+        jj = fmaf(jj, t, S.tj[iv][d]);
+        rr = fmaf(rr, t, S.tr[iv][d]);
+    }
+    const float y = fmaf(0.63661977236758134f * logf(0.5f * z), jj, rr);
+    return cfmk(-0.25f * y, 0.25f * jj);
+}
+
+// acc[i] += sum_{j < sn} S.g[j][tb + i] * S.q[j][r]
+template <int NTH>
+__device__ __forceinline__ void pc_mac(const PcShared& S, int sn, int r, int tb, cf* acc) {
+#pragma unroll 2
+    for (int j = 0; j < sn; ++j) {
+        const cf qv = S.q[j][r];
+        const float4* gp = (const float4*)&S.g[j][tb];
+#pragma unroll
+        for (int i = 0; i < NTH; i += 2) {
+            const float4 g2 = gp[i >> 1];
+            cfma32(acc[i], cfmk(g2.x, g2.y), qv);
+            cfma32(acc[i + 1], cfmk(g2.z, g2.w), qv);
+        }
+    }
+}
+
+template <int NTH>
+__device__ __forceinline__ void p2p_pass(PcShared& S, const int32_t* lb, int L, int64_t b, int ix, int iy,
+                                         const float2* xl, const cf* qs, int64_t n, int nrhs, int r0, int32_t t0,
+                                         int w, float k, float h, bool near, const cf* loc, const cf* basis,
+                                         int nc, cf* ys) {
+    const int tid = threadIdx.x;
+    const int r = tid & (PC_RHS - 1), half = tid >> 6;
+    const int tb = half * NTH;                       // first target of this thread
+    const int m = 1 << L;
+    cf acc[NTH];
+#pragma unroll
+    for (int i = 0; i < NTH; ++i) acc[i] = cfmk(0.f, 0.f);
+    __syncthreads();
+    if (tid < w) S.tp[tid] = xl[t0 + tid];
+    for (int dy = -1; dy <= 1 && near; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int sx = ix + dx, sy = iy + dy;
+            if (sx < 0 || sy < 0 || sx >= m || sy >= m) continue;
+            const uint32_t s = morton((uint32_t)sx, (uint32_t)sy);
+            const int32_t slo = lb[s], shi = lb[s + 1];
+            const float ox = (float)(-dx) * h, oy = (float)(-dy) * h;   // c_T - c_S
+            for (int32_t s0 = slo; s0 < shi; s0 += PC_SRC) {
+                const int sn = min(PC_SRC, shi - s0);
+                __syncthreads();
+                // strengths: consecutive threads take consecutive points of one RHS row
+                for (int e = tid; e < sn * PC_RHS; e += PC_THREADS) {
+                    const int rr = e / sn, j = e - rr * sn;
+                    S.q[j][rr] = (r0 + rr < nrhs) ? qs[(int64_t)(r0 + rr) * n + s0 + j] : cfmk(0.f, 0.f);
+                }
+                for (int e = tid; e < sn * w; e += PC_THREADS) {
+                    const int j = e / w, t = e - j * w;
+                    cf g = cfmk(0.f, 0.f);
+                    if (t0 + t != s0 + j) {
+                        const float2 sp = xl[s0 + j];
+                        const float ddx = ox + (S.tp[t].x - sp.x);
+                        const float ddy = oy + (S.tp[t].y - sp.y);
+                        const float z = k * sqrtf(ddx * ddx + ddy * ddy);
+                        if (z < H0_ZMAX) {
+                            g = green_free_f32_tab(S, z);
+                        } else {
+                            const cd h0 = hankel0((double)z);
+                            g = cfmk((float)(-0.25 * h0.y), (float)(0.25 * h0.x));
+                        }
+                    }
+                    S.g[j][t] = g;
+                }
+                __syncthreads();
+                pc_mac<NTH>(S, sn, r, tb, acc);
+            }
+        }
+    if (loc) {
+        // L2P (Algorithm 1, step 4) as more staged chunks of the same product:
+        // "strengths" beta~[r][m] of the leaf, "kernel" (i/4) conj(B[t][m])
+        for (int m0 = 0; m0 < nc; m0 += PC_SRC) {
+            const int mb = min(PC_SRC, nc - m0);
+            __syncthreads();
+            for (int e = tid; e < mb * PC_RHS; e += PC_THREADS) {
+                const int rr = e / mb, j = e - rr * mb;
+                S.q[j][rr] = (r0 + rr < nrhs) ? loc[((int64_t)b * nrhs + r0 + rr) * nc + m0 + j] : cfmk(0.f, 0.f);
+            }
+            for (int e = tid; e < mb * w; e += PC_THREADS) {
+                const int t = e / mb, j = e - t * mb;
+                const cf B = basis[(int64_t)(t0 + t) * nc + m0 + j];
+                S.g[j][t] = cfmk(0.25f * B.y, 0.25f * B.x);
+            }
+            __syncthreads();
+            pc_mac<NTH>(S, mb, r, tb, acc);
+        }
+    }
+    // stage y[t][r] in shared memory, then add it to y along the points
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NTH; ++i)
+        if (tb + i < w) S.q[tb + i][r] = acc[i];
+    __syncthreads();
+    for (int e = tid; e < w * PC_RHS; e += PC_THREADS) {
+        const int rr = e / w, t = e - rr * w;
+        if (r0 + rr < nrhs) {
+            cf* yy = ys + (int64_t)(r0 + rr) * n + t0 + t;
+            const cf a = S.q[t][rr];
+            yy->x += a.x;
+            yy->y += a.y;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(PC_THREADS) p2p32c_kernel(const int32_t* lb, int L, const float2* xl,
                                                             const cf* qs, int64_t n, int nrhs, float k,
-                                                            float h, cf* ys) {
-    __shared__ cf G[P2T][P2T + 1];
-    __shared__ cf Q[P2R][P2T + 1];
-    __shared__ float2 sp[P2T];
-    __shared__ float2 tp[P2T];
-    __shared__ float tj[H0_NI][H0_DEG + 1];
-    __shared__ float tr[H0_NI][H0_DEG + 1];
+                                                            float h, int near, const cf* loc,
+                                                            const cf* basis, int nc, cf* ys) {
+    __shared__ PcShared S;
     const int64_t b = blockIdx.x;
     const int32_t tlo = lb[b], thi = lb[b + 1];
     if (thi <= tlo) return;
     for (int e = threadIdx.x; e < H0_NI * (H0_DEG + 1); e += blockDim.x) {
-        tj[e / (H0_DEG + 1)][e % (H0_DEG + 1)] = c_h0j[e / (H0_DEG + 1)][e % (H0_DEG + 1)];
-        tr[e / (H0_DEG + 1)][e % (H0_DEG + 1)] = c_h0r[e / (H0_DEG + 1)][e % (H0_DEG + 1)];
+        S.tj[e / (H0_DEG + 1)][e % (H0_DEG + 1)] = c_h0j[e / (H0_DEG + 1)][e % (H0_DEG + 1)];
+        S.tr[e / (H0_DEG + 1)][e % (H0_DEG + 1)] = c_h0r[e / (H0_DEG + 1)][e % (H0_DEG + 1)];
     }
-    const int m = 1 << L;
     const int ix = (int)morton_x((uint32_t)b), iy = (int)morton_y((uint32_t)b);
-    const int tpair = threadIdx.x & 15, rg = threadIdx.x >> 4;   // targets 2*tpair(+1), rhs 4*rg..4*rg+3
-    for (int r0 = 0; r0 < nrhs; r0 += P2R) {
-        const int nr = min(P2R, nrhs - r0);
-        for (int32_t t0 = tlo; t0 < thi; t0 += P2T) {
-            const int tn = min(P2T, thi - t0);
-            cf acc[2][4];
-            for (int a = 0; a < 2; ++a)
-                for (int c = 0; c < 4; ++c) acc[a][c] = cfmk(0.f, 0.f);
-            __syncthreads();
-            if (threadIdx.x < tn) tp[threadIdx.x] = xl[t0 + threadIdx.x];
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int sx = ix + dx, sy = iy + dy;
-                    if (sx < 0 || sy < 0 || sx >= m || sy >= m) continue;
-                    const uint32_t s = morton((uint32_t)sx, (uint32_t)sy);
-                    const int32_t slo = lb[s], shi = lb[s + 1];
-                    const float ox = (float)(-dx) * h, oy = (float)(-dy) * h;   // c_T - c_S
-                    for (int32_t s0 = slo; s0 < shi; s0 += P2T) {
-                        const int sn = min(P2T, shi - s0);
-                        __syncthreads();
-                        if (threadIdx.x < sn) sp[threadIdx.x] = xl[s0 + threadIdx.x];
-                        for (int e = threadIdx.x; e < P2R * P2T; e += blockDim.x) {
-                            const int rr = e / P2T, j = e % P2T;
-                            Q[rr][j] = (rr < nr && j < sn) ? qs[(int64_t)(r0 + rr) * n + s0 + j] : cfmk(0.f, 0.f);
-                        }
-                        __syncthreads();
-                        for (int e = threadIdx.x; e < P2T * P2T; e += blockDim.x) {
-                            const int i = e / P2T, j = e % P2T;
-                            cf g = cfmk(0.f, 0.f);
-                            if (i < tn && j < sn && (t0 + i) != (s0 + j)) {
-                                const float ddx = ox + (tp[i].x - sp[j].x);
-                                const float ddy = oy + (tp[i].y - sp[j].y);
-                                const float z = k * sqrtf(ddx * ddx + ddy * ddy);
-                                if (z < H0_ZMAX) {
-                                    const int iv = min((int)(z * H0_INV_DZ), H0_NI - 1);
-                                    const float t = (z - ((float)iv + 0.5f) / H0_INV_DZ) * (2.0f * H0_INV_DZ);
-                                    float jj = tj[iv][H0_DEG], rr2 = tr[iv][H0_DEG];
+    for (int r0 = 0; r0 < nrhs; r0 += PC_RHS)
+        for (int32_t t0 = tlo; t0 < thi; t0 += PC_TGT) {
+            const int w = min(PC_TGT, thi - t0);
+            if (w <= 8) p2p_pass<4>(S, lb, L, b, ix, iy, xl, qs, n, nrhs, r0, t0, w, k, h, near, loc, basis, nc, ys);
+            else if (w <= 16) p2p_pass<8>(S, lb, L, b, ix, iy, xl, qs, n, nrhs, r0, t0, w, k, h, near, loc, basis, nc, ys);
+            else if (w <= 24) p2p_pass<12>(S, lb, L, b, ix, iy, xl, qs, n, nrhs, r0, t0, w, k, h, near, loc, basis, nc, ys);
+            else p2p_pass<16>(S, lb, L, b, ix, iy, xl, qs, n, nrhs, r0, t0, w, k, h, near, loc, basis, nc, ys);
+        }
+}
+
+// P2M, FP32 (Algorithm 1, step 1): one CTA of 128 threads per leaf computes
+// the scaled multipoles a~[r][m] = sum over the leaf's points of
+// q_r(pt) B[pt][m] with the plan-time basis B.  Same tiling as the P2P pass:
+// thread (r, half) owns NTH coefficients of a pass of up to 32, points are
+// streamed in chunks of 32 (strengths [j][r], basis [j][m] in shared memory).
+template <int NTH>
+__device__ __forceinline__ void p2m_pass(PcShared& S, const cf* qs, const cf* basis, int64_t n, int nrhs, int r0,
+                                         int32_t lo, int32_t hi, int nc, int m0, int w, cf* out) {
+    const int tid = threadIdx.x;
+    const int r = tid & (PC_RHS - 1), half = tid >> 6;
+    const int tb = half * NTH;
+    cf acc[NTH];
 #pragma unroll
-                                    for (int d = H0_DEG - 1; d >= 0; --d) {
-                                        jj = fmaf(jj, t, tj[iv][d]);
-                                        rr2 = fmaf(rr2, t, tr[iv][d]);
-                                    }
-                                    const float y = fmaf(0.63661977236758134f * logf(0.5f * z), jj, rr2);
-                                    g = cfmk(-0.25f * y, 0.25f * jj);
-                                } else {
-                                    cd h0 = hankel0((double)z);
-                                    g = cfmk((float)(-0.25 * h0.y), (float)(0.25 * h0.x));
-                                }
-                            }
-                            G[i][j] = g;
-                        }
-                        __syncthreads();
-#pragma unroll 4
-                        for (int j = 0; j < P2T; ++j) {
-                            const cf g0 = G[2 * tpair][j], g1 = G[2 * tpair + 1][j];
+    for (int i = 0; i < NTH; ++i) acc[i] = cfmk(0.f, 0.f);
+    for (int32_t s0 = lo; s0 < hi; s0 += PC_SRC) {
+        const int sn = min(PC_SRC, hi - s0);
+        __syncthreads();
+        for (int e = tid; e < sn * PC_RHS; e += PC_THREADS) {
+            const int rr = e / sn, j = e - rr * sn;
+            S.q[j][rr] = (r0 + rr < nrhs) ? qs[(int64_t)(r0 + rr) * n + s0 + j] : cfmk(0.f, 0.f);
+        }
+        for (int e = tid; e < sn * w; e += PC_THREADS) {
+            const int j = e / w, t = e - j * w;
+            S.g[j][t] = basis[(int64_t)(s0 + j) * nc + m0 + t];
+        }
+        __syncthreads();
+        pc_mac<NTH>(S, sn, r, tb, acc);
+    }
+    __syncthreads();
 #pragma unroll
-                            for (int c = 0; c < 4; ++c) {
-                                const cf qv = Q[4 * rg + c][j];
-                                cfma32(acc[0][c], g0, qv);
-                                cfma32(acc[1][c], g1, qv);
-                            }
-                        }
-                    }
+    for (int i = 0; i < NTH; ++i)
+        if (tb + i < w) S.q[tb + i][r] = acc[i];
+    __syncthreads();
+    for (int e = tid; e < w * PC_RHS; e += PC_THREADS) {
+        const int rr = e / w, t = e - rr * w;
+        if (r0 + rr < nrhs) out[(int64_t)(r0 + rr) * nc + m0 + t] = S.q[t][rr];
+    }
+}
+
+__device__ __forceinline__ uint32_t tf32_rna32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// Writes mult[b] and, when amma is given, its MMA-ready copy (TF32 hi / lo,
+// 64-row core-matrix blocks of kc K chunks, Re then Im, zero padding) for the
+// tensor-core M2M and M2L of the leaf level.
+__global__ void __launch_bounds__(PC_THREADS) p2m32c_kernel(const int32_t* lb, const cf* qs, const cf* basis,
+                                                            int64_t n, int nrhs, int nc, cf* mult, float* amma,
+                                                            int kc, int nrc) {
+    __shared__ PcShared S;
+    const int64_t b = blockIdx.x;
+    const int32_t lo = lb[b], hi = lb[b + 1];
+    cf* out = mult + (int64_t)b * nrhs * nc;
+    for (int r0 = 0; r0 < nrhs; r0 += PC_RHS) {
+        for (int m0 = 0; m0 < nc; m0 += PC_TGT) {
+            const int w = min(PC_TGT, nc - m0);
+            if (w <= 8) p2m_pass<4>(S, qs, basis, n, nrhs, r0, lo, hi, nc, m0, w, out);
+            else if (w <= 16) p2m_pass<8>(S, qs, basis, n, nrhs, r0, lo, hi, nc, m0, w, out);
+            else if (w <= 24) p2m_pass<12>(S, qs, basis, n, nrhs, r0, lo, hi, nc, m0, w, out);
+            else p2m_pass<16>(S, qs, basis, n, nrhs, r0, lo, hi, nc, m0, w, out);
+        }
+        if (amma) {
+            __syncthreads();   // this block's rows of mult are written
+            const int rc = r0 / PC_RHS;
+            // warp = 8 rows x 4 consecutive k of one core matrix: 32 contiguous floats
+            const int nq = kc * 4;
+            for (int e = threadIdx.x; e < 8 * nq * 32; e += PC_THREADS) {
+                const int lane = e & 31, gq = e >> 5;
+                const int g = gq & 7, kq = gq >> 3;
+                const int r = g * 8 + (lane >> 2), k = kq * 4 + (lane & 3);
+                float v = 0.0f;
+                if (r0 + r < nrhs && k < 2 * nc) {
+                    const cf z = out[(int64_t)(r0 + r) * nc + (k < nc ? k : k - nc)];
+                    v = k < nc ? z.x : z.y;
                 }
-            for (int a = 0; a < 2; ++a) {
-                const int i = 2 * tpair + a;
-                if (i >= tn) continue;
-                for (int c = 0; c < 4; ++c) {
-                    const int rr = 4 * rg + c;
-                    if (rr >= nr) continue;
-                    cf* yy = ys + (int64_t)(r0 + rr) * n + t0 + i;
-                    yy->x += acc[a][c].x;
-                    yy->y += acc[a][c].y;
-                }
+                const float vh = __uint_as_float(tf32_rna32(v));
+                const float vl = __uint_as_float(tf32_rna32(v - vh));
+                const int c = k >> 4, kk = k & 15;
+                float* d = amma + (((b * nrc + rc) * kc + c) * 2) * 1024 + ((r >> 3) * 4 + (kk >> 2)) * 32 +
+                           (r & 7) * 4 + (kk & 3);
+                d[0] = vh;
+                d[1024] = vl;
             }
         }
     }
 }
 
-// P2P free-space part in FP32
-constexpr int PT = 32;
-constexpr int P2P_THREADS = 256;
-constexpr int P2P_RHS = 64;
-constexpr int P2P_ITEMS = P2P_RHS * PT / P2P_THREADS;   // 8
-
-__global__ void __launch_bounds__(P2P_THREADS) p2p32_kernel(const int32_t* lb, int L, const double2* xs,
-                                                            const cf* qs, int64_t n, int nrhs, double k,
-                                                            cf* ys) {
-    __shared__ cf G[PT][PT + 1];
-    __shared__ double2 sp[PT];
-    __shared__ double2 tp[PT];
+// Plan-time scaled P2M basis of every sorted point (FP64, stored in FP32).
+__global__ void basis32_kernel(const int32_t* lb, const double2* xs, int64_t nleaf, double x0, double y0, double h,
+                               double k, int p, const double* log_s, cf* basis) {
+    extern __shared__ double jt_smem[];
     const int64_t b = blockIdx.x;
-    const int32_t tlo = lb[b], thi = lb[b + 1];
-    if (thi <= tlo) return;
-    const int m = 1 << L;
-    const int ix = (int)morton_x((uint32_t)b), iy = (int)morton_y((uint32_t)b);
-    for (int r0 = 0; r0 < nrhs; r0 += P2P_RHS) {
-        const int nr = min(P2P_RHS, nrhs - r0);
-        for (int32_t t0 = tlo; t0 < thi; t0 += PT) {
-            const int tn = min(PT, thi - t0);
-            cf acc[P2P_ITEMS];
-            for (int u = 0; u < P2P_ITEMS; ++u) acc[u] = cfmk(0.f, 0.f);
-            __syncthreads();
-            if (threadIdx.x < tn) tp[threadIdx.x] = xs[t0 + threadIdx.x];
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int sx = ix + dx, sy = iy + dy;
-                    if (sx < 0 || sy < 0 || sx >= m || sy >= m) continue;
-                    const uint32_t s = morton((uint32_t)sx, (uint32_t)sy);
-                    const int32_t slo = lb[s], shi = lb[s + 1];
-                    for (int32_t s0 = slo; s0 < shi; s0 += PT) {
-                        const int sn = min(PT, shi - s0);
-                        __syncthreads();
-                        if (threadIdx.x < sn) sp[threadIdx.x] = xs[s0 + threadIdx.x];
-                        __syncthreads();
-                        for (int e = threadIdx.x; e < PT * PT; e += blockDim.x) {
-                            const int i = e / PT, j = e % PT;
-                            cf g = cfmk(0.f, 0.f);
-                            if (i < tn && j < sn && (t0 + i) != (s0 + j)) {
-                                // coordinates differences in FP64, distance rounded to FP32
-                                const double r = hypot(tp[i].x - sp[j].x, tp[i].y - sp[j].y);
-                                const double z = k * r;
-                                if (z < (double)H0_ZMAX) {
-                                    g = green_free_f32((float)z);
-                                } else {
-                                    cd h0 = hankel0(z);
-                                    g = cfmk((float)(-0.25 * h0.y), (float)(0.25 * h0.x));
-                                }
-                            }
-                            G[i][j] = g;
-                        }
-                        __syncthreads();
-                        for (int u = 0; u < P2P_ITEMS; ++u) {
-                            const int it = u * P2P_THREADS + threadIdx.x;
-                            const int rr = it / PT, i = it % PT;
-                            if (rr >= nr || i >= tn) continue;
-                            const cf* qr = qs + (int64_t)(r0 + rr) * n + s0;
-                            cf a = acc[u];
-                            for (int j = 0; j < sn; ++j) cfma32(a, G[i][j], qr[j]);
-                            acc[u] = a;
-                        }
-                    }
-                }
-            for (int u = 0; u < P2P_ITEMS; ++u) {
-                const int it = u * P2P_THREADS + threadIdx.x;
-                const int rr = it / PT, i = it % PT;
-                if (rr >= nr || i >= tn) continue;
-                cf* yy = ys + (int64_t)(r0 + rr) * n + t0 + i;
-                yy->x += acc[u].x;
-                yy->y += acc[u].y;
-            }
-        }
-    }
+    if (b >= nleaf) return;
+    const int ncoef = 2 * p + 1;
+    const double cx = x0 + (morton_x((uint32_t)b) + 0.5) * h;
+    const double cy = y0 + (morton_y((uint32_t)b) + 0.5) * h;
+    double* Jt = jt_smem + (size_t)threadIdx.x * (p + 1);
+    for (int32_t i = lb[b] + threadIdx.x; i < lb[b + 1]; i += blockDim.x)
+        point_basis32(xs[i].x, xs[i].y, cx, cy, k, p, -1, log_s, Jt, basis + (int64_t)i * ncoef);
 }
 
 __global__ void direct32_kernel(const int32_t* lb, const int32_t* d_begin, const int32_t* d_src,
@@ -513,11 +532,6 @@ __global__ void direct32_kernel(const int32_t* lb, const int32_t* d_begin, const
     }
 }
 
-int pick_chunk32(int p) {
-    const int ncoef = 2 * p + 1;
-    int c = (int)(40000 / (ncoef * 8 + (p + 1) * 8));
-    return std::max(1, std::min(32, c));
-}
 
 }  // namespace
 
@@ -536,6 +550,14 @@ hfmm_status build_local_coords(hfmm_plan_s* P, cudaStream_t st) {
     const LevelInfo& lv = P->lev[P->L];
     local_coords_kernel<<<(unsigned)lv.nbox, 128, 0, st>>>(P->leaf_begin, P->xy_sorted, lv.nbox, P->x0, P->y0, lv.h,
                                                            P->xl32);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    // P2M / L2P basis of every point, once per plan
+    const size_t bb = sizeof(cf) * (size_t)P->n * lv.ncoef;
+    HFMM_TRY(plan_alloc(P, (void**)&P->basis32, bb));
+    P->buffer_bytes += (double)bb;
+    const int thr = std::max(1, std::min(128, 6000 / (lv.p + 1)));
+    basis32_kernel<<<(unsigned)lv.nbox, thr, (size_t)thr * (lv.p + 1) * sizeof(double), st>>>(
+        P->leaf_begin, P->xy_sorted, lv.nbox, P->x0, P->y0, lv.h, P->k, lv.p, lv.d_log_s, P->basis32);
     HFMM_CUDA_TRY(cudaGetLastError());
     return HFMM_OK;
 }
@@ -580,22 +602,18 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
     if (far) {
         {
             LevelInfo& lv = P->lev[L];
-            const int chunk = pick_chunk32(lv.p);
-            const size_t sm = (size_t)chunk * ((2 * lv.p + 1) * sizeof(cf) + (lv.p + 1) * sizeof(double));
             tm.begin(HFMM_STAGE_P2M);
-            p2m32_kernel<<<(unsigned)lv.nbox, 128, sm, st>>>(P->leaf_begin, P->xy_sorted, P->q32, n, nrhs, P->x0,
-                                                             P->y0, lv.h, P->k, lv.p, lv.d_log_s, chunk, lv.mult32);
+            const int nrc = (P->max_rhs + 63) / 64;
+            p2m32c_kernel<<<(unsigned)lv.nbox, PC_THREADS, 0, st>>>(P->leaf_begin, P->q32, P->basis32, n, nrhs,
+                                                                     lv.ncoef, lv.mult32,
+                                                                     P->tc_on ? lv.tc_amma : nullptr, lv.tc_kc, nrc);
             ++P->launches;
             HFMM_CUDA_TRY(cudaGetLastError());
             tm.end(HFMM_STAGE_P2M);
             P->st_flops[HFMM_STAGE_P2M] = MAC * n * lv.ncoef;
-            P->st_bytes[HFMM_STAGE_P2M] = C * n + 16.0 * n + C * lv.nbox * lv.ncoef;
+            P->st_bytes[HFMM_STAGE_P2M] = C * n + 8.0 * n * lv.ncoef + C * lv.nbox * lv.ncoef;
         }
         tm.begin(HFMM_STAGE_M2M);
-        if (P->tc_on) {
-            HFMM_TRY(split_mult_tc(P, L, nrhs, st));
-            ++P->launches;
-        }
         for (int l = L - 1; l >= P->lmin; --l) {
             LevelInfo& lv = P->lev[l];
             if (P->tc_on) {
@@ -642,29 +660,22 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
                                             (has_parent ? C * P->lev[l - 1].nbox * npp : 0.0);
         }
         tm.end(HFMM_STAGE_DOWN);
-        {
-            LevelInfo& lv = P->lev[L];
-            const int chunk = pick_chunk32(lv.p);
-            const size_t sm = (size_t)chunk * ((2 * lv.p + 1) * sizeof(cf) + (lv.p + 1) * sizeof(double));
-            tm.begin(HFMM_STAGE_L2P);
-            l2p32_kernel<<<(unsigned)lv.nbox, 128, sm, st>>>(P->leaf_begin, P->xy_sorted, lv.loc32, n, nrhs, P->x0,
-                                                             P->y0, lv.h, P->k, lv.p, lv.d_log_s, chunk, P->y32);
-            ++P->launches;
-            HFMM_CUDA_TRY(cudaGetLastError());
-            tm.end(HFMM_STAGE_L2P);
-            P->st_flops[HFMM_STAGE_L2P] = MAC * n * lv.ncoef;
-            P->st_bytes[HFMM_STAGE_L2P] = C * lv.nbox * lv.ncoef + 16.0 * n + 2.0 * C * n;
-        }
     }
-    if (parts & HFMM_PART_NEAR_FREE) {
+    // near free-space field and the leaves' local expansions, one fused kernel
+    if ((parts & HFMM_PART_NEAR_FREE) || far) {
+        const LevelInfo& lv = P->lev[L];
+        const bool near = (parts & HFMM_PART_NEAR_FREE) != 0;
         tm.begin(HFMM_STAGE_P2P);
-        p2p32b_kernel<<<(unsigned)P->lev[L].nbox, P2_THREADS, 0, st>>>(P->leaf_begin, L, P->xl32, P->q32, n, nrhs,
-                                                                       (float)P->k, (float)P->lev[L].h, P->y32);
+        p2p32c_kernel<<<(unsigned)lv.nbox, PC_THREADS, 0, st>>>(P->leaf_begin, L, P->xl32, P->q32, n, nrhs,
+                                                                (float)P->k, (float)lv.h, near ? 1 : 0,
+                                                                far ? lv.loc32 : nullptr, P->basis32, lv.ncoef,
+                                                                P->y32);
         ++P->launches;
         HFMM_CUDA_TRY(cudaGetLastError());
         tm.end(HFMM_STAGE_P2P);
-        P->st_flops[HFMM_STAGE_P2P] = MAC * (double)P->p2p_point_pairs;
-        P->st_bytes[HFMM_STAGE_P2P] = 3.0 * C * n + 16.0 * n;
+        P->st_flops[HFMM_STAGE_P2P] = (near ? MAC * (double)P->p2p_point_pairs : 0.0) +
+                                      (far ? MAC * n * lv.ncoef : 0.0);
+        P->st_bytes[HFMM_STAGE_P2P] = 3.0 * C * n + 16.0 * n + (far ? C * lv.nbox * lv.ncoef + 8.0 * n * lv.ncoef : 0.0);
     }
     if ((parts & HFMM_PART_NEAR_REACT) && P->nd > 0) {
         tm.begin(HFMM_STAGE_DIRECT);

@@ -126,49 +126,21 @@ __global__ void tc_btable_kernel(const cf* M, int nmat, int nin, int nout, int N
     }
 }
 
-// MMA-ready copy of expansions: per box, per 64-row right-hand-side chunk rc,
-// per K chunk c (16 real values: Re a_0..a_{nin-1} then Im), hi and lo TF32
-// parts, each 64 rows x 16 floats in the no-swizzle core-matrix layout:
+// MMA-ready expansions: per box, per 64-row right-hand-side chunk rc, per K
+// chunk c (16 real values: Re a_0..a_{nin-1} then Im, zero padded), hi and lo
+// TF32 parts, each 64 rows x 16 floats in the no-swizzle core-matrix layout:
 //   float offset (((box * nrc + rc) * kc + c) * 2 + part) * 1024
 //                + ((r / 8) * 4 + kk / 4) * 32 + (r % 8) * 4 + kk % 4.
-__global__ void split_rows_kernel(const cf* __restrict__ src, int64_t nbox, int nrhs, int nin, int kc, int nrc,
-                                  float* __restrict__ dst) {
-    const int64_t total = nbox * nrc * 64;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t box = e / (nrc * 64);
-        const int rc = (int)((e / 64) % nrc);
-        const int r = (int)(e % 64);
-        const int rhs = rc * 64 + r;
-        const cf* row = (rhs < nrhs) ? src + ((int64_t)box * nrhs + rhs) * nin : nullptr;
-        for (int c = 0; c < kc; ++c) {
-            float hv[16], lv[16];
-#pragma unroll
-            for (int kk = 0; kk < 16; ++kk) {
-                const int k = 16 * c + kk;
-                float v = 0.0f;
-                if (row && k < 2 * nin) v = (k < nin) ? row[k].x : row[k - nin].y;
-                const float h = __uint_as_float(tf32_rna(v));
-                hv[kk] = h;
-                lv[kk] = __uint_as_float(tf32_rna(v - h));
-            }
-            float* base = dst + (((box * nrc + rc) * kc + c) * 2) * 1024;
-#pragma unroll
-            for (int kb = 0; kb < 4; ++kb) {
-                const int off = ((r >> 3) * 4 + kb) * 32 + (r & 7) * 4;
-                *(float4*)(base + off) = make_float4(hv[4 * kb], hv[4 * kb + 1], hv[4 * kb + 2], hv[4 * kb + 3]);
-                *(float4*)(base + 1024 + off) = make_float4(lv[4 * kb], lv[4 * kb + 1], lv[4 * kb + 2], lv[4 * kb + 3]);
-            }
-        }
-    }
-}
+// The leaf multipoles are written in this form by P2M, all other expansions
+// by the tensor-core kernel that produces them.
 
 constexpr int TC2_THREADS = 192;   // warps 0-3 drain, warp 4 TMA, warp 5 MMA
 
 // One CTA = one target pair x 64 right-hand sides x one block of NB real
 // output columns (blockIdx.z; columns n0 .. n0 + NB - 1 of the Np-wide GEMM).
 // The result goes to the FP32 coefficients out[box][r][0 .. nc) and, when
-// sdst is given, also in MMA-ready form (kcd K chunks, split_rows_kernel
-// layout) for the next tensor-core consumer of these coefficients.
+// sdst is given, also in MMA-ready form (kcd K chunks, the layout above)
+// for the next tensor-core consumer of these coefficients.
 template <int NB>
 __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
     const TcTile* __restrict__ tiles, const TcStep* __restrict__ steps, const float* __restrict__ Bfree,
@@ -568,14 +540,6 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
     return HFMM_OK;
 }
 
-// MMA-ready copy of the leaf multipoles (after P2M).
-hfmm_status split_mult_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st) {
-    LevelInfo& lv = P->lev[l];
-    const int nrc = (P->max_rhs + 63) / 64;
-    split_rows_kernel<<<4 * 152, 128, 0, st>>>(lv.mult32, lv.nbox, nrhs, lv.ncoef, lv.tc_kc, nrc, lv.tc_amma);
-    HFMM_CUDA_TRY(cudaGetLastError());
-    return HFMM_OK;
-}
 
 // Tensor-core M2M into level l (children at l + 1 already MMA-ready); writes
 // the FP32 multipoles and their MMA-ready copy.

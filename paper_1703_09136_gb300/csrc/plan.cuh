@@ -110,6 +110,9 @@ struct hfmm_plan_s {
     cf* y32 = nullptr;
     cf* d_vals32 = nullptr;
     float2* xl32 = nullptr;         // [n] point offsets from their own leaf centre (FP32)
+    cf* basis32 = nullptr;          // [n][2 p_L + 1] scaled P2M basis of each sorted point
+                                    // (J_|m| e^{-i m theta} / s(|m|), sign of Graf's addition
+                                    // theorem folded in); its conjugate is the L2P basis
     // position gradients (FP64): field-gradient buffers and d/dX, d/dY of the
     // directly summed reaction blocks
     cd* grad_buf = nullptr;         // [5][max_rhs][n]
@@ -179,7 +182,6 @@ hfmm_status build_local_coords(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status launch_m2l_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st);
 hfmm_status launch_m2m_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st);
-hfmm_status split_mult_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st);
 
 // Morton helpers
 HD uint32_t spread_bits(uint32_t v) {
