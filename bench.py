@@ -50,7 +50,7 @@ def _measured_bf16():
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=4)
@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=0)
+    ap.add_argument("--box", type=float, nargs=4, default=None, metavar=("X0", "X1", "Y0", "Y1"),
+                    help="draw the points in this box instead of the workload's domain (small profiling cases)")
     return ap.parse_args()
 
 
@@ -182,7 +184,11 @@ def run_ours(args):
     nrhs = args.nrhs or w.nrhs
     prec = FP64 if args.precision == "fp64" else MIXED
     cdt = torch.complex128 if prec == FP64 else torch.complex64
-    xy_h = W.points(cfg, n)
+    if args.box:
+        x0, x1, y0, y1 = args.box
+        xy_h = W.points_in_box(cfg, n, ((x0, x1), (y0, y1)))
+    else:
+        xy_h = W.points(cfg, n)
     q_h = W.strengths(cfg, n, nrhs)
     dev = torch.device("cuda", local)
     xy = torch.from_numpy(xy_h).to(dev)
@@ -262,6 +268,7 @@ def run_ours(args):
         "config": {"workload": w.name, "n": n, "nrhs": nrhs, "medium": "three-layer k=40/80/60 d=0.5",
                    "tol": w.tol, "levels": info["levels"], "p": info["p"], "plan_s": plan_s,
                    "l2": "inputs larger than L2 (q, y and expansions are GBs)",
+                   **({"box": args.box} if args.box else {}),
                    "parallelism": f"replicas{world}"},
         "stage_ms": avg, "adjoint_ms": None, "gpu_launches": launches, "e2e": e2e, "roofline": roof,
         "clocks": ck,

@@ -92,26 +92,59 @@ HD void cfma32(cf& acc, cf a, cf b) {
     acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
 }
 
-__global__ void gather_q32(const cf* q, const int64_t* perm, int64_t n, int nrhs, bool conj_in, cf* qs) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t j = perm[i];
-    for (int r = 0; r < nrhs; ++r) {
-        cf v = q[(int64_t)r * n + j];
-        if (conj_in) v.y = -v.y;
-        qs[(int64_t)r * n + i] = v;
+// Sorted FP32 strengths and fields are point-major, [n][nrhs].  Gather and
+// scatter move one tile of 64 consecutive caller indices: the caller side
+// ([nrhs][n]) is read / written along the points, the sorted side along the
+// right-hand sides of each point (iperm: sorted position of caller index j).
+constexpr int TP_PTS = 64;
+
+__global__ void gather_q32(const cf* q, const int32_t* iperm, int64_t n, int nrhs, bool conj_in, cf* qs) {
+    __shared__ cf T[TP_PTS][TP_PTS + 1];
+    const int64_t j0 = (int64_t)blockIdx.x * TP_PTS;
+    const int jn = (int)min((int64_t)TP_PTS, n - j0);
+    for (int r0 = 0; r0 < nrhs; r0 += TP_PTS) {
+        const int rn = min(TP_PTS, nrhs - r0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < rn * TP_PTS; e += blockDim.x) {
+            const int rr = e / TP_PTS, jj = e % TP_PTS;
+            if (jj < jn) {
+                cf v = q[(int64_t)(r0 + rr) * n + j0 + jj];
+                if (conj_in) v.y = -v.y;
+                T[jj][rr] = v;
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < jn * rn; e += blockDim.x) {
+            const int jj = e / rn, rr = e % rn;
+            qs[(int64_t)iperm[j0 + jj] * nrhs + r0 + rr] = T[jj][rr];
+        }
     }
 }
-
-__global__ void scatter_y32(const cf* ys, const int64_t* perm, int64_t n, int nrhs, bool conj_out, cf* y) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t j = perm[i];
-    for (int r = 0; r < nrhs; ++r) {
-        cf v = ys[(int64_t)r * n + i];
-        if (conj_out) v.y = -v.y;
-        y[(int64_t)r * n + j] = v;
+__global__ void scatter_y32(const cf* ys, const int32_t* iperm, int64_t n, int nrhs, bool conj_out, cf* y) {
+    __shared__ cf T[TP_PTS][TP_PTS + 1];
+    const int64_t j0 = (int64_t)blockIdx.x * TP_PTS;
+    const int jn = (int)min((int64_t)TP_PTS, n - j0);
+    for (int r0 = 0; r0 < nrhs; r0 += TP_PTS) {
+        const int rn = min(TP_PTS, nrhs - r0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < jn * rn; e += blockDim.x) {
+            const int jj = e / rn, rr = e % rn;
+            T[jj][rr] = ys[(int64_t)iperm[j0 + jj] * nrhs + r0 + rr];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < rn * TP_PTS; e += blockDim.x) {
+            const int rr = e / TP_PTS, jj = e % TP_PTS;
+            if (jj < jn) {
+                cf v = T[jj][rr];
+                if (conj_out) v.y = -v.y;
+                y[(int64_t)(r0 + rr) * n + j0 + jj] = v;
+            }
+        }
     }
+}
+__global__ void iperm_kernel(const int64_t* perm, int64_t n, int32_t* iperm) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) iperm[perm[i]] = (int32_t)i;
 }
 
 // scaled point basis B[m + p] = J_m(k rho) e^{sgn i m theta} / s(|m|), FP64 then FP32
@@ -320,10 +353,10 @@ __device__ __forceinline__ void p2p_pass(PcShared& S, const int32_t* lb, int L, 
             for (int32_t s0 = slo; s0 < shi; s0 += PC_SRC) {
                 const int sn = min(PC_SRC, shi - s0);
                 __syncthreads();
-                // strengths: consecutive threads take consecutive points of one RHS row
+                // strengths: consecutive threads take consecutive RHS of one point
                 for (int e = tid; e < sn * PC_RHS; e += PC_THREADS) {
-                    const int rr = e / sn, j = e - rr * sn;
-                    S.q[j][rr] = (r0 + rr < nrhs) ? qs[(int64_t)(r0 + rr) * n + s0 + j] : cfmk(0.f, 0.f);
+                    const int j = e >> 6, rr = e & (PC_RHS - 1);
+                    S.q[j][rr] = (r0 + rr < nrhs) ? qs[(int64_t)(s0 + j) * nrhs + r0 + rr] : cfmk(0.f, 0.f);
                 }
                 for (int e = tid; e < sn * w; e += PC_THREADS) {
                     const int j = e / w, t = e - j * w;
@@ -372,9 +405,9 @@ __device__ __forceinline__ void p2p_pass(PcShared& S, const int32_t* lb, int L, 
         if (tb + i < w) S.q[tb + i][r] = acc[i];
     __syncthreads();
     for (int e = tid; e < w * PC_RHS; e += PC_THREADS) {
-        const int rr = e / w, t = e - rr * w;
+        const int t = e >> 6, rr = e & (PC_RHS - 1);
         if (r0 + rr < nrhs) {
-            cf* yy = ys + (int64_t)(r0 + rr) * n + t0 + t;
+            cf* yy = ys + (int64_t)(t0 + t) * nrhs + r0 + rr;
             const cf a = S.q[t][rr];
             yy->x += a.x;
             yy->y += a.y;
@@ -423,8 +456,8 @@ __device__ __forceinline__ void p2m_pass(PcShared& S, const cf* qs, const cf* ba
         const int sn = min(PC_SRC, hi - s0);
         __syncthreads();
         for (int e = tid; e < sn * PC_RHS; e += PC_THREADS) {
-            const int rr = e / sn, j = e - rr * sn;
-            S.q[j][rr] = (r0 + rr < nrhs) ? qs[(int64_t)(r0 + rr) * n + s0 + j] : cfmk(0.f, 0.f);
+            const int j = e >> 6, rr = e & (PC_RHS - 1);
+            S.q[j][rr] = (r0 + rr < nrhs) ? qs[(int64_t)(s0 + j) * nrhs + r0 + rr] : cfmk(0.f, 0.f);
         }
         for (int e = tid; e < sn * w; e += PC_THREADS) {
             const int j = e / w, t = e - j * w;
@@ -517,16 +550,16 @@ __global__ void direct32_kernel(const int32_t* lb, const int32_t* d_begin, const
     const int32_t tlo = lb[b], tn = lb[b + 1] - tlo;
     const int items = nrhs * tn;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int r = it / tn, i = it % tn;
+        const int i = it / nrhs, r = it % nrhs;
         cf acc = cfmk(0.f, 0.f);
         for (int32_t e = e0; e < e1; ++e) {
             const int32_t s = d_src[e];
             const int32_t slo = lb[s], sn = lb[s + 1] - slo;
             const cf* G = vals + d_blk[e] + (int64_t)i * sn;
-            const cf* qr = qs + (int64_t)r * n + slo;
-            for (int j = 0; j < sn; ++j) cfma32(acc, G[j], qr[j]);
+            const cf* qr = qs + (int64_t)slo * nrhs + r;
+            for (int j = 0; j < sn; ++j) cfma32(acc, G[j], qr[(int64_t)j * nrhs]);
         }
-        cf* yy = ys + (int64_t)r * n + tlo + i;
+        cf* yy = ys + (int64_t)(tlo + i) * nrhs + r;
         yy->x += acc.x;
         yy->y += acc.y;
     }
@@ -550,6 +583,9 @@ hfmm_status build_local_coords(hfmm_plan_s* P, cudaStream_t st) {
     const LevelInfo& lv = P->lev[P->L];
     local_coords_kernel<<<(unsigned)lv.nbox, 128, 0, st>>>(P->leaf_begin, P->xy_sorted, lv.nbox, P->x0, P->y0, lv.h,
                                                            P->xl32);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    HFMM_TRY(plan_alloc(P, (void**)&P->iperm32, sizeof(int32_t) * P->n));
+    iperm_kernel<<<(unsigned)ceil_div(P->n, 256), 256, 0, st>>>(P->perm, P->n, P->iperm32);
     HFMM_CUDA_TRY(cudaGetLastError());
     // P2M / L2P basis of every point, once per plan
     const size_t bb = sizeof(cf) * (size_t)P->n * lv.ncoef;
@@ -586,14 +622,14 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
                         cudaStream_t st) {
     const int64_t n = P->n;
     const int L = P->L;
-    const int nb = ceil_div(n, 256);
     StageTimer tm{P, st};
     P->launches = 0;
     for (int s = 0; s < HFMM_NUM_STAGES; ++s) { P->st_flops[s] = 0.0; P->st_bytes[s] = 0.0; P->ev_used[s] = false; }
     const double C = 8.0 * nrhs;
     const double MAC = 8.0 * nrhs;
     tm.begin(HFMM_STAGE_GATHER);
-    gather_q32<<<nb, 256, 0, st>>>(q, P->perm, n, nrhs, adjoint, P->q32);
+    const unsigned ntile = (unsigned)ceil_div(n, TP_PTS);
+    gather_q32<<<ntile, 256, 0, st>>>(q, P->iperm32, n, nrhs, adjoint, P->q32);
     ++P->launches;
     HFMM_CUDA_TRY(cudaMemsetAsync(P->y32, 0, sizeof(cf) * n * nrhs, st));
     tm.end(HFMM_STAGE_GATHER);
@@ -688,7 +724,7 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
         P->st_bytes[HFMM_STAGE_DIRECT] = 8.0 * (double)P->nd_vals;
     }
     tm.begin(HFMM_STAGE_SCATTER);
-    scatter_y32<<<nb, 256, 0, st>>>(P->y32, P->perm, n, nrhs, adjoint, y);
+    scatter_y32<<<ntile, 256, 0, st>>>(P->y32, P->iperm32, n, nrhs, adjoint, y);
     ++P->launches;
     HFMM_CUDA_TRY(cudaGetLastError());
     tm.end(HFMM_STAGE_SCATTER);

@@ -17,17 +17,17 @@
 // x = hi + lo).
 //
 // Operands are stored MMA-ready (pre-split TF32 hi / lo, core-matrix layout):
-// the leaf multipoles are copied into that form after P2M, every other
-// expansion is written in that form by the kernel that produces it, the
-// operators at plan time.  Pipeline (one CTA = one target pair x 64
-// right-hand sides x one column block): warp 4 streams every K chunk with
-// cp.async.bulk (two 64-row A halves per part plus the operator block) into a
-// 4-stage shared-memory ring; warp 5 issues tcgen05.mma into one of two TMEM
-// buffers per source step; warps 0-3 drain each finished step with
-// tcgen05.ld into round-to-nearest FP32 registers (tensor-core accumulation
-// truncates, so long chains in TMEM lose accuracy) and write the result.
-// Every mbarrier wait is bounded; a timeout sets an error flag instead of
-// hanging.
+// the leaf multipoles by P2M, every other expansion by the kernel that
+// produces it, the operators at plan time.  Pipeline (one CTA = one target
+// pair x 64 right-hand sides x one column block): warp 4 streams every K
+// chunk with cp.async.bulk (two 64-row A halves per part plus the operator
+// block) into a shared-memory ring as deep as two CTAs per SM allow; warp 5
+// issues tcgen05.mma into one of two TMEM buffers per source step (long
+// steps are cut into sub-steps of at most 8 K chunks); warps 0-3 drain each
+// finished step with tcgen05.ld into round-to-nearest FP32 registers
+// (tensor-core accumulation truncates, so long chains in TMEM lose accuracy)
+// and write the result.  Every mbarrier wait is bounded; a timeout sets an
+// error flag instead of hanging.
 #include <algorithm>
 #include <map>
 #include <vector>
@@ -36,7 +36,12 @@
 
 namespace {
 
-constexpr int TC_STAGES = 4;
+// Shared-memory ring depth for column blocks of NB: as many stages as fit
+// two CTAs on one SM (about 113 KB each), so more operand bytes are in flight.
+template <int NB>
+constexpr int tc_stages() {
+    return (115200 - 256) / (16384 + NB * 128) < 8 ? (115200 - 256) / (16384 + NB * 128) : 8;
+}
 constexpr int TC_MAX_NP = 128;         // widest column block (one 128-column TMEM buffer)
 constexpr long TC_SPIN = 20000000;     // bounded mbarrier polls
 constexpr int TC_STEP_CHUNKS = 8;      // K chunks accumulated in TMEM before a drain
@@ -151,6 +156,7 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr int stage_bytes = 16384 + NB * 128;
+    constexpr int TC_STAGES = tc_stages<NB>();
     uint64_t* full = (uint64_t*)(smem + TC_STAGES * stage_bytes);
     uint64_t* empty = full + TC_STAGES;
     uint64_t* dfull = empty + TC_STAGES;
@@ -249,6 +255,8 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
         }
     } else if (warp == 4 && lane == 0) {
         // ---------------- TMA: A halves (two source boxes) and the operator block ----------------
+        // (hi and lo of a single-block operator are contiguous: one copy)
+        const bool one_b = Np == NB;
         int i = 0;
         for (int s = 0; s < nsteps; ++s) {
             const TcStep st = steps[tile.s0 + s];
@@ -276,8 +284,12 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
                     }
                 }
                 const float* Bc = Bm + (int64_t)c * 32 * Np + (int64_t)n0 * 16;
-                bulk_g2s(sb + 16384, Bc, (uint32_t)(NB * 64), &full[stg]);
-                bulk_g2s(sb + 16384 + NB * 64, Bc + (int64_t)Np * 16, (uint32_t)(NB * 64), &full[stg]);
+                if (one_b) {
+                    bulk_g2s(sb + 16384, Bc, (uint32_t)(NB * 128), &full[stg]);
+                } else {
+                    bulk_g2s(sb + 16384, Bc, (uint32_t)(NB * 64), &full[stg]);
+                    bulk_g2s(sb + 16384 + NB * 64, Bc + (int64_t)Np * 16, (uint32_t)(NB * 64), &full[stg]);
+                }
             }
             if (stop) break;
         }
@@ -397,7 +409,7 @@ struct TcLaunch {
 
 template <int NB>
 hfmm_status launch_nb(hfmm_plan_s* P, const TcLaunch& a, int nrhs, cudaStream_t st) {
-    const size_t smem = (size_t)TC_STAGES * (16384 + NB * 128) + 256;
+    const size_t smem = (size_t)tc_stages<NB>() * (16384 + NB * 128) + 256;
     static bool attr_set = false;
     if (!attr_set) {
         HFMM_CUDA_TRY(cudaFuncSetAttribute(m2l_tc_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -106,8 +106,9 @@ struct hfmm_plan_s {
     cd* io_y = nullptr;
     double* io_gxy = nullptr;
     // mixed path
-    cf* q32 = nullptr;              // [max_rhs][n]
-    cf* y32 = nullptr;
+    cf* q32 = nullptr;              // [n][nrhs] (point-major)
+    cf* y32 = nullptr;              // [n][nrhs]
+    int32_t* iperm32 = nullptr;     // [n] sorted position of caller index j
     cf* d_vals32 = nullptr;
     float2* xl32 = nullptr;         // [n] point offsets from their own leaf centre (FP32)
     cf* basis32 = nullptr;          // [n][2 p_L + 1] scaled P2M basis of each sorted point
