@@ -21,7 +21,7 @@
 // produces it, the operators at plan time.  Pipeline (one CTA = one target
 // pair x 64 right-hand sides x one column block): warp 4 streams every K
 // chunk with cp.async.bulk (two 64-row A halves per part plus the operator
-// block) into a shared-memory ring as deep as two CTAs per SM allow; warp 5
+// block) into a shared-memory ring sized for the CTAs per SM; warp 5
 // issues tcgen05.mma into one of two TMEM buffers per source step (long
 // steps are cut into sub-steps of at most 8 K chunks); warps 0-3 drain each
 // finished step with tcgen05.ld into round-to-nearest FP32 registers
@@ -33,71 +33,32 @@
 #include <vector>
 
 #include "plan.cuh"
+#include "tcgen05.cuh"
 
 namespace {
 
-// Shared-memory ring depth for column blocks of NB: as many stages as fit
-// two CTAs on one SM (about 113 KB each), so more operand bytes are in flight.
+using namespace tc;
+
+// Occupancy of the tensor-core kernel.  Each CTA is one dependent chain (TMA
+// -> MMA -> drain per step), so the pass is latency-bound and wants as many
+// CTAs per SM as tensor memory, registers and shared memory allow: two TMEM
+// accumulation buffers of NB columns in a power-of-two allocation (128
+// columns for NB <= 64, i.e. four CTAs per SM; 256 beyond, where the drain
+// registers limit the SM to two CTAs anyway), and as many ring stages as fit
+// the CTA's share of shared memory (at least two).
 template <int NB>
-constexpr int tc_stages() {
-    return (115200 - 256) / (16384 + NB * 128) < 8 ? (115200 - 256) / (16384 + NB * 128) : 8;
-}
+struct TcCfg {
+    static constexpr int tmem_cols = 2 * NB <= 128 ? 128 : 256;
+    static constexpr int buf_cols = tmem_cols / 2;
+    static constexpr int ctas = 512 / tmem_cols;
+    static constexpr int stage_bytes = 16384 + NB * 128;
+    static constexpr int budget = 232448 / ctas - 1024 - 256 - 64;
+    static constexpr int stages = budget / stage_bytes < 8 ? budget / stage_bytes : 8;
+    static_assert(stages >= 2, "ring needs two stages");
+    static constexpr size_t smem = (size_t)stages * stage_bytes + 256;
+};
 constexpr int TC_MAX_NP = 128;         // widest column block (one 128-column TMEM buffer)
-constexpr long TC_SPIN = 20000000;     // bounded mbarrier polls
 constexpr int TC_STEP_CHUNKS = 8;      // K chunks accumulated in TMEM before a drain
-
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-    // no-swizzle K-major canonical layout: core matrices of 8 rows x 16 B;
-    // K-direction core stride (LBO) 128 B, M/N-direction core stride (SBO) 512 B
-    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)(128 >> 4) << 16;
-    d |= (uint64_t)(512 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    const uint32_t a = su32(bar);
-    for (long it = 0; it < TC_SPIN; ++it) {
-        uint32_t ok;
-        asm volatile("{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, P;\n\t}\n" : "=r"(ok) : "r"(a), "r"(parity) : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(su32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(su32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 :: "r"(su32(dst)), "l"(src), "r"(bytes), "r"(su32(bar)) : "memory");
-}
-
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
-                 :: "r"(dtmem), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                 :: "r"(su32(bar)) : "memory");
-}
 
 struct TcTile { int32_t b0, b1, s0, s1; };          // boxes (-1: empty), step range
 // kind 0 free M2L, 1 reaction M2L, 2 secondary source (L2L parent or M2M child);
@@ -155,8 +116,9 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr int stage_bytes = 16384 + NB * 128;
-    constexpr int TC_STAGES = tc_stages<NB>();
+    using CFG = TcCfg<NB>;
+    constexpr int stage_bytes = CFG::stage_bytes;
+    constexpr int TC_STAGES = CFG::stages;
     uint64_t* full = (uint64_t*)(smem + TC_STAGES * stage_bytes);
     uint64_t* empty = full + TC_STAGES;
     uint64_t* dfull = empty + TC_STAGES;
@@ -165,7 +127,7 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
     const TcTile tile = tiles[blockIdx.x];
     const int rc = blockIdx.y;
     const int n0 = blockIdx.z * NB;
-    const uint32_t ncols = 256;
+    const uint32_t ncols = CFG::tmem_cols;
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(&full[s])), "r"(1));
@@ -201,7 +163,7 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
             good = __all_sync(0xffffffffu, good);
             if (!good) { ok = false; s_abort = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t tb = taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 128);
+            const uint32_t tb = taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * CFG::buf_cols);
 #pragma unroll
             for (int c0 = 0; c0 < NB; c0 += 16) {
                 uint32_t v[16];
@@ -302,7 +264,7 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
             const int b = s & 1;
             if (s_abort || !mbar_wait(&dfree[b], (uint32_t)(((s >> 1) & 1) ^ 1))) { s_abort = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t dt = taddr + (uint32_t)(b * 128);
+            const uint32_t dt = taddr + (uint32_t)(b * CFG::buf_cols);
             const int nk = steps[tile.s0 + s].c1 - steps[tile.s0 + s].c0;
             uint32_t accf = 0;
             for (int c = 0; c < nk; ++c, ++i) {
@@ -409,7 +371,7 @@ struct TcLaunch {
 
 template <int NB>
 hfmm_status launch_nb(hfmm_plan_s* P, const TcLaunch& a, int nrhs, cudaStream_t st) {
-    const size_t smem = (size_t)tc_stages<NB>() * (16384 + NB * 128) + 256;
+    const size_t smem = TcCfg<NB>::smem;
     static bool attr_set = false;
     if (!attr_set) {
         HFMM_CUDA_TRY(cudaFuncSetAttribute(m2l_tc_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
