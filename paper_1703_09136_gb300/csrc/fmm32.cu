@@ -415,7 +415,7 @@ __device__ __forceinline__ void p2p_pass(PcShared& S, const int32_t* lb, int L, 
     }
 }
 
-__global__ void __launch_bounds__(PC_THREADS) p2p32c_kernel(const int32_t* lb, int L, const float2* xl,
+__global__ void __launch_bounds__(PC_THREADS, 6) p2p32c_kernel(const int32_t* lb, int L, const float2* xl,
                                                             const cf* qs, int64_t n, int nrhs, float k,
                                                             float h, int near, const cf* loc,
                                                             const cf* basis, int nc, cf* ys) {

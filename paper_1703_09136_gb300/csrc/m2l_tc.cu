@@ -102,17 +102,58 @@ __global__ void tc_btable_kernel(const cf* M, int nmat, int nin, int nout, int N
 
 constexpr int TC2_THREADS = 192;   // warps 0-3 drain, warp 4 TMA, warp 5 MMA
 
+// Store one row of a finished tile: the FP32 coefficients out[box][r][0 .. nc)
+// (columns n0 .. n0 + NB - 1 of the real GEMM: Re then Im) and, when sdst is
+// given, the MMA-ready copy of the row (every row of the 64-row block, so
+// rows r >= nrhs stay zero).
+template <int NB>
+__device__ __forceinline__ void tc_store_row(const float (&acc)[NB], int box, int row, int rc, int n0, int nrhs, int nc,
+                                             int nrc, cf* __restrict__ out, float* __restrict__ sdst, int kcd) {
+    const int rr = row & 63, r = rc * 64 + rr;
+    if (r < nrhs) {
+        float* o = (float*)(out + ((int64_t)box * nrhs + r) * nc);
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            const int g = n0 + j;
+            if (g < nc) o[2 * g] = acc[j];
+            else if (g < 2 * nc) o[2 * (g - nc) + 1] = acc[j];
+        }
+    }
+    if (sdst) {
+        float* base = sdst + (((int64_t)box * nrc + rc) * kcd * 2) * 1024 + ((rr >> 3) * 4) * 32 + (rr & 7) * 4;
+#pragma unroll
+        for (int j = 0; j < NB; j += 4) {
+            const int g = n0 + j;
+            if ((g >> 4) < kcd) {
+                float h[4], lo[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    h[u] = __uint_as_float(tf32_rna(acc[j + u]));
+                    lo[u] = __uint_as_float(tf32_rna(acc[j + u] - h[u]));
+                }
+                float* d = base + (int64_t)(g >> 4) * 2048 + ((g & 15) >> 2) * 32;
+                *(float4*)d = make_float4(h[0], h[1], h[2], h[3]);
+                *(float4*)(d + 1024) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+            }
+        }
+    }
+}
+
 // One CTA = one target pair x 64 right-hand sides x one block of NB real
-// output columns (blockIdx.z; columns n0 .. n0 + NB - 1 of the Np-wide GEMM).
-// The result goes to the FP32 coefficients out[box][r][0 .. nc) and, when
-// sdst is given, also in MMA-ready form (kcd K chunks, the layout above)
-// for the next tensor-core consumer of these coefficients.
+// output columns (columns n0 .. n0 + NB - 1 of the Np-wide GEMM) x one
+// segment of the tile's steps (blockIdx.z = segment * column blocks + block).
+// With one segment the result goes to the FP32 coefficients out[box][r][0 ..
+// nc) and, when sdst is given, also in MMA-ready form (kcd K chunks, the
+// layout above) for the next tensor-core consumer; with several segments
+// (levels with too few tiles to fill the GPU) each CTA writes its partial
+// sums to part and tc_reduce_kernel finishes the store.
 template <int NB>
 __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
     const TcTile* __restrict__ tiles, const TcStep* __restrict__ steps, const float* __restrict__ Bfree,
     const float* __restrict__ Breact, const float* __restrict__ Bl2l, const float* __restrict__ amma,
     const float* __restrict__ pmma, const float* __restrict__ zero4k, cf* __restrict__ out, int nrhs, int nc,
-    int kc, int kc2, int nrc, int Np, float* __restrict__ sdst, int kcd, int* err) {
+    int kc, int kc2, int nrc, int Np, float* __restrict__ sdst, int kcd, int nseg, float* __restrict__ part,
+    int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -126,7 +167,9 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
     uint32_t* tslot = (uint32_t*)(dfree + 2);
     const TcTile tile = tiles[blockIdx.x];
     const int rc = blockIdx.y;
-    const int n0 = blockIdx.z * NB;
+    const int nbz = Np / NB;
+    const int cb = (int)blockIdx.z % nbz, seg = (int)blockIdx.z / nbz;
+    const int n0 = cb * NB;
     const uint32_t ncols = CFG::tmem_cols;
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
@@ -149,10 +192,16 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t taddr = *tslot;
-    const int nsteps = tile.s1 - tile.s0;
+    int sbeg = tile.s0, nsteps = tile.s1 - tile.s0;
+    if (nseg > 1) {
+        const int len = (nsteps + nseg - 1) / nseg;
+        const int a = min(nsteps, seg * len);
+        sbeg = tile.s0 + a;
+        nsteps = min(nsteps, a + len) - a;
+    }
     if (warp < 4) {
         // ---------------- drain: FP32 round-to-nearest accumulation ----------------
-        const int row = tid, tgt = row >> 6, r = rc * 64 + (row & 63);
+        const int row = tid, tgt = row >> 6;
         float acc[NB];
 #pragma unroll
         for (int j = 0; j < NB; ++j) acc[j] = 0.0f;
@@ -181,39 +230,14 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
         }
         if (!ok || s_abort) {
             if (lane == 0) atomicExch(err, 1);
+        } else if (part) {
+            float* pp = part + ((((int64_t)seg * gridDim.x + blockIdx.x) * gridDim.y + rc) * nbz + cb) * 128 * NB +
+                        (int64_t)row * NB;
+#pragma unroll
+            for (int j = 0; j < NB; j += 4) *(float4*)(pp + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
         } else {
             const int box = tgt ? tile.b1 : tile.b0;
-            if (box >= 0) {
-                if (r < nrhs) {
-                    float* o = (float*)(out + ((int64_t)box * nrhs + r) * nc);
-#pragma unroll
-                    for (int j = 0; j < NB; ++j) {
-                        const int g = n0 + j;
-                        if (g < nc) o[2 * g] = acc[j];
-                        else if (g < 2 * nc) o[2 * (g - nc) + 1] = acc[j];
-                    }
-                }
-                if (sdst) {
-                    // every row of the 64-row block, so rows r >= nrhs stay zero
-                    const int rr = row & 63;
-                    float* base = sdst + (((int64_t)box * nrc + rc) * kcd * 2) * 1024 + ((rr >> 3) * 4) * 32 + (rr & 7) * 4;
-#pragma unroll
-                    for (int j = 0; j < NB; j += 4) {
-                        const int g = n0 + j;
-                        if ((g >> 4) < kcd) {
-                            float h[4], lo[4];
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                h[u] = __uint_as_float(tf32_rna(acc[j + u]));
-                                lo[u] = __uint_as_float(tf32_rna(acc[j + u] - h[u]));
-                            }
-                            float* d = base + (int64_t)(g >> 4) * 2048 + ((g & 15) >> 2) * 32;
-                            *(float4*)d = make_float4(h[0], h[1], h[2], h[3]);
-                            *(float4*)(d + 1024) = make_float4(lo[0], lo[1], lo[2], lo[3]);
-                        }
-                    }
-                }
-            }
+            if (box >= 0) tc_store_row<NB>(acc, box, row, rc, n0, nrhs, nc, nrc, out, sdst, kcd);
         }
     } else if (warp == 4 && lane == 0) {
         // ---------------- TMA: A halves (two source boxes) and the operator block ----------------
@@ -221,7 +245,7 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
         const bool one_b = Np == NB;
         int i = 0;
         for (int s = 0; s < nsteps; ++s) {
-            const TcStep st = steps[tile.s0 + s];
+            const TcStep st = steps[sbeg + s];
             const bool sec = st.kind == 2;
             const int nk = sec ? kc2 : kc;
             const float* base = sec ? pmma : amma;
@@ -265,7 +289,7 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
             if (s_abort || !mbar_wait(&dfree[b], (uint32_t)(((s >> 1) & 1) ^ 1))) { s_abort = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t dt = taddr + (uint32_t)(b * CFG::buf_cols);
-            const int nk = steps[tile.s0 + s].c1 - steps[tile.s0 + s].c0;
+            const int nk = steps[sbeg + s].c1 - steps[sbeg + s].c0;
             uint32_t accf = 0;
             for (int c = 0; c < nk; ++c, ++i) {
                 const int stg = i % TC_STAGES;
@@ -290,6 +314,59 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(ncols));
+}
+
+// Sum the segments' partial results of a split launch and store them like
+// the single-segment epilogue; one thread per (tile, RHS block, column block,
+// row, group of four columns).
+template <int NB>
+__global__ void tc_reduce_kernel(const TcTile* __restrict__ tiles, int ntiles, int nrcl, int nbz, int nseg,
+                                 const float* __restrict__ part, cf* __restrict__ out, int nrhs, int nc, int nrc,
+                                 float* __restrict__ sdst, int kcd) {
+    constexpr int NQ = NB / 4;
+    const int64_t total = (int64_t)ntiles * nrcl * nbz * 128 * NQ;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int jq = (int)(e % NQ);
+        int64_t rest = e / NQ;
+        const int row = (int)(rest % 128);
+        rest /= 128;
+        const int cb = (int)(rest % nbz);
+        rest /= nbz;
+        const int rc = (int)(rest % nrcl);
+        const int64_t t = rest / nrcl;
+        const TcTile tile = tiles[t];
+        const int box = (row >> 6) ? tile.b1 : tile.b0;
+        if (box < 0) continue;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int sg = 0; sg < nseg; ++sg) {
+            const float4 w = *(const float4*)(part + ((((int64_t)sg * ntiles + t) * nrcl + rc) * nbz + cb) * 128 * NB +
+                                              (int64_t)row * NB + 4 * jq);
+            v.x += w.x; v.y += w.y; v.z += w.z; v.w += w.w;
+        }
+        const float a4[4] = {v.x, v.y, v.z, v.w};
+        const int rr = row & 63, r = rc * 64 + rr, g0 = cb * NB + 4 * jq;
+        if (r < nrhs) {
+            float* o = (float*)(out + ((int64_t)box * nrhs + r) * nc);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int g = g0 + u;
+                if (g < nc) o[2 * g] = a4[u];
+                else if (g < 2 * nc) o[2 * (g - nc) + 1] = a4[u];
+            }
+        }
+        if (sdst && (g0 >> 4) < kcd) {
+            float h[4], lo[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                h[u] = __uint_as_float(tf32_rna(a4[u]));
+                lo[u] = __uint_as_float(tf32_rna(a4[u] - h[u]));
+            }
+            float* d = sdst + (((int64_t)box * nrc + rc) * kcd * 2) * 1024 + ((rr >> 3) * 4) * 32 + (rr & 7) * 4 +
+                       (int64_t)(g0 >> 4) * 2048 + ((g0 & 15) >> 2) * 32;
+            *(float4*)d = make_float4(h[0], h[1], h[2], h[3]);
+            *(float4*)(d + 1024) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+        }
+    }
 }
 
 inline int round16(int x) { return (x + 15) / 16 * 16; }
@@ -332,8 +409,10 @@ void pair_tiles(int64_t nbox, NonEmpty nonempty, Add add, std::vector<TcTile>& t
 }
 
 hfmm_status upload_tiles(hfmm_plan_s* P, const std::vector<TcTile>& tiles, const std::vector<TcStep>& steps,
-                         void** dt, void** ds, int64_t* nt) {
+                         void** dt, void** ds, int64_t* nt, int* maxsteps) {
     *nt = (int64_t)tiles.size();
+    *maxsteps = 0;
+    for (const TcTile& t : tiles) *maxsteps = std::max(*maxsteps, (int)(t.s1 - t.s0));
     HFMM_TRY(plan_alloc(P, dt, sizeof(TcTile) * std::max<size_t>(tiles.size(), 1)));
     HFMM_TRY(plan_alloc(P, ds, sizeof(TcStep) * std::max<size_t>(steps.size(), 1)));
     if (!tiles.empty()) {
@@ -367,7 +446,17 @@ struct TcLaunch {
     int nc, kc, kc2, np, nb, nbw;
     float* sdst;
     int kcd;
+    int maxsteps;
 };
+
+// Segments per tile for a launch of ntiles x nb CTAs (x nrc RHS blocks): split
+// the step lists when the launch would leave most SMs idle.
+int tc_nseg(int64_t ntiles, int nb, int nrc, int maxsteps) {
+    const int64_t ctas = ntiles * nb * nrc;
+    if (ctas >= 2 * 152 || maxsteps < 4) return 1;
+    const int64_t want = (4 * 152 + ctas - 1) / ctas;
+    return (int)std::max<int64_t>(1, std::min<int64_t>({want, 16, maxsteps / 2}));
+}
 
 template <int NB>
 hfmm_status launch_nb(hfmm_plan_s* P, const TcLaunch& a, int nrhs, cudaStream_t st) {
@@ -378,11 +467,22 @@ hfmm_status launch_nb(hfmm_plan_s* P, const TcLaunch& a, int nrhs, cudaStream_t 
         attr_set = true;
     }
     const int nrc = (P->max_rhs + 63) / 64;
-    dim3 grid((unsigned)a.ntiles, (unsigned)((nrhs + 63) / 64), (unsigned)a.nb);
+    const int nrcl = (nrhs + 63) / 64;
+    const int nseg = tc_nseg(a.ntiles, a.nb, nrc, a.maxsteps);
+    float* part = nseg > 1 ? P->tc_part : nullptr;
+    dim3 grid((unsigned)a.ntiles, (unsigned)nrcl, (unsigned)(a.nb * nseg));
     m2l_tc_kernel<NB><<<grid, TC2_THREADS, smem, st>>>(
         (const TcTile*)a.tiles, (const TcStep*)a.steps, a.Bfree, a.Breact, a.Bsec, a.amma, a.pmma, P->tc_zero, a.out,
-        nrhs, a.nc, a.kc, a.kc2, nrc, a.np, a.sdst, a.kcd, P->tc_err);
+        nrhs, a.nc, a.kc, a.kc2, nrc, a.np, a.sdst, a.kcd, nseg, part, P->tc_err);
     HFMM_CUDA_TRY(cudaGetLastError());
+    if (part) {
+        const int64_t total = a.ntiles * nrcl * a.nb * 128 * (NB / 4);
+        const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 8 * 152);
+        tc_reduce_kernel<NB><<<blocks, 256, 0, st>>>((const TcTile*)a.tiles, (int)a.ntiles, nrcl, a.nb, nseg, part,
+                                                      a.out, nrhs, a.nc, nrc, a.sdst, a.kcd);
+        HFMM_CUDA_TRY(cudaGetLastError());
+        ++P->launches;
+    }
     return HFMM_OK;
 }
 
@@ -484,7 +584,7 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
                 for (auto& kv : mm) push_step(steps, 1, kv.first, kv.second.first, kv.second.second, lv.tc_kc);
             }
         }, tiles, steps);
-        HFMM_TRY(upload_tiles(P, tiles, steps, &lv.tc_tiles, &lv.tc_steps, &lv.tc_ntiles));
+        HFMM_TRY(upload_tiles(P, tiles, steps, &lv.tc_tiles, &lv.tc_steps, &lv.tc_ntiles, &lv.tc_maxsteps));
     }
     // M2M into level l from its children (level l + 1)
     for (int l = P->lmin; l < L; ++l) {
@@ -503,7 +603,21 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
                 if (s0 >= 0 || s1 >= 0) push_step(steps, 2, c, s0, s1, ch.tc_kc);
             }
         }, tiles, steps);
-        HFMM_TRY(upload_tiles(P, tiles, steps, &lv.tc_mtiles, &lv.tc_msteps, &lv.tc_nmtiles));
+        HFMM_TRY(upload_tiles(P, tiles, steps, &lv.tc_mtiles, &lv.tc_msteps, &lv.tc_nmtiles, &lv.tc_mmaxsteps));
+    }
+    // partial-sum buffer of split launches (largest need over the levels)
+    size_t need = 0;
+    for (int l = P->lmin; l <= L; ++l) {
+        const LevelInfo& lv = P->lev[l];
+        const int sd = tc_nseg(lv.tc_ntiles, lv.tc_nb, nrc, lv.tc_maxsteps);
+        if (sd > 1) need = std::max(need, (size_t)sd * lv.tc_ntiles * nrc * lv.tc_nb * 128 * lv.tc_nbw);
+        const int sm = tc_nseg(lv.tc_nmtiles, lv.tc_nb, nrc, lv.tc_mmaxsteps);
+        if (sm > 1) need = std::max(need, (size_t)sm * lv.tc_nmtiles * nrc * lv.tc_nb * 128 * lv.tc_nbw);
+    }
+    if (need) {
+        HFMM_TRY(plan_alloc(P, (void**)&P->tc_part, sizeof(float) * need));
+        P->tc_part_floats = need;
+        P->buffer_bytes += sizeof(float) * (double)need;
     }
     HFMM_TRY(plan_alloc(P, (void**)&P->tc_err, sizeof(int)));
     HFMM_CUDA_TRY(cudaMemsetAsync(P->tc_err, 0, sizeof(int), st));
@@ -521,7 +635,8 @@ hfmm_status launch_m2m_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st) {
     LevelInfo& lv = P->lev[l];
     const LevelInfo& ch = P->lev[l + 1];
     TcLaunch a{lv.tc_mtiles, lv.tc_msteps, lv.tc_nmtiles, nullptr, nullptr, lv.tc_bm2m, nullptr, ch.tc_amma,
-               lv.mult32, lv.ncoef, 0, ch.tc_kc, lv.tc_np, lv.tc_nb, lv.tc_nbw, lv.tc_amma, lv.tc_kc};
+               lv.mult32, lv.ncoef, 0, ch.tc_kc, lv.tc_np, lv.tc_nb, lv.tc_nbw, lv.tc_amma, lv.tc_kc,
+               lv.tc_mmaxsteps};
     return launch_tc(P, a, nrhs, st);
 }
 
@@ -532,6 +647,6 @@ hfmm_status launch_m2l_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st) {
     const bool below = l < P->L;
     TcLaunch a{lv.tc_tiles, lv.tc_steps, lv.tc_ntiles, lv.tc_bfree, lv.tc_breact, lv.tc_bl2l, lv.tc_amma,
                lv.tc_pmma, lv.loc32, lv.ncoef, lv.tc_kc, lv.tc_kc2, lv.tc_np, lv.tc_nb, lv.tc_nbw,
-               below ? P->lev[l + 1].tc_pmma : nullptr, below ? P->lev[l + 1].tc_kc2 : 0};
+               below ? P->lev[l + 1].tc_pmma : nullptr, below ? P->lev[l + 1].tc_kc2 : 0, lv.tc_maxsteps};
     return launch_tc(P, a, nrhs, st);
 }

@@ -68,6 +68,7 @@ struct LevelInfo {
     void* tc_mtiles = nullptr;
     void* tc_msteps = nullptr;
     int64_t tc_nmtiles = 0;
+    int tc_maxsteps = 0, tc_mmaxsteps = 0;   // longest step list of a tile (downward, M2M)
     float* tc_amma = nullptr;     // MMA-ready multipoles of this level
     float* tc_pmma = nullptr;     // MMA-ready local expansions of the parent level
 };
@@ -124,6 +125,8 @@ struct hfmm_plan_s {
     bool tc_on = false;             // every level lmin..L has tensor-core M2M / downward state
     int* tc_err = nullptr;          // set by the tensor-core pass when a bounded wait gave up
     float* tc_zero = nullptr;       // 4 KB of zeros: the A half of a missing source box
+    float* tc_part = nullptr;       // partial sums of split launches (levels with few tiles)
+    size_t tc_part_floats = 0;
 
     // info
     int64_t u_pairs = 0;
