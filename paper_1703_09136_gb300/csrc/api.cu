@@ -285,6 +285,7 @@ static hfmm_status plan_create_one(hfmm_plan_t* out, int64_t n, const double* xy
             if ((s = init_h0_table(st)) != HFMM_OK) break;
             if ((s = build_local_coords(P, st)) != HFMM_OK) break;
             if (!(P->flags & HFMM_FLAG_SIMT_M2L) && (s = build_tc(P, st)) != HFMM_OK) break;
+            if (P->tc_on && (s = build_p2p_tc(P, st)) != HFMM_OK) break;
         }
         if (P->flags & HFMM_FLAG_PROFILE) {
             for (int sg = 0; sg < HFMM_NUM_STAGES && s == HFMM_OK; ++sg)

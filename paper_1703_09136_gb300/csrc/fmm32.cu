@@ -29,6 +29,12 @@ __constant__ float c_h0r[H0_NI][H0_DEG + 1];
 float h_h0j[H0_NI][H0_DEG + 1], h_h0r[H0_NI][H0_DEG + 1];
 bool h0_ready = false;
 
+__device__ __forceinline__ uint32_t f32_to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
 void fit_h0_table() {
     const int n = H0_DEG + 1;
     double tn[n], cheb[n][n];   // Chebyshev -> monomial coefficients
@@ -418,9 +424,10 @@ __device__ __forceinline__ void p2p_pass(PcShared& S, const int32_t* lb, int L, 
 __global__ void __launch_bounds__(PC_THREADS, 6) p2p32c_kernel(const int32_t* lb, int L, const float2* xl,
                                                             const cf* qs, int64_t n, int nrhs, float k,
                                                             float h, int near, const cf* loc,
-                                                            const cf* basis, int nc, cf* ys) {
+                                                            const cf* basis, int nc, const int32_t* leaves,
+                                                            cf* ys) {
     __shared__ PcShared S;
-    const int64_t b = blockIdx.x;
+    const int64_t b = leaves ? (int64_t)leaves[blockIdx.x] : (int64_t)blockIdx.x;
     const int32_t tlo = lb[b], thi = lb[b + 1];
     if (thi <= tlo) return;
     for (int e = threadIdx.x; e < H0_NI * (H0_DEG + 1); e += blockDim.x) {
@@ -578,6 +585,102 @@ hfmm_status init_h0_table(cudaStream_t st) {
     return HFMM_OK;
 }
 
+// Plan-time B tiles of the tensor-core near field.  Thread per (chunk, tile
+// row, K pair j): for a source chunk the value (i/4) H0(k |x_t - x_s|) of the
+// row's target and the chunk's j-th source (0 for padding, for the self pair),
+// computed exactly as in the SIMT near-field kernel; for an L2P chunk
+// (i/4) conj(basis[t][8 kk + j]).  Stored as (Re g, -Im g), TF32 hi and lo, in
+// the core-matrix layout of a rows x 16 tile.
+__global__ void near_tiles_kernel(const NtChunk* __restrict__ chunks, const int64_t* __restrict__ row0, int64_t nch,
+                                  int64_t total, const int32_t* __restrict__ lb, int L, const float2* __restrict__ xl,
+                                  const cf* __restrict__ basis, int nc, float k, float h, float* __restrict__ tiles) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total * 8;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t gr = e >> 3;
+        const int j = (int)(e & 7);
+        // chunk of this global row (row0: first global row of each chunk)
+        int64_t lo = 0, hi = nch - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (row0[mid] <= gr) lo = mid; else hi = mid - 1;
+        }
+        const NtChunk ch = chunks[lo];
+        const int n = (int)(gr - row0[lo]);
+        // target of row n: leaves of the mask in order, each padded to a multiple of 16
+        int c = 0, t = n;
+        for (c = 0; c < 4; ++c) {
+            if (!(ch.mask >> c & 1)) continue;
+            const int64_t lf = 4 * (int64_t)ch.par + c;
+            const int w = (lb[lf + 1] - lb[lf] + 15) / 16 * 16;
+            if (t < w) break;
+            t -= w;
+        }
+        const int64_t lf = 4 * (int64_t)ch.par + c;
+        const int32_t tlo = lb[lf], tn = lb[lf + 1] - tlo;
+        cf g = cfmk(0.f, 0.f);
+        if (c < 4 && t < tn) {
+            const int32_t ti = tlo + t;
+            if (ch.src >= 0) {
+                if (j < ch.cnt && ch.src + j != ti) {
+                    const int32_t si = ch.src + j;
+                    // c_T - c_S in box units: target child c of the parent, source leaf code aux
+                    const float ox = (float)((c & 1) - ((ch.aux & 3) - 1)) * h;
+                    const float oy = (float)((c >> 1) - ((ch.aux >> 2) - 1)) * h;
+                    const float ddx = ox + (xl[ti].x - xl[si].x);
+                    const float ddy = oy + (xl[ti].y - xl[si].y);
+                    const float z = k * sqrtf(ddx * ddx + ddy * ddy);
+                    if (z < H0_ZMAX) {
+                        g = green_free_f32(z);
+                    } else {
+                        const cd h0 = hankel0((double)z);
+                        g = cfmk((float)(-0.25 * h0.y), (float)(0.25 * h0.x));
+                    }
+                }
+            } else {
+                const int mm = 8 * ch.cnt + j;
+                if (mm < nc) {
+                    const cf bb = basis[(int64_t)ti * nc + mm];
+                    g = cfmk(0.25f * bb.y, 0.25f * bb.x);
+                }
+            }
+        }
+        const float re = g.x, im = -g.y;
+        const float reh = __uint_as_float(f32_to_tf32(re)), imh = __uint_as_float(f32_to_tf32(im));
+        const float rel = __uint_as_float(f32_to_tf32(re - reh)), iml = __uint_as_float(f32_to_tf32(im - imh));
+        const int k0 = 2 * j;
+        const int64_t o = ((n >> 3) * 4 + (k0 >> 2)) * 32 + (n & 7) * 4 + (k0 & 3);
+        float* tile = tiles + ch.boff;
+        *(float2*)(tile + o) = make_float2(reh, imh);
+        *(float2*)(tile + (int64_t)ch.rows * 16 + o) = make_float2(rel, iml);
+    }
+}
+
+hfmm_status fill_near_tiles(hfmm_plan_s* P, int64_t nchunks, int64_t total_rows, cudaStream_t st) {
+    // first global row of every chunk
+    std::vector<NtChunk> h(nchunks);
+    HFMM_CUDA_TRY(cudaMemcpy(h.data(), P->nt_chunks, sizeof(NtChunk) * nchunks, cudaMemcpyDeviceToHost));
+    std::vector<int64_t> r0(nchunks);
+    int64_t acc = 0;
+    for (int64_t i = 0; i < nchunks; ++i) { r0[i] = acc; acc += h[i].rows; }
+    int64_t* d_r0 = nullptr;
+    HFMM_CUDA_TRY(cudaMalloc(&d_r0, sizeof(int64_t) * std::max<int64_t>(nchunks, 1)));
+    cudaError_t e = cudaMemcpy(d_r0, r0.data(), sizeof(int64_t) * nchunks, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        const LevelInfo& lv = P->lev[P->L];
+        near_tiles_kernel<<<8 * 152, 256, 0, st>>>(P->nt_chunks, d_r0, nchunks, total_rows, P->leaf_begin, P->L,
+                                                    P->xl32, P->basis32, lv.ncoef, (float)P->k, (float)lv.h,
+                                                    P->nt_tiles);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    cudaFree(d_r0);
+    if (e != cudaSuccess) {
+        hfmm_set_error("near-field tiles: %s", cudaGetErrorString(e));
+        return HFMM_ERR_CUDA;
+    }
+    return HFMM_OK;
+}
+
 hfmm_status build_local_coords(hfmm_plan_s* P, cudaStream_t st) {
     HFMM_TRY(plan_alloc(P, (void**)&P->xl32, sizeof(float2) * P->n));
     const LevelInfo& lv = P->lev[P->L];
@@ -702,12 +805,25 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
         const LevelInfo& lv = P->lev[L];
         const bool near = (parts & HFMM_PART_NEAR_FREE) != 0;
         tm.begin(HFMM_STAGE_P2P);
-        p2p32c_kernel<<<(unsigned)lv.nbox, PC_THREADS, 0, st>>>(P->leaf_begin, L, P->xl32, P->q32, n, nrhs,
-                                                                (float)P->k, (float)lv.h, near ? 1 : 0,
-                                                                far ? lv.loc32 : nullptr, P->basis32, lv.ncoef,
-                                                                P->y32);
-        ++P->launches;
-        HFMM_CUDA_TRY(cudaGetLastError());
+        if (P->tc_on) {
+            // tensor-core blocks of four leaves; SIMT kernel for the leaves of wider blocks
+            HFMM_TRY(launch_p2p_tc(P, nrhs, near, far, st));
+            ++P->launches;
+            if (P->nt_nfallback > 0) {
+                p2p32c_kernel<<<(unsigned)P->nt_nfallback, PC_THREADS, 0, st>>>(
+                    P->leaf_begin, L, P->xl32, P->q32, n, nrhs, (float)P->k, (float)lv.h, near ? 1 : 0,
+                    far ? lv.loc32 : nullptr, P->basis32, lv.ncoef, P->nt_fallback, P->y32);
+                ++P->launches;
+                HFMM_CUDA_TRY(cudaGetLastError());
+            }
+        } else {
+            p2p32c_kernel<<<(unsigned)lv.nbox, PC_THREADS, 0, st>>>(P->leaf_begin, L, P->xl32, P->q32, n, nrhs,
+                                                                    (float)P->k, (float)lv.h, near ? 1 : 0,
+                                                                    far ? lv.loc32 : nullptr, P->basis32, lv.ncoef,
+                                                                    nullptr, P->y32);
+            ++P->launches;
+            HFMM_CUDA_TRY(cudaGetLastError());
+        }
         tm.end(HFMM_STAGE_P2P);
         P->st_flops[HFMM_STAGE_P2P] = (near ? MAC * (double)P->p2p_point_pairs : 0.0) +
                                       (far ? MAC * n * lv.ncoef : 0.0);

@@ -1,0 +1,380 @@
+// Near field of the mixed path on tensor cores (tcgen05, sm_103a): the
+// free-space P2P sum (Algorithm 1, step 5) and the L2P evaluation (step 4) of
+// the four leaves of one parent box (a block), as one real GEMM per CTA.
+//
+// With rows = (right-hand side r, part) (part 0: real, 1: imaginary; M = 128
+// for 64 right-hand sides), columns = the block's targets (each leaf padded to
+// a multiple of 16, N <= 128) and K = (source j, re / im), the complex sum
+// y_t = sum_j G_tj q_j is
+//     D[(r, 0)][t] = sum_j  Re q_j Re G_tj + Im q_j (-Im G_tj)
+//     D[(r, 1)][t] = sum_j  Im q_j Re G_tj + (-Re q_j)(-Im G_tj),
+// so the A rows are (Re q, Im q) and (Im q, -Re q) and the B rows
+// (Re G, -Im G).  The points are fixed, so the B tiles (G = (i/4) H0(k r) of
+// each 8-source chunk of each source leaf of the 4 x 4 neighbourhood against
+// the adjacent target leaves only, and (i/4) conj(basis) of each leaf's L2P)
+// are computed once per plan, pre-split into TF32 hi / lo in the core-matrix
+// layout (fmm32.cu, near_tiles_kernel).  Per apply, warp 4 streams the tiles
+// with cp.async.bulk (prefetched into L2 a few chunks ahead); warps 0-3 build the A rows of each chunk from the
+// strengths (or the leaf's local coefficients) in shared memory; warp 5 issues
+// one 3xTF32 MMA set (hi*hi + hi*lo + lo*hi) per run of adjacent target leaves
+// into one of two TMEM buffers used in turn; warps 0-3 finally sum the buffers
+// in FP32 and store y (point-major, [n][nrhs]; the kernel is the first writer
+// of its targets).  Every mbarrier wait is bounded.
+#include <algorithm>
+#include <vector>
+
+#include "plan.cuh"
+#include "tcgen05.cuh"
+
+namespace {
+
+using namespace tc;
+
+constexpr int NT_THREADS = 192;    // warps 0-3 build A and drain, warp 4 TMA, warp 5 MMA
+constexpr int NT_STAGES = 3;
+constexpr int NT_MAXN = 128;       // padded targets of a block
+constexpr int NT_A = 16384;        // A: 128 rows x 16 K, hi then lo
+constexpr int NT_B = NT_MAXN * 128;
+constexpr int NT_STAGE = NT_A + NT_B;
+constexpr int NT_MAXCH = 192;     // chunks of a block (kept in shared memory)
+constexpr int NT_PREF = 6;         // tiles brought into L2 ahead of their copy
+constexpr size_t NT_SMEM = (size_t)NT_STAGES * NT_STAGE + 1024;
+
+// float offset of (row, k) in a core-matrix tile (K = 16)
+__device__ __forceinline__ int core_off(int row, int k) {
+    return ((row >> 3) * 4 + (k >> 2)) * 32 + (row & 7) * 4 + (k & 3);
+}
+
+__device__ __forceinline__ void split2(float x, float& h, float& l) {
+    h = __uint_as_float(tf32_rna(x));
+    l = __uint_as_float(tf32_rna(x - h));
+}
+
+// A operand: the complex value v of (K pair j, right-hand side r) into rows r
+// (Re v, Im v) and 64 + r (Im v, -Re v), K columns 2j, 2j + 1, hi and lo parts.
+__device__ __forceinline__ void put_a(float* A, int j, int r, cf v) {
+    float rh, rl, ih, il;
+    split2(v.x, rh, rl);
+    split2(v.y, ih, il);
+    const int o0 = core_off(r, 2 * j), o1 = core_off(64 + r, 2 * j);
+    *(float2*)(A + o0) = make_float2(rh, ih);
+    *(float2*)(A + 2048 + o0) = make_float2(rl, il);
+    *(float2*)(A + o1) = make_float2(ih, -rh);
+    *(float2*)(A + 2048 + o1) = make_float2(il, -rl);
+}
+
+struct NtSmall {
+    NtChunk ch[NT_MAXCH];      // the block's chunk records
+    int32_t tidx[NT_MAXN];     // target of each column, -1: padding
+    int32_t off[5], wid[4], lbox[4];
+};
+
+__global__ void __launch_bounds__(NT_THREADS, 2) p2p_tc_kernel(
+    const int32_t* __restrict__ blocks, const NtChunk* __restrict__ chunks, const float* __restrict__ tiles,
+    const int32_t* __restrict__ lb, const cf* __restrict__ qs, int nrhs, int near, int far, const cf* __restrict__ loc,
+    int nc, cf* __restrict__ ys, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ NtSmall S;
+    __shared__ uint64_t afull[NT_STAGES], bfull[NT_STAGES], empty[NT_STAGES], done;
+    __shared__ uint32_t tslot;
+    __shared__ volatile int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t P = blocks[4 * blockIdx.x];
+    const int cb = near ? blocks[4 * blockIdx.x + 1] : blocks[4 * blockIdx.x + 2];
+    const int ce = far ? blocks[4 * blockIdx.x + 3] : blocks[4 * blockIdx.x + 2];
+    const int nch = ce - cb;
+    const int rc = blockIdx.y, r0 = rc * 64;
+    if (tid == 0) {
+        int o = 0;
+        for (int c = 0; c < 4; ++c) {
+            const int64_t lf = 4 * P + c;
+            S.lbox[c] = (int32_t)lf;
+            S.off[c] = o;
+            S.wid[c] = (lb[lf + 1] - lb[lf] + 15) / 16 * 16;
+            o += S.wid[c];
+        }
+        S.off[4] = o;
+        for (int s = 0; s < NT_STAGES; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(&afull[s])), "r"(128));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(&bfull[s])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(&empty[s])), "r"(1));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(&done)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        s_abort = 0;
+    }
+    __syncthreads();
+    const int N = S.off[4];
+    for (int i = tid; i < nch; i += NT_THREADS) S.ch[i] = chunks[cb + i];
+    for (int n = tid; n < NT_MAXN; n += NT_THREADS) {
+        int32_t ti = -1;
+        if (n < N) {
+            int c = 0;
+            while (n >= S.off[c + 1]) ++c;
+            const int64_t lf = 4 * P + c;
+            const int t = n - S.off[c];
+            if (t < lb[lf + 1] - lb[lf]) ti = lb[lf] + t;
+        }
+        S.tidx[n] = ti;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(su32(&tslot)), "r"(256));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t taddr = tslot;
+    if (warp < 4) {
+        // zero both accumulation buffers (every MMA accumulates)
+        const uint32_t tl = taddr + ((uint32_t)(warp * 32) << 16);
+        for (int c0 = 0; c0 < 256; c0 += 16)
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};"
+                         :: "r"(tl + (uint32_t)c0), "r"(0u) : "memory");
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp < 4) {
+        // ---------------- A rows: strengths of the chunk's sources (or the leaf's locals) ----------------
+        auto fetch = [&](int i, cf* out) {
+            const NtChunk& ch = S.ch[i];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = tid + 128 * u, j = e >> 6, r = e & 63;
+                cf v = cfmk(0.f, 0.f);
+                if (r0 + r < nrhs) {
+                    if (ch.src >= 0) {
+                        if (j < ch.cnt) v = qs[(int64_t)(ch.src + j) * nrhs + r0 + r];
+                    } else {
+                        const int mm = 8 * ch.cnt + j;
+                        int c = 0;
+                        while (!(ch.mask >> c & 1)) ++c;
+                        if (mm < nc) v = loc[((int64_t)S.lbox[c] * nrhs + r0 + r) * nc + mm];
+                    }
+                }
+                out[u] = v;
+            }
+        };
+        // strengths two chunks ahead: pa = chunk i, pb = chunk i + 1
+        cf pa[4], pb[4], pn[4];
+        if (nch > 0) fetch(0, pa);
+        if (nch > 1) fetch(1, pb);
+        for (int i = 0; i < nch; ++i) {
+            const int stg = i % NT_STAGES;
+            bool good = !s_abort && mbar_wait(&empty[stg], (uint32_t)(((i / NT_STAGES) & 1) ^ 1));
+            good = __all_sync(0xffffffffu, good);
+            if (!good) { s_abort = 1; break; }
+            if (i + 2 < nch) fetch(i + 2, pn);
+            float* A = (float*)(smem + stg * NT_STAGE);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = tid + 128 * u;
+                put_a(A, e >> 6, e & 63, pa[u]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&afull[stg]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { pa[u] = pb[u]; pb[u] = pn[u]; }
+        }
+        // ---------------- drain: sum the two buffers, store y ----------------
+        bool good = !s_abort && mbar_wait(&done, 0u);
+        good = __all_sync(0xffffffffu, good);
+        if (!good) {
+            s_abort = 1;
+            if (lane == 0) atomicExch(err, 1);
+        } else if (nch > 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int row = tid;
+            const uint32_t tl = taddr + ((uint32_t)(warp * 32) << 16);
+            float* stg0 = (float*)smem;   // stage 0 is free now
+            for (int g0 = 0; g0 < N; g0 += 16) {
+                uint32_t w0[16], w1[16];
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                             : "=r"(w0[0]), "=r"(w0[1]), "=r"(w0[2]), "=r"(w0[3]), "=r"(w0[4]), "=r"(w0[5]), "=r"(w0[6]),
+                               "=r"(w0[7]), "=r"(w0[8]), "=r"(w0[9]), "=r"(w0[10]), "=r"(w0[11]), "=r"(w0[12]),
+                               "=r"(w0[13]), "=r"(w0[14]), "=r"(w0[15])
+                             : "r"(tl + (uint32_t)g0));
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                             : "=r"(w1[0]), "=r"(w1[1]), "=r"(w1[2]), "=r"(w1[3]), "=r"(w1[4]), "=r"(w1[5]), "=r"(w1[6]),
+                               "=r"(w1[7]), "=r"(w1[8]), "=r"(w1[9]), "=r"(w1[10]), "=r"(w1[11]), "=r"(w1[12]),
+                               "=r"(w1[13]), "=r"(w1[14]), "=r"(w1[15])
+                             : "r"(tl + (uint32_t)(128 + g0)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int u = 0; u < 16; ++u) stg0[u * 128 + row] = __uint_as_float(w0[u]) + __uint_as_float(w1[u]);
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+#pragma unroll
+                for (int qq = 0; qq < 8; ++qq) {
+                    const int e = tid + 128 * qq, u = e >> 6, rr = e & 63;
+                    const int32_t t = S.tidx[g0 + u];
+                    if (t >= 0 && r0 + rr < nrhs)
+                        ys[(int64_t)t * nrhs + r0 + rr] = cfmk(stg0[u * 128 + rr], stg0[u * 128 + 64 + rr]);
+                }
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+            }
+        }
+    } else if (warp == 4 && lane == 0) {
+        // ---------------- TMA: the chunk's pre-split B tile (L2 prefetch NT_PREF chunks ahead) ----------------
+        for (int i = 0; i < min(nch, NT_PREF); ++i)
+            bulk_prefetch_l2(tiles + S.ch[i].boff, (uint32_t)S.ch[i].rows * 128u);
+        for (int i = 0; i < nch; ++i) {
+            if (i + NT_PREF < nch)
+                bulk_prefetch_l2(tiles + S.ch[i + NT_PREF].boff, (uint32_t)S.ch[i + NT_PREF].rows * 128u);
+            const int stg = i % NT_STAGES;
+            if (s_abort || !mbar_wait(&empty[stg], (uint32_t)(((i / NT_STAGES) & 1) ^ 1))) { s_abort = 1; break; }
+            const NtChunk& ch = S.ch[i];
+            const uint32_t bytes = (uint32_t)ch.rows * 128u;
+            mbar_arrive_tx(&bfull[stg], bytes);
+            bulk_g2s(smem + stg * NT_STAGE + NT_A, tiles + ch.boff, bytes, &bfull[stg]);
+        }
+    } else if (warp == 5 && lane == 0) {
+        // ---------------- MMA issuer: one MMA set per run of adjacent target leaves ----------------
+        for (int i = 0; i < nch; ++i) {
+            const int stg = i % NT_STAGES;
+            const uint32_t ph = (uint32_t)((i / NT_STAGES) & 1);
+            if (s_abort || !mbar_wait(&afull[stg], ph) || !mbar_wait(&bfull[stg], ph)) { s_abort = 1; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const NtChunk& ch = S.ch[i];
+            const uint32_t sa = su32(smem + stg * NT_STAGE), sb = sa + NT_A;
+            const uint32_t lo_b = (uint32_t)ch.rows * 64u;
+            const uint32_t dbuf = taddr + (uint32_t)((i & 1) * 128);
+            int rowoff = 0;
+            for (int c = 0; c < 4;) {
+                if (!(ch.mask >> c & 1) || S.wid[c] == 0) { ++c; continue; }
+                int nn = 0;
+                const int c0 = c;
+                while (c < 4 && (ch.mask >> c & 1)) { nn += S.wid[c]; ++c; }
+                if (nn == 0) continue;
+                const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nn >> 3) << 17) |
+                                       ((128u >> 4) << 24);
+                const uint32_t dt = dbuf + (uint32_t)S.off[c0];
+                const uint32_t bro = (uint32_t)rowoff * 64u;
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+                    const uint64_t ah = sdesc(sa + ks * 256), al = sdesc(sa + 8192 + ks * 256);
+                    const uint64_t bh = sdesc(sb + bro + ks * 256), bl = sdesc(sb + lo_b + bro + ks * 256);
+                    mma_tf32(dt, ah, bh, idesc, 1u);
+                    mma_tf32(dt, ah, bl, idesc, 1u);
+                    mma_tf32(dt, al, bh, idesc, 1u);
+                }
+                rowoff += nn;
+            }
+            mma_commit(&empty[stg]);
+        }
+        mma_commit(&done);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(256));
+}
+
+}  // namespace
+
+// Plan time: blocks (parent boxes of level L - 1) whose padded targets fit
+// NT_MAXN, their chunks (source chunks, then L2P chunks) and tile store; the
+// leaves of the other blocks are left to the SIMT kernel.
+hfmm_status build_p2p_tc(hfmm_plan_s* P, cudaStream_t st) {
+    const int L = P->L;
+    if (L < 1) return HFMM_OK;
+    const auto& lb = P->h_leaf_begin;
+    const int m = 1 << L;
+    const int nc = P->lev[L].ncoef;
+    const int kcl = (nc + 7) / 8;
+    const int64_t npar = (int64_t)1 << (2 * (L - 1));
+    std::vector<int32_t> blocks, fallback;
+    std::vector<NtChunk> chunks;
+    int64_t boff = 0, rows = 0;
+    for (int64_t par = 0; par < npar; ++par) {
+        int cnt[4], wid[4], ncol = 0, ntgt = 0;
+        for (int c = 0; c < 4; ++c) {
+            cnt[c] = lb[4 * par + c + 1] - lb[4 * par + c];
+            wid[c] = (cnt[c] + 15) / 16 * 16;
+            ncol += wid[c];
+            ntgt += cnt[c];
+        }
+        if (ntgt == 0) continue;
+        if (ncol > NT_MAXN) {
+            for (int c = 0; c < 4; ++c)
+                if (cnt[c] > 0) fallback.push_back((int32_t)(4 * par + c));
+            continue;
+        }
+        const int px = (int)morton_x((uint32_t)par), py = (int)morton_y((uint32_t)par);
+        const int32_t c_begin = (int32_t)chunks.size();
+        for (int u = 0; u < 16; ++u) {
+            const int sx = 2 * px - 1 + (u & 3), sy = 2 * py - 1 + (u >> 2);
+            if (sx < 0 || sy < 0 || sx >= m || sy >= m) continue;
+            const uint32_t sb = morton((uint32_t)sx, (uint32_t)sy);
+            const int32_t slo = lb[sb], sn = lb[sb + 1] - slo;
+            if (sn == 0) continue;
+            int mask = 0, r = 0;
+            for (int c = 0; c < 4; ++c) {
+                const int dx = (u & 3) - 1 - (c & 1), dy = (u >> 2) - 1 - (c >> 1);
+                if (cnt[c] > 0 && dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) { mask |= 1 << c; r += wid[c]; }
+            }
+            if (mask == 0) continue;
+            for (int s0 = 0; s0 < sn; s0 += 8) {
+                chunks.push_back({slo + s0, std::min(8, sn - s0), mask, r, boff, (int32_t)par, u});
+                boff += (int64_t)r * 32;
+                rows += r;
+            }
+        }
+        const int32_t c_l2p = (int32_t)chunks.size();
+        for (int c = 0; c < 4; ++c) {
+            if (cnt[c] == 0) continue;
+            for (int kk = 0; kk < kcl; ++kk) {
+                chunks.push_back({-1, kk, 1 << c, wid[c], boff, (int32_t)par, 0});
+                boff += (int64_t)wid[c] * 32;
+                rows += wid[c];
+            }
+        }
+        if ((int)chunks.size() - c_begin > NT_MAXCH) {
+            // too many chunks for the kernel's shared record table: SIMT kernel
+            for (size_t i = c_begin; i < chunks.size(); ++i) { boff -= (int64_t)chunks[i].rows * 32; rows -= chunks[i].rows; }
+            chunks.resize(c_begin);
+            for (int c = 0; c < 4; ++c)
+                if (cnt[c] > 0) fallback.push_back((int32_t)(4 * par + c));
+            continue;
+        }
+        blocks.push_back((int32_t)par);
+        blocks.push_back(c_begin);
+        blocks.push_back(c_l2p);
+        blocks.push_back((int32_t)chunks.size());
+    }
+    P->nt_nblocks = (int64_t)blocks.size() / 4;
+    P->nt_nfallback = (int64_t)fallback.size();
+    HFMM_TRY(plan_alloc(P, (void**)&P->nt_blocks, sizeof(int32_t) * std::max<size_t>(blocks.size(), 4)));
+    HFMM_TRY(plan_alloc(P, (void**)&P->nt_fallback, sizeof(int32_t) * std::max<size_t>(fallback.size(), 1)));
+    HFMM_TRY(plan_alloc(P, (void**)&P->nt_chunks, sizeof(NtChunk) * std::max<size_t>(chunks.size(), 1)));
+    HFMM_TRY(plan_alloc(P, (void**)&P->nt_tiles, sizeof(float) * (size_t)std::max<int64_t>(boff, 32)));
+    P->table_bytes += sizeof(float) * (double)boff + sizeof(NtChunk) * (double)chunks.size();
+    if (!blocks.empty())
+        HFMM_CUDA_TRY(cudaMemcpy(P->nt_blocks, blocks.data(), sizeof(int32_t) * blocks.size(), cudaMemcpyHostToDevice));
+    if (!fallback.empty())
+        HFMM_CUDA_TRY(cudaMemcpy(P->nt_fallback, fallback.data(), sizeof(int32_t) * fallback.size(),
+                                 cudaMemcpyHostToDevice));
+    if (!chunks.empty()) {
+        HFMM_CUDA_TRY(cudaMemcpy(P->nt_chunks, chunks.data(), sizeof(NtChunk) * chunks.size(), cudaMemcpyHostToDevice));
+        HFMM_TRY(fill_near_tiles(P, (int64_t)chunks.size(), rows, st));
+    }
+    return HFMM_OK;
+}
+
+// Launch the tensor-core near field (near: P2P chunks, far: L2P chunks) over
+// the plan's blocks; it stores y of their targets.
+hfmm_status launch_p2p_tc(hfmm_plan_s* P, int nrhs, bool near, bool far, cudaStream_t st) {
+    if (P->nt_nblocks == 0) return HFMM_OK;
+    static bool attr_set = false;
+    if (!attr_set) {
+        HFMM_CUDA_TRY(cudaFuncSetAttribute(p2p_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NT_SMEM));
+        attr_set = true;
+    }
+    const LevelInfo& lv = P->lev[P->L];
+    dim3 grid((unsigned)P->nt_nblocks, (unsigned)((nrhs + 63) / 64));
+    p2p_tc_kernel<<<grid, NT_THREADS, NT_SMEM, st>>>(P->nt_blocks, P->nt_chunks, P->nt_tiles, P->leaf_begin, P->q32,
+                                                     nrhs, near ? 1 : 0, far ? 1 : 0, lv.loc32, lv.ncoef, P->y32,
+                                                     P->tc_err);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    return HFMM_OK;
+}

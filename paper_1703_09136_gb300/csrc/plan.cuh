@@ -73,6 +73,22 @@ struct LevelInfo {
     float* tc_pmma = nullptr;     // MMA-ready local expansions of the parent level
 };
 
+// Near field on tensor cores: one K chunk of a block (the four leaves of a
+// parent box at level L - 1).  A source chunk holds up to 8 consecutive sorted
+// points of one source leaf of the 4 x 4 neighbourhood; an L2P chunk holds
+// 8 local coefficients of one target leaf.  The pre-split B tile of the chunk
+// (rows = the padded targets of the adjacent leaves, in leaf order) starts at
+// float offset boff of the plan's tile store: hi rows x 16, then lo.
+struct NtChunk {
+    int32_t src;     // first source point (sorted index); -1: L2P chunk
+    int32_t cnt;     // sources in the chunk (1 .. 8); L2P: K chunk index
+    int32_t mask;    // target leaves the tile covers (bit c = child c)
+    int32_t rows;    // rows of the tile (sum of their padded widths)
+    int64_t boff;
+    int32_t par;     // parent box (level L - 1)
+    int32_t aux;     // source leaf code (sx + 1) + 4 (sy + 1); L2P: unused
+};
+
 struct hfmm_plan_s {
     int64_t n = 0;
     int L = 0;
@@ -110,6 +126,15 @@ struct hfmm_plan_s {
     cf* q32 = nullptr;              // [n][nrhs] (point-major)
     cf* y32 = nullptr;              // [n][nrhs]
     int32_t* iperm32 = nullptr;     // [n] sorted position of caller index j
+    // near field on tensor cores (p2p_tc.cu): blocks (parent box, first chunk,
+    // first L2P chunk, end), their chunks, the pre-split tile store, and the
+    // leaves of blocks too wide for the kernel (SIMT kernel)
+    int32_t* nt_blocks = nullptr;
+    int64_t nt_nblocks = 0;
+    NtChunk* nt_chunks = nullptr;
+    float* nt_tiles = nullptr;
+    int32_t* nt_fallback = nullptr;
+    int64_t nt_nfallback = 0;
     cf* d_vals32 = nullptr;
     float2* xl32 = nullptr;         // [n] point offsets from their own leaf centre (FP32)
     cf* basis32 = nullptr;          // [n][2 p_L + 1] scaled P2M basis of each sorted point
@@ -182,6 +207,10 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
                         cudaStream_t st);
 hfmm_status init_h0_table(cudaStream_t st);
 hfmm_status build_local_coords(hfmm_plan_s* P, cudaStream_t st);
+hfmm_status fill_near_tiles(hfmm_plan_s* P, int64_t nchunks, int64_t total_rows, cudaStream_t st);
+// p2p_tc.cu
+hfmm_status build_p2p_tc(hfmm_plan_s* P, cudaStream_t st);
+hfmm_status launch_p2p_tc(hfmm_plan_s* P, int nrhs, bool near, bool far, cudaStream_t st);
 // m2l_tc.cu
 hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status launch_m2l_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st);
