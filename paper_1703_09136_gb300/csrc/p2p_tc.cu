@@ -16,8 +16,8 @@
 // layout (fmm32.cu, near_tiles_kernel).  Per apply, warp 4 streams the tiles
 // with cp.async.bulk (prefetched into L2 a few chunks ahead); warps 0-3 build the A rows of each chunk from the
 // strengths (or the leaf's local coefficients) in shared memory; warp 5 issues
-// one 3xTF32 MMA set (hi*hi + hi*lo + lo*hi) per run of adjacent target leaves
-// into one of two TMEM buffers used in turn; warps 0-3 finally sum the buffers
+// one 3xTF32 MMA set (hi*hi + hi*lo + lo*hi) per run of adjacent target leaves,
+// alternating between two TMEM buffers; warps 0-3 finally sum the buffers
 // in FP32 and store y (point-major, [n][nrhs]; the kernel is the first writer
 // of its targets).  Every mbarrier wait is bounded.
 #include <algorithm>
@@ -239,27 +239,24 @@ __global__ void __launch_bounds__(NT_THREADS, 2) p2p_tc_kernel(
             const NtChunk& ch = S.ch[i];
             const uint32_t sa = su32(smem + stg * NT_STAGE), sb = sa + NT_A;
             const uint32_t lo_b = (uint32_t)ch.rows * 64u;
-            const uint32_t dbuf = taddr + (uint32_t)((i & 1) * 128);
-            int rowoff = 0;
-            for (int c = 0; c < 4;) {
-                if (!(ch.mask >> c & 1) || S.wid[c] == 0) { ++c; continue; }
-                int nn = 0;
-                const int c0 = c;
-                while (c < 4 && (ch.mask >> c & 1)) { nn += S.wid[c]; ++c; }
-                if (nn == 0) continue;
+            // runs alternate between the two TMEM buffers: two independent accumulation chains
+            int which = 0;
+            for (int q = 0; q < ch.nrun; ++q) {
+                const int rw = ch.run[q];
+                const int nn = rw & 0xff, col = (rw >> 8) & 0xff, rowoff = rw >> 16;
                 const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nn >> 3) << 17) |
                                        ((128u >> 4) << 24);
-                const uint32_t dt = dbuf + (uint32_t)S.off[c0];
                 const uint32_t bro = (uint32_t)rowoff * 64u;
 #pragma unroll
                 for (int ks = 0; ks < 2; ++ks) {
                     const uint64_t ah = sdesc(sa + ks * 256), al = sdesc(sa + 8192 + ks * 256);
                     const uint64_t bh = sdesc(sb + bro + ks * 256), bl = sdesc(sb + lo_b + bro + ks * 256);
-                    mma_tf32(dt, ah, bh, idesc, 1u);
-                    mma_tf32(dt, ah, bl, idesc, 1u);
-                    mma_tf32(dt, al, bh, idesc, 1u);
+                    const uint32_t d0 = taddr + (uint32_t)(which * 128 + col), d1 = taddr + (uint32_t)((which ^ 1) * 128 + col);
+                    mma_tf32(d0, ah, bh, idesc, 1u);
+                    mma_tf32(d1, ah, bl, idesc, 1u);
+                    mma_tf32(d0, al, bh, idesc, 1u);
+                    which ^= 1;
                 }
-                rowoff += nn;
             }
             mma_commit(&empty[stg]);
         }
@@ -314,8 +311,19 @@ hfmm_status build_p2p_tc(hfmm_plan_s* P, cudaStream_t st) {
                 if (cnt[c] > 0 && dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) { mask |= 1 << c; r += wid[c]; }
             }
             if (mask == 0) continue;
+            int nrun = 0, run[2] = {0, 0}, rowoff = 0, col[5];
+            col[0] = 0;
+            for (int c = 0; c < 4; ++c) col[c + 1] = col[c] + wid[c];
+            for (int c = 0; c < 4;) {
+                if (!(mask >> c & 1)) { ++c; continue; }
+                const int c0 = c;
+                int w = 0;
+                while (c < 4 && (mask >> c & 1)) w += wid[c++];
+                run[nrun++] = w | (col[c0] << 8) | (rowoff << 16);
+                rowoff += w;
+            }
             for (int s0 = 0; s0 < sn; s0 += 8) {
-                chunks.push_back({slo + s0, std::min(8, sn - s0), mask, r, boff, (int32_t)par, u});
+                chunks.push_back({slo + s0, std::min(8, sn - s0), mask, r, boff, (int32_t)par, u, nrun, {run[0], run[1]}, 0});
                 boff += (int64_t)r * 32;
                 rows += r;
             }
@@ -323,8 +331,10 @@ hfmm_status build_p2p_tc(hfmm_plan_s* P, cudaStream_t st) {
         const int32_t c_l2p = (int32_t)chunks.size();
         for (int c = 0; c < 4; ++c) {
             if (cnt[c] == 0) continue;
+            int col = 0;
+            for (int cc = 0; cc < c; ++cc) col += wid[cc];
             for (int kk = 0; kk < kcl; ++kk) {
-                chunks.push_back({-1, kk, 1 << c, wid[c], boff, (int32_t)par, 0});
+                chunks.push_back({-1, kk, 1 << c, wid[c], boff, (int32_t)par, 0, 1, {wid[c] | (col << 8), 0}, 0});
                 boff += (int64_t)wid[c] * 32;
                 rows += wid[c];
             }

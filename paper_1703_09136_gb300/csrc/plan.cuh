@@ -87,6 +87,9 @@ struct NtChunk {
     int64_t boff;
     int32_t par;     // parent box (level L - 1)
     int32_t aux;     // source leaf code (sx + 1) + 4 (sy + 1); L2P: unused
+    int32_t nrun;    // runs of consecutive covered leaves (1 or 2)
+    int32_t run[2];  // each: width | first column << 8 | first tile row << 16
+    int32_t pad;
 };
 
 struct hfmm_plan_s {
