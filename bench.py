@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-fp64-check", action="store_true",
                     help="skip the FP64 reference apply (accuracy and one-RHS FP64 time)")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=0)
     ap.add_argument("--box", type=float, nargs=4, default=None, metavar=("X0", "X1", "Y0", "Y1"),
@@ -251,6 +251,7 @@ def run_ours(args):
     # end to end through the C ABI with pinned host buffers
     qh = torch.from_numpy(q_h).to(cdt).pin_memory()
     yh = torch.empty_like(qh).pin_memory()
+    plan._run(plan_lib_apply(), qh, yh, None)        # untimed: first touch of the pinned pages
     e2e_t = []
     for _ in range(args.e2e_steps):
         t1 = time.perf_counter()

@@ -172,7 +172,11 @@ hfmm_status hfmm_plan_create(hfmm_plan_t* out, int64_t n, const double* xy,
 /*
  * y = A q for nrhs right-hand sides (1 <= nrhs <= max_rhs).  q, y: [nrhs][n]
  * complex, complex128 for HFMM_FP64 plans, complex64 for HFMM_MIXED plans,
- * in the caller's point order.  q and y must not overlap.
+ * in the caller's point order.  q and y must not overlap.  Device buffers:
+ * stream-ordered, no host synchronisation.  Page-locked (registered) host
+ * buffers are read and written in place by the permutation kernels; other
+ * host buffers are staged through plan-owned device buffers.  With any host
+ * buffer the call synchronises `stream` before returning.
  */
 hfmm_status hfmm_apply(hfmm_plan_t plan, int32_t nrhs, const void* q, void* y, void* stream);
 

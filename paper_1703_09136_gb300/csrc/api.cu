@@ -54,6 +54,18 @@ static bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device-accessible address of page-locked (registered) host memory, or
+// nullptr for other pointers.  Such buffers are read and written in place by
+// the gather / scatter kernels (over NVLink-C2C) instead of being staged.
+static void* mapped_host_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 static int choose_levels(int64_t n, int leaf) {
     int L = 2;
     while (n > (int64_t)leaf * ((int64_t)1 << (2 * L)) && L < 15) ++L;
@@ -322,14 +334,18 @@ static hfmm_status apply_common(hfmm_plan_t P, int32_t nrhs, const void* q, void
     const bool mixed = P->precision == HFMM_MIXED;
     const size_t bytes = (mixed ? sizeof(cf) : sizeof(cd)) * (size_t)P->n * nrhs;
     const bool qd = is_device_ptr(q), yd = is_device_ptr(y);
-    const cd* dq = (const cd*)q;
-    cd* dy = (cd*)y;
-    if (!qd) {
+    // page-locked host buffers are used in place; other host buffers are staged
+    void* qm = qd ? nullptr : mapped_host_ptr(q);
+    void* ym = yd ? nullptr : mapped_host_ptr(y);
+    const cd* dq = qd ? (const cd*)q : (const cd*)qm;
+    cd* dy = yd ? (cd*)y : (cd*)ym;
+    if (!dq) {
         if (!P->io_q) HFMM_TRY(plan_alloc(P, (void**)&P->io_q, sizeof(cd) * (size_t)P->n * P->max_rhs));
         HFMM_CUDA_TRY(cudaMemcpyAsync(P->io_q, q, bytes, cudaMemcpyHostToDevice, st));
         dq = P->io_q;
     }
-    if (!yd) {
+    const bool stage_y = !dy;
+    if (stage_y) {
         if (!P->io_y) HFMM_TRY(plan_alloc(P, (void**)&P->io_y, sizeof(cd) * (size_t)P->n * P->max_rhs));
         dy = P->io_y;
     }
@@ -338,7 +354,7 @@ static hfmm_status apply_common(hfmm_plan_t P, int32_t nrhs, const void* q, void
     } else {
         HFMM_TRY(apply_fp64(P, nrhs, dq, dy, parts, adjoint, st));
     }
-    if (!yd) {
+    if (stage_y) {
         HFMM_CUDA_TRY(cudaMemcpyAsync(y, P->io_y, bytes, cudaMemcpyDeviceToHost, st));
     }
     if (!qd || !yd) HFMM_CUDA_TRY(cudaStreamSynchronize(st));

@@ -326,6 +326,26 @@ def test_autotune_keeps_fastest_depth_and_same_result():
     fixed.close()
 
 
+def test_page_locked_host_buffers_match_device_buffers():
+    """Page-locked host q / y (used in place by the permutation kernels) give
+    the device-buffer result, FP64 and mixed; pageable host buffers too."""
+    from paper_1703_09136_gb300 import MIXED
+    med = W.WORKLOADS[2].medium
+    xy = W.points(2, 5000)
+    q = W.strengths(2, 5000, 3)
+    for prec, cdt in ((0, torch.complex128), (MIXED, torch.complex64)):
+        plan = Plan(xy, med, tol=1e-6, max_rhs=3, precision=prec)
+        qd = torch.from_numpy(q).to(cdt).cuda()
+        yd = plan.apply(qd).cpu()
+        qh = torch.from_numpy(q).to(cdt).pin_memory()
+        yh = torch.empty_like(qh).pin_memory()
+        plan.apply(qh, out=yh)
+        assert torch.equal(yh, yd)
+        yp = plan.apply(torch.from_numpy(q).to(cdt))
+        assert torch.equal(yp, yd)
+        plan.close()
+
+
 # --- gradients ---------------------------------------------------------------------
 
 def test_position_gradient_matches_oracle_direct_sum_gradient():
