@@ -347,10 +347,110 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_batch(args):
+    """Config 5: uneven independent instances applied together through the
+    batch API (one captured CUDA graph, a branch per instance)."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_1703_09136_gb300 import Batch, FP64, MIXED
+    from paper_1703_09136_gb300 import build as _build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        _build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    cfg = 5
+    w = W.WORKLOADS[cfg]
+    sizes = [int(v) for v in W.batch_sizes(cfg)]
+    nrhs = args.nrhs or w.nrhs
+    prec = FP64 if args.precision == "fp64" else MIXED
+    cdt = torch.complex128 if prec == FP64 else torch.complex64
+    dev = torch.device("cuda", local)
+    xys = [W.points(cfg, n, salt=i) for i, n in enumerate(sizes)]
+    qs_h = [torch.from_numpy(W.strengths(cfg, n, nrhs, salt=i)).to(cdt) for i, n in enumerate(sizes)]
+    qs = [q.to(dev) for q in qs_h]
+    ys = [torch.empty_like(q) for q in qs]
+    t0 = time.perf_counter()
+    batch = Batch(xys, w.medium, tol=w.tol, leaf_size=w.leaf, precision=prec, max_rhs=nrhs)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        batch.apply(qs, ys)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(args.steps):
+        batch.apply(qs, ys)
+    e1.record(st)
+    torch.cuda.synchronize()
+    total_ms = e0.elapsed_time(e1)
+    ck = clocks.stop()
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    ntot = sum(sizes)
+    value = world * ntot * nrhs / (ms_per_step * 1e-3) / 1e6
+    # end to end: pinned host strengths in, results out, around every batch apply
+    qh = [q.pin_memory() for q in qs_h]
+    yh = [torch.empty_like(q).pin_memory() for q in qh]
+    e2e_t = []
+    for it in range(1 + max(1, args.e2e_steps)):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for q, qd in zip(qh, qs):
+            qd.copy_(q, non_blocking=True)
+        batch.apply(qs, ys)
+        for y, yd in zip(yh, ys):
+            y.copy_(yd, non_blocking=True)
+        torch.cuda.synchronize()
+        if it > 0:
+            e2e_t.append(time.perf_counter() - t1)
+    e2e_s = statistics.median(e2e_t)
+    cbytes = 16 if prec == FP64 else 8
+    out = {
+        "metric": "batched H-FMM matvec throughput (targets x RHS per second), 32 uneven impedance instances",
+        "value": value, "unit": "Mtargets/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == FP64 else "f32", "data": "synthetic",
+        "config": {"workload": w.name, "instances": len(sizes), "total_n": ntot, "n_min": min(sizes),
+                   "n_max": max(sizes), "nrhs": nrhs, "medium": "impedance k=40 alpha=20", "tol": w.tol,
+                   "plan_s": plan_s, "l2": "inputs and expansions larger than L2",
+                   "parallelism": f"replicas{world}"},
+        "gpu_launches": None,
+        "e2e": {"value": world * ntot * nrhs / e2e_s / 1e6, "unit": "Mtargets/s",
+                "h2d_bytes_per_step": cbytes * ntot * nrhs, "d2h_bytes_per_step": cbytes * ntot * nrhs},
+        "roofline": None, "clocks": ck, "cpu_baseline": None,
+    }
+    batch.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == 5:
+        run_batch(args)
     else:
         run_ours(args)
 
