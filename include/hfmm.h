@@ -143,6 +143,8 @@ typedef struct {
     int32_t tensor_levels;      /* levels whose downward pass runs on tcgen05 tensor cores */
     int32_t tune_levels[3];     /* HFMM_FLAG_AUTOTUNE: leaf levels tried (0 = not tried) */
     double tune_ms[3];          /* and the apply time measured for each */
+    int64_t near_tc_blocks;     /* HFMM_MIXED: four-leaf blocks of the tensor-core near field */
+    int64_t near_simt_leaves;   /*             leaves of wider blocks, on the SIMT kernel */
 } hfmm_plan_info;
 
 /* Bits of `parts` in hfmm_apply_parts (sum of the selected terms). */

@@ -452,6 +452,8 @@ hfmm_status hfmm_plan_get_info(hfmm_plan_t P, hfmm_plan_info* info) {
         info->tune_levels[c] = P->tune_levels[c];
         info->tune_ms[c] = P->tune_ms[c];
     }
+    info->near_tc_blocks = P->nt_nblocks;
+    info->near_simt_leaves = P->nt_nfallback;
     return HFMM_OK;
 }
 

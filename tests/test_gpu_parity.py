@@ -326,6 +326,27 @@ def test_autotune_keeps_fastest_depth_and_same_result():
     fixed.close()
 
 
+def test_near_field_tensor_blocks_and_simt_fallback():
+    """Clustered points: the tensor-core near field (precomputed tiles) and
+    the SIMT kernel for blocks wider than 128 padded targets both run, and
+    every term matches the FP64 path."""
+    from paper_1703_09136_gb300 import MIXED
+    med = W.WORKLOADS[2].medium
+    xy = W.points(2, 6400)
+    q = W.strengths(2, 6400, 2)
+    tc = Plan(xy, med, tol=1e-6, leaf_size=24, max_rhs=2, precision=MIXED)
+    f64 = Plan(xy, med, tol=1e-6, leaf_size=24, max_rhs=2)
+    inf = tc.info
+    assert inf["near_tc_blocks"] > 0 and inf["near_simt_leaves"] > 0, inf
+    full = f64.apply(torch.from_numpy(q).cuda()).cpu().numpy()
+    for part in (1, 2, 4, 8, 15):
+        a = tc.apply(torch.from_numpy(q.astype(np.complex64)).cuda(), parts=part).cpu().numpy()
+        b = f64.apply(torch.from_numpy(q).cuda(), parts=part).cpu().numpy()
+        assert np.linalg.norm(a - b) / np.linalg.norm(full) < MIXED_TOL, part
+    tc.close()
+    f64.close()
+
+
 def test_page_locked_host_buffers_match_device_buffers():
     """Page-locked host q / y (used in place by the permutation kernels) give
     the device-buffer result, FP64 and mixed; pageable host buffers too."""
