@@ -204,9 +204,12 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t plan, int32_t nrhs, const void* v, vo
  * ((d/dx +- i d/dy) J_p e^{ip theta} = -+k J_{p+-1} e^{i(p+-1) theta}), of the
  * free-space kernel ((i/4)(-k H1(kr)) (x - x_j)/r) and of the Sommerfeld
  * integrand (factors i lambda and -s1) for directly summed reaction pairs.
- * Strength gradients are hfmm_apply_adjoint(g).  q, g: complex128; gxy: [n][2]
- * doubles; host or device pointers.  HFMM_FP64 plans only (UNSUPPORTED for
- * HFMM_MIXED).
+ * Strength gradients are hfmm_apply_adjoint(g).  q, g: the plan's complex type
+ * (complex128, or complex64 for HFMM_MIXED); gxy: [n][2] doubles; host or
+ * device pointers.  A mixed plan widens q and g to complex128 and runs the FP64
+ * tree pass with its FP64 translation tables; its first call allocates the FP64
+ * expansions (2 x boxes x max_rhs x (2p+1) complex128 per level) and three
+ * n x max_rhs complex128 buffers, held until hfmm_plan_destroy.
  */
 hfmm_status hfmm_apply_grad(hfmm_plan_t plan, int32_t nrhs, const void* q, const void* g, double* gxy,
                             void* stream);

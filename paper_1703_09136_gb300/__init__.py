@@ -188,14 +188,18 @@ class Plan:
         g = dL/dRe(y) + i dL/dIm(y) (hfmm_apply_grad)."""
         torch = _torch()
         is_t = torch is not None and isinstance(q, torch.Tensor)
+        want = self._complex_dtype()
         if is_t:
+            tdt = torch.complex128 if want == np.complex128 else torch.complex64
+            if q.dtype != tdt:
+                raise ValueError(f"q must be {tdt}")
             q = q.contiguous()
             g = g.contiguous().to(q.dtype)
             if out is None:
                 out = torch.empty((self.n, 2), dtype=torch.float64, device=q.device)
         else:
-            q = np.ascontiguousarray(q, dtype=np.complex128)
-            g = np.ascontiguousarray(g, dtype=np.complex128)
+            q = np.ascontiguousarray(q, dtype=want)
+            g = np.ascontiguousarray(g, dtype=want)
             if out is None:
                 out = np.empty((self.n, 2), dtype=np.float64)
         nrhs = 1 if q.ndim == 1 else int(np.prod(q.shape[:-1]))
@@ -315,8 +319,9 @@ def matvec(xy, q, medium, **plan_options):
 
     Builds a plan for the positions, applies it, and in backward returns
     A^H g for q (hfmm_apply_adjoint) and the position gradient of
-    hfmm_apply_grad for xy.  FP64 plans (complex128 q) support both
-    gradients; plan_options are passed to Plan (tol, leaf_size, ...)."""
+    hfmm_apply_grad for xy.  Both precisions support both gradients (the
+    position gradient of a mixed plan is computed in FP64 from its complex64
+    q and g); plan_options are passed to Plan (tol, leaf_size, ...)."""
     return _MatvecFn.apply(xy, q, medium, plan_options)
 
 

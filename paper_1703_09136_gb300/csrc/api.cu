@@ -378,20 +378,38 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t plan, int32_t nrhs, const void* v, vo
     return apply_common(plan, nrhs, v, w, HFMM_PART_ALL, true, stream);
 }
 
+// Widen complex64 to complex128 (gradients of mixed-precision plans run on the FP64 path).
+__global__ void widen_kernel(const cf* __restrict__ in, cd* __restrict__ out, int64_t count) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = cmk((double)in[i].x, (double)in[i].y);
+}
+
+// FP64 expansion and strength buffers of a mixed-precision plan, allocated on
+// its first gradient call (the FP64 tables are part of every plan).
+static hfmm_status ensure_fp64_buffers(hfmm_plan_s* P) {
+    for (int l = P->lmin; l <= P->L; ++l) {
+        LevelInfo& lv = P->lev[l];
+        const size_t bytes = sizeof(cd) * (size_t)lv.nbox * P->max_rhs * lv.ncoef;
+        if (!lv.mult) HFMM_TRY(plan_alloc(P, (void**)&lv.mult, bytes));
+        if (!lv.loc) HFMM_TRY(plan_alloc(P, (void**)&lv.loc, bytes));
+    }
+    if (!P->q_sorted) HFMM_TRY(plan_alloc(P, (void**)&P->q_sorted, sizeof(cd) * (size_t)P->n * P->max_rhs));
+    if (!P->grad_q) HFMM_TRY(plan_alloc(P, (void**)&P->grad_q, sizeof(cd) * (size_t)P->n * P->max_rhs));
+    if (!P->grad_g) HFMM_TRY(plan_alloc(P, (void**)&P->grad_g, sizeof(cd) * (size_t)P->n * P->max_rhs));
+    return HFMM_OK;
+}
+
 hfmm_status hfmm_apply_grad(hfmm_plan_t P, int32_t nrhs, const void* q, const void* g, double* gxy,
                             void* stream) {
     if (!P) { hfmm_set_error("plan is NULL"); return HFMM_ERR_INVALID_ARG; }
-    if (P->precision != HFMM_FP64) {
-        hfmm_set_error("hfmm_apply_grad needs an HFMM_FP64 plan");
-        return HFMM_ERR_UNSUPPORTED;
-    }
     if (nrhs < 1 || nrhs > P->max_rhs) {
         hfmm_set_error("nrhs must be in [1, max_rhs=%d] (got %d)", P->max_rhs, nrhs);
         return HFMM_ERR_INVALID_ARG;
     }
     if (!q || !g || !gxy) { hfmm_set_error("q, g or gxy is NULL"); return HFMM_ERR_INVALID_ARG; }
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t bytes = sizeof(cd) * (size_t)P->n * nrhs;
+    const bool mixed = P->precision == HFMM_MIXED;
+    const size_t bytes = (mixed ? sizeof(cf) : sizeof(cd)) * (size_t)P->n * nrhs;
     const bool qd = is_device_ptr(q), gd = is_device_ptr(g), od = is_device_ptr(gxy);
     const cd* dq = (const cd*)q;
     const cd* dg = (const cd*)g;
@@ -405,6 +423,17 @@ hfmm_status hfmm_apply_grad(hfmm_plan_t P, int32_t nrhs, const void* q, const vo
         if (!P->io_y) HFMM_TRY(plan_alloc(P, (void**)&P->io_y, sizeof(cd) * (size_t)P->n * P->max_rhs));
         HFMM_CUDA_TRY(cudaMemcpyAsync(P->io_y, g, bytes, cudaMemcpyHostToDevice, st));
         dg = P->io_y;
+    }
+    if (mixed) {
+        // complex64 inputs, gradient on the FP64 path
+        HFMM_TRY(ensure_fp64_buffers(P));
+        const int64_t count = P->n * (int64_t)nrhs;
+        const unsigned blocks = (unsigned)std::min<int64_t>((count + 255) / 256, 8 * 152);
+        widen_kernel<<<blocks, 256, 0, st>>>((const cf*)dq, P->grad_q, count);
+        widen_kernel<<<blocks, 256, 0, st>>>((const cf*)dg, P->grad_g, count);
+        HFMM_CUDA_TRY(cudaGetLastError());
+        dq = P->grad_q;
+        dg = P->grad_g;
     }
     if (!od) {
         if (!P->io_gxy) HFMM_TRY(plan_alloc(P, (void**)&P->io_gxy, sizeof(double) * 2 * (size_t)P->n));

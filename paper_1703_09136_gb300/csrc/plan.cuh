@@ -146,6 +146,8 @@ struct hfmm_plan_s {
     // position gradients (FP64): field-gradient buffers and d/dX, d/dY of the
     // directly summed reaction blocks
     cd* grad_buf = nullptr;         // [5][max_rhs][n]
+    cd* grad_q = nullptr;           // mixed plans: widened strengths / loss gradient
+    cd* grad_g = nullptr;
     cd* d_gvals = nullptr;          // [2][nd_vals]
     void* dj_jobs = nullptr;        // direct-block quadrature jobs and segments (tables.cu)
     void* dj_segs = nullptr;

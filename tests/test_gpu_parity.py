@@ -383,6 +383,29 @@ def test_position_gradient_matches_oracle_direct_sum_gradient():
     plan.close()
 
 
+def test_mixed_plan_position_gradient_runs_the_fp64_tree_pass():
+    """A mixed plan's position gradient widens its complex64 q and g and runs
+    the FP64 pass: it equals an FP64 plan's gradient of the same rounded
+    inputs (same tree, same orders) and the oracle's direct-sum gradient."""
+    from paper_1703_09136_gb300 import MIXED
+    for wl in (1, 5):
+        med = W.WORKLOADS[wl].medium
+        n = 700
+        xy = W.points(wl, n)
+        q32 = W.strengths(wl, n, 3, salt=4).astype(np.complex64)
+        g32 = W.strengths(wl, n, 3, salt=5).astype(np.complex64)
+        p32 = Plan(xy, med, tol=1e-6, leaf_size=24, max_rhs=3, precision=MIXED)
+        p64 = Plan(xy, med, tol=1e-6, leaf_size=24, max_rhs=3)
+        got = p32.grad(q32, g32)
+        ref = p64.grad(q32.astype(np.complex128), g32.astype(np.complex128))
+        assert np.linalg.norm(got - ref) < 1e-12 * np.linalg.norm(ref), wl
+        want = direct.position_grad(med, xy, q32.astype(np.complex128), g32.astype(np.complex128))
+        assert np.linalg.norm(got - want) < 1e-4 * np.linalg.norm(want), wl
+        gt = p32.grad(torch.from_numpy(q32).cuda(), torch.from_numpy(g32).cuda())
+        assert torch.equal(gt.cpu(), torch.from_numpy(got)), wl
+        p32.close(); p64.close()
+
+
 def test_autograd_gradients_match_finite_differences():
     """torch.autograd through the C ABI (adjoint for strengths, field
     gradients for positions) against central differences, h = 1e-6."""
