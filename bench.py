@@ -237,11 +237,12 @@ def run_ours(args):
     if prec == FP64:
         peak, src = FP64_PEAK_TFLOPS, "nominal GB300 FP64 rate (MEASURED_PEAKS.json has no FP64 figure)"
     elif dom in ("m2m", "down") and info["tensor_levels"] > 0:
-        # FP32 terms as three TF32 tensor-core products (3xTF32): the measured
-        # bf16 burst peak x the nominal TF32 / BF16 dense ratio (1.1 / 2.25) / 3
+        # FP32-accurate terms as three f16 tensor-core products (hi*hi + hi*lo +
+        # lo*hi, kind::f16 with FP32 accumulation): the measured bf16 burst
+        # peak (f16 runs at the bf16 rate) / 3
         bf16, how = _measured_bf16()
-        peak = bf16 * (1.1 / 2.25) / 3.0
-        src = f"derived 3xTF32 peak: {how} bf16 {bf16:.1f} TFLOP/s x (1.1 / 2.25) / 3"
+        peak = bf16 / 3.0
+        src = f"derived 3xF16 peak: {how} bf16 {bf16:.1f} TFLOP/s (= f16 rate) / 3"
         bound = "tensor"
     else:
         peak, src = FP32_PEAK_TFLOPS, "derived FP32 SIMT peak: 152 SMs x 128 lanes x 2 x 2.07 GHz"

@@ -14,6 +14,7 @@
 
 #include "bessel.cuh"
 #include "plan.cuh"
+#include "tcgen05.cuh"
 
 namespace {
 
@@ -484,19 +485,17 @@ __device__ __forceinline__ void p2m_pass(PcShared& S, const cf* qs, const cf* ba
     }
 }
 
-__device__ __forceinline__ uint32_t tf32_rna32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-// Writes mult[b] and, when amma is given, its MMA-ready copy (TF32 hi / lo,
-// 64-row core-matrix blocks of kc K chunks, Re then Im, zero padding) for the
-// tensor-core M2M and M2L of the leaf level.
+// Writes mult[b] and, when amma is given, its MMA-ready copy for the
+// tensor-core M2M and M2L of the leaf level: f16 hi / lo, 4 KB blocks of 64
+// rows x 16 K (parts interleaved per 8-row group; Re then Im, zero padding)
+// per K chunk, every (row, column block
+// of sblk chunks) scaled by the power of two 2^e that puts its largest entry
+// in [2^14, 2^15), with 2^-e stored in asc[((b * nrc + rc) * nsb + block) * 64 + row].
 __global__ void __launch_bounds__(PC_THREADS) p2m32c_kernel(const int32_t* lb, const cf* qs, const cf* basis,
-                                                            int64_t n, int nrhs, int nc, cf* mult, float* amma,
-                                                            int kc, int nrc) {
+                                                            int64_t n, int nrhs, int nc, cf* mult, __half* amma,
+                                                            float* asc, int kc, int nrc, int nsb, int sblk) {
     __shared__ PcShared S;
+    __shared__ int s_e[16][PC_RHS];   // [column block][row]: consecutive rows in consecutive banks
     const int64_t b = blockIdx.x;
     const int32_t lo = lb[b], hi = lb[b + 1];
     cf* out = mult + (int64_t)b * nrhs * nc;
@@ -511,25 +510,53 @@ __global__ void __launch_bounds__(PC_THREADS) p2m32c_kernel(const int32_t* lb, c
         if (amma) {
             __syncthreads();   // this block's rows of mult are written
             const int rc = r0 / PC_RHS;
-            // warp = 8 rows x 4 consecutive k of one core matrix: 32 contiguous floats
-            const int nq = kc * 4;
-            for (int e = threadIdx.x; e < 8 * nq * 32; e += PC_THREADS) {
-                const int lane = e & 31, gq = e >> 5;
-                const int g = gq & 7, kq = gq >> 3;
-                const int r = g * 8 + (lane >> 2), k = kq * 4 + (lane & 3);
-                float v = 0.0f;
-                if (r0 + r < nrhs && k < 2 * nc) {
-                    const cf z = out[(int64_t)(r0 + r) * nc + (k < nc ? k : k - nc)];
-                    v = k < nc ? z.x : z.y;
+            // the 16 real values of K chunk c of row r (Re a_0 .. a_{nc-1}, Im ..., zero padding)
+            auto load16 = [&](int r, int c, float (&v)[16]) {
+                const bool live = r0 + r < nrhs;
+                const float* row = (const float*)(out + (int64_t)(r0 + r) * nc);
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int k = c * 16 + u;
+                    v[u] = !live || k >= 2 * nc ? 0.0f : (k < nc ? row[2 * k] : row[2 * (k - nc) + 1]);
                 }
-                const float vh = __uint_as_float(tf32_rna32(v));
-                const float vl = __uint_as_float(tf32_rna32(v - vh));
-                const int c = k >> 4, kk = k & 15;
-                float* d = amma + (((b * nrc + rc) * kc + c) * 2) * 1024 + ((r >> 3) * 4 + (kk >> 2)) * 32 +
-                           (r & 7) * 4 + (kk & 3);
-                d[0] = vh;
-                d[1024] = vl;
+            };
+            // largest |entry| of every (row, column block), by integer max of the float bits
+            for (int e = threadIdx.x; e < PC_RHS * 16; e += PC_THREADS) s_e[e >> 6][e & 63] = 0;
+            __syncthreads();
+            for (int e = threadIdx.x; e < PC_RHS * kc; e += PC_THREADS) {
+                const int r = e & (PC_RHS - 1), c = e >> 6;
+                float v[16];
+                load16(r, c, v);
+                float m = 0.0f;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) m = fmaxf(m, fabsf(v[u]));
+                if (m > 0.0f) atomicMax(&s_e[c / sblk][r], __float_as_int(m));
             }
+            __syncthreads();
+            for (int e = threadIdx.x; e < PC_RHS * nsb; e += PC_THREADS) {
+                const int r = e & (PC_RHS - 1), blk = e >> 6;
+                const int ex = tc::f16_exp(__int_as_float(s_e[blk][r]));
+                s_e[blk][r] = ex;
+                asc[(((int64_t)b * nrc + rc) * nsb + blk) * 64 + r] = tc::pow2f(-ex);
+            }
+            __syncthreads();
+            // scaled hi / lo of the chunk: two 16-byte core rows per part
+            for (int e = threadIdx.x; e < PC_RHS * kc; e += PC_THREADS) {
+                const int r = e & (PC_RHS - 1), c = e >> 6;
+                float v[16];
+                load16(r, c, v);
+                const float s = tc::pow2f(s_e[c / sblk][r]);
+                uint16_t* d = (uint16_t*)amma + ((b * nrc + rc) * kc + c) * 2048 + (r >> 3) * 256 + (r & 7) * 8;
+#pragma unroll
+                for (int hf = 0; hf < 2; ++hf) {
+                    uint16_t h[8], l[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) tc::split_f16(v[hf * 8 + u] * s, h[u], l[u]);
+                    *(uint4*)(d + hf * 64) = tc::pack8(h);
+                    *(uint4*)(d + hf * 64 + 128) = tc::pack8(l);
+                }
+            }
+            __syncthreads();   // s_e is reused by the next RHS block
         }
     }
 }
@@ -743,9 +770,9 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
             LevelInfo& lv = P->lev[L];
             tm.begin(HFMM_STAGE_P2M);
             const int nrc = (P->max_rhs + 63) / 64;
-            p2m32c_kernel<<<(unsigned)lv.nbox, PC_THREADS, 0, st>>>(P->leaf_begin, P->q32, P->basis32, n, nrhs,
-                                                                     lv.ncoef, lv.mult32,
-                                                                     P->tc_on ? lv.tc_amma : nullptr, lv.tc_kc, nrc);
+            p2m32c_kernel<<<(unsigned)lv.nbox, PC_THREADS, 0, st>>>(
+                P->leaf_begin, P->q32, P->basis32, n, nrhs, lv.ncoef, lv.mult32, P->tc_on ? lv.tc_amma : nullptr,
+                lv.tc_asc, lv.tc_kc, nrc, lv.tc_nb, lv.tc_nbw / 16);
             ++P->launches;
             HFMM_CUDA_TRY(cudaGetLastError());
             tm.end(HFMM_STAGE_P2M);

@@ -12,22 +12,33 @@
 //     D[row][n] += sum_k A[row][k] B_s[n][k],
 // rows = (target, r) (2 x 64 = M 128), k = (Re a_m | Im a_m) (K = 2 nc_in,
 // padded to 16), n = (Re b_p | Im b_p) (N = 2 nc padded into column blocks
-// of at most 128), with B = [[Re M, -Im M], [Im M, Re M]] blocks.  FP32
-// accuracy comes from three TF32 products per term (hi*hi + hi*lo + lo*hi,
-// x = hi + lo).
+// of at most 128), with B = [[Re M, -Im M], [Im M, Re M]] blocks.
 //
-// Operands are stored MMA-ready (pre-split TF32 hi / lo, core-matrix layout):
-// the leaf multipoles by P2M, every other expansion by the kernel that
-// produces it, the operators at plan time.  Pipeline (one CTA = one target
-// pair x 64 right-hand sides x one column block): warp 4 streams every K
-// chunk with cp.async.bulk (two 64-row A halves per part plus the operator
-// block) into a shared-memory ring sized for the CTAs per SM; warp 5
-// issues tcgen05.mma into one of two TMEM buffers per source step (long
-// steps are cut into sub-steps of at most 8 K chunks); warps 0-3 drain each
-// finished step with tcgen05.ld into round-to-nearest FP32 registers
-// (tensor-core accumulation truncates, so long chains in TMEM lose accuracy)
-// and write the result.  Every mbarrier wait is bounded; a timeout sets an
-// error flag instead of hanging.
+// Operand format: f16 pairs x = hi + lo (11 + 11 significant bits, the
+// precision of a TF32 pair) and three f16 products per term (hi*hi + hi*lo +
+// lo*hi), at twice the TF32 tensor rate and half its operand bytes.  f16 has
+// a narrow exponent range, so every operand row is scaled by a power of two
+// that puts its largest entry in [2^14, 2^15): one factor per operator
+// matrix (plan time) and one per (box, right-hand side, column block) of an
+// expansion (written by the kernel that produces it).  A step's product is
+// then exact up to the split's rounding times 2^(ea + eb), and the drain
+// undoes both factors when it adds the step in FP32 (multiplying by a power
+// of two is exact).  Entries far below their row's maximum keep an absolute
+// error of about 2^-39 of that maximum.
+//
+// Operands are stored MMA-ready (pre-split, scaled, core-matrix layout): the
+// leaf multipoles by P2M, every other expansion by the kernel that produces
+// it, the operators at plan time.  Pipeline (one CTA = one target pair x 64
+// right-hand sides x one column block): warp 4 streams every K chunk with
+// cp.async.bulk (two 64-row A halves per part plus the operator block) into
+// a shared-memory ring sized for the CTAs per SM; warp 5 issues tcgen05.mma
+// into one of two TMEM buffers per source step (steps are cut into
+// sub-steps at the column blocks of the producing level, so that one
+// expansion factor covers a sub-step); warps 0-3 drain each finished step
+// with tcgen05.ld into round-to-nearest FP32 registers (tensor-core
+// accumulation truncates, so long chains in TMEM lose accuracy) and write the
+// result.  Every mbarrier wait is bounded; a timeout sets an error flag
+// instead of hanging.
 #include <algorithm>
 #include <map>
 #include <vector>
@@ -44,33 +55,59 @@ using namespace tc;
 // CTAs per SM as tensor memory, registers and shared memory allow: two TMEM
 // accumulation buffers of NB columns in a power-of-two allocation (128
 // columns for NB <= 64, i.e. four CTAs per SM; 256 beyond, where the drain
-// registers limit the SM to two CTAs anyway), and as many ring stages as fit
-// the CTA's share of shared memory (at least two).
+// registers limit the SM to two CTAs anyway), and as many ring stages (one
+// 16-wide K chunk each: the two 4 KB A halves (hi and lo interleaved), B hi,
+// B lo) as fit the CTA's share of shared memory (at least two).  The stage
+// count matters less than the number of bulk copies per chunk (three): the
+// SM's copy engine, not bandwidth, paces this pass.
 template <int NB>
 struct TcCfg {
     static constexpr int tmem_cols = 2 * NB <= 128 ? 128 : 256;
     static constexpr int buf_cols = tmem_cols / 2;
     static constexpr int ctas = 512 / tmem_cols;
-    static constexpr int stage_bytes = 16384 + NB * 128;
-    static constexpr int budget = 232448 / ctas - 1024 - 256 - 64;
+    static constexpr int stage_bytes = 8192 + NB * 64;
+    // 228 KB of shared memory per SM; per CTA 1 KB reserved by the system,
+    // 1 KB of static shared memory and 256 B of barriers
+    static constexpr int budget = 233472 / ctas - 1024 - 1024 - 256;
     static constexpr int stages = budget / stage_bytes < 8 ? budget / stage_bytes : 8;
     static_assert(stages >= 2, "ring needs two stages");
     static constexpr size_t smem = (size_t)stages * stage_bytes + 256;
 };
 constexpr int TC_MAX_NP = 128;         // widest column block (one 128-column TMEM buffer)
-constexpr int TC_STEP_CHUNKS = 8;      // K chunks accumulated in TMEM before a drain
 
 struct TcTile { int32_t b0, b1, s0, s1; };          // boxes (-1: empty), step range
 // kind 0 free M2L, 1 reaction M2L, 2 secondary source (L2L parent or M2M child);
 // src -1: none; K chunks c0 .. c1 - 1 of the operator
 struct TcStep { int32_t kind, idx, src0, src1, c0, c1; };
 
+// Largest |Re|, |Im| of each complex matrix M[i] (nin x nout) -> 2^-e, the
+// factor that undoes its f16 scaling.
+__global__ void tc_bscale_kernel(const cf* M, int nin, int nout, float* sc) {
+    const int i = blockIdx.x;
+    const int64_t per = (int64_t)nin * nout;
+    float m = 0.0f;
+    for (int64_t e = threadIdx.x; e < per; e += blockDim.x) {
+        const cf z = M[(int64_t)i * per + e];
+        m = fmaxf(m, fmaxf(fabsf(z.x), fabsf(z.y)));
+    }
+    __shared__ float red[32];
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+        sc[i] = pow2f(-f16_exp(m));
+    }
+}
+
 // Pre-split B chunks: for matrix index i, chunk c, part (0 hi, 1 lo):
-//   float offset ((i * kc + c) * 2 + part) * (Np * 16) + ((n / 8) * 4 + (k % 16) / 4) * 32 + (n % 8) * 4 + k % 4
-// M is a column-major complex matrix [m][p] (nin x nout).
-__global__ void tc_btable_kernel(const cf* M, int nmat, int nin, int nout, int Np, int kc, float* out) {
+//   half offset ((i * kc + c) * 2 + part) * (Np * 16) + ((n / 8) * 2 + (k % 16) / 8) * 64 + (n % 8) * 8 + k % 8
+// of the entry scaled by 1 / sc[i].  M is a column-major complex matrix [m][p] (nin x nout).
+__global__ void tc_btable_kernel(const cf* M, const float* sc, int nmat, int nin, int nout, int Np, int kc,
+                                 __half* out) {
     const int64_t per = (int64_t)kc * 16 * Np;   // (n, k) entries per matrix
     const int64_t total = (int64_t)nmat * per;
+    uint16_t* o = (uint16_t*)out;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(e / per);
         const int r = (int)(e % per);
@@ -82,33 +119,40 @@ __global__ void tc_btable_kernel(const cf* M, int nmat, int nin, int nout, int N
             const bool re_out = n < nout, re_in = k < nin;
             v = re_out ? (re_in ? z.x : -z.y) : (re_in ? z.y : z.x);
         }
-        const float hi = __uint_as_float(tf32_rna(v));
-        const float lo = __uint_as_float(tf32_rna(v - hi));
+        uint16_t hi, lo;
+        split_f16(v / sc[i], hi, lo);
         const int c = k / 16, kk = k % 16;
         const int64_t base = (((int64_t)i * kc + c) * 2) * (Np * 16);
-        const int64_t core = ((n / 8) * 4 + kk / 4) * 32 + (n % 8) * 4 + kk % 4;
-        out[base + core] = hi;
-        out[base + Np * 16 + core] = lo;
+        const int64_t core = ((n / 8) * 2 + kk / 8) * 64 + (n % 8) * 8 + kk % 8;
+        o[base + core] = hi;
+        o[base + Np * 16 + core] = lo;
     }
 }
 
 // MMA-ready expansions: per box, per 64-row right-hand-side chunk rc, per K
-// chunk c (16 real values: Re a_0..a_{nin-1} then Im, zero padded), hi and lo
-// TF32 parts, each 64 rows x 16 floats in the no-swizzle core-matrix layout:
-//   float offset (((box * nrc + rc) * kc + c) * 2 + part) * 1024
-//                + ((r / 8) * 4 + kk / 4) * 32 + (r % 8) * 4 + kk % 4.
-// The leaf multipoles are written in this form by P2M, all other expansions
-// by the tensor-core kernel that produces them.
+// chunk c (16 real values: Re a_0..a_{nin-1} then Im, zero padded), one 4 KB
+// block of 64 rows x 16 halves x (hi, lo) in the no-swizzle core-matrix
+// layout with the two parts interleaved per 8-row group (row-group stride
+// 512 B, part stride 256 B, K-core stride 128 B), so that one bulk copy moves
+// both parts of a 64-row operand half:
+//   half offset ((box * nrc + rc) * kc + c) * 2048
+//               + (r / 8) * 256 + part * 128 + (kk / 8) * 64 + (r % 8) * 8 + kk % 8,
+// of the coefficient times 2^e(box, rc, block, r); the factor 2^-e is stored at
+//   ((box * nrc + rc) * nsb + block) * 64 + r,
+// block = c / sblk, where the producing level has nsb column blocks of sblk
+// K chunks.  The leaf multipoles are written in this form by P2M, all other
+// expansions by the tensor-core kernel that produces them.
 
 constexpr int TC2_THREADS = 192;   // warps 0-3 drain, warp 4 TMA, warp 5 MMA
 
 // Store one row of a finished tile: the FP32 coefficients out[box][r][0 .. nc)
 // (columns n0 .. n0 + NB - 1 of the real GEMM: Re then Im) and, when sdst is
-// given, the MMA-ready copy of the row (every row of the 64-row block, so
-// rows r >= nrhs stay zero).
+// given, the MMA-ready copy of the row with its factor (every row of the
+// 64-row block, so rows r >= nrhs stay zero).
 template <int NB>
-__device__ __forceinline__ void tc_store_row(const float (&acc)[NB], int box, int row, int rc, int n0, int nrhs, int nc,
-                                             int nrc, cf* __restrict__ out, float* __restrict__ sdst, int kcd) {
+__device__ __forceinline__ void tc_store_row(const float (&acc)[NB], int box, int row, int rc, int cb, int nbz,
+                                             int n0, int nrhs, int nc, int nrc, cf* __restrict__ out,
+                                             __half* __restrict__ sdst, float* __restrict__ ssc, int kcd) {
     const int rr = row & 63, r = rc * 64 + rr;
     if (r < nrhs) {
         float* o = (float*)(out + ((int64_t)box * nrhs + r) * nc);
@@ -120,20 +164,23 @@ __device__ __forceinline__ void tc_store_row(const float (&acc)[NB], int box, in
         }
     }
     if (sdst) {
-        float* base = sdst + (((int64_t)box * nrc + rc) * kcd * 2) * 1024 + ((rr >> 3) * 4) * 32 + (rr & 7) * 4;
+        float m = 0.0f;
 #pragma unroll
-        for (int j = 0; j < NB; j += 4) {
+        for (int j = 0; j < NB; ++j) m = fmaxf(m, fabsf(acc[j]));
+        const int e = f16_exp(m);
+        const float s = pow2f(e);
+        ssc[(((int64_t)box * nrc + rc) * nbz + cb) * 64 + rr] = pow2f(-e);
+        uint16_t* base = (uint16_t*)sdst + ((int64_t)box * nrc + rc) * kcd * 2048 + (rr >> 3) * 256 + (rr & 7) * 8;
+#pragma unroll
+        for (int j = 0; j < NB; j += 8) {
             const int g = n0 + j;
             if ((g >> 4) < kcd) {
-                float h[4], lo[4];
+                uint16_t h[8], lo[8];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    h[u] = __uint_as_float(tf32_rna(acc[j + u]));
-                    lo[u] = __uint_as_float(tf32_rna(acc[j + u] - h[u]));
-                }
-                float* d = base + (int64_t)(g >> 4) * 2048 + ((g & 15) >> 2) * 32;
-                *(float4*)d = make_float4(h[0], h[1], h[2], h[3]);
-                *(float4*)(d + 1024) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+                for (int u = 0; u < 8; ++u) split_f16(acc[j + u] * s, h[u], lo[u]);
+                uint16_t* d = base + (int64_t)(g >> 4) * 2048 + ((g & 15) >> 3) * 64;
+                *(uint4*)d = pack8(h);
+                *(uint4*)(d + 128) = pack8(lo);
             }
         }
     }
@@ -146,14 +193,18 @@ __device__ __forceinline__ void tc_store_row(const float (&acc)[NB], int box, in
 // nc) and, when sdst is given, also in MMA-ready form (kcd K chunks, the
 // layout above) for the next tensor-core consumer; with several segments
 // (levels with too few tiles to fill the GPU) each CTA writes its partial
-// sums to part and tc_reduce_kernel finishes the store.
+// sums to part and tc_reduce_kernel finishes the store.  Sources of kind 0
+// and 1 are read from amma (factors asc, nsba column blocks of sba chunks),
+// kind 2 from pmma (psc, nsbp, sbp); operator factors sfree, sreact, ssec.
 template <int NB>
 __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
-    const TcTile* __restrict__ tiles, const TcStep* __restrict__ steps, const float* __restrict__ Bfree,
-    const float* __restrict__ Breact, const float* __restrict__ Bl2l, const float* __restrict__ amma,
-    const float* __restrict__ pmma, const float* __restrict__ zero4k, cf* __restrict__ out, int nrhs, int nc,
-    int kc, int kc2, int nrc, int Np, float* __restrict__ sdst, int kcd, int nseg, float* __restrict__ part,
-    int* err) {
+    const TcTile* __restrict__ tiles, const TcStep* __restrict__ steps, const __half* __restrict__ Bfree,
+    const __half* __restrict__ Breact, const __half* __restrict__ Bl2l, const float* __restrict__ sfree,
+    const float* __restrict__ sreact, const float* __restrict__ ssec, const __half* __restrict__ amma,
+    const float* __restrict__ asc, int nsba, int sba, const __half* __restrict__ pmma,
+    const float* __restrict__ psc, int nsbp, int sbp, const __half* __restrict__ zero4k, cf* __restrict__ out,
+    int nrhs, int nc, int kc, int kc2, int nrc, int Np, __half* __restrict__ sdst, float* __restrict__ ssc, int kcd,
+    int nseg, float* __restrict__ part, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -201,13 +252,24 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
     }
     if (warp < 4) {
         // ---------------- drain: FP32 round-to-nearest accumulation ----------------
-        const int row = tid, tgt = row >> 6;
+        const int row = tid, tgt = row >> 6, rr = row & 63;
         float acc[NB];
 #pragma unroll
         for (int j = 0; j < NB; ++j) acc[j] = 0.0f;
         bool ok = true;
         for (int s = 0; s < nsteps && ok; ++s) {
             const int b = s & 1;
+            // the step's factor 2^-(ea + eb) for this row
+            const TcStep st = steps[sbeg + s];
+            const int src = tgt ? st.src1 : st.src0;
+            float f = 0.0f;
+            if (src >= 0) {
+                const bool sec = st.kind == 2;
+                const float* scs = sec ? psc : asc;
+                const int nsb = sec ? nsbp : nsba, sbk = sec ? sbp : sba;
+                const float fb = st.kind == 0 ? sfree[st.idx] : st.kind == 1 ? sreact[st.idx] : ssec[st.idx];
+                f = scs[(((int64_t)src * nrc + rc) * nsb + st.c0 / sbk) * 64 + rr] * fb;
+            }
             bool good = !s_abort && mbar_wait(&dfull[b], (uint32_t)((s >> 1) & 1));
             good = __all_sync(0xffffffffu, good);
             if (!good) { ok = false; s_abort = 1; break; }
@@ -223,7 +285,7 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
                              : "r"(tb + (uint32_t)c0));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int j = 0; j < 16; ++j) acc[c0 + j] += __uint_as_float(v[j]);
+                for (int j = 0; j < 16; ++j) acc[c0 + j] = fmaf(__uint_as_float(v[j]), f, acc[c0 + j]);
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(&dfree[b]);
@@ -237,21 +299,23 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
             for (int j = 0; j < NB; j += 4) *(float4*)(pp + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
         } else {
             const int box = tgt ? tile.b1 : tile.b0;
-            if (box >= 0) tc_store_row<NB>(acc, box, row, rc, n0, nrhs, nc, nrc, out, sdst, kcd);
+            if (box >= 0) tc_store_row<NB>(acc, box, row, rc, cb, nbz, n0, nrhs, nc, nrc, out, sdst, ssc, kcd);
         }
     } else if (warp == 4 && lane == 0) {
         // ---------------- TMA: A halves (two source boxes) and the operator block ----------------
         // (hi and lo of a single-block operator are contiguous: one copy)
         const bool one_b = Np == NB;
         int i = 0;
+        TcStep nxt = nsteps > 0 ? steps[sbeg] : TcStep{0, 0, -1, -1, 0, 0};
         for (int s = 0; s < nsteps; ++s) {
-            const TcStep st = steps[sbeg + s];
+            const TcStep st = nxt;
+            if (s + 1 < nsteps) nxt = steps[sbeg + s + 1];   // one step ahead
             const bool sec = st.kind == 2;
             const int nk = sec ? kc2 : kc;
-            const float* base = sec ? pmma : amma;
-            const float* Bm = st.kind == 0 ? Bfree + (int64_t)st.idx * nk * 32 * Np
-                            : st.kind == 1 ? Breact + (int64_t)st.idx * nk * 32 * Np
-                                           : Bl2l + (int64_t)st.idx * nk * 32 * Np;
+            const __half* base = sec ? pmma : amma;
+            const __half* Bm = st.kind == 0 ? Bfree + (int64_t)st.idx * nk * 32 * Np
+                             : st.kind == 1 ? Breact + (int64_t)st.idx * nk * 32 * Np
+                                            : Bl2l + (int64_t)st.idx * nk * 32 * Np;
             bool stop = false;
             for (int c = st.c0; c < st.c1; ++c, ++i) {
                 const int stg = i % TC_STAGES;
@@ -262,50 +326,43 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int src = h ? st.src1 : st.src0;
-#pragma unroll
-                    for (int part = 0; part < 2; ++part) {
-                        const float* g = (src >= 0) ? base + ((((int64_t)src * nrc + rc) * nk + c) * 2 + part) * 1024
-                                                    : zero4k;
-                        bulk_g2s(sb + part * 8192 + h * 4096, g, 4096u, &full[stg]);
-                    }
+                    const __half* g = (src >= 0) ? base + (((int64_t)src * nrc + rc) * nk + c) * 2048 : zero4k;
+                    bulk_g2s(sb + h * 4096, g, 4096u, &full[stg]);
                 }
-                const float* Bc = Bm + (int64_t)c * 32 * Np + (int64_t)n0 * 16;
+                const __half* Bc = Bm + (int64_t)c * 32 * Np + (int64_t)n0 * 16;
                 if (one_b) {
-                    bulk_g2s(sb + 16384, Bc, (uint32_t)(NB * 128), &full[stg]);
+                    bulk_g2s(sb + 8192, Bc, (uint32_t)(NB * 64), &full[stg]);
                 } else {
-                    bulk_g2s(sb + 16384, Bc, (uint32_t)(NB * 64), &full[stg]);
-                    bulk_g2s(sb + 16384 + NB * 64, Bc + (int64_t)Np * 16, (uint32_t)(NB * 64), &full[stg]);
+                    bulk_g2s(sb + 8192, Bc, (uint32_t)(NB * 32), &full[stg]);
+                    bulk_g2s(sb + 8192 + NB * 32, Bc + (int64_t)Np * 16, (uint32_t)(NB * 32), &full[stg]);
                 }
             }
             if (stop) break;
         }
     } else if (warp == 5 && lane == 0) {
         // ---------------- MMA issuer: one TMEM buffer per source step ----------------
-        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NB >> 3) << 17) | ((128u >> 4) << 24);
+        constexpr uint32_t idesc = idesc_f16(NB);
         int i = 0;
         bool ok = true;
+        int nk_next = nsteps > 0 ? steps[sbeg].c1 - steps[sbeg].c0 : 0;
         for (int s = 0; s < nsteps && ok; ++s) {
+            const int nk = nk_next;
+            if (s + 1 < nsteps) nk_next = steps[sbeg + s + 1].c1 - steps[sbeg + s + 1].c0;
             const int b = s & 1;
             if (s_abort || !mbar_wait(&dfree[b], (uint32_t)(((s >> 1) & 1) ^ 1))) { s_abort = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t dt = taddr + (uint32_t)(b * CFG::buf_cols);
-            const int nk = steps[sbeg + s].c1 - steps[sbeg + s].c0;
-            uint32_t accf = 0;
             for (int c = 0; c < nk; ++c, ++i) {
                 const int stg = i % TC_STAGES;
                 const uint32_t ph = (uint32_t)((i / TC_STAGES) & 1);
                 if (s_abort || !mbar_wait(&full[stg], ph)) { ok = false; s_abort = 1; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t sb = su32(smem + stg * stage_bytes);
-#pragma unroll
-                for (int ks = 0; ks < 2; ++ks) {
-                    const uint64_t ah = sdesc(sb + ks * 256), al = sdesc(sb + 8192 + ks * 256);
-                    const uint64_t bh = sdesc(sb + 16384 + ks * 256), bl = sdesc(sb + 16384 + NB * 64 + ks * 256);
-                    mma_tf32(dt, ah, bh, idesc, accf);
-                    accf = 1;
-                    mma_tf32(dt, ah, bl, idesc, 1);
-                    mma_tf32(dt, al, bh, idesc, 1);
-                }
+                const uint64_t ah = sdesc(sb, 512), al = sdesc(sb + 256, 512);
+                const uint64_t bh = sdesc(sb + 8192, 256), bl = sdesc(sb + 8192 + NB * 32, 256);
+                mma_f16(dt, ah, bh, idesc, c > 0 ? 1u : 0u);
+                mma_f16(dt, ah, bl, idesc, 1);
+                mma_f16(dt, al, bh, idesc, 1);
                 mma_commit(&empty[stg]);
             }
             if (ok) mma_commit(&dfull[b]);
@@ -317,35 +374,37 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
 }
 
 // Sum the segments' partial results of a split launch and store them like
-// the single-segment epilogue; one thread per (tile, RHS block, column block,
-// row, group of four columns).
+// the single-segment epilogue; one warp per (tile, RHS block, column block,
+// row), lane jq holding columns 4 jq .. 4 jq + 3 of the block.
 template <int NB>
 __global__ void tc_reduce_kernel(const TcTile* __restrict__ tiles, int ntiles, int nrcl, int nbz, int nseg,
                                  const float* __restrict__ part, cf* __restrict__ out, int nrhs, int nc, int nrc,
-                                 float* __restrict__ sdst, int kcd) {
+                                 __half* __restrict__ sdst, float* __restrict__ ssc, int kcd) {
     constexpr int NQ = NB / 4;
-    const int64_t total = (int64_t)ntiles * nrcl * nbz * 128 * NQ;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int jq = (int)(e % NQ);
-        int64_t rest = e / NQ;
-        const int row = (int)(rest % 128);
-        rest /= 128;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarp = (int64_t)ntiles * nrcl * nbz * 128;
+    const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t wi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wi < nwarp; wi += wstride) {
+        const int row = (int)(wi % 128);
+        int64_t rest = wi / 128;
         const int cb = (int)(rest % nbz);
         rest /= nbz;
         const int rc = (int)(rest % nrcl);
         const int64_t t = rest / nrcl;
         const TcTile tile = tiles[t];
         const int box = (row >> 6) ? tile.b1 : tile.b0;
-        if (box < 0) continue;
+        if (box < 0) continue;   // uniform over the warp
+        const int jq = lane;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int sg = 0; sg < nseg; ++sg) {
-            const float4 w = *(const float4*)(part + ((((int64_t)sg * ntiles + t) * nrcl + rc) * nbz + cb) * 128 * NB +
-                                              (int64_t)row * NB + 4 * jq);
-            v.x += w.x; v.y += w.y; v.z += w.z; v.w += w.w;
-        }
+        if (jq < NQ)
+            for (int sg = 0; sg < nseg; ++sg) {
+                const float4 w = *(const float4*)(part + ((((int64_t)sg * ntiles + t) * nrcl + rc) * nbz + cb) * 128 * NB +
+                                                  (int64_t)row * NB + 4 * jq);
+                v.x += w.x; v.y += w.y; v.z += w.z; v.w += w.w;
+            }
         const float a4[4] = {v.x, v.y, v.z, v.w};
         const int rr = row & 63, r = rc * 64 + rr, g0 = cb * NB + 4 * jq;
-        if (r < nrhs) {
+        if (jq < NQ && r < nrhs) {
             float* o = (float*)(out + ((int64_t)box * nrhs + r) * nc);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -354,17 +413,22 @@ __global__ void tc_reduce_kernel(const TcTile* __restrict__ tiles, int ntiles, i
                 else if (g < 2 * nc) o[2 * (g - nc) + 1] = a4[u];
             }
         }
-        if (sdst && (g0 >> 4) < kcd) {
-            float h[4], lo[4];
+        if (sdst) {
+            float m = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            const int e = f16_exp(m);
+            if (lane == 0) ssc[(((int64_t)box * nrc + rc) * nbz + cb) * 64 + rr] = pow2f(-e);
+            if (jq < NQ && (g0 >> 4) < kcd) {
+                const float s = pow2f(e);
+                uint16_t h[4], lo[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                h[u] = __uint_as_float(tf32_rna(a4[u]));
-                lo[u] = __uint_as_float(tf32_rna(a4[u] - h[u]));
+                for (int u = 0; u < 4; ++u) split_f16(a4[u] * s, h[u], lo[u]);
+                uint16_t* d = (uint16_t*)sdst + ((int64_t)box * nrc + rc) * kcd * 2048 + (rr >> 3) * 256 + (rr & 7) * 8 +
+                              (int64_t)(g0 >> 4) * 2048 + ((g0 & 15) >> 3) * 64 + (g0 & 7);
+                *(uint2*)d = make_uint2((uint32_t)h[0] | ((uint32_t)h[1] << 16), (uint32_t)h[2] | ((uint32_t)h[3] << 16));
+                *(uint2*)(d + 128) =
+                    make_uint2((uint32_t)lo[0] | ((uint32_t)lo[1] << 16), (uint32_t)lo[2] | ((uint32_t)lo[3] << 16));
             }
-            float* d = sdst + (((int64_t)box * nrc + rc) * kcd * 2) * 1024 + ((rr >> 3) * 4) * 32 + (rr & 7) * 4 +
-                       (int64_t)(g0 >> 4) * 2048 + ((g0 & 15) >> 2) * 32;
-            *(float4*)d = make_float4(h[0], h[1], h[2], h[3]);
-            *(float4*)(d + 1024) = make_float4(lo[0], lo[1], lo[2], lo[3]);
         }
     }
 }
@@ -384,10 +448,11 @@ void tc_widths(int ncoef, int* nb, int* nbw, int* np, int* kc) {
 // Target pairs (b, b + 4) with b = 8 j + c (same child position, parents 2j
 // and 2j + 1); a missing or empty box is -1.  add(b0, b1) appends the pair's
 // source steps.
-// Append one source step as sub-steps of at most TC_STEP_CHUNKS K chunks.
-void push_step(std::vector<TcStep>& steps, int kind, int idx, int32_t s0, int32_t s1, int nk) {
-    for (int c0 = 0; c0 < nk; c0 += TC_STEP_CHUNKS)
-        steps.push_back({kind, idx, s0, s1, c0, std::min(nk, c0 + TC_STEP_CHUNKS)});
+// Append one source step as sub-steps of sblk K chunks (the column blocks of
+// the level that produced the source expansion: one factor per sub-step).
+void push_step(std::vector<TcStep>& steps, int kind, int idx, int32_t s0, int32_t s1, int nk, int sblk) {
+    for (int c0 = 0; c0 < nk; c0 += sblk)
+        steps.push_back({kind, idx, s0, s1, c0, std::min(nk, c0 + sblk)});
 }
 
 template <class NonEmpty, class Add>
@@ -422,29 +487,43 @@ hfmm_status upload_tiles(hfmm_plan_s* P, const std::vector<TcTile>& tiles, const
     return HFMM_OK;
 }
 
-hfmm_status btable(hfmm_plan_s* P, const cf* M, int nmat, int nin, int nout, int Np, int kc, float** out,
-                   cudaStream_t st) {
-    const size_t floats = (size_t)nmat * kc * 32 * Np;
-    HFMM_TRY(plan_alloc(P, (void**)out, sizeof(float) * floats));
-    tc_btable_kernel<<<4 * 152, 256, 0, st>>>(M, nmat, nin, nout, Np, kc, *out);
+hfmm_status btable(hfmm_plan_s* P, const cf* M, int nmat, int nin, int nout, int Np, int kc, __half** out,
+                   float** sc, cudaStream_t st) {
+    const size_t halves = (size_t)nmat * kc * 32 * Np;
+    HFMM_TRY(plan_alloc(P, (void**)out, sizeof(__half) * halves));
+    HFMM_TRY(plan_alloc(P, (void**)sc, sizeof(float) * nmat));
+    tc_bscale_kernel<<<nmat, 256, 0, st>>>(M, nin, nout, *sc);
     HFMM_CUDA_TRY(cudaGetLastError());
-    P->table_bytes += sizeof(float) * (double)floats;
+    tc_btable_kernel<<<4 * 152, 256, 0, st>>>(M, *sc, nmat, nin, nout, Np, kc, *out);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    P->table_bytes += sizeof(__half) * (double)halves + sizeof(float) * (double)nmat;
     return HFMM_OK;
 }
 
-// Arguments of one launch of the tensor-core kernel.
+// Arguments of one launch of the tensor-core kernel: sources of kind 0 / 1
+// from amma (factors asc; nsba column blocks of sba K chunks), kind 2 from
+// pmma (psc, nsbp, sbp); the result to out and, when sdst is given, in
+// MMA-ready form with factors ssc.
 struct TcLaunch {
     const void* tiles;
     const void* steps;
     int64_t ntiles;
-    const float* Bfree;
-    const float* Breact;
-    const float* Bsec;
-    const float* amma;
-    const float* pmma;
+    const __half* Bfree;
+    const __half* Breact;
+    const __half* Bsec;
+    const float* sfree;
+    const float* sreact;
+    const float* ssec;
+    const __half* amma;
+    const float* asc;
+    int nsba, sba;
+    const __half* pmma;
+    const float* psc;
+    int nsbp, sbp;
     cf* out;
     int nc, kc, kc2, np, nb, nbw;
-    float* sdst;
+    __half* sdst;
+    float* ssc;
     int kcd;
     int maxsteps;
 };
@@ -472,14 +551,15 @@ hfmm_status launch_nb(hfmm_plan_s* P, const TcLaunch& a, int nrhs, cudaStream_t 
     float* part = nseg > 1 ? P->tc_part : nullptr;
     dim3 grid((unsigned)a.ntiles, (unsigned)nrcl, (unsigned)(a.nb * nseg));
     m2l_tc_kernel<NB><<<grid, TC2_THREADS, smem, st>>>(
-        (const TcTile*)a.tiles, (const TcStep*)a.steps, a.Bfree, a.Breact, a.Bsec, a.amma, a.pmma, P->tc_zero, a.out,
-        nrhs, a.nc, a.kc, a.kc2, nrc, a.np, a.sdst, a.kcd, nseg, part, P->tc_err);
+        (const TcTile*)a.tiles, (const TcStep*)a.steps, a.Bfree, a.Breact, a.Bsec, a.sfree, a.sreact, a.ssec, a.amma,
+        a.asc, a.nsba, a.sba, a.pmma, a.psc, a.nsbp, a.sbp, P->tc_zero, a.out, nrhs, a.nc, a.kc, a.kc2, nrc, a.np,
+        a.sdst, a.ssc, a.kcd, nseg, part, P->tc_err);
     HFMM_CUDA_TRY(cudaGetLastError());
     if (part) {
-        const int64_t total = a.ntiles * nrcl * a.nb * 128 * (NB / 4);
-        const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 8 * 152);
+        const int64_t warps = a.ntiles * nrcl * a.nb * 128;
+        const unsigned blocks = (unsigned)std::min<int64_t>((warps + 7) / 8, 8 * 152);
         tc_reduce_kernel<NB><<<blocks, 256, 0, st>>>((const TcTile*)a.tiles, (int)a.ntiles, nrcl, a.nb, nseg, part,
-                                                      a.out, nrhs, a.nc, nrc, a.sdst, a.kcd);
+                                                      a.out, nrhs, a.nc, nrc, a.sdst, a.ssc, a.kcd);
         HFMM_CUDA_TRY(cudaGetLastError());
         ++P->launches;
     }
@@ -517,26 +597,40 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
         const int npp = has_parent ? P->lev[l - 1].ncoef : 0;
         lv.tc_kc2 = has_parent ? P->lev[l - 1].tc_kc : 0;
         const int Np = lv.tc_np;
-        // MMA-ready copies: this level's multipoles and the parent's locals
-        const size_t ab = sizeof(float) * (size_t)lv.nbox * nrc * lv.tc_kc * 2048;
+        if (lv.tc_nb > 16) {
+            hfmm_set_error("tensor-core pass: level %d needs %d column blocks (at most 16)", l, lv.tc_nb);
+            return HFMM_ERR_UNSUPPORTED;
+        }
+        // MMA-ready copies (and their factors): this level's multipoles and the parent's locals
+        const size_t ab = sizeof(__half) * (size_t)lv.nbox * nrc * lv.tc_kc * 2048;
+        const size_t as = sizeof(float) * (size_t)lv.nbox * nrc * lv.tc_nb * 64;
         HFMM_TRY(plan_alloc(P, (void**)&lv.tc_amma, ab));
         HFMM_CUDA_TRY(cudaMemsetAsync(lv.tc_amma, 0, ab, st));
-        P->buffer_bytes += (double)ab;
+        HFMM_TRY(plan_alloc(P, (void**)&lv.tc_asc, as));
+        HFMM_CUDA_TRY(cudaMemsetAsync(lv.tc_asc, 0, as, st));
+        P->buffer_bytes += (double)(ab + as);
         if (has_parent) {
-            const size_t pb = sizeof(float) * (size_t)P->lev[l - 1].nbox * nrc * lv.tc_kc2 * 2048;
+            const LevelInfo& pv = P->lev[l - 1];
+            const size_t pb = sizeof(__half) * (size_t)pv.nbox * nrc * lv.tc_kc2 * 2048;
+            const size_t ps = sizeof(float) * (size_t)pv.nbox * nrc * pv.tc_nb * 64;
             HFMM_TRY(plan_alloc(P, (void**)&lv.tc_pmma, pb));
             HFMM_CUDA_TRY(cudaMemsetAsync(lv.tc_pmma, 0, pb, st));
-            P->buffer_bytes += (double)pb;
+            HFMM_TRY(plan_alloc(P, (void**)&lv.tc_psc, ps));
+            HFMM_CUDA_TRY(cudaMemsetAsync(lv.tc_psc, 0, ps, st));
+            P->buffer_bytes += (double)(pb + ps);
         }
-        if (lv.nv > 0) HFMM_TRY(btable(P, lv.t_free32, 49, lv.ncoef, lv.ncoef, Np, lv.tc_kc, &lv.tc_bfree, st));
+        if (lv.nv > 0)
+            HFMM_TRY(btable(P, lv.t_free32, 49, lv.ncoef, lv.ncoef, Np, lv.tc_kc, &lv.tc_bfree, &lv.tc_sfree, st));
         if (lv.nr > 0 && !(lv.t_react32 && lv.n_react_entries > 0)) {
             hfmm_set_error("tensor-core pass: level %d has reaction pairs but no reaction table", l);
             return HFMM_ERR_UNSUPPORTED;
         }
         if (lv.nr > 0)
-            HFMM_TRY(btable(P, lv.t_react32, lv.n_react_entries, lv.ncoef, lv.ncoef, Np, lv.tc_kc, &lv.tc_breact, st));
+            HFMM_TRY(btable(P, lv.t_react32, lv.n_react_entries, lv.ncoef, lv.ncoef, Np, lv.tc_kc, &lv.tc_breact,
+                            &lv.tc_sreact, st));
         if (has_parent)
-            HFMM_TRY(btable(P, P->lev[l - 1].t_l2l32, 4, npp, lv.ncoef, Np, lv.tc_kc2, &lv.tc_bl2l, st));
+            HFMM_TRY(btable(P, P->lev[l - 1].t_l2l32, 4, npp, lv.ncoef, Np, lv.tc_kc2, &lv.tc_bl2l, &lv.tc_sl2l, st));
+        const int sb_own = lv.tc_nbw / 16, sb_par = has_parent ? P->lev[l - 1].tc_nbw / 16 : 1;
 
         // downward tiles: L2L from the parent, every V-list offset, every reaction entry
         const int64_t nbox = lv.nbox;
@@ -563,14 +657,14 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
         std::vector<TcStep> steps;
         pair_tiles(nbox, nonempty, [&](int32_t b0, int32_t b1) {
             const int c = (int)((b0 >= 0 ? b0 : b1) & 3);
-            if (has_parent) push_step(steps, 2, c, b0 >= 0 ? b0 >> 2 : -1, b1 >= 0 ? b1 >> 2 : -1, lv.tc_kc2);
+            if (has_parent) push_step(steps, 2, c, b0 >= 0 ? b0 >> 2 : -1, b1 >= 0 ? b1 >> 2 : -1, lv.tc_kc2, sb_par);
             if (lv.nv) {
                 int32_t s0[49], s1[49];
                 for (int o = 0; o < 49; ++o) s0[o] = s1[o] = -1;
                 if (b0 >= 0) for (int32_t e = vb[b0]; e < vb[b0 + 1]; ++e) s0[vo[e]] = vs[e];
                 if (b1 >= 0) for (int32_t e = vb[b1]; e < vb[b1 + 1]; ++e) s1[vo[e]] = vs[e];
                 for (int o = 0; o < 49; ++o)
-                    if (s0[o] >= 0 || s1[o] >= 0) push_step(steps, 0, o, s0[o], s1[o], lv.tc_kc);
+                    if (s0[o] >= 0 || s1[o] >= 0) push_step(steps, 0, o, s0[o], s1[o], lv.tc_kc, sb_own);
             }
             if (lv.nr) {
                 // merge the two reaction lists by table entry (dx, ysum)
@@ -581,7 +675,8 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
                     if (it == mm.end()) mm[rt[e]] = {-1, rs[e]};
                     else it->second.second = rs[e];
                 }
-                for (auto& kv : mm) push_step(steps, 1, kv.first, kv.second.first, kv.second.second, lv.tc_kc);
+                for (auto& kv : mm)
+                    push_step(steps, 1, kv.first, kv.second.first, kv.second.second, lv.tc_kc, sb_own);
             }
         }, tiles, steps);
         HFMM_TRY(upload_tiles(P, tiles, steps, &lv.tc_tiles, &lv.tc_steps, &lv.tc_ntiles, &lv.tc_maxsteps));
@@ -590,7 +685,7 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
     for (int l = P->lmin; l < L; ++l) {
         LevelInfo& lv = P->lev[l];
         const LevelInfo& ch = P->lev[l + 1];
-        HFMM_TRY(btable(P, lv.t_m2m32, 4, ch.ncoef, lv.ncoef, lv.tc_np, ch.tc_kc, &lv.tc_bm2m, st));
+        HFMM_TRY(btable(P, lv.t_m2m32, 4, ch.ncoef, lv.ncoef, lv.tc_np, ch.tc_kc, &lv.tc_bm2m, &lv.tc_sm2m, st));
         const int64_t span = (int64_t)1 << (2 * (L - l)), cspan = span >> 2;
         auto nonempty = [&](int64_t b) { return lb[(b + 1) * span] > lb[b * span]; };
         auto cnonempty = [&](int64_t b) { return lb[(b + 1) * cspan] > lb[b * cspan]; };
@@ -600,7 +695,7 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
             for (int c = 0; c < 4; ++c) {
                 const int32_t s0 = (b0 >= 0 && cnonempty(4 * (int64_t)b0 + c)) ? 4 * b0 + c : -1;
                 const int32_t s1 = (b1 >= 0 && cnonempty(4 * (int64_t)b1 + c)) ? 4 * b1 + c : -1;
-                if (s0 >= 0 || s1 >= 0) push_step(steps, 2, c, s0, s1, ch.tc_kc);
+                if (s0 >= 0 || s1 >= 0) push_step(steps, 2, c, s0, s1, ch.tc_kc, ch.tc_nbw / 16);
             }
         }, tiles, steps);
         HFMM_TRY(upload_tiles(P, tiles, steps, &lv.tc_mtiles, &lv.tc_msteps, &lv.tc_nmtiles, &lv.tc_mmaxsteps));
@@ -634,8 +729,9 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
 hfmm_status launch_m2m_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st) {
     LevelInfo& lv = P->lev[l];
     const LevelInfo& ch = P->lev[l + 1];
-    TcLaunch a{lv.tc_mtiles, lv.tc_msteps, lv.tc_nmtiles, nullptr, nullptr, lv.tc_bm2m, nullptr, ch.tc_amma,
-               lv.mult32, lv.ncoef, 0, ch.tc_kc, lv.tc_np, lv.tc_nb, lv.tc_nbw, lv.tc_amma, lv.tc_kc,
+    TcLaunch a{lv.tc_mtiles, lv.tc_msteps, lv.tc_nmtiles, nullptr, nullptr, lv.tc_bm2m, nullptr, nullptr,
+               lv.tc_sm2m, nullptr, nullptr, 1, 1, ch.tc_amma, ch.tc_asc, ch.tc_nb, ch.tc_nbw / 16,
+               lv.mult32, lv.ncoef, 0, ch.tc_kc, lv.tc_np, lv.tc_nb, lv.tc_nbw, lv.tc_amma, lv.tc_asc, lv.tc_kc,
                lv.tc_mmaxsteps};
     return launch_tc(P, a, nrhs, st);
 }
@@ -645,8 +741,12 @@ hfmm_status launch_m2m_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st) {
 hfmm_status launch_m2l_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st) {
     LevelInfo& lv = P->lev[l];
     const bool below = l < P->L;
-    TcLaunch a{lv.tc_tiles, lv.tc_steps, lv.tc_ntiles, lv.tc_bfree, lv.tc_breact, lv.tc_bl2l, lv.tc_amma,
-               lv.tc_pmma, lv.loc32, lv.ncoef, lv.tc_kc, lv.tc_kc2, lv.tc_np, lv.tc_nb, lv.tc_nbw,
-               below ? P->lev[l + 1].tc_pmma : nullptr, below ? P->lev[l + 1].tc_kc2 : 0, lv.tc_maxsteps};
+    const bool has_parent = l > P->lmin;
+    const LevelInfo* pv = has_parent ? &P->lev[l - 1] : nullptr;
+    TcLaunch a{lv.tc_tiles, lv.tc_steps, lv.tc_ntiles, lv.tc_bfree, lv.tc_breact, lv.tc_bl2l, lv.tc_sfree,
+               lv.tc_sreact, lv.tc_sl2l, lv.tc_amma, lv.tc_asc, lv.tc_nb, lv.tc_nbw / 16, lv.tc_pmma, lv.tc_psc,
+               pv ? pv->tc_nb : 1, pv ? pv->tc_nbw / 16 : 1, lv.loc32, lv.ncoef, lv.tc_kc, lv.tc_kc2, lv.tc_np,
+               lv.tc_nb, lv.tc_nbw, below ? P->lev[l + 1].tc_pmma : nullptr, below ? P->lev[l + 1].tc_psc : nullptr,
+               below ? P->lev[l + 1].tc_kc2 : 0, lv.tc_maxsteps};
     return launch_tc(P, a, nrhs, st);
 }

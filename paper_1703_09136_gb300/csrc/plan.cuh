@@ -15,6 +15,8 @@
 
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 
 struct LevelInfo {
@@ -55,13 +57,18 @@ struct LevelInfo {
     double* d_log_s = nullptr;    // [p + 1] log s(n) on the device
     // tensor-core passes (m2l_tc.cu): real GEMM width tc_np = tc_nb column blocks
     // of tc_nbw, K chunks of this level (tc_kc) and of the parent (tc_kc2),
-    // pre-split TF32 operator chunks, target-pair tiles and their source steps
-    // for the downward pass (L2L + M2L) and for M2M into this level
+    // pre-split f16 operator chunks with one power-of-two factor per matrix,
+    // target-pair tiles and their source steps for the downward pass (L2L +
+    // M2L) and for M2M into this level
     int tc_np = 0, tc_nb = 0, tc_nbw = 0, tc_kc = 0, tc_kc2 = 0;
-    float* tc_bfree = nullptr;
-    float* tc_breact = nullptr;
-    float* tc_bl2l = nullptr;
-    float* tc_bm2m = nullptr;
+    __half* tc_bfree = nullptr;
+    __half* tc_breact = nullptr;
+    __half* tc_bl2l = nullptr;
+    __half* tc_bm2m = nullptr;
+    float* tc_sfree = nullptr;    // 2^-e of each operator matrix (undoes its scaling)
+    float* tc_sreact = nullptr;
+    float* tc_sl2l = nullptr;
+    float* tc_sm2m = nullptr;
     void* tc_tiles = nullptr;
     void* tc_steps = nullptr;
     int64_t tc_ntiles = 0;
@@ -69,8 +76,12 @@ struct LevelInfo {
     void* tc_msteps = nullptr;
     int64_t tc_nmtiles = 0;
     int tc_maxsteps = 0, tc_mmaxsteps = 0;   // longest step list of a tile (downward, M2M)
-    float* tc_amma = nullptr;     // MMA-ready multipoles of this level
-    float* tc_pmma = nullptr;     // MMA-ready local expansions of the parent level
+    // MMA-ready expansions (f16 hi / lo) and the 2^-e factor of every
+    // (box, RHS block, column block, row) that undoes their scaling
+    __half* tc_amma = nullptr;    // multipoles of this level
+    float* tc_asc = nullptr;
+    __half* tc_pmma = nullptr;    // local expansions of the parent level
+    float* tc_psc = nullptr;
 };
 
 // Near field on tensor cores: one K chunk of a block (the four leaves of a
@@ -154,7 +165,7 @@ struct hfmm_plan_s {
     int64_t dj_njobs = 0;
     bool tc_on = false;             // every level lmin..L has tensor-core M2M / downward state
     int* tc_err = nullptr;          // set by the tensor-core pass when a bounded wait gave up
-    float* tc_zero = nullptr;       // 4 KB of zeros: the A half of a missing source box
+    __half* tc_zero = nullptr;      // 4 KB of zeros: the A half of a missing source box
     float* tc_part = nullptr;       // partial sums of split launches (levels with few tiles)
     size_t tc_part_floats = 0;
 
