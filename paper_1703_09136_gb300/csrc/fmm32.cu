@@ -105,46 +105,64 @@ HD void cfma32(cf& acc, cf a, cf b) {
 // right-hand sides of each point (iperm: sorted position of caller index j).
 constexpr int TP_PTS = 64;
 
-__global__ void gather_q32(const cf* q, const int32_t* iperm, int64_t n, int nrhs, bool conj_in, cf* qs) {
+constexpr int TP_THREADS = 256;
+constexpr int TP_PER = TP_PTS * TP_PTS / TP_THREADS;   // elements per thread and pass
+
+// Each pass moves a 64 x 64 tile: all loads of a thread are issued before its
+// shared-memory stores (16 independent 8-byte loads in flight per thread).
+__global__ void __launch_bounds__(TP_THREADS) gather_q32(const cf* __restrict__ q, const int32_t* __restrict__ iperm,
+                                                         int64_t n, int nrhs, bool conj_in, cf* __restrict__ qs) {
     __shared__ cf T[TP_PTS][TP_PTS + 1];
     const int64_t j0 = (int64_t)blockIdx.x * TP_PTS;
     const int jn = (int)min((int64_t)TP_PTS, n - j0);
     for (int r0 = 0; r0 < nrhs; r0 += TP_PTS) {
         const int rn = min(TP_PTS, nrhs - r0);
-        __syncthreads();
-        for (int e = threadIdx.x; e < rn * TP_PTS; e += blockDim.x) {
-            const int rr = e / TP_PTS, jj = e % TP_PTS;
-            if (jj < jn) {
-                cf v = q[(int64_t)(r0 + rr) * n + j0 + jj];
-                if (conj_in) v.y = -v.y;
-                T[jj][rr] = v;
-            }
+        cf v[TP_PER];
+#pragma unroll
+        for (int u = 0; u < TP_PER; ++u) {
+            const int e = threadIdx.x + u * TP_THREADS, rr = e / TP_PTS, jj = e % TP_PTS;
+            v[u] = (rr < rn && jj < jn) ? q[(int64_t)(r0 + rr) * n + j0 + jj] : cfmk(0.f, 0.f);
+        }
+        __syncthreads();   // the previous pass has read T
+#pragma unroll
+        for (int u = 0; u < TP_PER; ++u) {
+            const int e = threadIdx.x + u * TP_THREADS, rr = e / TP_PTS, jj = e % TP_PTS;
+            T[jj][rr] = conj_in ? cfmk(v[u].x, -v[u].y) : v[u];
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < jn * rn; e += blockDim.x) {
-            const int jj = e / rn, rr = e % rn;
-            qs[(int64_t)iperm[j0 + jj] * nrhs + r0 + rr] = T[jj][rr];
+#pragma unroll
+        for (int u = 0; u < TP_PER; ++u) {
+            const int e = threadIdx.x + u * TP_THREADS, jj = e / TP_PTS, rr = e % TP_PTS;
+            if (jj < jn && rr < rn) qs[(int64_t)iperm[j0 + jj] * nrhs + r0 + rr] = T[jj][rr];
         }
     }
 }
-__global__ void scatter_y32(const cf* ys, const int32_t* iperm, int64_t n, int nrhs, bool conj_out, cf* y) {
+__global__ void __launch_bounds__(TP_THREADS) scatter_y32(const cf* __restrict__ ys, const int32_t* __restrict__ iperm,
+                                                          int64_t n, int nrhs, bool conj_out, cf* __restrict__ y) {
     __shared__ cf T[TP_PTS][TP_PTS + 1];
     const int64_t j0 = (int64_t)blockIdx.x * TP_PTS;
     const int jn = (int)min((int64_t)TP_PTS, n - j0);
     for (int r0 = 0; r0 < nrhs; r0 += TP_PTS) {
         const int rn = min(TP_PTS, nrhs - r0);
-        __syncthreads();
-        for (int e = threadIdx.x; e < jn * rn; e += blockDim.x) {
-            const int jj = e / rn, rr = e % rn;
-            T[jj][rr] = ys[(int64_t)iperm[j0 + jj] * nrhs + r0 + rr];
+        cf v[TP_PER];
+#pragma unroll
+        for (int u = 0; u < TP_PER; ++u) {
+            const int e = threadIdx.x + u * TP_THREADS, jj = e / TP_PTS, rr = e % TP_PTS;
+            v[u] = (jj < jn && rr < rn) ? ys[(int64_t)iperm[j0 + jj] * nrhs + r0 + rr] : cfmk(0.f, 0.f);
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < rn * TP_PTS; e += blockDim.x) {
-            const int rr = e / TP_PTS, jj = e % TP_PTS;
-            if (jj < jn) {
-                cf v = T[jj][rr];
-                if (conj_out) v.y = -v.y;
-                y[(int64_t)(r0 + rr) * n + j0 + jj] = v;
+#pragma unroll
+        for (int u = 0; u < TP_PER; ++u) {
+            const int e = threadIdx.x + u * TP_THREADS, jj = e / TP_PTS, rr = e % TP_PTS;
+            T[jj][rr] = v[u];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < TP_PER; ++u) {
+            const int e = threadIdx.x + u * TP_THREADS, rr = e / TP_PTS, jj = e % TP_PTS;
+            if (rr < rn && jj < jn) {
+                const cf w = T[jj][rr];
+                y[(int64_t)(r0 + rr) * n + j0 + jj] = conj_out ? cfmk(w.x, -w.y) : w;
             }
         }
     }
@@ -759,7 +777,7 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
     const double MAC = 8.0 * nrhs;
     tm.begin(HFMM_STAGE_GATHER);
     const unsigned ntile = (unsigned)ceil_div(n, TP_PTS);
-    gather_q32<<<ntile, 256, 0, st>>>(q, P->iperm32, n, nrhs, adjoint, P->q32);
+    gather_q32<<<ntile, TP_THREADS, 0, st>>>(q, P->iperm32, n, nrhs, adjoint, P->q32);
     ++P->launches;
     HFMM_CUDA_TRY(cudaMemsetAsync(P->y32, 0, sizeof(cf) * n * nrhs, st));
     tm.end(HFMM_STAGE_GATHER);
@@ -779,11 +797,13 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
             P->st_flops[HFMM_STAGE_P2M] = MAC * n * lv.ncoef;
             P->st_bytes[HFMM_STAGE_P2M] = C * n + 8.0 * n * lv.ncoef + C * lv.nbox * lv.ncoef;
         }
+        // the tensor-core pass fuses both far parts of a level; subsets run on SIMT cores
+        const bool tc_down = P->tc_on && (parts & HFMM_PART_FAR_FREE) && (parts & HFMM_PART_FAR_REACT);
         tm.begin(HFMM_STAGE_M2M);
         for (int l = L - 1; l >= P->lmin; --l) {
             LevelInfo& lv = P->lev[l];
             if (P->tc_on) {
-                HFMM_TRY(launch_m2m_tc(P, l, nrhs, st));
+                HFMM_TRY(launch_m2m_tc(P, l, nrhs, !tc_down, st));
             } else {
                 m2m32_kernel<<<(unsigned)lv.nbox, 128, 0, st>>>(P->lev[l + 1].mult32, lv.t_m2m32, P->lev[l + 1].p,
                                                                lv.p, nrhs, lv.mult32);
@@ -795,8 +815,6 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
         }
         tm.end(HFMM_STAGE_M2M);
         tm.begin(HFMM_STAGE_DOWN);
-        // the tensor-core pass fuses both far parts of a level; subsets run on SIMT cores
-        const bool tc_down = P->tc_on && (parts & HFMM_PART_FAR_FREE) && (parts & HFMM_PART_FAR_REACT);
         for (int l = P->lmin; l <= L; ++l) {
             LevelInfo& lv = P->lev[l];
             const bool has_parent = l > P->lmin;
@@ -807,7 +825,7 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
             rc = std::max(1, std::min(rc, (8 * DOWN_THREADS) / lv.ncoef));
             const size_t sm = (size_t)rc * wmax * sizeof(cf);
             if (tc_down) {
-                HFMM_TRY(launch_m2l_tc(P, l, nrhs, st));
+                HFMM_TRY(launch_m2l_tc(P, l, nrhs, l == L, st));
             } else {
                 down32_kernel<<<(unsigned)lv.nbox, DOWN_THREADS, sm, st>>>(
                     P->leaf_begin, L, l, P->lmin, nrhs, lv.p, has_parent ? P->lev[l - 1].p : 0,
@@ -867,7 +885,7 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
         P->st_bytes[HFMM_STAGE_DIRECT] = 8.0 * (double)P->nd_vals;
     }
     tm.begin(HFMM_STAGE_SCATTER);
-    scatter_y32<<<ntile, 256, 0, st>>>(P->y32, P->iperm32, n, nrhs, adjoint, y);
+    scatter_y32<<<ntile, TP_THREADS, 0, st>>>(P->y32, P->iperm32, n, nrhs, adjoint, y);
     ++P->launches;
     HFMM_CUDA_TRY(cudaGetLastError());
     tm.end(HFMM_STAGE_SCATTER);

@@ -154,7 +154,7 @@ __device__ __forceinline__ void tc_store_row(const float (&acc)[NB], int box, in
                                              int n0, int nrhs, int nc, int nrc, cf* __restrict__ out,
                                              __half* __restrict__ sdst, float* __restrict__ ssc, int kcd) {
     const int rr = row & 63, r = rc * 64 + rr;
-    if (r < nrhs) {
+    if (out && r < nrhs) {
         float* o = (float*)(out + ((int64_t)box * nrhs + r) * nc);
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
@@ -197,7 +197,7 @@ __device__ __forceinline__ void tc_store_row(const float (&acc)[NB], int box, in
 // and 1 are read from amma (factors asc, nsba column blocks of sba chunks),
 // kind 2 from pmma (psc, nsbp, sbp); operator factors sfree, sreact, ssec.
 template <int NB>
-__global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
+__global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
     const TcTile* __restrict__ tiles, const TcStep* __restrict__ steps, const __half* __restrict__ Bfree,
     const __half* __restrict__ Breact, const __half* __restrict__ Bl2l, const float* __restrict__ sfree,
     const float* __restrict__ sreact, const float* __restrict__ ssec, const __half* __restrict__ amma,
@@ -298,8 +298,33 @@ __global__ void __launch_bounds__(TC2_THREADS) m2l_tc_kernel(
 #pragma unroll
             for (int j = 0; j < NB; j += 4) *(float4*)(pp + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
         } else {
-            const int box = tgt ? tile.b1 : tile.b0;
-            if (box >= 0) tc_store_row<NB>(acc, box, row, rc, cb, nbz, n0, nrhs, nc, nrc, out, sdst, ssc, kcd);
+            const int box = tgt ? tile.b1 : tile.b0;   // uniform over the warp
+            if (box >= 0) {
+                tc_store_row<NB>(acc, box, row, rc, cb, nbz, n0, nrhs, nc, nrc, nullptr, sdst, ssc, kcd);
+                if (out) {
+                    // FP32 coefficients: the warp's 32 rows are one contiguous range of out
+                    // ([box][r][coef] complex); stage them in the ring (every MMA of this
+                    // CTA has completed) and store along that range
+                    static_assert(128 * (NB + 1) * 4 <= TC_STAGES * stage_bytes, "staging fits the ring");
+                    float* stg = (float*)smem + warp * 32 * (NB + 1);
+#pragma unroll
+                    for (int j = 0; j < NB; ++j) stg[lane * (NB + 1) + j] = acc[j];
+                    __syncwarp();
+                    const int rfirst = rc * 64 + ((warp * 32) & 63);
+                    const int nrows = min(32, nrhs - rfirst);
+                    if (nrows > 0) {
+                        float* o = (float*)(out + ((int64_t)box * nrhs + rfirst) * nc);
+                        const int w2 = 2 * nc;
+                        int i = lane / w2, w = lane - (lane / w2) * w2;   // f = i * w2 + w
+                        for (int f = lane; f < nrows * w2; f += 32) {
+                            const int g = (w & 1) * nc + (w >> 1);
+                            if (g >= n0 && g < n0 + NB) o[f] = stg[i * (NB + 1) + g - n0];
+                            w += 32;
+                            while (w >= w2) { w -= w2; ++i; }
+                        }
+                    }
+                }
+            }
         }
     } else if (warp == 4 && lane == 0) {
         // ---------------- TMA: A halves (two source boxes) and the operator block ----------------
@@ -404,7 +429,7 @@ __global__ void tc_reduce_kernel(const TcTile* __restrict__ tiles, int ntiles, i
             }
         const float a4[4] = {v.x, v.y, v.z, v.w};
         const int rr = row & 63, r = rc * 64 + rr, g0 = cb * NB + 4 * jq;
-        if (jq < NQ && r < nrhs) {
+        if (out && jq < NQ && r < nrhs) {
             float* o = (float*)(out + ((int64_t)box * nrhs + r) * nc);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -725,27 +750,29 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
 
 
 // Tensor-core M2M into level l (children at l + 1 already MMA-ready); writes
-// the FP32 multipoles and their MMA-ready copy.
-hfmm_status launch_m2m_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st) {
+// the MMA-ready multipoles and, when fp32_out, the FP32 ones (read only by
+// the SIMT downward pass).
+hfmm_status launch_m2m_tc(hfmm_plan_s* P, int l, int nrhs, bool fp32_out, cudaStream_t st) {
     LevelInfo& lv = P->lev[l];
     const LevelInfo& ch = P->lev[l + 1];
     TcLaunch a{lv.tc_mtiles, lv.tc_msteps, lv.tc_nmtiles, nullptr, nullptr, lv.tc_bm2m, nullptr, nullptr,
                lv.tc_sm2m, nullptr, nullptr, 1, 1, ch.tc_amma, ch.tc_asc, ch.tc_nb, ch.tc_nbw / 16,
-               lv.mult32, lv.ncoef, 0, ch.tc_kc, lv.tc_np, lv.tc_nb, lv.tc_nbw, lv.tc_amma, lv.tc_asc, lv.tc_kc,
+               fp32_out ? lv.mult32 : nullptr, lv.ncoef, 0, ch.tc_kc, lv.tc_np, lv.tc_nb, lv.tc_nbw, lv.tc_amma, lv.tc_asc, lv.tc_kc,
                lv.tc_mmaxsteps};
     return launch_tc(P, a, nrhs, st);
 }
 
-// Tensor-core downward pass of level l; writes the FP32 local expansions and,
-// below the leaves, their MMA-ready copy for the children's L2L.
-hfmm_status launch_m2l_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st) {
+// Tensor-core downward pass of level l; writes the FP32 local expansions when
+// fp32_out (the leaves, for L2P) and, below the leaves, their MMA-ready copy
+// for the children's L2L.
+hfmm_status launch_m2l_tc(hfmm_plan_s* P, int l, int nrhs, bool fp32_out, cudaStream_t st) {
     LevelInfo& lv = P->lev[l];
     const bool below = l < P->L;
     const bool has_parent = l > P->lmin;
     const LevelInfo* pv = has_parent ? &P->lev[l - 1] : nullptr;
     TcLaunch a{lv.tc_tiles, lv.tc_steps, lv.tc_ntiles, lv.tc_bfree, lv.tc_breact, lv.tc_bl2l, lv.tc_sfree,
                lv.tc_sreact, lv.tc_sl2l, lv.tc_amma, lv.tc_asc, lv.tc_nb, lv.tc_nbw / 16, lv.tc_pmma, lv.tc_psc,
-               pv ? pv->tc_nb : 1, pv ? pv->tc_nbw / 16 : 1, lv.loc32, lv.ncoef, lv.tc_kc, lv.tc_kc2, lv.tc_np,
+               pv ? pv->tc_nb : 1, pv ? pv->tc_nbw / 16 : 1, fp32_out ? lv.loc32 : nullptr, lv.ncoef, lv.tc_kc, lv.tc_kc2, lv.tc_np,
                lv.tc_nb, lv.tc_nbw, below ? P->lev[l + 1].tc_pmma : nullptr, below ? P->lev[l + 1].tc_psc : nullptr,
                below ? P->lev[l + 1].tc_kc2 : 0, lv.tc_maxsteps};
     return launch_tc(P, a, nrhs, st);

@@ -229,8 +229,8 @@ hfmm_status build_p2p_tc(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status launch_p2p_tc(hfmm_plan_s* P, int nrhs, bool near, bool far, cudaStream_t st);
 // m2l_tc.cu
 hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st);
-hfmm_status launch_m2l_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st);
-hfmm_status launch_m2m_tc(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st);
+hfmm_status launch_m2l_tc(hfmm_plan_s* P, int l, int nrhs, bool fp32_out, cudaStream_t st);
+hfmm_status launch_m2m_tc(hfmm_plan_s* P, int l, int nrhs, bool fp32_out, cudaStream_t st);
 
 // Morton helpers
 HD uint32_t spread_bits(uint32_t v) {
