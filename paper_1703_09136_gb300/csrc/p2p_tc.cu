@@ -16,10 +16,13 @@
 // layout (fmm32.cu, near_tiles_kernel).  Per apply, warp 4 streams the tiles
 // with cp.async.bulk (prefetched into L2 a few chunks ahead); warps 0-3 build the A rows of each chunk from the
 // strengths (or the leaf's local coefficients) in shared memory; warp 5 issues
-// one 3xTF32 MMA set (hi*hi + hi*lo + lo*hi) per run of adjacent target leaves,
-// alternating between two TMEM buffers; warps 0-3 finally sum the buffers
-// in FP32 and store y (point-major, [n][nrhs]; the kernel is the first writer
-// of its targets).  Every mbarrier wait is bounded.
+// one 3xTF32 MMA set (hi*hi + hi*lo + lo*hi) per run of adjacent target leaves
+// into one 128-column TMEM accumulator; warps 0-3 finally store y
+// (point-major, [n][nrhs]; the kernel is the first writer of its targets).
+// One accumulator, a two-stage ring and at most 128 chunk records keep a CTA
+// within a third of the SM: the pass is paced by each CTA's chain of tile
+// copy, operand build and MMA, so three CTAs per SM beat deeper buffering.
+// Every mbarrier wait is bounded.
 #include <algorithm>
 #include <vector>
 
@@ -31,12 +34,12 @@ namespace {
 using namespace tc;
 
 constexpr int NT_THREADS = 192;    // warps 0-3 build A and drain, warp 4 TMA, warp 5 MMA
-constexpr int NT_STAGES = 3;
+constexpr int NT_STAGES = 2;
 constexpr int NT_MAXN = 128;       // padded targets of a block
 constexpr int NT_A = 16384;        // A: 128 rows x 16 K, hi then lo
 constexpr int NT_B = NT_MAXN * 128;
 constexpr int NT_STAGE = NT_A + NT_B;
-constexpr int NT_MAXCH = 192;     // chunks of a block (kept in shared memory)
+constexpr int NT_MAXCH = 128;     // chunks of a block (kept in shared memory; more: SIMT kernel)
 constexpr int NT_PREF = 6;         // tiles brought into L2 ahead of their copy
 constexpr size_t NT_SMEM = (size_t)NT_STAGES * NT_STAGE + 1024;
 
@@ -69,7 +72,7 @@ struct NtSmall {
     int32_t off[5], wid[4], lbox[4];
 };
 
-__global__ void __launch_bounds__(NT_THREADS, 2) p2p_tc_kernel(
+__global__ void __launch_bounds__(NT_THREADS, 3) p2p_tc_kernel(
     const int32_t* __restrict__ blocks, const NtChunk* __restrict__ chunks, const float* __restrict__ tiles,
     const int32_t* __restrict__ lb, const cf* __restrict__ qs, int nrhs, int near, int far, const cf* __restrict__ loc,
     int nc, cf* __restrict__ ys, int* err) {
@@ -118,7 +121,7 @@ __global__ void __launch_bounds__(NT_THREADS, 2) p2p_tc_kernel(
         S.tidx[n] = ti;
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(su32(&tslot)), "r"(256));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(su32(&tslot)), "r"(128));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -126,9 +129,9 @@ __global__ void __launch_bounds__(NT_THREADS, 2) p2p_tc_kernel(
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t taddr = tslot;
     if (warp < 4) {
-        // zero both accumulation buffers (every MMA accumulates)
+        // zero the accumulator (every MMA accumulates)
         const uint32_t tl = taddr + ((uint32_t)(warp * 32) << 16);
-        for (int c0 = 0; c0 < 256; c0 += 16)
+        for (int c0 = 0; c0 < 128; c0 += 16)
             asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};"
                          :: "r"(tl + (uint32_t)c0), "r"(0u) : "memory");
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(NT_THREADS, 2) p2p_tc_kernel(
 #pragma unroll
             for (int u = 0; u < 4; ++u) { pa[u] = pb[u]; pb[u] = pn[u]; }
         }
-        // ---------------- drain: sum the two buffers, store y ----------------
+        // ---------------- drain: store y ----------------
         bool good = !s_abort && mbar_wait(&done, 0u);
         good = __all_sync(0xffffffffu, good);
         if (!good) {
@@ -190,20 +193,15 @@ __global__ void __launch_bounds__(NT_THREADS, 2) p2p_tc_kernel(
             const uint32_t tl = taddr + ((uint32_t)(warp * 32) << 16);
             float* stg0 = (float*)smem;   // stage 0 is free now
             for (int g0 = 0; g0 < N; g0 += 16) {
-                uint32_t w0[16], w1[16];
+                uint32_t w0[16];
                 asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                              : "=r"(w0[0]), "=r"(w0[1]), "=r"(w0[2]), "=r"(w0[3]), "=r"(w0[4]), "=r"(w0[5]), "=r"(w0[6]),
                                "=r"(w0[7]), "=r"(w0[8]), "=r"(w0[9]), "=r"(w0[10]), "=r"(w0[11]), "=r"(w0[12]),
                                "=r"(w0[13]), "=r"(w0[14]), "=r"(w0[15])
                              : "r"(tl + (uint32_t)g0));
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                             : "=r"(w1[0]), "=r"(w1[1]), "=r"(w1[2]), "=r"(w1[3]), "=r"(w1[4]), "=r"(w1[5]), "=r"(w1[6]),
-                               "=r"(w1[7]), "=r"(w1[8]), "=r"(w1[9]), "=r"(w1[10]), "=r"(w1[11]), "=r"(w1[12]),
-                               "=r"(w1[13]), "=r"(w1[14]), "=r"(w1[15])
-                             : "r"(tl + (uint32_t)(128 + g0)));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int u = 0; u < 16; ++u) stg0[u * 128 + row] = __uint_as_float(w0[u]) + __uint_as_float(w1[u]);
+                for (int u = 0; u < 16; ++u) stg0[u * 128 + row] = __uint_as_float(w0[u]);
                 asm volatile("bar.sync 1, 128;" ::: "memory");
 #pragma unroll
                 for (int qq = 0; qq < 8; ++qq) {
@@ -239,8 +237,6 @@ __global__ void __launch_bounds__(NT_THREADS, 2) p2p_tc_kernel(
             const NtChunk& ch = S.ch[i];
             const uint32_t sa = su32(smem + stg * NT_STAGE), sb = sa + NT_A;
             const uint32_t lo_b = (uint32_t)ch.rows * 64u;
-            // runs alternate between the two TMEM buffers: two independent accumulation chains
-            int which = 0;
             for (int q = 0; q < ch.nrun; ++q) {
                 const int rw = ch.run[q];
                 const int nn = rw & 0xff, col = (rw >> 8) & 0xff, rowoff = rw >> 16;
@@ -251,11 +247,10 @@ __global__ void __launch_bounds__(NT_THREADS, 2) p2p_tc_kernel(
                 for (int ks = 0; ks < 2; ++ks) {
                     const uint64_t ah = sdesc(sa + ks * 256), al = sdesc(sa + 8192 + ks * 256);
                     const uint64_t bh = sdesc(sb + bro + ks * 256), bl = sdesc(sb + lo_b + bro + ks * 256);
-                    const uint32_t d0 = taddr + (uint32_t)(which * 128 + col), d1 = taddr + (uint32_t)((which ^ 1) * 128 + col);
-                    mma_tf32(d0, ah, bh, idesc, 1u);
-                    mma_tf32(d1, ah, bl, idesc, 1u);
-                    mma_tf32(d0, al, bh, idesc, 1u);
-                    which ^= 1;
+                    const uint32_t d = taddr + (uint32_t)col;
+                    mma_tf32(d, ah, bh, idesc, 1u);
+                    mma_tf32(d, ah, bl, idesc, 1u);
+                    mma_tf32(d, al, bh, idesc, 1u);
                 }
             }
             mma_commit(&empty[stg]);
@@ -264,7 +259,7 @@ __global__ void __launch_bounds__(NT_THREADS, 2) p2p_tc_kernel(
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(256));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(128));
 }
 
 }  // namespace
