@@ -783,6 +783,42 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
     tm.end(HFMM_STAGE_GATHER);
     P->st_bytes[HFMM_STAGE_GATHER] = 2.0 * C * n + 8.0 * n;
     const bool far = (parts & (HFMM_PART_FAR_FREE | HFMM_PART_FAR_REACT)) != 0;
+    // near free-space field and, unless the downward epilogue does it, the
+    // leaves' local expansions (L2P), one fused kernel
+    auto near_section = [&](bool near, bool l2p) -> hfmm_status {
+        const LevelInfo& lv = P->lev[L];
+        tm.begin(HFMM_STAGE_P2P);
+        if (P->tc_on) {
+            // tensor-core blocks of four leaves; SIMT kernel for the leaves of wider blocks
+            HFMM_TRY(launch_p2p_tc(P, nrhs, near, l2p, st));
+            ++P->launches;
+            if (P->nt_nfallback > 0) {
+                p2p32c_kernel<<<(unsigned)P->nt_nfallback, PC_THREADS, 0, st>>>(
+                    P->leaf_begin, L, P->xl32, P->q32, n, nrhs, (float)P->k, (float)lv.h, near ? 1 : 0,
+                    l2p ? lv.loc32 : nullptr, P->basis32, lv.ncoef, P->nt_fallback, P->y32);
+                ++P->launches;
+                HFMM_CUDA_TRY(cudaGetLastError());
+            }
+        } else {
+            p2p32c_kernel<<<(unsigned)lv.nbox, PC_THREADS, 0, st>>>(P->leaf_begin, L, P->xl32, P->q32, n, nrhs,
+                                                                    (float)P->k, (float)lv.h, near ? 1 : 0,
+                                                                    l2p ? lv.loc32 : nullptr, P->basis32, lv.ncoef,
+                                                                    nullptr, P->y32);
+            ++P->launches;
+            HFMM_CUDA_TRY(cudaGetLastError());
+        }
+        tm.end(HFMM_STAGE_P2P);
+        P->st_flops[HFMM_STAGE_P2P] = (near ? MAC * (double)P->p2p_point_pairs : 0.0) +
+                                      (l2p ? MAC * n * lv.ncoef : 0.0);
+        P->st_bytes[HFMM_STAGE_P2P] = 3.0 * C * n + 16.0 * n + (l2p ? C * lv.nbox * lv.ncoef + 8.0 * n * lv.ncoef : 0.0);
+        return HFMM_OK;
+    };
+    const bool near_free = (parts & HFMM_PART_NEAR_FREE) != 0;
+    // the tensor-core pass fuses both far parts of a level; subsets run on SIMT cores
+    const bool tc_down = P->tc_on && (parts & HFMM_PART_FAR_FREE) && (parts & HFMM_PART_FAR_REACT);
+    // L2P in the leaf-level downward epilogue: the near field runs first (first writer of y32)
+    const bool l2p_fused = far && tc_down && P->tc_l2p;
+    if (l2p_fused && near_free) HFMM_TRY(near_section(true, false));
     if (far) {
         {
             LevelInfo& lv = P->lev[L];
@@ -797,8 +833,6 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
             P->st_flops[HFMM_STAGE_P2M] = MAC * n * lv.ncoef;
             P->st_bytes[HFMM_STAGE_P2M] = C * n + 8.0 * n * lv.ncoef + C * lv.nbox * lv.ncoef;
         }
-        // the tensor-core pass fuses both far parts of a level; subsets run on SIMT cores
-        const bool tc_down = P->tc_on && (parts & HFMM_PART_FAR_FREE) && (parts & HFMM_PART_FAR_REACT);
         tm.begin(HFMM_STAGE_M2M);
         for (int l = L - 1; l >= P->lmin; --l) {
             LevelInfo& lv = P->lev[l];
@@ -825,7 +859,7 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
             rc = std::max(1, std::min(rc, (8 * DOWN_THREADS) / lv.ncoef));
             const size_t sm = (size_t)rc * wmax * sizeof(cf);
             if (tc_down) {
-                HFMM_TRY(launch_m2l_tc(P, l, nrhs, l == L, st));
+                HFMM_TRY(launch_m2l_tc(P, l, nrhs, l == L && !l2p_fused, l2p_fused, st));
             } else {
                 down32_kernel<<<(unsigned)lv.nbox, DOWN_THREADS, sm, st>>>(
                     P->leaf_begin, L, l, P->lmin, nrhs, lv.p, has_parent ? P->lev[l - 1].p : 0,
@@ -843,37 +877,13 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
             P->st_bytes[HFMM_STAGE_DOWN] += C * lv.nbox * lv.ncoef * 2.0 +
                                             (has_parent ? C * P->lev[l - 1].nbox * npp : 0.0);
         }
+        if (l2p_fused) {
+            P->st_flops[HFMM_STAGE_DOWN] += MAC * n * P->lev[L].ncoef;
+            P->st_bytes[HFMM_STAGE_DOWN] += 2.0 * C * n + 8.0 * n * P->lev[L].ncoef;
+        }
         tm.end(HFMM_STAGE_DOWN);
     }
-    // near free-space field and the leaves' local expansions, one fused kernel
-    if ((parts & HFMM_PART_NEAR_FREE) || far) {
-        const LevelInfo& lv = P->lev[L];
-        const bool near = (parts & HFMM_PART_NEAR_FREE) != 0;
-        tm.begin(HFMM_STAGE_P2P);
-        if (P->tc_on) {
-            // tensor-core blocks of four leaves; SIMT kernel for the leaves of wider blocks
-            HFMM_TRY(launch_p2p_tc(P, nrhs, near, far, st));
-            ++P->launches;
-            if (P->nt_nfallback > 0) {
-                p2p32c_kernel<<<(unsigned)P->nt_nfallback, PC_THREADS, 0, st>>>(
-                    P->leaf_begin, L, P->xl32, P->q32, n, nrhs, (float)P->k, (float)lv.h, near ? 1 : 0,
-                    far ? lv.loc32 : nullptr, P->basis32, lv.ncoef, P->nt_fallback, P->y32);
-                ++P->launches;
-                HFMM_CUDA_TRY(cudaGetLastError());
-            }
-        } else {
-            p2p32c_kernel<<<(unsigned)lv.nbox, PC_THREADS, 0, st>>>(P->leaf_begin, L, P->xl32, P->q32, n, nrhs,
-                                                                    (float)P->k, (float)lv.h, near ? 1 : 0,
-                                                                    far ? lv.loc32 : nullptr, P->basis32, lv.ncoef,
-                                                                    nullptr, P->y32);
-            ++P->launches;
-            HFMM_CUDA_TRY(cudaGetLastError());
-        }
-        tm.end(HFMM_STAGE_P2P);
-        P->st_flops[HFMM_STAGE_P2P] = (near ? MAC * (double)P->p2p_point_pairs : 0.0) +
-                                      (far ? MAC * n * lv.ncoef : 0.0);
-        P->st_bytes[HFMM_STAGE_P2P] = 3.0 * C * n + 16.0 * n + (far ? C * lv.nbox * lv.ncoef + 8.0 * n * lv.ncoef : 0.0);
-    }
+    if (!l2p_fused && (near_free || far)) HFMM_TRY(near_section(near_free, far));
     if ((parts & HFMM_PART_NEAR_REACT) && P->nd > 0) {
         tm.begin(HFMM_STAGE_DIRECT);
         direct32_kernel<<<(unsigned)P->lev[L].nbox, 128, 0, st>>>(P->leaf_begin, P->d_begin, P->d_src, P->d_blk,

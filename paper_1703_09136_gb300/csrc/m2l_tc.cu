@@ -75,6 +75,30 @@ struct TcCfg {
 };
 constexpr int TC_MAX_NP = 128;         // widest column block (one 128-column TMEM buffer)
 
+// Shared memory of the leaf L2P in the downward epilogue, per drain warp: its
+// 32 rows of beta~ (stride NB + 1), the basis rows of 8 points and its rows of
+// y for them; used only where the four warps' regions fit the ring.
+template <int NB>
+struct TcL2p {
+    static constexpr int pts = 8;
+    static constexpr int warp_bytes = 32 * (NB + 1) * 4 + pts * (NB / 2) * 8 + pts * 32 * 8;
+    static constexpr bool fits = 4 * warp_bytes <= TcCfg<NB>::stages * TcCfg<NB>::stage_bytes;
+};
+
+bool tc_l2p_fits(int nbw) {
+    switch (nbw) {
+        case 16: return TcL2p<16>::fits;
+        case 32: return TcL2p<32>::fits;
+        case 48: return TcL2p<48>::fits;
+        case 64: return TcL2p<64>::fits;
+        case 80: return TcL2p<80>::fits;
+        case 96: return TcL2p<96>::fits;
+        case 112: return TcL2p<112>::fits;
+        case 128: return TcL2p<128>::fits;
+    }
+    return false;
+}
+
 struct TcTile { int32_t b0, b1, s0, s1; };          // boxes (-1: empty), step range
 // kind 0 free M2L, 1 reaction M2L, 2 secondary source (L2L parent or M2M child);
 // src -1: none; K chunks c0 .. c1 - 1 of the operator
@@ -204,7 +228,8 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
     const float* __restrict__ asc, int nsba, int sba, const __half* __restrict__ pmma,
     const float* __restrict__ psc, int nsbp, int sbp, const __half* __restrict__ zero4k, cf* __restrict__ out,
     int nrhs, int nc, int kc, int kc2, int nrc, int Np, __half* __restrict__ sdst, float* __restrict__ ssc, int kcd,
-    int nseg, float* __restrict__ part, int* err) {
+    int nseg, float* __restrict__ part, const cf* __restrict__ l2p_basis, const int32_t* __restrict__ lbeg,
+    cf* __restrict__ ys, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -301,6 +326,59 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
             const int box = tgt ? tile.b1 : tile.b0;   // uniform over the warp
             if (box >= 0) {
                 tc_store_row<NB>(acc, box, row, rc, cb, nbz, n0, nrhs, nc, nrc, nullptr, sdst, ssc, kcd);
+                if (TcL2p<NB>::fits && l2p_basis) {
+                    // L2P of the leaf (Algorithm 1, step 4), one column block:
+                    // y[t][r] += sum_m beta~[r][m] (i/4) conj(B[t][m]) over the leaf's points t.
+                    // In the ring (every MMA has completed; one region per warp): the warp's
+                    // 32 rows of beta~ and, per 16 points, the basis rows and the warp's rows
+                    // of y (asynchronous copies, all in flight together); the sum reads
+                    // beta~ by row and the basis as broadcasts.
+                    constexpr int TCH = TcL2p<NB>::pts, WB = TcL2p<NB>::warp_bytes;
+                    float* bet = (float*)(smem + warp * WB);
+                    cf* sbs = (cf*)(bet + 32 * (NB + 1));
+                    cf* sy = sbs + TCH * (NB / 2);
+#pragma unroll
+                    for (int j = 0; j < NB; ++j) bet[lane * (NB + 1) + j] = acc[j];
+                    const float* br = bet + lane * (NB + 1);   // Re beta~_m at m, Im at nc + m
+                    const int r = rc * 64 + (row & 63);
+                    const bool live = r < nrhs;
+                    const int32_t t0 = lbeg[box], t1 = lbeg[box + 1];
+                    for (int32_t tc0 = t0; tc0 < t1; tc0 += TCH) {
+                        const int tn = min(TCH, t1 - tc0);
+                        __syncwarp();
+                        for (int e = lane; e < tn * nc; e += 32) cp_async8(sbs + e, l2p_basis + (int64_t)tc0 * nc + e);
+                        if (live)
+                            for (int t = 0; t < tn; ++t) cp_async8(sy + t * 32 + lane, ys + (int64_t)(tc0 + t) * nrhs + r);
+                        cp_async_wait_all();
+                        __syncwarp();
+                        // four points per pass: each beta~ load feeds sixteen FMAs
+                        for (int tq = 0; tq < tn; tq += 4) {
+                            float yr[4] = {0.f, 0.f, 0.f, 0.f}, yi[4] = {0.f, 0.f, 0.f, 0.f};
+                            const cf* Bt = sbs + tq * nc;
+                            const int nq = min(4, tn - tq);
+#pragma unroll 2
+                            for (int m = 0; m < nc; ++m) {
+                                const float are = br[m], aim = br[nc + m];
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) {
+                                    const cf b = Bt[(u < nq ? u : 0) * nc + m];
+                                    yr[u] = fmaf(are, b.y, fmaf(-aim, b.x, yr[u]));
+                                    yi[u] = fmaf(are, b.x, fmaf(aim, b.y, yi[u]));
+                                }
+                            }
+                            if (live) {
+#pragma unroll
+                                for (int u = 0; u < 4; ++u)
+                                    if (u < nq) {
+                                        const int t = tq + u;
+                                        const cf y0 = sy[t * 32 + lane];
+                                        ys[(int64_t)(tc0 + t) * nrhs + r] =
+                                            cfmk(y0.x + 0.25f * yr[u], y0.y + 0.25f * yi[u]);
+                                    }
+                            }
+                        }
+                    }
+                }
                 if (out) {
                     // FP32 coefficients: the warp's 32 rows are one contiguous range of out
                     // ([box][r][coef] complex); stage them in the ring (every MMA of this
@@ -551,6 +629,7 @@ struct TcLaunch {
     float* ssc;
     int kcd;
     int maxsteps;
+    bool l2p;        // leaf level: L2P into y32 from the epilogue
 };
 
 // Segments per tile for a launch of ntiles x nb CTAs (x nrc RHS blocks): split
@@ -578,7 +657,7 @@ hfmm_status launch_nb(hfmm_plan_s* P, const TcLaunch& a, int nrhs, cudaStream_t 
     m2l_tc_kernel<NB><<<grid, TC2_THREADS, smem, st>>>(
         (const TcTile*)a.tiles, (const TcStep*)a.steps, a.Bfree, a.Breact, a.Bsec, a.sfree, a.sreact, a.ssec, a.amma,
         a.asc, a.nsba, a.sba, a.pmma, a.psc, a.nsbp, a.sbp, P->tc_zero, a.out, nrhs, a.nc, a.kc, a.kc2, nrc, a.np,
-        a.sdst, a.ssc, a.kcd, nseg, part, P->tc_err);
+        a.sdst, a.ssc, a.kcd, nseg, part, a.l2p ? P->basis32 : nullptr, P->leaf_begin, P->y32, P->tc_err);
     HFMM_CUDA_TRY(cudaGetLastError());
     if (part) {
         const int64_t warps = a.ntiles * nrcl * a.nb * 128;
@@ -739,6 +818,12 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
         P->tc_part_floats = need;
         P->buffer_bytes += sizeof(float) * (double)need;
     }
+    // the leaves' L2P runs in the downward epilogue when one CTA holds a whole
+    // leaf row (one column block, no step split) and its staging fits the ring
+    {
+        const LevelInfo& lf = P->lev[L];
+        P->tc_l2p = lf.tc_nb == 1 && tc_nseg(lf.tc_ntiles, 1, nrc, lf.tc_maxsteps) == 1 && tc_l2p_fits(lf.tc_nbw);
+    }
     HFMM_TRY(plan_alloc(P, (void**)&P->tc_err, sizeof(int)));
     HFMM_CUDA_TRY(cudaMemsetAsync(P->tc_err, 0, sizeof(int), st));
     HFMM_TRY(plan_alloc(P, (void**)&P->tc_zero, 4096));
@@ -758,14 +843,15 @@ hfmm_status launch_m2m_tc(hfmm_plan_s* P, int l, int nrhs, bool fp32_out, cudaSt
     TcLaunch a{lv.tc_mtiles, lv.tc_msteps, lv.tc_nmtiles, nullptr, nullptr, lv.tc_bm2m, nullptr, nullptr,
                lv.tc_sm2m, nullptr, nullptr, 1, 1, ch.tc_amma, ch.tc_asc, ch.tc_nb, ch.tc_nbw / 16,
                fp32_out ? lv.mult32 : nullptr, lv.ncoef, 0, ch.tc_kc, lv.tc_np, lv.tc_nb, lv.tc_nbw, lv.tc_amma, lv.tc_asc, lv.tc_kc,
-               lv.tc_mmaxsteps};
+               lv.tc_mmaxsteps, false};
     return launch_tc(P, a, nrhs, st);
 }
 
 // Tensor-core downward pass of level l; writes the FP32 local expansions when
-// fp32_out (the leaves, for L2P) and, below the leaves, their MMA-ready copy
-// for the children's L2L.
-hfmm_status launch_m2l_tc(hfmm_plan_s* P, int l, int nrhs, bool fp32_out, cudaStream_t st) {
+// fp32_out (the leaves, for a separate L2P), below the leaves their MMA-ready
+// copy for the children's L2L, and at the leaves, when l2p (P->tc_l2p), adds
+// the L2P of every leaf to y32 from the epilogue.
+hfmm_status launch_m2l_tc(hfmm_plan_s* P, int l, int nrhs, bool fp32_out, bool l2p, cudaStream_t st) {
     LevelInfo& lv = P->lev[l];
     const bool below = l < P->L;
     const bool has_parent = l > P->lmin;
@@ -774,6 +860,6 @@ hfmm_status launch_m2l_tc(hfmm_plan_s* P, int l, int nrhs, bool fp32_out, cudaSt
                lv.tc_sreact, lv.tc_sl2l, lv.tc_amma, lv.tc_asc, lv.tc_nb, lv.tc_nbw / 16, lv.tc_pmma, lv.tc_psc,
                pv ? pv->tc_nb : 1, pv ? pv->tc_nbw / 16 : 1, fp32_out ? lv.loc32 : nullptr, lv.ncoef, lv.tc_kc, lv.tc_kc2, lv.tc_np,
                lv.tc_nb, lv.tc_nbw, below ? P->lev[l + 1].tc_pmma : nullptr, below ? P->lev[l + 1].tc_psc : nullptr,
-               below ? P->lev[l + 1].tc_kc2 : 0, lv.tc_maxsteps};
+               below ? P->lev[l + 1].tc_kc2 : 0, lv.tc_maxsteps, l2p && l == P->L};
     return launch_tc(P, a, nrhs, st);
 }

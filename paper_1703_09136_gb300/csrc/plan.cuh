@@ -164,6 +164,7 @@ struct hfmm_plan_s {
     void* dj_segs = nullptr;
     int64_t dj_njobs = 0;
     bool tc_on = false;             // every level lmin..L has tensor-core M2M / downward state
+    bool tc_l2p = false;            // leaf L2P fused into the tensor-core downward epilogue
     int* tc_err = nullptr;          // set by the tensor-core pass when a bounded wait gave up
     __half* tc_zero = nullptr;      // 4 KB of zeros: the A half of a missing source box
     float* tc_part = nullptr;       // partial sums of split launches (levels with few tiles)
@@ -229,7 +230,7 @@ hfmm_status build_p2p_tc(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status launch_p2p_tc(hfmm_plan_s* P, int nrhs, bool near, bool far, cudaStream_t st);
 // m2l_tc.cu
 hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st);
-hfmm_status launch_m2l_tc(hfmm_plan_s* P, int l, int nrhs, bool fp32_out, cudaStream_t st);
+hfmm_status launch_m2l_tc(hfmm_plan_s* P, int l, int nrhs, bool fp32_out, bool l2p, cudaStream_t st);
 hfmm_status launch_m2m_tc(hfmm_plan_s* P, int l, int nrhs, bool fp32_out, cudaStream_t st);
 
 // Morton helpers
