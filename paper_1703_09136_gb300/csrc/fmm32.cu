@@ -110,9 +110,13 @@ constexpr int TP_PER = TP_PTS * TP_PTS / TP_THREADS;   // elements per thread an
 
 // Each pass moves a 64 x 64 tile: all loads of a thread are issued before its
 // shared-memory stores (16 independent 8-byte loads in flight per thread).
+// With qmax given, also the largest |Re q|, |Im q| of every right-hand side
+// (float bits, an integer max: the values are non-negative; qmax zeroed before).
 __global__ void __launch_bounds__(TP_THREADS) gather_q32(const cf* __restrict__ q, const int32_t* __restrict__ iperm,
-                                                         int64_t n, int nrhs, bool conj_in, cf* __restrict__ qs) {
+                                                         int64_t n, int nrhs, bool conj_in, cf* __restrict__ qs,
+                                                         unsigned* __restrict__ qmax) {
     __shared__ cf T[TP_PTS][TP_PTS + 1];
+    __shared__ unsigned smax[TP_PTS];
     const int64_t j0 = (int64_t)blockIdx.x * TP_PTS;
     const int jn = (int)min((int64_t)TP_PTS, n - j0);
     for (int r0 = 0; r0 < nrhs; r0 += TP_PTS) {
@@ -123,17 +127,28 @@ __global__ void __launch_bounds__(TP_THREADS) gather_q32(const cf* __restrict__ 
             const int e = threadIdx.x + u * TP_THREADS, rr = e / TP_PTS, jj = e % TP_PTS;
             v[u] = (rr < rn && jj < jn) ? q[(int64_t)(r0 + rr) * n + j0 + jj] : cfmk(0.f, 0.f);
         }
-        __syncthreads();   // the previous pass has read T
+        __syncthreads();   // the previous pass has read T and smax
+        if (qmax && threadIdx.x < TP_PTS) smax[threadIdx.x] = 0u;
+        __syncthreads();
 #pragma unroll
         for (int u = 0; u < TP_PER; ++u) {
             const int e = threadIdx.x + u * TP_THREADS, rr = e / TP_PTS, jj = e % TP_PTS;
             T[jj][rr] = conj_in ? cfmk(v[u].x, -v[u].y) : v[u];
         }
         __syncthreads();
+        // every element of a thread below has right-hand side threadIdx.x % 64
+        float m = 0.0f;
 #pragma unroll
         for (int u = 0; u < TP_PER; ++u) {
             const int e = threadIdx.x + u * TP_THREADS, jj = e / TP_PTS, rr = e % TP_PTS;
-            if (jj < jn && rr < rn) qs[(int64_t)iperm[j0 + jj] * nrhs + r0 + rr] = T[jj][rr];
+            const cf w = T[jj][rr];
+            m = fmaxf(m, fmaxf(fabsf(w.x), fabsf(w.y)));
+            if (jj < jn && rr < rn) qs[(int64_t)iperm[j0 + jj] * nrhs + r0 + rr] = w;
+        }
+        if (qmax) {
+            if (m > 0.0f) atomicMax(&smax[threadIdx.x % TP_PTS], __float_as_uint(m));
+            __syncthreads();
+            if (threadIdx.x < rn && smax[threadIdx.x] > 0u) atomicMax(&qmax[r0 + threadIdx.x], smax[threadIdx.x]);
         }
     }
 }
@@ -471,7 +486,7 @@ __global__ void __launch_bounds__(PC_THREADS, 6) p2p32c_kernel(const int32_t* lb
 // streamed in chunks of 32 (strengths [j][r], basis [j][m] in shared memory).
 template <int NTH>
 __device__ __forceinline__ void p2m_pass(PcShared& S, const cf* qs, const cf* basis, int64_t n, int nrhs, int r0,
-                                         int32_t lo, int32_t hi, int nc, int m0, int w, cf* out) {
+                                         int32_t lo, int32_t hi, int nc, int m0, int w, cf* out, bool write_out) {
     const int tid = threadIdx.x;
     const int r = tid & (PC_RHS - 1), half = tid >> 6;
     const int tb = half * NTH;
@@ -497,10 +512,11 @@ __device__ __forceinline__ void p2m_pass(PcShared& S, const cf* qs, const cf* ba
     for (int i = 0; i < NTH; ++i)
         if (tb + i < w) S.q[tb + i][r] = acc[i];
     __syncthreads();
-    for (int e = tid; e < w * PC_RHS; e += PC_THREADS) {
-        const int rr = e / w, t = e - rr * w;
-        if (r0 + rr < nrhs) out[(int64_t)(r0 + rr) * nc + m0 + t] = S.q[t][rr];
-    }
+    if (write_out)
+        for (int e = tid; e < w * PC_RHS; e += PC_THREADS) {
+            const int rr = e / w, t = e - rr * w;
+            if (r0 + rr < nrhs) out[(int64_t)(r0 + rr) * nc + m0 + t] = S.q[t][rr];
+        }
 }
 
 // Writes mult[b] and, when amma is given, its MMA-ready copy for the
@@ -509,21 +525,27 @@ __device__ __forceinline__ void p2m_pass(PcShared& S, const cf* qs, const cf* ba
 // per K chunk, every (row, column block
 // of sblk chunks) scaled by the power of two 2^e that puts its largest entry
 // in [2^14, 2^15), with 2^-e stored in asc[((b * nrc + rc) * nsb + block) * 64 + row].
+// mult is written when write_mult (the SIMT passes read it) or when nc > 32
+// (the MMA-ready copy is then built from it); otherwise the MMA-ready copy is
+// built from the pass's shared-memory staging.
 __global__ void __launch_bounds__(PC_THREADS) p2m32c_kernel(const int32_t* lb, const cf* qs, const cf* basis,
                                                             int64_t n, int nrhs, int nc, cf* mult, __half* amma,
-                                                            float* asc, int kc, int nrc, int nsb, int sblk) {
+                                                            float* asc, int kc, int nrc, int nsb, int sblk,
+                                                            bool write_mult) {
     __shared__ PcShared S;
     __shared__ int s_e[16][PC_RHS];   // [column block][row]: consecutive rows in consecutive banks
     const int64_t b = blockIdx.x;
     const int32_t lo = lb[b], hi = lb[b + 1];
     cf* out = mult + (int64_t)b * nrhs * nc;
+    const bool from_smem = amma && nc <= PC_TGT;   // one pass: all coefficients staged in S.q
+    const bool wo = write_mult || !from_smem;
     for (int r0 = 0; r0 < nrhs; r0 += PC_RHS) {
         for (int m0 = 0; m0 < nc; m0 += PC_TGT) {
             const int w = min(PC_TGT, nc - m0);
-            if (w <= 8) p2m_pass<4>(S, qs, basis, n, nrhs, r0, lo, hi, nc, m0, w, out);
-            else if (w <= 16) p2m_pass<8>(S, qs, basis, n, nrhs, r0, lo, hi, nc, m0, w, out);
-            else if (w <= 24) p2m_pass<12>(S, qs, basis, n, nrhs, r0, lo, hi, nc, m0, w, out);
-            else p2m_pass<16>(S, qs, basis, n, nrhs, r0, lo, hi, nc, m0, w, out);
+            if (w <= 8) p2m_pass<4>(S, qs, basis, n, nrhs, r0, lo, hi, nc, m0, w, out, wo);
+            else if (w <= 16) p2m_pass<8>(S, qs, basis, n, nrhs, r0, lo, hi, nc, m0, w, out, wo);
+            else if (w <= 24) p2m_pass<12>(S, qs, basis, n, nrhs, r0, lo, hi, nc, m0, w, out, wo);
+            else p2m_pass<16>(S, qs, basis, n, nrhs, r0, lo, hi, nc, m0, w, out, wo);
         }
         if (amma) {
             __syncthreads();   // this block's rows of mult are written
@@ -535,7 +557,9 @@ __global__ void __launch_bounds__(PC_THREADS) p2m32c_kernel(const int32_t* lb, c
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
                     const int k = c * 16 + u;
-                    v[u] = !live || k >= 2 * nc ? 0.0f : (k < nc ? row[2 * k] : row[2 * (k - nc) + 1]);
+                    if (!live || k >= 2 * nc) v[u] = 0.0f;
+                    else if (from_smem) v[u] = k < nc ? S.q[k][r].x : S.q[k - nc][r].y;
+                    else v[u] = k < nc ? row[2 * k] : row[2 * (k - nc) + 1];
                 }
             };
             // largest |entry| of every (row, column block), by integer max of the float bits
@@ -636,9 +660,16 @@ hfmm_status init_h0_table(cudaStream_t st) {
 // computed exactly as in the SIMT near-field kernel; for an L2P chunk
 // (i/4) conj(basis[t][8 kk + j]).  Stored as (Re g, -Im g), TF32 hi and lo, in
 // the core-matrix layout of a rows x 16 tile.
+// Pre-split B tiles of the tensor-core near field: row n = the n-th padded
+// target of the chunk's adjacent leaves, K pair j = source point j of the
+// chunk, entries (Re G, -Im G) of G = (i/4) H0(k r) times 2^NT_GSCALE_EXP,
+// split into f16 hi / lo in the no-swizzle core-matrix layout (half offset
+// ((n / 8) * 2 + k / 8) * 64 + (n % 8) * 8 + k % 8; lo after rows * 16 halves).
+// |G| stays below 2^5 for any two distinct FP32 points (|H0(z)| reaches 128
+// only for z near 1e-80), so the scaled entries stay below the f16 range.
 __global__ void near_tiles_kernel(const NtChunk* __restrict__ chunks, const int64_t* __restrict__ row0, int64_t nch,
                                   int64_t total, const int32_t* __restrict__ lb, int L, const float2* __restrict__ xl,
-                                  const cf* __restrict__ basis, int nc, float k, float h, float* __restrict__ tiles) {
+                                  float k, float h, __half* __restrict__ tiles) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total * 8;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t gr = e >> 3;
@@ -665,38 +696,31 @@ __global__ void near_tiles_kernel(const NtChunk* __restrict__ chunks, const int6
         cf g = cfmk(0.f, 0.f);
         if (c < 4 && t < tn) {
             const int32_t ti = tlo + t;
-            if (ch.src >= 0) {
-                if (j < ch.cnt && ch.src + j != ti) {
-                    const int32_t si = ch.src + j;
-                    // c_T - c_S in box units: target child c of the parent, source leaf code aux
-                    const float ox = (float)((c & 1) - ((ch.aux & 3) - 1)) * h;
-                    const float oy = (float)((c >> 1) - ((ch.aux >> 2) - 1)) * h;
-                    const float ddx = ox + (xl[ti].x - xl[si].x);
-                    const float ddy = oy + (xl[ti].y - xl[si].y);
-                    const float z = k * sqrtf(ddx * ddx + ddy * ddy);
-                    if (z < H0_ZMAX) {
-                        g = green_free_f32(z);
-                    } else {
-                        const cd h0 = hankel0((double)z);
-                        g = cfmk((float)(-0.25 * h0.y), (float)(0.25 * h0.x));
-                    }
-                }
-            } else {
-                const int mm = 8 * ch.cnt + j;
-                if (mm < nc) {
-                    const cf bb = basis[(int64_t)ti * nc + mm];
-                    g = cfmk(0.25f * bb.y, 0.25f * bb.x);
+            if (j < ch.cnt && ch.src + j != ti) {
+                const int32_t si = ch.src + j;
+                // c_T - c_S in box units: target child c of the parent, source leaf code aux
+                const float ox = (float)((c & 1) - ((ch.aux & 3) - 1)) * h;
+                const float oy = (float)((c >> 1) - ((ch.aux >> 2) - 1)) * h;
+                const float ddx = ox + (xl[ti].x - xl[si].x);
+                const float ddy = oy + (xl[ti].y - xl[si].y);
+                const float z = k * sqrtf(ddx * ddx + ddy * ddy);
+                if (z < H0_ZMAX) {
+                    g = green_free_f32(z);
+                } else {
+                    const cd h0 = hankel0((double)z);
+                    g = cfmk((float)(-0.25 * h0.y), (float)(0.25 * h0.x));
                 }
             }
         }
-        const float re = g.x, im = -g.y;
-        const float reh = __uint_as_float(f32_to_tf32(re)), imh = __uint_as_float(f32_to_tf32(im));
-        const float rel = __uint_as_float(f32_to_tf32(re - reh)), iml = __uint_as_float(f32_to_tf32(im - imh));
+        const float sc = (float)(1 << NT_GSCALE_EXP);
+        uint16_t reh, rel, imh, iml;
+        tc::split_f16(g.x * sc, reh, rel);
+        tc::split_f16(-g.y * sc, imh, iml);
         const int k0 = 2 * j;
-        const int64_t o = ((n >> 3) * 4 + (k0 >> 2)) * 32 + (n & 7) * 4 + (k0 & 3);
-        float* tile = tiles + ch.boff;
-        *(float2*)(tile + o) = make_float2(reh, imh);
-        *(float2*)(tile + (int64_t)ch.rows * 16 + o) = make_float2(rel, iml);
+        const int64_t o = ((n >> 3) * 2 + (k0 >> 3)) * 64 + (n & 7) * 8 + (k0 & 7);
+        uint16_t* tile = (uint16_t*)tiles + ch.boff;
+        *(uint32_t*)(tile + o) = (uint32_t)reh | ((uint32_t)imh << 16);
+        *(uint32_t*)(tile + (int64_t)ch.rows * 16 + o) = (uint32_t)rel | ((uint32_t)iml << 16);
     }
 }
 
@@ -713,8 +737,7 @@ hfmm_status fill_near_tiles(hfmm_plan_s* P, int64_t nchunks, int64_t total_rows,
     if (e == cudaSuccess) {
         const LevelInfo& lv = P->lev[P->L];
         near_tiles_kernel<<<8 * 152, 256, 0, st>>>(P->nt_chunks, d_r0, nchunks, total_rows, P->leaf_begin, P->L,
-                                                    P->xl32, P->basis32, lv.ncoef, (float)P->k, (float)lv.h,
-                                                    P->nt_tiles);
+                                                    P->xl32, (float)P->k, (float)lv.h, P->nt_tiles);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
@@ -777,7 +800,8 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
     const double MAC = 8.0 * nrhs;
     tm.begin(HFMM_STAGE_GATHER);
     const unsigned ntile = (unsigned)ceil_div(n, TP_PTS);
-    gather_q32<<<ntile, TP_THREADS, 0, st>>>(q, P->iperm32, n, nrhs, adjoint, P->q32);
+    if (P->qmax) HFMM_CUDA_TRY(cudaMemsetAsync(P->qmax, 0, sizeof(unsigned) * nrhs, st));
+    gather_q32<<<ntile, TP_THREADS, 0, st>>>(q, P->iperm32, n, nrhs, adjoint, P->q32, P->qmax);
     ++P->launches;
     HFMM_CUDA_TRY(cudaMemsetAsync(P->y32, 0, sizeof(cf) * n * nrhs, st));
     tm.end(HFMM_STAGE_GATHER);
@@ -789,13 +813,23 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
         const LevelInfo& lv = P->lev[L];
         tm.begin(HFMM_STAGE_P2P);
         if (P->tc_on) {
-            // tensor-core blocks of four leaves; SIMT kernel for the leaves of wider blocks
-            HFMM_TRY(launch_p2p_tc(P, nrhs, near, l2p, st));
-            ++P->launches;
-            if (P->nt_nfallback > 0) {
+            // P2P: tensor-core blocks of four leaves (first writer of their targets), SIMT
+            // kernel for the leaves of wider blocks; a separate L2P on the SIMT kernel
+            if (near) {
+                HFMM_TRY(launch_p2p_tc(P, nrhs, st));
+                ++P->launches;
+            }
+            if (P->nt_nfallback > 0 && (near || l2p)) {
                 p2p32c_kernel<<<(unsigned)P->nt_nfallback, PC_THREADS, 0, st>>>(
                     P->leaf_begin, L, P->xl32, P->q32, n, nrhs, (float)P->k, (float)lv.h, near ? 1 : 0,
                     l2p ? lv.loc32 : nullptr, P->basis32, lv.ncoef, P->nt_fallback, P->y32);
+                ++P->launches;
+                HFMM_CUDA_TRY(cudaGetLastError());
+            }
+            if (l2p && P->nt_nblocks > 0) {
+                p2p32c_kernel<<<(unsigned)P->nt_nleaves, PC_THREADS, 0, st>>>(
+                    P->leaf_begin, L, P->xl32, P->q32, n, nrhs, (float)P->k, (float)lv.h, 0, lv.loc32, P->basis32,
+                    lv.ncoef, P->nt_leaves, P->y32);
                 ++P->launches;
                 HFMM_CUDA_TRY(cudaGetLastError());
             }
@@ -826,7 +860,7 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
             const int nrc = (P->max_rhs + 63) / 64;
             p2m32c_kernel<<<(unsigned)lv.nbox, PC_THREADS, 0, st>>>(
                 P->leaf_begin, P->q32, P->basis32, n, nrhs, lv.ncoef, lv.mult32, P->tc_on ? lv.tc_amma : nullptr,
-                lv.tc_asc, lv.tc_kc, nrc, lv.tc_nb, lv.tc_nbw / 16);
+                lv.tc_asc, lv.tc_kc, nrc, lv.tc_nb, lv.tc_nbw / 16, !tc_down);
             ++P->launches;
             HFMM_CUDA_TRY(cudaGetLastError());
             tm.end(HFMM_STAGE_P2M);

@@ -1,6 +1,6 @@
 // Near field of the mixed path on tensor cores (tcgen05, sm_103a): the
-// free-space P2P sum (Algorithm 1, step 5) and the L2P evaluation (step 4) of
-// the four leaves of one parent box (a block), as one real GEMM per CTA.
+// free-space P2P sum (Algorithm 1, step 5) of the four leaves of one parent
+// box (a block), as one real GEMM per CTA.
 //
 // With rows = (right-hand side r, part) (part 0: real, 1: imaginary; M = 128
 // for 64 right-hand sides), columns = the block's targets (each leaf padded to
@@ -11,18 +11,20 @@
 // so the A rows are (Re q, Im q) and (Im q, -Re q) and the B rows
 // (Re G, -Im G).  The points are fixed, so the B tiles (G = (i/4) H0(k r) of
 // each 8-source chunk of each source leaf of the 4 x 4 neighbourhood against
-// the adjacent target leaves only, and (i/4) conj(basis) of each leaf's L2P)
-// are computed once per plan, pre-split into TF32 hi / lo in the core-matrix
-// layout (fmm32.cu, near_tiles_kernel).  Per apply, warp 4 streams the tiles
-// with cp.async.bulk (prefetched into L2 a few chunks ahead); warps 0-3 build the A rows of each chunk from the
-// strengths (or the leaf's local coefficients) in shared memory; warp 5 issues
-// one 3xTF32 MMA set (hi*hi + hi*lo + lo*hi) per run of adjacent target leaves
-// into one 128-column TMEM accumulator; warps 0-3 finally store y
-// (point-major, [n][nrhs]; the kernel is the first writer of its targets).
-// One accumulator, a two-stage ring and at most 128 chunk records keep a CTA
-// within a third of the SM: the pass is paced by each CTA's chain of tile
-// copy, operand build and MMA, so three CTAs per SM beat deeper buffering.
-// Every mbarrier wait is bounded.
+// the adjacent target leaves only) are computed once per plan, scaled by
+// 2^NT_GSCALE_EXP and pre-split into f16 hi / lo in the core-matrix layout
+// (fmm32.cu, near_tiles_kernel).  Per apply, warp 4 streams the tiles with
+// cp.async.bulk (prefetched into L2 a few chunks ahead); warps 0-3 build the
+// A rows of each chunk from the strengths, each right-hand side scaled by the
+// power of two that puts its largest |Re q|, |Im q| (reduced by the gather
+// kernel) in [2^14, 2^15), and split into f16 hi / lo; warp 5 issues three
+// kind::f16 MMAs (hi*hi + hi*lo + lo*hi: 22 significant bits, like a TF32
+// pair) per run of adjacent target leaves into one 128-column TMEM
+// accumulator; warps 0-3 finally undo both scales and store y (point-major,
+// [n][nrhs]; the kernel is the first writer of its targets).  The pass is
+// paced by each CTA's chain of tile copy, operand build and MMA: one
+// accumulator, 16 KB stages and at most 128 chunk records fit four CTAs per
+// SM.  Every mbarrier wait is bounded.
 #include <algorithm>
 #include <vector>
 
@@ -36,34 +38,31 @@ using namespace tc;
 constexpr int NT_THREADS = 192;    // warps 0-3 build A and drain, warp 4 TMA, warp 5 MMA
 constexpr int NT_STAGES = 2;
 constexpr int NT_MAXN = 128;       // padded targets of a block
-constexpr int NT_A = 16384;        // A: 128 rows x 16 K, hi then lo
-constexpr int NT_B = NT_MAXN * 128;
+constexpr int NT_A = 8192;         // A: 128 rows x 16 K halves, hi then lo
+constexpr int NT_B = NT_MAXN * 64;  // B: up to 128 rows x 16 K halves, hi then lo
 constexpr int NT_STAGE = NT_A + NT_B;
 constexpr int NT_MAXCH = 128;     // chunks of a block (kept in shared memory; more: SIMT kernel)
 constexpr int NT_PREF = 6;         // tiles brought into L2 ahead of their copy
 constexpr size_t NT_SMEM = (size_t)NT_STAGES * NT_STAGE + 1024;
 
-// float offset of (row, k) in a core-matrix tile (K = 16)
+// half offset of (row, k) in a core-matrix tile (K = 16)
 __device__ __forceinline__ int core_off(int row, int k) {
-    return ((row >> 3) * 4 + (k >> 2)) * 32 + (row & 7) * 4 + (k & 3);
+    return ((row >> 3) * 2 + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
 }
 
-__device__ __forceinline__ void split2(float x, float& h, float& l) {
-    h = __uint_as_float(tf32_rna(x));
-    l = __uint_as_float(tf32_rna(x - h));
-}
-
-// A operand: the complex value v of (K pair j, right-hand side r) into rows r
-// (Re v, Im v) and 64 + r (Im v, -Re v), K columns 2j, 2j + 1, hi and lo parts.
-__device__ __forceinline__ void put_a(float* A, int j, int r, cf v) {
-    float rh, rl, ih, il;
-    split2(v.x, rh, rl);
-    split2(v.y, ih, il);
+// A operand: the complex value v (already scaled) of (K pair j, right-hand
+// side r) into rows r (Re v, Im v) and 64 + r (Im v, -Re v), K columns 2j,
+// 2j + 1, f16 hi and lo parts (lo 2048 halves after hi).
+__device__ __forceinline__ void put_a(uint16_t* A, int j, int r, cf v) {
+    uint16_t rh, rl, ih, il, nrh, nrl;
+    split_f16(v.x, rh, rl);
+    split_f16(v.y, ih, il);
+    split_f16(-v.x, nrh, nrl);
     const int o0 = core_off(r, 2 * j), o1 = core_off(64 + r, 2 * j);
-    *(float2*)(A + o0) = make_float2(rh, ih);
-    *(float2*)(A + 2048 + o0) = make_float2(rl, il);
-    *(float2*)(A + o1) = make_float2(ih, -rh);
-    *(float2*)(A + 2048 + o1) = make_float2(il, -rl);
+    *(uint32_t*)(A + o0) = (uint32_t)rh | ((uint32_t)ih << 16);
+    *(uint32_t*)(A + 2048 + o0) = (uint32_t)rl | ((uint32_t)il << 16);
+    *(uint32_t*)(A + o1) = (uint32_t)ih | ((uint32_t)nrh << 16);
+    *(uint32_t*)(A + 2048 + o1) = (uint32_t)il | ((uint32_t)nrl << 16);
 }
 
 struct NtSmall {
@@ -72,10 +71,10 @@ struct NtSmall {
     int32_t off[5], wid[4], lbox[4];
 };
 
-__global__ void __launch_bounds__(NT_THREADS, 3) p2p_tc_kernel(
-    const int32_t* __restrict__ blocks, const NtChunk* __restrict__ chunks, const float* __restrict__ tiles,
-    const int32_t* __restrict__ lb, const cf* __restrict__ qs, int nrhs, int near, int far, const cf* __restrict__ loc,
-    int nc, cf* __restrict__ ys, int* err) {
+__global__ void __launch_bounds__(NT_THREADS, 4) p2p_tc_kernel(
+    const int32_t* __restrict__ blocks, const NtChunk* __restrict__ chunks, const __half* __restrict__ tiles,
+    const int32_t* __restrict__ lb, const cf* __restrict__ qs, int nrhs, const unsigned* __restrict__ qmax,
+    cf* __restrict__ ys, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ NtSmall S;
     __shared__ uint64_t afull[NT_STAGES], bfull[NT_STAGES], empty[NT_STAGES], done;
@@ -83,8 +82,8 @@ __global__ void __launch_bounds__(NT_THREADS, 3) p2p_tc_kernel(
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t P = blocks[4 * blockIdx.x];
-    const int cb = near ? blocks[4 * blockIdx.x + 1] : blocks[4 * blockIdx.x + 2];
-    const int ce = far ? blocks[4 * blockIdx.x + 3] : blocks[4 * blockIdx.x + 2];
+    const int cb = blocks[4 * blockIdx.x + 1];
+    const int ce = blocks[4 * blockIdx.x + 2];
     const int nch = ce - cb;
     const int rc = blockIdx.y, r0 = rc * 64;
     if (tid == 0) {
@@ -140,26 +139,22 @@ __global__ void __launch_bounds__(NT_THREADS, 3) p2p_tc_kernel(
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (warp < 4) {
-        // ---------------- A rows: strengths of the chunk's sources (or the leaf's locals) ----------------
+        // ---------------- A rows: scaled strengths of the chunk's sources ----------------
+        // the power of two of each right-hand side (rows r and 64 + r share it)
+        const int rr_own = tid & 63;
+        const int e_own = (r0 + rr_own < nrhs) ? f16_exp(__uint_as_float(qmax[r0 + rr_own])) : 0;
         auto fetch = [&](int i, cf* out) {
             const NtChunk& ch = S.ch[i];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int e = tid + 128 * u, j = e >> 6, r = e & 63;
                 cf v = cfmk(0.f, 0.f);
-                if (r0 + r < nrhs) {
-                    if (ch.src >= 0) {
-                        if (j < ch.cnt) v = qs[(int64_t)(ch.src + j) * nrhs + r0 + r];
-                    } else {
-                        const int mm = 8 * ch.cnt + j;
-                        int c = 0;
-                        while (!(ch.mask >> c & 1)) ++c;
-                        if (mm < nc) v = loc[((int64_t)S.lbox[c] * nrhs + r0 + r) * nc + mm];
-                    }
-                }
+                if (r0 + r < nrhs && j < ch.cnt) v = qs[(int64_t)(ch.src + j) * nrhs + r0 + r];
                 out[u] = v;
             }
         };
+        // thread (u, tid) always handles right-hand side tid & 63: one scale per thread
+        const float qs_scale = pow2f(e_own);
         // strengths two chunks ahead: pa = chunk i, pb = chunk i + 1
         cf pa[4], pb[4], pn[4];
         if (nch > 0) fetch(0, pa);
@@ -170,11 +165,11 @@ __global__ void __launch_bounds__(NT_THREADS, 3) p2p_tc_kernel(
             good = __all_sync(0xffffffffu, good);
             if (!good) { s_abort = 1; break; }
             if (i + 2 < nch) fetch(i + 2, pn);
-            float* A = (float*)(smem + stg * NT_STAGE);
+            uint16_t* A = (uint16_t*)(smem + stg * NT_STAGE);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int e = tid + 128 * u;
-                put_a(A, e >> 6, e & 63, pa[u]);
+                put_a(A, e >> 6, e & 63, cfmk(pa[u].x * qs_scale, pa[u].y * qs_scale));
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(&afull[stg]);
@@ -191,6 +186,7 @@ __global__ void __launch_bounds__(NT_THREADS, 3) p2p_tc_kernel(
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int row = tid;
             const uint32_t tl = taddr + ((uint32_t)(warp * 32) << 16);
+            const float unscale = pow2f(-(e_own + NT_GSCALE_EXP));   // row r or 64 + r: right-hand side tid & 63
             float* stg0 = (float*)smem;   // stage 0 is free now
             for (int g0 = 0; g0 < N; g0 += 16) {
                 uint32_t w0[16];
@@ -201,7 +197,7 @@ __global__ void __launch_bounds__(NT_THREADS, 3) p2p_tc_kernel(
                              : "r"(tl + (uint32_t)g0));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int u = 0; u < 16; ++u) stg0[u * 128 + row] = __uint_as_float(w0[u]);
+                for (int u = 0; u < 16; ++u) stg0[u * 128 + row] = __uint_as_float(w0[u]) * unscale;
                 asm volatile("bar.sync 1, 128;" ::: "memory");
 #pragma unroll
                 for (int qq = 0; qq < 8; ++qq) {
@@ -216,14 +212,14 @@ __global__ void __launch_bounds__(NT_THREADS, 3) p2p_tc_kernel(
     } else if (warp == 4 && lane == 0) {
         // ---------------- TMA: the chunk's pre-split B tile (L2 prefetch NT_PREF chunks ahead) ----------------
         for (int i = 0; i < min(nch, NT_PREF); ++i)
-            bulk_prefetch_l2(tiles + S.ch[i].boff, (uint32_t)S.ch[i].rows * 128u);
+            bulk_prefetch_l2(tiles + S.ch[i].boff, (uint32_t)S.ch[i].rows * 64u);
         for (int i = 0; i < nch; ++i) {
             if (i + NT_PREF < nch)
-                bulk_prefetch_l2(tiles + S.ch[i + NT_PREF].boff, (uint32_t)S.ch[i + NT_PREF].rows * 128u);
+                bulk_prefetch_l2(tiles + S.ch[i + NT_PREF].boff, (uint32_t)S.ch[i + NT_PREF].rows * 64u);
             const int stg = i % NT_STAGES;
             if (s_abort || !mbar_wait(&empty[stg], (uint32_t)(((i / NT_STAGES) & 1) ^ 1))) { s_abort = 1; break; }
             const NtChunk& ch = S.ch[i];
-            const uint32_t bytes = (uint32_t)ch.rows * 128u;
+            const uint32_t bytes = (uint32_t)ch.rows * 64u;
             mbar_arrive_tx(&bfull[stg], bytes);
             bulk_g2s(smem + stg * NT_STAGE + NT_A, tiles + ch.boff, bytes, &bfull[stg]);
         }
@@ -236,22 +232,18 @@ __global__ void __launch_bounds__(NT_THREADS, 3) p2p_tc_kernel(
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const NtChunk& ch = S.ch[i];
             const uint32_t sa = su32(smem + stg * NT_STAGE), sb = sa + NT_A;
-            const uint32_t lo_b = (uint32_t)ch.rows * 64u;
+            const uint32_t lo_b = (uint32_t)ch.rows * 32u;
             for (int q = 0; q < ch.nrun; ++q) {
                 const int rw = ch.run[q];
                 const int nn = rw & 0xff, col = (rw >> 8) & 0xff, rowoff = rw >> 16;
-                const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nn >> 3) << 17) |
-                                       ((128u >> 4) << 24);
-                const uint32_t bro = (uint32_t)rowoff * 64u;
-#pragma unroll
-                for (int ks = 0; ks < 2; ++ks) {
-                    const uint64_t ah = sdesc(sa + ks * 256), al = sdesc(sa + 8192 + ks * 256);
-                    const uint64_t bh = sdesc(sb + bro + ks * 256), bl = sdesc(sb + lo_b + bro + ks * 256);
-                    const uint32_t d = taddr + (uint32_t)col;
-                    mma_tf32(d, ah, bh, idesc, 1u);
-                    mma_tf32(d, ah, bl, idesc, 1u);
-                    mma_tf32(d, al, bh, idesc, 1u);
-                }
+                const uint32_t idesc = idesc_f16(nn);
+                const uint32_t bro = (uint32_t)rowoff * 32u;
+                const uint64_t ah = sdesc(sa, 256), al = sdesc(sa + 4096, 256);
+                const uint64_t bh = sdesc(sb + bro, 256), bl = sdesc(sb + lo_b + bro, 256);
+                const uint32_t d = taddr + (uint32_t)col;
+                mma_f16(d, ah, bh, idesc, 1u);
+                mma_f16(d, ah, bl, idesc, 1u);
+                mma_f16(d, al, bh, idesc, 1u);
             }
             mma_commit(&empty[stg]);
         }
@@ -265,17 +257,15 @@ __global__ void __launch_bounds__(NT_THREADS, 3) p2p_tc_kernel(
 }  // namespace
 
 // Plan time: blocks (parent boxes of level L - 1) whose padded targets fit
-// NT_MAXN, their chunks (source chunks, then L2P chunks) and tile store; the
-// leaves of the other blocks are left to the SIMT kernel.
+// NT_MAXN, their source chunks and tile store ([parent, first chunk, end, 0]
+// per block); the leaves of the other blocks are left to the SIMT kernel.
 hfmm_status build_p2p_tc(hfmm_plan_s* P, cudaStream_t st) {
     const int L = P->L;
     if (L < 1) return HFMM_OK;
     const auto& lb = P->h_leaf_begin;
     const int m = 1 << L;
-    const int nc = P->lev[L].ncoef;
-    const int kcl = (nc + 7) / 8;
     const int64_t npar = (int64_t)1 << (2 * (L - 1));
-    std::vector<int32_t> blocks, fallback;
+    std::vector<int32_t> blocks, fallback, leaves;
     std::vector<NtChunk> chunks;
     int64_t boff = 0, rows = 0;
     for (int64_t par = 0; par < npar; ++par) {
@@ -323,17 +313,6 @@ hfmm_status build_p2p_tc(hfmm_plan_s* P, cudaStream_t st) {
                 rows += r;
             }
         }
-        const int32_t c_l2p = (int32_t)chunks.size();
-        for (int c = 0; c < 4; ++c) {
-            if (cnt[c] == 0) continue;
-            int col = 0;
-            for (int cc = 0; cc < c; ++cc) col += wid[cc];
-            for (int kk = 0; kk < kcl; ++kk) {
-                chunks.push_back({-1, kk, 1 << c, wid[c], boff, (int32_t)par, 0, 1, {wid[c] | (col << 8), 0}, 0});
-                boff += (int64_t)wid[c] * 32;
-                rows += wid[c];
-            }
-        }
         if ((int)chunks.size() - c_begin > NT_MAXCH) {
             // too many chunks for the kernel's shared record table: SIMT kernel
             for (size_t i = c_begin; i < chunks.size(); ++i) { boff -= (int64_t)chunks[i].rows * 32; rows -= chunks[i].rows; }
@@ -342,18 +321,25 @@ hfmm_status build_p2p_tc(hfmm_plan_s* P, cudaStream_t st) {
                 if (cnt[c] > 0) fallback.push_back((int32_t)(4 * par + c));
             continue;
         }
+        for (int c = 0; c < 4; ++c)
+            if (cnt[c] > 0) leaves.push_back((int32_t)(4 * par + c));
         blocks.push_back((int32_t)par);
         blocks.push_back(c_begin);
-        blocks.push_back(c_l2p);
         blocks.push_back((int32_t)chunks.size());
+        blocks.push_back(0);
     }
     P->nt_nblocks = (int64_t)blocks.size() / 4;
     P->nt_nfallback = (int64_t)fallback.size();
+    P->nt_nleaves = (int64_t)leaves.size();
+    HFMM_TRY(plan_alloc(P, (void**)&P->nt_leaves, sizeof(int32_t) * std::max<size_t>(leaves.size(), 1)));
+    if (!leaves.empty())
+        HFMM_CUDA_TRY(cudaMemcpy(P->nt_leaves, leaves.data(), sizeof(int32_t) * leaves.size(), cudaMemcpyHostToDevice));
+    HFMM_TRY(plan_alloc(P, (void**)&P->qmax, sizeof(unsigned) * (size_t)P->max_rhs));
     HFMM_TRY(plan_alloc(P, (void**)&P->nt_blocks, sizeof(int32_t) * std::max<size_t>(blocks.size(), 4)));
     HFMM_TRY(plan_alloc(P, (void**)&P->nt_fallback, sizeof(int32_t) * std::max<size_t>(fallback.size(), 1)));
     HFMM_TRY(plan_alloc(P, (void**)&P->nt_chunks, sizeof(NtChunk) * std::max<size_t>(chunks.size(), 1)));
-    HFMM_TRY(plan_alloc(P, (void**)&P->nt_tiles, sizeof(float) * (size_t)std::max<int64_t>(boff, 32)));
-    P->table_bytes += sizeof(float) * (double)boff + sizeof(NtChunk) * (double)chunks.size();
+    HFMM_TRY(plan_alloc(P, (void**)&P->nt_tiles, sizeof(__half) * (size_t)std::max<int64_t>(boff, 32)));
+    P->table_bytes += sizeof(__half) * (double)boff + sizeof(NtChunk) * (double)chunks.size();
     if (!blocks.empty())
         HFMM_CUDA_TRY(cudaMemcpy(P->nt_blocks, blocks.data(), sizeof(int32_t) * blocks.size(), cudaMemcpyHostToDevice));
     if (!fallback.empty())
@@ -368,18 +354,16 @@ hfmm_status build_p2p_tc(hfmm_plan_s* P, cudaStream_t st) {
 
 // Launch the tensor-core near field (near: P2P chunks, far: L2P chunks) over
 // the plan's blocks; it stores y of their targets.
-hfmm_status launch_p2p_tc(hfmm_plan_s* P, int nrhs, bool near, bool far, cudaStream_t st) {
+hfmm_status launch_p2p_tc(hfmm_plan_s* P, int nrhs, cudaStream_t st) {
     if (P->nt_nblocks == 0) return HFMM_OK;
     static bool attr_set = false;
     if (!attr_set) {
         HFMM_CUDA_TRY(cudaFuncSetAttribute(p2p_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NT_SMEM));
         attr_set = true;
     }
-    const LevelInfo& lv = P->lev[P->L];
     dim3 grid((unsigned)P->nt_nblocks, (unsigned)((nrhs + 63) / 64));
     p2p_tc_kernel<<<grid, NT_THREADS, NT_SMEM, st>>>(P->nt_blocks, P->nt_chunks, P->nt_tiles, P->leaf_begin, P->q32,
-                                                     nrhs, near ? 1 : 0, far ? 1 : 0, lv.loc32, lv.ncoef, P->y32,
-                                                     P->tc_err);
+                                                     nrhs, P->qmax, P->y32, P->tc_err);
     HFMM_CUDA_TRY(cudaGetLastError());
     return HFMM_OK;
 }

@@ -84,6 +84,9 @@ struct LevelInfo {
     float* tc_psc = nullptr;
 };
 
+// Power-of-two scale of the stored near-field Green's function tiles (f16).
+constexpr int NT_GSCALE_EXP = 10;
+
 // Near field on tensor cores: one K chunk of a block (the four leaves of a
 // parent box at level L - 1).  A source chunk holds up to 8 consecutive sorted
 // points of one source leaf of the 4 x 4 neighbourhood; an L2P chunk holds
@@ -146,9 +149,12 @@ struct hfmm_plan_s {
     int32_t* nt_blocks = nullptr;
     int64_t nt_nblocks = 0;
     NtChunk* nt_chunks = nullptr;
-    float* nt_tiles = nullptr;
+    __half* nt_tiles = nullptr;     // f16 hi / lo tiles of (i/4) H0 x 2^NT_GSCALE_EXP
+    unsigned* qmax = nullptr;       // per right-hand side: largest |Re q|, |Im q| (float bits), each apply
     int32_t* nt_fallback = nullptr;
     int64_t nt_nfallback = 0;
+    int32_t* nt_leaves = nullptr;   // non-empty leaves of the tensor-core blocks (separate L2P)
+    int64_t nt_nleaves = 0;
     cf* d_vals32 = nullptr;
     float2* xl32 = nullptr;         // [n] point offsets from their own leaf centre (FP32)
     cf* basis32 = nullptr;          // [n][2 p_L + 1] scaled P2M basis of each sorted point
@@ -227,7 +233,7 @@ hfmm_status build_local_coords(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status fill_near_tiles(hfmm_plan_s* P, int64_t nchunks, int64_t total_rows, cudaStream_t st);
 // p2p_tc.cu
 hfmm_status build_p2p_tc(hfmm_plan_s* P, cudaStream_t st);
-hfmm_status launch_p2p_tc(hfmm_plan_s* P, int nrhs, bool near, bool far, cudaStream_t st);
+hfmm_status launch_p2p_tc(hfmm_plan_s* P, int nrhs, cudaStream_t st);
 // m2l_tc.cu
 hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status launch_m2l_tc(hfmm_plan_s* P, int l, int nrhs, bool fp32_out, bool l2p, cudaStream_t st);
