@@ -96,7 +96,9 @@ typedef struct {
     int32_t precision;          /* hfmm_precision */
     int32_t max_rhs;            /* largest nrhs of later apply calls (buffers sized for it) */
     int32_t flags;              /* HFMM_FLAG_* bits, 0 = none */
-    int64_t spin_limit;         /* reserved for bounded device waits, 0 = default */
+    int64_t spin_limit;         /* polls of each bounded device wait (each suspends <= ~1 us);
+                                   0 = default (2e6, about 2 s).  A wait that gives up sets
+                                   device_error; host-buffer applies then return HFMM_ERR_TIMEOUT */
 } hfmm_options;
 
 /* Option flags. */
@@ -316,6 +318,15 @@ const char* hfmm_last_error(void);
  * Used by tests to compare the library's Bessel evaluation with other
  * implementations.
  */
+/*
+ * One bounded device wait, as the tensor-core kernels wait on their
+ * mbarriers: on a barrier whose phase completes only when `arrive` is nonzero
+ * (the arrival precedes the wait).  HFMM_ERR_TIMEOUT when the wait gave up
+ * after `spin` polls (each suspends at most ~1 us), HFMM_OK when it completed.
+ * Exercises the timeout path without any fault; needs a GPU.
+ */
+hfmm_status hfmm_debug_wait_timeout(int64_t spin, int32_t arrive);
+
 hfmm_status hfmm_debug_bessel(double x, int32_t nmax, double* j, double* h);
 
 /*

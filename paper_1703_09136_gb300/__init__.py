@@ -104,7 +104,7 @@ class Plan:
     """An H-FMM plan for fixed points: y = A q with A_ij = u_{x_j}(x_i)."""
 
     def __init__(self, xy, medium, tol=1e-6, p=0, leaf_size=32, levels=0, precision=FP64,
-                 max_rhs=1, stream=None, profile=False, simt_m2l=False, autotune=False):
+                 max_rhs=1, stream=None, profile=False, simt_m2l=False, autotune=False, spin_limit=0):
         lib = _n.lib()
         m = Medium.of(medium)
         opts = _n.hfmm_options()
@@ -117,6 +117,7 @@ class Plan:
         opts.max_rhs = int(max_rhs)
         opts.flags = ((_n.FLAG_PROFILE if profile else 0) | (_n.FLAG_SIMT_M2L if simt_m2l else 0) |
                       (_n.FLAG_AUTOTUNE if autotune else 0))
+        opts.spin_limit = int(spin_limit)
         torch = _torch()
         if torch is not None and isinstance(xy, torch.Tensor):
             if xy.dtype != torch.float64:
@@ -354,3 +355,10 @@ def _make_fn():
 
 
 _MatvecFn = _make_fn()
+
+
+def debug_wait_timeout(spin, arrive):
+    """One bounded device wait of at most `spin` polls on a barrier that
+    completes only when `arrive` (hfmm_debug_wait_timeout): raises HfmmError
+    (HFMM_ERR_TIMEOUT) when the wait gave up."""
+    _n.check(_n.lib().hfmm_debug_wait_timeout(ctypes.c_int64(int(spin)), ctypes.c_int32(1 if arrive else 0)))

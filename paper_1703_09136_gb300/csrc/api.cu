@@ -11,6 +11,7 @@
 
 #include "bessel.cuh"
 #include "plan.cuh"
+#include "tcgen05.cuh"
 
 static thread_local std::string g_last_error;
 
@@ -240,6 +241,7 @@ static hfmm_status plan_create_one(hfmm_plan_t* out, int64_t n, const double* xy
         return HFMM_ERR_INVALID_ARG;
     }
     if (o.levels < 0 || o.levels > 15) { hfmm_set_error("levels must be in [0, 15]"); return HFMM_ERR_INVALID_ARG; }
+    if (o.spin_limit < 0) { hfmm_set_error("spin_limit must be >= 0"); return HFMM_ERR_INVALID_ARG; }
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t st = (cudaStream_t)stream;
     hfmm_plan_s* P = new (std::nothrow) hfmm_plan_s();
@@ -251,6 +253,7 @@ static hfmm_status plan_create_one(hfmm_plan_t* out, int64_t n, const double* xy
     P->precision = o.precision;
     P->max_rhs = o.max_rhs;
     P->flags = o.flags;
+    P->tc_spin = o.spin_limit > 0 ? (long)o.spin_limit : tc::TC_SPIN;
     P->L = o.levels > 0 ? o.levels : choose_levels(n, o.leaf_size);
     hfmm_status s = HFMM_OK;
     do {
@@ -334,6 +337,7 @@ static hfmm_status apply_common(hfmm_plan_t P, int32_t nrhs, const void* q, void
     const bool mixed = P->precision == HFMM_MIXED;
     const size_t bytes = (mixed ? sizeof(cf) : sizeof(cd)) * (size_t)P->n * nrhs;
     const bool qd = is_device_ptr(q), yd = is_device_ptr(y);
+    if (P->tc_err) HFMM_CUDA_TRY(cudaMemsetAsync(P->tc_err, 0, sizeof(int), st));   // this apply's flag
     // page-locked host buffers are used in place; other host buffers are staged
     void* qm = qd ? nullptr : mapped_host_ptr(q);
     void* ym = yd ? nullptr : mapped_host_ptr(y);
@@ -357,7 +361,17 @@ static hfmm_status apply_common(hfmm_plan_t P, int32_t nrhs, const void* q, void
     if (stage_y) {
         HFMM_CUDA_TRY(cudaMemcpyAsync(y, P->io_y, bytes, cudaMemcpyDeviceToHost, st));
     }
-    if (!qd || !yd) HFMM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!qd || !yd) {
+        HFMM_CUDA_TRY(cudaStreamSynchronize(st));
+        if (P->tc_err) {
+            int e = 0;
+            HFMM_CUDA_TRY(cudaMemcpy(&e, P->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+            if (e) {
+                hfmm_set_error("a bounded device wait gave up after %ld polls; the result is invalid", P->tc_spin);
+                return HFMM_ERR_TIMEOUT;
+            }
+        }
+    }
     return HFMM_OK;
 }
 
@@ -571,6 +585,17 @@ hfmm_status hfmm_plan_get_pairs(hfmm_plan_t P, int32_t kind, int32_t level, int3
 
 hfmm_status hfmm_plan_destroy(hfmm_plan_t plan) {
     plan_free(plan);
+    return HFMM_OK;
+}
+
+hfmm_status hfmm_debug_wait_timeout(int64_t spin, int32_t arrive) {
+    if (spin < 1) { hfmm_set_error("spin must be >= 1"); return HFMM_ERR_INVALID_ARG; }
+    int timed_out = 0;
+    HFMM_TRY(tc_wait_probe((long)spin, arrive ? 1 : 0, &timed_out));
+    if (timed_out) {
+        hfmm_set_error("bounded wait gave up after %lld polls", (long long)spin);
+        return HFMM_ERR_TIMEOUT;
+    }
     return HFMM_OK;
 }
 

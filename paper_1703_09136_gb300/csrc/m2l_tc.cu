@@ -229,9 +229,10 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
     const float* __restrict__ psc, int nsbp, int sbp, const __half* __restrict__ zero4k, cf* __restrict__ out,
     int nrhs, int nc, int kc, int kc2, int nrc, int Np, __half* __restrict__ sdst, float* __restrict__ ssc, int kcd,
     int nseg, float* __restrict__ part, const cf* __restrict__ l2p_basis, const int32_t* __restrict__ lbeg,
-    cf* __restrict__ ys, int* err) {
+    cf* __restrict__ ys, long spin, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ volatile int s_abort;
+    __shared__ uint64_t mdone;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     using CFG = TcCfg<NB>;
     constexpr int stage_bytes = CFG::stage_bytes;
@@ -256,6 +257,7 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(&dfull[b])), "r"(1));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(&dfree[b])), "r"(128));
         }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(&mdone)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
         s_abort = 0;
     }
@@ -295,7 +297,7 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
                 const float fb = st.kind == 0 ? sfree[st.idx] : st.kind == 1 ? sreact[st.idx] : ssec[st.idx];
                 f = scs[(((int64_t)src * nrc + rc) * nsb + st.c0 / sbk) * 64 + rr] * fb;
             }
-            bool good = !s_abort && mbar_wait(&dfull[b], (uint32_t)((s >> 1) & 1));
+            bool good = !s_abort && mbar_wait(&dfull[b], (uint32_t)((s >> 1) & 1), spin);
             good = __all_sync(0xffffffffu, good);
             if (!good) { ok = false; s_abort = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -423,7 +425,7 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
             for (int c = st.c0; c < st.c1; ++c, ++i) {
                 const int stg = i % TC_STAGES;
                 const uint32_t ph = (uint32_t)((i / TC_STAGES) & 1);
-                if (s_abort || !mbar_wait(&empty[stg], ph ^ 1u)) { s_abort = 1; stop = true; break; }
+                if (s_abort || !mbar_wait(&empty[stg], ph ^ 1u, spin)) { s_abort = 1; stop = true; break; }
                 unsigned char* sb = smem + stg * stage_bytes;
                 mbar_arrive_tx(&full[stg], (uint32_t)stage_bytes);
 #pragma unroll
@@ -442,6 +444,12 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
             }
             if (stop) break;
         }
+        if (s_abort) {
+            // copies still in flight land in the ring: wait for them (default bound,
+            // whatever the plan's limit) before the exit
+            for (int k = max(0, i - TC_STAGES); k < i; ++k)
+                mbar_wait(&full[k % TC_STAGES], (uint32_t)((k / TC_STAGES) & 1));
+        }
     } else if (warp == 5 && lane == 0) {
         // ---------------- MMA issuer: one TMEM buffer per source step ----------------
         constexpr uint32_t idesc = idesc_f16(NB);
@@ -452,13 +460,13 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
             const int nk = nk_next;
             if (s + 1 < nsteps) nk_next = steps[sbeg + s + 1].c1 - steps[sbeg + s + 1].c0;
             const int b = s & 1;
-            if (s_abort || !mbar_wait(&dfree[b], (uint32_t)(((s >> 1) & 1) ^ 1))) { s_abort = 1; break; }
+            if (s_abort || !mbar_wait(&dfree[b], (uint32_t)(((s >> 1) & 1) ^ 1), spin)) { s_abort = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t dt = taddr + (uint32_t)(b * CFG::buf_cols);
             for (int c = 0; c < nk; ++c, ++i) {
                 const int stg = i % TC_STAGES;
                 const uint32_t ph = (uint32_t)((i / TC_STAGES) & 1);
-                if (s_abort || !mbar_wait(&full[stg], ph)) { ok = false; s_abort = 1; break; }
+                if (s_abort || !mbar_wait(&full[stg], ph, spin)) { ok = false; s_abort = 1; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t sb = su32(smem + stg * stage_bytes);
                 const uint64_t ah = sdesc(sb, 512), al = sdesc(sb + 256, 512);
@@ -470,6 +478,9 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
             }
             if (ok) mma_commit(&dfull[b]);
         }
+        // every MMA of this thread has completed before TMEM is released
+        mma_commit(&mdone);
+        mbar_wait(&mdone, 0u);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -657,7 +668,7 @@ hfmm_status launch_nb(hfmm_plan_s* P, const TcLaunch& a, int nrhs, cudaStream_t 
     m2l_tc_kernel<NB><<<grid, TC2_THREADS, smem, st>>>(
         (const TcTile*)a.tiles, (const TcStep*)a.steps, a.Bfree, a.Breact, a.Bsec, a.sfree, a.sreact, a.ssec, a.amma,
         a.asc, a.nsba, a.sba, a.pmma, a.psc, a.nsbp, a.sbp, P->tc_zero, a.out, nrhs, a.nc, a.kc, a.kc2, nrc, a.np,
-        a.sdst, a.ssc, a.kcd, nseg, part, a.l2p ? P->basis32 : nullptr, P->leaf_begin, P->y32, P->tc_err);
+        a.sdst, a.ssc, a.kcd, nseg, part, a.l2p ? P->basis32 : nullptr, P->leaf_begin, P->y32, P->tc_spin, P->tc_err);
     HFMM_CUDA_TRY(cudaGetLastError());
     if (part) {
         const int64_t warps = a.ntiles * nrcl * a.nb * 128;
@@ -687,6 +698,32 @@ hfmm_status launch_tc(hfmm_plan_s* P, const TcLaunch& a, int nrhs, cudaStream_t 
 }
 
 }  // namespace
+
+// One bounded wait on a barrier whose phase completes only when `arrive` is
+// set (the arrival happens before the wait): out = 1 if the wait gave up.
+__global__ void tc_wait_probe_kernel(long spin, int arrive, int* out) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(tc::su32(&bar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        if (arrive) tc::mbar_arrive(&bar);
+        *out = tc::mbar_wait(&bar, 0u, spin) ? 0 : 1;
+    }
+}
+
+hfmm_status tc_wait_probe(long spin, int arrive, int* timed_out) {
+    int* d = nullptr;
+    HFMM_CUDA_TRY(cudaMalloc(&d, sizeof(int)));
+    tc_wait_probe_kernel<<<1, 32>>>(spin, arrive, d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(timed_out, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        hfmm_set_error("wait probe: %s", cudaGetErrorString(e));
+        return HFMM_ERR_CUDA;
+    }
+    return HFMM_OK;
+}
 
 // Plan-time preparation of the tensor-core upward (M2M) and downward
 // (L2L + M2L) passes of every level lmin .. L.

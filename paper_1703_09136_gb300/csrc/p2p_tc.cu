@@ -74,7 +74,7 @@ struct NtSmall {
 __global__ void __launch_bounds__(NT_THREADS, 4) p2p_tc_kernel(
     const int32_t* __restrict__ blocks, const NtChunk* __restrict__ chunks, const __half* __restrict__ tiles,
     const int32_t* __restrict__ lb, const cf* __restrict__ qs, int nrhs, const unsigned* __restrict__ qmax,
-    cf* __restrict__ ys, int* err) {
+    cf* __restrict__ ys, long spin, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ NtSmall S;
     __shared__ uint64_t afull[NT_STAGES], bfull[NT_STAGES], empty[NT_STAGES], done;
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(NT_THREADS, 4) p2p_tc_kernel(
         if (nch > 1) fetch(1, pb);
         for (int i = 0; i < nch; ++i) {
             const int stg = i % NT_STAGES;
-            bool good = !s_abort && mbar_wait(&empty[stg], (uint32_t)(((i / NT_STAGES) & 1) ^ 1));
+            bool good = !s_abort && mbar_wait(&empty[stg], (uint32_t)(((i / NT_STAGES) & 1) ^ 1), spin);
             good = __all_sync(0xffffffffu, good);
             if (!good) { s_abort = 1; break; }
             if (i + 2 < nch) fetch(i + 2, pn);
@@ -177,7 +177,9 @@ __global__ void __launch_bounds__(NT_THREADS, 4) p2p_tc_kernel(
             for (int u = 0; u < 4; ++u) { pa[u] = pb[u]; pb[u] = pn[u]; }
         }
         // ---------------- drain: store y ----------------
-        bool good = !s_abort && mbar_wait(&done, 0u);
+        // always wait (bounded) for the MMA thread's final commit: no MMA may
+        // still write the accumulator when TMEM is released
+        bool good = mbar_wait(&done, 0u) && !s_abort;   // default bound, whatever the plan's limit
         good = __all_sync(0xffffffffu, good);
         if (!good) {
             s_abort = 1;
@@ -213,22 +215,29 @@ __global__ void __launch_bounds__(NT_THREADS, 4) p2p_tc_kernel(
         // ---------------- TMA: the chunk's pre-split B tile (L2 prefetch NT_PREF chunks ahead) ----------------
         for (int i = 0; i < min(nch, NT_PREF); ++i)
             bulk_prefetch_l2(tiles + S.ch[i].boff, (uint32_t)S.ch[i].rows * 64u);
+        int issued = 0;
         for (int i = 0; i < nch; ++i) {
             if (i + NT_PREF < nch)
                 bulk_prefetch_l2(tiles + S.ch[i + NT_PREF].boff, (uint32_t)S.ch[i + NT_PREF].rows * 64u);
             const int stg = i % NT_STAGES;
-            if (s_abort || !mbar_wait(&empty[stg], (uint32_t)(((i / NT_STAGES) & 1) ^ 1))) { s_abort = 1; break; }
+            if (s_abort || !mbar_wait(&empty[stg], (uint32_t)(((i / NT_STAGES) & 1) ^ 1), spin)) { s_abort = 1; break; }
             const NtChunk& ch = S.ch[i];
             const uint32_t bytes = (uint32_t)ch.rows * 64u;
             mbar_arrive_tx(&bfull[stg], bytes);
             bulk_g2s(smem + stg * NT_STAGE + NT_A, tiles + ch.boff, bytes, &bfull[stg]);
+            issued = i + 1;
+        }
+        if (s_abort) {
+            // tiles still in flight land in the ring: wait for them (default bound) before the exit
+            for (int k = max(0, issued - NT_STAGES); k < issued; ++k)
+                mbar_wait(&bfull[k % NT_STAGES], (uint32_t)((k / NT_STAGES) & 1));
         }
     } else if (warp == 5 && lane == 0) {
         // ---------------- MMA issuer: one MMA set per run of adjacent target leaves ----------------
         for (int i = 0; i < nch; ++i) {
             const int stg = i % NT_STAGES;
             const uint32_t ph = (uint32_t)((i / NT_STAGES) & 1);
-            if (s_abort || !mbar_wait(&afull[stg], ph) || !mbar_wait(&bfull[stg], ph)) { s_abort = 1; break; }
+            if (s_abort || !mbar_wait(&afull[stg], ph, spin) || !mbar_wait(&bfull[stg], ph, spin)) { s_abort = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const NtChunk& ch = S.ch[i];
             const uint32_t sa = su32(smem + stg * NT_STAGE), sb = sa + NT_A;
@@ -363,7 +372,7 @@ hfmm_status launch_p2p_tc(hfmm_plan_s* P, int nrhs, cudaStream_t st) {
     }
     dim3 grid((unsigned)P->nt_nblocks, (unsigned)((nrhs + 63) / 64));
     p2p_tc_kernel<<<grid, NT_THREADS, NT_SMEM, st>>>(P->nt_blocks, P->nt_chunks, P->nt_tiles, P->leaf_begin, P->q32,
-                                                     nrhs, P->qmax, P->y32, P->tc_err);
+                                                     nrhs, P->qmax, P->y32, P->tc_spin, P->tc_err);
     HFMM_CUDA_TRY(cudaGetLastError());
     return HFMM_OK;
 }

@@ -172,6 +172,7 @@ struct hfmm_plan_s {
     bool tc_on = false;             // every level lmin..L has tensor-core M2M / downward state
     bool tc_l2p = false;            // leaf L2P fused into the tensor-core downward epilogue
     int* tc_err = nullptr;          // set by the tensor-core pass when a bounded wait gave up
+    long tc_spin = 0;               // polls of a bounded device wait (options.spin_limit or the default)
     __half* tc_zero = nullptr;      // 4 KB of zeros: the A half of a missing source box
     float* tc_part = nullptr;       // partial sums of split launches (levels with few tiles)
     size_t tc_part_floats = 0;
@@ -238,6 +239,7 @@ hfmm_status launch_p2p_tc(hfmm_plan_s* P, int nrhs, cudaStream_t st);
 hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status launch_m2l_tc(hfmm_plan_s* P, int l, int nrhs, bool fp32_out, bool l2p, cudaStream_t st);
 hfmm_status launch_m2m_tc(hfmm_plan_s* P, int l, int nrhs, bool fp32_out, cudaStream_t st);
+hfmm_status tc_wait_probe(long spin, int arrive, int* timed_out);
 
 // Morton helpers
 HD uint32_t spread_bits(uint32_t v) {

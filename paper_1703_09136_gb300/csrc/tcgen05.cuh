@@ -9,7 +9,13 @@
 
 namespace tc {
 
-constexpr long TC_SPIN = 20000000;     // bounded mbarrier polls
+// Bounded mbarrier waits: each poll suspends the thread until the phase
+// completes or TC_SUSPEND_NS pass (a woken thread returns at once), so
+// waiting warps leave the issue slots to the copy and MMA threads; TC_SPIN
+// polls (the default; plans may set their own) bound a wait at about 2 s,
+// after which the caller reports a timeout.
+constexpr long TC_SPIN = 2000000;
+#define TC_SUSPEND_NS "1000"
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -24,11 +30,11 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t sbo = 512) {
     return d;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long spin = TC_SPIN) {
     const uint32_t a = su32(bar);
-    for (long it = 0; it < TC_SPIN; ++it) {
+    for (long it = 0; it < spin; ++it) {
         uint32_t ok;
-        asm volatile("{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        asm volatile("{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2, " TC_SUSPEND_NS ";\n\t"
                      "selp.u32 %0, 1, 0, P;\n\t}\n" : "=r"(ok) : "r"(a), "r"(parity) : "memory");
         if (ok) return true;
     }

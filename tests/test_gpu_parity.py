@@ -171,6 +171,26 @@ def test_tiny_inputs_match_direct_sum(n):
     plan.close()
 
 
+def test_bounded_device_wait_gives_up_with_a_timeout_status():
+    """The tensor-core kernels' bounded mbarrier wait: on a barrier that
+    nothing completes it gives up after the given polls (HFMM_ERR_TIMEOUT,
+    no fault); released, it completes.  A mixed plan with an explicit bound
+    runs to completion with no device error."""
+    from paper_1703_09136_gb300 import debug_wait_timeout, MIXED
+    debug_wait_timeout(1000, arrive=True)
+    with pytest.raises(HfmmError) as e:
+        debug_wait_timeout(1000, arrive=False)
+    assert e.value.status == 6
+    med = W.WORKLOADS[5].medium
+    xy = W.points(5, 3000)
+    q = W.strengths(5, 3000, 4, salt=9).astype(np.complex64)
+    plan = Plan(xy, med, tol=1e-6, leaf_size=16, max_rhs=4, precision=MIXED, spin_limit=3_000_000)
+    ref = Plan(xy, med, tol=1e-6, leaf_size=16, max_rhs=4, precision=MIXED)
+    assert np.array_equal(plan.apply(q), ref.apply(q))
+    assert plan.info["device_error"] == 0
+    plan.close(); ref.close()
+
+
 def test_device_side_input_errors():
     med = W.WORKLOADS[1].medium
     xy = W.points(1, 50)

@@ -86,6 +86,14 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.hfmm_plan_create(ctypes.byref(h), 2, p, ctypes.byref(m), None, None) == 2
     m.kind = 7
     assert lib.hfmm_plan_create(ctypes.byref(h), 2, p, ctypes.byref(m), None, None) == 1
+    # a negative bound on device waits
+    m.kind = 0
+    m.k[1], m.k[2], m.d = 0.0, 0.0, 0.0
+    o = N.hfmm_options()
+    lib.hfmm_options_default(ctypes.byref(o))
+    o.spin_limit = -1
+    assert lib.hfmm_plan_create(ctypes.byref(h), 2, p, ctypes.byref(m), ctypes.byref(o), None) == 1
+    assert b"spin_limit" in lib.hfmm_last_error()
     # apply on a null plan
     q = np.zeros(2, dtype=np.complex128)
     assert lib.hfmm_apply(None, 1, q.ctypes.data_as(vp), q.ctypes.data_as(vp), None) == 1
