@@ -342,7 +342,8 @@ def run_reference(args):
            "value": value, "unit": "Mtargets/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic",
-           "config": {"workload": w.name, "sample_n": s["n"], "nrhs": s["nrhs"]},
+           "config": {"workload": w.name, "n": w.n, "nrhs": s["nrhs"], "medium": "three-layer k=40/80/60 d=0.5",
+                      "tol": w.tol, "sample_n": s["n"], "parallelism": "rank 0 only (CPU)"},
            "cpu_baseline": {"value": value, "unit": "Mtargets/s", "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "Mtargets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
