@@ -147,6 +147,9 @@ typedef struct {
     double tune_ms[3];          /* and the apply time measured for each */
     int64_t near_tc_blocks;     /* HFMM_MIXED: four-leaf blocks of the tensor-core near field */
     int64_t near_simt_leaves;   /*             leaves of wider blocks, on the SIMT kernel */
+    int32_t leaf_l2p_fused;     /* HFMM_MIXED: 1 if the leaves' L2P runs in the tensor-core downward
+                                   epilogue, 0 if on the SIMT kernel */
+    int32_t reserved0;
 } hfmm_plan_info;
 
 /* Bits of `parts` in hfmm_apply_parts (sum of the selected terms). */

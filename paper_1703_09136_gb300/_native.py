@@ -58,7 +58,8 @@ class hfmm_plan_info(ctypes.Structure):
                 ("flops_last_apply", ctypes.c_double * 8), ("bytes_last_apply", ctypes.c_double * 8),
                 ("device_error", ctypes.c_int32), ("tensor_levels", ctypes.c_int32),
                 ("tune_levels", ctypes.c_int32 * 3), ("tune_ms", ctypes.c_double * 3),
-                ("near_tc_blocks", ctypes.c_int64), ("near_simt_leaves", ctypes.c_int64)]
+                ("near_tc_blocks", ctypes.c_int64), ("near_simt_leaves", ctypes.c_int64),
+                ("leaf_l2p_fused", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
 hfmm_plan_t = ctypes.c_void_p

@@ -496,6 +496,7 @@ hfmm_status hfmm_plan_get_info(hfmm_plan_t P, hfmm_plan_info* info) {
         info->tune_ms[c] = P->tune_ms[c];
     }
     info->near_tc_blocks = P->nt_nblocks;
+    info->leaf_l2p_fused = P->tc_l2p ? 1 : 0;
     info->near_simt_leaves = P->nt_nfallback;
     return HFMM_OK;
 }

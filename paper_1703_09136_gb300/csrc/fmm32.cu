@@ -30,12 +30,6 @@ __constant__ float c_h0r[H0_NI][H0_DEG + 1];
 float h_h0j[H0_NI][H0_DEG + 1], h_h0r[H0_NI][H0_DEG + 1];
 bool h0_ready = false;
 
-__device__ __forceinline__ uint32_t f32_to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
 void fit_h0_table() {
     const int n = H0_DEG + 1;
     double tn[n], cheb[n][n];   // Chebyshev -> monomial coefficients
@@ -654,12 +648,6 @@ hfmm_status init_h0_table(cudaStream_t st) {
     return HFMM_OK;
 }
 
-// Plan-time B tiles of the tensor-core near field.  Thread per (chunk, tile
-// row, K pair j): for a source chunk the value (i/4) H0(k |x_t - x_s|) of the
-// row's target and the chunk's j-th source (0 for padding, for the self pair),
-// computed exactly as in the SIMT near-field kernel; for an L2P chunk
-// (i/4) conj(basis[t][8 kk + j]).  Stored as (Re g, -Im g), TF32 hi and lo, in
-// the core-matrix layout of a rows x 16 tile.
 // Pre-split B tiles of the tensor-core near field: row n = the n-th padded
 // target of the chunk's adjacent leaves, K pair j = source point j of the
 // chunk, entries (Re G, -Im G) of G = (i/4) H0(k r) times 2^NT_GSCALE_EXP,

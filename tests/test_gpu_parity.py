@@ -188,6 +188,8 @@ def test_bounded_device_wait_gives_up_with_a_timeout_status():
     ref = Plan(xy, med, tol=1e-6, leaf_size=16, max_rhs=4, precision=MIXED)
     assert np.array_equal(plan.apply(q), ref.apply(q))
     assert plan.info["device_error"] == 0
+    # few leaf tiles: split steps, so the leaves' L2P runs on the SIMT kernel
+    assert plan.info["leaf_l2p_fused"] == 0
     plan.close(); ref.close()
 
 
@@ -278,10 +280,10 @@ def test_mixed_many_rhs_and_adjoint():
 
 
 def test_tensor_core_downward_pass_matches_simt_and_fp64():
-    """tcgen05 3xTF32 M2M and downward passes (every level, wide coarse
-    levels in column blocks) against the FP32 SIMT passes (same plan
-    otherwise) and against the FP64 path, 64 right-hand sides (one full
-    M = 128 tile of two target boxes)."""
+    """tcgen05 3xF16 M2M and downward passes (every level, wide coarse
+    levels in column blocks; the leaves' L2P in the downward epilogue)
+    against the FP32 SIMT passes (same plan otherwise) and against the FP64
+    path, 64 right-hand sides (one full M = 128 tile of two target boxes)."""
     from paper_1703_09136_gb300 import MIXED
     xy = W.points_in_box(4, 8192, ((0.0, 1.0), (0.02, 1.02)))
     q = W.strengths(4, 8192, 64, salt=3)
@@ -291,6 +293,7 @@ def test_tensor_core_downward_pass_matches_simt_and_fp64():
     f64 = Plan(xy, CFG4_MED, tol=1e-6, leaf_size=16, max_rhs=4)
     assert tc.info["tensor_levels"] == tc.info["levels"] - tc.info["lmin"] + 1
     assert si.info["tensor_levels"] == 0
+    assert tc.info["leaf_l2p_fused"] == 1 and si.info["leaf_l2p_fused"] == 0
     y_tc = tc.apply(q32).cpu().numpy()
     y_si = si.apply(q32).cpu().numpy()
     y64 = f64.apply(torch.from_numpy(q[:4].copy()).cuda()).cpu().numpy()
@@ -298,7 +301,7 @@ def test_tensor_core_downward_pass_matches_simt_and_fp64():
     e_tc = direct.rel_l2(y_tc[:4], y64)
     e_si = direct.rel_l2(y_si[:4], y64)
     assert e_tc < MIXED_TOL and e_si < MIXED_TOL, (e_tc, e_si)
-    # 3xTF32 drops the lo*lo term and truncates inside TMEM between drains:
+    # 3xF16 drops the lo*lo term and truncates inside TMEM between drains:
     # a little above the SIMT FP32 error, never far above it
     assert e_tc < 2.5 * e_si, (e_tc, e_si)
     assert direct.rel_l2(y_tc, y_si) < 2.0 * (e_tc + e_si)
