@@ -275,13 +275,15 @@ class Batch:
     (hfmm_batch_*).  xys: list of [n_i, 2] float64 arrays / tensors."""
 
     def __init__(self, xys, medium, tol=1e-6, p=0, leaf_size=32, levels=0, precision=FP64, max_rhs=1,
-                 stream=None):
+                 stream=None, simt_m2l=False, spin_limit=0):
         lib = _n.lib()
         m = Medium.of(medium)
         opts = _n.hfmm_options()
         lib.hfmm_options_default(ctypes.byref(opts))
         opts.tol, opts.p, opts.leaf_size, opts.levels = float(tol), int(p), int(leaf_size), int(levels)
         opts.precision, opts.max_rhs = int(precision), int(max_rhs)
+        opts.flags = _n.FLAG_SIMT_M2L if simt_m2l else 0
+        opts.spin_limit = int(spin_limit)
         keep = [_ptr(np.ascontiguousarray(x, dtype=np.float64) if not hasattr(x, "data_ptr") else x.contiguous())
                 for x in xys]
         ns = (ctypes.c_int64 * len(xys))(*[int(x.shape[0]) for x in xys])
