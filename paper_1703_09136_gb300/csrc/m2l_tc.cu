@@ -284,19 +284,22 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
 #pragma unroll
         for (int j = 0; j < NB; ++j) acc[j] = 0.0f;
         bool ok = true;
-        for (int s = 0; s < nsteps && ok; ++s) {
-            const int b = s & 1;
-            // the step's factor 2^-(ea + eb) for this row
+        // the factor 2^-(ea + eb) of step s for this row (0 for a missing source)
+        auto factor = [&](int s) -> float {
             const TcStep st = steps[sbeg + s];
             const int src = tgt ? st.src1 : st.src0;
-            float f = 0.0f;
-            if (src >= 0) {
-                const bool sec = st.kind == 2;
-                const float* scs = sec ? psc : asc;
-                const int nsb = sec ? nsbp : nsba, sbk = sec ? sbp : sba;
-                const float fb = st.kind == 0 ? sfree[st.idx] : st.kind == 1 ? sreact[st.idx] : ssec[st.idx];
-                f = scs[(((int64_t)src * nrc + rc) * nsb + st.c0 / sbk) * 64 + rr] * fb;
-            }
+            if (src < 0) return 0.0f;
+            const bool sec = st.kind == 2;
+            const float* scs = sec ? psc : asc;
+            const int nsb = sec ? nsbp : nsba, sbk = sec ? sbp : sba;
+            const float fb = st.kind == 0 ? sfree[st.idx] : st.kind == 1 ? sreact[st.idx] : ssec[st.idx];
+            return scs[(((int64_t)src * nrc + rc) * nsb + st.c0 / sbk) * 64 + rr] * fb;
+        };
+        float f_next = nsteps > 0 ? factor(0) : 0.0f;
+        for (int s = 0; s < nsteps && ok; ++s) {
+            const int b = s & 1;
+            const float f = f_next;
+            if (s + 1 < nsteps) f_next = factor(s + 1);   // one step ahead
             bool good = !s_abort && mbar_wait(&dfull[b], (uint32_t)((s >> 1) & 1), spin);
             good = __all_sync(0xffffffffu, good);
             if (!good) { ok = false; s_abort = 1; break; }
@@ -328,79 +331,78 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
             const int box = tgt ? tile.b1 : tile.b0;   // uniform over the warp
             if (box >= 0) {
                 tc_store_row<NB>(acc, box, row, rc, cb, nbz, n0, nrhs, nc, nrc, nullptr, sdst, ssc, kcd);
-                if (TcL2p<NB>::fits && l2p_basis) {
-                    // L2P of the leaf (Algorithm 1, step 4), one column block:
-                    // y[t][r] += sum_m beta~[r][m] (i/4) conj(B[t][m]) over the leaf's points t.
-                    // In the ring (every MMA has completed; one region per warp): the warp's
-                    // 32 rows of beta~ and, per 16 points, the basis rows and the warp's rows
-                    // of y (asynchronous copies, all in flight together); the sum reads
-                    // beta~ by row and the basis as broadcasts.
-                    constexpr int TCH = TcL2p<NB>::pts, WB = TcL2p<NB>::warp_bytes;
-                    float* bet = (float*)(smem + warp * WB);
-                    cf* sbs = (cf*)(bet + 32 * (NB + 1));
-                    cf* sy = sbs + TCH * (NB / 2);
+                if ((TcL2p<NB>::fits && l2p_basis) || out) {
+                    // The warp's 32 rows of the result go to the ring once (every MMA of
+                    // this CTA has completed; one region per warp); the leaf L2P and the
+                    // FP32 store read them from there.
+                    constexpr int WS = TcL2p<NB>::fits ? TcL2p<NB>::warp_bytes : 32 * (NB + 1) * 4;
+                    static_assert(4 * WS <= TC_STAGES * stage_bytes, "staging fits the ring");
+                    float* bet = (float*)(smem + warp * WS);
 #pragma unroll
                     for (int j = 0; j < NB; ++j) bet[lane * (NB + 1) + j] = acc[j];
-                    const float* br = bet + lane * (NB + 1);   // Re beta~_m at m, Im at nc + m
-                    const int r = rc * 64 + (row & 63);
-                    const bool live = r < nrhs;
-                    const int32_t t0 = lbeg[box], t1 = lbeg[box + 1];
-                    for (int32_t tc0 = t0; tc0 < t1; tc0 += TCH) {
-                        const int tn = min(TCH, t1 - tc0);
-                        __syncwarp();
-                        for (int e = lane; e < tn * nc; e += 32) cp_async8(sbs + e, l2p_basis + (int64_t)tc0 * nc + e);
-                        if (live)
-                            for (int t = 0; t < tn; ++t) cp_async8(sy + t * 32 + lane, ys + (int64_t)(tc0 + t) * nrhs + r);
-                        cp_async_wait_all();
-                        __syncwarp();
-                        // four points per pass: each beta~ load feeds sixteen FMAs
-                        for (int tq = 0; tq < tn; tq += 4) {
-                            float yr[4] = {0.f, 0.f, 0.f, 0.f}, yi[4] = {0.f, 0.f, 0.f, 0.f};
-                            const cf* Bt = sbs + tq * nc;
-                            const int nq = min(4, tn - tq);
-#pragma unroll 2
+                    __syncwarp();
+                    if (TcL2p<NB>::fits && l2p_basis) {
+                        // L2P of the leaf (Algorithm 1, step 4), one column block:
+                        // y[t][r] += sum_m beta~[r][m] (i/4) conj(B[t][m]) over the leaf's
+                        // points t.  Per 8 points the warp brings the basis rows and its rows
+                        // of y into the ring (asynchronous copies, all in flight together);
+                        // the sum reads beta~ by row and the basis as broadcasts, eight points
+                        // per pass (each beta~ load feeds 32 FMAs).
+                        constexpr int TCH = TcL2p<NB>::pts;
+                        cf* sbs = (cf*)(bet + 32 * (NB + 1));
+                        cf* sy = sbs + TCH * (NB / 2);
+                        const float* br = bet + lane * (NB + 1);   // Re beta~_m at m, Im at nc + m
+                        const int r = rc * 64 + (row & 63);
+                        const bool live = r < nrhs;
+                        const int32_t t0 = lbeg[box], t1 = lbeg[box + 1];
+                        for (int32_t tc0 = t0; tc0 < t1; tc0 += TCH) {
+                            const int tn = min(TCH, t1 - tc0);
+                            __syncwarp();
+                            for (int e = lane; e < tn * nc; e += 32)
+                                cp_async8(sbs + e, l2p_basis + (int64_t)tc0 * nc + e);
+                            if (live)
+                                for (int t = 0; t < tn; ++t)
+                                    cp_async8(sy + t * 32 + lane, ys + (int64_t)(tc0 + t) * nrhs + r);
+                            cp_async_wait_all();
+                            __syncwarp();
+                            float yr[TCH], yi[TCH];
+#pragma unroll
+                            for (int u = 0; u < TCH; ++u) yr[u] = yi[u] = 0.0f;
                             for (int m = 0; m < nc; ++m) {
                                 const float are = br[m], aim = br[nc + m];
 #pragma unroll
-                                for (int u = 0; u < 4; ++u) {
-                                    const cf b = Bt[(u < nq ? u : 0) * nc + m];
+                                for (int u = 0; u < TCH; ++u) {
+                                    const cf b = sbs[(u < tn ? u : 0) * nc + m];
                                     yr[u] = fmaf(are, b.y, fmaf(-aim, b.x, yr[u]));
                                     yi[u] = fmaf(are, b.x, fmaf(aim, b.y, yi[u]));
                                 }
                             }
                             if (live) {
 #pragma unroll
-                                for (int u = 0; u < 4; ++u)
-                                    if (u < nq) {
-                                        const int t = tq + u;
-                                        const cf y0 = sy[t * 32 + lane];
-                                        ys[(int64_t)(tc0 + t) * nrhs + r] =
+                                for (int u = 0; u < TCH; ++u)
+                                    if (u < tn) {
+                                        const cf y0 = sy[u * 32 + lane];
+                                        ys[(int64_t)(tc0 + u) * nrhs + r] =
                                             cfmk(y0.x + 0.25f * yr[u], y0.y + 0.25f * yi[u]);
                                     }
                             }
                         }
                     }
-                }
-                if (out) {
-                    // FP32 coefficients: the warp's 32 rows are one contiguous range of out
-                    // ([box][r][coef] complex); stage them in the ring (every MMA of this
-                    // CTA has completed) and store along that range
-                    static_assert(128 * (NB + 1) * 4 <= TC_STAGES * stage_bytes, "staging fits the ring");
-                    float* stg = (float*)smem + warp * 32 * (NB + 1);
-#pragma unroll
-                    for (int j = 0; j < NB; ++j) stg[lane * (NB + 1) + j] = acc[j];
-                    __syncwarp();
-                    const int rfirst = rc * 64 + ((warp * 32) & 63);
-                    const int nrows = min(32, nrhs - rfirst);
-                    if (nrows > 0) {
-                        float* o = (float*)(out + ((int64_t)box * nrhs + rfirst) * nc);
-                        const int w2 = 2 * nc;
-                        int i = lane / w2, w = lane - (lane / w2) * w2;   // f = i * w2 + w
-                        for (int f = lane; f < nrows * w2; f += 32) {
-                            const int g = (w & 1) * nc + (w >> 1);
-                            if (g >= n0 && g < n0 + NB) o[f] = stg[i * (NB + 1) + g - n0];
-                            w += 32;
-                            while (w >= w2) { w -= w2; ++i; }
+                    if (out) {
+                        // FP32 coefficients: the warp's 32 rows are one contiguous range of
+                        // out ([box][r][coef] complex), stored along that range
+                        const int rfirst = rc * 64 + ((warp * 32) & 63);
+                        const int nrows = min(32, nrhs - rfirst);
+                        if (nrows > 0) {
+                            float* o = (float*)(out + ((int64_t)box * nrhs + rfirst) * nc);
+                            const int w2 = 2 * nc;
+                            int i = lane / w2, w = lane - (lane / w2) * w2;   // f = i * w2 + w
+                            for (int f = lane; f < nrows * w2; f += 32) {
+                                const int g = (w & 1) * nc + (w >> 1);
+                                if (g >= n0 && g < n0 + NB) o[f] = bet[i * (NB + 1) + g - n0];
+                                w += 32;
+                                while (w >= w2) { w -= w2; ++i; }
+                            }
                         }
                     }
                 }
