@@ -149,7 +149,8 @@ typedef struct {
     int64_t near_simt_leaves;   /*             leaves of wider blocks, on the SIMT kernel */
     int32_t leaf_l2p_fused;     /* HFMM_MIXED: 1 if the leaves' L2P runs in the tensor-core downward
                                    epilogue, 0 if on the SIMT kernel */
-    int32_t reserved0;
+    int32_t leaf_tc_width;      /* HFMM_MIXED: column-block width (MMA N) of the leaf-level
+                                   tensor-core pass, 0 without one */
 } hfmm_plan_info;
 
 /* Bits of `parts` in hfmm_apply_parts (sum of the selected terms). */
@@ -242,6 +243,15 @@ hfmm_status hfmm_batch_apply(hfmm_batch_t batch, int32_t nrhs, const void* const
 /* Plan of instance i (owned by the batch; for introspection and single applies). */
 hfmm_status hfmm_batch_get_plan(hfmm_batch_t batch, int32_t i, hfmm_plan_t* plan);
 hfmm_status hfmm_batch_destroy(hfmm_batch_t batch);
+
+/*
+ * HFMM_FLAG_PROFILE plans, mixed path: event time (ms) of the leaf-level
+ * tensor-core downward launch of the last apply (L2L + free and reaction
+ * M2L of the leaves, plus their L2P when info.leaf_l2p_fused) and its
+ * algorithmic real flops (8 nrhs per complex multiply-add, the per-level
+ * counts of flops_last_apply); both 0 when the last apply had no such launch.
+ */
+hfmm_status hfmm_plan_get_leaf_down(hfmm_plan_t plan, double* ms, double* flops);
 
 /* Fill *info (host pointer). */
 hfmm_status hfmm_plan_get_info(hfmm_plan_t plan, hfmm_plan_info* info);

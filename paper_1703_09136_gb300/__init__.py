@@ -223,6 +223,13 @@ class Plan:
         d["bytes_last_apply"] = dict(zip(_n.STAGES, list(inf.bytes_last_apply)))
         return d
 
+    def leaf_down_time(self):
+        """(ms, flops) of the leaf-level tensor-core downward launch of the last
+        apply (profile plans, hfmm_plan_get_leaf_down)."""
+        ms, fl = ctypes.c_double(), ctypes.c_double()
+        _n.check(_n.lib().hfmm_plan_get_leaf_down(self._h, ctypes.byref(ms), ctypes.byref(fl)))
+        return float(ms.value), float(fl.value)
+
     def stage_times(self):
         """Per-stage milliseconds of the last apply (plan built with profile=True)."""
         ms = (ctypes.c_double * _n.NUM_STAGES)()

@@ -21,7 +21,7 @@ EXPORTS = ["hfmm_options_default", "hfmm_plan_create", "hfmm_apply", "hfmm_apply
            "hfmm_plan_get_pairs", "hfmm_plan_destroy", "hfmm_status_string", "hfmm_last_error",
            "hfmm_debug_bessel", "hfmm_plan_get_stage_times", "hfmm_debug_green_f32",
            "hfmm_leaf_order_noalloc", "hfmm_apply_grad", "hfmm_batch_create", "hfmm_batch_apply",
-           "hfmm_batch_get_plan", "hfmm_batch_destroy", "hfmm_debug_wait_timeout"]
+           "hfmm_batch_get_plan", "hfmm_batch_destroy", "hfmm_debug_wait_timeout", "hfmm_plan_get_leaf_down"]
 NUM_STAGES = 8
 STAGES = ["gather", "p2m", "m2m", "down", "l2p", "p2p", "direct", "scatter"]
 FLAG_PROFILE = 1
@@ -59,7 +59,7 @@ class hfmm_plan_info(ctypes.Structure):
                 ("device_error", ctypes.c_int32), ("tensor_levels", ctypes.c_int32),
                 ("tune_levels", ctypes.c_int32 * 3), ("tune_ms", ctypes.c_double * 3),
                 ("near_tc_blocks", ctypes.c_int64), ("near_simt_leaves", ctypes.c_int64),
-                ("leaf_l2p_fused", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+                ("leaf_l2p_fused", ctypes.c_int32), ("leaf_tc_width", ctypes.c_int32)]
 
 
 hfmm_plan_t = ctypes.c_void_p
@@ -97,12 +97,13 @@ def lib():
         L.hfmm_batch_get_plan.argtypes = [vp, i32, ctypes.POINTER(hfmm_plan_t)]
         L.hfmm_batch_destroy.argtypes = [vp]
         L.hfmm_debug_wait_timeout.argtypes = [i64, i32]
+        L.hfmm_plan_get_leaf_down.argtypes = [hfmm_plan_t, vp, vp]
         for name in ("hfmm_plan_create", "hfmm_apply", "hfmm_apply_parts", "hfmm_apply_adjoint",
                      "hfmm_plan_get_info", "hfmm_plan_get_tree", "hfmm_plan_get_pairs",
                      "hfmm_plan_destroy", "hfmm_debug_bessel", "hfmm_plan_get_stage_times",
                      "hfmm_debug_green_f32", "hfmm_leaf_order_noalloc", "hfmm_apply_grad",
                      "hfmm_batch_create", "hfmm_batch_apply", "hfmm_batch_get_plan", "hfmm_batch_destroy",
-                     "hfmm_debug_wait_timeout"):
+                     "hfmm_debug_wait_timeout", "hfmm_plan_get_leaf_down"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib

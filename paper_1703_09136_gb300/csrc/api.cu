@@ -40,8 +40,11 @@ hfmm_status plan_alloc(hfmm_plan_s* P, void** ptr, size_t bytes) {
 static void plan_free(hfmm_plan_s* P) {
     if (!P) return;
     cudaDeviceSynchronize();
-    if (P->events_ready)
+    if (P->events_ready) {
         for (int s = 0; s < HFMM_NUM_STAGES; ++s) { cudaEventDestroy(P->ev[s][0]); cudaEventDestroy(P->ev[s][1]); }
+        cudaEventDestroy(P->ev_leaf[0]);
+        cudaEventDestroy(P->ev_leaf[1]);
+    }
     for (void* p : P->allocations) cudaFree(p);
     delete P;
 }
@@ -309,6 +312,11 @@ static hfmm_status plan_create_one(hfmm_plan_t* out, int64_t n, const double* xy
                         hfmm_set_error("cudaEventCreate failed");
                         s = HFMM_ERR_CUDA;
                     }
+            for (int k2 = 0; k2 < 2 && s == HFMM_OK; ++k2)
+                if (cudaEventCreate(&P->ev_leaf[k2]) != cudaSuccess) {
+                    hfmm_set_error("cudaEventCreate failed");
+                    s = HFMM_ERR_CUDA;
+                }
             if (s != HFMM_OK) break;
             P->events_ready = true;
         }
@@ -497,6 +505,7 @@ hfmm_status hfmm_plan_get_info(hfmm_plan_t P, hfmm_plan_info* info) {
     }
     info->near_tc_blocks = P->nt_nblocks;
     info->leaf_l2p_fused = P->tc_l2p ? 1 : 0;
+    info->leaf_tc_width = P->tc_on ? P->lev[P->L].tc_nbw : 0;
     info->near_simt_leaves = P->nt_nfallback;
     return HFMM_OK;
 }
@@ -512,6 +521,20 @@ hfmm_status hfmm_plan_get_stage_times(hfmm_plan_t P, double* ms) {
         HFMM_CUDA_TRY(cudaEventElapsedTime(&t, P->ev[s][0], P->ev[s][1]));
         ms[s] = t;
     }
+    return HFMM_OK;
+}
+
+hfmm_status hfmm_plan_get_leaf_down(hfmm_plan_t P, double* ms, double* flops) {
+    if (!P || !ms || !flops) { hfmm_set_error("plan, ms or flops is NULL"); return HFMM_ERR_INVALID_ARG; }
+    if (!P->events_ready) { hfmm_set_error("plan was created without HFMM_FLAG_PROFILE"); return HFMM_ERR_INVALID_ARG; }
+    *ms = 0.0;
+    *flops = 0.0;
+    if (!P->ev_leaf_used) return HFMM_OK;
+    HFMM_CUDA_TRY(cudaStreamSynchronize(P->last_stream));
+    float t = 0.0f;
+    HFMM_CUDA_TRY(cudaEventElapsedTime(&t, P->ev_leaf[0], P->ev_leaf[1]));
+    *ms = t;
+    *flops = P->leaf_flops;
     return HFMM_OK;
 }
 

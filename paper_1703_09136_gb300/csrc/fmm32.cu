@@ -784,6 +784,8 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
     StageTimer tm{P, st};
     P->launches = 0;
     for (int s = 0; s < HFMM_NUM_STAGES; ++s) { P->st_flops[s] = 0.0; P->st_bytes[s] = 0.0; P->ev_used[s] = false; }
+    P->ev_leaf_used = false;
+    P->leaf_flops = 0.0;
     const double C = 8.0 * nrhs;
     const double MAC = 8.0 * nrhs;
     tm.begin(HFMM_STAGE_GATHER);
@@ -881,7 +883,16 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
             rc = std::max(1, std::min(rc, (8 * DOWN_THREADS) / lv.ncoef));
             const size_t sm = (size_t)rc * wmax * sizeof(cf);
             if (tc_down) {
+                const bool leaf_ev = l == L && P->events_ready;
+                if (leaf_ev) cudaEventRecord(P->ev_leaf[0], st);
                 HFMM_TRY(launch_m2l_tc(P, l, nrhs, l == L && !l2p_fused, l2p_fused, st));
+                if (leaf_ev) {
+                    cudaEventRecord(P->ev_leaf[1], st);
+                    P->ev_leaf_used = true;
+                    P->leaf_flops = MAC * ((double)lv.nv + (double)lv.nr) * lv.ncoef * lv.ncoef +
+                                    (has_parent ? MAC * lv.nbox * lv.ncoef * npp : 0.0) +
+                                    (l2p_fused ? MAC * n * lv.ncoef : 0.0);
+                }
             } else {
                 down32_kernel<<<(unsigned)lv.nbox, DOWN_THREADS, sm, st>>>(
                     P->leaf_begin, L, l, P->lmin, nrhs, lv.p, has_parent ? P->lev[l - 1].p : 0,

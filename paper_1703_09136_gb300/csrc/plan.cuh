@@ -193,6 +193,9 @@ struct hfmm_plan_s {
     int flags = 0;
     bool events_ready = false;
     cudaEvent_t ev[HFMM_NUM_STAGES][2];
+    cudaEvent_t ev_leaf[2];         // around the leaf-level tensor-core downward launch
+    bool ev_leaf_used = false;
+    double leaf_flops = 0.0;        // its algorithmic flops in the last apply
     bool ev_used[HFMM_NUM_STAGES] = {};
     cudaStream_t last_stream = nullptr;
     int64_t launches = 0;

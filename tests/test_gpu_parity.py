@@ -309,6 +309,31 @@ def test_tensor_core_downward_pass_matches_simt_and_fp64():
         p.close()
 
 
+def test_profile_plan_reports_stage_and_leaf_kernel_times():
+    """Profile plans: per-stage event times of the last apply, and the
+    leaf-level tensor-core downward launch's own time and algorithmic flops
+    (the downward stage's flops minus the other levels', plus the L2P)."""
+    from paper_1703_09136_gb300 import MIXED
+    xy = W.points_in_box(4, 8192, ((0.0, 1.0), (0.02, 1.02)))
+    q = torch.from_numpy(W.strengths(4, 8192, 64, salt=6).astype(np.complex64)).cuda()
+    plan = Plan(xy, CFG4_MED, tol=1e-6, leaf_size=16, max_rhs=64, precision=MIXED, profile=True)
+    plan.apply(q)
+    st = plan.stage_times()
+    ms, fl = plan.leaf_down_time()
+    inf = plan.info
+    assert st["down"] > 0.0 and st["p2p"] > 0.0 and st["gather"] > 0.0
+    assert 0.0 < ms <= st["down"]
+    assert inf["leaf_l2p_fused"] == 1 and inf["leaf_tc_width"] % 16 == 0
+    # leaf flops: part of the downward stage's count plus the L2P (8 nrhs (2p+1) per point)
+    l2p = 8.0 * 64 * 8192 * (2 * inf["p"][inf["levels"]] + 1)
+    assert 0.0 < fl - l2p < inf["flops_last_apply"]["down"] - l2p
+    # a plan without profiling refuses
+    plain = Plan(xy, CFG4_MED, tol=1e-6, leaf_size=16, max_rhs=64, precision=MIXED)
+    with pytest.raises(HfmmError):
+        plain.leaf_down_time()
+    plan.close(); plain.close()
+
+
 def test_tensor_core_ragged_rhs_blocks_and_changing_width():
     """Two 64-row right-hand-side blocks with a ragged second block (70 RHS),
     then a narrower apply (5 RHS) on the same plan: every column agrees with
