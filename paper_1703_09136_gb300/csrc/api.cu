@@ -45,6 +45,10 @@ static void plan_free(hfmm_plan_s* P) {
         cudaEventDestroy(P->ev_leaf[0]);
         cudaEventDestroy(P->ev_leaf[1]);
     }
+    if (P->far_st) cudaStreamDestroy(P->far_st);
+    if (P->near_st) cudaStreamDestroy(P->near_st);
+    for (cudaEvent_t e : {P->ev_fork, P->ev_near_done, P->ev_far_done})
+        if (e) cudaEventDestroy(e);
     for (void* p : P->allocations) cudaFree(p);
     delete P;
 }

@@ -171,6 +171,11 @@ struct hfmm_plan_s {
     int64_t dj_njobs = 0;
     bool tc_on = false;             // every level lmin..L has tensor-core M2M / downward state
     bool tc_l2p = false;            // leaf L2P fused into the tensor-core downward epilogue
+    // concurrent near field: the far-field chain on a high-priority stream, the
+    // near field on a low-priority one, both forked from and joined back into the
+    // caller's stream (created on first use)
+    cudaStream_t far_st = nullptr, near_st = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_near_done = nullptr, ev_far_done = nullptr;
     int* tc_err = nullptr;          // set by the tensor-core pass when a bounded wait gave up
     long tc_spin = 0;               // polls of a bounded device wait (options.spin_limit or the default)
     __half* tc_zero = nullptr;      // 4 KB of zeros: the A half of a missing source box
