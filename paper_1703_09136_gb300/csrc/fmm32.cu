@@ -348,8 +348,8 @@ __device__ __forceinline__ cf green_free_f32_tab(const PcShared& S, float z) {
 }
 
 // acc[i] += sum_{j < sn} S.g[j][tb + i] * S.q[j][r]
-template <int NTH>
-__device__ __forceinline__ void pc_mac(const PcShared& S, int sn, int r, int tb, cf* acc) {
+template <int NTH, class SH>
+__device__ __forceinline__ void pc_mac(const SH& S, int sn, int r, int tb, cf* acc) {
 #pragma unroll 2
     for (int j = 0; j < sn; ++j) {
         const cf qv = S.q[j][r];
@@ -410,7 +410,7 @@ __device__ __forceinline__ void p2p_pass(PcShared& S, const int32_t* lb, int L, 
                     S.g[j][t] = g;
                 }
                 __syncthreads();
-                pc_mac<NTH>(S, sn, r, tb, acc);
+                pc_mac<NTH, PcShared>(S, sn, r, tb, acc);
             }
         }
     if (loc) {
@@ -429,7 +429,7 @@ __device__ __forceinline__ void p2p_pass(PcShared& S, const int32_t* lb, int L, 
                 S.g[j][t] = cfmk(0.25f * B.y, 0.25f * B.x);
             }
             __syncthreads();
-            pc_mac<NTH>(S, mb, r, tb, acc);
+            pc_mac<NTH, PcShared>(S, mb, r, tb, acc);
         }
     }
     // stage y[t][r] in shared memory, then add it to y along the points
@@ -478,8 +478,14 @@ __global__ void __launch_bounds__(PC_THREADS, 6) p2p32c_kernel(const int32_t* lb
 // q_r(pt) B[pt][m] with the plan-time basis B.  Same tiling as the P2P pass:
 // thread (r, half) owns NTH coefficients of a pass of up to 32, points are
 // streamed in chunks of 32 (strengths [j][r], basis [j][m] in shared memory).
+// P2M's shared staging: the P2P tables are not needed.
+struct P2mShared {
+    cf q[PC_SRC][PC_RHS + 1];      // strengths of the chunk; reused as output staging [m][r]
+    __align__(16) cf g[PC_SRC][PC_TGT];
+};
+
 template <int NTH>
-__device__ __forceinline__ void p2m_pass(PcShared& S, const cf* qs, const cf* basis, int64_t n, int nrhs, int r0,
+__device__ __forceinline__ void p2m_pass(P2mShared& S, const cf* qs, const cf* basis, int64_t n, int nrhs, int r0,
                                          int32_t lo, int32_t hi, int nc, int m0, int w, cf* out, bool write_out) {
     const int tid = threadIdx.x;
     const int r = tid & (PC_RHS - 1), half = tid >> 6;
@@ -499,7 +505,7 @@ __device__ __forceinline__ void p2m_pass(PcShared& S, const cf* qs, const cf* ba
             S.g[j][t] = basis[(int64_t)(s0 + j) * nc + m0 + t];
         }
         __syncthreads();
-        pc_mac<NTH>(S, sn, r, tb, acc);
+        pc_mac<NTH, P2mShared>(S, sn, r, tb, acc);
     }
     __syncthreads();
 #pragma unroll
@@ -526,8 +532,11 @@ __global__ void __launch_bounds__(PC_THREADS) p2m32c_kernel(const int32_t* lb, c
                                                             int64_t n, int nrhs, int nc, cf* mult, __half* amma,
                                                             float* asc, int kc, int nrc, int nsb, int sblk,
                                                             bool write_mult) {
-    __shared__ PcShared S;
-    __shared__ int s_e[16][PC_RHS];   // [column block][row]: consecutive rows in consecutive banks
+    __shared__ P2mShared S;
+    // [column block][row] exponents (consecutive rows in consecutive banks), in the
+    // basis staging, which the MMA-ready writer no longer needs
+    static_assert(sizeof(S.g) >= 16 * PC_RHS * sizeof(int), "exponents fit the basis staging");
+    int (*s_e)[PC_RHS] = reinterpret_cast<int (*)[PC_RHS]>(&S.g[0][0]);
     const int64_t b = blockIdx.x;
     const int32_t lo = lb[b], hi = lb[b + 1];
     cf* out = mult + (int64_t)b * nrhs * nc;

@@ -66,11 +66,13 @@ struct TcCfg {
     static constexpr int buf_cols = tmem_cols / 2;
     static constexpr int ctas = 512 / tmem_cols;
     static constexpr int stage_bytes = 8192 + NB * 64;
-    // 228 KB of shared memory per SM; per CTA 1 KB reserved by the system,
-    // 1 KB of static shared memory and 256 B of barriers
-    static constexpr int budget = 233472 / ctas - 1024 - 1024 - 256;
+    // 228 KB of shared memory per SM; per CTA 1 KB reserved by the system and
+    // 256 B of barriers (the kernel has no static shared memory: its 1024-byte
+    // aligned dynamic block would pad any to 1 KB)
+    static constexpr int budget = 233472 / ctas - 1024 - 256;
     static constexpr int stages = budget / stage_bytes < 8 ? budget / stage_bytes : 8;
     static_assert(stages >= 2, "ring needs two stages");
+    static_assert((2 * stages + 4 + 3) * 8 <= 256, "barrier area fits 256 bytes");
     static constexpr size_t smem = (size_t)stages * stage_bytes + 256;
 };
 constexpr int TC_MAX_NP = 128;         // widest column block (one 128-column TMEM buffer)
@@ -231,8 +233,6 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
     int nseg, float* __restrict__ part, const cf* __restrict__ l2p_basis, const int32_t* __restrict__ lbeg,
     cf* __restrict__ ys, long spin, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ volatile int s_abort;
-    __shared__ uint64_t mdone;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     using CFG = TcCfg<NB>;
     constexpr int stage_bytes = CFG::stage_bytes;
@@ -241,7 +241,11 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
     uint64_t* empty = full + TC_STAGES;
     uint64_t* dfull = empty + TC_STAGES;
     uint64_t* dfree = dfull + 2;
+    // barrier area after the ring: full[], empty[], dfull[2], dfree[2], then 8-byte
+    // slots for the TMEM address, the MMA-completion barrier and the abort flag
     uint32_t* tslot = (uint32_t*)(dfree + 2);
+    uint64_t& mdone = *(dfree + 3);
+    volatile int& s_abort = *(volatile int*)(dfree + 4);
     const TcTile tile = tiles[blockIdx.x];
     const int rc = blockIdx.y;
     const int nbz = Np / NB;
