@@ -38,6 +38,16 @@ SAMPLE_BOX = ((0.0, 1.0), (0.02, 1.02))
 FALLBACK_BF16_TFLOPS = 1900.0  # used only when MEASURED_PEAKS.json is absent
 
 
+# DRAM bytes of one full-size launch of the leaf-level downward kernel
+# (m2l_tc_kernel<48> with the fused L2P), from the ncu capture summarised in
+# profiles/m2l_tc_kernel48_three-layer-65536-64rhs_mixed.md: 110.8 MB read +
+# 12.8 MB written on 4096 leaves (p = 10, 16 points per leaf, 64 RHS), scaled
+# by the leaf count to the 65536 leaves of the 1M-point workload (same order,
+# width and points per leaf: the traffic grows in proportion).  It belongs to
+# the kernel as captured; a changed kernel reports null until re-captured.
+LEAF48_TRAFFIC_BYTES = (110.776320e6 + 12.816128e6) * 16
+
+
 def _measured_bf16(key="bf16_tflops"):
     """Dense bf16 TFLOP/s measured on this GPU type (burst, or with
     key="bf16_tflops_sustained" the seconds-long figure), and its source."""
@@ -263,7 +273,11 @@ def run_ours(args):
         roof = {"kernel": f"m2l_tc_kernel<{info['leaf_tc_width']}> (leaf-level downward: L2L + free and reaction "
                           f"M2L{' + L2P' if info['leaf_l2p_fused'] else ''})",
                 "bound": "tensor", "achieved": leaf_flops / (leaf_ms * 1e-3) / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "traffic": None, "peak_source": src,
+                "unit": "TFLOP/s",
+                "traffic": (LEAF48_TRAFFIC_BYTES if info["leaf_tc_width"] == 48 and info["leaf_l2p_fused"]
+                            and n == 1048576 and nrhs == 64 else None),
+                "traffic_source": "ncu dram bytes of the 65536-point case x 16 leaves (see profiles/)",
+                "peak_source": src,
                 "launch_ms": leaf_ms / args.steps}
         roof["frac"] = roof["achieved"] / roof["peak"]
         # the timed region is 30 short applies at full clock: the burst figure applies;
