@@ -361,8 +361,8 @@ hfmm_status build_p2p_tc(hfmm_plan_s* P, cudaStream_t st) {
     return HFMM_OK;
 }
 
-// Launch the tensor-core near field (near: P2P chunks, far: L2P chunks) over
-// the plan's blocks; it stores y of their targets.
+// Launch the tensor-core near field over the plan's blocks; it stores (not
+// adds) y of their targets, so it runs before any other writer of y32.
 hfmm_status launch_p2p_tc(hfmm_plan_s* P, int nrhs, cudaStream_t st) {
     if (P->nt_nblocks == 0) return HFMM_OK;
     static bool attr_set = false;

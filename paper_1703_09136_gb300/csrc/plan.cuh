@@ -88,19 +88,18 @@ struct LevelInfo {
 constexpr int NT_GSCALE_EXP = 10;
 
 // Near field on tensor cores: one K chunk of a block (the four leaves of a
-// parent box at level L - 1).  A source chunk holds up to 8 consecutive sorted
-// points of one source leaf of the 4 x 4 neighbourhood; an L2P chunk holds
-// 8 local coefficients of one target leaf.  The pre-split B tile of the chunk
-// (rows = the padded targets of the adjacent leaves, in leaf order) starts at
-// float offset boff of the plan's tile store: hi rows x 16, then lo.
+// parent box at level L - 1): up to 8 consecutive sorted points of one source
+// leaf of the 4 x 4 neighbourhood.  The pre-split B tile of the chunk (rows =
+// the padded targets of the adjacent leaves, in leaf order) starts at half
+// offset boff of the plan's tile store: hi rows x 16, then lo.
 struct NtChunk {
-    int32_t src;     // first source point (sorted index); -1: L2P chunk
-    int32_t cnt;     // sources in the chunk (1 .. 8); L2P: K chunk index
+    int32_t src;     // first source point (sorted index)
+    int32_t cnt;     // sources in the chunk (1 .. 8)
     int32_t mask;    // target leaves the tile covers (bit c = child c)
     int32_t rows;    // rows of the tile (sum of their padded widths)
     int64_t boff;
     int32_t par;     // parent box (level L - 1)
-    int32_t aux;     // source leaf code (sx + 1) + 4 (sy + 1); L2P: unused
+    int32_t aux;     // source leaf code (sx + 1) + 4 (sy + 1)
     int32_t nrun;    // runs of consecutive covered leaves (1 or 2)
     int32_t run[2];  // each: width | first column << 8 | first tile row << 16
     int32_t pad;
@@ -144,8 +143,8 @@ struct hfmm_plan_s {
     cf* y32 = nullptr;              // [n][nrhs]
     int32_t* iperm32 = nullptr;     // [n] sorted position of caller index j
     // near field on tensor cores (p2p_tc.cu): blocks (parent box, first chunk,
-    // first L2P chunk, end), their chunks, the pre-split tile store, and the
-    // leaves of blocks too wide for the kernel (SIMT kernel)
+    // end, 0), their chunks, the pre-split tile store, and the leaves of blocks
+    // too wide for the kernel (SIMT kernel)
     int32_t* nt_blocks = nullptr;
     int64_t nt_nblocks = 0;
     NtChunk* nt_chunks = nullptr;
