@@ -511,3 +511,29 @@ def test_batch_graph_equals_individual_plans():
                 single.close()
                 assert torch.equal(ref, y)
         batch.close()
+
+
+def test_batch_graph_captures_the_concurrent_near_field():
+    """An instance large enough for the fused leaf L2P runs its near field on
+    a low-priority stream concurrently with the far-field chain; captured into
+    the batch graph, that fork-join gives exactly the single-plan result."""
+    from paper_1703_09136_gb300 import Batch, MIXED
+    med = W.WORKLOADS[5].medium
+    sizes = [60000, 2000]
+    xys = [W.points(5, n, salt=10 + i) for i, n in enumerate(sizes)]
+    qs = [torch.from_numpy(W.strengths(5, n, 4, salt=i)).cuda().to(torch.complex64) for i, n in enumerate(sizes)]
+    singles = [Plan(xy, med, leaf_size=16, precision=MIXED, max_rhs=4) for xy in xys]
+    assert singles[0].info["leaf_l2p_fused"] == 1 and singles[1].info["leaf_l2p_fused"] == 0
+    refs = [p.apply(q) for p, q in zip(singles, qs)]
+    batch = Batch(xys, med, leaf_size=16, precision=MIXED, max_rhs=4)
+    ys = [torch.empty_like(q) for q in qs]
+    for rep in range(3):
+        for y in ys:
+            y.zero_()
+        batch.apply(qs, ys)
+        torch.cuda.synchronize()
+        for ref, y in zip(refs, ys):
+            assert torch.equal(ref, y), rep
+    batch.close()
+    for p in singles:
+        p.close()
