@@ -39,9 +39,9 @@ FALLBACK_BF16_TFLOPS = 1900.0  # used only when MEASURED_PEAKS.json is absent
 
 
 # DRAM bytes of one full-size launch of the leaf-level downward kernel
-# (m2l_tc_kernel<48> with the fused L2P), from the ncu capture summarised in
-# profiles/m2l_tc_kernel48_three-layer-65536-64rhs_mixed.md: 110.8 MB read +
-# 12.8 MB written on 4096 leaves (p = 10, 16 points per leaf, 64 RHS), scaled
+# (m2l_tc_kernel<48> with the fused L2P), from an ncu capture of the
+# 65536-point case of the same workload (dram__bytes_read.sum 110.8 MB,
+# dram__bytes_write.sum 12.8 MB on 4096 leaves: p = 10, 16 points per leaf, 64 RHS), scaled
 # by the leaf count to the 65536 leaves of the 1M-point workload (same order,
 # width and points per leaf: the traffic grows in proportion).  It belongs to
 # the kernel as captured; a changed kernel reports null until re-captured.
@@ -287,7 +287,7 @@ def run_ours(args):
                 "unit": "TFLOP/s",
                 "traffic": (LEAF48_TRAFFIC_BYTES if info["leaf_tc_width"] == 48 and info["leaf_l2p_fused"]
                             and n == 1048576 and nrhs == 64 else None),
-                "traffic_source": "ncu dram bytes of the 65536-point case x 16 leaves (see profiles/)",
+                "traffic_source": "ncu dram bytes of the 65536-point case (4096 leaves) x 16 leaves",
                 "peak_source": src,
                 "launch_ms": leaf_ms / args.steps}
         roof["frac"] = roof["achieved"] / roof["peak"]
