@@ -68,7 +68,7 @@ __device__ __forceinline__ void put_a(uint16_t* A, int j, int r, cf v) {
 struct NtSmall {
     NtChunk ch[NT_MAXCH];      // the block's chunk records
     int32_t tidx[NT_MAXN];     // target of each column, -1: padding
-    int32_t off[5], wid[4], lbox[4];
+    int32_t off[5], wid[4];
 };
 
 __global__ void __launch_bounds__(NT_THREADS, 4) p2p_tc_kernel(
@@ -90,7 +90,6 @@ __global__ void __launch_bounds__(NT_THREADS, 4) p2p_tc_kernel(
         int o = 0;
         for (int c = 0; c < 4; ++c) {
             const int64_t lf = 4 * P + c;
-            S.lbox[c] = (int32_t)lf;
             S.off[c] = o;
             S.wid[c] = (lb[lf + 1] - lb[lf] + 15) / 16 * 16;
             o += S.wid[c];
