@@ -97,6 +97,11 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     # apply on a null plan
     q = np.zeros(2, dtype=np.complex128)
     assert lib.hfmm_apply(None, 1, q.ctypes.data_as(vp), q.ctypes.data_as(vp), None) == 1
+    # leaf-kernel timing of a null plan, a wait probe without polls
+    ms, fl = ctypes.c_double(), ctypes.c_double()
+    assert lib.hfmm_plan_get_leaf_down(None, ctypes.byref(ms), ctypes.byref(fl)) == 1
+    assert lib.hfmm_debug_wait_timeout(0, 0) == 1
+    assert b"spin" in lib.hfmm_last_error()
     assert lib.hfmm_plan_destroy(None) == 0
 
 
