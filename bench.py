@@ -295,6 +295,21 @@ def run_ours(args):
         # against the seconds-long (sustained) bf16 figure for comparison
         sus, _ = _measured_bf16("bf16_tflops_sustained")
         roof["frac_vs_sustained"] = roof["achieved"] / (sus / 3.0)
+    # the near field alone (no far field, so nothing runs beside it): its own
+    # CUDA-event time and algorithmic flops, against the same 3xF16 peak
+    near_roof = None
+    if prec != FP64 and stage_roof is not None:
+        from paper_1703_09136_gb300 import PART_NEAR_FREE
+        nm = nf = 0.0
+        for _ in range(3):
+            plan.apply(q, out=y, parts=PART_NEAR_FREE)
+            nm += plan.stage_times()["p2p"]
+            nf += plan.info["flops_last_apply"]["p2p"]
+        if nm > 0.0:
+            near_roof = {"kernel": "p2p_tc_kernel (near-field P2P, precomputed Green's-function tiles)",
+                         "bound": "tensor", "achieved": nf / (nm * 1e-3) / 1e12, "peak": peak,
+                         "unit": "TFLOP/s", "launch_ms": nm / 3, "peak_source": src}
+            near_roof["frac"] = near_roof["achieved"] / near_roof["peak"]
     # end to end through the C ABI with pinned host buffers
     qh = torch.from_numpy(q_h).to(cdt).pin_memory()
     yh = torch.empty_like(qh).pin_memory()
@@ -320,6 +335,7 @@ def run_ours(args):
                    "parallelism": f"replicas{world}"},
         "stage_ms": avg, "adjoint_ms": None, "gpu_launches": launches, "e2e": e2e, "roofline": roof,
         **({"roofline_stage": stage_roof} if stage_roof else {}),
+        **({"roofline_near": near_roof} if near_roof else {}),
         "clocks": ck,
     }
     # adjoint time
