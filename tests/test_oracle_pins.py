@@ -112,6 +112,32 @@ def test_three_layer_contour_passes_guided_mode_poles_on_the_radiating_side():
     assert len(green.singular_t(CFG4)) == 2
 
 
+def _lossy_two_layer_real_axis(k1, k2, X, Y, eps, width=0.01):
+    """Two-layer G^s with an absorbing lower layer (k2 -> k2 (1 + i eps)) on the
+    real t axis: the branch point of s2 has left the axis, so no deformation."""
+    med = Medium(TWO, (k1, k2 * (1 + 1j * eps)))
+    tau, wt = green._panels(0.0, math.pi, 400)
+    lam = -k1 * np.cos(tau)
+    prop = np.sum(wt * np.exp(1j * k1 * (Y * np.sin(tau) - X * np.cos(tau)))
+                  * green.sigma(med, lam * lam + 0j, -1j * k1 * np.sin(tau)))
+    T = 45.0 / Y
+    t, w = green._panels(0.0, T, int(T / width) + 1)
+    xi = np.sqrt(t * t + k1 * k1)
+    evan = np.sum(w * np.exp(-t * Y) * np.cos(xi * X) / xi * green.sigma(med, xi * xi + 0j, t + 0j))
+    return 1j / (4 * math.pi) * prop + evan / (2 * math.pi)
+
+
+def test_two_layer_contour_equals_limit_of_absorbing_lower_layer():
+    """Two layers (k1 = 60 over k2 = 90): the deformed evanescent contour of
+    the lossless medium equals the eps -> 0 limit (Richardson, two eps) of an
+    absorbing lower layer integrated on the real axis."""
+    X, Y = 0.35, 0.3
+    lossless = green.green_reaction(Medium(TWO, (60.0, 90.0)), X, Y)[0]
+    g1 = _lossy_two_layer_real_axis(60.0, 90.0, X, Y, 2e-4)
+    g2 = _lossy_two_layer_real_axis(60.0, 90.0, X, Y, 1e-4)
+    assert abs(2 * g2 - g1 - lossless) <= 1e-6 * abs(lossless)
+
+
 def _laplacian_residual(med, X, Y, h):
     f = lambda dx, dy: green.green_reaction(med, X + dx, Y + dy)[0]
     c = f(0, 0)
@@ -319,6 +345,40 @@ def test_cpu_fmm_matches_direct_sum():
     assert direct.rel_l2(lo.apply(q), yd) < 1e-6
     hi = fmm.CpuFmm(xy, med, tol=1e-12, leaf_size=16)
     assert direct.rel_l2(hi.apply(q), yd) < 1e-11
+
+
+LAYERED = [Medium(TWO, (60.0, 90.0)), CFG4]
+
+
+@pytest.mark.parametrize("med", LAYERED, ids=["two-layer", "three-layer"])
+def test_factorised_reaction_sum_equals_pairwise_green_function(med):
+    """direct.reaction_sum (sources summed under the Sommerfeld integral,
+    Eq. (eq:uncompressed)) equals the matrix of G^s(x_i - x_j, y_i + y_j)
+    evaluated pair by pair, each pair on its own quadrature rule, for both
+    layered media (guided-mode poles and branch points on the contour)."""
+    n = 30
+    xy = W.points_in_box(3, n, ((0.0, 0.3), (0.02, 0.32)), salt=21)
+    q = W.strengths(3, n, 2, salt=21)
+    G = np.zeros((n, n), dtype=complex)
+    for i in range(n):
+        for j in range(n):
+            G[i, j] = green.green_reaction(med, xy[i, 0] - xy[j, 0], xy[i, 1] + xy[j, 1])[0]
+    assert direct.rel_l2(direct.reaction_sum(med, xy, xy, q), q @ G.T) < 1e-12
+
+
+@pytest.mark.parametrize("med", LAYERED, ids=["two-layer", "three-layer"])
+def test_cpu_fmm_matches_direct_sum_layered(med):
+    """The plain CPU H-FMM against the O(N^2) direct sum for the two-layer
+    (k = 60 / 90) and three-layer (k = 40 / 80 / 60, d = 0.5) media, 600
+    points down to y = 0.02 above the interface: reaction M2L on four levels
+    plus directly summed leaf pairs, at tol 1e-6 and 1e-10."""
+    xy = W.points_in_box(3, 600, ((0.0, 2.0), (0.02, 2.02)), salt=22)
+    q = W.strengths(3, 600, 1, salt=22)
+    yd = direct.direct_apply(med, xy, q)
+    for tol in (1e-6, 1e-10):
+        F = fmm.CpuFmm(xy, med, tol=tol, leaf_size=8)
+        assert sum(len(F.R[l]) > 0 for l in F.R) >= 3 and len(F.direct_pairs) > 0
+        assert direct.rel_l2(F.apply(q), yd) < tol, tol
 
 
 def _table1_points(n_side):
