@@ -171,6 +171,22 @@ def test_tiny_inputs_match_direct_sum(n):
     plan.close()
 
 
+@pytest.mark.parametrize("n", [1, 2, 3, 33, 1000])
+def test_tiny_and_ragged_inputs_on_the_mixed_path(n):
+    """Mixed precision on tiny and ragged inputs (leaves of 1..4 points, a
+    ragged last tile, 3 right-hand sides) against the direct sum."""
+    from paper_1703_09136_gb300 import MIXED
+    med = W.WORKLOADS[4].medium
+    xy = W.points_in_box(4, n, ((0.0, 0.5), (0.02, 0.52)), salt=3)
+    q = W.strengths(4, n, 3, salt=3)
+    plan = Plan(xy, med, tol=1e-6, leaf_size=4, max_rhs=3, precision=MIXED)
+    y = plan.apply(q.astype(np.complex64)).astype(np.complex128)
+    assert plan.info["device_error"] == 0
+    plan.close()
+    yd = direct.direct_apply(med, xy, q)
+    assert direct.rel_l2(y, yd) < MIXED_TOL, direct.rel_l2(y, yd)
+
+
 def test_bounded_device_wait_gives_up_with_a_timeout_status():
     """The tensor-core kernels' bounded mbarrier wait: on a barrier that
     nothing completes it gives up after the given polls (HFMM_ERR_TIMEOUT,
@@ -231,8 +247,116 @@ def test_full_size_workload_on_sampled_targets(cfg):
     w, xy, q, tgt, yd = _sparse_probe(cfg)
     plan = Plan(torch.from_numpy(xy).cuda(), w.medium, tol=w.tol, leaf_size=w.leaf, max_rhs=1)
     y = plan.apply(torch.from_numpy(q).cuda()).cpu().numpy()[:, tgt]
-    assert direct.rel_l2(y, yd) < 2 * w.tol
+    err = direct.rel_l2(y, yd)
+    assert err < w.tol, (cfg, err)
     plan.close()
+
+
+def test_full_size_mixed_64_rhs_on_sampled_targets():
+    """The benchmarked configuration itself (three layers, N = 1,048,576, 64
+    right-hand sides, mixed precision with tensor cores on every level and the
+    tensor-core near field) against the oracle's direct sum: every right-hand
+    side has strengths on the same 1500 random sources (its own values), the
+    300 sampled targets are compared element by element for all 64."""
+    from paper_1703_09136_gb300 import MIXED
+    cfg = 4
+    w = W.WORKLOADS[cfg]
+    xy = W.points(cfg)
+    n = xy.shape[0]
+    src = W.sample_indices(cfg, n, 1500, salt=4)
+    tgt = W.sample_indices(cfg, n, 300, salt=5)
+    qs = W.strengths(cfg, 1500, 64, salt=10)
+    q = np.zeros((64, n), dtype=np.complex64)
+    q[:, src] = qs.astype(np.complex64)
+    qs = q[:, src].astype(np.complex128)
+    self_index = np.where(np.isin(tgt, src), np.searchsorted(src, tgt), -1)
+    yd = direct.free_sum(xy[tgt], xy[src], qs, w.medium.k1, self_index=self_index)
+    yd = yd + direct.reaction_sum(w.medium, xy[tgt], xy[src], qs)
+    plan = Plan(torch.from_numpy(xy).cuda(), w.medium, tol=w.tol, leaf_size=w.leaf, max_rhs=64, precision=MIXED)
+    inf = plan.info
+    assert inf["tensor_levels"] == inf["levels"] - inf["lmin"] + 1 and inf["leaf_l2p_fused"] == 1
+    assert inf["near_tc_blocks"] > 0
+    y = plan.apply(torch.from_numpy(q).cuda()).cpu().numpy()[:, tgt].astype(np.complex128)
+    assert plan.info["device_error"] == 0
+    plan.close()
+    assert direct.rel_l2(y, yd) < MIXED_TOL, direct.rel_l2(y, yd)
+    worst = max(direct.rel_l2(y[r], yd[r]) for r in range(64))
+    assert worst < MIXED_TOL, worst
+
+
+# --- adjoint against the oracle --------------------------------------------------
+
+def _adjoint_case(name):
+    if name == "cfg1":
+        return W.WORKLOADS[1].medium, W.points(1)
+    return CFG4_MED, W.points_in_box(4, 1200, ((0.0, 0.5), (0.02, 0.52)), salt=6)
+
+
+_dense_cache = {}
+
+
+def _dense_matrix(name):
+    """G entry by entry from the oracle's direct sum (free H0 part plus the
+    Sommerfeld-quadrature reaction, free self term dropped): column j is the
+    direct sum of the unit strength e_j.  No symmetry is assumed."""
+    if name not in _dense_cache:
+        med, xy = _adjoint_case(name)
+        n = xy.shape[0]
+        _dense_cache[name] = direct.direct_apply(med, xy, np.eye(n, dtype=complex)).T
+    return _dense_cache[name]
+
+
+def _close(got, want, tol):
+    """rel-l2 below tol, and every element within 10 tol of the largest entry."""
+    got = np.asarray(got, dtype=np.complex128)
+    e2 = direct.rel_l2(got, want)
+    emax = float(np.max(np.abs(got - want)) / np.max(np.abs(want)))
+    return e2 < tol and emax < 10 * tol, (e2, emax)
+
+
+@pytest.mark.parametrize("name", ["cfg1", "cfg4-adjoint"])
+def test_adjoint_matches_dense_oracle_matrix(name):
+    """hfmm_apply_adjoint(v) against G^H v with G built densely from the oracle
+    (Sec. 2.4: A_ij = u_{x_j}(x_i); G^H is formed explicitly, so a conjugation
+    or transposition error in the adjoint cannot cancel): FP64 at tol 1e-10,
+    mixed precision at tol 1e-6 within the mixed bound."""
+    from paper_1703_09136_gb300 import MIXED
+    med, xy = _adjoint_case(name)
+    n = xy.shape[0]
+    G = _dense_matrix(name)
+    v = W.strengths(1, n, 2, salt=13)
+    want = (G.conj().T @ v.T).T
+    p64 = Plan(xy, med, tol=1e-10, leaf_size=16, max_rhs=2)
+    ok, errs = _close(p64.adjoint(v), want, 1e-9)
+    assert ok, ("fp64", errs)
+    p32 = Plan(xy, med, tol=1e-6, leaf_size=16, max_rhs=2, precision=MIXED)
+    ok, errs = _close(p32.adjoint(v.astype(np.complex64)), want, MIXED_TOL)
+    assert ok, ("mixed", errs)
+    # the forward pass against the same matrix
+    ok, errs = _close(p64.apply(v), (G @ v.T).T, 1e-9)
+    assert ok, ("fp64 forward", errs)
+    p64.close(); p32.close()
+
+
+@pytest.mark.parametrize("name", ["cfg1", "cfg4-adjoint"])
+def test_adjoint_matches_cpu_fmm_transposed(name):
+    """The adjoint against the CPU FMM at equal p: conj(F conj v), which is
+    F^H v because the CPU FMM's operator is symmetric (symmetric lists,
+    transposition identities of its translations); FP64 per term 1e-11,
+    mixed 1e-5."""
+    from paper_1703_09136_gb300 import MIXED
+    med, xy = _adjoint_case(name)
+    n = xy.shape[0]
+    v = W.strengths(1, n, 2, salt=14)
+    F = fmm.CpuFmm(xy, med, tol=1e-6, leaf_size=16)
+    want = np.conj(F.apply(np.conj(v)))
+    p64 = Plan(xy, med, tol=1e-6, leaf_size=16, max_rhs=2)
+    got = p64.adjoint(v)
+    assert direct.rel_l2(got, want) < PARITY_TOL, direct.rel_l2(got, want)
+    p32 = Plan(xy, med, tol=1e-6, leaf_size=16, max_rhs=2, precision=MIXED)
+    got32 = p32.adjoint(v.astype(np.complex64)).astype(np.complex128)
+    assert direct.rel_l2(got32, want) < MIXED_TOL, direct.rel_l2(got32, want)
+    p64.close(); p32.close()
 
 
 # --- mixed precision ------------------------------------------------------------
@@ -510,6 +634,11 @@ def test_batch_graph_equals_individual_plans():
                 ref = single.apply(q)
                 single.close()
                 assert torch.equal(ref, y)
+        # and against the oracle's direct sum (two instances)
+        for i in (1, 3):
+            yd = direct.direct_apply(med, xys[i], W.strengths(5, sizes[i], 2, salt=i))
+            err = direct.rel_l2(ys[i].cpu().numpy().astype(np.complex128), yd)
+            assert err < (1e-6 if prec == 0 else MIXED_TOL), (prec, i, err)
         batch.close()
 
 
