@@ -11,10 +11,13 @@ built once before timing, as the paper precomputes its tables.
 
 Prints one JSON line.  value = N * nrhs / time per step / 1e6 over all ranks
 (independent replicas, one per GPU).  e2e = the same through the C ABI with
-pinned host buffers (copies inside the timed region).  cpu_baseline / the
-reference arm = the CPU oracle (plain NumPy/SciPy H-FMM) on a bounded sample
-of the same workload: the points of a 1 x 1 corner of the domain
-(same density, same distance to the interface), 64 right-hand sides.
+pinned host buffers (copies inside the timed region).  The timed plan is
+built without profiling; stage times and the leaf-kernel roofline come from a
+second, profiling plan after the timed region.  cpu_baseline / the reference
+arm = the CPU oracle (plain NumPy/SciPy H-FMM) on a bounded sample of the
+same workload: the points of a 2 x 2 corner of the domain (same density, same
+distance to the interface), all 64 right-hand sides split over one
+single-threaded worker process per host core.
 """
 from __future__ import annotations
 
@@ -34,8 +37,10 @@ if ROOT not in sys.path:
 FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 rate (no measured FP64 figure exists)
 # FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz (max SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-SAMPLE_BOX = ((0.0, 1.0), (0.02, 1.02))
+CPU_SAMPLE_SIDE = 2.0       # side of the corner of the domain the CPU oracle is timed on
 FALLBACK_BF16_TFLOPS = 1900.0  # used only when MEASURED_PEAKS.json is absent
+HEADLINE_METRIC = "H-FMM matvec Mtargets/s at N=1M (64 RHS) & rel-l2 err vs FP64; adjoint time"
+PROFILE_STEPS = 10           # applies of the profiling plan (stage and leaf-kernel times)
 
 
 # DRAM bytes of one full-size launch of the leaf-level downward kernel
@@ -93,44 +98,91 @@ def parse():
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle on a bounded sample (runs in a child process with one thread)
+# CPU oracle on a bounded sample: a child process runs a spawn pool with one
+# single-threaded worker per host core; each worker holds the oracle's plan for
+# the sample's points and applies it to its own chunk of right-hand sides.
 # ---------------------------------------------------------------------------
-_CPU_CHILD = r"""
-import json, sys, time
-sys.path.insert(0, {root!r})
-import numpy as np
-import workloads as W
-from oracle import fmm
-w = W.WORKLOADS[{cfg}]
-(x0, x1), (y0, y1) = {box!r}
-n = {n}
-xy = W.points_in_box({cfg}, n, ((x0, x1), (y0, y1)))
-q = W.strengths({cfg}, n, {nrhs})
-t0 = time.perf_counter()
-F = fmm.CpuFmm(xy, w.medium, tol=w.tol, leaf_size=16)
-plan_s = time.perf_counter() - t0
-times = []
-for _ in range({reps}):
-    t0 = time.perf_counter()
-    F.apply(q)
-    times.append(time.perf_counter() - t0)
-print(json.dumps({{"n": n, "nrhs": {nrhs}, "plan_s": plan_s, "apply_s": times}}))
-"""
+_CPU_WORKER = {}
 
 
-def cpu_oracle_sample(cfg, nrhs, reps=1, n=0):
-    w_density = 1048576 / 64.0                     # points per unit area of the 8 x 8 workload
-    (x0, x1), (y0, y1) = SAMPLE_BOX
-    n = n or int(round(w_density * (x1 - x0) * (y1 - y0)))
+def _cpu_worker_init(cfg, box, n, nrhs, lo, hi):
+    import workloads as W
+    from oracle import fmm
+    w = W.WORKLOADS[cfg]
+    xy = W.points_in_box(cfg, n, box)
+    q = W.strengths(cfg, n, nrhs)[lo:hi]
+    _CPU_WORKER["F"] = fmm.CpuFmm(xy, w.medium, tol=w.tol, leaf_size=16) if hi > lo else None
+    _CPU_WORKER["q"] = q
+
+
+def _cpu_worker_apply(_):
+    F = _CPU_WORKER["F"]
+    if F is not None:
+        F.apply(_CPU_WORKER["q"])
+    return os.getpid()
+
+
+def _cpu_child(spec):
+    """Body of the CPU child process: times `reps` applies of the oracle over
+    all right-hand sides, spread over `cores` worker processes."""
+    import multiprocessing as mp
+    cfg, box, n, nrhs, reps, cores = (spec[k] for k in ("cfg", "box", "n", "nrhs", "reps", "cores"))
+    box = tuple(tuple(b) for b in box)
+    cores = max(1, min(cores, nrhs))
+    ctx = mp.get_context("spawn")
+    bounds = [(nrhs * c // cores, nrhs * (c + 1) // cores) for c in range(cores)]
+    pools = [ctx.Pool(1, initializer=_cpu_worker_init, initargs=(cfg, box, n, nrhs, lo, hi)) for lo, hi in bounds]
+    try:
+        for pl in pools:                   # wait until every worker holds its plan
+            pl.apply(os.getpid)
+        times = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            res = [pl.apply_async(_cpu_worker_apply, (0,)) for pl in pools]
+            for r in res:
+                r.get()
+            times.append(time.perf_counter() - t0)
+    finally:
+        for pl in pools:
+            pl.terminate()
+    return {"n": n, "nrhs": nrhs, "apply_s": times, "cores": cores}
+
+
+def cpu_oracle_sample(cfg, nrhs, reps=1, n=0, side=None):
+    """The oracle on the points of a side x side corner of the workload's
+    domain at the workload's density (default 2 x 2, i.e. 1/16 of the 8 x 8
+    three-layer domain), all right-hand sides, one worker per host core."""
+    import workloads as W
+    w = W.WORKLOADS[cfg]
+    (X0, X1), (Y0, Y1) = w.box
+    density = w.n / ((X1 - X0) * (Y1 - Y0))
+    side = side or CPU_SAMPLE_SIDE
+    box = ((X0, X0 + side), (Y0, Y0 + side))
+    n = n or int(round(density * side * side))
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[v] = "1"
-    code = _CPU_CHILD.format(root=ROOT, cfg=cfg, box=SAMPLE_BOX, n=n, nrhs=nrhs, reps=reps)
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    spec = {"cfg": cfg, "box": box, "n": n, "nrhs": nrhs, "reps": reps, "cores": cores}
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child", json.dumps(spec)],
+                       capture_output=True, text=True, env=env, timeout=3600)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     out = json.loads(r.stdout.strip().splitlines()[-1])
+    out["box"] = box
+    out["share"] = n / w.n
     return out
+
+
+def _cpu_sample_text(s, t_apply):
+    return (f"CPU oracle H-FMM (oracle/fmm.py, FP64) on the {s['n']} points of the "
+            f"[{s['box'][0][0]:g}, {s['box'][0][1]:g}] x [{s['box'][1][0]:g}, {s['box'][1][1]:g}] corner of "
+            f"the workload ({100 * s['share']:.2f}% of its points, same density and medium), {s['nrhs']} RHS "
+            f"split over {s['cores']} single-threaded worker processes (one per host core); "
+            f"apply {t_apply:.2f} s (tables built in an untimed first apply)")
 
 
 # ---------------------------------------------------------------------------
@@ -152,7 +204,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -183,6 +235,38 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+def _profile_pass(Plan, xy, w, prec, nrhs, q, steps):
+    """Per-stage and leaf-kernel times from a plan built with profiling (its
+    own events around every stage; each query synchronises), kept out of the
+    timed region: returns (avg stage ms, info, leaf ms, leaf flops, near ms,
+    near flops)."""
+    from paper_1703_09136_gb300 import FP64, PART_NEAR_FREE
+    import torch
+    plan = Plan(xy, w.medium, tol=w.tol, leaf_size=w.leaf, precision=prec, max_rhs=nrhs, profile=True)
+    y = torch.empty_like(q)
+    for _ in range(2):
+        plan.apply(q, out=y)
+    stage_ms, leaf_ms, leaf_flops = {}, 0.0, 0.0
+    for _ in range(steps):
+        plan.apply(q, out=y)
+        for k, v in plan.stage_times().items():
+            stage_ms[k] = stage_ms.get(k, 0.0) + v / steps
+        if prec != FP64:
+            lm, lf = plan.leaf_down_time()
+            leaf_ms += lm / steps
+            leaf_flops += lf / steps
+    info = plan.info
+    # the near field alone (no far field, so nothing runs beside it)
+    near_ms = near_flops = 0.0
+    if prec != FP64:
+        for _ in range(3):
+            plan.apply(q, out=y, parts=PART_NEAR_FREE)
+            near_ms += plan.stage_times()["p2p"] / 3
+            near_flops += plan.info["flops_last_apply"]["p2p"] / 3
+    plan.close()
+    return stage_ms, info, leaf_ms, leaf_flops, near_ms, near_flops
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -218,8 +302,9 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     xy = torch.from_numpy(xy_h).to(dev)
     q = torch.from_numpy(q_h).to(dev, cdt)
+    # the timed plan: no profiling, so the K applies run back to back
     t0 = time.perf_counter()
-    plan = Plan(xy, w.medium, tol=w.tol, leaf_size=w.leaf, precision=prec, max_rhs=nrhs, profile=True)
+    plan = Plan(xy, w.medium, tol=w.tol, leaf_size=w.leaf, precision=prec, max_rhs=nrhs)
     torch.cuda.synchronize()
     plan_s = time.perf_counter() - t0
     y = torch.empty_like(q)
@@ -233,18 +318,10 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    stage_ms = {}
-    leaf_ms = leaf_flops = 0.0
     torch.cuda.synchronize()
     ev0.record(stream)
     for _ in range(args.steps):
         plan.apply(q, out=y)
-        for k, v in plan.stage_times().items():
-            stage_ms[k] = stage_ms.get(k, 0.0) + v
-        if prec != FP64:
-            lm, lf = plan.leaf_down_time()
-            leaf_ms += lm
-            leaf_flops += lf
     ev1.record(stream)
     torch.cuda.synchronize()
     total_ms = ev0.elapsed_time(ev1)
@@ -256,60 +333,6 @@ def run_ours(args):
     value = world * n * nrhs / (ms_per_step * 1e-3) / 1e6
     info = plan.info
     launches = int(info["launches_last_apply"]) * args.steps
-    # roofline of the dominant stage
-    avg = {k: v / args.steps for k, v in stage_ms.items()}
-    dom = max(avg, key=avg.get)
-    flops = info["flops_last_apply"][dom]
-    bound = "alu"
-    if prec == FP64:
-        peak, src = FP64_PEAK_TFLOPS, "nominal GB300 FP64 rate (MEASURED_PEAKS.json has no FP64 figure)"
-    elif dom in ("m2m", "down") and info["tensor_levels"] > 0:
-        # FP32-accurate terms as three f16 tensor-core products (hi*hi + hi*lo +
-        # lo*hi, kind::f16 with FP32 accumulation): the measured bf16 burst
-        # peak (f16 runs at the bf16 rate) / 3
-        bf16, how = _measured_bf16()
-        peak = bf16 / 3.0
-        src = f"derived 3xF16 peak: {how} bf16 {bf16:.1f} TFLOP/s (= f16 rate) / 3"
-        bound = "tensor"
-    else:
-        peak, src = FP32_PEAK_TFLOPS, "derived FP32 SIMT peak: 152 SMs x 128 lanes x 2 x 2.07 GHz"
-    roof = {"kernel": dom, "bound": bound, "achieved": flops / (avg[dom] * 1e-3) / 1e12,
-            "peak": peak, "unit": "TFLOP/s", "traffic": None, "peak_source": src}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    stage_roof = None
-    if leaf_ms > 0.0 and bound == "tensor":
-        # the dominant kernel itself: the leaf-level downward launch, its CUDA-event
-        # time on the launching stream (the library's events) and its algorithmic flops
-        stage_roof = dict(roof, kernel=f"stage '{dom}' (all levels)")
-        roof = {"kernel": f"m2l_tc_kernel<{info['leaf_tc_width']}> (leaf-level downward: L2L + free and reaction "
-                          f"M2L{' + L2P' if info['leaf_l2p_fused'] else ''})",
-                "bound": "tensor", "achieved": leaf_flops / (leaf_ms * 1e-3) / 1e12, "peak": peak,
-                "unit": "TFLOP/s",
-                "traffic": (LEAF48_TRAFFIC_BYTES if info["leaf_tc_width"] == 48 and info["leaf_l2p_fused"]
-                            and n == 1048576 and nrhs == 64 else None),
-                "traffic_source": "ncu dram bytes of the 65536-point case (4096 leaves) x 16 leaves",
-                "peak_source": src,
-                "launch_ms": leaf_ms / args.steps}
-        roof["frac"] = roof["achieved"] / roof["peak"]
-        # the timed region is 30 short applies at full clock: the burst figure applies;
-        # against the seconds-long (sustained) bf16 figure for comparison
-        sus, _ = _measured_bf16("bf16_tflops_sustained")
-        roof["frac_vs_sustained"] = roof["achieved"] / (sus / 3.0)
-    # the near field alone (no far field, so nothing runs beside it): its own
-    # CUDA-event time and algorithmic flops, against the same 3xF16 peak
-    near_roof = None
-    if prec != FP64 and stage_roof is not None:
-        from paper_1703_09136_gb300 import PART_NEAR_FREE
-        nm = nf = 0.0
-        for _ in range(3):
-            plan.apply(q, out=y, parts=PART_NEAR_FREE)
-            nm += plan.stage_times()["p2p"]
-            nf += plan.info["flops_last_apply"]["p2p"]
-        if nm > 0.0:
-            near_roof = {"kernel": "p2p_tc_kernel (near-field P2P, precomputed Green's-function tiles)",
-                         "bound": "tensor", "achieved": nf / (nm * 1e-3) / 1e12, "peak": peak,
-                         "unit": "TFLOP/s", "launch_ms": nm / 3, "peak_source": src}
-            near_roof["frac"] = near_roof["achieved"] / near_roof["peak"]
     # end to end through the C ABI with pinned host buffers
     qh = torch.from_numpy(q_h).to(cdt).pin_memory()
     yh = torch.empty_like(qh).pin_memory()
@@ -323,29 +346,17 @@ def run_ours(args):
     cbytes = 16 if prec == FP64 else 8
     e2e = {"value": world * n * nrhs / e2e_s / 1e6, "unit": "Mtargets/s",
            "h2d_bytes_per_step": cbytes * n * nrhs, "d2h_bytes_per_step": cbytes * n * nrhs}
-    out = {
-        "metric": "H-FMM matvec throughput (targets x RHS per second), three-layer medium, N=1M, 64 RHS",
-        "value": value, "unit": "Mtargets/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == FP64 else "f32", "data": "synthetic",
-        "config": {"workload": w.name, "n": n, "nrhs": nrhs, "medium": "three-layer k=40/80/60 d=0.5",
-                   "tol": w.tol, "levels": info["levels"], "p": info["p"], "plan_s": plan_s,
-                   "l2": "inputs larger than L2 (q, y and expansions are GBs)",
-                   **({"box": args.box} if args.box else {}),
-                   "parallelism": f"replicas{world}"},
-        "stage_ms": avg, "adjoint_ms": None, "gpu_launches": launches, "e2e": e2e, "roofline": roof,
-        **({"roofline_stage": stage_roof} if stage_roof else {}),
-        **({"roofline_near": near_roof} if near_roof else {}),
-        "clocks": ck,
-    }
-    # adjoint time
-    ev0.record(stream)
+    # adjoint time (one warm-up, then the mean of five)
     plan.adjoint(q, out=y)
+    ev0.record(stream)
+    for _ in range(5):
+        plan.adjoint(q, out=y)
     ev1.record(stream)
     torch.cuda.synchronize()
-    out["adjoint_ms"] = ev0.elapsed_time(ev1)
+    adjoint_ms = ev0.elapsed_time(ev1) / 5
     # accuracy against the plain FP64 path on the first right-hand sides, and
     # the FP64 path's time for one right-hand side
+    accuracy = fp64_ms = None
     if prec != FP64 and not args.no_fp64_check:
         nchk = min(2, nrhs)
         plan.apply(q, out=y)
@@ -362,18 +373,82 @@ def run_ours(args):
         p64.apply(q1, out=y1)
         ev1.record(stream)
         torch.cuda.synchronize()
-        out["accuracy"] = {"rel_l2_vs_fp64": err, "rhs_compared": nchk}
-        out["fp64_one_rhs_ms"] = ev0.elapsed_time(ev1)
+        accuracy = {"rel_l2_vs_fp64": err, "rhs_compared": nchk}
+        fp64_ms = ev0.elapsed_time(ev1)
         p64.close()
+    plan.close()
+    del y
+    # stage and leaf-kernel times from a profiling plan, outside the timed region
+    avg, pinfo, leaf_ms, leaf_flops, near_ms, near_flops = _profile_pass(Plan, xy, w, prec, nrhs, q,
+                                                                          PROFILE_STEPS)
+    dom = max(avg, key=avg.get)
+    flops = pinfo["flops_last_apply"][dom]
+    bound = "alu"
+    if prec == FP64:
+        peak, src = FP64_PEAK_TFLOPS, "nominal GB300 FP64 rate (MEASURED_PEAKS.json has no FP64 figure)"
+    elif dom in ("m2m", "down") and pinfo["tensor_levels"] > 0:
+        # FP32-accurate terms as three f16 tensor-core products (hi*hi + hi*lo +
+        # lo*hi, kind::f16 with FP32 accumulation): the measured bf16 burst
+        # peak (f16 runs at the bf16 rate) / 3
+        bf16, how = _measured_bf16()
+        peak = bf16 / 3.0
+        src = f"derived 3xF16 peak: {how} bf16 {bf16:.1f} TFLOP/s (= f16 rate) / 3"
+        bound = "tensor"
+    else:
+        peak, src = FP32_PEAK_TFLOPS, "derived FP32 SIMT peak: 152 SMs x 128 lanes x 2 x 2.07 GHz"
+    roof = {"kernel": dom, "bound": bound, "achieved": flops / (avg[dom] * 1e-3) / 1e12,
+            "peak": peak, "unit": "TFLOP/s", "traffic": None, "peak_source": src}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    stage_roof = near_roof = None
+    if leaf_ms > 0.0 and bound == "tensor":
+        # the dominant kernel itself: the leaf-level downward launch, its CUDA-event
+        # time on the launching stream (the library's events) and its algorithmic flops
+        stage_roof = dict(roof, kernel=f"stage '{dom}' (all levels)")
+        roof = {"kernel": f"m2l_tc_kernel<{pinfo['leaf_tc_width']}> (leaf-level downward: L2L + free and reaction "
+                          f"M2L{' + L2P' if pinfo['leaf_l2p_fused'] else ''})",
+                "bound": "tensor", "achieved": leaf_flops / (leaf_ms * 1e-3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s",
+                "traffic": (LEAF48_TRAFFIC_BYTES if pinfo["leaf_tc_width"] == 48 and pinfo["leaf_l2p_fused"]
+                            and n == 1048576 and nrhs == 64 else None),
+                "traffic_source": "ncu dram bytes of the 65536-point case (4096 leaves) x 16 leaves",
+                "peak_source": src,
+                "launch_ms": leaf_ms,
+                "timing": f"CUDA events around the launch on its stream, mean of {PROFILE_STEPS} applies "
+                          "of a profiling plan after the timed region"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        sus, _ = _measured_bf16("bf16_tflops_sustained")
+        roof["frac_vs_sustained"] = roof["achieved"] / (sus / 3.0)
+        if near_ms > 0.0:
+            near_roof = {"kernel": "p2p_tc_kernel (near-field P2P, precomputed Green's-function tiles)",
+                         "bound": "tensor", "achieved": near_flops / (near_ms * 1e-3) / 1e12, "peak": peak,
+                         "unit": "TFLOP/s", "launch_ms": near_ms, "peak_source": src}
+            near_roof["frac"] = near_roof["achieved"] / near_roof["peak"]
+    medium = {0: f"impedance k={w.medium.k[0]:g} alpha={w.medium.alpha:g}",
+              1: f"two-layer k={w.medium.k[0]:g}/{w.medium.k[1]:g}",
+              2: f"three-layer k={w.medium.k[0]:g}/{w.medium.k[1]:g}/{w.medium.k[2]:g} d={w.medium.d:g}"}[w.medium.kind]
+    out = {
+        "metric": _metric_name(cfg, w, n, nrhs),
+        "value": value, "unit": "Mtargets/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == FP64 else "f32", "data": "synthetic",
+        "config": {"workload": w.name, "n": n, "nrhs": nrhs, "medium": medium,
+                   "tol": w.tol, "levels": info["levels"], "p": info["p"], "plan_s": plan_s,
+                   "l2": "inputs larger than L2 (q, y and expansions are GBs)",
+                   **({"box": args.box} if args.box else {}),
+                   "parallelism": f"replicas{world}"},
+        "stage_ms": avg, "adjoint_ms": adjoint_ms, "gpu_launches": launches, "e2e": e2e, "roofline": roof,
+        **({"roofline_stage": stage_roof} if stage_roof else {}),
+        **({"roofline_near": near_roof} if near_roof else {}),
+        **({"accuracy": accuracy, "fp64_one_rhs_ms": fp64_ms} if accuracy else {}),
+        "clocks": ck,
+    }
     if rank == 0 and not args.no_cpu_baseline:
         s = cpu_oracle_sample(cfg, nrhs, reps=2, n=args.cpu_sample_n)
-        t_apply = min(s["apply_s"])
-        out["cpu_baseline"] = {"value": s["n"] * s["nrhs"] / t_apply / 1e6, "unit": "Mtargets/s", "cores": 1,
-                               "kind": "oracle",
-                               "sample": f"CPU oracle H-FMM on the {s['n']} points of the {SAMPLE_BOX} corner "
-                                         f"of the workload (same density and medium), {s['nrhs']} RHS; "
-                                         f"apply {t_apply:.2f} s, plan {s['plan_s']:.2f} s, 1 thread"}
-    plan.close()
+        t_apply = s["apply_s"][-1]
+        out["cpu_baseline"] = {"value": s["n"] * s["nrhs"] / t_apply / 1e6, "unit": "Mtargets/s",
+                               "cores": s["cores"], "kind": "oracle", "sample": _cpu_sample_text(s, t_apply)}
+        out["config"]["cpu_sample"] = {"n": s["n"], "share_of_points": s["share"], "box": s["box"],
+                                       "cores": s["cores"]}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -385,7 +460,18 @@ def plan_lib_apply():
     return library().hfmm_apply
 
 
+def _metric_name(cfg, w, n, nrhs):
+    if cfg == 4 and n == w.n and nrhs == w.nrhs:
+        return HEADLINE_METRIC
+    kind = {0: "impedance half-space", 1: "two-layer", 2: "three-layer"}[w.medium.kind]
+    return f"H-FMM matvec throughput (targets x RHS per second), {kind} medium, N={n}, {nrhs} RHS"
+
+
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, on every host core, each
+    step one apply over all right-hand sides on a corner of the workload
+    (2 x 2 when the whole run is at most 12 steps, else 1 x 1 so that it ends
+    within a few minutes)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -394,20 +480,21 @@ def run_reference(args):
     cfg = args.config
     w = W.WORKLOADS[cfg]
     nrhs = args.nrhs or w.nrhs
-    s = cpu_oracle_sample(cfg, nrhs, reps=args.warmup + args.steps, n=args.cpu_sample_n)
-    times = s["apply_s"][args.warmup:]
+    side = CPU_SAMPLE_SIDE if args.warmup + args.steps <= 12 else 1.0
+    s = cpu_oracle_sample(cfg, nrhs, reps=max(1, args.warmup) + args.steps, n=args.cpu_sample_n, side=side)
+    times = s["apply_s"][max(1, args.warmup):]
     t = sum(times) / len(times)
     value = s["n"] * s["nrhs"] / t / 1e6
-    sample = (f"CPU oracle H-FMM on the {s['n']} points of the {SAMPLE_BOX} corner of the workload, "
-              f"{s['nrhs']} RHS, 1 thread")
-    out = {"impl": "reference", "metric": "H-FMM matvec throughput (targets x RHS per second), "
-                                          "three-layer medium, N=1M, 64 RHS",
+    out = {"impl": "reference", "metric": _metric_name(cfg, w, args.n or w.n, nrhs),
            "value": value, "unit": "Mtargets/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic",
-           "config": {"workload": w.name, "n": w.n, "nrhs": s["nrhs"], "medium": "three-layer k=40/80/60 d=0.5",
-                      "tol": w.tol, "sample_n": s["n"], "parallelism": "rank 0 only (CPU)"},
-           "cpu_baseline": {"value": value, "unit": "Mtargets/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "config": {"workload": w.name, "n": w.n, "nrhs": s["nrhs"], "tol": w.tol,
+                      "cpu_sample": {"n": s["n"], "share_of_points": s["share"], "box": s["box"],
+                                     "cores": s["cores"]},
+                      "parallelism": "rank 0 only (CPU)"},
+           "cpu_baseline": {"value": value, "unit": "Mtargets/s", "cores": s["cores"], "kind": "oracle",
+                            "sample": _cpu_sample_text(s, t)},
            "e2e": {"value": value, "unit": "Mtargets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -509,6 +596,9 @@ def run_batch(args):
 
 
 def main():
+    if len(sys.argv) == 3 and sys.argv[1] == "--cpu-child":
+        print(json.dumps(_cpu_child(json.loads(sys.argv[2]))), flush=True)
+        return
     args = parse()
     if args.impl == "reference":
         run_reference(args)

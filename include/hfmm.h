@@ -300,13 +300,15 @@ hfmm_status hfmm_plan_get_stage_times(hfmm_plan_t plan, double* ms);
  *               leaf with Morton index b are perm[leaf_begin[b] .. leaf_begin[b+1]).
  * Limits: 1 <= n <= HFMM_NOALLOC_MAX_POINTS and 2 <= levels <=
  * HFMM_NOALLOC_MAX_LEVELS; anything larger returns INVALID_ARG with a message
- * naming the limit.  Non-finite coordinates or y <= 0 return INVALID_ARG
- * (the call waits for `stream` to read that check back).
+ * naming the limit.  Non-finite coordinates or y <= 0 return INVALID_ARG.
+ * Every call synchronises `stream` once, after the bounding-box pass, to read
+ * that input check back to the host; the remaining work is queued on `stream`
+ * without waiting.
  *
  * All temporaries live in one static device array of about 6 MB that every
  * GPU loading this library holds until the process exits.  The first call on
  * a device looks up that array's device address (with that device current);
- * make the first call before any stream capture.  Every call shares the
+ * make that first call before any stream capture.  Every call shares the
  * array and it keeps the last call's contents: calls whose work overlaps on
  * the GPU (other streams, other host threads) race and must be serialised by
  * the caller.
