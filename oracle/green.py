@@ -141,18 +141,50 @@ def _panels(a, b, n):
     return x, w
 
 
+def _edge_panels(edges):
+    """Gauss-Legendre nodes and weights on the panels between given edges."""
+    edges = np.asarray(edges, dtype=float)
+    lo, hi = edges[:-1], edges[1:]
+    half = 0.5 * (hi - lo)
+    mid = 0.5 * (hi + lo)
+    x = (mid[:, None] + half[:, None] * _GL_X[None, :]).ravel()
+    w = (half[:, None] * _GL_W[None, :]).ravel()
+    return x, w
+
+
+def impedance_pole_tau(medium):
+    """The impedance sigma_hat = (s1 + i alpha)/(s1 - i alpha) (Sec. 2.2) has a
+    pole at s1 = i alpha.  On the propagating path s1 = -i k1 sin tau, so for
+    0 < alpha < k1 the pole lies on the real tau axis at -delta and
+    pi + delta, delta = asin(alpha / k1); returns delta (None otherwise)."""
+    if medium.kind == IMPEDANCE and 0.0 < medium.alpha < medium.k1:
+        return math.asin(medium.alpha / medium.k1)
+    return None
+
+
 def tau_rule(medium, xmax, ymax, nmax, refine=1):
     """Nodes and weights on [0, pi] for integrands e^{i k1 (Y sin - X cos)}
-    e^{-i n tau} sigma with |X| <= xmax, Y <= ymax, |n| <= nmax."""
+    e^{-i n tau} sigma with |X| <= xmax, Y <= ymax, |n| <= nmax.  Near an
+    impedance pole no panel is wider than 1.5 times its distance to it."""
     k1 = medium.k1
     rate = k1 * (abs(xmax) + abs(ymax)) + nmax + 1.0
     if medium.kind == THREE_LAYER:
         rate += 2.0 * medium.d * max(abs(medium.k[1]), k1)   # e^{-2 s2 d} of sigma_1
     brk = [0.0] + tau_kinks(medium) + [math.pi]
+    delta = impedance_pole_tau(medium)
     xs, ws = [], []
     for a, b in zip(brk[:-1], brk[1:]):
         n = refine * (int(math.ceil((b - a) * rate / 5.0)) + 2)
-        x, w = _panels(a, b, n)
+        if delta is None:
+            x, w = _panels(a, b, n)
+        else:
+            width = (b - a) / n
+            edges = [a]
+            while edges[-1] < b:
+                e = edges[-1]
+                step = min(width, 1.5 * (e + delta) / refine, 0.6 * (math.pi + delta - e) / refine, b - e)
+                edges.append(b if b - (e + step) < 1e-14 else e + step)
+            x, w = _edge_panels(edges)
         xs.append(x)
         ws.append(w)
     return np.concatenate(xs), np.concatenate(ws)
@@ -218,10 +250,14 @@ def t_rule(medium, xmax, ymin, nmax, refine=1):
         wmax = min(wmax, 5.0 / xmax)
     if medium.kind == THREE_LAYER and medium.d > 0:
         wmax = min(wmax, 2.5 / medium.d)
+    # impedance pole at t = i alpha (Sec. 2.2): panel width <= 1.5 x its distance
+    alpha = medium.alpha if medium.kind == IMPEDANCE and medium.alpha > 0 else None
     edges = [u0]
     a = u0
     while a < T:
         w = min(wmax, max(5.0 * max(a, 0.5 / k1) / max(nmax, 1), 0.02 * wmax, 1e-3), T - a)
+        if alpha is not None:
+            w = min(w, 1.5 * math.hypot(a, alpha))
         w = max(w / refine, 1e-12)
         a = a + w
         edges.append(a)

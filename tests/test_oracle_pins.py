@@ -63,6 +63,19 @@ def test_impedance_reaction_equals_complex_line_image(X, Y):
     assert abs(a - b) <= 2e-12 * abs(b) + 1e-15
 
 
+@pytest.mark.parametrize("alpha", [0.5, 2.0, 19.0])
+@pytest.mark.parametrize("X,Y", [(0.0, 0.1), (0.1, 0.2), (0.5, 0.3)])
+def test_impedance_reaction_with_a_pole_near_the_path(alpha, X, Y):
+    """sigma_hat (Sec. 2.2) has a pole at s1 = i alpha: at t = i alpha off the
+    evanescent path and, for alpha < k, on the real tau axis just outside
+    [0, pi].  Small alpha / k brings it close to both paths; the quadrature
+    must still reproduce the complex line image of Eq. (Sfield)."""
+    med = Medium(IMP, (20.0,), alpha=alpha)
+    a = green.green_reaction(med, X, Y)[0]
+    b = green.green_reaction_line_image(20.0, alpha, X, Y)
+    assert abs(a - b) <= 1e-11 * abs(b)
+
+
 @pytest.mark.parametrize("X,Y", [(0.0, 0.2), (0.37, 0.15), (-1.3, 0.6)])
 def test_impedance_limits_are_image_sources(X, Y):
     r = math.hypot(X, Y)
