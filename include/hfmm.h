@@ -99,7 +99,21 @@ typedef struct {
     int64_t spin_limit;         /* polls of each bounded device wait (each suspends <= ~1 us);
                                    0 = default (2e6, about 2 s).  A wait that gives up sets
                                    device_error; host-buffer applies then return HFMM_ERR_TIMEOUT */
+    double quad_scale;          /* scale of the panel counts of every table quadrature rule
+                                   (0 = 1).  Each reaction table entry and each directly summed
+                                   block is also computed on the rule with twice the panels;
+                                   hfmm_plan_create returns HFMM_ERR_NUMERICS when the two differ
+                                   by more than 1e-12 (relative, weighted by what the normalised
+                                   expansions can reach; see hfmm_plan_info.table_check).
+                                   Values below 1 coarsen the rules (a test of that check). */
+    int32_t small_rhs;          /* HFMM_MIXED: applies with nrhs <= small_rhs run on warp-level
+                                   SIMT kernels (one warp per box and coefficient chunk, a few
+                                   right-hand sides per pass) instead of the tensor-core tiles,
+                                   whose 128-row tiles hold 64 right-hand sides; 0 = default
+                                   (HFMM_SMALL_RHS_DEFAULT), -1 = never */
 } hfmm_options;
+
+#define HFMM_SMALL_RHS_DEFAULT 4
 
 /* Option flags. */
 #define HFMM_FLAG_PROFILE 1     /* record CUDA events around every stage of each apply */
@@ -151,6 +165,10 @@ typedef struct {
                                    epilogue, 0 if on the SIMT kernel */
     int32_t leaf_tc_width;      /* HFMM_MIXED: column-block width (MMA N) of the leaf-level
                                    tensor-core pass, 0 without one */
+    double table_check;         /* largest difference between a quadrature table entry (reaction
+                                   A_n, weighted by s(|m|) s(|p|) of the translations it feeds,
+                                   or a directly summed G^s block) and its node-doubled value,
+                                   relative to the entry's largest weighted value (<= 1e-12) */
 } hfmm_plan_info;
 
 /* Bits of `parts` in hfmm_apply_parts (sum of the selected terms). */

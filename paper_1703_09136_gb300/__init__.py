@@ -104,7 +104,8 @@ class Plan:
     """An H-FMM plan for fixed points: y = A q with A_ij = u_{x_j}(x_i)."""
 
     def __init__(self, xy, medium, tol=1e-6, p=0, leaf_size=32, levels=0, precision=FP64,
-                 max_rhs=1, stream=None, profile=False, simt_m2l=False, autotune=False, spin_limit=0):
+                 max_rhs=1, stream=None, profile=False, simt_m2l=False, autotune=False, spin_limit=0,
+                 quad_scale=0.0, small_rhs=0):
         lib = _n.lib()
         m = Medium.of(medium)
         opts = _n.hfmm_options()
@@ -118,6 +119,8 @@ class Plan:
         opts.flags = ((_n.FLAG_PROFILE if profile else 0) | (_n.FLAG_SIMT_M2L if simt_m2l else 0) |
                       (_n.FLAG_AUTOTUNE if autotune else 0))
         opts.spin_limit = int(spin_limit)
+        opts.quad_scale = float(quad_scale)
+        opts.small_rhs = int(small_rhs)
         torch = _torch()
         if torch is not None and isinstance(xy, torch.Tensor):
             if xy.dtype != torch.float64:
@@ -282,13 +285,14 @@ class Batch:
     (hfmm_batch_*).  xys: list of [n_i, 2] float64 arrays / tensors."""
 
     def __init__(self, xys, medium, tol=1e-6, p=0, leaf_size=32, levels=0, precision=FP64, max_rhs=1,
-                 stream=None, simt_m2l=False, spin_limit=0):
+                 stream=None, simt_m2l=False, spin_limit=0, small_rhs=0):
         lib = _n.lib()
         m = Medium.of(medium)
         opts = _n.hfmm_options()
         lib.hfmm_options_default(ctypes.byref(opts))
         opts.tol, opts.p, opts.leaf_size, opts.levels = float(tol), int(p), int(leaf_size), int(levels)
         opts.precision, opts.max_rhs = int(precision), int(max_rhs)
+        opts.small_rhs = int(small_rhs)
         opts.flags = _n.FLAG_SIMT_M2L if simt_m2l else 0
         opts.spin_limit = int(spin_limit)
         keep = [_ptr(np.ascontiguousarray(x, dtype=np.float64) if not hasattr(x, "data_ptr") else x.contiguous())

@@ -43,7 +43,8 @@ class hfmm_medium(ctypes.Structure):
 class hfmm_options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("p", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
                 ("levels", ctypes.c_int32), ("precision", ctypes.c_int32), ("max_rhs", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("spin_limit", ctypes.c_int64)]
+                ("flags", ctypes.c_int32), ("spin_limit", ctypes.c_int64), ("quad_scale", ctypes.c_double),
+                ("small_rhs", ctypes.c_int32)]
 
 
 class hfmm_plan_info(ctypes.Structure):
@@ -59,7 +60,8 @@ class hfmm_plan_info(ctypes.Structure):
                 ("device_error", ctypes.c_int32), ("tensor_levels", ctypes.c_int32),
                 ("tune_levels", ctypes.c_int32 * 3), ("tune_ms", ctypes.c_double * 3),
                 ("near_tc_blocks", ctypes.c_int64), ("near_simt_leaves", ctypes.c_int64),
-                ("leaf_l2p_fused", ctypes.c_int32), ("leaf_tc_width", ctypes.c_int32)]
+                ("leaf_l2p_fused", ctypes.c_int32), ("leaf_tc_width", ctypes.c_int32),
+                ("table_check", ctypes.c_double)]
 
 
 hfmm_plan_t = ctypes.c_void_p

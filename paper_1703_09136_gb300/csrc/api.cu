@@ -249,6 +249,11 @@ static hfmm_status plan_create_one(hfmm_plan_t* out, int64_t n, const double* xy
     }
     if (o.levels < 0 || o.levels > 15) { hfmm_set_error("levels must be in [0, 15]"); return HFMM_ERR_INVALID_ARG; }
     if (o.spin_limit < 0) { hfmm_set_error("spin_limit must be >= 0"); return HFMM_ERR_INVALID_ARG; }
+    if (o.small_rhs < -1) { hfmm_set_error("small_rhs must be >= -1"); return HFMM_ERR_INVALID_ARG; }
+    if (!(o.quad_scale >= 0.0) || !std::isfinite(o.quad_scale) || o.quad_scale > 64.0) {
+        hfmm_set_error("quad_scale must be in [0, 64] (got %g)", o.quad_scale);
+        return HFMM_ERR_INVALID_ARG;
+    }
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t st = (cudaStream_t)stream;
     hfmm_plan_s* P = new (std::nothrow) hfmm_plan_s();
@@ -261,6 +266,8 @@ static hfmm_status plan_create_one(hfmm_plan_t* out, int64_t n, const double* xy
     P->max_rhs = o.max_rhs;
     P->flags = o.flags;
     P->tc_spin = o.spin_limit > 0 ? (long)o.spin_limit : tc::TC_SPIN;
+    P->quad_scale = o.quad_scale > 0.0 ? o.quad_scale : 1.0;
+    P->small_rhs = o.small_rhs == 0 ? HFMM_SMALL_RHS_DEFAULT : std::max(0, (int)o.small_rhs);
     P->L = o.levels > 0 ? o.levels : choose_levels(n, o.leaf_size);
     hfmm_status s = HFMM_OK;
     do {
@@ -305,6 +312,7 @@ static hfmm_status plan_create_one(hfmm_plan_t* out, int64_t n, const double* xy
         if (mixed) {
             if ((s = build_tables32(P, st)) != HFMM_OK) break;
             if ((s = init_h0_table(st)) != HFMM_OK) break;
+            if ((s = init_small(P, st)) != HFMM_OK) break;
             if ((s = build_local_coords(P, st)) != HFMM_OK) break;
             if (!(P->flags & HFMM_FLAG_SIMT_M2L) && (s = build_tc(P, st)) != HFMM_OK) break;
             if (P->tc_on && (s = build_p2p_tc(P, st)) != HFMM_OK) break;
@@ -511,6 +519,7 @@ hfmm_status hfmm_plan_get_info(hfmm_plan_t P, hfmm_plan_info* info) {
     info->leaf_l2p_fused = P->tc_l2p ? 1 : 0;
     info->leaf_tc_width = P->tc_on ? P->lev[P->L].tc_nbw : 0;
     info->near_simt_leaves = P->nt_nfallback;
+    info->table_check = P->table_check;
     return HFMM_OK;
 }
 

@@ -647,6 +647,19 @@ __global__ void direct32_kernel(const int32_t* lb, const int32_t* d_begin, const
 
 }  // namespace
 
+// Host copy of the fitted FP32 H0 table (64 intervals x 6 coefficients of J0,
+// then of R0), for kernels of other translation units.
+const float* h0_table_host() {
+    static float both[2][H0_NI][H0_DEG + 1];
+    if (!h0_ready) {
+        fit_h0_table();
+        h0_ready = true;
+    }
+    std::copy(&h_h0j[0][0], &h_h0j[0][0] + H0_NI * (H0_DEG + 1), &both[0][0][0]);
+    std::copy(&h_h0r[0][0], &h_h0r[0][0] + H0_NI * (H0_DEG + 1), &both[1][0][0]);
+    return &both[0][0][0];
+}
+
 hfmm_status init_h0_table(cudaStream_t st) {
     if (!h0_ready) {
         fit_h0_table();
@@ -806,154 +819,160 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
     tm.end(HFMM_STAGE_GATHER);
     P->st_bytes[HFMM_STAGE_GATHER] = 2.0 * C * n + 8.0 * n;
     const bool far = (parts & (HFMM_PART_FAR_FREE | HFMM_PART_FAR_REACT)) != 0;
-    // near free-space field and, unless the downward epilogue does it, the
-    // leaves' local expansions (L2P), one fused kernel
-    auto near_section = [&](bool near, bool l2p, cudaStream_t ns) -> hfmm_status {
-        const LevelInfo& lv = P->lev[L];
-        StageTimer tn{P, ns};
-        tn.begin(HFMM_STAGE_P2P);
-        if (P->tc_on) {
-            // P2P: tensor-core blocks of four leaves (first writer of their targets), SIMT
-            // kernel for the leaves of wider blocks; a separate L2P on the SIMT kernel
-            if (near) {
-                HFMM_TRY(launch_p2p_tc(P, nrhs, ns));
-                ++P->launches;
-            }
-            if (P->nt_nfallback > 0 && (near || l2p)) {
-                p2p32c_kernel<<<(unsigned)P->nt_nfallback, PC_THREADS, 0, ns>>>(
-                    P->leaf_begin, L, P->xl32, P->q32, n, nrhs, (float)P->k, (float)lv.h, near ? 1 : 0,
-                    l2p ? lv.loc32 : nullptr, P->basis32, lv.ncoef, P->nt_fallback, P->y32);
-                ++P->launches;
-                HFMM_CUDA_TRY(cudaGetLastError());
-            }
-            if (l2p && P->nt_nblocks > 0) {
-                p2p32c_kernel<<<(unsigned)P->nt_nleaves, PC_THREADS, 0, ns>>>(
-                    P->leaf_begin, L, P->xl32, P->q32, n, nrhs, (float)P->k, (float)lv.h, 0, lv.loc32, P->basis32,
-                    lv.ncoef, P->nt_leaves, P->y32);
-                ++P->launches;
-                HFMM_CUDA_TRY(cudaGetLastError());
-            }
-        } else {
-            p2p32c_kernel<<<(unsigned)lv.nbox, PC_THREADS, 0, ns>>>(P->leaf_begin, L, P->xl32, P->q32, n, nrhs,
-                                                                    (float)P->k, (float)lv.h, near ? 1 : 0,
-                                                                    l2p ? lv.loc32 : nullptr, P->basis32, lv.ncoef,
-                                                                    nullptr, P->y32);
-            ++P->launches;
-            HFMM_CUDA_TRY(cudaGetLastError());
-        }
-        tn.end(HFMM_STAGE_P2P);
-        P->st_flops[HFMM_STAGE_P2P] = (near ? MAC * (double)P->p2p_point_pairs : 0.0) +
-                                      (l2p ? MAC * n * lv.ncoef : 0.0);
-        P->st_bytes[HFMM_STAGE_P2P] = 3.0 * C * n + 16.0 * n + (l2p ? C * lv.nbox * lv.ncoef + 8.0 * n * lv.ncoef : 0.0);
-        return HFMM_OK;
-    };
-    const bool near_free = (parts & HFMM_PART_NEAR_FREE) != 0;
-    // the tensor-core pass fuses both far parts of a level; subsets run on SIMT cores
-    const bool tc_down = P->tc_on && (parts & HFMM_PART_FAR_FREE) && (parts & HFMM_PART_FAR_REACT);
-    // L2P in the leaf-level downward epilogue: the near field is then independent
-    // of the far field until the leaves' L2P adds into y32, so it runs concurrently
-    // (first writer of y32) on a low-priority stream while the far-field chain runs
-    // on a high-priority one: the near field fills what the chain leaves idle (the
-    // coarse levels launch few CTAs); both join before the leaf-level launch
-    const bool l2p_fused = far && tc_down && P->tc_l2p;
-    const bool concurrent = l2p_fused && near_free;
-    cudaStream_t fs = st;
-    if (concurrent) {
-        if (!P->far_st) {
-            int least = 0, greatest = 0;
-            HFMM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-            HFMM_CUDA_TRY(cudaStreamCreateWithPriority(&P->far_st, cudaStreamNonBlocking, greatest));
-            HFMM_CUDA_TRY(cudaStreamCreateWithPriority(&P->near_st, cudaStreamNonBlocking, least));
-            for (cudaEvent_t* e : {&P->ev_fork, &P->ev_near_done, &P->ev_far_done})
-                HFMM_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
-        }
-        HFMM_CUDA_TRY(cudaEventRecord(P->ev_fork, st));
-        HFMM_CUDA_TRY(cudaStreamWaitEvent(P->far_st, P->ev_fork, 0));
-        HFMM_CUDA_TRY(cudaStreamWaitEvent(P->near_st, P->ev_fork, 0));
-        HFMM_TRY(near_section(true, false, P->near_st));
-        HFMM_CUDA_TRY(cudaEventRecord(P->ev_near_done, P->near_st));
-        fs = P->far_st;
-    }
-    if (far) {
-        StageTimer tf{P, fs};
-        {
-            LevelInfo& lv = P->lev[L];
-            tf.begin(HFMM_STAGE_P2M);
-            const int nrc = (P->max_rhs + 63) / 64;
-            p2m32c_kernel<<<(unsigned)lv.nbox, PC_THREADS, 0, fs>>>(
-                P->leaf_begin, P->q32, P->basis32, n, nrhs, lv.ncoef, lv.mult32, P->tc_on ? lv.tc_amma : nullptr,
-                lv.tc_asc, lv.tc_kc, nrc, lv.tc_nb, lv.tc_nbw / 16, !tc_down);
-            ++P->launches;
-            HFMM_CUDA_TRY(cudaGetLastError());
-            tf.end(HFMM_STAGE_P2M);
-            P->st_flops[HFMM_STAGE_P2M] = MAC * n * lv.ncoef;
-            P->st_bytes[HFMM_STAGE_P2M] = C * n + 8.0 * n * lv.ncoef + C * lv.nbox * lv.ncoef;
-        }
-        tf.begin(HFMM_STAGE_M2M);
-        for (int l = L - 1; l >= P->lmin; --l) {
-            LevelInfo& lv = P->lev[l];
+    // few right-hand sides: warp-level kernels (small.cu) instead of the tensor-core tiles
+    const bool small = nrhs <= P->small_rhs && !(P->flags & HFMM_FLAG_SIMT_M2L);
+    auto large_path = [&]() -> hfmm_status {
+        // near free-space field and, unless the downward epilogue does it, the
+        // leaves' local expansions (L2P), one fused kernel
+        auto near_section = [&](bool near, bool l2p, cudaStream_t ns) -> hfmm_status {
+            const LevelInfo& lv = P->lev[L];
+            StageTimer tn{P, ns};
+            tn.begin(HFMM_STAGE_P2P);
             if (P->tc_on) {
-                HFMM_TRY(launch_m2m_tc(P, l, nrhs, !tc_down, fs));
-            } else {
-                m2m32_kernel<<<(unsigned)lv.nbox, 128, 0, fs>>>(P->lev[l + 1].mult32, lv.t_m2m32, P->lev[l + 1].p,
-                                                               lv.p, nrhs, lv.mult32);
-                HFMM_CUDA_TRY(cudaGetLastError());
-            }
-            ++P->launches;
-            P->st_flops[HFMM_STAGE_M2M] += MAC * 4.0 * lv.nbox * lv.ncoef * P->lev[l + 1].ncoef;
-            P->st_bytes[HFMM_STAGE_M2M] += C * (4.0 * lv.nbox * P->lev[l + 1].ncoef + lv.nbox * lv.ncoef);
-        }
-        tf.end(HFMM_STAGE_M2M);
-        tf.begin(HFMM_STAGE_DOWN);
-        for (int l = P->lmin; l <= L; ++l) {
-            LevelInfo& lv = P->lev[l];
-            const bool has_parent = l > P->lmin;
-            const int npp = has_parent ? P->lev[l - 1].ncoef : 0;
-            const int wmax = std::max(lv.ncoef, npp);
-            // right-hand sides per pass: staged a~ fits 32 KB, items <= 8 per thread
-            int rc = std::max(1, std::min(nrhs, (int)(32768 / (wmax * sizeof(cf)))));
-            rc = std::max(1, std::min(rc, (8 * DOWN_THREADS) / lv.ncoef));
-            const size_t sm = (size_t)rc * wmax * sizeof(cf);
-            if (tc_down) {
-                if (l == L && concurrent) HFMM_CUDA_TRY(cudaStreamWaitEvent(fs, P->ev_near_done, 0));
-                const bool leaf_ev = l == L && P->events_ready;
-                if (leaf_ev) cudaEventRecord(P->ev_leaf[0], fs);
-                HFMM_TRY(launch_m2l_tc(P, l, nrhs, l == L && !l2p_fused, l2p_fused, fs));
-                if (leaf_ev) {
-                    cudaEventRecord(P->ev_leaf[1], fs);
-                    P->ev_leaf_used = true;
-                    P->leaf_flops = MAC * ((double)lv.nv + (double)lv.nr) * lv.ncoef * lv.ncoef +
-                                    (has_parent ? MAC * lv.nbox * lv.ncoef * npp : 0.0) +
-                                    (l2p_fused ? MAC * n * lv.ncoef : 0.0);
+                // P2P: tensor-core blocks of four leaves (first writer of their targets), SIMT
+                // kernel for the leaves of wider blocks; a separate L2P on the SIMT kernel
+                if (near) {
+                    HFMM_TRY(launch_p2p_tc(P, nrhs, ns));
+                    ++P->launches;
+                }
+                if (P->nt_nfallback > 0 && (near || l2p)) {
+                    p2p32c_kernel<<<(unsigned)P->nt_nfallback, PC_THREADS, 0, ns>>>(
+                        P->leaf_begin, L, P->xl32, P->q32, n, nrhs, (float)P->k, (float)lv.h, near ? 1 : 0,
+                        l2p ? lv.loc32 : nullptr, P->basis32, lv.ncoef, P->nt_fallback, P->y32);
+                    ++P->launches;
+                    HFMM_CUDA_TRY(cudaGetLastError());
+                }
+                if (l2p && P->nt_nblocks > 0) {
+                    p2p32c_kernel<<<(unsigned)P->nt_nleaves, PC_THREADS, 0, ns>>>(
+                        P->leaf_begin, L, P->xl32, P->q32, n, nrhs, (float)P->k, (float)lv.h, 0, lv.loc32, P->basis32,
+                        lv.ncoef, P->nt_leaves, P->y32);
+                    ++P->launches;
+                    HFMM_CUDA_TRY(cudaGetLastError());
                 }
             } else {
-                down32_kernel<<<(unsigned)lv.nbox, DOWN_THREADS, sm, fs>>>(
-                    P->leaf_begin, L, l, P->lmin, nrhs, lv.p, has_parent ? P->lev[l - 1].p : 0,
-                    has_parent ? P->lev[l - 1].loc32 : nullptr, has_parent ? P->lev[l - 1].t_l2l32 : nullptr,
-                    lv.mult32, lv.nv ? lv.v_begin : nullptr, lv.v_src, lv.v_off, lv.t_free32,
-                    lv.nr ? lv.r_begin : nullptr, lv.r_src, lv.r_tab, lv.t_react32, parts, rc, lv.loc32);
+                p2p32c_kernel<<<(unsigned)lv.nbox, PC_THREADS, 0, ns>>>(P->leaf_begin, L, P->xl32, P->q32, n, nrhs,
+                                                                        (float)P->k, (float)lv.h, near ? 1 : 0,
+                                                                        l2p ? lv.loc32 : nullptr, P->basis32, lv.ncoef,
+                                                                        nullptr, P->y32);
+                ++P->launches;
+                HFMM_CUDA_TRY(cudaGetLastError());
             }
-            ++P->launches;
-            HFMM_CUDA_TRY(cudaGetLastError());
-            double pairs = 0.0;
-            if (parts & HFMM_PART_FAR_FREE) pairs += (double)lv.nv;
-            if (parts & HFMM_PART_FAR_REACT) pairs += (double)lv.nr;
-            P->st_flops[HFMM_STAGE_DOWN] += MAC * pairs * lv.ncoef * lv.ncoef;
-            if (has_parent) P->st_flops[HFMM_STAGE_DOWN] += MAC * lv.nbox * lv.ncoef * npp;
-            P->st_bytes[HFMM_STAGE_DOWN] += C * lv.nbox * lv.ncoef * 2.0 +
-                                            (has_parent ? C * P->lev[l - 1].nbox * npp : 0.0);
+            tn.end(HFMM_STAGE_P2P);
+            P->st_flops[HFMM_STAGE_P2P] = (near ? MAC * (double)P->p2p_point_pairs : 0.0) +
+                                          (l2p ? MAC * n * lv.ncoef : 0.0);
+            P->st_bytes[HFMM_STAGE_P2P] = 3.0 * C * n + 16.0 * n + (l2p ? C * lv.nbox * lv.ncoef + 8.0 * n * lv.ncoef : 0.0);
+            return HFMM_OK;
+        };
+        const bool near_free = (parts & HFMM_PART_NEAR_FREE) != 0;
+        // the tensor-core pass fuses both far parts of a level; subsets run on SIMT cores
+        const bool tc_down = P->tc_on && (parts & HFMM_PART_FAR_FREE) && (parts & HFMM_PART_FAR_REACT);
+        // L2P in the leaf-level downward epilogue: the near field is then independent
+        // of the far field until the leaves' L2P adds into y32, so it runs concurrently
+        // (first writer of y32) on a low-priority stream while the far-field chain runs
+        // on a high-priority one: the near field fills what the chain leaves idle (the
+        // coarse levels launch few CTAs); both join before the leaf-level launch
+        const bool l2p_fused = far && tc_down && P->tc_l2p;
+        const bool concurrent = l2p_fused && near_free;
+        cudaStream_t fs = st;
+        if (concurrent) {
+            if (!P->far_st) {
+                int least = 0, greatest = 0;
+                HFMM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+                HFMM_CUDA_TRY(cudaStreamCreateWithPriority(&P->far_st, cudaStreamNonBlocking, greatest));
+                HFMM_CUDA_TRY(cudaStreamCreateWithPriority(&P->near_st, cudaStreamNonBlocking, least));
+                for (cudaEvent_t* e : {&P->ev_fork, &P->ev_near_done, &P->ev_far_done})
+                    HFMM_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+            }
+            HFMM_CUDA_TRY(cudaEventRecord(P->ev_fork, st));
+            HFMM_CUDA_TRY(cudaStreamWaitEvent(P->far_st, P->ev_fork, 0));
+            HFMM_CUDA_TRY(cudaStreamWaitEvent(P->near_st, P->ev_fork, 0));
+            HFMM_TRY(near_section(true, false, P->near_st));
+            HFMM_CUDA_TRY(cudaEventRecord(P->ev_near_done, P->near_st));
+            fs = P->far_st;
         }
-        if (l2p_fused) {
-            P->st_flops[HFMM_STAGE_DOWN] += MAC * n * P->lev[L].ncoef;
-            P->st_bytes[HFMM_STAGE_DOWN] += 2.0 * C * n + 8.0 * n * P->lev[L].ncoef;
+        if (far) {
+            StageTimer tf{P, fs};
+            {
+                LevelInfo& lv = P->lev[L];
+                tf.begin(HFMM_STAGE_P2M);
+                const int nrc = (P->max_rhs + 63) / 64;
+                p2m32c_kernel<<<(unsigned)lv.nbox, PC_THREADS, 0, fs>>>(
+                    P->leaf_begin, P->q32, P->basis32, n, nrhs, lv.ncoef, lv.mult32, P->tc_on ? lv.tc_amma : nullptr,
+                    lv.tc_asc, lv.tc_kc, nrc, lv.tc_nb, lv.tc_nbw / 16, !tc_down);
+                ++P->launches;
+                HFMM_CUDA_TRY(cudaGetLastError());
+                tf.end(HFMM_STAGE_P2M);
+                P->st_flops[HFMM_STAGE_P2M] = MAC * n * lv.ncoef;
+                P->st_bytes[HFMM_STAGE_P2M] = C * n + 8.0 * n * lv.ncoef + C * lv.nbox * lv.ncoef;
+            }
+            tf.begin(HFMM_STAGE_M2M);
+            for (int l = L - 1; l >= P->lmin; --l) {
+                LevelInfo& lv = P->lev[l];
+                if (P->tc_on) {
+                    HFMM_TRY(launch_m2m_tc(P, l, nrhs, !tc_down, fs));
+                } else {
+                    m2m32_kernel<<<(unsigned)lv.nbox, 128, 0, fs>>>(P->lev[l + 1].mult32, lv.t_m2m32, P->lev[l + 1].p,
+                                                                   lv.p, nrhs, lv.mult32);
+                    HFMM_CUDA_TRY(cudaGetLastError());
+                }
+                ++P->launches;
+                P->st_flops[HFMM_STAGE_M2M] += MAC * 4.0 * lv.nbox * lv.ncoef * P->lev[l + 1].ncoef;
+                P->st_bytes[HFMM_STAGE_M2M] += C * (4.0 * lv.nbox * P->lev[l + 1].ncoef + lv.nbox * lv.ncoef);
+            }
+            tf.end(HFMM_STAGE_M2M);
+            tf.begin(HFMM_STAGE_DOWN);
+            for (int l = P->lmin; l <= L; ++l) {
+                LevelInfo& lv = P->lev[l];
+                const bool has_parent = l > P->lmin;
+                const int npp = has_parent ? P->lev[l - 1].ncoef : 0;
+                const int wmax = std::max(lv.ncoef, npp);
+                // right-hand sides per pass: staged a~ fits 32 KB, items <= 8 per thread
+                int rc = std::max(1, std::min(nrhs, (int)(32768 / (wmax * sizeof(cf)))));
+                rc = std::max(1, std::min(rc, (8 * DOWN_THREADS) / lv.ncoef));
+                const size_t sm = (size_t)rc * wmax * sizeof(cf);
+                if (tc_down) {
+                    if (l == L && concurrent) HFMM_CUDA_TRY(cudaStreamWaitEvent(fs, P->ev_near_done, 0));
+                    const bool leaf_ev = l == L && P->events_ready;
+                    if (leaf_ev) cudaEventRecord(P->ev_leaf[0], fs);
+                    HFMM_TRY(launch_m2l_tc(P, l, nrhs, l == L && !l2p_fused, l2p_fused, fs));
+                    if (leaf_ev) {
+                        cudaEventRecord(P->ev_leaf[1], fs);
+                        P->ev_leaf_used = true;
+                        P->leaf_flops = MAC * ((double)lv.nv + (double)lv.nr) * lv.ncoef * lv.ncoef +
+                                        (has_parent ? MAC * lv.nbox * lv.ncoef * npp : 0.0) +
+                                        (l2p_fused ? MAC * n * lv.ncoef : 0.0);
+                    }
+                } else {
+                    down32_kernel<<<(unsigned)lv.nbox, DOWN_THREADS, sm, fs>>>(
+                        P->leaf_begin, L, l, P->lmin, nrhs, lv.p, has_parent ? P->lev[l - 1].p : 0,
+                        has_parent ? P->lev[l - 1].loc32 : nullptr, has_parent ? P->lev[l - 1].t_l2l32 : nullptr,
+                        lv.mult32, lv.nv ? lv.v_begin : nullptr, lv.v_src, lv.v_off, lv.t_free32,
+                        lv.nr ? lv.r_begin : nullptr, lv.r_src, lv.r_tab, lv.t_react32, parts, rc, lv.loc32);
+                }
+                ++P->launches;
+                HFMM_CUDA_TRY(cudaGetLastError());
+                double pairs = 0.0;
+                if (parts & HFMM_PART_FAR_FREE) pairs += (double)lv.nv;
+                if (parts & HFMM_PART_FAR_REACT) pairs += (double)lv.nr;
+                P->st_flops[HFMM_STAGE_DOWN] += MAC * pairs * lv.ncoef * lv.ncoef;
+                if (has_parent) P->st_flops[HFMM_STAGE_DOWN] += MAC * lv.nbox * lv.ncoef * npp;
+                P->st_bytes[HFMM_STAGE_DOWN] += C * lv.nbox * lv.ncoef * 2.0 +
+                                                (has_parent ? C * P->lev[l - 1].nbox * npp : 0.0);
+            }
+            if (l2p_fused) {
+                P->st_flops[HFMM_STAGE_DOWN] += MAC * n * P->lev[L].ncoef;
+                P->st_bytes[HFMM_STAGE_DOWN] += 2.0 * C * n + 8.0 * n * P->lev[L].ncoef;
+            }
+            tf.end(HFMM_STAGE_DOWN);
         }
-        tf.end(HFMM_STAGE_DOWN);
-    }
-    if (concurrent) {
-        HFMM_CUDA_TRY(cudaEventRecord(P->ev_far_done, fs));
-        HFMM_CUDA_TRY(cudaStreamWaitEvent(st, P->ev_far_done, 0));
-    }
-    if (!l2p_fused && (near_free || far)) HFMM_TRY(near_section(near_free, far, st));
+        if (concurrent) {
+            HFMM_CUDA_TRY(cudaEventRecord(P->ev_far_done, fs));
+            HFMM_CUDA_TRY(cudaStreamWaitEvent(st, P->ev_far_done, 0));
+        }
+        if (!l2p_fused && (near_free || far)) HFMM_TRY(near_section(near_free, far, st));
+        return HFMM_OK;
+    };
+    HFMM_TRY(small ? apply_small(P, nrhs, parts, st) : large_path());
     if ((parts & HFMM_PART_NEAR_REACT) && P->nd > 0) {
         tm.begin(HFMM_STAGE_DIRECT);
         direct32_kernel<<<(unsigned)P->lev[L].nbox, 128, 0, st>>>(P->leaf_begin, P->d_begin, P->d_src, P->d_blk,

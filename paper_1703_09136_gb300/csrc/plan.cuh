@@ -181,6 +181,14 @@ struct hfmm_plan_s {
     float* tc_part = nullptr;       // partial sums of split launches (levels with few tiles)
     size_t tc_part_floats = 0;
 
+    // table quadrature: panel-count scale (hfmm_options.quad_scale) and the
+    // node-doubling check's largest weighted relative difference and where
+    // (level, dx, ysum; level -1 for a directly summed block)
+    double quad_scale = 1.0;
+    int small_rhs = 0;              // HFMM_MIXED: applies with nrhs <= small_rhs run on small.cu
+    double table_check = 0.0;
+    int table_check_where[3] = {0, 0, 0};
+
     // info
     int64_t u_pairs = 0;
     double table_bytes = 0.0;
@@ -237,6 +245,11 @@ hfmm_status apply_fp64(hfmm_plan_s* P, int nrhs, const cd* q, cd* y, int parts, 
 hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts, bool adjoint,
                         cudaStream_t st);
 hfmm_status init_h0_table(cudaStream_t st);
+const float* h0_table_host();        // [2][64][6]: J0 then R0 = Y0 - (2/pi) ln(z/2) J0 pieces
+// small.cu: the small-nrhs mixed path (warp-level SIMT kernels, no tensor cores)
+hfmm_status init_small(hfmm_plan_s* P, cudaStream_t st);
+// P2M, M2M, downward pass and near field + L2P of one apply on the sorted q32 / y32
+hfmm_status apply_small(hfmm_plan_s* P, int nrhs, int parts, cudaStream_t st);
 hfmm_status build_local_coords(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status fill_near_tiles(hfmm_plan_s* P, int64_t nchunks, int64_t total_rows, cudaStream_t st);
 // p2p_tc.cu

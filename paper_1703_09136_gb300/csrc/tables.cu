@@ -28,6 +28,11 @@
 namespace {
 
 constexpr int GLN = 16;
+// Largest accepted difference between a table and its node-doubled rule
+// (weighted as in react_check_kernel).  Converged FP64 rules agree to a few
+// 1e-14; the bound sits well above that and ten times below the FP64 path's
+// 1e-11 parity bound.
+constexpr double TABLE_RTOL = 1e-12;
 __constant__ double c_glx[GLN];
 __constant__ double c_glw[GLN];
 double h_glx[GLN], h_glw[GLN];
@@ -87,6 +92,8 @@ struct Entry {
     int seg0, seg1;
     int64_t nodes;
     int64_t out;      // offset of A_{-nmax} in the output
+    int64_t wofs;     // offset of this level's weights w_n in the check's weight array
+    int level, dx, ysum;
 };
 
 // real t >= 0 where sigma is not analytic (branch points of s_j, k_j > k1;
@@ -144,14 +151,16 @@ double t_end(double k1, double Y, int nmax) {
 }
 
 // Build the segments of one integral; returns the number of nodes.
+// `scale` multiplies every panel count: 1 is the table's rule, 2 its
+// node-doubled check, other values come from hfmm_options.quad_scale.
 int64_t make_rule(const hfmm_medium& m, double xmax, double ymin, double ymax, int nmax,
-                  std::vector<Seg>& segs) {
+                  std::vector<Seg>& segs, double scale) {
     const double k1 = m.k[0];
     const bool three = m.kind == HFMM_THREE_LAYER;
     const double dd = three ? m.d : 0.0;
     int64_t nodes = 0;
     auto push = [&](double a, double b, int kind, int npan, double c, double tb) {
-        Seg s{a, b, c, tb, kind, std::max(npan, 1), nodes};
+        Seg s{a, b, c, tb, kind, std::max((int)std::ceil(npan * scale), 1), nodes};
         nodes += (int64_t)s.npan * GLN;
         segs.push_back(s);
     };
@@ -162,9 +171,38 @@ int64_t make_rule(const hfmm_medium& m, double xmax, double ymin, double ymax, i
     tau_kinks(m, brk);
     brk.push_back(HFMM_PI);
     std::sort(brk.begin(), brk.end());
+    // impedance: sigma has a pole at s1 = i alpha, i.e. sin tau = -alpha / k1; for
+    // 0 < alpha < k1 it lies on the real tau axis at -delta and pi + delta,
+    // delta = asin(alpha / k1), so the panels near both ends are graded: no
+    // panel is wider than 1.5 times its distance to the pole
+    const bool imp_pole = m.kind == HFMM_IMPEDANCE && m.alpha > 0.0;
+    const double delta = (imp_pole && m.alpha < k1) ? std::asin(m.alpha / k1) : -1.0;
+    const double wu = 4.0 / rate;
     for (size_t i = 0; i + 1 < brk.size(); ++i) {
-        double len = brk[i + 1] - brk[i];
-        push(brk[i], brk[i + 1], 0, (int)std::ceil(len * rate / 4.0) + 1, 0.0, 0.0);
+        const double A = brk[i], B = brk[i + 1];
+        if (delta <= 0.0 || 1.5 * delta >= wu) {
+            push(A, B, 0, (int)std::ceil((B - A) * rate / 4.0) + 1, 0.0, 0.0);
+            continue;
+        }
+        const double M = 0.5 * (A + B);
+        std::vector<std::pair<double, double>> right;
+        for (double a = A; a < M;) {
+            const double w = std::min(wu, 1.5 * (a + delta));
+            const double b = w >= wu ? M : std::min(M, std::max(a + 8.0 * w, 2.0 * a + delta));
+            push(a, b, 0, (int)std::ceil((b - a) / w), 0.0, 0.0);
+            a = b;
+        }
+        for (double b = B; b > M;) {
+            const double dist = HFMM_PI + delta - b;
+            const double w = std::min(wu, 1.5 * dist);
+            const double a = w >= wu ? M : std::max(M, std::min(b - 8.0 * w, b - dist));
+            right.push_back({a, b});
+            b = a;
+        }
+        for (auto it = right.rbegin(); it != right.rend(); ++it) {
+            const double w = std::min(wu, 1.5 * (HFMM_PI + delta - it->second));
+            push(it->first, it->second, 0, (int)std::ceil((it->second - it->first) / w), 0.0, 0.0);
+        }
     }
     // evanescent part
     const double xa = std::max(std::fabs(xmax), 1e-12);
@@ -189,6 +227,8 @@ int64_t make_rule(const hfmm_medium& m, double xmax, double ymin, double ymax, i
     while (a < T) {
         double wl = nmax > 0 ? 3.0 * a / nmax : wc;
         double w = std::min(wc, std::max(wmin, wl));
+        // impedance pole at t = i alpha: panel width <= 1.5 x its distance
+        if (imp_pole) w = std::min(w, 1.5 * std::sqrt(a * a + m.alpha * m.alpha));
         double b = (w < wc) ? std::min(T, std::max(a + 16.0 * w, 2.0 * a)) : T;
         push(a, b, 2, (int)std::ceil((b - a) / w), 0.0, 0.0);
         a = b;
@@ -420,6 +460,64 @@ __global__ void direct_grad_block_kernel(MedDev m, const DirectJob* jobs, const 
     }
 }
 
+// Node-doubling check of the tables.  The reaction entry A_n feeds the
+// translation entries s(|m|) s(|p|) A_n (m + p = -n) that act on the
+// normalised expansions (|J_m(k rho)| <= s(|m|) inside a box); its weight w_n
+// is the largest such product, so a difference that no translated field can
+// see (the tiny coefficients the expansions never reach) does not count.
+// One CTA per entry: max_n w_n |A_n - A2_n| / max_n w_n |A2_n|.
+__device__ double block_max(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__global__ void react_check_kernel(const Entry* ents, const cd* a1, const cd* a2, const double* w,
+                                   double* ratio) {
+    __shared__ double red[32];
+    const Entry e = ents[blockIdx.x];
+    double dm = 0.0, am = 0.0;
+    for (int i = threadIdx.x; i < 2 * e.nmax + 1; i += blockDim.x) {
+        const cd x = a1[e.out + i], y = a2[e.out + i];
+        const double wi = w[e.wofs + i];
+        dm = fmax(dm, wi * hypot(x.x - y.x, x.y - y.y));
+        am = fmax(am, wi * hypot(y.x, y.y));
+    }
+    dm = block_max(dm, red);
+    am = block_max(am, red);
+    if (threadIdx.x == 0) ratio[blockIdx.x] = am > 0.0 ? dm / am : (dm > 0.0 ? INFINITY : 0.0);
+}
+
+// Directly summed blocks: max |G - G2| / max |G2| over the block's point pairs.
+__global__ void direct_check_kernel(const DirectJob* jobs, const cd* v1, const cd* v2, double* ratio) {
+    __shared__ double red[32];
+    const DirectJob jb = jobs[blockIdx.x];
+    double dm = 0.0, am = 0.0;
+    for (int64_t i = threadIdx.x; i < (int64_t)jb.t_n * jb.s_n; i += blockDim.x) {
+        const cd x = v1[jb.blk + i], y = v2[jb.blk + i];
+        dm = fmax(dm, hypot(x.x - y.x, x.y - y.y));
+        am = fmax(am, hypot(y.x, y.y));
+    }
+    dm = block_max(dm, red);
+    am = block_max(am, red);
+    if (threadIdx.x == 0) ratio[blockIdx.x] = am > 0.0 ? dm / am : (dm > 0.0 ? INFINITY : 0.0);
+}
+
+// Mirrored reaction entries: out[dst + nmax + n] = out[src + nmax - n].
+struct int64_t3 {
+    int64_t dst, src, nmax;
+};
+
+__global__ void mirror_kernel(const int64_t3* mir, cd* out) {
+    const int64_t3 m = mir[blockIdx.x];
+    for (int64_t i = threadIdx.x; i <= 2 * m.nmax; i += blockDim.x) out[m.dst + i] = out[m.src + 2 * m.nmax - i];
+}
+
 // free-space M2L: one thread per (offset) of one level
 __global__ void free_table_kernel(double k, double h, int p, cd* out) {
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
@@ -500,9 +598,12 @@ hfmm_status build_tables(hfmm_plan_s* P, cudaStream_t st) {
             P->table_bytes += sizeof(cd) * 8.0 * w;
         }
     }
-    // reaction tables
-    std::vector<Seg> segs;
-    std::vector<Entry> ents;
+    // reaction tables (on the panel rule, and on the node-doubled rule for the check)
+    const double qs = P->quad_scale;
+    std::vector<Seg> segs, segs2;
+    std::vector<Entry> ents, ents2;
+    std::vector<int64_t3> mirrors;   // (destination, source, nmax) of mirrored entries
+    std::vector<double> wts;
     int64_t total = 0;
     std::vector<int64_t> lev_off(L + 1, 0);
     for (int l = 0; l <= L; ++l) {
@@ -514,6 +615,24 @@ hfmm_status build_tables(hfmm_plan_s* P, cudaStream_t st) {
         lv.n_react_entries = (2 * dxmax + 1) * 3;
         const int nmax = 2 * lv.p;
         lev_off[l] = total;
+        // weights w_n = max over m + p = -n (|m|, |p| <= p_l) of s(|m|) s(|p|),
+        // s(n) = min(1, (k R_l / 2)^n / n!)
+        const int64_t wofs = (int64_t)wts.size();
+        {
+            const double kR = P->k * lv.h / std::sqrt(2.0);
+            std::vector<double> ls(lv.p + 1);
+            for (int j = 0; j <= lv.p; ++j)
+                ls[j] = std::min(0.0, j * std::log(0.5 * kR) - std::lgamma(j + 1.0));
+            for (int n = -nmax; n <= nmax; ++n) {
+                double best = -1e300;
+                for (int mm = -lv.p; mm <= lv.p; ++mm) {
+                    const int pp = -n - mm;
+                    if (pp < -lv.p || pp > lv.p) continue;
+                    best = std::max(best, ls[std::abs(mm)] + ls[std::abs(pp)]);
+                }
+                wts.push_back(std::exp(std::max(best, -700.0)));
+            }
+        }
         for (int dx = -dxmax; dx <= dxmax; ++dx)
             for (int ys = 0; ys < 3; ++ys) {
                 const int64_t idx = (int64_t)(dx + dxmax) * 3 + ys;
@@ -521,17 +640,34 @@ hfmm_status build_tables(hfmm_plan_s* P, cudaStream_t st) {
                                      : (ys <= 2 && reaction_admissible(ys, 0, P->y0, lv.h) && !(ys == 2 && m < 2));
                 if (l == 0) used = used && P->lstar == 0;
                 if (!used) continue;
+                if (dx < 0) {
+                    // sigma is even in lambda: A_n(-X, Y) = A_{-n}(X, Y), a copy of the dx > 0 entry
+                    mirrors.push_back({total + idx * (2 * nmax + 1), total + ((int64_t)(-dx + dxmax) * 3 + ys) * (2 * nmax + 1),
+                                       (int64_t)nmax});
+                    continue;
+                }
                 Entry e;
                 e.X = dx * lv.h;
                 e.Y = 2.0 * P->y0 + (ys + 1) * lv.h;
                 e.nmax = nmax;
-                e.seg0 = (int)segs.size();
-                std::vector<Seg> tmp;
-                e.nodes = make_rule(P->med, e.X, e.Y, e.Y, nmax, tmp);
-                for (auto& s : tmp) segs.push_back(s);
-                e.seg1 = (int)segs.size();
                 e.out = total + idx * (2 * nmax + 1);
+                e.wofs = wofs;
+                e.level = l;
+                e.dx = dx;
+                e.ysum = ys;
+                Entry e2 = e;
+                std::vector<Seg> tmp;
+                e.seg0 = (int)segs.size();
+                e.nodes = make_rule(P->med, e.X, e.Y, e.Y, nmax, tmp, qs);
+                for (auto& sg : tmp) segs.push_back(sg);
+                e.seg1 = (int)segs.size();
                 ents.push_back(e);
+                tmp.clear();
+                e2.seg0 = (int)segs2.size();
+                e2.nodes = make_rule(P->med, e2.X, e2.Y, e2.Y, nmax, tmp, 2.0 * qs);
+                for (auto& sg : tmp) segs2.push_back(sg);
+                e2.seg1 = (int)segs2.size();
+                ents2.push_back(e2);
             }
         total += (int64_t)lv.n_react_entries * (2 * nmax + 1);
     }
@@ -549,7 +685,43 @@ hfmm_status build_tables(hfmm_plan_s* P, cudaStream_t st) {
         HFMM_CUDA_TRY(cudaMemcpyAsync(dents, ents.data(), sizeof(Entry) * ents.size(), cudaMemcpyHostToDevice, st));
         react_table_kernel<<<(unsigned)ents.size(), 256, 0, st>>>(md, dents, dsegs, tab, 1.0);
         HFMM_CUDA_TRY(cudaGetLastError());
+        if (!mirrors.empty()) {
+            int64_t3* dmir = nullptr;
+            HFMM_TRY(plan_alloc(P, (void**)&dmir, sizeof(int64_t3) * mirrors.size()));
+            HFMM_CUDA_TRY(cudaMemcpyAsync(dmir, mirrors.data(), sizeof(int64_t3) * mirrors.size(),
+                                          cudaMemcpyHostToDevice, st));
+            mirror_kernel<<<(unsigned)mirrors.size(), 128, 0, st>>>(dmir, tab);
+            HFMM_CUDA_TRY(cudaGetLastError());
+        }
         P->table_bytes += sizeof(cd) * (double)total;
+        // the same entries on the node-doubled rule, compared entry by entry
+        cd* tab2 = nullptr;
+        Seg* dsegs2 = nullptr;
+        Entry* dents2 = nullptr;
+        double *dw = nullptr, *dratio = nullptr;
+        HFMM_TRY(plan_alloc(P, (void**)&tab2, sizeof(cd) * total));
+        HFMM_TRY(plan_alloc(P, (void**)&dsegs2, sizeof(Seg) * segs2.size()));
+        HFMM_TRY(plan_alloc(P, (void**)&dents2, sizeof(Entry) * ents2.size()));
+        HFMM_TRY(plan_alloc(P, (void**)&dw, sizeof(double) * wts.size()));
+        HFMM_TRY(plan_alloc(P, (void**)&dratio, sizeof(double) * ents.size()));
+        HFMM_CUDA_TRY(cudaMemcpyAsync(dsegs2, segs2.data(), sizeof(Seg) * segs2.size(), cudaMemcpyHostToDevice, st));
+        HFMM_CUDA_TRY(cudaMemcpyAsync(dents2, ents2.data(), sizeof(Entry) * ents2.size(), cudaMemcpyHostToDevice, st));
+        HFMM_CUDA_TRY(cudaMemcpyAsync(dw, wts.data(), sizeof(double) * wts.size(), cudaMemcpyHostToDevice, st));
+        HFMM_CUDA_TRY(cudaMemsetAsync(tab2, 0, sizeof(cd) * total, st));
+        react_table_kernel<<<(unsigned)ents2.size(), 256, 0, st>>>(md, dents2, dsegs2, tab2, 1.0);
+        react_check_kernel<<<(unsigned)ents.size(), 128, 0, st>>>(dents, tab, tab2, dw, dratio);
+        HFMM_CUDA_TRY(cudaGetLastError());
+        std::vector<double> ratio(ents.size());
+        HFMM_CUDA_TRY(cudaMemcpyAsync(ratio.data(), dratio, sizeof(double) * ratio.size(), cudaMemcpyDeviceToHost, st));
+        HFMM_CUDA_TRY(cudaStreamSynchronize(st));
+        for (size_t i = 0; i < ratio.size(); ++i) {
+            if (!(ratio[i] <= P->table_check)) {       // also catches NaN
+                P->table_check = std::isnan(ratio[i]) ? INFINITY : ratio[i];
+                P->table_check_where[0] = ents[i].level;
+                P->table_check_where[1] = ents[i].dx;
+                P->table_check_where[2] = ents[i].ysum;
+            }
+        }
     }
     // direct reaction blocks
     if (P->nd > 0) {
@@ -559,8 +731,8 @@ hfmm_status build_tables(hfmm_plan_s* P, cudaStream_t st) {
         HFMM_CUDA_TRY(cudaMemcpyAsync(dbeg.data(), P->d_begin, sizeof(int32_t) * dbeg.size(), cudaMemcpyDeviceToHost, st));
         HFMM_CUDA_TRY(cudaMemcpyAsync(dsrc.data(), P->d_src, sizeof(int32_t) * P->nd, cudaMemcpyDeviceToHost, st));
         HFMM_CUDA_TRY(cudaStreamSynchronize(st));
-        std::vector<Seg> dsg;
-        std::vector<DirectJob> jobs;
+        std::vector<Seg> dsg, dsg2;
+        std::vector<DirectJob> jobs, jobs2;
         std::vector<int64_t> blk(P->nd);
         int64_t off = 0;
         int maxpairs = 0;
@@ -573,16 +745,23 @@ hfmm_status build_tables(hfmm_plan_s* P, cudaStream_t st) {
                 jb.s_lo = lb[s]; jb.s_n = lb[s + 1] - lb[s];
                 const int dx = (int)morton_x((uint32_t)b) - (int)morton_x((uint32_t)s);
                 const double xmax = (std::abs(dx) + 1) * h;
+                jb.blk = off;
+                DirectJob jb2 = jb;
                 jb.seg0 = (int)dsg.size();
                 std::vector<Seg> tmp;
-                jb.nodes = make_rule(P->med, xmax, 2.0 * P->y0, 2.0 * P->y0 + 2.0 * h, 0, tmp);
+                jb.nodes = make_rule(P->med, xmax, 2.0 * P->y0, 2.0 * P->y0 + 2.0 * h, 0, tmp, qs);
                 for (auto& sgm : tmp) dsg.push_back(sgm);
                 jb.seg1 = (int)dsg.size();
-                jb.blk = off;
+                tmp.clear();
+                jb2.seg0 = (int)dsg2.size();
+                jb2.nodes = make_rule(P->med, xmax, 2.0 * P->y0, 2.0 * P->y0 + 2.0 * h, 0, tmp, 2.0 * qs);
+                for (auto& sgm : tmp) dsg2.push_back(sgm);
+                jb2.seg1 = (int)dsg2.size();
                 blk[e] = off;
                 off += (int64_t)jb.t_n * jb.s_n;
                 maxpairs = std::max(maxpairs, jb.t_n * jb.s_n);
                 jobs.push_back(jb);
+                jobs2.push_back(jb2);
             }
         }
         (void)m;
@@ -599,6 +778,31 @@ hfmm_status build_tables(hfmm_plan_s* P, cudaStream_t st) {
         if (maxpairs > 0) {
             direct_block_kernel<<<(unsigned)jobs.size(), 128, 0, st>>>(md, djobs, dsegs, P->xy_sorted, P->d_vals);
             HFMM_CUDA_TRY(cudaGetLastError());
+            // node-doubled blocks for the check
+            cd* vals2 = nullptr;
+            Seg* dsegs2 = nullptr;
+            DirectJob* djobs2 = nullptr;
+            double* dratio = nullptr;
+            HFMM_TRY(plan_alloc(P, (void**)&vals2, sizeof(cd) * off));
+            HFMM_TRY(plan_alloc(P, (void**)&dsegs2, sizeof(Seg) * dsg2.size()));
+            HFMM_TRY(plan_alloc(P, (void**)&djobs2, sizeof(DirectJob) * jobs2.size()));
+            HFMM_TRY(plan_alloc(P, (void**)&dratio, sizeof(double) * jobs.size()));
+            HFMM_CUDA_TRY(cudaMemcpyAsync(dsegs2, dsg2.data(), sizeof(Seg) * dsg2.size(), cudaMemcpyHostToDevice, st));
+            HFMM_CUDA_TRY(cudaMemcpyAsync(djobs2, jobs2.data(), sizeof(DirectJob) * jobs2.size(), cudaMemcpyHostToDevice, st));
+            direct_block_kernel<<<(unsigned)jobs2.size(), 128, 0, st>>>(md, djobs2, dsegs2, P->xy_sorted, vals2);
+            direct_check_kernel<<<(unsigned)jobs.size(), 128, 0, st>>>(djobs, P->d_vals, vals2, dratio);
+            HFMM_CUDA_TRY(cudaGetLastError());
+            std::vector<double> ratio(jobs.size());
+            HFMM_CUDA_TRY(cudaMemcpyAsync(ratio.data(), dratio, sizeof(double) * ratio.size(), cudaMemcpyDeviceToHost, st));
+            HFMM_CUDA_TRY(cudaStreamSynchronize(st));
+            for (size_t i = 0; i < ratio.size(); ++i) {
+                if (!(ratio[i] <= P->table_check)) {
+                    P->table_check = std::isnan(ratio[i]) ? INFINITY : ratio[i];
+                    P->table_check_where[0] = -1;      // a directly summed leaf pair
+                    P->table_check_where[1] = (int)i;
+                    P->table_check_where[2] = 0;
+                }
+            }
         }
         P->dj_jobs = djobs;
         P->dj_segs = dsegs;
@@ -606,6 +810,17 @@ hfmm_status build_tables(hfmm_plan_s* P, cudaStream_t st) {
         P->table_bytes += sizeof(cd) * (double)off;
     }
     HFMM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!(P->table_check <= TABLE_RTOL)) {
+        if (P->table_check_where[0] >= 0)
+            hfmm_set_error("reaction table quadrature not converged: level %d, dx %d, ysum %d differs from its "
+                           "node-doubled rule by %.3g (bound %.1g)", P->table_check_where[0],
+                           P->table_check_where[1], P->table_check_where[2], P->table_check, TABLE_RTOL);
+        else
+            hfmm_set_error("direct reaction quadrature not converged: leaf-pair block %d differs from its "
+                           "node-doubled rule by %.3g (bound %.1g)", P->table_check_where[1], P->table_check,
+                           TABLE_RTOL);
+        return HFMM_ERR_NUMERICS;
+    }
     return HFMM_OK;
 }
 

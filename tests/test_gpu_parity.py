@@ -171,15 +171,17 @@ def test_tiny_inputs_match_direct_sum(n):
     plan.close()
 
 
+@pytest.mark.parametrize("engine", ["small", "tensor"])
 @pytest.mark.parametrize("n", [1, 2, 3, 33, 1000])
-def test_tiny_and_ragged_inputs_on_the_mixed_path(n):
+def test_tiny_and_ragged_inputs_on_the_mixed_path(n, engine):
     """Mixed precision on tiny and ragged inputs (leaves of 1..4 points, a
-    ragged last tile, 3 right-hand sides) against the direct sum."""
+    ragged last tile, 3 right-hand sides) against the direct sum, on both
+    mixed engines."""
     from paper_1703_09136_gb300 import MIXED
     med = W.WORKLOADS[4].medium
     xy = W.points_in_box(4, n, ((0.0, 0.5), (0.02, 0.52)), salt=3)
     q = W.strengths(4, n, 3, salt=3)
-    plan = Plan(xy, med, tol=1e-6, leaf_size=4, max_rhs=3, precision=MIXED)
+    plan = Plan(xy, med, tol=1e-6, leaf_size=4, max_rhs=3, precision=MIXED, small_rhs=0 if engine == "small" else -1)
     y = plan.apply(q.astype(np.complex64)).astype(np.complex128)
     assert plan.info["device_error"] == 0
     plan.close()
@@ -200,8 +202,8 @@ def test_bounded_device_wait_gives_up_with_a_timeout_status():
     med = W.WORKLOADS[5].medium
     xy = W.points(5, 3000)
     q = W.strengths(5, 3000, 4, salt=9).astype(np.complex64)
-    plan = Plan(xy, med, tol=1e-6, leaf_size=16, max_rhs=4, precision=MIXED, spin_limit=3_000_000)
-    ref = Plan(xy, med, tol=1e-6, leaf_size=16, max_rhs=4, precision=MIXED)
+    plan = Plan(xy, med, tol=1e-6, leaf_size=16, max_rhs=4, precision=MIXED, spin_limit=3_000_000, small_rhs=-1)
+    ref = Plan(xy, med, tol=1e-6, leaf_size=16, max_rhs=4, precision=MIXED, small_rhs=-1)
     assert np.array_equal(plan.apply(q), ref.apply(q))
     assert plan.info["device_error"] == 0
     # few leaf tiles: split steps, so the leaves' L2P runs on the SIMT kernel
@@ -329,13 +331,15 @@ def test_adjoint_matches_dense_oracle_matrix(name):
     p64 = Plan(xy, med, tol=1e-10, leaf_size=16, max_rhs=2)
     ok, errs = _close(p64.adjoint(v), want, 1e-9)
     assert ok, ("fp64", errs)
-    p32 = Plan(xy, med, tol=1e-6, leaf_size=16, max_rhs=2, precision=MIXED)
-    ok, errs = _close(p32.adjoint(v.astype(np.complex64)), want, MIXED_TOL)
-    assert ok, ("mixed", errs)
+    for sr in (0, -1):                         # warp-level and tensor-core engines
+        p32 = Plan(xy, med, tol=1e-6, leaf_size=16, max_rhs=2, precision=MIXED, small_rhs=sr)
+        ok, errs = _close(p32.adjoint(v.astype(np.complex64)), want, MIXED_TOL)
+        assert ok, ("mixed", sr, errs)
+        p32.close()
     # the forward pass against the same matrix
     ok, errs = _close(p64.apply(v), (G @ v.T).T, 1e-9)
     assert ok, ("fp64 forward", errs)
-    p64.close(); p32.close()
+    p64.close()
 
 
 @pytest.mark.parametrize("name", ["cfg1", "cfg4-adjoint"])
@@ -364,20 +368,23 @@ def test_adjoint_matches_cpu_fmm_transposed(name):
 MIXED_TOL = 1e-5
 
 
+@pytest.mark.parametrize("engine", ["small", "tensor"])
 @pytest.mark.parametrize("name", CASES)
-def test_mixed_matches_fp64_and_oracle(name):
-    """FP32 expansions / near field with scaled FP32 translation matrices:
-    rel-l2 against the FP64 GPU path and against the CPU FMM <= 1e-5."""
+def test_mixed_matches_fp64_and_oracle(name, engine):
+    """FP32 expansions / near field with scaled FP32 translation matrices,
+    on the warp-level few-RHS kernels and on the tensor-core passes: rel-l2
+    against the FP64 GPU path and against the CPU FMM <= 1e-5, whole and per term."""
     from paper_1703_09136_gb300 import MIXED
     F, parts = _oracle(name)
     med, xy, q, tol, leaf, p = _case(name)
     full = sum(parts.values())
-    plan = Plan(xy, med, tol=tol, leaf_size=leaf, p=p, max_rhs=q.shape[0], precision=MIXED)
+    sr = 0 if engine == "small" else -1
+    plan = Plan(xy, med, tol=tol, leaf_size=leaf, p=p, max_rhs=q.shape[0], precision=MIXED, small_rhs=sr)
     y32 = plan.apply(torch.from_numpy(q.astype(np.complex64)).cuda()).cpu().numpy()
     plan.close()
     assert direct.rel_l2(y32, full) < MIXED_TOL, direct.rel_l2(y32, full)
     for part in (1, 2, 4, 8):
-        plan = Plan(xy, med, tol=tol, leaf_size=leaf, p=p, max_rhs=q.shape[0], precision=MIXED)
+        plan = Plan(xy, med, tol=tol, leaf_size=leaf, p=p, max_rhs=q.shape[0], precision=MIXED, small_rhs=sr)
         yp = plan.apply(torch.from_numpy(q.astype(np.complex64)).cuda(), parts=part).cpu().numpy()
         plan.close()
         err = np.linalg.norm(yp - parts[part]) / np.linalg.norm(full)
@@ -506,7 +513,7 @@ def test_near_field_tensor_blocks_and_simt_fallback():
     med = W.WORKLOADS[2].medium
     xy = W.points(2, 6400)
     q = W.strengths(2, 6400, 2)
-    tc = Plan(xy, med, tol=1e-6, leaf_size=24, max_rhs=2, precision=MIXED)
+    tc = Plan(xy, med, tol=1e-6, leaf_size=24, max_rhs=2, precision=MIXED, small_rhs=-1)
     f64 = Plan(xy, med, tol=1e-6, leaf_size=24, max_rhs=2)
     inf = tc.info
     assert inf["near_tc_blocks"] > 0 and inf["near_simt_leaves"] > 0, inf
@@ -651,10 +658,10 @@ def test_batch_graph_captures_the_concurrent_near_field():
     sizes = [60000, 2000]
     xys = [W.points(5, n, salt=10 + i) for i, n in enumerate(sizes)]
     qs = [torch.from_numpy(W.strengths(5, n, 4, salt=i)).cuda().to(torch.complex64) for i, n in enumerate(sizes)]
-    singles = [Plan(xy, med, leaf_size=16, precision=MIXED, max_rhs=4) for xy in xys]
+    singles = [Plan(xy, med, leaf_size=16, precision=MIXED, max_rhs=4, small_rhs=-1) for xy in xys]
     assert singles[0].info["leaf_l2p_fused"] == 1 and singles[1].info["leaf_l2p_fused"] == 0
     refs = [p.apply(q) for p, q in zip(singles, qs)]
-    batch = Batch(xys, med, leaf_size=16, precision=MIXED, max_rhs=4)
+    batch = Batch(xys, med, leaf_size=16, precision=MIXED, max_rhs=4, small_rhs=-1)
     ys = [torch.empty_like(q) for q in qs]
     for rep in range(3):
         for y in ys:
@@ -665,4 +672,75 @@ def test_batch_graph_captures_the_concurrent_near_field():
             assert torch.equal(ref, y), rep
     batch.close()
     for p in singles:
+        p.close()
+
+
+# --- table quadrature convergence ----------------------------------------------
+
+@pytest.mark.parametrize("name", ["cfg1", "cfg3-small", "cfg4-small", "near-interface", "small-alpha"])
+def test_table_quadrature_is_checked_against_its_node_doubled_rule(name):
+    """Every reaction table entry A_n (Eq. (eq:m2loperator)) and every directly
+    summed G^s block is recomputed at plan time on the rule with twice the
+    panels; the converged rules agree far below 1e-12 (weighted by what the
+    normalised expansions reach), and rules coarsened through quad_scale are
+    rejected with HFMM_ERR_NUMERICS instead of giving a silently worse result."""
+    if name == "near-interface":
+        med = CFG4_MED
+        xy = W.points_in_box(4, 2048, ((0.0, 0.5), (0.002, 0.502)), salt=8)
+        leaf = 16
+    elif name == "small-alpha":
+        med = Medium(W.IMPEDANCE, (20.0,), alpha=0.5)
+        xy = W.points(1)
+        leaf = 32
+    else:
+        med, xy, q, tol, leaf, p = _case(name)
+    plan = Plan(xy, med, tol=1e-6, leaf_size=leaf)
+    inf = plan.info
+    assert 0.0 < inf["table_check"] < 1e-12, inf["table_check"]
+    if name == "near-interface":
+        assert inf["direct_leaf_pairs"] > 0
+    plan.close()
+    with pytest.raises(HfmmError) as e:
+        Plan(xy, med, tol=1e-6, leaf_size=leaf, quad_scale=0.05)
+    assert e.value.status == 5 and "node-doubled" in str(e.value)
+
+
+def test_impedance_with_small_alpha_matches_direct_sum():
+    """alpha / k = 0.025: the pole of sigma_hat at s1 = i alpha (Sec. 2.2)
+    sits close to both quadrature paths of the tables and of the directly
+    summed blocks; FP64 at tol 1e-10 against the oracle's direct sum."""
+    med = Medium(W.IMPEDANCE, (20.0,), alpha=0.5)
+    xy = W.points(1)
+    q = W.strengths(1, xy.shape[0], 1, salt=15)
+    plan = Plan(xy, med, tol=1e-10, leaf_size=32)
+    assert plan.info["direct_leaf_pairs"] > 0
+    y = plan.apply(q)
+    plan.close()
+    err = direct.rel_l2(y, direct.direct_apply(med, xy, q))
+    assert err < 1e-10, err
+
+
+@pytest.mark.parametrize("nrhs", [1, 2, 3, 4, 7])
+def test_small_rhs_engine_matches_tensor_engine_and_fp64(nrhs):
+    """The warp-level kernels for few right-hand sides (default for nrhs <= 4,
+    forced here up to 7: passes of 8, 4, 2, 1 right-hand sides and ragged
+    passes) against the tensor-core engine and the FP64 path, right-hand
+    side by right-hand side, on the three-layer medium with every level,
+    the reaction lists and the fused near field involved."""
+    from paper_1703_09136_gb300 import MIXED
+    xy = W.points_in_box(4, 8192, ((0.0, 1.0), (0.02, 1.02)), salt=2)
+    q = W.strengths(4, 8192, nrhs, salt=16)
+    sm = Plan(xy, CFG4_MED, tol=1e-6, leaf_size=16, max_rhs=nrhs, precision=MIXED, small_rhs=8)
+    tc = Plan(xy, CFG4_MED, tol=1e-6, leaf_size=16, max_rhs=nrhs, precision=MIXED, small_rhs=-1)
+    f64 = Plan(xy, CFG4_MED, tol=1e-6, leaf_size=16, max_rhs=nrhs)
+    q32 = torch.from_numpy(q.astype(np.complex64)).cuda()
+    y_sm = sm.apply(q32).cpu().numpy().astype(np.complex128)
+    y_tc = tc.apply(q32).cpu().numpy().astype(np.complex128)
+    y64 = f64.apply(torch.from_numpy(q).cuda()).cpu().numpy()
+    for r in range(nrhs):
+        assert direct.rel_l2(y_sm[r], y64[r]) < MIXED_TOL, (r, direct.rel_l2(y_sm[r], y64[r]))
+        assert direct.rel_l2(y_sm[r], y_tc[r]) < MIXED_TOL
+    # deterministic: the same apply twice gives the same bits
+    assert torch.equal(sm.apply(q32), sm.apply(q32))
+    for p in (sm, tc, f64):
         p.close()

@@ -94,6 +94,12 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     o.spin_limit = -1
     assert lib.hfmm_plan_create(ctypes.byref(h), 2, p, ctypes.byref(m), ctypes.byref(o), None) == 1
     assert b"spin_limit" in lib.hfmm_last_error()
+    # a negative or non-finite quadrature panel scale
+    o.spin_limit = 0
+    for bad in (-0.5, float("nan"), 1e9):
+        o.quad_scale = bad
+        assert lib.hfmm_plan_create(ctypes.byref(h), 2, p, ctypes.byref(m), ctypes.byref(o), None) == 1
+        assert b"quad_scale" in lib.hfmm_last_error()
     # apply on a null plan
     q = np.zeros(2, dtype=np.complex128)
     assert lib.hfmm_apply(None, 1, q.ctypes.data_as(vp), q.ctypes.data_as(vp), None) == 1
@@ -111,3 +117,26 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(N, "_lib", None)
     with pytest.raises(ImportError):
         N.lib()
+
+
+def test_options_and_info_layout_match_the_header(lib):
+    """The ctypes mirrors of hfmm_options and hfmm_plan_info end with the
+    fields the header declares last (quad_scale, table_check), and
+    hfmm_options_default leaves the quadrature scale at 0 (= 1)."""
+    from paper_1703_09136_gb300 import _native as N
+    text = open(os.path.join(ROOT, "include", "hfmm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    for struct, cls in (("hfmm_options", N.hfmm_options), ("hfmm_plan_info", N.hfmm_plan_info)):
+        body = re.search(r"typedef struct \{([^}]*)\}\s*" + struct + ";", text).group(1)
+        flat = []
+        for decl in body.split(";"):
+            words = decl.split()
+            if len(words) < 2:
+                continue
+            names = " ".join(words[1:]).split(",")        # "x0, y0, size" on one line
+            flat += [re.sub(r"\[.*\]", "", nm).strip() for nm in names]
+        assert [f[0] for f in cls._fields_] == flat, struct
+    o = N.hfmm_options()
+    o.quad_scale = 5.0
+    lib.hfmm_options_default(ctypes.byref(o))
+    assert o.quad_scale == 0.0 and o.tol == 1e-6
