@@ -91,6 +91,8 @@ def parse():
                     help="skip the FP64 reference apply (accuracy and one-RHS FP64 time)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the two-layer and uneven-batch workloads measured after the headline")
     ap.add_argument("--cpu-sample-n", type=int, default=0)
     ap.add_argument("--box", type=float, nargs=4, default=None, metavar=("X0", "X1", "Y0", "Y1"),
                     help="draw the points in this box instead of the workload's domain (small profiling cases)")
@@ -105,14 +107,24 @@ def parse():
 _CPU_WORKER = {}
 
 
-def _cpu_worker_init(cfg, box, n, nrhs, lo, hi):
+def _cpu_worker_init(job):
+    """One worker's share of the CPU oracle: the points of a box of workload
+    job["cfg"] (or instance job["salt"] of its own point family) and the
+    right-hand sides lo..hi of its strengths."""
     import workloads as W
     from oracle import fmm
+    cfg = job["cfg"]
     w = W.WORKLOADS[cfg]
-    xy = W.points_in_box(cfg, n, box)
-    q = W.strengths(cfg, n, nrhs)[lo:hi]
+    if job.get("box"):
+        box = tuple(tuple(b) for b in job["box"])
+        xy = W.points_in_box(cfg, job["n"], box)
+        q = W.strengths(cfg, job["n"], job["nrhs"])
+    else:
+        xy = W.points(cfg, job["n"], salt=job["salt"])
+        q = W.strengths(cfg, job["n"], job["nrhs"], salt=job["salt"])
+    lo, hi = job["lo"], job["hi"]
     _CPU_WORKER["F"] = fmm.CpuFmm(xy, w.medium, tol=w.tol, leaf_size=16) if hi > lo else None
-    _CPU_WORKER["q"] = q
+    _CPU_WORKER["q"] = q[lo:hi]
 
 
 def _cpu_worker_apply(_):
@@ -123,20 +135,16 @@ def _cpu_worker_apply(_):
 
 
 def _cpu_child(spec):
-    """Body of the CPU child process: times `reps` applies of the oracle over
-    all right-hand sides, spread over `cores` worker processes."""
+    """Body of the CPU child process: one single-threaded worker process per
+    job, `reps` applies of all jobs at once; returns the wall time of each."""
     import multiprocessing as mp
-    cfg, box, n, nrhs, reps, cores = (spec[k] for k in ("cfg", "box", "n", "nrhs", "reps", "cores"))
-    box = tuple(tuple(b) for b in box)
-    cores = max(1, min(cores, nrhs))
     ctx = mp.get_context("spawn")
-    bounds = [(nrhs * c // cores, nrhs * (c + 1) // cores) for c in range(cores)]
-    pools = [ctx.Pool(1, initializer=_cpu_worker_init, initargs=(cfg, box, n, nrhs, lo, hi)) for lo, hi in bounds]
+    pools = [ctx.Pool(1, initializer=_cpu_worker_init, initargs=(job,)) for job in spec["jobs"]]
     try:
         for pl in pools:                   # wait until every worker holds its plan
             pl.apply(os.getpid)
         times = []
-        for _ in range(reps):
+        for _ in range(spec["reps"]):
             t0 = time.perf_counter()
             res = [pl.apply_async(_cpu_worker_apply, (0,)) for pl in pools]
             for r in res:
@@ -145,13 +153,33 @@ def _cpu_child(spec):
     finally:
         for pl in pools:
             pl.terminate()
-    return {"n": n, "nrhs": nrhs, "apply_s": times, "cores": cores}
+    return {"apply_s": times, "cores": len(spec["jobs"])}
+
+
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _run_cpu_child(jobs, reps):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    spec = {"jobs": jobs, "reps": reps}
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child", json.dumps(spec)],
+                       capture_output=True, text=True, env=env, timeout=3600)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
 
 
 def cpu_oracle_sample(cfg, nrhs, reps=1, n=0, side=None):
     """The oracle on the points of a side x side corner of the workload's
     domain at the workload's density (default 2 x 2, i.e. 1/16 of the 8 x 8
-    three-layer domain), all right-hand sides, one worker per host core."""
+    three-layer domain), all right-hand sides split over one worker per host
+    core (a single worker for one right-hand side)."""
     import workloads as W
     w = W.WORKLOADS[cfg]
     (X0, X1), (Y0, Y1) = w.box
@@ -159,30 +187,43 @@ def cpu_oracle_sample(cfg, nrhs, reps=1, n=0, side=None):
     side = side or CPU_SAMPLE_SIDE
     box = ((X0, X0 + side), (Y0, Y0 + side))
     n = n or int(round(density * side * side))
-    try:
-        cores = len(os.sched_getaffinity(0))
-    except AttributeError:
-        cores = os.cpu_count() or 1
-    env = dict(os.environ)
-    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
-        env[v] = "1"
-    spec = {"cfg": cfg, "box": box, "n": n, "nrhs": nrhs, "reps": reps, "cores": cores}
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child", json.dumps(spec)],
-                       capture_output=True, text=True, env=env, timeout=3600)
-    if r.returncode != 0:
-        raise RuntimeError(r.stderr[-2000:])
-    out = json.loads(r.stdout.strip().splitlines()[-1])
-    out["box"] = box
-    out["share"] = n / w.n
+    cores = max(1, min(_host_cores(), nrhs))
+    jobs = [{"cfg": cfg, "box": box, "n": n, "nrhs": nrhs, "lo": nrhs * c // cores, "hi": nrhs * (c + 1) // cores}
+            for c in range(cores)]
+    out = _run_cpu_child(jobs, reps)
+    out.update({"n": n, "nrhs": nrhs, "box": box, "share": n / w.n})
+    return out
+
+
+def cpu_oracle_instances(cfg, sizes, nrhs, reps=2, max_points=60000):
+    """The oracle on the smallest instances of an uneven batch (their sizes
+    summing to at most max_points), one worker per instance, all at once."""
+    order = sorted(range(len(sizes)), key=lambda i: sizes[i])
+    pick, tot = [], 0
+    for i in order:
+        if pick and (tot + sizes[i] > max_points or len(pick) >= _host_cores()):
+            break
+        pick.append(i)
+        tot += sizes[i]
+    jobs = [{"cfg": cfg, "n": int(sizes[i]), "salt": i, "nrhs": nrhs, "lo": 0, "hi": nrhs} for i in pick]
+    out = _run_cpu_child(jobs, reps)
+    out.update({"n": tot, "nrhs": nrhs, "instances": pick, "share": tot / float(sum(sizes))})
     return out
 
 
 def _cpu_sample_text(s, t_apply):
-    return (f"CPU oracle H-FMM (oracle/fmm.py, FP64) on the {s['n']} points of the "
-            f"[{s['box'][0][0]:g}, {s['box'][0][1]:g}] x [{s['box'][1][0]:g}, {s['box'][1][1]:g}] corner of "
-            f"the workload ({100 * s['share']:.2f}% of its points, same density and medium), {s['nrhs']} RHS "
-            f"split over {s['cores']} single-threaded worker processes (one per host core); "
-            f"apply {t_apply:.2f} s (tables built in an untimed first apply)")
+    if "box" in s:
+        where = (f"the {s['n']} points of the [{s['box'][0][0]:g}, {s['box'][0][1]:g}] x "
+                 f"[{s['box'][1][0]:g}, {s['box'][1][1]:g}] corner of the workload ({100 * s['share']:.2f}% of its "
+                 f"points, same density and medium)")
+        split = (f"{s['nrhs']} RHS split over {s['cores']} single-threaded worker processes (one per host core)"
+                 if s["cores"] > 1 else f"{s['nrhs']} RHS on one single-threaded worker")
+    else:
+        where = (f"the {len(s['instances'])} smallest instances of the batch ({s['n']} points, "
+                 f"{100 * s['share']:.2f}% of the batch's points)")
+        split = f"{s['nrhs']} RHS, one single-threaded worker process per instance ({s['cores']} at once)"
+    return (f"CPU oracle H-FMM (oracle/fmm.py, FP64) on {where}, {split}; apply {t_apply:.2f} s "
+            f"(tables built in an untimed first apply)")
 
 
 # ---------------------------------------------------------------------------
@@ -265,6 +306,165 @@ def _profile_pass(Plan, xy, w, prec, nrhs, q, steps):
             near_flops += plan.info["flops_last_apply"]["p2p"] / 3
     plan.close()
     return stage_ms, info, leaf_ms, leaf_flops, near_ms, near_flops
+
+
+def _events_ms(fn, reps):
+    """Mean CUDA-event time (ms) of fn() on the current stream, after two
+    untimed calls."""
+    import torch
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _dominant_roofline(Plan, xy, w, prec, nrhs, q):
+    """Stage times of a profiling plan and the roofline of its dominant stage
+    (the warp-level SIMT kernels of few-RHS applies: FP32 pipe)."""
+    avg, info, leaf_ms, leaf_fl, near_ms, near_fl = _profile_pass(Plan, xy, w, prec, nrhs, q, PROFILE_STEPS)
+    dom = max(avg, key=avg.get)
+    fl = info["flops_last_apply"][dom]
+    if prec == 0:
+        peak, src = FP64_PEAK_TFLOPS, "nominal GB300 FP64 rate"
+    else:
+        peak, src = FP32_PEAK_TFLOPS, "derived FP32 SIMT peak: 152 SMs x 128 lanes x 2 x 2.07 GHz"
+    roof = {"kernel": f"stage '{dom}'", "bound": "alu", "achieved": fl / (avg[dom] * 1e-3) / 1e12, "peak": peak,
+            "unit": "TFLOP/s", "peak_source": src, "traffic": None}
+    roof["frac"] = roof["achieved"] / peak
+    return avg, roof
+
+
+def measure_two_layer(dev, steps, cpu=True):
+    """Two-layer medium (k = 60 over 90), N = 262,144 uniform in [0, 4] x
+    [0.02, 4.02], one right-hand side, tol 1e-6: the mixed-precision apply
+    (few-RHS warp-level engine) against the plain FP64 apply on the same GPU."""
+    import torch
+    import workloads as W
+    from paper_1703_09136_gb300 import Plan, FP64, MIXED
+    cfg = 3
+    w = W.WORKLOADS[cfg]
+    xy_h = W.points(cfg)
+    q_h = W.strengths(cfg, w.n, 1)
+    xy = torch.from_numpy(xy_h).to(dev)
+    q64 = torch.from_numpy(q_h).to(dev)
+    q32 = q64.to(torch.complex64)
+    t0 = time.perf_counter()
+    pm = Plan(xy, w.medium, tol=w.tol, leaf_size=w.leaf, precision=MIXED, max_rhs=1)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    ym = torch.empty_like(q32)
+    ms_mixed = _events_ms(lambda: pm.apply(q32, out=ym), steps)
+    launches = int(pm.info["launches_last_apply"])
+    qh = q32.cpu().pin_memory()
+    yh = torch.empty_like(qh).pin_memory()
+    pm._run(plan_lib_apply(), qh, yh, None)
+    e2e_t = []
+    for _ in range(5):
+        t1 = time.perf_counter()
+        pm._run(plan_lib_apply(), qh, yh, None)
+        e2e_t.append(time.perf_counter() - t1)
+    e2e_s = statistics.median(e2e_t)
+    adj_ms = _events_ms(lambda: pm.adjoint(q32, out=ym), 5)
+    pm.apply(q32, out=ym)
+    y_mixed = ym.to(torch.complex128)
+    pm.close()
+    p64 = Plan(xy, w.medium, tol=w.tol, leaf_size=w.leaf, precision=FP64, max_rhs=1)
+    y64 = torch.empty_like(q64)
+    ms_fp64 = _events_ms(lambda: p64.apply(q64, out=y64), 3)
+    p64.apply(q64, out=y64)
+    err = float(torch.linalg.norm(y_mixed - y64) / torch.linalg.norm(y64))
+    p64.close()
+    stages, roof = _dominant_roofline(Plan, xy, w, MIXED, 1, q32)
+    out = {"workload": w.name, "n": w.n, "nrhs": 1, "tol": w.tol, "medium": "two-layer k=60/90",
+           "metric": "Mtargets/s (N x nrhs / apply time)", "value": w.n / (ms_mixed * 1e-3) / 1e6,
+           "ms_per_apply": ms_mixed, "fp64_ms_per_apply": ms_fp64, "mixed_speedup_vs_fp64": ms_fp64 / ms_mixed,
+           "rel_l2_mixed_vs_fp64": err, "adjoint_ms": adj_ms, "plan_s": plan_s, "gpu_launches": launches,
+           "engine": "few-RHS warp-level kernels (small_rhs default 4)", "stage_ms": stages, "roofline": roof,
+           "e2e": {"value": w.n / e2e_s / 1e6, "unit": "Mtargets/s", "h2d_bytes_per_step": 8 * w.n,
+                   "d2h_bytes_per_step": 8 * w.n}}
+    if cpu:
+        s = cpu_oracle_sample(cfg, 1, reps=2, side=1.0)
+        t = s["apply_s"][-1]
+        out["cpu_baseline"] = {"value": s["n"] / t / 1e6, "unit": "Mtargets/s", "cores": s["cores"],
+                               "kind": "oracle", "sample": _cpu_sample_text(s, t)}
+    return out
+
+
+def measure_batch(dev, steps, cpu=True):
+    """32 impedance instances (k = 40, alpha = 20) with N log-uniform in
+    [4096, 200000], one right-hand side, through the batch API (one CUDA graph
+    per apply), mixed precision and FP64."""
+    import torch
+    import workloads as W
+    from paper_1703_09136_gb300 import Batch, FP64, MIXED
+    cfg = 5
+    w = W.WORKLOADS[cfg]
+    sizes = [int(v) for v in W.batch_sizes(cfg)]
+    ntot = sum(sizes)
+    xys = [W.points(cfg, n, salt=i) for i, n in enumerate(sizes)]
+    out = {"workload": w.name, "instances": len(sizes), "total_n": ntot, "n_min": min(sizes), "n_max": max(sizes),
+           "nrhs": 1, "tol": w.tol, "medium": "impedance k=40 alpha=20",
+           "metric": "Mtargets/s (sum of N x nrhs / batch apply time)"}
+    for prec, name, cdt, pers in ((MIXED, "mixed", torch.complex64, False),
+                                  (MIXED, "mixed_persistent", torch.complex64, True),
+                                  (FP64, "fp64", torch.complex128, False)):
+        qs = [torch.from_numpy(W.strengths(cfg, n, 1, salt=i)).to(dev, cdt) for i, n in enumerate(sizes)]
+        ys = [torch.empty_like(q) for q in qs]
+        t0 = time.perf_counter()
+        batch = Batch(xys, w.medium, tol=w.tol, leaf_size=w.leaf, precision=prec, max_rhs=1, persistent=pers)
+        torch.cuda.synchronize()
+        plan_s = time.perf_counter() - t0
+        ms = _events_ms(lambda: batch.apply(qs, ys), steps if prec == MIXED else 3)
+        rec = {"ms_per_apply": ms, "value": ntot / (ms * 1e-3) / 1e6, "plan_s": plan_s}
+        if pers:
+            rec["engine"] = "one persistent kernel over a device work queue (HFMM_FLAG_PERSISTENT)"
+            rec["device_error"] = batch.device_error
+            batch.close()
+            out[name] = rec
+            continue
+        if prec == MIXED:
+            rec["engine"] = "one CUDA graph, a branch of warp-level kernels per instance"
+            rec["adjoint_ms"] = _events_ms(lambda: batch.apply(qs, ys, adjoint=True), 5)
+            # end to end: pinned host strengths in, results out, around every batch apply
+            qh = [q.cpu().pin_memory() for q in qs]
+            yh = [torch.empty_like(q).pin_memory() for q in qh]
+            e2e_t = []
+            for it in range(6):
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                for a, d in zip(qh, qs):
+                    d.copy_(a, non_blocking=True)
+                batch.apply(qs, ys)
+                for a, d in zip(yh, ys):
+                    a.copy_(d, non_blocking=True)
+                torch.cuda.synchronize()
+                if it:
+                    e2e_t.append(time.perf_counter() - t1)
+            rec["e2e"] = {"value": ntot / statistics.median(e2e_t) / 1e6, "unit": "Mtargets/s",
+                          "h2d_bytes_per_step": 8 * ntot, "d2h_bytes_per_step": 8 * ntot}
+            batch.apply(qs, ys)
+            y_mixed = [y.to(torch.complex128) for y in ys]
+        else:
+            batch.apply(qs, ys)
+            num = sum(float(torch.linalg.norm(a - b) ** 2) for a, b in zip(y_mixed, ys))
+            den = sum(float(torch.linalg.norm(b) ** 2) for b in ys)
+            out["rel_l2_mixed_vs_fp64"] = (num / den) ** 0.5
+        batch.close()
+        out[name] = rec
+    out["value"] = out["mixed"]["value"]
+    out["mixed_speedup_vs_fp64"] = out["fp64"]["ms_per_apply"] / out["mixed"]["ms_per_apply"]
+    if cpu:
+        s = cpu_oracle_instances(cfg, sizes, 1, reps=2)
+        t = s["apply_s"][-1]
+        out["cpu_baseline"] = {"value": s["n"] / t / 1e6, "unit": "Mtargets/s", "cores": s["cores"],
+                               "kind": "oracle", "sample": _cpu_sample_text(s, t)}
+    return out
 
 
 def run_ours(args):
@@ -442,6 +642,10 @@ def run_ours(args):
         **({"accuracy": accuracy, "fp64_one_rhs_ms": fp64_ms} if accuracy else {}),
         "clocks": ck,
     }
+    if not args.no_extra and cfg == 4 and n == w.n and nrhs == w.nrhs and not args.box:
+        # the other full-size workloads, measured in the same run on the same GPU
+        out["workloads"] = {"two-layer-262144-1rhs": measure_two_layer(dev, 20, cpu=rank == 0 and not args.no_cpu_baseline),
+                            "impedance-batch32-1rhs": measure_batch(dev, 20, cpu=rank == 0 and not args.no_cpu_baseline)}
     if rank == 0 and not args.no_cpu_baseline:
         s = cpu_oracle_sample(cfg, nrhs, reps=2, n=args.cpu_sample_n)
         t_apply = s["apply_s"][-1]

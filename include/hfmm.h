@@ -122,6 +122,10 @@ typedef struct {
 #define HFMM_FLAG_AUTOTUNE 4    /* build the plan at the leaf levels L-1, L, L+1 around the
                                    leaf_size choice, time max_rhs-wide applies on the device
                                    and keep the fastest (hfmm_plan_info.tune_*) */
+#define HFMM_FLAG_PERSISTENT 8  /* batches: mixed-precision applies with nrhs <= small_rhs run as
+                                   one persistent kernel over a device work queue (see
+                                   hfmm_batch_device_error) instead of one graph branch per
+                                   instance */
 
 /* Stages reported by hfmm_plan_get_stage_times (milliseconds of the last apply). */
 #define HFMM_STAGE_GATHER   0   /* caller order -> leaf order */
@@ -245,7 +249,8 @@ hfmm_status hfmm_apply_grad(hfmm_plan_t plan, int32_t nrhs, const void* q, const
  * set of buffers runs them once eagerly on `stream` (lazily initialised
  * state is set up outside capture; `stream` is synchronised), then records
  * all instances' applies into one CUDA graph on a private stream of the
- * batch (one branch per instance) and launches it on `stream`; later calls
+ * batch (one branch per instance, or one persistent launch with
+ * HFMM_FLAG_PERSISTENT) and launches it on `stream`; later calls
  * with the same buffers only launch the graph.  q[i], y[i]: device buffers
  * [nrhs][n_i] of instance i (dtype as for hfmm_apply); adjoint != 0 applies
  * A_i^H instead.  Changing any buffer pointer, nrhs or adjoint re-records the
@@ -258,6 +263,16 @@ hfmm_status hfmm_batch_create(hfmm_batch_t* out, int32_t ninst, const int64_t* n
                               const hfmm_medium* medium, const hfmm_options* opts, void* stream);
 hfmm_status hfmm_batch_apply(hfmm_batch_t batch, int32_t nrhs, const void* const* q, void* const* y,
                              int32_t adjoint, void* stream);
+/*
+ * Batches created with HFMM_FLAG_PERSISTENT whose mixed-precision applies have
+ * nrhs <= the plans' small_rhs run as one persistent kernel: a device queue
+ * of work items over every stage and level of every instance; an item waits
+ * for the items it depends on with a bounded wait (options.spin_limit polls).  A wait that gave up sets a flag of the
+ * batch and the results of that apply are invalid.  hfmm_batch_device_error
+ * synchronises the device and returns that flag of the last apply in
+ * *device_error (0 = none; always 0 for batches on the per-instance graph).
+ */
+hfmm_status hfmm_batch_device_error(hfmm_batch_t batch, int32_t* device_error);
 /* Plan of instance i (owned by the batch; for introspection and single applies). */
 hfmm_status hfmm_batch_get_plan(hfmm_batch_t batch, int32_t i, hfmm_plan_t* plan);
 hfmm_status hfmm_batch_destroy(hfmm_batch_t batch);

@@ -282,10 +282,12 @@ class Plan:
 
 class Batch:
     """Independent problems of uneven sizes applied through one CUDA graph
-    (hfmm_batch_*).  xys: list of [n_i, 2] float64 arrays / tensors."""
+    (hfmm_batch_*).  xys: list of [n_i, 2] float64 arrays / tensors.
+    persistent=True runs mixed-precision applies with few right-hand sides as
+    one persistent kernel over a device work queue."""
 
     def __init__(self, xys, medium, tol=1e-6, p=0, leaf_size=32, levels=0, precision=FP64, max_rhs=1,
-                 stream=None, simt_m2l=False, spin_limit=0, small_rhs=0):
+                 stream=None, simt_m2l=False, spin_limit=0, small_rhs=0, persistent=False):
         lib = _n.lib()
         m = Medium.of(medium)
         opts = _n.hfmm_options()
@@ -293,7 +295,7 @@ class Batch:
         opts.tol, opts.p, opts.leaf_size, opts.levels = float(tol), int(p), int(leaf_size), int(levels)
         opts.precision, opts.max_rhs = int(precision), int(max_rhs)
         opts.small_rhs = int(small_rhs)
-        opts.flags = _n.FLAG_SIMT_M2L if simt_m2l else 0
+        opts.flags = (_n.FLAG_SIMT_M2L if simt_m2l else 0) | (_n.FLAG_PERSISTENT if persistent else 0)
         opts.spin_limit = int(spin_limit)
         keep = [_ptr(np.ascontiguousarray(x, dtype=np.float64) if not hasattr(x, "data_ptr") else x.contiguous())
                 for x in xys]
@@ -315,6 +317,13 @@ class Batch:
         yp = (ctypes.c_void_p * len(ys))(*[y.data_ptr() for y in ys])
         _n.check(_n.lib().hfmm_batch_apply(self._h, nrhs, qp, yp, 1 if adjoint else 0, _stream_handle(stream)))
         return ys
+
+    @property
+    def device_error(self):
+        """Flag of the last persistent-kernel apply (a bounded wait gave up); synchronises."""
+        e = ctypes.c_int32(0)
+        _n.check(_n.lib().hfmm_batch_device_error(self._h, ctypes.byref(e)))
+        return int(e.value)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -21,12 +21,14 @@ EXPORTS = ["hfmm_options_default", "hfmm_plan_create", "hfmm_apply", "hfmm_apply
            "hfmm_plan_get_pairs", "hfmm_plan_destroy", "hfmm_status_string", "hfmm_last_error",
            "hfmm_debug_bessel", "hfmm_plan_get_stage_times", "hfmm_debug_green_f32",
            "hfmm_leaf_order_noalloc", "hfmm_apply_grad", "hfmm_batch_create", "hfmm_batch_apply",
-           "hfmm_batch_get_plan", "hfmm_batch_destroy", "hfmm_debug_wait_timeout", "hfmm_plan_get_leaf_down"]
+           "hfmm_batch_get_plan", "hfmm_batch_destroy", "hfmm_debug_wait_timeout", "hfmm_plan_get_leaf_down",
+           "hfmm_batch_device_error"]
 NUM_STAGES = 8
 STAGES = ["gather", "p2m", "m2m", "down", "l2p", "p2p", "direct", "scatter"]
 FLAG_PROFILE = 1
 FLAG_SIMT_M2L = 2
 FLAG_AUTOTUNE = 4
+FLAG_PERSISTENT = 8
 
 
 class HfmmError(RuntimeError):
@@ -100,12 +102,13 @@ def lib():
         L.hfmm_batch_destroy.argtypes = [vp]
         L.hfmm_debug_wait_timeout.argtypes = [i64, i32]
         L.hfmm_plan_get_leaf_down.argtypes = [hfmm_plan_t, vp, vp]
+        L.hfmm_batch_device_error.argtypes = [vp, vp]
         for name in ("hfmm_plan_create", "hfmm_apply", "hfmm_apply_parts", "hfmm_apply_adjoint",
                      "hfmm_plan_get_info", "hfmm_plan_get_tree", "hfmm_plan_get_pairs",
                      "hfmm_plan_destroy", "hfmm_debug_bessel", "hfmm_plan_get_stage_times",
                      "hfmm_debug_green_f32", "hfmm_leaf_order_noalloc", "hfmm_apply_grad",
                      "hfmm_batch_create", "hfmm_batch_apply", "hfmm_batch_get_plan", "hfmm_batch_destroy",
-                     "hfmm_debug_wait_timeout", "hfmm_plan_get_leaf_down"):
+                     "hfmm_debug_wait_timeout", "hfmm_plan_get_leaf_down", "hfmm_batch_device_error"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib

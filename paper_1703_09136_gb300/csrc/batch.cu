@@ -1,12 +1,16 @@
 // Batches of independent H-FMM problems of uneven sizes (one plan per
-// instance) applied together: the applies of all instances are captured once
-// into one CUDA graph (on a private stream of the batch, so that any caller
-// stream, the legacy default stream included, can launch it), each instance
-// on its own branch forked from and joined back to the capture stream, and
-// the graph is replayed on the caller's stream on every later call with the
-// same buffers.  Branches of small and large instances
-// run concurrently on the GPU; one graph launch replaces ~20 launches per
-// instance.
+// instance) applied together, recorded once into one CUDA graph (on a private
+// stream of the batch, so that any caller stream, the legacy default stream
+// included, can launch it) and replayed on the caller's stream on every later
+// call with the same buffers.
+//
+// Each instance's apply is a branch of the graph forked from and joined back
+// to the capture stream, so branches of small and large instances run
+// concurrently.  With HFMM_FLAG_PERSISTENT, mixed-precision batches with few
+// right-hand sides (nrhs <= small_rhs) run instead as ONE persistent kernel
+// (small.cu): a device queue of work items over every stage and level of
+// every instance with bounded dependency waits; the graph then holds a
+// counter reset and that launch.
 #include <cstring>
 #include <new>
 #include <vector>
@@ -27,7 +31,18 @@ struct hfmm_batch_s {
     bool key_adjoint = false;
     std::vector<const void*> key_q;
     std::vector<void*> key_y;
+    PersistBatch* persist = nullptr;  // created on the first apply that takes the persistent path
+    bool key_persist = false;
 };
+
+// The persistent path: asked for, every plan mixed, the warp-level engine chosen for nrhs.
+static bool batch_persistent(const hfmm_batch_s* B, int nrhs) {
+    for (auto p : B->plans)
+        if (!(p->flags & HFMM_FLAG_PERSISTENT) || p->precision != HFMM_MIXED || nrhs > p->small_rhs ||
+            (p->flags & HFMM_FLAG_SIMT_M2L))
+            return false;
+    return true;
+}
 
 hfmm_status batch_apply_one(hfmm_plan_t P, int nrhs, const void* q, void* y, bool adjoint, cudaStream_t st);
 
@@ -40,6 +55,7 @@ static void batch_free(hfmm_batch_s* B) {
     if (B->fork) cudaEventDestroy(B->fork);
     if (B->cap) cudaStreamDestroy(B->cap);
     for (auto s : B->streams) cudaStreamDestroy(s);
+    persist_destroy(B->persist);
     for (auto p : B->plans) hfmm_plan_destroy(p);
     delete B;
 }
@@ -48,10 +64,17 @@ static hfmm_status batch_capture(hfmm_batch_s* B, int nrhs, const void* const* q
     cudaStream_t st = B->cap;
     if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
     if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
+    const bool pers = batch_persistent(B, nrhs);
+    if (pers) {
+        if (!B->persist) HFMM_TRY(persist_create(B->plans, &B->persist));
+        HFMM_TRY(persist_set_buffers(B->persist, q, y, st));
+    }
     HFMM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     hfmm_status s = HFMM_OK;
-    cudaError_t e = cudaEventRecord(B->fork, st);
-    for (int i = 0; i < B->ninst && e == cudaSuccess && s == HFMM_OK; ++i) {
+    cudaError_t e = cudaSuccess;
+    if (pers) s = persist_launch(B->persist, nrhs, adjoint, st);
+    else e = cudaEventRecord(B->fork, st);
+    for (int i = 0; !pers && i < B->ninst && e == cudaSuccess && s == HFMM_OK; ++i) {
         e = cudaStreamWaitEvent(B->streams[i], B->fork, 0);
         if (e != cudaSuccess) break;
         s = batch_apply_one(B->plans[i], nrhs, q[i], y[i], adjoint, B->streams[i]);
@@ -72,6 +95,7 @@ static hfmm_status batch_capture(hfmm_batch_s* B, int nrhs, const void* const* q
     HFMM_CUDA_TRY(cudaGraphInstantiate(&B->exec, g, 0));
     B->key_nrhs = nrhs;
     B->key_adjoint = adjoint;
+    B->key_persist = pers;
     B->key_q.assign(q, q + B->ninst);
     B->key_y.assign(y, y + B->ninst);
     return HFMM_OK;
@@ -146,6 +170,16 @@ hfmm_status hfmm_batch_apply(hfmm_batch_t B, int32_t nrhs, const void* const* q,
         HFMM_TRY(batch_capture(B, nrhs, q, y, adjoint != 0));
     }
     HFMM_CUDA_TRY(cudaGraphLaunch(B->exec, st));
+    return HFMM_OK;
+}
+
+hfmm_status hfmm_batch_device_error(hfmm_batch_t B, int32_t* device_error) {
+    if (!B || !device_error) { hfmm_set_error("batch or device_error is NULL"); return HFMM_ERR_INVALID_ARG; }
+    *device_error = 0;
+    if (!B->persist) return HFMM_OK;
+    int e = 0;
+    HFMM_TRY(persist_device_error(B->persist, &e));
+    *device_error = e;
     return HFMM_OK;
 }
 

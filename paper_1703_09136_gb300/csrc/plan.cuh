@@ -246,6 +246,49 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
                         cudaStream_t st);
 hfmm_status init_h0_table(cudaStream_t st);
 const float* h0_table_host();        // [2][64][6]: J0 then R0 = Y0 - (2/pi) ln(z/2) J0 pieces
+// Persistent batch kernel (small.cu): segments of work items, instances and levels.
+struct PSeg {
+    int kind, inst, level, nchunk;   // stage, instance, level, coefficient chunks per box
+    int item0, nitems;               // first global item number, item count
+    int dep0, dep1;                  // segments that must be complete first (-1: none)
+    int wpb;                         // 1 = eight boxes per item, one per warp (P2M, near field, and M2M /
+                                     // downward levels with at most 32 coefficients), 0 = one (box,
+                                     // coefficient chunk) per item
+    int idep, irel;                  // segment whose items covering this item's boxes must be done first:
+                                     // irel 0 the same boxes, 1 their children, 2 their parents
+    int pad;
+};
+struct PLev {                        // one level of one instance (mixed-path buffers and tables)
+    int p, pp, pc;                   // order of this level, of its parent and of its children
+    cf* mult;
+    cf* loc;
+    const cf* cmult;                 // children's multipoles (M2M into this level)
+    const cf* ploc;                  // parent's locals (null at the coarsest level)
+    const cf *Tl2l, *Tfree, *Treact, *Tm2m;
+    const int32_t *v_begin, *v_src, *v_off, *r_begin, *r_src, *r_tab;
+};
+struct PInst {
+    const int32_t* lb;
+    int L, lmin, lev0, nc;           // leaf level, coarsest level, first PLev, leaf coefficients
+    int64_t n;
+    float k, h;                      // wavenumber, leaf side
+    const float2* xl;
+    const cf* basis;
+    cf *q32, *y32;
+    const int32_t* iperm;
+    const int32_t *d_begin, *d_src;
+    const int64_t* d_blk;
+    const cf* d_vals;
+    const cf* q;                     // caller buffers the batch graph was recorded for
+    cf* y;
+};
+struct PersistBatch;
+hfmm_status persist_create(const std::vector<hfmm_plan_s*>& plans, PersistBatch** out);
+hfmm_status persist_set_buffers(PersistBatch* B, const void* const* q, void* const* y, cudaStream_t st);
+hfmm_status persist_launch(PersistBatch* B, int nrhs, bool adjoint, cudaStream_t st);
+hfmm_status persist_device_error(PersistBatch* B, int* err);
+void persist_destroy(PersistBatch* B);
+
 // small.cu: the small-nrhs mixed path (warp-level SIMT kernels, no tensor cores)
 hfmm_status init_small(hfmm_plan_s* P, cudaStream_t st);
 // P2M, M2M, downward pass and near field + L2P of one apply on the sorted q32 / y32

@@ -22,6 +22,8 @@
 // Expansion layouts are those of the mixed path (scaled a~, b~ in [box][rhs][coef]).
 #include <algorithm>
 #include <cmath>
+#include <new>
+#include <vector>
 
 #include "bessel.cuh"
 #include "plan.cuh"
@@ -101,7 +103,10 @@ __device__ __forceinline__ void translate_source(cf (&acc)[U][R], const cf* __re
     const int lane = threadIdx.x & 31;
     m_hi = min(m_hi, ncs);
     __syncwarp();
-    for (int e = lane; e < R * ncs; e += 32) stage[e] = e < rows * ncs ? src[e] : cfmk(0.f, 0.f);
+    // L2 loads (ld.global.cg): in the persistent batch kernel the source was
+    // written by another CTA of the same launch, after this SM's L1 may have
+    // cached neighbouring lines
+    for (int e = lane; e < R * ncs; e += 32) stage[e] = e < rows * ncs ? __ldcg(src + e) : cfmk(0.f, 0.f);
     __syncwarp();
     bool pl[U];
 #pragma unroll
@@ -342,6 +347,337 @@ __global__ void __launch_bounds__(128) near_small_kernel(const int32_t* __restri
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Persistent batch kernel: every stage of every instance of a batch in one
+// launch.  The work items (one CTA each) are numbered in an order in which
+// every item's inputs come from items with smaller numbers: gathers and P2M
+// of all instances, M2M deepest level first, then the downward passes top
+// level first, each instance's near field, direct reaction and scatter right
+// after its leaf level.  A CTA takes the
+// next number from a counter, waits (bounded) until the segments its item
+// depends on are complete, does the item and counts it done.  Because items
+// are taken in order, an item only waits on items that running CTAs already
+// hold, so the launch cannot deadlock whatever the number of resident CTAs.
+// Data produced in the launch is read through L2 (ld.global.cg).
+// ---------------------------------------------------------------------------
+enum PKind { PK_GATHER = 0, PK_P2M, PK_M2M, PK_DOWN, PK_NEAR, PK_DIRECT, PK_SCATTER };
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <int R>
+__global__ void __launch_bounds__(SM_W * 32, 3) persist_kernel(const PSeg* __restrict__ segs, int nseg, int total,
+                                                            const PInst* __restrict__ insts,
+                                                            const PLev* __restrict__ levs, int nrhs, int adjoint,
+                                                            int ncs_max, int* __restrict__ ctr, long spin) {
+    extern __shared__ float4 sm_small[];
+    __shared__ float tj[H0N][H0D + 1], tr[H0N][H0D + 1];
+    __shared__ int s_item, s_seg;
+    for (int e = threadIdx.x; e < H0N * (H0D + 1); e += blockDim.x) {
+        tj[e / (H0D + 1)][e % (H0D + 1)] = c_h0[0][e / (H0D + 1)][e % (H0D + 1)];
+        tr[e / (H0D + 1)][e % (H0D + 1)] = c_h0[1][e / (H0D + 1)][e % (H0D + 1)];
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    cf* stage = (cf*)sm_small + (int64_t)w * R * ncs_max;
+    cf* red = (cf*)sm_small + (int64_t)SM_W * R * ncs_max;
+    // first item of every segment, for the segment lookup of each item
+    int* s_item0 = (int*)(red + (int64_t)SM_W * R * 32);
+    for (int e = tid; e < nseg; e += blockDim.x) s_item0[e] = segs[e].item0;
+    int* done = ctr + 2;
+    int* done_item = ctr + 2 + nseg;
+    for (;;) {
+        __syncthreads();                       // previous item finished with s_item, s_seg
+        if (tid == 0) {
+            const int it = atomicAdd(ctr, 1);
+            int sg = 0;
+            if (it < total) {
+                int lo = 0, hi = nseg - 1;     // last segment with item0 <= it
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_item0[mid] <= it) lo = mid; else hi = mid - 1;
+                }
+                sg = lo;
+                const PSeg S0 = segs[sg];
+                const int deps[2] = {S0.dep0, S0.dep1};
+                long polls = 0;
+                bool gave_up = false;
+                for (int d = 0; d < 2 && !gave_up; ++d) {      // whole segments
+                    if (deps[d] < 0) continue;
+                    const int need = segs[deps[d]].nitems;
+                    while (ld_acquire(done + deps[d]) < need) {
+                        if (++polls > spin) { gave_up = true; break; }
+                        __nanosleep(200);
+                    }
+                }
+                if (S0.idep >= 0 && !gave_up) {
+                    // the items of segment idep that cover this item's boxes at
+                    // their level: the same boxes, the children or the parents
+                    const PSeg D = segs[S0.idep];
+                    const int local = it - S0.item0;
+                    int64_t blo, bhi;
+                    if (S0.wpb) { blo = (int64_t)local * SM_W; bhi = blo + SM_W - 1; }
+                    else { blo = bhi = local / S0.nchunk; }
+                    if (S0.irel == 1) { blo = 4 * blo; bhi = 4 * bhi + 3; }
+                    else if (S0.irel == 2) { blo >>= 2; bhi >>= 2; }
+                    const int64_t nb = (int64_t)1 << (2 * D.level);
+                    bhi = min(bhi, nb - 1);
+                    int ilo, ihi;
+                    if (D.wpb) { ilo = (int)(blo / SM_W); ihi = (int)(bhi / SM_W); }
+                    else { ilo = (int)(blo * D.nchunk); ihi = (int)((bhi + 1) * D.nchunk - 1); }
+                    for (int k = ilo; k <= ihi && !gave_up; ++k)
+                        while (ld_acquire(done_item + D.item0 + k) == 0) {
+                            if (++polls > spin) { gave_up = true; break; }
+                            __nanosleep(200);
+                        }
+                }
+                if (gave_up) atomicExch(ctr + 1, 1);          // flag the batch and go on
+                __threadfence();
+            }
+            s_item = it;
+            s_seg = sg;
+        }
+        __syncthreads();
+        const int it = s_item;
+        if (it >= total) break;
+        const PSeg S = segs[s_seg];
+        const PInst I = insts[S.inst];
+        const int local = it - S.item0;
+        const int64_t n = I.n;
+        switch (S.kind) {
+            case PK_GATHER:
+            case PK_SCATTER: {
+                const int64_t j0 = (int64_t)local * 64;
+                const int jn = (int)min((int64_t)64, n - j0);
+                for (int e = tid; e < 64 * nrhs; e += blockDim.x) {
+                    const int r = e >> 6, jj = e & 63;
+                    if (jj >= jn) continue;
+                    const int64_t j = j0 + jj;
+                    const int64_t sidx = (int64_t)I.iperm[j] * nrhs + r;
+                    if (S.kind == PK_GATHER) {
+                        cf v = I.q[(int64_t)r * n + j];
+                        if (adjoint) v.y = -v.y;
+                        I.q32[sidx] = v;
+                    } else {
+                        cf v = __ldcg(I.y32 + sidx);
+                        if (adjoint) v.y = -v.y;
+                        I.y[(int64_t)r * n + j] = v;
+                    }
+                }
+                break;
+            }
+            case PK_P2M: {
+                const int64_t b = (int64_t)local * SM_W + w;
+                const int nc = I.nc;
+                if (b < ((int64_t)1 << (2 * I.L))) {
+                    const int32_t lo = I.lb[b], hi = I.lb[b + 1];
+                    cf* mult = levs[I.lev0 + I.L].mult;
+                    for (int r0 = 0; r0 < nrhs; r0 += R)
+                        for (int m0 = 0; m0 < nc; m0 += 32) {
+                            const int m = m0 + lane;
+                            cf acc[R];
+#pragma unroll
+                            for (int r = 0; r < R; ++r) acc[r] = cfmk(0.f, 0.f);
+                            for (int32_t j = lo; j < hi; ++j) {
+                                const cf bv = m < nc ? I.basis[(int64_t)j * nc + m] : cfmk(0.f, 0.f);
+#pragma unroll
+                                for (int r = 0; r < R; ++r)
+                                    cfma(acc[r], bv, r0 + r < nrhs ? __ldcg(I.q32 + (int64_t)j * nrhs + r0 + r)
+                                                                   : cfmk(0.f, 0.f));
+                            }
+                            if (m < nc)
+#pragma unroll
+                                for (int r = 0; r < R; ++r)
+                                    if (r0 + r < nrhs) mult[(b * nrhs + r0 + r) * nc + m] = acc[r];
+                        }
+                }
+                break;
+            }
+            case PK_M2M: {
+                const PLev V = levs[I.lev0 + S.level];
+                if (S.wpb) {                                  // one parent box per warp
+                    const int64_t b = (int64_t)local * SM_W + w;
+                    if (b >= ((int64_t)1 << (2 * S.level))) break;
+                    const int ncc = 2 * V.pc + 1, np = 2 * V.p + 1;
+                    for (int r0 = 0; r0 < nrhs; r0 += R) {
+                        cf acc[1][R];
+#pragma unroll
+                        for (int r = 0; r < R; ++r) acc[0][r] = cfmk(0.f, 0.f);
+                        for (int c = 0; c < 4; ++c) {
+                            int32_t lo, hi;
+                            box_range(I.lb, I.L, S.level + 1, 4 * b + c, &lo, &hi);
+                            if (hi > lo)
+                                translate_source<R, 1>(acc, V.cmult + ((4 * b + c) * nrhs + r0) * (int64_t)ncc,
+                                                       V.Tm2m + (int64_t)c * ncc * np, ncc, np, 0, min(R, nrhs - r0),
+                                                       stage);
+                        }
+                        if (lane < np)
+#pragma unroll
+                            for (int r = 0; r < R; ++r)
+                                if (r0 + r < nrhs) V.mult[(b * nrhs + r0 + r) * np + lane] = acc[0][r];
+                    }
+                    break;
+                }
+                const int64_t b = local / S.nchunk;
+                const int p0 = (local % S.nchunk) * 32;
+                const int ncc = 2 * V.pc + 1, np = 2 * V.p + 1;
+                const int c = w & 3, half = (ncc + 1) / 2;
+                int32_t lo, hi;
+                box_range(I.lb, I.L, S.level + 1, 4 * b + c, &lo, &hi);
+                for (int r0 = 0; r0 < nrhs; r0 += R) {
+                    cf acc[1][R];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) acc[0][r] = cfmk(0.f, 0.f);
+                    if (hi > lo)
+                        translate_source<R, 1>(acc, V.cmult + ((4 * b + c) * nrhs + r0) * (int64_t)ncc,
+                                               V.Tm2m + (int64_t)c * ncc * np, ncc, np, p0, min(R, nrhs - r0), stage,
+                                               (w >> 2) * half, (w >> 2) * half + half);
+                    reduce_store<R, 1>(acc, red, V.mult, b * nrhs, nrhs, r0, np, p0);
+                }
+                break;
+            }
+            case PK_DOWN: {
+                const PLev V = levs[I.lev0 + S.level];
+                const int l = S.level;
+                const int64_t b = S.wpb ? (int64_t)local * SM_W + w : local / S.nchunk;
+                const int p0 = S.wpb ? 0 : (local % S.nchunk) * 32;
+                if (S.wpb && b >= ((int64_t)1 << (2 * l))) break;   // warp-uniform
+                int32_t lo, hi;
+                box_range(I.lb, I.L, l, b, &lo, &hi);
+                if (hi <= lo) break;                     // uniform over the CTA (over the warp when wpb)
+                const int nc = 2 * V.p + 1, npp = 2 * V.pp + 1;
+                const bool has_parent = V.ploc != nullptr;
+                const int64_t Pb = b >> 2;
+                const int nv0 = V.v_begin ? V.v_begin[b] : 0, nv1 = V.v_begin ? V.v_begin[b + 1] : 0;
+                const int nr0 = V.r_begin ? V.r_begin[b] : 0, nr1 = V.r_begin ? V.r_begin[b + 1] : 0;
+                const int nsrc = (has_parent ? 1 : 0) + (nv1 - nv0) + (nr1 - nr0);
+                for (int r0 = 0; r0 < nrhs; r0 += R) {
+                    const int rows = min(R, nrhs - r0);
+                    cf acc[1][R];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) acc[0][r] = cfmk(0.f, 0.f);
+                    for (int s = S.wpb ? 0 : w; s < nsrc; s += S.wpb ? 1 : SM_W) {
+                        if (has_parent && s == 0) {
+                            translate_source<R, 1>(acc, V.ploc + (Pb * nrhs + r0) * (int64_t)npp,
+                                                   V.Tl2l + (int64_t)(b & 3) * npp * nc, npp, nc, p0, rows, stage);
+                            continue;
+                        }
+                        int e = s - (has_parent ? 1 : 0);
+                        const cf* src;
+                        const cf* M;
+                        if (e < nv1 - nv0) {
+                            src = V.mult + ((int64_t)V.v_src[nv0 + e] * nrhs + r0) * nc;
+                            M = V.Tfree + (int64_t)V.v_off[nv0 + e] * nc * nc;
+                        } else {
+                            e -= nv1 - nv0;
+                            src = V.mult + ((int64_t)V.r_src[nr0 + e] * nrhs + r0) * nc;
+                            M = V.Treact + (int64_t)V.r_tab[nr0 + e] * nc * nc;
+                        }
+                        translate_source<R, 1>(acc, src, M, nc, nc, p0, rows, stage);
+                    }
+                    if (S.wpb) {
+                        if (lane < nc)
+#pragma unroll
+                            for (int r = 0; r < R; ++r)
+                                if (r0 + r < nrhs) V.loc[(b * nrhs + r0 + r) * nc + lane] = acc[0][r];
+                    } else {
+                        reduce_store<R, 1>(acc, red, V.loc, b * nrhs, nrhs, r0, nc, p0);
+                    }
+                }
+                break;
+            }
+            case PK_NEAR: {
+                const int64_t b = (int64_t)local * SM_W + w;
+                if (b >= ((int64_t)1 << (2 * I.L))) break;
+                const int32_t tlo = I.lb[b], thi = I.lb[b + 1];
+                const int ix = (int)morton_x((uint32_t)b), iy = (int)morton_y((uint32_t)b);
+                const int mside = 1 << I.L;
+                const cf* loc = levs[I.lev0 + I.L].loc;
+                const int nc = I.nc;
+                const float h = I.h, k = I.k;
+                for (int r0 = 0; r0 < nrhs; r0 += R)
+                    for (int32_t t0 = tlo; t0 < thi; t0 += 32) {
+                        const int32_t t = t0 + lane;
+                        const bool live = t < thi;
+                        const float2 tp = live ? I.xl[t] : make_float2(0.f, 0.f);
+                        cf acc[R];
+#pragma unroll
+                        for (int r = 0; r < R; ++r) acc[r] = cfmk(0.f, 0.f);
+                        for (int dy = -1; dy <= 1; ++dy)
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                const int sx = ix + dx, sy = iy + dy;
+                                if (sx < 0 || sy < 0 || sx >= mside || sy >= mside) continue;
+                                const uint32_t sb = morton((uint32_t)sx, (uint32_t)sy);
+                                const int32_t slo = I.lb[sb], shi = I.lb[sb + 1];
+                                const float ox = (float)(-dx) * h, oy = (float)(-dy) * h;
+                                for (int32_t j = slo; j < shi; ++j) {
+                                    const float2 sp = I.xl[j];
+                                    cf g = cfmk(0.f, 0.f);
+                                    if (live && t != j) {
+                                        const float ddx = ox + (tp.x - sp.x), ddy = oy + (tp.y - sp.y);
+                                        const float z = k * sqrtf(ddx * ddx + ddy * ddy);
+                                        if (z < H0_ZMAX) {
+                                            g = green_tab(tj, tr, z);
+                                        } else {
+                                            const cd h0 = hankel0((double)z);
+                                            g = cfmk((float)(-0.25 * h0.y), (float)(0.25 * h0.x));
+                                        }
+                                    }
+#pragma unroll
+                                    for (int r = 0; r < R; ++r)
+                                        cfma(acc[r], g, r0 + r < nrhs ? __ldcg(I.q32 + (int64_t)j * nrhs + r0 + r)
+                                                                      : cfmk(0.f, 0.f));
+                                }
+                            }
+                        for (int m = 0; m < nc; ++m) {          // L2P
+                            const cf B = live ? I.basis[(int64_t)t * nc + m] : cfmk(0.f, 0.f);
+                            const cf g = cfmk(0.25f * B.y, 0.25f * B.x);
+#pragma unroll
+                            for (int r = 0; r < R; ++r)
+                                cfma(acc[r], g, r0 + r < nrhs ? __ldcg(loc + (b * nrhs + r0 + r) * nc + m)
+                                                              : cfmk(0.f, 0.f));
+                        }
+                        if (live)
+#pragma unroll
+                            for (int r = 0; r < R; ++r)
+                                if (r0 + r < nrhs) I.y32[(int64_t)t * nrhs + r0 + r] = acc[r];   // first writer
+                    }
+                break;
+            }
+            case PK_DIRECT: {
+                const int64_t b = local;
+                const int32_t e0 = I.d_begin[b], e1 = I.d_begin[b + 1];
+                if (e1 <= e0) break;
+                const int32_t tlo = I.lb[b], tn = I.lb[b + 1] - tlo;
+                for (int itm = tid; itm < nrhs * tn; itm += blockDim.x) {
+                    const int i = itm / nrhs, r = itm % nrhs;
+                    cf acc = cfmk(0.f, 0.f);
+                    for (int32_t e = e0; e < e1; ++e) {
+                        const int32_t sb = I.d_src[e];
+                        const int32_t slo = I.lb[sb], sn = I.lb[sb + 1] - slo;
+                        const cf* G = I.d_vals + I.d_blk[e] + (int64_t)i * sn;
+                        for (int j = 0; j < sn; ++j) cfma(acc, G[j], __ldcg(I.q32 + (int64_t)(slo + j) * nrhs + r));
+                    }
+                    cf* yy = I.y32 + (int64_t)(tlo + i) * nrhs + r;
+                    const cf v = __ldcg(yy);
+                    *yy = cfmk(v.x + acc.x, v.y + acc.y);
+                }
+                break;
+            }
+        }
+        // this item's writes are visible before it is counted
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            atomicExch(done_item + it, 1);
+            atomicAdd(done + s_seg, 1);
+        }
+    }
+}
+
 // right-hand sides per pass: the largest of 8, 4, 2, 1 not above nrhs whose
 // staging (SM_W warps x R rows x ncs) stays within the shared-memory budget
 int pick_r(int nrhs, int ncs_max, int U) {
@@ -518,5 +854,225 @@ hfmm_status apply_small(hfmm_plan_s* P, int nrhs, int parts, cudaStream_t st) {
                                       (far ? MAC * n * leaf.ncoef : 0.0);
         P->st_bytes[HFMM_STAGE_P2P] = 3.0 * C * n + 16.0 * n + (far ? C * leaf.nbox * leaf.ncoef + 8.0 * n * leaf.ncoef : 0.0);
     }
+    return HFMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent batch: host side
+// ---------------------------------------------------------------------------
+struct PersistBatch {
+    std::vector<PSeg> segs;
+    std::vector<PInst> inst;
+    std::vector<PLev> lev;
+    int total = 0;
+    int ncs_max = 1;
+    long spin = 0;
+    PSeg* d_segs = nullptr;
+    PInst* d_inst = nullptr;
+    PLev* d_lev = nullptr;
+    int* d_ctr = nullptr;            // [0] next item, [1] error flag, [2 ..] done per segment, then per item
+    int grid[4] = {0, 0, 0, 0};      // persistent CTAs for R = 1, 2, 4, 8
+};
+
+namespace {
+
+size_t persist_smem(PersistBatch* B, int R) {
+    return smem_bytes(R, 1, B->ncs_max) + sizeof(int) * B->segs.size();
+}
+
+template <int R>
+hfmm_status persist_grid(PersistBatch* B, int* grid) {
+    const size_t sm = persist_smem(B, R);
+    auto kern = persist_kernel<R>;
+    HFMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int per_sm = 0, dev = 0, nsm = 0;
+    HFMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SM_W * 32, sm));
+    HFMM_CUDA_TRY(cudaGetDevice(&dev));
+    HFMM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (per_sm < 1) {
+        hfmm_set_error("persistent batch kernel does not fit an SM (%zu bytes of shared memory)", sm);
+        return HFMM_ERR_UNSUPPORTED;
+    }
+    *grid = std::max(1, std::min(B->total, per_sm * nsm));
+    return HFMM_OK;
+}
+
+template <int R>
+hfmm_status persist_go(PersistBatch* B, int nrhs, bool adjoint, cudaStream_t st, int grid) {
+    const size_t sm = persist_smem(B, R);
+    persist_kernel<R><<<grid, SM_W * 32, sm, st>>>(B->d_segs, (int)B->segs.size(), B->total, B->d_inst, B->d_lev,
+                                                  nrhs, adjoint ? 1 : 0, B->ncs_max, B->d_ctr, B->spin);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    return HFMM_OK;
+}
+
+}  // namespace
+
+void persist_destroy(PersistBatch* B) {
+    if (!B) return;
+    cudaFree(B->d_segs);
+    cudaFree(B->d_inst);
+    cudaFree(B->d_lev);
+    cudaFree(B->d_ctr);
+    delete B;
+}
+
+hfmm_status persist_create(const std::vector<hfmm_plan_s*>& plans, PersistBatch** out) {
+    *out = nullptr;
+    PersistBatch* B = new (std::nothrow) PersistBatch();
+    if (!B) { hfmm_set_error("host allocation failed"); return HFMM_ERR_OOM; }
+    const int ni = (int)plans.size();
+    int Lmax = 0, dmax = 0;
+    for (int i = 0; i < ni; ++i) {
+        hfmm_plan_s* P = plans[i];
+        PInst I{};
+        I.lb = P->leaf_begin;
+        I.L = P->L;
+        I.lmin = P->lmin;
+        I.lev0 = (int)B->lev.size();
+        I.nc = P->lev[P->L].ncoef;
+        I.n = P->n;
+        I.k = (float)P->k;
+        I.h = (float)P->lev[P->L].h;
+        I.xl = P->xl32;
+        I.basis = P->basis32;
+        I.q32 = P->q32;
+        I.y32 = P->y32;
+        I.iperm = P->iperm32;
+        I.d_begin = P->d_begin;
+        I.d_src = P->d_src;
+        I.d_blk = P->d_blk;
+        I.d_vals = P->d_vals32;
+        B->inst.push_back(I);
+        for (int l = 0; l <= P->L; ++l) {
+            const LevelInfo& lv = P->lev[l];
+            PLev V{};
+            if (l >= P->lmin) {
+                V.p = lv.p;
+                V.pp = l > P->lmin ? P->lev[l - 1].p : 0;
+                V.pc = l < P->L ? P->lev[l + 1].p : 0;
+                V.mult = lv.mult32;
+                V.loc = lv.loc32;
+                V.cmult = l < P->L ? P->lev[l + 1].mult32 : nullptr;
+                V.ploc = l > P->lmin ? P->lev[l - 1].loc32 : nullptr;
+                V.Tl2l = l > P->lmin ? P->lev[l - 1].t_l2l32 : nullptr;
+                V.Tfree = lv.t_free32;
+                V.Treact = lv.t_react32;
+                V.Tm2m = lv.t_m2m32;
+                V.v_begin = lv.nv ? lv.v_begin : nullptr;
+                V.v_src = lv.v_src;
+                V.v_off = lv.v_off;
+                V.r_begin = lv.nr ? lv.r_begin : nullptr;
+                V.r_src = lv.r_src;
+                V.r_tab = lv.r_tab;
+                B->ncs_max = std::max({B->ncs_max, lv.ncoef, l > P->lmin ? P->lev[l - 1].ncoef : 0,
+                                       l < P->L ? P->lev[l + 1].ncoef : 0});
+            }
+            B->lev.push_back(V);
+        }
+        Lmax = std::max(Lmax, P->L);
+        dmax = std::max(dmax, P->L - P->lmin);
+        B->spin = std::max(B->spin, P->tc_spin);
+    }
+    // segments in dependency order; seg index of (stage, instance[, level])
+    auto add = [&](int kind, int inst, int level, int nitems, int nchunk, int d0, int d1, int wpb = 0,
+                   int idep = -1, int irel = 0) {
+        PSeg S{kind, inst, level, nchunk, B->total, nitems, d0, d1, wpb, idep, irel, 0};
+        B->total += nitems;
+        B->segs.push_back(S);
+        return (int)B->segs.size() - 1;
+    };
+    std::vector<int> s_gather(ni), s_p2m(ni), s_near(ni), s_direct(ni, -1);
+    std::vector<std::vector<int>> s_up(ni), s_down(ni);
+    for (int i = 0; i < ni; ++i) {
+        s_up[i].assign(plans[i]->L + 1, -1);
+        s_down[i].assign(plans[i]->L + 1, -1);
+    }
+    for (int i = 0; i < ni; ++i) s_gather[i] = add(PK_GATHER, i, 0, ceil_div(plans[i]->n, 64), 1, -1, -1);
+    for (int i = 0; i < ni; ++i) {
+        s_p2m[i] = add(PK_P2M, i, plans[i]->L, ceil_div(plans[i]->lev[plans[i]->L].nbox, SM_W), 1, s_gather[i], -1, 1);
+        s_up[i][plans[i]->L] = s_p2m[i];
+    }
+    for (int d = 1; d <= dmax; ++d)
+        for (int i = 0; i < ni; ++i) {
+            hfmm_plan_s* P = plans[i];
+            const int l = P->L - d;
+            if (l < P->lmin) continue;
+            const int nchunk = (P->lev[l].ncoef + 31) / 32;
+            if (nchunk == 1 && P->lev[l].nbox >= 4 * SM_W)
+                s_up[i][l] = add(PK_M2M, i, l, ceil_div(P->lev[l].nbox, SM_W), 1, -1, -1, 1, s_up[i][l + 1], 1);
+            else
+                s_up[i][l] = add(PK_M2M, i, l, (int)(P->lev[l].nbox * nchunk), nchunk, -1, -1, 0, s_up[i][l + 1], 1);
+        }
+    // downward passes top level first over all instances, then the near
+    // fields, direct reactions and scatters
+    for (int l = 0; l <= Lmax; ++l)
+        for (int i = 0; i < ni; ++i) {
+            hfmm_plan_s* P = plans[i];
+            if (l < P->lmin || l > P->L) continue;
+            const int nchunk = (P->lev[l].ncoef + 31) / 32;
+            const int dprev = l > P->lmin ? s_down[i][l - 1] : -1;
+            if (nchunk == 1 && P->lev[l].nbox >= 4 * SM_W)
+                s_down[i][l] = add(PK_DOWN, i, l, ceil_div(P->lev[l].nbox, SM_W), 1, s_up[i][l], -1, 1, dprev, 2);
+            else
+                s_down[i][l] = add(PK_DOWN, i, l, (int)(P->lev[l].nbox * nchunk), nchunk, s_up[i][l], -1, 0, dprev, 2);
+        }
+    for (int i = 0; i < ni; ++i) {
+        hfmm_plan_s* P = plans[i];
+        s_near[i] = add(PK_NEAR, i, P->L, ceil_div(P->lev[P->L].nbox, SM_W), 1, s_gather[i], -1, 1, s_down[i][P->L], 0);
+    }
+    for (int i = 0; i < ni; ++i)
+        if (plans[i]->nd > 0)
+            s_direct[i] = add(PK_DIRECT, i, plans[i]->L, (int)plans[i]->lev[plans[i]->L].nbox, 1, -1, -1, 0,
+                              s_near[i], 0);
+    for (int i = 0; i < ni; ++i)
+        add(PK_SCATTER, i, 0, ceil_div(plans[i]->n, 64), 1, s_direct[i] >= 0 ? s_direct[i] : s_near[i], -1);
+    hfmm_status s = HFMM_OK;
+    auto fail = [&](cudaError_t e) {
+        hfmm_set_error("persistent batch setup: %s", cudaGetErrorString(e));
+        persist_destroy(B);
+        return e == cudaErrorMemoryAllocation ? HFMM_ERR_OOM : HFMM_ERR_CUDA;
+    };
+    cudaError_t e = cudaMalloc(&B->d_segs, sizeof(PSeg) * B->segs.size());
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_inst, sizeof(PInst) * B->inst.size());
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_lev, sizeof(PLev) * B->lev.size());
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_ctr, sizeof(int) * (2 + B->segs.size() + B->total));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(B->d_segs, B->segs.data(), sizeof(PSeg) * B->segs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(B->d_lev, B->lev.data(), sizeof(PLev) * B->lev.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(B->d_ctr, 0, sizeof(int) * (2 + B->segs.size() + B->total));
+    if (e != cudaSuccess) return fail(e);
+    if ((s = persist_grid<1>(B, &B->grid[0])) != HFMM_OK || (s = persist_grid<2>(B, &B->grid[1])) != HFMM_OK ||
+        (s = persist_grid<4>(B, &B->grid[2])) != HFMM_OK || (s = persist_grid<8>(B, &B->grid[3])) != HFMM_OK) {
+        persist_destroy(B);
+        return s;
+    }
+    *out = B;
+    return HFMM_OK;
+}
+
+hfmm_status persist_set_buffers(PersistBatch* B, const void* const* q, void* const* y, cudaStream_t st) {
+    for (size_t i = 0; i < B->inst.size(); ++i) {
+        B->inst[i].q = (const cf*)q[i];
+        B->inst[i].y = (cf*)y[i];
+    }
+    HFMM_CUDA_TRY(cudaMemcpyAsync(B->d_inst, B->inst.data(), sizeof(PInst) * B->inst.size(), cudaMemcpyHostToDevice,
+                                  st));
+    HFMM_CUDA_TRY(cudaStreamSynchronize(st));
+    return HFMM_OK;
+}
+
+hfmm_status persist_launch(PersistBatch* B, int nrhs, bool adjoint, cudaStream_t st) {
+    HFMM_CUDA_TRY(cudaMemsetAsync(B->d_ctr, 0, sizeof(int) * (2 + B->segs.size() + B->total), st));
+    if (nrhs >= 8) return persist_go<8>(B, nrhs, adjoint, st, B->grid[3]);
+    if (nrhs >= 4) return persist_go<4>(B, nrhs, adjoint, st, B->grid[2]);
+    if (nrhs >= 2) return persist_go<2>(B, nrhs, adjoint, st, B->grid[1]);
+    return persist_go<1>(B, nrhs, adjoint, st, B->grid[0]);
+}
+
+hfmm_status persist_device_error(PersistBatch* B, int* err) {
+    HFMM_CUDA_TRY(cudaDeviceSynchronize());
+    HFMM_CUDA_TRY(cudaMemcpy(err, B->d_ctr + 1, sizeof(int), cudaMemcpyDeviceToHost));
     return HFMM_OK;
 }

@@ -744,3 +744,61 @@ def test_small_rhs_engine_matches_tensor_engine_and_fp64(nrhs):
     assert torch.equal(sm.apply(q32), sm.apply(q32))
     for p in (sm, tc, f64):
         p.close()
+
+
+def test_persistent_batch_forward_and_adjoint_match_single_plans():
+    """Uneven mixed-precision instances (1 and 3 right-hand sides) through the
+    persistent batch kernel: every stage of every instance from one device
+    work queue; forward and adjoint against single-plan applies and the FP64
+    path, on the recording call and on a replay."""
+    from paper_1703_09136_gb300 import Batch, MIXED
+    med = W.WORKLOADS[5].medium
+    sizes = [4100, 900, 30000, 1500, 12000, 60]
+    xys = [W.points(5, n, salt=20 + i) for i, n in enumerate(sizes)]
+    for nrhs in (1, 3):
+        qs = [torch.from_numpy(W.strengths(5, n, nrhs, salt=i)).cuda().to(torch.complex64)
+              for i, n in enumerate(sizes)]
+        batch = Batch(xys, med, leaf_size=32, precision=MIXED, max_rhs=nrhs, persistent=True)
+        singles = [Plan(xy, med, leaf_size=32, precision=MIXED, max_rhs=nrhs) for xy in xys]
+        f64 = [Plan(xy, med, leaf_size=32, max_rhs=nrhs) for xy in xys]
+        for adjoint in (False, True):
+            ys = [torch.empty_like(q) for q in qs]
+            for rep in range(2):
+                for y in ys:
+                    y.fill_(float("nan"))
+                batch.apply(qs, ys, adjoint=adjoint)
+                torch.cuda.synchronize()
+                assert batch.device_error == 0
+                for sp, p64, q, y in zip(singles, f64, qs, ys):
+                    ref = sp.adjoint(q) if adjoint else sp.apply(q)
+                    err = float(torch.linalg.norm(ref - y) / torch.linalg.norm(ref))
+                    assert err < 1e-6, (nrhs, adjoint, rep, err)
+                    q64 = q.to(torch.complex128)
+                    r64 = p64.adjoint(q64) if adjoint else p64.apply(q64)
+                    assert float(torch.linalg.norm(y.to(torch.complex128) - r64) / torch.linalg.norm(r64)) < MIXED_TOL
+        batch.close()
+        for p in singles + f64:
+            p.close()
+
+
+def test_persistent_batch_wait_limit_reports_instead_of_hanging():
+    """Every dependency wait of the persistent batch kernel is bounded: with a
+    one-poll limit, items that find their inputs unfinished give up, the batch
+    reports a device error, and the kernel still finishes (no hang, no fault);
+    with the default limit the same batch reports none."""
+    from paper_1703_09136_gb300 import Batch, MIXED
+    med = W.WORKLOADS[5].medium
+    sizes = [40000, 30000, 20000, 10000]
+    xys = [W.points(5, n, salt=30 + i) for i, n in enumerate(sizes)]
+    qs = [torch.from_numpy(W.strengths(5, n, 1, salt=i)).cuda().to(torch.complex64) for i, n in enumerate(sizes)]
+    ys = [torch.empty_like(q) for q in qs]
+    tight = Batch(xys, med, leaf_size=32, precision=MIXED, max_rhs=1, spin_limit=1, persistent=True)
+    tight.apply(qs, ys)
+    tight.apply(qs, ys)
+    assert tight.device_error == 1
+    tight.close()
+    ok = Batch(xys, med, leaf_size=32, precision=MIXED, max_rhs=1, persistent=True)
+    ok.apply(qs, ys)
+    ok.apply(qs, ys)
+    assert ok.device_error == 0
+    ok.close()
