@@ -186,13 +186,26 @@ def p_schedule(k, tree, tol, p_fixed=0):
     """p_l = base + ceil(k R_l + 1.8 d^(2/3) max(k R_l - 1, 0)^(1/3)),
     R_l = h_l / sqrt(2), d = -log10(tol), base = p_fixed if given, else
     p_low(tol).  The second term is the excess bandwidth of wide-band FMMs
-    for boxes larger than the wavelength.  Returns p per level 0..L."""
+    for boxes larger than the wavelength.
+
+    Range cap: the translations use unscaled H_n(k r), n <= 2 p_l, whose size
+    near the closest translated distance r = min(2 h_l, 2 y0 + h_l) is about
+    (n-1)! (2/(k r))^n / pi for k r << n; p_l is lowered until
+    lgamma(2p) + 2p log(2/(k r)) <= 680, so every entry stays inside the
+    double range (e^709).  This only binds at low frequency on deep trees
+    with a large fixed p (e.g. k = 0.1 and p = 39 below h = 1/32).
+    Returns p per level 0..L."""
     base = p_fixed if p_fixed > 0 else p_low(tol)
     d = max(1.0, -math.log10(tol))
     out = []
     for l in range(tree.L + 1):
-        kR = k * tree.h(l) / math.sqrt(2.0)
-        out.append(base + int(math.ceil(kR + 1.8 * d ** (2.0 / 3.0) * max(kR - 1.0, 0.0) ** (1.0 / 3.0))))
+        h = tree.h(l)
+        kR = k * h / math.sqrt(2.0)
+        p = base + int(math.ceil(kR + 1.8 * d ** (2.0 / 3.0) * max(kR - 1.0, 0.0) ** (1.0 / 3.0)))
+        lx = math.log(2.0 / (k * min(2.0 * h, 2.0 * tree.y0 + h)))
+        while p > 1 and math.lgamma(2.0 * p) + 2.0 * p * lx > 680.0:
+            p -= 1
+        out.append(p)
     return out
 
 

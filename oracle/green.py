@@ -258,6 +258,9 @@ def t_rule(medium, xmax, ymin, nmax, refine=1):
         w = min(wmax, max(5.0 * max(a, 0.5 / k1) / max(nmax, 1), 0.02 * wmax, 1e-3), T - a)
         if alpha is not None:
             w = min(w, 1.5 * math.hypot(a, alpha))
+        # 1/xi, xi = sqrt(t^2 + k1^2), has branch points at t = +-i k1: at low
+        # frequency they sit close to t = 0, so the panels there are graded too
+        w = min(w, 1.5 * math.hypot(a, k1))
         w = max(w / refine, 1e-12)
         a = a + w
         edges.append(a)

@@ -63,6 +63,19 @@ def test_impedance_reaction_equals_complex_line_image(X, Y):
     assert abs(a - b) <= 2e-12 * abs(b) + 1e-15
 
 
+@pytest.mark.parametrize("k,alpha,X,Y", [(0.1, 1.0, 0.3, 3.1), (0.1, 1.0, 0.0, 2.0), (0.1, 0.05, 0.4, 2.5),
+                                         (1.0, 1.0, 0.2, 0.05), (0.1, 1.0, 0.5, 0.04)])
+def test_impedance_reaction_at_low_frequency(k, alpha, X, Y):
+    """Low frequency (the paper's timing runs, Sec. 4: k = 0.1, alpha = 1):
+    the evanescent integrand's 1/xi has branch points at t = +-i k, close to
+    the path near t = 0; the rule must still reproduce the line image of
+    Eq. (Sfield)."""
+    med = Medium(IMP, (k,), alpha=alpha)
+    a = green.green_reaction(med, X, Y)[0]
+    b = green.green_reaction_line_image(k, alpha, X, Y)
+    assert abs(a - b) <= 1e-11 * abs(b)
+
+
 @pytest.mark.parametrize("alpha", [0.5, 2.0, 19.0])
 @pytest.mark.parametrize("X,Y", [(0.0, 0.1), (0.1, 0.2), (0.5, 0.3)])
 def test_impedance_reaction_with_a_pole_near_the_path(alpha, X, Y):
@@ -461,3 +474,23 @@ def test_position_gradient_of_the_loss_matches_finite_differences():
             zm = xy.copy(); zm[j, d] -= h
             fd = (loss(zp) - loss(zm)) / (2 * h)
             assert abs(fd - G[j, d]) < 1e-5 * max(1.0, abs(G[j, d]))
+
+
+def test_order_cap_keeps_translation_entries_in_double_range():
+    """Low frequency on a deep tree with the paper's p = 39 (Sec. 4: k = 0.1):
+    the capped order keeps every free-space translation entry H_n(k r) of the
+    closest V-list distance finite (SciPy), and the cap does not bind at the
+    paper's own depth (L = 3) or at the default tolerance orders."""
+    xy = W.points_in_box(6, 2000, ((-0.5, 0.5), (1.0, 2.0)))
+    k = 0.1
+    deep = fmm.build_tree(xy, L=8)
+    p = fmm.p_schedule(k, deep, 1e-6, p_fixed=38)
+    assert p[3] == 39 and p[8] < 39
+    for l in range(2, 9):
+        x = k * 2.0 * deep.h(l)
+        assert np.all(np.isfinite(hankel1(np.arange(0, 2 * p[l] + 1), x))), l
+        # one order more would overflow somewhere the cap is active
+        if p[l] < 39:
+            assert not np.all(np.isfinite(hankel1(np.arange(0, 2 * p[l] + 9), x))), l
+    shallow = fmm.build_tree(xy, L=3)
+    assert fmm.p_schedule(k, shallow, 1e-6, p_fixed=38) == [39] * 4
