@@ -91,6 +91,8 @@ def parse():
                     help="skip the FP64 reference apply (accuracy and one-RHS FP64 time)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="the N-sweep of the paper's timing table instead of the benchmark")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the two-layer and uneven-batch workloads measured after the headline")
     ap.add_argument("--cpu-sample-n", type=int, default=0)
@@ -467,6 +469,55 @@ def measure_batch(dev, steps, cpu=True):
     return out
 
 
+# Times of the paper's serial CPU code for this sweep (Sec. 4, Table 2: Xeon E5
+# 3.7 GHz, k = 0.1, p = 39; the precision is not stated), seconds per apply.
+PAPER_TABLE2_S = {100: 0.01, 6400: 0.67, 10000: 1.19, 90000: 10.92, 360000: 46.58, 640000: 100.85,
+                  810000: 116.03, 1000000: 135.05}
+
+
+def run_sweep(args):
+    """The N-sweep of the paper's timing table: impedance alpha = 1, k = 0.1
+    and 1, points uniform in the unit box centred at (0, 1.5), fixed order
+    p = 39 on every level, one right-hand side; FP64 and mixed precision."""
+    import torch
+    import workloads as W
+    from paper_1703_09136_gb300 import Plan, FP64, MIXED
+    from paper_1703_09136_gb300 import build as _build
+    _build.build()
+    w = W.WORKLOADS[6]
+    dev = torch.device("cuda", 0)
+    rows = []
+    for k in w.extra["k"]:
+        med = W.Medium(W.IMPEDANCE, (k,), alpha=w.medium.alpha)
+        for n in w.extra["n"]:
+            xy = torch.from_numpy(W.points_in_box(6, n, w.box)).to(dev)
+            q64 = torch.from_numpy(W.strengths(6, n, 1)).to(dev)
+            row = {"k": k, "n": n, "paper_cpu_s": PAPER_TABLE2_S.get(n) if k == 0.1 else None}
+            for prec, name in ((FP64, "fp64"), (MIXED, "mixed")):
+                q = q64 if prec == FP64 else q64.to(torch.complex64)
+                # the order rule adds ceil(k R_l) = 1 at these sizes: base 38 gives p = 39 on every level
+                t0 = time.perf_counter()
+                plan = Plan(xy, med, p=w.extra["p"] - 1, leaf_size=w.leaf, precision=prec, max_rhs=1)
+                torch.cuda.synchronize()
+                row[name + "_plan_s"] = time.perf_counter() - t0
+                y = torch.empty_like(q)
+                row[name + "_ms"] = _events_ms(lambda: plan.apply(q, out=y), 5 if prec == FP64 else 20)
+                inf = plan.info
+                row["levels"], row["p"] = inf["levels"], sorted(set(inf["p"][inf["lmin"]:]))
+                if prec == FP64:
+                    y64 = y.clone()
+                else:
+                    row["rel_l2_mixed_vs_fp64"] = float(torch.linalg.norm(y.to(torch.complex128) - y64)
+                                                        / torch.linalg.norm(y64))
+                plan.close()
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+    out = {"metric": "H-FMM apply time vs N (shape of the paper's timing table)", "unit": "ms",
+           "workload": w.name, "medium": "impedance alpha=1", "box": w.box, "p": w.extra["p"], "nrhs": 1,
+           "rows": rows, "paper_hardware": "serial CPU code, Xeon E5 3.7 GHz, 32 GB, gcc 4.9.3 (k = 0.1)"}
+    print(json.dumps(out), flush=True)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -804,7 +855,9 @@ def main():
         print(json.dumps(_cpu_child(json.loads(sys.argv[2]))), flush=True)
         return
     args = parse()
-    if args.impl == "reference":
+    if args.sweep:
+        run_sweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.config == 5:
         run_batch(args)

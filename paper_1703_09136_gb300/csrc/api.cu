@@ -291,6 +291,13 @@ static hfmm_status plan_create_one(hfmm_plan_t* out, int64_t n, const double* xy
             const double kR = P->k * lv.h / std::sqrt(2.0);
             lv.p = base + (int)std::ceil(kR + 1.8 * std::pow(dgt, 2.0 / 3.0) *
                                                   std::pow(std::max(kR - 1.0, 0.0), 1.0 / 3.0));
+            // range cap: the unscaled translation entries H_n(k r), n <= 2p, of the
+            // closest translated pair (r >= min(2 h_l, 2 y0 + h_l)) stay below
+            // ~e^680, |H_n(x)| ~ (n-1)! (2/x)^n / pi for x << n
+            const double lx = std::log(2.0 / (P->k * std::min(2.0 * lv.h, 2.0 * P->y0 + lv.h)));
+            int pcap = lv.p;
+            while (pcap > 1 && std::lgamma(2.0 * pcap) + 2.0 * pcap * lx > 680.0) --pcap;
+            lv.p = pcap;
             lv.ncoef = 2 * lv.p + 1;
         }
         if ((s = build_lists(P, st)) != HFMM_OK) break;

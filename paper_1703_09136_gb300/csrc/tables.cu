@@ -229,6 +229,9 @@ int64_t make_rule(const hfmm_medium& m, double xmax, double ymin, double ymax, i
         double w = std::min(wc, std::max(wmin, wl));
         // impedance pole at t = i alpha: panel width <= 1.5 x its distance
         if (imp_pole) w = std::min(w, 1.5 * std::sqrt(a * a + m.alpha * m.alpha));
+        // branch points of 1/xi, xi = sqrt(t^2 + k1^2), at t = +-i k1 (close to
+        // t = 0 at low frequency): the same grading
+        w = std::min(w, 1.5 * std::sqrt(a * a + k1 * k1));
         double b = (w < wc) ? std::min(T, std::max(a + 16.0 * w, 2.0 * a)) : T;
         push(a, b, 2, (int)std::ceil((b - a) / w), 0.0, 0.0);
         a = b;

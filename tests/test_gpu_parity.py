@@ -802,3 +802,24 @@ def test_persistent_batch_wait_limit_reports_instead_of_hanging():
     ok.apply(qs, ys)
     assert ok.device_error == 0
     ok.close()
+
+
+def test_low_frequency_deep_tree_with_the_papers_order():
+    """The setting of the paper's timing table (Sec. 4: impedance alpha = 1,
+    k = 0.1, p = 39) on a deep tree: the order is capped where the unscaled
+    translation entries would leave the double range, both precisions stay
+    finite and match the oracle's direct sum."""
+    from paper_1703_09136_gb300 import MIXED
+    med = Medium(W.IMPEDANCE, (0.1,), alpha=1.0)
+    xy = W.points_in_box(6, 3000, ((-0.5, 0.5), (1.0, 2.0)))
+    q = W.strengths(6, 3000, 1)
+    yd = direct.direct_apply(med, xy, q)
+    F = fmm.CpuFmm(xy, med, p=38, L=7)
+    p64 = Plan(xy, med, p=38, levels=7)
+    assert p64.info["p"] == F.p and min(F.p) < 39
+    y64 = p64.apply(q)
+    assert np.all(np.isfinite(y64)) and direct.rel_l2(y64, yd) < 1e-8, direct.rel_l2(y64, yd)
+    p32 = Plan(xy, med, p=38, levels=7, precision=MIXED)
+    y32 = p32.apply(q.astype(np.complex64)).astype(np.complex128)
+    assert np.all(np.isfinite(y32)) and direct.rel_l2(y32, yd) < MIXED_TOL, direct.rel_l2(y32, yd)
+    p64.close(); p32.close()

@@ -69,6 +69,13 @@ WORKLOADS = {
     5: Workload("impedance-batch32-k40", Medium(IMPEDANCE, (40.0,), alpha=20.0),
                 0, ((0.0, 1.0), (0.05, 1.05)), 1, 1e-6, 32, "batch",
                 {"ninst": 32, "nmin": 4096, "nmax": 200000}),
+    # the setting of the paper's timing table (Sec. 4): impedance alpha = 1,
+    # low frequency, sources = targets in the unit box centred at (0, 1.5),
+    # fixed order p = 39; N runs over the table's sizes
+    6: Workload("impedance-table2-sweep", Medium(IMPEDANCE, (0.1,), alpha=1.0),
+                0, ((-0.5, 0.5), (1.0, 2.0)), 1, 1e-6, 32, "sweep",
+                {"p": 39, "k": (0.1, 1.0),
+                 "n": (100, 6400, 10000, 90000, 360000, 640000, 810000, 1000000)}),
 }
 
 
