@@ -316,6 +316,7 @@ static hfmm_status plan_create_one(hfmm_plan_t* out, int64_t n, const double* xy
         if ((s = plan_alloc(P, mixed ? (void**)&P->y32 : (void**)&P->y_sorted, esz * n * o.max_rhs)) != HFMM_OK) break;
         P->buffer_bytes += 2.0 * esz * n * o.max_rhs;
         if ((s = build_tables(P, st)) != HFMM_OK) break;
+        if (!mixed && (s = build_near64(P, st)) != HFMM_OK) break;
         if (mixed) {
             if ((s = build_tables32(P, st)) != HFMM_OK) break;
             if ((s = init_h0_table(st)) != HFMM_OK) break;

@@ -286,6 +286,78 @@ __global__ void direct_react_kernel(const int32_t* lb, const int32_t* d_begin, c
     }
 }
 
+// Near field from per-plan blocks (FP64 plans): for every target leaf T the
+// values (i/4) H0(k |x_t - x_s|) of all its U-list sources s (the 3 x 3
+// neighbourhood in dy, dx order, each leaf's points in order; 0 for s = t),
+// stored source-major, G[off[T] + j * n_T + i], so that the lanes (targets)
+// of a warp read consecutive values.  The plan computes each H0 once; an
+// apply streams the blocks.
+__global__ void near64_fill_kernel(const int32_t* __restrict__ lb, int L, const double2* __restrict__ xs, double k,
+                                   const int64_t* __restrict__ off, cd* __restrict__ G) {
+    const int64_t b = blockIdx.x;
+    const int32_t tlo = lb[b], tn = lb[b + 1] - tlo;
+    if (tn <= 0) return;
+    const int m = 1 << L;
+    const int ix = (int)morton_x((uint32_t)b), iy = (int)morton_y((uint32_t)b);
+    int64_t j0 = 0;
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int sx = ix + dx, sy = iy + dy;
+            if (sx < 0 || sy < 0 || sx >= m || sy >= m) continue;
+            const uint32_t s = morton((uint32_t)sx, (uint32_t)sy);
+            const int32_t slo = lb[s], sn = lb[s + 1] - slo;
+            for (int e = threadIdx.x; e < sn * tn; e += blockDim.x) {
+                const int j = e / tn, i = e % tn;
+                cd g = cmk(0.0, 0.0);
+                if (tlo + i != slo + j) {
+                    const double2 a = xs[tlo + i], c = xs[slo + j];
+                    const cd h0 = hankel0(k * hypot(a.x - c.x, a.y - c.y));
+                    g = cmk(-0.25 * h0.y, 0.25 * h0.x);
+                }
+                G[off[b] + (j0 + j) * tn + i] = g;
+            }
+            j0 += sn;
+        }
+}
+
+// y[r][t] += sum over the U-list sources s of G[s][t] q[r][s]: a warp per
+// target leaf (four per CTA), lane = target (passes of 32).
+__global__ void __launch_bounds__(128) near64_kernel(const int32_t* __restrict__ lb, int L, int64_t nleaf,
+                                                     const int64_t* __restrict__ off, const cd* __restrict__ G,
+                                                     const cd* __restrict__ qs, int64_t n, int nrhs,
+                                                     cd* __restrict__ ys) {
+    const int64_t b = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (b >= nleaf) return;
+    const int lane = threadIdx.x & 31;
+    const int32_t tlo = lb[b], tn = lb[b + 1] - tlo;
+    if (tn <= 0) return;
+    const int m = 1 << L;
+    const int ix = (int)morton_x((uint32_t)b), iy = (int)morton_y((uint32_t)b);
+    const cd* Gb = G + off[b];
+    for (int r = 0; r < nrhs; ++r)
+        for (int i0 = 0; i0 < tn; i0 += 32) {
+            const int i = i0 + lane;
+            const bool live = i < tn;
+            cd acc = cmk(0.0, 0.0);
+            int64_t j = 0;
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int sx = ix + dx, sy = iy + dy;
+                    if (sx < 0 || sy < 0 || sx >= m || sy >= m) continue;
+                    const uint32_t s = morton((uint32_t)sx, (uint32_t)sy);
+                    const int32_t slo = lb[s], shi = lb[s + 1];
+                    const cd* qr = qs + (int64_t)r * n;
+#pragma unroll 4
+                    for (int32_t js = slo; js < shi; ++js, ++j)
+                        if (live) cfma(acc, Gb[j * tn + i], qr[js]);
+                }
+            if (live) {
+                cd* yy = ys + (int64_t)r * n + tlo + i;
+                *yy = cadd(*yy, acc);
+            }
+        }
+}
+
 int pick_chunk(int p) {
     const int ncoef = 2 * p + 1;
     int c = (int)(40000 / (ncoef * 16 + (p + 1) * 8));
@@ -376,13 +448,18 @@ hfmm_status apply_fp64(hfmm_plan_s* P, int nrhs, const cd* q, cd* y, int parts, 
     // step 5: direct interactions
     if (parts & HFMM_PART_NEAR_FREE) {
         tm.begin(HFMM_STAGE_P2P);
-        p2p_kernel<<<(unsigned)P->lev[L].nbox, P2P_THREADS, 0, st>>>(P->leaf_begin, L, P->xy_sorted,
-                                                                     P->q_sorted, n, nrhs, P->k, P->y_sorted);
+        if (P->near64_vals)
+            near64_kernel<<<(unsigned)ceil_div(P->lev[L].nbox, 4), 128, 0, st>>>(
+                P->leaf_begin, L, P->lev[L].nbox, P->near64_off, P->near64_vals, P->q_sorted, n, nrhs, P->y_sorted);
+        else
+            p2p_kernel<<<(unsigned)P->lev[L].nbox, P2P_THREADS, 0, st>>>(P->leaf_begin, L, P->xy_sorted,
+                                                                         P->q_sorted, n, nrhs, P->k, P->y_sorted);
         ++P->launches;
         HFMM_CUDA_TRY(cudaGetLastError());
         tm.end(HFMM_STAGE_P2P);
         P->st_flops[HFMM_STAGE_P2P] = MAC * (double)P->p2p_point_pairs;
-        P->st_bytes[HFMM_STAGE_P2P] = C * n + 2.0 * C * n + 16.0 * n;
+        P->st_bytes[HFMM_STAGE_P2P] = C * n + 2.0 * C * n + 16.0 * n +
+                                      (P->near64_vals ? 16.0 * (double)P->p2p_point_pairs : 0.0);
     }
     if ((parts & HFMM_PART_NEAR_REACT) && P->nd > 0) {
         tm.begin(HFMM_STAGE_DIRECT);
@@ -670,5 +747,41 @@ hfmm_status apply_grad_fp64(hfmm_plan_s* P, int nrhs, const cd* q, const cd* g, 
     gather_q<<<nb, 256, 0, st>>>(q, P->perm, n, nrhs, false, P->q_sorted);
     grad_combine_kernel<<<nb, 256, 0, st>>>(P->q_sorted, gsc, ux, uy, wx, wy, P->perm, n, nrhs, gxy);
     HFMM_CUDA_TRY(cudaGetLastError());
+    return HFMM_OK;
+}
+
+// Plan-time near-field blocks of an FP64 plan (skipped above the byte budget:
+// the apply then evaluates H0 per pair).
+hfmm_status build_near64(hfmm_plan_s* P, cudaStream_t st) {
+    const int L = P->L;
+    const int64_t nleaf = P->lev[L].nbox;
+    const auto& lb = P->h_leaf_begin;
+    const int m = 1 << L;
+    std::vector<int64_t> off(nleaf + 1, 0);
+    for (int64_t b = 0; b < nleaf; ++b) {
+        const int64_t tn = lb[b + 1] - lb[b];
+        int64_t ns = 0;
+        if (tn > 0) {
+            const int ix = (int)morton_x((uint32_t)b), iy = (int)morton_y((uint32_t)b);
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int sx = ix + dx, sy = iy + dy;
+                    if (sx < 0 || sy < 0 || sx >= m || sy >= m) continue;
+                    const uint32_t s = morton((uint32_t)sx, (uint32_t)sy);
+                    ns += lb[s + 1] - lb[s];
+                }
+        }
+        off[b + 1] = off[b] + tn * ns;
+    }
+    const double bytes = 16.0 * (double)off[nleaf];
+    if (bytes > NEAR64_MAX_BYTES) return HFMM_OK;
+    HFMM_TRY(plan_alloc(P, (void**)&P->near64_off, sizeof(int64_t) * (nleaf + 1)));
+    HFMM_TRY(plan_alloc(P, (void**)&P->near64_vals, sizeof(cd) * std::max<int64_t>(off[nleaf], 1)));
+    HFMM_CUDA_TRY(cudaMemcpyAsync(P->near64_off, off.data(), sizeof(int64_t) * (nleaf + 1), cudaMemcpyHostToDevice, st));
+    near64_fill_kernel<<<(unsigned)nleaf, 128, 0, st>>>(P->leaf_begin, L, P->xy_sorted, P->k, P->near64_off,
+                                                        P->near64_vals);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    P->table_bytes += bytes;
+    HFMM_CUDA_TRY(cudaStreamSynchronize(st));
     return HFMM_OK;
 }

@@ -161,6 +161,10 @@ struct hfmm_plan_s {
                                     // theorem folded in); its conjugate is the L2P basis
     // position gradients (FP64): field-gradient buffers and d/dX, d/dY of the
     // directly summed reaction blocks
+    // FP64 near field: (i/4) H0 blocks of every target leaf's U list, built
+    // at plan time (fmm64.cu), and their offsets per leaf; null above the budget
+    int64_t* near64_off = nullptr;
+    cd* near64_vals = nullptr;
     cd* grad_buf = nullptr;         // [5][max_rhs][n]
     cd* grad_q = nullptr;           // mixed plans: widened strengths / loss gradient
     cd* grad_g = nullptr;
@@ -239,6 +243,8 @@ hfmm_status build_tables32(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status build_direct_grad(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status apply_grad_fp64(hfmm_plan_s* P, int nrhs, const cd* q, const cd* g, double* gxy, cudaStream_t st);
 // fmm64.cu
+constexpr double NEAR64_MAX_BYTES = 32e9;   // plan-time FP64 near-field blocks up to this size
+hfmm_status build_near64(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status apply_fp64(hfmm_plan_s* P, int nrhs, const cd* q, cd* y, int parts, bool adjoint,
                        cudaStream_t st);
 // fmm32.cu
