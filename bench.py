@@ -424,6 +424,12 @@ def measure_batch(dev, steps, cpu=True):
         plan_s = time.perf_counter() - t0
         ms = _events_ms(lambda: batch.apply(qs, ys), steps if prec == MIXED else 3)
         rec = {"ms_per_apply": ms, "value": ntot / (ms * 1e-3) / 1e6, "plan_s": plan_s}
+        if not pers:
+            # position gradient of every instance (FP64 pass for both precisions) and the
+            # strength gradient (the batch adjoint), for a loss gradient g = y
+            ys_g = [y.clone() for y in ys]
+            rec["position_grad_ms"] = _events_ms(lambda: batch.grad(qs, ys_g), 3)
+            rec["strength_grad_ms"] = _events_ms(lambda: batch.apply(ys_g, ys, adjoint=True), 3)
         if pers:
             rec["engine"] = "one persistent kernel over a device work queue (HFMM_FLAG_PERSISTENT)"
             rec["device_error"] = batch.device_error

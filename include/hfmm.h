@@ -273,6 +273,16 @@ hfmm_status hfmm_batch_apply(hfmm_batch_t batch, int32_t nrhs, const void* const
  * *device_error (0 = none; always 0 for batches on the per-instance graph).
  */
 hfmm_status hfmm_batch_device_error(hfmm_batch_t batch, int32_t* device_error);
+/*
+ * Position gradients of every instance of a batch (hfmm_apply_grad per
+ * instance, in order, on `stream`): gxy[i] = dL/dx, dL/dy of instance i for a
+ * real loss of y_i = A_i q_i, given g[i] = dL/dRe(y_i) + i dL/dIm(y_i).
+ * Strength gradients are the adjoint (hfmm_batch_apply with adjoint != 0).
+ * Same buffer rules and errors as hfmm_apply_grad (Sec. 2.4: A_ij =
+ * u_{x_j}(x_i); the derivative acts on both arguments of G).
+ */
+hfmm_status hfmm_batch_apply_grad(hfmm_batch_t batch, int32_t nrhs, const void* const* q, const void* const* g,
+                                  double* const* gxy, void* stream);
 /* Plan of instance i (owned by the batch; for introspection and single applies). */
 hfmm_status hfmm_batch_get_plan(hfmm_batch_t batch, int32_t i, hfmm_plan_t* plan);
 hfmm_status hfmm_batch_destroy(hfmm_batch_t batch);

@@ -318,6 +318,20 @@ class Batch:
         _n.check(_n.lib().hfmm_batch_apply(self._h, nrhs, qp, yp, 1 if adjoint else 0, _stream_handle(stream)))
         return ys
 
+    def grad(self, qs, gs, outs=None, stream=None):
+        """Position gradients [n_i, 2] (float64) of every instance for a real
+        loss of y_i = A_i q_i, given g_i = dL/dRe(y_i) + i dL/dIm(y_i)
+        (hfmm_batch_apply_grad); device tensors."""
+        if outs is None:
+            outs = [torch_empty2(q) for q in qs]
+        nrhs = 1 if qs[0].dim() == 1 else int(qs[0].shape[0])
+        gs = [g.contiguous().to(q.dtype) for g, q in zip(gs, qs)]
+        qp = (ctypes.c_void_p * len(qs))(*[q.data_ptr() for q in qs])
+        gp = (ctypes.c_void_p * len(gs))(*[g.data_ptr() for g in gs])
+        op = (ctypes.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+        _n.check(_n.lib().hfmm_batch_apply_grad(self._h, nrhs, qp, gp, op, _stream_handle(stream)))
+        return outs
+
     @property
     def device_error(self):
         """Flag of the last persistent-kernel apply (a bounded wait gave up); synchronises."""
@@ -335,6 +349,12 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def torch_empty2(q):
+    """[n, 2] float64 tensor on q's device for the gradient of q's points."""
+    torch = _torch()
+    return torch.empty((int(q.shape[-1]), 2), dtype=torch.float64, device=q.device)
 
 
 def matvec(xy, q, medium, **plan_options):

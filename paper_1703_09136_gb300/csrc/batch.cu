@@ -173,6 +173,18 @@ hfmm_status hfmm_batch_apply(hfmm_batch_t B, int32_t nrhs, const void* const* q,
     return HFMM_OK;
 }
 
+hfmm_status hfmm_apply_grad(hfmm_plan_t P, int32_t nrhs, const void* q, const void* g, double* gxy, void* stream);
+
+hfmm_status hfmm_batch_apply_grad(hfmm_batch_t B, int32_t nrhs, const void* const* q, const void* const* g,
+                                  double* const* gxy, void* stream) {
+    if (!B || !q || !g || !gxy) { hfmm_set_error("batch, q, g or gxy is NULL"); return HFMM_ERR_INVALID_ARG; }
+    for (int i = 0; i < B->ninst; ++i) {
+        hfmm_status s = hfmm_apply_grad(B->plans[i], nrhs, q[i], g[i], gxy[i], stream);
+        if (s != HFMM_OK) return s;
+    }
+    return HFMM_OK;
+}
+
 hfmm_status hfmm_batch_device_error(hfmm_batch_t B, int32_t* device_error) {
     if (!B || !device_error) { hfmm_set_error("batch or device_error is NULL"); return HFMM_ERR_INVALID_ARG; }
     *device_error = 0;

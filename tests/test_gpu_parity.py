@@ -823,3 +823,62 @@ def test_low_frequency_deep_tree_with_the_papers_order():
     y32 = p32.apply(q.astype(np.complex64)).astype(np.complex128)
     assert np.all(np.isfinite(y32)) and direct.rel_l2(y32, yd) < MIXED_TOL, direct.rel_l2(y32, yd)
     p64.close(); p32.close()
+
+
+def test_batch_gradients_at_the_uneven_batch_spec():
+    """Differentiation on an uneven impedance batch (k = 40, alpha = 20): loss
+    L = sum_i |A_i(x_i) q_i - y_obs_i|^2 with y_obs_i from positions moved by
+    N(0, (1e-3)^2); the strength gradient through the batch adjoint and the
+    position gradient through hfmm_batch_apply_grad, FP64 against central
+    differences (h = 1e-6) and both precisions against the oracle's
+    direct-sum gradient on two instances (Sec. 2.4: A_ij = u_{x_j}(x_i))."""
+    from paper_1703_09136_gb300 import Batch, MIXED
+    med = W.WORKLOADS[5].medium
+    sizes = [1500, 400, 2600, 800]
+    xys = [W.points(5, n, salt=40 + i) for i, n in enumerate(sizes)]
+    q_h = [W.strengths(5, n, 1, salt=40 + i) for i, n in enumerate(sizes)]
+    y_obs = []
+    for i, n in enumerate(sizes):
+        p = Plan(W.perturb(5, xys[i], 1e-3, salt=i), med, tol=1e-12, leaf_size=32)
+        y_obs.append(p.apply(q_h[i]))
+        p.close()
+    opts = dict(tol=1e-12, leaf_size=32)
+
+    def loss_i(i, xy, q):
+        p = Plan(xy, med, **opts)
+        r = p.apply(q) - y_obs[i]
+        p.close()
+        return float(np.sum(np.abs(r) ** 2))
+
+    grads = {}
+    for prec, cdt, tol in ((0, torch.complex128, 1e-12), (MIXED, torch.complex64, 1e-6)):
+        batch = Batch(xys, med, tol=tol, leaf_size=32, precision=prec, max_rhs=1)
+        qs = [torch.from_numpy(q).to(cdt).cuda() for q in q_h]
+        ys = batch.apply(qs)
+        gs = [2.0 * (y - torch.from_numpy(yo).to(cdt).cuda()) for y, yo in zip(ys, y_obs)]
+        gq = [t.cpu().numpy() for t in batch.apply(gs, adjoint=True)]
+        gx = [t.cpu().numpy() for t in batch.grad(qs, gs)]
+        torch.cuda.synchronize()
+        grads[prec] = (gq, gx, [g.cpu().numpy().astype(np.complex128) for g in gs])
+        batch.close()
+    gq, gx, g64 = grads[0]
+    h = 1e-6
+    for i, j, d in ((0, 5, 0), (0, 1200, 1), (2, 77, 0), (3, 0, 1)):
+        zp = xys[i].copy(); zp[j, d] += h
+        zm = xys[i].copy(); zm[j, d] -= h
+        fd = (loss_i(i, zp, q_h[i]) - loss_i(i, zm, q_h[i])) / (2 * h)
+        assert abs(fd - gx[i][j, d]) < 1e-5 * max(1.0, abs(fd)), (i, j, d, fd, gx[i][j, d])
+    for i, j in ((1, 3), (2, 2000)):
+        for part in (1.0, 1j):
+            qp = q_h[i].copy(); qp[0, j] += h * part
+            qm = q_h[i].copy(); qm[0, j] -= h * part
+            fd = (loss_i(i, xys[i], qp) - loss_i(i, xys[i], qm)) / (2 * h)
+            want = gq[i][0, j].real if part == 1.0 else gq[i][0, j].imag
+            assert abs(fd - want) < 1e-5 * max(1.0, abs(fd)), (i, j, part)
+    for i in (1, 3):
+        ref = direct.position_grad(med, xys[i], q_h[i], g64[i])
+        assert np.linalg.norm(gx[i] - ref) < 1e-8 * np.linalg.norm(ref), i
+        gq32, gx32, g32 = grads[MIXED]
+        ref32 = direct.position_grad(med, xys[i], q_h[i].astype(np.complex64).astype(np.complex128), g32[i])
+        assert np.linalg.norm(gx32[i] - ref32) < 1e-4 * np.linalg.norm(ref32), i
+        assert np.linalg.norm(gq32[i] - gq[i]) < 1e-4 * np.linalg.norm(gq[i]), i
