@@ -643,7 +643,7 @@ def run_ours(args):
     bound = "alu"
     if prec == FP64:
         peak, src = FP64_PEAK_TFLOPS, "nominal GB300 FP64 rate (MEASURED_PEAKS.json has no FP64 figure)"
-    elif dom in ("m2m", "down") and pinfo["tensor_levels"] > 0:
+    elif dom in ("m2m", "down") and pinfo["tensor_levels"] > 0 and nrhs > pinfo["small_rhs"]:
         # FP32-accurate terms as three f16 tensor-core products (hi*hi + hi*lo +
         # lo*hi, kind::f16 with FP32 accumulation): the measured bf16 burst
         # peak (f16 runs at the bf16 rate) / 3
@@ -680,9 +680,7 @@ def run_ours(args):
                          "bound": "tensor", "achieved": near_flops / (near_ms * 1e-3) / 1e12, "peak": peak,
                          "unit": "TFLOP/s", "launch_ms": near_ms, "peak_source": src}
             near_roof["frac"] = near_roof["achieved"] / near_roof["peak"]
-    medium = {0: f"impedance k={w.medium.k[0]:g} alpha={w.medium.alpha:g}",
-              1: f"two-layer k={w.medium.k[0]:g}/{w.medium.k[1]:g}",
-              2: f"three-layer k={w.medium.k[0]:g}/{w.medium.k[1]:g}/{w.medium.k[2]:g} d={w.medium.d:g}"}[w.medium.kind]
+    medium = _medium_text(w.medium)
     out = {
         "metric": _metric_name(cfg, w, n, nrhs),
         "value": value, "unit": "Mtargets/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -719,6 +717,14 @@ def run_ours(args):
 def plan_lib_apply():
     from paper_1703_09136_gb300 import library
     return library().hfmm_apply
+
+
+def _medium_text(m):
+    if m.kind == 0:
+        return f"impedance k={m.k[0]:g} alpha={m.alpha:g}"
+    if m.kind == 1:
+        return f"two-layer k={m.k[0]:g}/{m.k[1]:g}"
+    return f"three-layer k={m.k[0]:g}/{m.k[1]:g}/{m.k[2]:g} d={m.d:g}"
 
 
 def _metric_name(cfg, w, n, nrhs):

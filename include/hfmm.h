@@ -173,6 +173,9 @@ typedef struct {
                                    A_n, weighted by s(|m|) s(|p|) of the translations it feeds,
                                    or a directly summed G^s block) and its node-doubled value,
                                    relative to the entry's largest weighted value (<= 1e-12) */
+    int32_t small_rhs;          /* HFMM_MIXED: applies with nrhs <= small_rhs run on the warp-level
+                                   kernels (0 for FP64 plans) */
+    int32_t reserved2;
 } hfmm_plan_info;
 
 /* Bits of `parts` in hfmm_apply_parts (sum of the selected terms). */

@@ -63,7 +63,7 @@ class hfmm_plan_info(ctypes.Structure):
                 ("tune_levels", ctypes.c_int32 * 3), ("tune_ms", ctypes.c_double * 3),
                 ("near_tc_blocks", ctypes.c_int64), ("near_simt_leaves", ctypes.c_int64),
                 ("leaf_l2p_fused", ctypes.c_int32), ("leaf_tc_width", ctypes.c_int32),
-                ("table_check", ctypes.c_double)]
+                ("table_check", ctypes.c_double), ("small_rhs", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 hfmm_plan_t = ctypes.c_void_p

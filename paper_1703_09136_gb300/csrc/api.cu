@@ -528,6 +528,7 @@ hfmm_status hfmm_plan_get_info(hfmm_plan_t P, hfmm_plan_info* info) {
     info->leaf_tc_width = P->tc_on ? P->lev[P->L].tc_nbw : 0;
     info->near_simt_leaves = P->nt_nfallback;
     info->table_check = P->table_check;
+    info->small_rhs = P->precision == HFMM_MIXED && !(P->flags & HFMM_FLAG_SIMT_M2L) ? P->small_rhs : 0;
     return HFMM_OK;
 }
 
