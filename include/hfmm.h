@@ -121,7 +121,10 @@ typedef struct {
                                    instead of the tcgen05 tensor-core pass */
 #define HFMM_FLAG_AUTOTUNE 4    /* build the plan at the leaf levels L-1, L, L+1 around the
                                    leaf_size choice, time max_rhs-wide applies on the device
-                                   and keep the fastest (hfmm_plan_info.tune_*) */
+                                   and keep the fastest (hfmm_plan_info.tune_*); mixed plans
+                                   with tensor-core state and small_rhs = 0 then time both
+                                   engines at nrhs = 1, 2, 4, ... and set small_rhs to the
+                                   largest nrhs where the warp-level kernels are faster */
 #define HFMM_FLAG_PERSISTENT 8  /* batches: mixed-precision applies with nrhs <= small_rhs run as
                                    one persistent kernel over a device work queue (see
                                    hfmm_batch_device_error) instead of one graph branch per

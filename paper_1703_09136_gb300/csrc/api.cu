@@ -156,10 +156,12 @@ static hfmm_status validate_medium(const hfmm_medium* m) {
 static hfmm_status plan_create_one(hfmm_plan_t* out, int64_t n, const double* xy, const hfmm_medium* medium,
                                    const hfmm_options* opts, void* stream);
 
-// Time one max_rhs-wide apply of a plan (device buffers, CUDA events).
-static hfmm_status time_apply(hfmm_plan_t P, cudaStream_t st, double* ms) {
+// Time one apply of nrhs right-hand sides (max_rhs if 0) of a plan (device
+// buffers, CUDA events).
+static hfmm_status time_apply(hfmm_plan_t P, cudaStream_t st, double* ms, int nrhs = 0) {
+    if (nrhs <= 0) nrhs = P->max_rhs;
     const size_t esz = P->precision == HFMM_MIXED ? sizeof(cf) : sizeof(cd);
-    const size_t bytes = esz * (size_t)P->n * P->max_rhs;
+    const size_t bytes = esz * (size_t)P->n * nrhs;
     if (!P->io_q) HFMM_TRY(plan_alloc(P, (void**)&P->io_q, sizeof(cd) * (size_t)P->n * P->max_rhs));
     if (!P->io_y) HFMM_TRY(plan_alloc(P, (void**)&P->io_y, sizeof(cd) * (size_t)P->n * P->max_rhs));
     HFMM_CUDA_TRY(cudaMemsetAsync(P->io_q, 0, bytes, st));
@@ -170,8 +172,8 @@ static hfmm_status time_apply(hfmm_plan_t P, cudaStream_t st, double* ms) {
     for (int it = 0; it < 3 && s == HFMM_OK; ++it) {
         if (it == 1) cudaEventRecord(e0, st);
         s = P->precision == HFMM_MIXED
-                ? apply_mixed(P, P->max_rhs, (const cf*)P->io_q, (cf*)P->io_y, HFMM_PART_ALL, false, st)
-                : apply_fp64(P, P->max_rhs, P->io_q, P->io_y, HFMM_PART_ALL, false, st);
+                ? apply_mixed(P, nrhs, (const cf*)P->io_q, (cf*)P->io_y, HFMM_PART_ALL, false, st)
+                : apply_fp64(P, nrhs, P->io_q, P->io_y, HFMM_PART_ALL, false, st);
     }
     cudaEventRecord(e1, st);
     cudaEventSynchronize(e1);
@@ -225,6 +227,22 @@ hfmm_status hfmm_plan_create(hfmm_plan_t* out, int64_t n, const double* xy, cons
     }
     if (!best) { hfmm_set_error("autotune: no candidate plan could be built"); return HFMM_ERR_OOM; }
     for (int c = 0; c < 3; ++c) { best->tune_levels[c] = tried[c]; best->tune_ms[c] = times[c]; }
+    // mixed plans: the largest power-of-two nrhs up to which the warp-level
+    // engine is faster than the tensor-core passes (unless the caller fixed it)
+    if (best->precision == HFMM_MIXED && best->tc_on && opts->small_rhs == 0) {
+        int cross = 0;
+        for (int nr = 1; nr <= std::min(best->max_rhs, 32); nr *= 2) {
+            double t_small = 0.0, t_tc = 0.0;
+            best->small_rhs = nr;
+            hfmm_status s = time_apply(best, (cudaStream_t)stream, &t_small, nr);
+            best->small_rhs = 0;
+            if (s == HFMM_OK) s = time_apply(best, (cudaStream_t)stream, &t_tc, nr);
+            if (s != HFMM_OK) { hfmm_plan_destroy(best); return s; }
+            if (t_small >= t_tc) break;
+            cross = nr;
+        }
+        best->small_rhs = cross;
+    }
     best->flags |= HFMM_FLAG_AUTOTUNE;
     *out = best;
     return HFMM_OK;

@@ -662,6 +662,88 @@ __global__ void grad_combine_kernel(const cd* qs, const cd* gs_conj, const cd* u
     gxy[2 * j + 1] = ay;
 }
 
+// Near-field gradient blocks (built on a plan's first position-gradient
+// request): d/dx and d/dy of (i/4) H0(k |x_t - x_s|) at the target,
+// (i/4)(-k H1(k r)) (x_t - x_s) / r, for the same pairs and layout as the
+// near-field blocks above (0 for s = t).
+__global__ void near64_grad_fill_kernel(const int32_t* __restrict__ lb, int L, const double2* __restrict__ xs,
+                                        double k, const int64_t* __restrict__ off, cd* __restrict__ Gx,
+                                        cd* __restrict__ Gy) {
+    const int64_t b = blockIdx.x;
+    const int32_t tlo = lb[b], tn = lb[b + 1] - tlo;
+    if (tn <= 0) return;
+    const int m = 1 << L;
+    const int ix = (int)morton_x((uint32_t)b), iy = (int)morton_y((uint32_t)b);
+    int64_t j0 = 0;
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int sx = ix + dx, sy = iy + dy;
+            if (sx < 0 || sy < 0 || sx >= m || sy >= m) continue;
+            const uint32_t s = morton((uint32_t)sx, (uint32_t)sy);
+            const int32_t slo = lb[s], sn = lb[s + 1] - slo;
+            for (int e = threadIdx.x; e < sn * tn; e += blockDim.x) {
+                const int j = e / tn, i = e % tn;
+                cd gx = cmk(0.0, 0.0), gy = cmk(0.0, 0.0);
+                if (tlo + i != slo + j) {
+                    const double2 a = xs[tlo + i], c = xs[slo + j];
+                    const double ddx = a.x - c.x, ddy = a.y - c.y;
+                    const double r = hypot(ddx, ddy);
+                    cd h0, h1;
+                    hankel01(k * r, &h0, &h1);
+                    const cd cc = cscale(cmuli(h1), -0.25 * k / r);
+                    gx = cscale(cc, ddx);
+                    gy = cscale(cc, ddy);
+                }
+                const int64_t o = off[b] + (j0 + j) * tn + i;
+                Gx[o] = gx;
+                Gy[o] = gy;
+            }
+            j0 += sn;
+        }
+}
+
+// fx[r][t] += sum_s Gx[s][t] v[r][s], fy likewise: a warp per target leaf.
+__global__ void __launch_bounds__(128) near64_grad_kernel(const int32_t* __restrict__ lb, int L, int64_t nleaf,
+                                                          const int64_t* __restrict__ off, const cd* __restrict__ Gx,
+                                                          const cd* __restrict__ Gy, const cd* __restrict__ qs,
+                                                          int64_t n, int nrhs, cd* __restrict__ fx,
+                                                          cd* __restrict__ fy) {
+    const int64_t b = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (b >= nleaf) return;
+    const int lane = threadIdx.x & 31;
+    const int32_t tlo = lb[b], tn = lb[b + 1] - tlo;
+    if (tn <= 0) return;
+    const int m = 1 << L;
+    const int ix = (int)morton_x((uint32_t)b), iy = (int)morton_y((uint32_t)b);
+    for (int r = 0; r < nrhs; ++r)
+        for (int i0 = 0; i0 < tn; i0 += 32) {
+            const int i = i0 + lane;
+            const bool live = i < tn;
+            cd ax = cmk(0.0, 0.0), ay = cmk(0.0, 0.0);
+            int64_t j = 0;
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int sx = ix + dx, sy = iy + dy;
+                    if (sx < 0 || sy < 0 || sx >= m || sy >= m) continue;
+                    const uint32_t s = morton((uint32_t)sx, (uint32_t)sy);
+                    const int32_t slo = lb[s], shi = lb[s + 1];
+                    const cd* qr = qs + (int64_t)r * n;
+                    for (int32_t js = slo; js < shi; ++js, ++j)
+                        if (live) {
+                            const cd v = qr[js];
+                            const int64_t o = off[b] + j * tn + i;
+                            cfma(ax, Gx[o], v);
+                            cfma(ay, Gy[o], v);
+                        }
+                }
+            if (live) {
+                const int64_t o = (int64_t)r * n + tlo + i;
+                fx[o] = cadd(fx[o], ax);
+                fy[o] = cadd(fy[o], ay);
+            }
+        }
+}
+
 int pick_chunk_grad(int p) {
     const int nc = 2 * p + 1;
     int c = (int)(40000 / ((3 * nc + 2) * 16 + (p + 2) * 8));
@@ -706,8 +788,12 @@ hfmm_status field_grad_fp64(hfmm_plan_s* P, int nrhs, cd* fx, cd* fy, cudaStream
                                                           P->y0, lv.h, P->k, lv.p, chunk, fx, fy);
         HFMM_CUDA_TRY(cudaGetLastError());
     }
-    p2p_grad_kernel<<<(unsigned)P->lev[L].nbox, 256, 0, st>>>(P->leaf_begin, L, P->xy_sorted, P->q_sorted, n, nrhs,
-                                                              P->k, fx, fy);
+    if (P->near64g_x)
+        near64_grad_kernel<<<(unsigned)ceil_div(P->lev[L].nbox, 4), 128, 0, st>>>(
+            P->leaf_begin, L, P->lev[L].nbox, P->near64_off, P->near64g_x, P->near64g_y, P->q_sorted, n, nrhs, fx, fy);
+    else
+        p2p_grad_kernel<<<(unsigned)P->lev[L].nbox, 256, 0, st>>>(P->leaf_begin, L, P->xy_sorted, P->q_sorted, n,
+                                                                  nrhs, P->k, fx, fy);
     HFMM_CUDA_TRY(cudaGetLastError());
     if (P->nd > 0) {
         direct_grad_kernel<<<(unsigned)P->lev[L].nbox, TB, 0, st>>>(P->leaf_begin, P->d_begin, P->d_src, P->d_blk,
@@ -727,6 +813,7 @@ hfmm_status apply_grad_fp64(hfmm_plan_s* P, int nrhs, const cd* q, const cd* g, 
     if (!P->grad_buf) {
         HFMM_TRY(plan_alloc(P, (void**)&P->grad_buf, 5 * bytes));
         HFMM_TRY(build_direct_grad(P, st));
+        HFMM_TRY(build_near64_grad(P, st));
     }
     cd* ux = P->grad_buf;
     cd* uy = ux + (size_t)n * P->max_rhs;
@@ -746,6 +833,54 @@ hfmm_status apply_grad_fp64(hfmm_plan_s* P, int nrhs, const cd* q, const cd* g, 
     // sorted q again for the combination
     gather_q<<<nb, 256, 0, st>>>(q, P->perm, n, nrhs, false, P->q_sorted);
     grad_combine_kernel<<<nb, 256, 0, st>>>(P->q_sorted, gsc, ux, uy, wx, wy, P->perm, n, nrhs, gxy);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    return HFMM_OK;
+}
+
+// Offsets of the near-field blocks (every target leaf's U-list pairs) on
+// the device, once per plan; returns the number of pairs in *pairs.
+static hfmm_status near64_offsets(hfmm_plan_s* P, int64_t* pairs, bool alloc, cudaStream_t st) {
+    const int L = P->L;
+    const int64_t nleaf = P->lev[L].nbox;
+    const auto& lb = P->h_leaf_begin;
+    const int m = 1 << L;
+    std::vector<int64_t> off(nleaf + 1, 0);
+    for (int64_t b = 0; b < nleaf; ++b) {
+        const int64_t tn = lb[b + 1] - lb[b];
+        int64_t ns = 0;
+        if (tn > 0) {
+            const int ix = (int)morton_x((uint32_t)b), iy = (int)morton_y((uint32_t)b);
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int sx = ix + dx, sy = iy + dy;
+                    if (sx < 0 || sy < 0 || sx >= m || sy >= m) continue;
+                    const uint32_t s = morton((uint32_t)sx, (uint32_t)sy);
+                    ns += lb[s + 1] - lb[s];
+                }
+        }
+        off[b + 1] = off[b] + tn * ns;
+    }
+    *pairs = off[nleaf];
+    if (alloc && !P->near64_off) {
+        HFMM_TRY(plan_alloc(P, (void**)&P->near64_off, sizeof(int64_t) * (nleaf + 1)));
+        HFMM_CUDA_TRY(cudaMemcpyAsync(P->near64_off, off.data(), sizeof(int64_t) * (nleaf + 1),
+                                      cudaMemcpyHostToDevice, st));
+        HFMM_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return HFMM_OK;
+}
+
+// Near-field gradient blocks, on a plan's first position-gradient request
+// (skipped above the byte budget: the gradient then evaluates H1 per pair).
+hfmm_status build_near64_grad(hfmm_plan_s* P, cudaStream_t st) {
+    int64_t pairs = 0;
+    HFMM_TRY(near64_offsets(P, &pairs, false, st));
+    if (32.0 * (double)pairs > NEAR64_MAX_BYTES) return HFMM_OK;
+    HFMM_TRY(near64_offsets(P, &pairs, true, st));
+    HFMM_TRY(plan_alloc(P, (void**)&P->near64g_x, sizeof(cd) * std::max<int64_t>(pairs, 1)));
+    HFMM_TRY(plan_alloc(P, (void**)&P->near64g_y, sizeof(cd) * std::max<int64_t>(pairs, 1)));
+    near64_grad_fill_kernel<<<(unsigned)P->lev[P->L].nbox, 128, 0, st>>>(P->leaf_begin, P->L, P->xy_sorted, P->k,
+                                                                          P->near64_off, P->near64g_x, P->near64g_y);
     HFMM_CUDA_TRY(cudaGetLastError());
     return HFMM_OK;
 }

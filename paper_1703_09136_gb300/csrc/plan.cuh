@@ -165,6 +165,8 @@ struct hfmm_plan_s {
     // at plan time (fmm64.cu), and their offsets per leaf; null above the budget
     int64_t* near64_off = nullptr;
     cd* near64_vals = nullptr;
+    cd* near64g_x = nullptr;        // d/dx, d/dy of the same blocks (first gradient request)
+    cd* near64g_y = nullptr;
     cd* grad_buf = nullptr;         // [5][max_rhs][n]
     cd* grad_q = nullptr;           // mixed plans: widened strengths / loss gradient
     cd* grad_g = nullptr;
@@ -245,6 +247,7 @@ hfmm_status apply_grad_fp64(hfmm_plan_s* P, int nrhs, const cd* q, const cd* g, 
 // fmm64.cu
 constexpr double NEAR64_MAX_BYTES = 32e9;   // plan-time FP64 near-field blocks up to this size
 hfmm_status build_near64(hfmm_plan_s* P, cudaStream_t st);
+hfmm_status build_near64_grad(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status apply_fp64(hfmm_plan_s* P, int nrhs, const cd* q, cd* y, int parts, bool adjoint,
                        cudaStream_t st);
 // fmm32.cu

@@ -277,9 +277,13 @@ __global__ void __launch_bounds__(128) near_small_kernel(const int32_t* __restri
     if (thi <= tlo) return;
     const int ix = (int)morton_x((uint32_t)b), iy = (int)morton_y((uint32_t)b);
     const int mside = 1 << L;
+    // leaves of at most 16 points: the two half-warps take alternate sources
+    // (and alternate L2P coefficients) of the same 16 targets, then add
+    const bool split = thi - tlo <= 16;
+    const int half = split ? lane >> 4 : 0, nper = split ? 2 : 4, mstep = split ? 2 : 1;
     for (int r0 = 0; r0 < nrhs; r0 += R) {
         for (int32_t t0 = tlo; t0 < thi; t0 += 32) {
-            const int32_t t = t0 + lane;
+            const int32_t t = t0 + (split ? lane & 15 : lane);
             const bool live = t < thi;
             const float2 tp = live ? xl[t] : make_float2(0.f, 0.f);
             cf acc[R];
@@ -293,20 +297,23 @@ __global__ void __launch_bounds__(128) near_small_kernel(const int32_t* __restri
                     const int32_t slo = lb[s], shi = lb[s + 1];
                     const float ox = (float)(-dx) * h, oy = (float)(-dy) * h;   // c_T - c_S
                     for (int32_t j0 = slo; j0 < shi; j0 += 4) {
-                        // positions and strengths of up to four sources, loaded before use
+                        // positions and strengths of up to four sources (two per
+                        // half-warp when split), loaded before use
                         float2 sp[4];
                         cf qv[4][R];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
-                            const bool ok = j0 + i < shi;
-                            sp[i] = ok ? xl[j0 + i] : make_float2(0.f, 0.f);
+                            const int32_t j = j0 + (split ? 2 * i + half : i);
+                            const bool ok = i < nper && j < shi;
+                            sp[i] = ok ? xl[j] : make_float2(0.f, 0.f);
 #pragma unroll
                             for (int r = 0; r < R; ++r)
-                                qv[i][r] = (ok && r0 + r < nrhs) ? qs[(int64_t)(j0 + i) * nrhs + r0 + r] : cfmk(0.f, 0.f);
+                                qv[i][r] = (ok && r0 + r < nrhs) ? qs[(int64_t)j * nrhs + r0 + r] : cfmk(0.f, 0.f);
                         }
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
-                            const int32_t j = j0 + i;
+                            if (i >= nper) break;
+                            const int32_t j = j0 + (split ? 2 * i + half : i);
                             cf g = cfmk(0.f, 0.f);
                             if (live && j < shi && t != j) {
                                 const float ddx = ox + (tp.x - sp[i].x), ddy = oy + (tp.y - sp[i].y);
@@ -325,7 +332,7 @@ __global__ void __launch_bounds__(128) near_small_kernel(const int32_t* __restri
                 }
             if (loc) {
                 // L2P: (i/4) sum_m b~[r][m] conj(B[t][m])
-                for (int m = 0; m < nc; ++m) {
+                for (int m = half; m < nc; m += mstep) {
                     const cf B = live ? basis[(int64_t)t * nc + m] : cfmk(0.f, 0.f);
                     const cf g = cfmk(0.25f * B.y, 0.25f * B.x);
 #pragma unroll
@@ -335,7 +342,14 @@ __global__ void __launch_bounds__(128) near_small_kernel(const int32_t* __restri
                     }
                 }
             }
-            if (live)
+            if (split) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, 16);
+                    acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, 16);
+                }
+            }
+            if (live && lane < (split ? 16 : 32))
 #pragma unroll
                 for (int r = 0; r < R; ++r)
                     if (r0 + r < nrhs) {

@@ -882,3 +882,21 @@ def test_batch_gradients_at_the_uneven_batch_spec():
         ref32 = direct.position_grad(med, xys[i], q_h[i].astype(np.complex64).astype(np.complex128), g32[i])
         assert np.linalg.norm(gx32[i] - ref32) < 1e-4 * np.linalg.norm(ref32), i
         assert np.linalg.norm(gq32[i] - gq[i]) < 1e-4 * np.linalg.norm(gq[i]), i
+
+
+def test_autotune_picks_the_engine_crossover_for_mixed_plans():
+    """A mixed autotuned plan also times the warp-level and the tensor-core
+    engines at nrhs = 1, 2, 4, ... and keeps the crossover as small_rhs; its
+    applies stay within the mixed bound of FP64 on both sides of it."""
+    from paper_1703_09136_gb300 import MIXED
+    xy = W.points_in_box(4, 30000, ((0.0, 2.0), (0.02, 2.02)), salt=3)
+    tuned = Plan(xy, CFG4_MED, tol=1e-6, leaf_size=16, max_rhs=16, precision=MIXED, autotune=True)
+    inf = tuned.info
+    assert inf["small_rhs"] in (0, 1, 2, 4, 8, 16), inf["small_rhs"]
+    f64 = Plan(xy, CFG4_MED, tol=1e-6, levels=inf["levels"], max_rhs=16)
+    for nrhs in (1, 16):
+        q = W.strengths(4, 30000, nrhs, salt=nrhs)
+        y = tuned.apply(torch.from_numpy(q.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
+        y64 = f64.apply(torch.from_numpy(q).cuda()).cpu().numpy()
+        assert direct.rel_l2(y, y64) < MIXED_TOL, (nrhs, direct.rel_l2(y, y64))
+    tuned.close(); f64.close()
