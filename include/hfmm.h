@@ -367,6 +367,30 @@ hfmm_status hfmm_plan_get_stage_times(hfmm_plan_t plan, double* ms);
 hfmm_status hfmm_leaf_order_noalloc(int64_t n, const double* xy, int32_t levels, int64_t* perm,
                                     int32_t* leaf_begin, void* stream);
 
+/*
+ * Solve (sigma I + A) x = b for one right-hand side by restarted GMRES, with
+ * A_ij = u_{x_j}(x_i) the plan's matrix (Sec. 2.4: the discretised layer or
+ * volume potential of a second-kind integral equation).  Each iteration is
+ * one apply of the plan plus Krylov updates on the device (dot products
+ * accumulated in FP64); the Hessenberg least-squares problem is solved on the
+ * host, so every iteration synchronises `stream`.
+ *   sigma    host pointer to (re, im) of the shift;
+ *   b, x     device buffers of n complex values (complex128 for HFMM_FP64,
+ *            complex64 for HFMM_MIXED) in the caller's point order; x holds
+ *            the initial guess on entry and the solution on return;
+ *   tol      relative residual ||b - (sigma I + A) x|| / ||b|| to reach (the
+ *            mixed path's apply carries ~1e-6 relative error: ask >= 1e-5);
+ *   restart  Krylov dimension between restarts (1..1000), maxit the total
+ *            number of applies; *iters, *relres report them (the true
+ *            residual of the returned x).
+ * Returns HFMM_ERR_NUMERICS (x still holds the last iterate) when tol was not
+ * reached, HFMM_ERR_INVALID_ARG for host buffers or bad parameters.  The
+ * first call allocates (restart + 2) n complex values of Krylov vectors,
+ * held by the plan.
+ */
+hfmm_status hfmm_solve(hfmm_plan_t plan, const double* sigma, const void* b, void* x, double tol, int32_t restart,
+                       int32_t maxit, int32_t* iters, double* relres, void* stream);
+
 /* Release the plan (NULL is accepted).  Synchronises the device. */
 hfmm_status hfmm_plan_destroy(hfmm_plan_t plan);
 

@@ -213,6 +213,21 @@ class Plan:
         _n.check(_n.lib().hfmm_apply_grad(self._h, ctypes.c_int32(nrhs), qp, gp, op, _stream_handle(stream)))
         return out
 
+    def solve(self, b, sigma=1.0, x0=None, tol=1e-8, restart=50, maxit=1000, stream=None):
+        """x with (sigma I + A) x = b by restarted GMRES (hfmm_solve); b a
+        device tensor of n complex values.  Returns (x, iterations, relative
+        residual); raises HfmmError (HFMM_ERR_NUMERICS) if tol is not reached."""
+        torch = _torch()
+        b = b.contiguous().reshape(-1)
+        x = torch.zeros_like(b) if x0 is None else x0.clone().contiguous().reshape(-1)
+        sg = (ctypes.c_double * 2)(complex(sigma).real, complex(sigma).imag)
+        it = ctypes.c_int32(0)
+        rr = ctypes.c_double(0.0)
+        _n.check(_n.lib().hfmm_solve(self._h, sg, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                     ctypes.c_double(tol), ctypes.c_int32(restart), ctypes.c_int32(maxit),
+                                     ctypes.byref(it), ctypes.byref(rr), _stream_handle(stream)))
+        return x, int(it.value), float(rr.value)
+
     # ------------------------------------------------------------------
     @property
     def info(self):

@@ -22,7 +22,7 @@ EXPORTS = ["hfmm_options_default", "hfmm_plan_create", "hfmm_apply", "hfmm_apply
            "hfmm_debug_bessel", "hfmm_plan_get_stage_times", "hfmm_debug_green_f32",
            "hfmm_leaf_order_noalloc", "hfmm_apply_grad", "hfmm_batch_create", "hfmm_batch_apply",
            "hfmm_batch_get_plan", "hfmm_batch_destroy", "hfmm_debug_wait_timeout", "hfmm_plan_get_leaf_down",
-           "hfmm_batch_device_error", "hfmm_batch_apply_grad"]
+           "hfmm_batch_device_error", "hfmm_batch_apply_grad", "hfmm_solve"]
 NUM_STAGES = 8
 STAGES = ["gather", "p2m", "m2m", "down", "l2p", "p2p", "direct", "scatter"]
 FLAG_PROFILE = 1
@@ -104,13 +104,14 @@ def lib():
         L.hfmm_plan_get_leaf_down.argtypes = [hfmm_plan_t, vp, vp]
         L.hfmm_batch_device_error.argtypes = [vp, vp]
         L.hfmm_batch_apply_grad.argtypes = [vp, i32, vp, vp, vp, vp]
+        L.hfmm_solve.argtypes = [hfmm_plan_t, vp, vp, vp, dbl, i32, i32, vp, vp, vp]
         for name in ("hfmm_plan_create", "hfmm_apply", "hfmm_apply_parts", "hfmm_apply_adjoint",
                      "hfmm_plan_get_info", "hfmm_plan_get_tree", "hfmm_plan_get_pairs",
                      "hfmm_plan_destroy", "hfmm_debug_bessel", "hfmm_plan_get_stage_times",
                      "hfmm_debug_green_f32", "hfmm_leaf_order_noalloc", "hfmm_apply_grad",
                      "hfmm_batch_create", "hfmm_batch_apply", "hfmm_batch_get_plan", "hfmm_batch_destroy",
                      "hfmm_debug_wait_timeout", "hfmm_plan_get_leaf_down", "hfmm_batch_device_error",
-                     "hfmm_batch_apply_grad"):
+                     "hfmm_batch_apply_grad", "hfmm_solve"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib

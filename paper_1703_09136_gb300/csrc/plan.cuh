@@ -165,6 +165,9 @@ struct hfmm_plan_s {
     // at plan time (fmm64.cu), and their offsets per leaf; null above the budget
     int64_t* near64_off = nullptr;
     cd* near64_vals = nullptr;
+    void* krylov = nullptr;         // hfmm_solve: Krylov vectors (first call; grows with restart)
+    size_t krylov_bytes = 0;
+    double* krylov_part = nullptr;  // partial sums of its dot products
     cd* near64g_x = nullptr;        // d/dx, d/dy of the same blocks (first gradient request)
     cd* near64g_y = nullptr;
     cd* grad_buf = nullptr;         // [5][max_rhs][n]
