@@ -381,11 +381,22 @@ def measure_two_layer(dev, steps, cpu=True):
     ms_fp64 = _events_ms(lambda: p64.apply(q64, out=y64), 3)
     p64.apply(q64, out=y64)
     err = float(torch.linalg.norm(y_mixed - y64) / torch.linalg.norm(y64))
+    diag = {"levels": [l for l in range(32) if p64.info["diag_levels"] >> l & 1],
+            "check": p64.info["diag_check"]}
     p64.close()
+    # the same FP64 apply with every level's translations dense
+    pd = Plan(xy, w.medium, tol=w.tol, leaf_size=w.leaf, precision=FP64, max_rhs=1, dense_m2l=True)
+    yd = torch.empty_like(q64)
+    ms_dense = _events_ms(lambda: pd.apply(q64, out=yd), 3)
+    pd.apply(q64, out=yd)
+    diag["fp64_dense_ms_per_apply"] = ms_dense
+    diag["rel_l2_vs_dense"] = float(torch.linalg.norm(yd - y64) / torch.linalg.norm(yd))
+    pd.close()
     stages, roof = _dominant_roofline(Plan, xy, w, MIXED, 1, q32)
     out = {"workload": w.name, "n": w.n, "nrhs": 1, "tol": w.tol, "medium": "two-layer k=60/90",
            "metric": "Mtargets/s (N x nrhs / apply time)", "value": w.n / (ms_mixed * 1e-3) / 1e6,
            "ms_per_apply": ms_mixed, "fp64_ms_per_apply": ms_fp64, "mixed_speedup_vs_fp64": ms_fp64 / ms_mixed,
+           "fp64_diagonal_m2l": diag,
            "rel_l2_mixed_vs_fp64": err, "adjoint_ms": adj_ms, "plan_s": plan_s, "gpu_launches": launches,
            "engine": "few-RHS warp-level kernels (small_rhs default 4)", "stage_ms": stages, "roofline": roof,
            "e2e": {"value": w.n / e2e_s / 1e6, "unit": "Mtargets/s", "h2d_bytes_per_step": 8 * w.n,

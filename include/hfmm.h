@@ -129,6 +129,16 @@ typedef struct {
                                    one persistent kernel over a device work queue (see
                                    hfmm_batch_device_error) instead of one graph branch per
                                    instance */
+#define HFMM_FLAG_DENSE_M2L 16  /* HFMM_FP64: keep the dense (2p+1)^2 translations on every level.
+                                   Without it the plan tries the diagonal form of the free and
+                                   reaction translations (their matrices depend on m - p only,
+                                   Sec. 3.3, so a circulant embedding of length Q >= 4p + 1 makes
+                                   each translation an O(Q) pointwise product between one FFT per
+                                   source box and one inverse FFT per target box) on each level
+                                   and keeps it where it reproduces the dense product on random
+                                   expansions to 1e-12 (weighted as in table_check); that holds
+                                   only on levels whose boxes are large against the wavelength
+                                   (hfmm_plan_info.diag_levels) */
 
 /* Stages reported by hfmm_plan_get_stage_times (milliseconds of the last apply). */
 #define HFMM_STAGE_GATHER   0   /* caller order -> leaf order */
@@ -178,7 +188,9 @@ typedef struct {
                                    relative to the entry's largest weighted value (<= 1e-12) */
     int32_t small_rhs;          /* HFMM_MIXED: applies with nrhs <= small_rhs run on the warp-level
                                    kernels (0 for FP64 plans) */
-    int32_t reserved2;
+    int32_t diag_levels;        /* HFMM_FP64: bit l set if level l translates in diagonal form
+                                   (see HFMM_FLAG_DENSE_M2L) */
+    double diag_check;          /* largest plan-time difference of a level kept in diagonal form */
 } hfmm_plan_info;
 
 /* Bits of `parts` in hfmm_apply_parts (sum of the selected terms). */

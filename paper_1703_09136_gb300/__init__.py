@@ -105,7 +105,7 @@ class Plan:
 
     def __init__(self, xy, medium, tol=1e-6, p=0, leaf_size=32, levels=0, precision=FP64,
                  max_rhs=1, stream=None, profile=False, simt_m2l=False, autotune=False, spin_limit=0,
-                 quad_scale=0.0, small_rhs=0):
+                 quad_scale=0.0, small_rhs=0, dense_m2l=False):
         lib = _n.lib()
         m = Medium.of(medium)
         opts = _n.hfmm_options()
@@ -117,7 +117,7 @@ class Plan:
         opts.precision = int(precision)
         opts.max_rhs = int(max_rhs)
         opts.flags = ((_n.FLAG_PROFILE if profile else 0) | (_n.FLAG_SIMT_M2L if simt_m2l else 0) |
-                      (_n.FLAG_AUTOTUNE if autotune else 0))
+                      (_n.FLAG_AUTOTUNE if autotune else 0) | (_n.FLAG_DENSE_M2L if dense_m2l else 0))
         opts.spin_limit = int(spin_limit)
         opts.quad_scale = float(quad_scale)
         opts.small_rhs = int(small_rhs)

@@ -29,6 +29,7 @@ FLAG_PROFILE = 1
 FLAG_SIMT_M2L = 2
 FLAG_AUTOTUNE = 4
 FLAG_PERSISTENT = 8
+FLAG_DENSE_M2L = 16
 
 
 class HfmmError(RuntimeError):
@@ -63,7 +64,8 @@ class hfmm_plan_info(ctypes.Structure):
                 ("tune_levels", ctypes.c_int32 * 3), ("tune_ms", ctypes.c_double * 3),
                 ("near_tc_blocks", ctypes.c_int64), ("near_simt_leaves", ctypes.c_int64),
                 ("leaf_l2p_fused", ctypes.c_int32), ("leaf_tc_width", ctypes.c_int32),
-                ("table_check", ctypes.c_double), ("small_rhs", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("table_check", ctypes.c_double), ("small_rhs", ctypes.c_int32), ("diag_levels", ctypes.c_int32),
+                ("diag_check", ctypes.c_double)]
 
 
 hfmm_plan_t = ctypes.c_void_p

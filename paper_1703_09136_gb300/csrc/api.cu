@@ -335,6 +335,7 @@ static hfmm_status plan_create_one(hfmm_plan_t* out, int64_t n, const double* xy
         P->buffer_bytes += 2.0 * esz * n * o.max_rhs;
         if ((s = build_tables(P, st)) != HFMM_OK) break;
         if (!mixed && (s = build_near64(P, st)) != HFMM_OK) break;
+        if (!mixed && (s = build_diag(P, st)) != HFMM_OK) break;
         if (mixed) {
             if ((s = build_tables32(P, st)) != HFMM_OK) break;
             if ((s = init_h0_table(st)) != HFMM_OK) break;
@@ -547,6 +548,8 @@ hfmm_status hfmm_plan_get_info(hfmm_plan_t P, hfmm_plan_info* info) {
     info->near_simt_leaves = P->nt_nfallback;
     info->table_check = P->table_check;
     info->small_rhs = P->precision == HFMM_MIXED && !(P->flags & HFMM_FLAG_SIMT_M2L) ? P->small_rhs : 0;
+    info->diag_levels = P->diag_levels;
+    info->diag_check = P->diag_check;
     return HFMM_OK;
 }
 

@@ -366,6 +366,18 @@ int pick_chunk(int p) {
 
 }  // namespace
 
+// Dense free + reaction translations of level l alone (no L2L) from mult into
+// loc (used by the plan-time check of the diagonal form).
+hfmm_status down64_lists(hfmm_plan_s* P, int l, int nrhs, const cd* mult, cd* loc, cudaStream_t st) {
+    LevelInfo& lv = P->lev[l];
+    downward_kernel<<<(unsigned)lv.nbox, TB, 0, st>>>(P->leaf_begin, P->L, l, l, nrhs, lv.p, 0, nullptr, nullptr, mult,
+                                                     lv.nv ? lv.v_begin : nullptr, lv.v_src, lv.v_off, lv.t_free,
+                                                     lv.nr ? lv.r_begin : nullptr, lv.r_src, lv.r_tab, lv.t_react,
+                                                     HFMM_PART_ALL, loc);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    return HFMM_OK;
+}
+
 hfmm_status apply_fp64(hfmm_plan_s* P, int nrhs, const cd* q, cd* y, int parts, bool adjoint,
                        cudaStream_t st) {
     const int64_t n = P->n;
@@ -394,6 +406,7 @@ hfmm_status apply_fp64(hfmm_plan_s* P, int nrhs, const cd* q, cd* y, int parts, 
                                                          P->x0, P->y0, lv.h, L, P->k, lv.p, chunk, lv.mult);
             ++P->launches;
             HFMM_CUDA_TRY(cudaGetLastError());
+            if (lv.diag_logq) HFMM_TRY(diag_src(P, L, nrhs, st));
             tm.end(HFMM_STAGE_P2M);
             P->st_flops[HFMM_STAGE_P2M] = MAC * n * lv.ncoef;
             P->st_bytes[HFMM_STAGE_P2M] = C * n + 16.0 * n + C * lv.nbox * lv.ncoef;
@@ -405,6 +418,7 @@ hfmm_status apply_fp64(hfmm_plan_s* P, int nrhs, const cd* q, cd* y, int parts, 
                                                         nrhs, lv.mult);
             ++P->launches;
             HFMM_CUDA_TRY(cudaGetLastError());
+            if (lv.diag_logq) HFMM_TRY(diag_src(P, l, nrhs, st));
             P->st_flops[HFMM_STAGE_M2M] += MAC * 4.0 * lv.nbox * lv.ncoef * P->lev[l + 1].ncoef;
             P->st_bytes[HFMM_STAGE_M2M] += C * (4.0 * lv.nbox * P->lev[l + 1].ncoef + lv.nbox * lv.ncoef);
         }
@@ -414,17 +428,20 @@ hfmm_status apply_fp64(hfmm_plan_s* P, int nrhs, const cd* q, cd* y, int parts, 
         for (int l = P->lmin; l <= L; ++l) {
             LevelInfo& lv = P->lev[l];
             const bool has_parent = l > P->lmin;
+            const bool dg = lv.diag_logq > 0;   // translations in diagonal form after the L2L
             downward_kernel<<<(unsigned)lv.nbox, TB, 0, st>>>(
                 P->leaf_begin, L, l, P->lmin, nrhs, lv.p, has_parent ? P->lev[l - 1].p : 0,
                 has_parent ? P->lev[l - 1].loc : nullptr, has_parent ? P->lev[l - 1].t_l2l : nullptr,
-                lv.mult, lv.nv ? lv.v_begin : nullptr, lv.v_src, lv.v_off, lv.t_free,
-                lv.nr ? lv.r_begin : nullptr, lv.r_src, lv.r_tab, lv.t_react, parts, lv.loc);
+                lv.mult, lv.nv && !dg ? lv.v_begin : nullptr, lv.v_src, lv.v_off, lv.t_free,
+                lv.nr && !dg ? lv.r_begin : nullptr, lv.r_src, lv.r_tab, lv.t_react, parts, lv.loc);
             ++P->launches;
             HFMM_CUDA_TRY(cudaGetLastError());
+            if (dg) HFMM_TRY(diag_m2l(P, l, nrhs, parts, st));
             double pairs = 0.0;
             if (parts & HFMM_PART_FAR_FREE) pairs += (double)lv.nv;
             if (parts & HFMM_PART_FAR_REACT) pairs += (double)lv.nr;
-            P->st_flops[HFMM_STAGE_DOWN] += MAC * pairs * lv.ncoef * lv.ncoef;
+            if (dg) P->st_flops[HFMM_STAGE_DOWN] += diag_flops(P, l, nrhs, parts);
+            else P->st_flops[HFMM_STAGE_DOWN] += MAC * pairs * lv.ncoef * lv.ncoef;
             if (has_parent) P->st_flops[HFMM_STAGE_DOWN] += MAC * lv.nbox * lv.ncoef * P->lev[l - 1].ncoef;
             P->st_bytes[HFMM_STAGE_DOWN] += C * lv.nbox * lv.ncoef * 2.0 +
                                             (has_parent ? C * P->lev[l - 1].nbox * P->lev[l - 1].ncoef : 0.0);
@@ -763,21 +780,25 @@ hfmm_status field_grad_fp64(hfmm_plan_s* P, int nrhs, cd* fx, cd* fy, cudaStream
         p2m_kernel<<<(unsigned)lv.nbox, TB, sm, st>>>(P->leaf_begin, P->xy_sorted, P->q_sorted, n, nrhs, P->x0,
                                                      P->y0, lv.h, L, P->k, lv.p, chunk, lv.mult);
         HFMM_CUDA_TRY(cudaGetLastError());
+        if (lv.diag_logq) HFMM_TRY(diag_src(P, L, nrhs, st));
     }
     for (int l = L - 1; l >= P->lmin; --l) {
         LevelInfo& lv = P->lev[l];
         m2m_kernel<<<(unsigned)lv.nbox, TB, 0, st>>>(P->lev[l + 1].mult, lv.t_m2m, P->lev[l + 1].p, lv.p, nrhs, lv.mult);
         HFMM_CUDA_TRY(cudaGetLastError());
+        if (lv.diag_logq) HFMM_TRY(diag_src(P, l, nrhs, st));
     }
     for (int l = P->lmin; l <= L; ++l) {
         LevelInfo& lv = P->lev[l];
         const bool has_parent = l > P->lmin;
+        const bool dg = lv.diag_logq > 0;
         downward_kernel<<<(unsigned)lv.nbox, TB, 0, st>>>(
             P->leaf_begin, L, l, P->lmin, nrhs, lv.p, has_parent ? P->lev[l - 1].p : 0,
             has_parent ? P->lev[l - 1].loc : nullptr, has_parent ? P->lev[l - 1].t_l2l : nullptr, lv.mult,
-            lv.nv ? lv.v_begin : nullptr, lv.v_src, lv.v_off, lv.t_free, lv.nr ? lv.r_begin : nullptr, lv.r_src,
-            lv.r_tab, lv.t_react, HFMM_PART_ALL, lv.loc);
+            lv.nv && !dg ? lv.v_begin : nullptr, lv.v_src, lv.v_off, lv.t_free, lv.nr && !dg ? lv.r_begin : nullptr,
+            lv.r_src, lv.r_tab, lv.t_react, HFMM_PART_ALL, lv.loc);
         HFMM_CUDA_TRY(cudaGetLastError());
+        if (dg) HFMM_TRY(diag_m2l(P, l, nrhs, HFMM_PART_ALL, st));
     }
     {
         LevelInfo& lv = P->lev[L];

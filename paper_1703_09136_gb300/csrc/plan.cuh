@@ -82,7 +82,22 @@ struct LevelInfo {
     float* tc_asc = nullptr;
     __half* tc_pmma = nullptr;    // local expansions of the parent level
     float* tc_psc = nullptr;
+    // diagonal form of the FP64 translations (diag.cu): circulant length 2^diag_logq
+    // (0: dense), twiddles, spectra of the free / reaction table rows, spectra of
+    // the level's multipoles [nbox][max_rhs][Q], and the plan-time check's result
+    int diag_logq = 0;
+    cd* diag_tw = nullptr;
+    cd* diag_ofree = nullptr;
+    cd* diag_oreact = nullptr;
+    cd* diag_spec = nullptr;
+    double diag_err = -1.0;
+    int64_t nonempty = 0;         // non-empty boxes (set by the diagonal-form check)
 };
+
+// Diagonal form: kept on a level when its weighted difference to the dense
+// product on random expansions is at most DIAG_RTOL; spectra capped per level.
+constexpr double DIAG_RTOL = 1e-12;
+constexpr size_t DIAG_MAX_BYTES = (size_t)8 << 30;
 
 // Power-of-two scale of the stored near-field Green's function tiles (f16).
 constexpr int NT_GSCALE_EXP = 10;
@@ -197,6 +212,8 @@ struct hfmm_plan_s {
     int small_rhs = 0;              // HFMM_MIXED: applies with nrhs <= small_rhs run on small.cu
     double table_check = 0.0;
     int table_check_where[3] = {0, 0, 0};
+    int diag_levels = 0;            // bit l: level l translates in diagonal form (diag.cu)
+    double diag_check = 0.0;        // largest plan-time difference of a kept level
 
     // info
     int64_t u_pairs = 0;
@@ -250,6 +267,10 @@ hfmm_status apply_grad_fp64(hfmm_plan_s* P, int nrhs, const cd* q, const cd* g, 
 // fmm64.cu
 constexpr double NEAR64_MAX_BYTES = 32e9;   // plan-time FP64 near-field blocks up to this size
 hfmm_status build_near64(hfmm_plan_s* P, cudaStream_t st);
+hfmm_status build_diag(hfmm_plan_s* P, cudaStream_t st);
+hfmm_status diag_src(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st);
+hfmm_status diag_m2l(hfmm_plan_s* P, int l, int nrhs, int parts, cudaStream_t st);
+double diag_flops(const hfmm_plan_s* P, int l, int nrhs, int parts);
 hfmm_status build_near64_grad(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status apply_fp64(hfmm_plan_s* P, int nrhs, const cd* q, cd* y, int parts, bool adjoint,
                        cudaStream_t st);

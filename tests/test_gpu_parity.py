@@ -928,3 +928,61 @@ def test_gmres_solve_matches_dense_oracle_solve(sigma):
         p64.solve(torch.from_numpy(b).cuda(), sigma=sigma, tol=1e-12, restart=5, maxit=5)
     assert e.value.status == 5
     p64.close(); p32.close()
+
+
+# ---------------------------------------------------------------------------
+# Diagonal form of the FP64 translations (Sec. 3.3: the free and reaction
+# operators depend on m - p only).  k = 400 on the unit box makes the level-2
+# boxes ~70 wavelengths wide, where the plan keeps the circulant form.
+# ---------------------------------------------------------------------------
+HF_MED = Medium(W.IMPEDANCE, (400.0,), alpha=200.0)
+_hf = {}
+
+
+def _hf_case():
+    if not _hf:
+        xy = W.points_in_box(1, 2000, ((0.0, 1.0), (0.05, 1.05)), salt=7)
+        q = W.strengths(1, 2000, 2, salt=7)
+        F = fmm.CpuFmm(xy, HF_MED, tol=1e-6, leaf_size=32)
+        _hf.update(xy=xy, q=q, parts={part: F.apply(q, parts=part) for part in (1, 2, 4, 8)})
+    return _hf["xy"], _hf["q"], _hf["parts"]
+
+
+@pytest.mark.parametrize("part", [2, 4])
+def test_diagonal_translations_match_cpu_fmm(part):
+    """Free (2) and reaction (4) far-field terms with level 2 (and any other
+    level that passes the plan-time check) in diagonal form, against the CPU
+    FMM's dense translations at equal p: 1e-11 relative to the full result."""
+    xy, q, parts = _hf_case()
+    plan = Plan(xy, HF_MED, tol=1e-6, leaf_size=32, max_rhs=2)
+    inf = plan.info
+    assert inf["diag_levels"] & (1 << 2), inf["diag_levels"]
+    assert 0.0 <= inf["diag_check"] <= 1e-12
+    y = plan.apply(torch.from_numpy(q).cuda(), parts=part).cpu().numpy()
+    plan.close()
+    full = sum(parts.values())
+    err = np.linalg.norm(y - parts[part]) / np.linalg.norm(full)
+    assert err < PARITY_TOL, (part, err)
+
+
+def test_diagonal_translations_equal_dense_plan_forward_adjoint_gradient():
+    """The same plan with HFMM_FLAG_DENSE_M2L: forward and adjoint agree to
+    1e-12, position gradients to 1e-10; low-frequency plans keep every level
+    dense (the check fails there)."""
+    xy, q, _ = _hf_case()
+    a = Plan(xy, HF_MED, tol=1e-6, leaf_size=32, max_rhs=2)
+    b = Plan(xy, HF_MED, tol=1e-6, leaf_size=32, max_rhs=2, dense_m2l=True)
+    assert a.info["diag_levels"] != 0 and b.info["diag_levels"] == 0
+    qd = torch.from_numpy(q).cuda()
+    ya, yb = a.apply(qd).cpu().numpy(), b.apply(qd).cpu().numpy()
+    assert direct.rel_l2(ya, yb) < 1e-12, direct.rel_l2(ya, yb)
+    wa, wb = a.adjoint(qd).cpu().numpy(), b.adjoint(qd).cpu().numpy()
+    assert direct.rel_l2(wa, wb) < 1e-12, direct.rel_l2(wa, wb)
+    g = torch.from_numpy(W.strengths(1, xy.shape[0], 2, salt=8)).cuda()
+    ga, gb = a.grad(qd, g).cpu().numpy(), b.grad(qd, g).cpu().numpy()
+    assert np.linalg.norm(ga - gb) < 1e-10 * np.linalg.norm(gb)
+    a.close()
+    b.close()
+    med, xy1, q1, tol, leaf, p = _case("cfg1")
+    with Plan(xy1, med, tol=tol, leaf_size=leaf, max_rhs=2) as c:
+        assert c.info["diag_levels"] == 0
