@@ -91,6 +91,8 @@ def parse():
                     help="skip the FP64 reference apply (accuracy and one-RHS FP64 time)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--diag", action="store_true",
+                    help="FP64 diagonal vs dense translations at high frequency (k = 400, 1500) and exit")
     ap.add_argument("--sweep", action="store_true",
                     help="the N-sweep of the paper's timing table instead of the benchmark")
     ap.add_argument("--no-extra", action="store_true",
@@ -535,6 +537,52 @@ def run_sweep(args):
     print(json.dumps(out), flush=True)
 
 
+def run_diag(args):
+    """FP64 apply with the coarse levels' translations in diagonal form against
+    the same plan with every level dense (HFMM_FLAG_DENSE_M2L): impedance
+    half-space (alpha = k / 2) on the unit box at k = 400 and 1500, where the
+    level-2 boxes are ~30 and ~120 wavelengths wide; one right-hand side."""
+    import torch
+    import workloads as W
+    from paper_1703_09136_gb300 import Plan
+    from paper_1703_09136_gb300 import build as _build
+    _build.build()
+    w = W.WORKLOADS[7]
+    dev = torch.device("cuda", 0)
+    rows = []
+    for k, n in w.extra["cases"]:
+        med = W.Medium(W.IMPEDANCE, (k,), alpha=k / 2)
+        xy = torch.from_numpy(W.points_in_box(7, n, w.box)).to(dev)
+        q = torch.from_numpy(W.strengths(7, n, 1)).to(dev)
+        row = {"k": k, "n": n}
+        ys = {}
+        for dense in (False, True):
+            name = "dense" if dense else "diagonal"
+            t0 = time.perf_counter()
+            plan = Plan(xy, med, tol=w.tol, leaf_size=w.leaf, max_rhs=1, dense_m2l=dense, profile=True)
+            torch.cuda.synchronize()
+            row[name + "_plan_s"] = time.perf_counter() - t0
+            y = torch.empty_like(q)
+            row[name + "_ms"] = _events_ms(lambda: plan.apply(q, out=y), 5)
+            plan.apply(q, out=y)
+            row[name + "_down_ms"] = plan.stage_times()["down"]
+            inf = plan.info
+            row["p"] = inf["p"]
+            if not dense:
+                row["diagonal_levels"] = [l for l in range(32) if inf["diag_levels"] >> l & 1]
+                row["diagonal_check"] = inf["diag_check"]
+            ys[dense] = y.clone()
+            plan.close()
+        row["rel_l2_diagonal_vs_dense"] = float(torch.linalg.norm(ys[False] - ys[True]) / torch.linalg.norm(ys[True]))
+        row["speedup"] = row["dense_ms"] / row["diagonal_ms"]
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    out = {"metric": "FP64 H-FMM apply time, diagonal vs dense translations", "unit": "ms",
+           "workload": w.name, "medium": "impedance alpha = k/2", "box": w.box, "tol": w.tol, "nrhs": 1,
+           "rows": rows}
+    print(json.dumps(out), flush=True)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -878,6 +926,9 @@ def main():
         print(json.dumps(_cpu_child(json.loads(sys.argv[2]))), flush=True)
         return
     args = parse()
+    if args.diag:
+        run_diag(args)
+        return
     if args.sweep:
         run_sweep(args)
     elif args.impl == "reference":

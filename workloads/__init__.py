@@ -76,6 +76,11 @@ WORKLOADS = {
                 0, ((-0.5, 0.5), (1.0, 2.0)), 1, 1e-6, 32, "sweep",
                 {"p": 39, "k": (0.1, 1.0),
                  "n": (100, 6400, 10000, 90000, 360000, 640000, 810000, 1000000)}),
+    # high frequency on the unit box (level-2 boxes 30 and 120 wavelengths
+    # wide): the coarse levels' translations dominate the FP64 apply
+    7: Workload("impedance-unit-box-high-frequency", Medium(IMPEDANCE, (400.0,), alpha=200.0),
+                0, ((0.0, 1.0), (0.05, 1.05)), 1, 1e-6, 32, "uniform",
+                {"cases": ((400.0, 65536), (1500.0, 65536), (1500.0, 262144))}),
 }
 
 
