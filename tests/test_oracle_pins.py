@@ -494,3 +494,116 @@ def test_order_cap_keeps_translation_entries_in_double_range():
             assert not np.all(np.isfinite(hankel1(np.arange(0, 2 * p[l] + 9), x))), l
     shallow = fmm.build_tree(xy, L=3)
     assert fmm.p_schedule(k, shallow, 1e-6, p_fixed=38) == [39] * 4
+
+
+# --- adaptive tree (Sec. 3.1) -------------------------------------------------
+
+def _clustered_near_interface(n, salt):
+    """60% in a Gaussian blob (sigma 0.05) at (0.3, 0.08), redrawn below
+    y = 0.02; 40% uniform in [0, 0.6] x [0.02, 0.62]."""
+    g = np.random.Generator(np.random.PCG64(7000 + salt))
+    n1 = int(0.6 * n)
+    pts = []
+    while len(pts) < n1:
+        c = g.normal((0.3, 0.08), 0.05, size=(n1, 2))
+        c = c[(c[:, 1] >= 0.02) & (c[:, 0] >= 0.0) & (c[:, 0] <= 0.6) & (c[:, 1] <= 0.62)]
+        pts.extend(c.tolist())
+    u = np.stack([g.uniform(0.0, 0.6, n - n1), g.uniform(0.02, 0.62, n - n1)], axis=1)
+    return np.concatenate([np.array(pts[:n1]), u])
+
+
+def test_adaptive_lists_cover_every_leaf_pair_once():
+    """Adaptive tree on config 2's clusters (leaves on four levels): every
+    ordered leaf pair (T, S) is taken exactly once by U(T), by W(T) through an
+    ancestor of S, by X of an ancestor of T, or by the V list of a same-level
+    ancestor pair; and exactly once by an admissible reaction pair or a direct
+    pair of ancestors.  W and X are non-empty, and each W box is not adjacent
+    to its leaf while its parent is."""
+    from oracle import adaptive
+    F = adaptive.AdaptiveCpuFmm(W.points(2, 1200), W.WORKLOADS[2].medium, tol=1e-6, leaf_size=12)
+    t = F.tree
+    leaves = t.leaves()
+    assert len({b.level for b in leaves}) >= 3
+    assert sum(len(v) for v in F.W.values()) > 0
+
+    def chain(b):
+        out = []
+        while b is not None:
+            out.append(b.key)
+            b = b.parent
+        return out
+
+    anc = {b.key: set(chain(b)) for b in leaves}
+    free = {}
+    for T in leaves:
+        for S in F.U[T.key]:
+            free[(T.key, S.key)] = free.get((T.key, S.key), 0) + 1
+        for D in F.W[T.key]:
+            assert not adaptive.adjacent(D, T) and adaptive.adjacent(D.parent, T)
+            for S in leaves:
+                if D.key in anc[S.key]:
+                    free[(T.key, S.key)] = free.get((T.key, S.key), 0) + 1
+    for B_key, Cs in F.X.items():
+        for T in leaves:
+            if B_key in anc[T.key]:
+                for C in Cs:
+                    free[(T.key, C.key)] = free.get((T.key, C.key), 0) + 1
+    for B_key, Vs in F.V.items():
+        for T in leaves:
+            if B_key not in anc[T.key]:
+                continue
+            for Sv in Vs:
+                for S in leaves:
+                    if Sv.key in anc[S.key]:
+                        free[(T.key, S.key)] = free.get((T.key, S.key), 0) + 1
+    assert all(free.get((T.key, S.key), 0) == 1 for T in leaves for S in leaves)
+    cover = {}
+    pairs = [pr for l in F.R for pr in F.R[l]] + list(F.direct_pairs)
+    for A, B in pairs:
+        for T in leaves:
+            if A.key not in anc[T.key]:
+                continue
+            for S in leaves:
+                if B.key in anc[S.key]:
+                    cover[(T.key, S.key)] = cover.get((T.key, S.key), 0) + 1
+    assert all(cover.get((T.key, S.key), 0) == 1 for T in leaves for S in leaves)
+
+
+@pytest.mark.parametrize("case", ["impedance-clusters", "two-layer-clustered", "three-layer-clustered"])
+def test_adaptive_cpu_fmm_matches_direct_sum(case):
+    """The adaptive CPU H-FMM (U/V/W/X lists, reaction pairs down to leaves of
+    any level) against the O(N^2) direct sum at tol 1e-6 and 1e-10: config 2's
+    clusters (impedance) and a blob next to the interface (y >= 0.02) for the
+    two- and three-layer media."""
+    from oracle import adaptive
+    if case == "impedance-clusters":
+        med, xy = W.WORKLOADS[2].medium, W.points(2, 1200)
+    else:
+        med = Medium(TWO, (60.0, 90.0)) if case == "two-layer-clustered" else CFG4
+        xy = _clustered_near_interface(700, 1)
+    q = W.strengths(2, xy.shape[0], 1, salt=31)
+    yd = direct.direct_apply(med, xy, q)
+    for tol in (1e-6, 1e-10):
+        F = adaptive.AdaptiveCpuFmm(xy, med, tol=tol, leaf_size=12)
+        assert len({b.level for b in F.tree.leaves()}) >= 3
+        assert sum(len(v) for v in F.X.values()) > 0
+        assert direct.rel_l2(F.apply(q), yd) < tol, (case, tol)
+
+
+def test_adaptive_equals_uniform_fmm_on_a_uniform_tree():
+    """A 16 x 16 grid with one point per level-4 box and leaf size 1 gives an
+    adaptive tree whose leaves are all on level 4: no W or X pairs, and the
+    adaptive FMM equals the uniform one term by term."""
+    from oracle import adaptive
+    g = np.arange(16) / 15.0
+    X, Y = np.meshgrid(g, g + 0.05)
+    xy = np.stack([X.ravel(), Y.ravel()], axis=1)
+    med = Medium(IMP, (20.0,), alpha=10.0)
+    q = W.strengths(1, xy.shape[0], 2, salt=32)
+    A = adaptive.AdaptiveCpuFmm(xy, med, tol=1e-6, leaf_size=1)
+    U = fmm.CpuFmm(xy, med, tol=1e-6, leaf_size=1)
+    assert {b.level for b in A.tree.leaves()} == {4} and U.tree.L == 4
+    assert sum(len(v) for v in A.W.values()) == 0 and not A.X
+    for part in (1, 2, 4, 8):
+        ya, yu = A.apply(q, parts=part), U.apply(q, parts=part)
+        assert np.linalg.norm(ya - yu) <= 1e-13 * max(np.linalg.norm(yu), 1e-300), part
