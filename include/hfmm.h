@@ -129,6 +129,15 @@ typedef struct {
                                    one persistent kernel over a device work queue (see
                                    hfmm_batch_device_error) instead of one graph branch per
                                    instance */
+#define HFMM_FLAG_ADAPTIVE 32   /* HFMM_FP64: adaptive tree (Sec. 3.1): boxes with more than
+                                   leaf_size points are split (down to level 16), empty children
+                                   pruned, so leaves sit on many levels; U/V/W/X lists (W: a small
+                                   box's multipole evaluated at a leaf's points, X: a leaf's points
+                                   into a small box's local expansion), and the reaction pairs of
+                                   the uniform tree's recursion, summed directly below a leaf.  The
+                                   tree and lists are built on the host at plan time.  Not with
+                                   HFMM_MIXED or HFMM_FLAG_AUTOTUNE (HFMM_ERR_UNSUPPORTED); no
+                                   position gradients (hfmm_apply_grad returns UNSUPPORTED) */
 #define HFMM_FLAG_DENSE_M2L 16  /* HFMM_FP64: keep the dense (2p+1)^2 translations on every level.
                                    Without it the plan tries the diagonal form of the free and
                                    reaction translations (their matrices depend on m - p only,
@@ -191,6 +200,12 @@ typedef struct {
     int32_t diag_levels;        /* HFMM_FP64: bit l set if level l translates in diagonal form
                                    (see HFMM_FLAG_DENSE_M2L) */
     double diag_check;          /* largest plan-time difference of a level kept in diagonal form */
+    int32_t adaptive;           /* 1 for HFMM_FLAG_ADAPTIVE plans (levels = deepest level,
+                                   nonempty_leaves = leaves, direct_leaf_pairs = leaf pairs of
+                                   the directly summed reaction) */
+    int32_t reserved3;
+    int64_t w_pairs;            /* adaptive: (leaf, box) M2P pairs */
+    int64_t x_pairs;            /* adaptive: (box, leaf) P2L pairs */
 } hfmm_plan_info;
 
 /* Bits of `parts` in hfmm_apply_parts (sum of the selected terms). */
@@ -334,6 +349,24 @@ hfmm_status hfmm_plan_get_tree(hfmm_plan_t plan, int64_t* perm, int32_t* leaf_ix
  */
 hfmm_status hfmm_plan_get_pairs(hfmm_plan_t plan, int32_t kind, int32_t level,
                                 int32_t* out, int64_t cap, int64_t* count);
+
+/*
+ * Adaptive plans (HFMM_FLAG_ADAPTIVE): the boxes of the tree, by level and in
+ * Morton order within a level, as out[6*i .. 6*i+5] = (level, ix, iy, first
+ * sorted point, end, leaf flag) (the sorted order is hfmm_plan_get_tree's
+ * perm).  *count receives the number of boxes; out may be NULL to ask for it;
+ * INVALID_ARG if cap is smaller, UNSUPPORTED for uniform plans.
+ */
+hfmm_status hfmm_plan_get_boxes(hfmm_plan_t plan, int32_t* out, int64_t cap, int64_t* count);
+
+/*
+ * Adaptive plans: the pairs of one list as (target box, source box) indices
+ * into hfmm_plan_get_boxes in out[2*i], out[2*i+1]: kind 0 U (leaf, leaf),
+ * 1 V, 2 W (leaf, box: M2P), 3 X (box, leaf: P2L), 4 reaction M2L (same-level
+ * boxes), 5 directly summed reaction (box pairs with a leaf on one side; the
+ * sum runs over the leaf pairs below them).  Count / capacity as above.
+ */
+hfmm_status hfmm_plan_get_lists(hfmm_plan_t plan, int32_t kind, int32_t* out, int64_t cap, int64_t* count);
 
 /*
  * Stage times of the last apply of a plan created with HFMM_FLAG_PROFILE:

@@ -105,7 +105,7 @@ class Plan:
 
     def __init__(self, xy, medium, tol=1e-6, p=0, leaf_size=32, levels=0, precision=FP64,
                  max_rhs=1, stream=None, profile=False, simt_m2l=False, autotune=False, spin_limit=0,
-                 quad_scale=0.0, small_rhs=0, dense_m2l=False):
+                 quad_scale=0.0, small_rhs=0, dense_m2l=False, adaptive=False):
         lib = _n.lib()
         m = Medium.of(medium)
         opts = _n.hfmm_options()
@@ -117,7 +117,8 @@ class Plan:
         opts.precision = int(precision)
         opts.max_rhs = int(max_rhs)
         opts.flags = ((_n.FLAG_PROFILE if profile else 0) | (_n.FLAG_SIMT_M2L if simt_m2l else 0) |
-                      (_n.FLAG_AUTOTUNE if autotune else 0) | (_n.FLAG_DENSE_M2L if dense_m2l else 0))
+                      (_n.FLAG_AUTOTUNE if autotune else 0) | (_n.FLAG_DENSE_M2L if dense_m2l else 0) |
+                      (_n.FLAG_ADAPTIVE if adaptive else 0))
         opts.spin_limit = int(spin_limit)
         opts.quad_scale = float(quad_scale)
         opts.small_rhs = int(small_rhs)
@@ -277,6 +278,34 @@ class Plan:
                                          ctypes.c_int64(cnt.value), ctypes.byref(cnt)))
         return out[:cnt.value]
 
+    def perm(self):
+        """perm[i] = caller index of the i-th point in the tree's sorted order."""
+        perm = np.empty(self.n, dtype=np.int64)
+        _n.check(_n.lib().hfmm_plan_get_tree(self._h, perm.ctypes.data_as(ctypes.c_void_p), None, None))
+        return perm
+
+    def boxes(self):
+        """Adaptive plans: boxes [nbox, 6] int32 = (level, ix, iy, first sorted
+        point, end, leaf) (hfmm_plan_get_boxes)."""
+        lib = _n.lib()
+        cnt = ctypes.c_int64(0)
+        _n.check(lib.hfmm_plan_get_boxes(self._h, None, ctypes.c_int64(0), ctypes.byref(cnt)))
+        out = np.empty((max(cnt.value, 1), 6), dtype=np.int32)
+        _n.check(lib.hfmm_plan_get_boxes(self._h, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_int64(cnt.value),
+                                         ctypes.byref(cnt)))
+        return out[:cnt.value]
+
+    def lists(self, kind):
+        """Adaptive plans: (target box, source box) index pairs [npairs, 2] of
+        list kind 0 U, 1 V, 2 W, 3 X, 4 reaction M2L, 5 direct reaction."""
+        lib = _n.lib()
+        cnt = ctypes.c_int64(0)
+        _n.check(lib.hfmm_plan_get_lists(self._h, kind, None, ctypes.c_int64(0), ctypes.byref(cnt)))
+        out = np.empty((max(cnt.value, 1), 2), dtype=np.int32)
+        _n.check(lib.hfmm_plan_get_lists(self._h, kind, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_int64(cnt.value),
+                                         ctypes.byref(cnt)))
+        return out[:cnt.value]
+
     def close(self):
         if getattr(self, "_h", None):
             _n.lib().hfmm_plan_destroy(self._h)
@@ -302,7 +331,7 @@ class Batch:
     one persistent kernel over a device work queue."""
 
     def __init__(self, xys, medium, tol=1e-6, p=0, leaf_size=32, levels=0, precision=FP64, max_rhs=1,
-                 stream=None, simt_m2l=False, spin_limit=0, small_rhs=0, persistent=False):
+                 stream=None, simt_m2l=False, spin_limit=0, small_rhs=0, persistent=False, adaptive=False):
         lib = _n.lib()
         m = Medium.of(medium)
         opts = _n.hfmm_options()
@@ -310,7 +339,8 @@ class Batch:
         opts.tol, opts.p, opts.leaf_size, opts.levels = float(tol), int(p), int(leaf_size), int(levels)
         opts.precision, opts.max_rhs = int(precision), int(max_rhs)
         opts.small_rhs = int(small_rhs)
-        opts.flags = (_n.FLAG_SIMT_M2L if simt_m2l else 0) | (_n.FLAG_PERSISTENT if persistent else 0)
+        opts.flags = ((_n.FLAG_SIMT_M2L if simt_m2l else 0) | (_n.FLAG_PERSISTENT if persistent else 0) |
+                      (_n.FLAG_ADAPTIVE if adaptive else 0))
         opts.spin_limit = int(spin_limit)
         keep = [_ptr(np.ascontiguousarray(x, dtype=np.float64) if not hasattr(x, "data_ptr") else x.contiguous())
                 for x in xys]

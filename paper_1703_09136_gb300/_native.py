@@ -22,7 +22,8 @@ EXPORTS = ["hfmm_options_default", "hfmm_plan_create", "hfmm_apply", "hfmm_apply
            "hfmm_debug_bessel", "hfmm_plan_get_stage_times", "hfmm_debug_green_f32",
            "hfmm_leaf_order_noalloc", "hfmm_apply_grad", "hfmm_batch_create", "hfmm_batch_apply",
            "hfmm_batch_get_plan", "hfmm_batch_destroy", "hfmm_debug_wait_timeout", "hfmm_plan_get_leaf_down",
-           "hfmm_batch_device_error", "hfmm_batch_apply_grad", "hfmm_solve"]
+           "hfmm_batch_device_error", "hfmm_batch_apply_grad", "hfmm_solve", "hfmm_plan_get_boxes",
+           "hfmm_plan_get_lists"]
 NUM_STAGES = 8
 STAGES = ["gather", "p2m", "m2m", "down", "l2p", "p2p", "direct", "scatter"]
 FLAG_PROFILE = 1
@@ -30,6 +31,7 @@ FLAG_SIMT_M2L = 2
 FLAG_AUTOTUNE = 4
 FLAG_PERSISTENT = 8
 FLAG_DENSE_M2L = 16
+FLAG_ADAPTIVE = 32
 
 
 class HfmmError(RuntimeError):
@@ -65,7 +67,8 @@ class hfmm_plan_info(ctypes.Structure):
                 ("near_tc_blocks", ctypes.c_int64), ("near_simt_leaves", ctypes.c_int64),
                 ("leaf_l2p_fused", ctypes.c_int32), ("leaf_tc_width", ctypes.c_int32),
                 ("table_check", ctypes.c_double), ("small_rhs", ctypes.c_int32), ("diag_levels", ctypes.c_int32),
-                ("diag_check", ctypes.c_double)]
+                ("diag_check", ctypes.c_double), ("adaptive", ctypes.c_int32), ("reserved3", ctypes.c_int32),
+                ("w_pairs", ctypes.c_int64), ("x_pairs", ctypes.c_int64)]
 
 
 hfmm_plan_t = ctypes.c_void_p
@@ -107,13 +110,15 @@ def lib():
         L.hfmm_batch_device_error.argtypes = [vp, vp]
         L.hfmm_batch_apply_grad.argtypes = [vp, i32, vp, vp, vp, vp]
         L.hfmm_solve.argtypes = [hfmm_plan_t, vp, vp, vp, dbl, i32, i32, vp, vp, vp]
+        L.hfmm_plan_get_boxes.argtypes = [hfmm_plan_t, vp, i64, ctypes.POINTER(i64)]
+        L.hfmm_plan_get_lists.argtypes = [hfmm_plan_t, i32, vp, i64, ctypes.POINTER(i64)]
         for name in ("hfmm_plan_create", "hfmm_apply", "hfmm_apply_parts", "hfmm_apply_adjoint",
                      "hfmm_plan_get_info", "hfmm_plan_get_tree", "hfmm_plan_get_pairs",
                      "hfmm_plan_destroy", "hfmm_debug_bessel", "hfmm_plan_get_stage_times",
                      "hfmm_debug_green_f32", "hfmm_leaf_order_noalloc", "hfmm_apply_grad",
                      "hfmm_batch_create", "hfmm_batch_apply", "hfmm_batch_get_plan", "hfmm_batch_destroy",
                      "hfmm_debug_wait_timeout", "hfmm_plan_get_leaf_down", "hfmm_batch_device_error",
-                     "hfmm_batch_apply_grad", "hfmm_solve"):
+                     "hfmm_batch_apply_grad", "hfmm_solve", "hfmm_plan_get_boxes", "hfmm_plan_get_lists"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib

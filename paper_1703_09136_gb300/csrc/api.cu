@@ -50,6 +50,7 @@ static void plan_free(hfmm_plan_s* P) {
     for (cudaEvent_t e : {P->ev_fork, P->ev_near_done, P->ev_far_done})
         if (e) cudaEventDestroy(e);
     for (void* p : P->allocations) cudaFree(p);
+    adaptive_destroy(P->ad);
     delete P;
 }
 
@@ -187,6 +188,11 @@ static hfmm_status time_apply(hfmm_plan_t P, cudaStream_t st, double* ms, int nr
 
 hfmm_status hfmm_plan_create(hfmm_plan_t* out, int64_t n, const double* xy, const hfmm_medium* medium,
                              const hfmm_options* opts, void* stream) {
+    if (opts && (opts->flags & HFMM_FLAG_ADAPTIVE) && (opts->flags & HFMM_FLAG_AUTOTUNE)) {
+        if (out) *out = nullptr;
+        hfmm_set_error("HFMM_FLAG_AUTOTUNE chooses a uniform leaf level; adaptive trees set their own depths");
+        return HFMM_ERR_UNSUPPORTED;
+    }
     if (!opts || !(opts->flags & HFMM_FLAG_AUTOTUNE)) return plan_create_one(out, n, xy, medium, opts, stream);
     if (!out) { hfmm_set_error("out is NULL"); return HFMM_ERR_INVALID_ARG; }
     *out = nullptr;
@@ -268,6 +274,10 @@ static hfmm_status plan_create_one(hfmm_plan_t* out, int64_t n, const double* xy
     if (o.levels < 0 || o.levels > 15) { hfmm_set_error("levels must be in [0, 15]"); return HFMM_ERR_INVALID_ARG; }
     if (o.spin_limit < 0) { hfmm_set_error("spin_limit must be >= 0"); return HFMM_ERR_INVALID_ARG; }
     if (o.small_rhs < -1) { hfmm_set_error("small_rhs must be >= -1"); return HFMM_ERR_INVALID_ARG; }
+    if ((o.flags & HFMM_FLAG_ADAPTIVE) && o.precision != HFMM_FP64) {
+        hfmm_set_error("adaptive trees run on the FP64 path only");
+        return HFMM_ERR_UNSUPPORTED;
+    }
     if (!(o.quad_scale >= 0.0) || !std::isfinite(o.quad_scale) || o.quad_scale > 64.0) {
         hfmm_set_error("quad_scale must be in [0, 64] (got %g)", o.quad_scale);
         return HFMM_ERR_INVALID_ARG;
@@ -297,7 +307,8 @@ static hfmm_status plan_create_one(hfmm_plan_t* out, int64_t n, const double* xy
             if (e != cudaSuccess) { hfmm_set_error("copy of xy failed: %s", cudaGetErrorString(e)); s = HFMM_ERR_CUDA; break; }
             d_xy = tmp;
         }
-        if ((s = build_tree(P, d_xy, st)) != HFMM_OK) break;
+        const bool adaptive = (o.flags & HFMM_FLAG_ADAPTIVE) != 0;
+        if ((s = adaptive ? build_adaptive_tree(P, d_xy, o.leaf_size, st) : build_tree(P, d_xy, st)) != HFMM_OK) break;
         const int L = P->L;
         P->lev.resize(L + 1);
         const int base = o.p > 0 ? o.p : p_low(o.tol);
@@ -318,7 +329,7 @@ static hfmm_status plan_create_one(hfmm_plan_t* out, int64_t n, const double* xy
             lv.p = pcap;
             lv.ncoef = 2 * lv.p + 1;
         }
-        if ((s = build_lists(P, st)) != HFMM_OK) break;
+        if ((s = adaptive ? build_adaptive_lists(P, st) : build_lists(P, st)) != HFMM_OK) break;
         // expansion buffers
         const bool mixed = o.precision == HFMM_MIXED;
         const size_t esz = mixed ? sizeof(cf) : sizeof(cd);
@@ -334,7 +345,7 @@ static hfmm_status plan_create_one(hfmm_plan_t* out, int64_t n, const double* xy
         if ((s = plan_alloc(P, mixed ? (void**)&P->y32 : (void**)&P->y_sorted, esz * n * o.max_rhs)) != HFMM_OK) break;
         P->buffer_bytes += 2.0 * esz * n * o.max_rhs;
         if ((s = build_tables(P, st)) != HFMM_OK) break;
-        if (!mixed && (s = build_near64(P, st)) != HFMM_OK) break;
+        if (!mixed && !adaptive && (s = build_near64(P, st)) != HFMM_OK) break;
         if (!mixed && (s = build_diag(P, st)) != HFMM_OK) break;
         if (mixed) {
             if ((s = build_tables32(P, st)) != HFMM_OK) break;
@@ -468,6 +479,7 @@ hfmm_status hfmm_apply_grad(hfmm_plan_t P, int32_t nrhs, const void* q, const vo
         return HFMM_ERR_INVALID_ARG;
     }
     if (!q || !g || !gxy) { hfmm_set_error("q, g or gxy is NULL"); return HFMM_ERR_INVALID_ARG; }
+    if (P->ad) { hfmm_set_error("position gradients are not built for adaptive trees"); return HFMM_ERR_UNSUPPORTED; }
     cudaStream_t st = (cudaStream_t)stream;
     const bool mixed = P->precision == HFMM_MIXED;
     const size_t bytes = (mixed ? sizeof(cf) : sizeof(cd)) * (size_t)P->n * nrhs;
@@ -516,7 +528,12 @@ hfmm_status hfmm_plan_get_info(hfmm_plan_t P, hfmm_plan_info* info) {
     const auto& lb = P->h_leaf_begin;
     int64_t ne = 0;
     for (size_t b = 0; b + 1 < lb.size(); ++b) ne += lb[b + 1] > lb[b];
-    info->nonempty_leaves = ne;
+    info->nonempty_leaves = P->ad ? adaptive_count(P, 0) : ne;
+    if (P->ad) {
+        info->adaptive = 1;
+        info->w_pairs = adaptive_count(P, 2);
+        info->x_pairs = adaptive_count(P, 3);
+    }
     for (int l = 0; l <= P->L; ++l) { info->v_pairs += P->lev[l].nv; info->r_pairs += P->lev[l].nr; }
     info->direct_leaf_pairs = P->nd;
     info->u_pairs = P->u_pairs;
@@ -583,6 +600,10 @@ hfmm_status hfmm_plan_get_leaf_down(hfmm_plan_t P, double* ms, double* flops) {
 
 hfmm_status hfmm_plan_get_tree(hfmm_plan_t P, int64_t* perm, int32_t* leaf_ix, int32_t* leaf_iy) {
     if (!P) { hfmm_set_error("plan is NULL"); return HFMM_ERR_INVALID_ARG; }
+    if (P->ad && (leaf_ix || leaf_iy)) {
+        hfmm_set_error("adaptive trees: leaves sit on many levels (hfmm_plan_get_boxes)");
+        return HFMM_ERR_UNSUPPORTED;
+    }
     std::vector<int64_t> hp(P->n);
     HFMM_CUDA_TRY(cudaMemcpy(hp.data(), P->perm, sizeof(int64_t) * P->n, cudaMemcpyDeviceToHost));
     if (perm) std::memcpy(perm, hp.data(), sizeof(int64_t) * P->n);
@@ -599,6 +620,7 @@ hfmm_status hfmm_plan_get_tree(hfmm_plan_t P, int64_t* perm, int32_t* leaf_ix, i
 
 hfmm_status hfmm_plan_get_pairs(hfmm_plan_t P, int32_t kind, int32_t level, int32_t* out, int64_t cap,
                                 int64_t* count) {
+    if (P && P->ad) { hfmm_set_error("adaptive trees: use hfmm_plan_get_lists"); return HFMM_ERR_UNSUPPORTED; }
     if (!P || !count) { hfmm_set_error("plan or count is NULL"); return HFMM_ERR_INVALID_ARG; }
     if (level < 0 || level > P->L) { hfmm_set_error("level out of range"); return HFMM_ERR_INVALID_ARG; }
     std::vector<int32_t> pairs;
@@ -648,6 +670,24 @@ hfmm_status hfmm_plan_get_pairs(hfmm_plan_t P, int32_t kind, int32_t level, int3
     if (*count > cap) { hfmm_set_error("capacity %lld < %lld pairs", (long long)cap, (long long)*count); return HFMM_ERR_INVALID_ARG; }
     if (out && !pairs.empty()) std::memcpy(out, pairs.data(), sizeof(int32_t) * pairs.size());
     return HFMM_OK;
+}
+
+hfmm_status hfmm_plan_get_boxes(hfmm_plan_t P, int32_t* out, int64_t cap, int64_t* count) {
+    if (!P || !count) { hfmm_set_error("plan or count is NULL"); return HFMM_ERR_INVALID_ARG; }
+    if (!P->ad) { hfmm_set_error("the plan has a uniform tree (hfmm_plan_get_tree)"); return HFMM_ERR_UNSUPPORTED; }
+    HFMM_TRY(adaptive_boxes(P, count, nullptr));
+    if (!out) return HFMM_OK;
+    if (cap < *count) { hfmm_set_error("capacity %lld < %lld boxes", (long long)cap, (long long)*count); return HFMM_ERR_INVALID_ARG; }
+    return adaptive_boxes(P, count, out);
+}
+
+hfmm_status hfmm_plan_get_lists(hfmm_plan_t P, int32_t kind, int32_t* out, int64_t cap, int64_t* count) {
+    if (!P || !count) { hfmm_set_error("plan or count is NULL"); return HFMM_ERR_INVALID_ARG; }
+    if (!P->ad) { hfmm_set_error("the plan has a uniform tree (hfmm_plan_get_pairs)"); return HFMM_ERR_UNSUPPORTED; }
+    HFMM_TRY(adaptive_pairs(P, kind, count, nullptr));
+    if (!out) return HFMM_OK;
+    if (cap < *count) { hfmm_set_error("capacity %lld < %lld pairs", (long long)cap, (long long)*count); return HFMM_ERR_INVALID_ARG; }
+    return adaptive_pairs(P, kind, count, out);
 }
 
 hfmm_status hfmm_plan_destroy(hfmm_plan_t plan) {

@@ -79,6 +79,7 @@ void hfmm_set_error(const char* fmt, ...);
     do {                                                                           \
         cudaError_t _e = (call);                                                   \
         if (_e != cudaSuccess) {                                                   \
+            cudaGetLastError(); /* a non-sticky error must not reach later calls */ \
             hfmm_set_error("%s:%d %s: %s", __FILE__, __LINE__, #call,               \
                            cudaGetErrorString(_e));                                \
             return _e == cudaErrorMemoryAllocation ? HFMM_ERR_OOM : HFMM_ERR_CUDA; \

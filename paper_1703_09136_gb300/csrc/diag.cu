@@ -261,7 +261,7 @@ double diag_flops(const hfmm_plan_s* P, int l, int nrhs, int parts) {
 hfmm_status build_diag(hfmm_plan_s* P, cudaStream_t st) {
     P->diag_levels = 0;
     P->diag_check = 0.0;
-    if (P->precision != HFMM_FP64 || (P->flags & HFMM_FLAG_DENSE_M2L)) return HFMM_OK;
+    if (P->precision != HFMM_FP64 || (P->flags & HFMM_FLAG_DENSE_M2L) || P->ad) return HFMM_OK;
     HFMM_TRY(dg_attributes());
     for (int l = P->lmin; l <= P->L; ++l) {
         LevelInfo& lv = P->lev[l];

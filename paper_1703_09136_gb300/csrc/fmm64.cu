@@ -394,100 +394,103 @@ hfmm_status apply_fp64(hfmm_plan_s* P, int nrhs, const cd* q, cd* y, int parts, 
     HFMM_CUDA_TRY(cudaMemsetAsync(P->y_sorted, 0, sizeof(cd) * n * nrhs, st));
     tm.end(HFMM_STAGE_GATHER);
     P->st_bytes[HFMM_STAGE_GATHER] = 2.0 * C * n + 8.0 * n;
-    const bool far = (parts & (HFMM_PART_FAR_FREE | HFMM_PART_FAR_REACT)) != 0;
-    if (far) {
-        // step 2: upward pass
-        {
-            LevelInfo& lv = P->lev[L];
-            const int chunk = pick_chunk(lv.p);
-            const size_t sm = (size_t)chunk * ((2 * lv.p + 1) * sizeof(cd) + (lv.p + 1) * sizeof(double));
-            tm.begin(HFMM_STAGE_P2M);
-            p2m_kernel<<<(unsigned)lv.nbox, TB, sm, st>>>(P->leaf_begin, P->xy_sorted, P->q_sorted, n, nrhs,
-                                                         P->x0, P->y0, lv.h, L, P->k, lv.p, chunk, lv.mult);
+    if (P->ad) HFMM_TRY(apply_adaptive(P, nrhs, parts, st));
+    else {
+        const bool far = (parts & (HFMM_PART_FAR_FREE | HFMM_PART_FAR_REACT)) != 0;
+        if (far) {
+            // step 2: upward pass
+            {
+                LevelInfo& lv = P->lev[L];
+                const int chunk = pick_chunk(lv.p);
+                const size_t sm = (size_t)chunk * ((2 * lv.p + 1) * sizeof(cd) + (lv.p + 1) * sizeof(double));
+                tm.begin(HFMM_STAGE_P2M);
+                p2m_kernel<<<(unsigned)lv.nbox, TB, sm, st>>>(P->leaf_begin, P->xy_sorted, P->q_sorted, n, nrhs,
+                                                             P->x0, P->y0, lv.h, L, P->k, lv.p, chunk, lv.mult);
+                ++P->launches;
+                HFMM_CUDA_TRY(cudaGetLastError());
+                if (lv.diag_logq) HFMM_TRY(diag_src(P, L, nrhs, st));
+                tm.end(HFMM_STAGE_P2M);
+                P->st_flops[HFMM_STAGE_P2M] = MAC * n * lv.ncoef;
+                P->st_bytes[HFMM_STAGE_P2M] = C * n + 16.0 * n + C * lv.nbox * lv.ncoef;
+            }
+            tm.begin(HFMM_STAGE_M2M);
+            for (int l = L - 1; l >= P->lmin; --l) {
+                LevelInfo& lv = P->lev[l];
+                m2m_kernel<<<(unsigned)lv.nbox, TB, 0, st>>>(P->lev[l + 1].mult, lv.t_m2m, P->lev[l + 1].p, lv.p,
+                                                            nrhs, lv.mult);
+                ++P->launches;
+                HFMM_CUDA_TRY(cudaGetLastError());
+                if (lv.diag_logq) HFMM_TRY(diag_src(P, l, nrhs, st));
+                P->st_flops[HFMM_STAGE_M2M] += MAC * 4.0 * lv.nbox * lv.ncoef * P->lev[l + 1].ncoef;
+                P->st_bytes[HFMM_STAGE_M2M] += C * (4.0 * lv.nbox * P->lev[l + 1].ncoef + lv.nbox * lv.ncoef);
+            }
+            tm.end(HFMM_STAGE_M2M);
+            // step 3: downward pass
+            tm.begin(HFMM_STAGE_DOWN);
+            for (int l = P->lmin; l <= L; ++l) {
+                LevelInfo& lv = P->lev[l];
+                const bool has_parent = l > P->lmin;
+                const bool dg = lv.diag_logq > 0;   // translations in diagonal form after the L2L
+                downward_kernel<<<(unsigned)lv.nbox, TB, 0, st>>>(
+                    P->leaf_begin, L, l, P->lmin, nrhs, lv.p, has_parent ? P->lev[l - 1].p : 0,
+                    has_parent ? P->lev[l - 1].loc : nullptr, has_parent ? P->lev[l - 1].t_l2l : nullptr,
+                    lv.mult, lv.nv && !dg ? lv.v_begin : nullptr, lv.v_src, lv.v_off, lv.t_free,
+                    lv.nr && !dg ? lv.r_begin : nullptr, lv.r_src, lv.r_tab, lv.t_react, parts, lv.loc);
+                ++P->launches;
+                HFMM_CUDA_TRY(cudaGetLastError());
+                if (dg) HFMM_TRY(diag_m2l(P, l, nrhs, parts, st));
+                double pairs = 0.0;
+                if (parts & HFMM_PART_FAR_FREE) pairs += (double)lv.nv;
+                if (parts & HFMM_PART_FAR_REACT) pairs += (double)lv.nr;
+                if (dg) P->st_flops[HFMM_STAGE_DOWN] += diag_flops(P, l, nrhs, parts);
+                else P->st_flops[HFMM_STAGE_DOWN] += MAC * pairs * lv.ncoef * lv.ncoef;
+                if (has_parent) P->st_flops[HFMM_STAGE_DOWN] += MAC * lv.nbox * lv.ncoef * P->lev[l - 1].ncoef;
+                P->st_bytes[HFMM_STAGE_DOWN] += C * lv.nbox * lv.ncoef * 2.0 +
+                                                (has_parent ? C * P->lev[l - 1].nbox * P->lev[l - 1].ncoef : 0.0);
+            }
+            tm.end(HFMM_STAGE_DOWN);
+            // step 4: local expansions at the targets
+            {
+                LevelInfo& lv = P->lev[L];
+                const int chunk = pick_chunk(lv.p);
+                const size_t sm = (size_t)chunk * ((2 * lv.p + 1) * sizeof(cd) + (lv.p + 1) * sizeof(double));
+                tm.begin(HFMM_STAGE_L2P);
+                l2p_kernel<<<(unsigned)lv.nbox, TB, sm, st>>>(P->leaf_begin, P->xy_sorted, lv.loc, n, nrhs, P->x0,
+                                                             P->y0, lv.h, P->k, lv.p, chunk, P->y_sorted);
+                ++P->launches;
+                HFMM_CUDA_TRY(cudaGetLastError());
+                tm.end(HFMM_STAGE_L2P);
+                P->st_flops[HFMM_STAGE_L2P] = MAC * n * lv.ncoef;
+                P->st_bytes[HFMM_STAGE_L2P] = C * lv.nbox * lv.ncoef + 16.0 * n + 2.0 * C * n;
+            }
+        }
+        // step 5: direct interactions
+        if (parts & HFMM_PART_NEAR_FREE) {
+            tm.begin(HFMM_STAGE_P2P);
+            if (P->near64_vals)
+                near64_kernel<<<(unsigned)ceil_div(P->lev[L].nbox, 4), 128, 0, st>>>(
+                    P->leaf_begin, L, P->lev[L].nbox, P->near64_off, P->near64_vals, P->q_sorted, n, nrhs, P->y_sorted);
+            else
+                p2p_kernel<<<(unsigned)P->lev[L].nbox, P2P_THREADS, 0, st>>>(P->leaf_begin, L, P->xy_sorted,
+                                                                             P->q_sorted, n, nrhs, P->k, P->y_sorted);
             ++P->launches;
             HFMM_CUDA_TRY(cudaGetLastError());
-            if (lv.diag_logq) HFMM_TRY(diag_src(P, L, nrhs, st));
-            tm.end(HFMM_STAGE_P2M);
-            P->st_flops[HFMM_STAGE_P2M] = MAC * n * lv.ncoef;
-            P->st_bytes[HFMM_STAGE_P2M] = C * n + 16.0 * n + C * lv.nbox * lv.ncoef;
+            tm.end(HFMM_STAGE_P2P);
+            P->st_flops[HFMM_STAGE_P2P] = MAC * (double)P->p2p_point_pairs;
+            P->st_bytes[HFMM_STAGE_P2P] = C * n + 2.0 * C * n + 16.0 * n +
+                                          (P->near64_vals ? 16.0 * (double)P->p2p_point_pairs : 0.0);
         }
-        tm.begin(HFMM_STAGE_M2M);
-        for (int l = L - 1; l >= P->lmin; --l) {
-            LevelInfo& lv = P->lev[l];
-            m2m_kernel<<<(unsigned)lv.nbox, TB, 0, st>>>(P->lev[l + 1].mult, lv.t_m2m, P->lev[l + 1].p, lv.p,
-                                                        nrhs, lv.mult);
+        if ((parts & HFMM_PART_NEAR_REACT) && P->nd > 0) {
+            tm.begin(HFMM_STAGE_DIRECT);
+            direct_react_kernel<<<(unsigned)P->lev[L].nbox, TB, 0, st>>>(P->leaf_begin, P->d_begin, P->d_src,
+                                                                         P->d_blk, P->d_vals, P->q_sorted, n,
+                                                                         nrhs, P->y_sorted);
             ++P->launches;
             HFMM_CUDA_TRY(cudaGetLastError());
-            if (lv.diag_logq) HFMM_TRY(diag_src(P, l, nrhs, st));
-            P->st_flops[HFMM_STAGE_M2M] += MAC * 4.0 * lv.nbox * lv.ncoef * P->lev[l + 1].ncoef;
-            P->st_bytes[HFMM_STAGE_M2M] += C * (4.0 * lv.nbox * P->lev[l + 1].ncoef + lv.nbox * lv.ncoef);
+            tm.end(HFMM_STAGE_DIRECT);
+            P->st_flops[HFMM_STAGE_DIRECT] = MAC * (double)P->nd_vals;
+            P->st_bytes[HFMM_STAGE_DIRECT] = 16.0 * (double)P->nd_vals;
         }
-        tm.end(HFMM_STAGE_M2M);
-        // step 3: downward pass
-        tm.begin(HFMM_STAGE_DOWN);
-        for (int l = P->lmin; l <= L; ++l) {
-            LevelInfo& lv = P->lev[l];
-            const bool has_parent = l > P->lmin;
-            const bool dg = lv.diag_logq > 0;   // translations in diagonal form after the L2L
-            downward_kernel<<<(unsigned)lv.nbox, TB, 0, st>>>(
-                P->leaf_begin, L, l, P->lmin, nrhs, lv.p, has_parent ? P->lev[l - 1].p : 0,
-                has_parent ? P->lev[l - 1].loc : nullptr, has_parent ? P->lev[l - 1].t_l2l : nullptr,
-                lv.mult, lv.nv && !dg ? lv.v_begin : nullptr, lv.v_src, lv.v_off, lv.t_free,
-                lv.nr && !dg ? lv.r_begin : nullptr, lv.r_src, lv.r_tab, lv.t_react, parts, lv.loc);
-            ++P->launches;
-            HFMM_CUDA_TRY(cudaGetLastError());
-            if (dg) HFMM_TRY(diag_m2l(P, l, nrhs, parts, st));
-            double pairs = 0.0;
-            if (parts & HFMM_PART_FAR_FREE) pairs += (double)lv.nv;
-            if (parts & HFMM_PART_FAR_REACT) pairs += (double)lv.nr;
-            if (dg) P->st_flops[HFMM_STAGE_DOWN] += diag_flops(P, l, nrhs, parts);
-            else P->st_flops[HFMM_STAGE_DOWN] += MAC * pairs * lv.ncoef * lv.ncoef;
-            if (has_parent) P->st_flops[HFMM_STAGE_DOWN] += MAC * lv.nbox * lv.ncoef * P->lev[l - 1].ncoef;
-            P->st_bytes[HFMM_STAGE_DOWN] += C * lv.nbox * lv.ncoef * 2.0 +
-                                            (has_parent ? C * P->lev[l - 1].nbox * P->lev[l - 1].ncoef : 0.0);
-        }
-        tm.end(HFMM_STAGE_DOWN);
-        // step 4: local expansions at the targets
-        {
-            LevelInfo& lv = P->lev[L];
-            const int chunk = pick_chunk(lv.p);
-            const size_t sm = (size_t)chunk * ((2 * lv.p + 1) * sizeof(cd) + (lv.p + 1) * sizeof(double));
-            tm.begin(HFMM_STAGE_L2P);
-            l2p_kernel<<<(unsigned)lv.nbox, TB, sm, st>>>(P->leaf_begin, P->xy_sorted, lv.loc, n, nrhs, P->x0,
-                                                         P->y0, lv.h, P->k, lv.p, chunk, P->y_sorted);
-            ++P->launches;
-            HFMM_CUDA_TRY(cudaGetLastError());
-            tm.end(HFMM_STAGE_L2P);
-            P->st_flops[HFMM_STAGE_L2P] = MAC * n * lv.ncoef;
-            P->st_bytes[HFMM_STAGE_L2P] = C * lv.nbox * lv.ncoef + 16.0 * n + 2.0 * C * n;
-        }
-    }
-    // step 5: direct interactions
-    if (parts & HFMM_PART_NEAR_FREE) {
-        tm.begin(HFMM_STAGE_P2P);
-        if (P->near64_vals)
-            near64_kernel<<<(unsigned)ceil_div(P->lev[L].nbox, 4), 128, 0, st>>>(
-                P->leaf_begin, L, P->lev[L].nbox, P->near64_off, P->near64_vals, P->q_sorted, n, nrhs, P->y_sorted);
-        else
-            p2p_kernel<<<(unsigned)P->lev[L].nbox, P2P_THREADS, 0, st>>>(P->leaf_begin, L, P->xy_sorted,
-                                                                         P->q_sorted, n, nrhs, P->k, P->y_sorted);
-        ++P->launches;
-        HFMM_CUDA_TRY(cudaGetLastError());
-        tm.end(HFMM_STAGE_P2P);
-        P->st_flops[HFMM_STAGE_P2P] = MAC * (double)P->p2p_point_pairs;
-        P->st_bytes[HFMM_STAGE_P2P] = C * n + 2.0 * C * n + 16.0 * n +
-                                      (P->near64_vals ? 16.0 * (double)P->p2p_point_pairs : 0.0);
-    }
-    if ((parts & HFMM_PART_NEAR_REACT) && P->nd > 0) {
-        tm.begin(HFMM_STAGE_DIRECT);
-        direct_react_kernel<<<(unsigned)P->lev[L].nbox, TB, 0, st>>>(P->leaf_begin, P->d_begin, P->d_src,
-                                                                     P->d_blk, P->d_vals, P->q_sorted, n,
-                                                                     nrhs, P->y_sorted);
-        ++P->launches;
-        HFMM_CUDA_TRY(cudaGetLastError());
-        tm.end(HFMM_STAGE_DIRECT);
-        P->st_flops[HFMM_STAGE_DIRECT] = MAC * (double)P->nd_vals;
-        P->st_bytes[HFMM_STAGE_DIRECT] = 16.0 * (double)P->nd_vals;
     }
     tm.begin(HFMM_STAGE_SCATTER);
     scatter_y<<<nb, 256, 0, st>>>(P->y_sorted, P->perm, n, nrhs, adjoint, y);

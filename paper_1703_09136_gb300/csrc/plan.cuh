@@ -120,8 +120,13 @@ struct NtChunk {
     int32_t pad;
 };
 
+// Adaptive trees (adaptive.cu): deepest level, and the host / device tree.
+constexpr int AD_MAX_LEVEL = 16;
+struct AdaptiveTree;
+
 struct hfmm_plan_s {
     int64_t n = 0;
+    AdaptiveTree* ad = nullptr;     // HFMM_FLAG_ADAPTIVE plans
     int L = 0;
     int lmin = 0;
     int lstar = 0;                // first level whose bottom-row pairs are admissible
@@ -261,6 +266,14 @@ hfmm_status build_tree(hfmm_plan_s* P, const double* d_xy, cudaStream_t st);
 hfmm_status build_lists(hfmm_plan_s* P, cudaStream_t st);
 // tables.cu
 hfmm_status build_tables(hfmm_plan_s* P, cudaStream_t st);
+// a directly summed reaction block: target / source point ranges (sorted
+// indices) and the |X| bound and Y range of its point pairs
+struct DirectSpec {
+    int32_t t_lo, t_n, s_lo, s_n;
+    double xmax, ymin, ymax;
+};
+hfmm_status build_direct_blocks(hfmm_plan_s* P, const std::vector<DirectSpec>& specs, std::vector<int64_t>& blk,
+                                cudaStream_t st);
 hfmm_status build_tables32(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status build_direct_grad(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status apply_grad_fp64(hfmm_plan_s* P, int nrhs, const cd* q, const cd* g, double* gxy, cudaStream_t st);
@@ -268,6 +281,13 @@ hfmm_status apply_grad_fp64(hfmm_plan_s* P, int nrhs, const cd* q, const cd* g, 
 constexpr double NEAR64_MAX_BYTES = 32e9;   // plan-time FP64 near-field blocks up to this size
 hfmm_status build_near64(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status build_diag(hfmm_plan_s* P, cudaStream_t st);
+hfmm_status build_adaptive_tree(hfmm_plan_s* P, const double* d_xy, int leaf_size, cudaStream_t st);
+hfmm_status build_adaptive_lists(hfmm_plan_s* P, cudaStream_t st);
+hfmm_status apply_adaptive(hfmm_plan_s* P, int nrhs, int parts, cudaStream_t st);
+hfmm_status adaptive_boxes(const hfmm_plan_s* P, int64_t* count, int32_t* out);
+hfmm_status adaptive_pairs(const hfmm_plan_s* P, int kind, int64_t* count, int32_t* out);
+int64_t adaptive_count(const hfmm_plan_s* P, int kind);
+void adaptive_destroy(AdaptiveTree* T);
 hfmm_status diag_src(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st);
 hfmm_status diag_m2l(hfmm_plan_s* P, int l, int nrhs, int parts, cudaStream_t st);
 double diag_flops(const hfmm_plan_s* P, int l, int nrhs, int parts);

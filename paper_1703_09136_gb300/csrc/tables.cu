@@ -575,6 +575,91 @@ __global__ void shift_table_kernel(double k, double hc, int nmax, double* scratc
 
 }  // namespace
 
+// G^s blocks of directly summed point-range pairs (target range x source
+// range, row-major in the target) by quadrature on the panel rule for the
+// pair's largest |X| and its range of Y, each block checked against the
+// node-doubled rule (table_check).  Sets d_vals, nd_vals and the job list;
+// blk[i] = offset of pair i's block.
+hfmm_status build_direct_blocks(hfmm_plan_s* P, const std::vector<DirectSpec>& specs, std::vector<int64_t>& blk,
+                                cudaStream_t st) {
+    HFMM_TRY(ensure_gl());
+    const MedDev md = make_med(P->med);
+    const double qs = P->quad_scale;
+    std::vector<Seg> dsg, dsg2;
+    std::vector<DirectJob> jobs, jobs2;
+    blk.assign(specs.size(), 0);
+    int64_t off = 0;
+    int64_t maxpairs = 0;
+    for (size_t i = 0; i < specs.size(); ++i) {
+        const DirectSpec& sp = specs[i];
+        DirectJob jb;
+        jb.t_lo = sp.t_lo; jb.t_n = sp.t_n;
+        jb.s_lo = sp.s_lo; jb.s_n = sp.s_n;
+        jb.blk = off;
+        DirectJob jb2 = jb;
+        jb.seg0 = (int)dsg.size();
+        std::vector<Seg> tmp;
+        jb.nodes = make_rule(P->med, sp.xmax, sp.ymin, sp.ymax, 0, tmp, qs);
+        for (auto& sgm : tmp) dsg.push_back(sgm);
+        jb.seg1 = (int)dsg.size();
+        tmp.clear();
+        jb2.seg0 = (int)dsg2.size();
+        jb2.nodes = make_rule(P->med, sp.xmax, sp.ymin, sp.ymax, 0, tmp, 2.0 * qs);
+        for (auto& sgm : tmp) dsg2.push_back(sgm);
+        jb2.seg1 = (int)dsg2.size();
+        blk[i] = off;
+        off += (int64_t)jb.t_n * jb.s_n;
+        maxpairs = std::max<int64_t>(maxpairs, (int64_t)jb.t_n * jb.s_n);
+        jobs.push_back(jb);
+        jobs2.push_back(jb2);
+    }
+    P->nd_vals = off;
+    HFMM_TRY(plan_alloc(P, (void**)&P->d_vals, sizeof(cd) * std::max<int64_t>(off, 1)));
+    if (jobs.empty()) return HFMM_OK;
+    Seg* dsegs = nullptr;
+    DirectJob* djobs = nullptr;
+    HFMM_TRY(plan_alloc(P, (void**)&dsegs, sizeof(Seg) * std::max<size_t>(dsg.size(), 1)));
+    HFMM_TRY(plan_alloc(P, (void**)&djobs, sizeof(DirectJob) * jobs.size()));
+    if (!dsg.empty())
+        HFMM_CUDA_TRY(cudaMemcpyAsync(dsegs, dsg.data(), sizeof(Seg) * dsg.size(), cudaMemcpyHostToDevice, st));
+    HFMM_CUDA_TRY(cudaMemcpyAsync(djobs, jobs.data(), sizeof(DirectJob) * jobs.size(), cudaMemcpyHostToDevice, st));
+    if (maxpairs > 0) {
+        direct_block_kernel<<<(unsigned)jobs.size(), 128, 0, st>>>(md, djobs, dsegs, P->xy_sorted, P->d_vals);
+        HFMM_CUDA_TRY(cudaGetLastError());
+        // node-doubled blocks for the check
+        cd* vals2 = nullptr;
+        Seg* dsegs2 = nullptr;
+        DirectJob* djobs2 = nullptr;
+        double* dratio = nullptr;
+        HFMM_TRY(plan_alloc(P, (void**)&vals2, sizeof(cd) * off));
+        HFMM_TRY(plan_alloc(P, (void**)&dsegs2, sizeof(Seg) * std::max<size_t>(dsg2.size(), 1)));
+        HFMM_TRY(plan_alloc(P, (void**)&djobs2, sizeof(DirectJob) * jobs2.size()));
+        HFMM_TRY(plan_alloc(P, (void**)&dratio, sizeof(double) * jobs.size()));
+        if (!dsg2.empty())
+            HFMM_CUDA_TRY(cudaMemcpyAsync(dsegs2, dsg2.data(), sizeof(Seg) * dsg2.size(), cudaMemcpyHostToDevice, st));
+        HFMM_CUDA_TRY(cudaMemcpyAsync(djobs2, jobs2.data(), sizeof(DirectJob) * jobs2.size(), cudaMemcpyHostToDevice, st));
+        direct_block_kernel<<<(unsigned)jobs2.size(), 128, 0, st>>>(md, djobs2, dsegs2, P->xy_sorted, vals2);
+        direct_check_kernel<<<(unsigned)jobs.size(), 128, 0, st>>>(djobs, P->d_vals, vals2, dratio);
+        HFMM_CUDA_TRY(cudaGetLastError());
+        std::vector<double> ratio(jobs.size());
+        HFMM_CUDA_TRY(cudaMemcpyAsync(ratio.data(), dratio, sizeof(double) * ratio.size(), cudaMemcpyDeviceToHost, st));
+        HFMM_CUDA_TRY(cudaStreamSynchronize(st));
+        for (size_t i = 0; i < ratio.size(); ++i) {
+            if (!(ratio[i] <= P->table_check)) {
+                P->table_check = std::isnan(ratio[i]) ? INFINITY : ratio[i];
+                P->table_check_where[0] = -1;      // a directly summed pair
+                P->table_check_where[1] = (int)i;
+                P->table_check_where[2] = 0;
+            }
+        }
+    }
+    P->dj_jobs = djobs;
+    P->dj_segs = dsegs;
+    P->dj_njobs = (int64_t)jobs.size();
+    P->table_bytes += sizeof(cd) * (double)off;
+    return HFMM_OK;
+}
+
 hfmm_status build_tables(hfmm_plan_s* P, cudaStream_t st) {
     HFMM_TRY(ensure_gl());
     const int L = P->L;
@@ -726,91 +811,27 @@ hfmm_status build_tables(hfmm_plan_s* P, cudaStream_t st) {
             }
         }
     }
-    // direct reaction blocks
-    if (P->nd > 0) {
-        const int m = 1 << L;
+    // direct reaction blocks: leaf pairs of the bottom row (adaptive trees build theirs with their lists)
+    if (P->nd > 0 && !P->ad) {
         const double h = P->lev[L].h;
         std::vector<int32_t> dbeg((size_t)P->lev[L].nbox + 1), dsrc(P->nd);
         HFMM_CUDA_TRY(cudaMemcpyAsync(dbeg.data(), P->d_begin, sizeof(int32_t) * dbeg.size(), cudaMemcpyDeviceToHost, st));
         HFMM_CUDA_TRY(cudaMemcpyAsync(dsrc.data(), P->d_src, sizeof(int32_t) * P->nd, cudaMemcpyDeviceToHost, st));
         HFMM_CUDA_TRY(cudaStreamSynchronize(st));
-        std::vector<Seg> dsg, dsg2;
-        std::vector<DirectJob> jobs, jobs2;
-        std::vector<int64_t> blk(P->nd);
-        int64_t off = 0;
-        int maxpairs = 0;
         const auto& lb = P->h_leaf_begin;
-        for (int64_t b = 0; b < P->lev[L].nbox; ++b) {
+        std::vector<DirectSpec> specs;
+        specs.reserve(P->nd);
+        for (int64_t b = 0; b < P->lev[L].nbox; ++b)
             for (int32_t e = dbeg[b]; e < dbeg[b + 1]; ++e) {
                 const int64_t s = dsrc[e];
-                DirectJob jb;
-                jb.t_lo = lb[b]; jb.t_n = lb[b + 1] - lb[b];
-                jb.s_lo = lb[s]; jb.s_n = lb[s + 1] - lb[s];
                 const int dx = (int)morton_x((uint32_t)b) - (int)morton_x((uint32_t)s);
-                const double xmax = (std::abs(dx) + 1) * h;
-                jb.blk = off;
-                DirectJob jb2 = jb;
-                jb.seg0 = (int)dsg.size();
-                std::vector<Seg> tmp;
-                jb.nodes = make_rule(P->med, xmax, 2.0 * P->y0, 2.0 * P->y0 + 2.0 * h, 0, tmp, qs);
-                for (auto& sgm : tmp) dsg.push_back(sgm);
-                jb.seg1 = (int)dsg.size();
-                tmp.clear();
-                jb2.seg0 = (int)dsg2.size();
-                jb2.nodes = make_rule(P->med, xmax, 2.0 * P->y0, 2.0 * P->y0 + 2.0 * h, 0, tmp, 2.0 * qs);
-                for (auto& sgm : tmp) dsg2.push_back(sgm);
-                jb2.seg1 = (int)dsg2.size();
-                blk[e] = off;
-                off += (int64_t)jb.t_n * jb.s_n;
-                maxpairs = std::max(maxpairs, jb.t_n * jb.s_n);
-                jobs.push_back(jb);
-                jobs2.push_back(jb2);
+                specs.push_back({lb[b], lb[b + 1] - lb[b], lb[s], lb[s + 1] - lb[s], (std::abs(dx) + 1) * h,
+                                 2.0 * P->y0, 2.0 * P->y0 + 2.0 * h});
             }
-        }
-        (void)m;
-        P->nd_vals = off;
-        HFMM_TRY(plan_alloc(P, (void**)&P->d_vals, sizeof(cd) * std::max<int64_t>(off, 1)));
+        std::vector<int64_t> blk;
+        HFMM_TRY(build_direct_blocks(P, specs, blk, st));
         HFMM_TRY(plan_alloc(P, (void**)&P->d_blk, sizeof(int64_t) * P->nd));
         HFMM_CUDA_TRY(cudaMemcpyAsync(P->d_blk, blk.data(), sizeof(int64_t) * P->nd, cudaMemcpyHostToDevice, st));
-        Seg* dsegs = nullptr;
-        DirectJob* djobs = nullptr;
-        HFMM_TRY(plan_alloc(P, (void**)&dsegs, sizeof(Seg) * dsg.size()));
-        HFMM_TRY(plan_alloc(P, (void**)&djobs, sizeof(DirectJob) * jobs.size()));
-        HFMM_CUDA_TRY(cudaMemcpyAsync(dsegs, dsg.data(), sizeof(Seg) * dsg.size(), cudaMemcpyHostToDevice, st));
-        HFMM_CUDA_TRY(cudaMemcpyAsync(djobs, jobs.data(), sizeof(DirectJob) * jobs.size(), cudaMemcpyHostToDevice, st));
-        if (maxpairs > 0) {
-            direct_block_kernel<<<(unsigned)jobs.size(), 128, 0, st>>>(md, djobs, dsegs, P->xy_sorted, P->d_vals);
-            HFMM_CUDA_TRY(cudaGetLastError());
-            // node-doubled blocks for the check
-            cd* vals2 = nullptr;
-            Seg* dsegs2 = nullptr;
-            DirectJob* djobs2 = nullptr;
-            double* dratio = nullptr;
-            HFMM_TRY(plan_alloc(P, (void**)&vals2, sizeof(cd) * off));
-            HFMM_TRY(plan_alloc(P, (void**)&dsegs2, sizeof(Seg) * dsg2.size()));
-            HFMM_TRY(plan_alloc(P, (void**)&djobs2, sizeof(DirectJob) * jobs2.size()));
-            HFMM_TRY(plan_alloc(P, (void**)&dratio, sizeof(double) * jobs.size()));
-            HFMM_CUDA_TRY(cudaMemcpyAsync(dsegs2, dsg2.data(), sizeof(Seg) * dsg2.size(), cudaMemcpyHostToDevice, st));
-            HFMM_CUDA_TRY(cudaMemcpyAsync(djobs2, jobs2.data(), sizeof(DirectJob) * jobs2.size(), cudaMemcpyHostToDevice, st));
-            direct_block_kernel<<<(unsigned)jobs2.size(), 128, 0, st>>>(md, djobs2, dsegs2, P->xy_sorted, vals2);
-            direct_check_kernel<<<(unsigned)jobs.size(), 128, 0, st>>>(djobs, P->d_vals, vals2, dratio);
-            HFMM_CUDA_TRY(cudaGetLastError());
-            std::vector<double> ratio(jobs.size());
-            HFMM_CUDA_TRY(cudaMemcpyAsync(ratio.data(), dratio, sizeof(double) * ratio.size(), cudaMemcpyDeviceToHost, st));
-            HFMM_CUDA_TRY(cudaStreamSynchronize(st));
-            for (size_t i = 0; i < ratio.size(); ++i) {
-                if (!(ratio[i] <= P->table_check)) {
-                    P->table_check = std::isnan(ratio[i]) ? INFINITY : ratio[i];
-                    P->table_check_where[0] = -1;      // a directly summed leaf pair
-                    P->table_check_where[1] = (int)i;
-                    P->table_check_where[2] = 0;
-                }
-            }
-        }
-        P->dj_jobs = djobs;
-        P->dj_segs = dsegs;
-        P->dj_njobs = (int64_t)jobs.size();
-        P->table_bytes += sizeof(cd) * (double)off;
     }
     HFMM_CUDA_TRY(cudaStreamSynchronize(st));
     if (!(P->table_check <= TABLE_RTOL)) {

@@ -1,0 +1,161 @@
+"""Adaptive trees (Sec. 3.1, HFMM_FLAG_ADAPTIVE) on the CUDA path against the
+oracle's adaptive H-FMM (oracle/adaptive.py):
+
+* boxes, point sets and the U / V / W / X, reaction and direct lists equal
+  the oracle's as sets of (level, ix, iy) keys;
+* each of the four terms at <= 1e-11 (relative to the full result) against
+  the CPU FMM at equal p, on clustered clouds for the impedance and
+  three-layer media;
+* the whole apply against the O(N^2) direct sum at tol 1e-6 and 1e-10;
+* adjoint, batches and the options that adaptive plans refuse.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from workloads import Medium
+from oracle import adaptive, direct
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1703_09136_gb300 import Batch, HfmmError, MIXED, Plan  # noqa: E402
+
+PARITY_TOL = 1e-11
+CFG4_MED = W.WORKLOADS[4].medium
+
+
+def _near_interface(n, salt):
+    """60% in a Gaussian blob (sigma 0.05) at (0.3, 0.08), redrawn below
+    y = 0.02; 40% uniform in [0, 0.6] x [0.02, 0.62]."""
+    g = np.random.Generator(np.random.PCG64(7000 + salt))
+    n1 = int(0.6 * n)
+    pts = []
+    while len(pts) < n1:
+        c = g.normal((0.3, 0.08), 0.05, size=(n1, 2))
+        c = c[(c[:, 1] >= 0.02) & (c[:, 0] >= 0.0) & (c[:, 0] <= 0.6) & (c[:, 1] <= 0.62)]
+        pts.extend(c.tolist())
+    u = np.stack([g.uniform(0.0, 0.6, n - n1), g.uniform(0.02, 0.62, n - n1)], axis=1)
+    return np.concatenate([np.array(pts[:n1]), u])
+
+
+def _case(name):
+    """(medium, xy, q, tol, leaf)"""
+    if name == "cfg2-clusters":
+        xy = W.points(2, 1200)
+        return W.WORKLOADS[2].medium, xy, W.strengths(2, 1200, 2, salt=41), 1e-6, 12
+    if name == "three-layer-near-interface":
+        xy = _near_interface(700, 2)
+        return CFG4_MED, xy, W.strengths(4, 700, 2, salt=42), 1e-6, 12
+    raise KeyError(name)
+
+
+_cache = {}
+
+
+def _oracle(name):
+    if name not in _cache:
+        med, xy, q, tol, leaf = _case(name)
+        F = adaptive.AdaptiveCpuFmm(xy, med, tol=tol, leaf_size=leaf)
+        _cache[name] = (F, {part: F.apply(q, parts=part) for part in (1, 2, 4, 8)})
+    return _cache[name]
+
+
+def _plan(name, **kw):
+    med, xy, q, tol, leaf = _case(name)
+    return Plan(xy, med, tol=tol, leaf_size=leaf, max_rhs=q.shape[0], adaptive=True, **kw)
+
+
+@pytest.mark.parametrize("name", ["cfg2-clusters", "three-layer-near-interface"])
+def test_adaptive_tree_and_lists_equal_the_oracle(name):
+    F, _ = _oracle(name)
+    med, xy, q, tol, leaf = _case(name)
+    plan = _plan(name)
+    boxes = plan.boxes()
+    perm = plan.perm()
+    inf = plan.info
+    keys = [(int(b[0]), int(b[1]), int(b[2])) for b in boxes]
+    t = F.tree
+    assert set(keys) == set(t.boxes), "boxes"
+    for b, key in zip(boxes, keys):
+        pts = set(perm[b[3]:b[4]].tolist())
+        assert pts == set(t.boxes[key].idx.tolist()), key
+        assert bool(b[5]) == t.boxes[key].leaf, key
+    assert inf["adaptive"] == 1 and inf["levels"] == t.L
+    assert inf["nonempty_leaves"] == len(t.leaves())
+    assert inf["p"] == list(F.p)
+
+    def pairs(kind):
+        return {(keys[a], keys[b]) for a, b in plan.lists(kind)}
+
+    want_u = {(T.key, S.key) for T in t.leaves() for S in F.U[T.key]}
+    want_v = {(k, S.key) for k, vs in F.V.items() for S in vs}
+    want_w = {(T.key, D.key) for T in t.leaves() for D in F.W[T.key]}
+    want_x = {(k, C.key) for k, cs in F.X.items() for C in cs}
+    want_r = {(T.key, S.key) for l in F.R for T, S in F.R[l]}
+    want_d = {(T.key, S.key) for T, S in F.direct_pairs}
+    got = [pairs(k) for k in range(6)]
+    assert got[0] == want_u and got[1] == want_v and got[2] == want_w
+    assert got[3] == want_x and got[4] == want_r and got[5] == want_d
+    assert inf["w_pairs"] == len(want_w) > 0 and inf["x_pairs"] == len(want_x) > 0
+    plan.close()
+
+
+@pytest.mark.parametrize("part", [1, 2, 4, 8])
+@pytest.mark.parametrize("name", ["cfg2-clusters", "three-layer-near-interface"])
+def test_adaptive_terms_match_cpu_fmm(name, part):
+    """Each term (1 U-list H0, 2 free far field with V, W and X, 4 reaction
+    M2L, 8 directly summed reaction) against the oracle's adaptive FMM."""
+    F, parts = _oracle(name)
+    med, xy, q, tol, leaf = _case(name)
+    plan = _plan(name)
+    y = plan.apply(torch.from_numpy(q).cuda(), parts=part).cpu().numpy()
+    plan.close()
+    full = sum(parts.values())
+    err = np.linalg.norm(y - parts[part]) / np.linalg.norm(full)
+    assert err < PARITY_TOL, (name, part, err)
+
+
+@pytest.mark.parametrize("tol", [1e-6, 1e-10])
+def test_adaptive_matches_direct_sum_on_config_2(tol):
+    """Config 2 itself (6400 points, 80% in two Gaussian clusters) with the
+    adaptive tree at tol 1e-6 and 1e-10."""
+    w = W.WORKLOADS[2]
+    xy = W.points(2)
+    q = W.strengths(2, xy.shape[0], 1)
+    yd = direct.direct_apply(w.medium, xy, q)
+    plan = Plan(xy, w.medium, tol=tol, leaf_size=w.leaf, max_rhs=1, adaptive=True)
+    inf = plan.info
+    y = plan.apply(torch.from_numpy(q).cuda()).cpu().numpy()
+    plan.close()
+    assert inf["w_pairs"] > 0 and inf["x_pairs"] > 0
+    assert direct.rel_l2(y, yd) < tol, direct.rel_l2(y, yd)
+
+
+def test_adaptive_adjoint_batch_and_refused_options():
+    med, xy, q, tol, leaf = _case("three-layer-near-interface")
+    plan = _plan("three-layer-near-interface")
+    qd = torch.from_numpy(q).cuda()
+    rng = np.random.default_rng(43)
+    v = rng.standard_normal(q.shape) + 1j * rng.standard_normal(q.shape)
+    Gq = plan.apply(qd).cpu().numpy()
+    GHv = plan.adjoint(torch.from_numpy(v).cuda()).cpu().numpy()
+    assert abs(np.vdot(v, Gq) - np.vdot(GHv, q)) < 1e-12 * abs(np.vdot(v, Gq))
+    with pytest.raises(HfmmError):
+        plan.grad(qd, qd)
+    plan.close()
+    # two adaptive instances through the batch graph equal their single plans
+    xy2 = _near_interface(500, 3)
+    q2 = W.strengths(4, 500, 2, salt=44)
+    b = Batch([xy, xy2], med, tol=tol, leaf_size=leaf, max_rhs=2, adaptive=True)
+    ys = b.apply([qd, torch.from_numpy(q2).cuda()])
+    b.close()
+    for x_, q_, y_ in ((xy, q, ys[0]), (xy2, q2, ys[1])):
+        with Plan(x_, med, tol=tol, leaf_size=leaf, max_rhs=2, adaptive=True) as p1:
+            assert np.array_equal(p1.apply(torch.from_numpy(q_).cuda()).cpu().numpy(), y_.cpu().numpy())
+    with pytest.raises(HfmmError):
+        Plan(xy, med, tol=tol, leaf_size=leaf, precision=MIXED, adaptive=True)
+    with pytest.raises(HfmmError):
+        Plan(xy, med, tol=tol, leaf_size=leaf, autotune=True, adaptive=True)
