@@ -91,6 +91,8 @@ def parse():
                     help="skip the FP64 reference apply (accuracy and one-RHS FP64 time)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--adaptive", action="store_true",
+                    help="FP64 uniform vs adaptive tree on config 2's clusters (N = 6400 .. 262144) and exit")
     ap.add_argument("--diag", action="store_true",
                     help="FP64 diagonal vs dense translations at high frequency (k = 400, 1500) and exit")
     ap.add_argument("--sweep", action="store_true",
@@ -583,6 +585,54 @@ def run_diag(args):
     print(json.dumps(out), flush=True)
 
 
+def run_adaptive(args):
+    """FP64 apply on the uniform tree against the adaptive tree (Sec. 3.1):
+    config 2's clustered distribution (80% in two Gaussian blobs of sigma 0.1)
+    at N = 6400 (config 2 itself), 65,536 and 262,144, and particles on a
+    star-shaped curve (workload 8) at N = 65,536 and 262,144; impedance k = 40,
+    alpha = 20, tol 1e-6, leaf size 32, one right-hand side."""
+    import torch
+    import workloads as W
+    from paper_1703_09136_gb300 import Plan
+    from paper_1703_09136_gb300 import build as _build
+    _build.build()
+    dev = torch.device("cuda", 0)
+    rows = []
+    cases = [(2, n) for n in (6400, 65536, 262144)] + [(8, n) for n in W.WORKLOADS[8].extra["bench_n"]]
+    for cfg, n in cases:
+        w = W.WORKLOADS[cfg]
+        xy = torch.from_numpy(W.points(cfg, n)).to(dev)
+        q = torch.from_numpy(W.strengths(cfg, n, 1)).to(dev)
+        row = {"workload": w.name, "n": n}
+        ys = {}
+        for ad in (False, True):
+            name = "adaptive" if ad else "uniform"
+            t0 = time.perf_counter()
+            plan = Plan(xy, w.medium, tol=w.tol, leaf_size=w.leaf, max_rhs=1, adaptive=ad, profile=True)
+            torch.cuda.synchronize()
+            row[name + "_plan_s"] = time.perf_counter() - t0
+            y = torch.empty_like(q)
+            row[name + "_ms"] = _events_ms(lambda: plan.apply(q, out=y), 5)
+            plan.apply(q, out=y)
+            row[name + "_stage_ms"] = {k: round(v, 4) for k, v in plan.stage_times().items()}
+            inf = plan.info
+            row[name + "_levels"] = inf["levels"]
+            row[name + "_leaves"] = inf["nonempty_leaves"]
+            row[name + "_u_point_pairs"] = inf["u_pairs"]
+            if ad:
+                row["adaptive_w_pairs"], row["adaptive_x_pairs"] = inf["w_pairs"], inf["x_pairs"]
+            ys[ad] = y.clone()
+            plan.close()
+        row["rel_l2_adaptive_vs_uniform"] = float(torch.linalg.norm(ys[True] - ys[False]) / torch.linalg.norm(ys[False]))
+        row["speedup"] = row["uniform_ms"] / row["adaptive_ms"]
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    out = {"metric": "FP64 H-FMM apply time, uniform vs adaptive tree", "unit": "ms",
+           "workloads": [W.WORKLOADS[2].name, W.WORKLOADS[8].name], "medium": "impedance k=40 alpha=20",
+           "tol": 1e-6, "nrhs": 1, "rows": rows}
+    print(json.dumps(out), flush=True)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -926,6 +976,9 @@ def main():
         print(json.dumps(_cpu_child(json.loads(sys.argv[2]))), flush=True)
         return
     args = parse()
+    if args.adaptive:
+        run_adaptive(args)
+        return
     if args.diag:
         run_diag(args)
         return

@@ -59,68 +59,67 @@ __device__ __forceinline__ void ad_centre(double x0, double y0, double h, int ix
     *cy = y0 + (iy + 0.5) * h;
 }
 
-// B[m + p] = J_m(k rho) e^{sgn i m theta}, m = -p .. p, (rho, theta) of (dx, dy); Jt: p + 1 scratch
-__device__ void ad_jbasis(double dx, double dy, double k, int p, int sgn, double* Jt, cd* B) {
+// B[(m + p) sm] = J_m(k rho) e^{sgn i m theta}, m = -p .. p, (rho, theta) of
+// (dx, dy); Jt: p + 1 scratch; sm: elements between consecutive orders.
+__device__ void ad_jbasis(double dx, double dy, double k, int p, int sgn, double* Jt, cd* B, int sm) {
     const double rho = hypot(dx, dy);
     bessel_j_seq(k * rho, p, Jt);
     const cd e1 = cexpi(sgn * atan2(dy, dx));
     cd e = cmk(1.0, 0.0);
-    B[p] = cmk(Jt[0], 0.0);
+    B[p * sm] = cmk(Jt[0], 0.0);
     for (int m = 1; m <= p; ++m) {
         e = cmul(e, e1);
         const double sg = (m & 1) ? -1.0 : 1.0;
-        B[p + m] = cscale(e, Jt[m]);
-        B[p - m] = cscale(cconj(e), sg * Jt[m]);
+        B[(p + m) * sm] = cscale(e, Jt[m]);
+        B[(p - m) * sm] = cscale(cconj(e), sg * Jt[m]);
     }
 }
 
-// M2P basis B[m + p] = H_m(k r) e^{i m theta} and, with p2l = true, the P2L
-// basis B[q + p] = H_{-q}(k r) e^{-i q theta}; (r, theta) of (dx, dy), r > 0;
-// Ht: p + 1 scratch.  H_{-m} = (-1)^m H_m.
-__device__ void ad_hbasis(double dx, double dy, double k, int p, bool p2l, cd* Ht, cd* B) {
+// M2P basis B[(m + p) sm] = H_m(k r) e^{i m theta} and, with p2l = true, the
+// P2L basis B[(q + p) sm] = H_{-q}(k r) e^{-i q theta}; (r, theta) of (dx,
+// dy), r > 0; Ht: p + 1 scratch.  H_{-m} = (-1)^m H_m.
+__device__ void ad_hbasis(double dx, double dy, double k, int p, bool p2l, cd* Ht, cd* B, int sm) {
     hankel_seq(k * hypot(dx, dy), p, Ht);
     const cd e1 = cexpi(atan2(dy, dx));
     cd e = cmk(1.0, 0.0);
-    B[p] = Ht[0];
+    B[p * sm] = Ht[0];
     for (int m = 1; m <= p; ++m) {
         e = cmul(e, e1);                                   // e^{i m theta}
         const double sg = (m & 1) ? -1.0 : 1.0;
         const cd pos = cmul(Ht[m], e);                     // H_m e^{i m theta}
         const cd neg = cscale(cmul(Ht[m], cconj(e)), sg);  // H_{-m} e^{-i m theta}
-        if (p2l) {
-            B[p + m] = neg;                                // q = m:  H_{-m} e^{-i m theta}
-            B[p - m] = pos;                                // q = -m: H_m e^{i m theta}
-        } else {
-            B[p + m] = pos;
-            B[p - m] = neg;
-        }
+        B[(p + m) * sm] = p2l ? neg : pos;
+        B[(p - m) * sm] = p2l ? pos : neg;
     }
 }
 
-// P2M at the listed leaves.  Dynamic smem: chunk * ((2 pmax + 1) cd + (pmax + 1) double).
-__global__ void __launch_bounds__(AD_TB) ad_p2m_kernel(const AdBox* __restrict__ boxes, const int32_t* __restrict__ list,
-                                                       const double2* __restrict__ xs, const cd* __restrict__ qs,
-                                                       int64_t n, int nrhs, double x0, double y0, double k, AdLevels lv,
-                                                       int chunk) {
+// P2M at the listed leaves, one warp per leaf: per pass of up to `chunk`
+// points each lane builds its point's basis (row layout B[t][m]), then the
+// lanes split the (RHS, order) outputs.  Dynamic smem: chunk * ((2 pmax + 1)
+// + pmax + 1) cd.
+__global__ void __launch_bounds__(32) ad_p2m_kernel(const AdBox* __restrict__ boxes, const int32_t* __restrict__ list,
+                                                    const double2* __restrict__ xs, const cd* __restrict__ qs, int64_t n,
+                                                    int nrhs, double x0, double y0, double k, AdLevels lv, int chunk) {
     extern __shared__ double smem[];
     const AdBox b = boxes[list[blockIdx.x]];
+    const int lane = threadIdx.x;
     const int l = b.level, p = lv.p[l], nc = 2 * p + 1;
     cd* B = (cd*)smem;
-    double* Jt = (double*)(B + (size_t)chunk * nc);
+    cd* scr = B + (size_t)chunk * nc;
     double cx, cy;
     ad_centre(x0, y0, lv.h[l], b.ix, b.iy, &cx, &cy);
     cd* out = lv.mult[l] + (int64_t)b.lidx * nrhs * nc;
     const int items = nrhs * nc;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) out[it] = cmk(0.0, 0.0);
+    for (int it = lane; it < items; it += 32) out[it] = cmk(0.0, 0.0);
     for (int32_t c0 = b.lo; c0 < b.hi; c0 += chunk) {
         const int cnt = min(chunk, b.hi - c0);
-        __syncthreads();
-        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-            const double2 pt = xs[c0 + t];
-            ad_jbasis(pt.x - cx, pt.y - cy, k, p, -1, Jt + (size_t)t * (p + 1), B + (size_t)t * nc);
+        __syncwarp();
+        if (lane < cnt) {
+            const double2 pt = xs[c0 + lane];
+            ad_jbasis(pt.x - cx, pt.y - cy, k, p, -1, (double*)(scr + (size_t)lane * (p + 1)), B + (size_t)lane * nc, 1);
         }
-        __syncthreads();
-        for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        __syncwarp();
+        for (int it = lane; it < items; it += 32) {
             const int r = it / nc, m = it % nc;
             cd acc = out[it];
             const cd* qr = qs + (int64_t)r * n + c0;
@@ -210,7 +209,7 @@ __global__ void __launch_bounds__(AD_TB) ad_down_kernel(
             __syncthreads();
             for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
                 const double2 pt = xs[c0 + t];
-                ad_hbasis(cx - pt.x, cy - pt.y, k, p, true, Ht + (size_t)t * (p + 1), B + (size_t)t * nc);
+                ad_hbasis(cx - pt.x, cy - pt.y, k, p, true, Ht + (size_t)t * (p + 1), B + (size_t)t * nc, 1);
             }
             __syncthreads();
             for (int it = threadIdx.x; it < items; it += blockDim.x) {
@@ -224,127 +223,135 @@ __global__ void __launch_bounds__(AD_TB) ad_down_kernel(
     }
 }
 
-// Far field at the points of every leaf: L2P of its local expansion (levels
-// >= lmin) and M2P of its W-list multipoles.  Dynamic smem: chunk * ((2 pmax
-// + 1) + pmax + 1) cd.
-__global__ void __launch_bounds__(AD_TB) ad_leaf_far_kernel(
+// Far field at the points of every leaf, one warp per leaf (lane = point,
+// passes of up to `chunk` points): L2P of its local expansion (levels >=
+// lmin) and M2P of its W-list multipoles.  Each lane builds its point's basis
+// in the column layout B[m][lane] and sums it against the broadcast
+// coefficients.  Dynamic smem: chunk * ((2 pmax + 1) + pmax + 1) cd.
+__global__ void __launch_bounds__(32) ad_leaf_far_kernel(
     const AdBox* __restrict__ boxes, const int32_t* __restrict__ leaves, const int32_t* __restrict__ w_beg,
     const int32_t* __restrict__ w_src, const double2* __restrict__ xs, int64_t n, int nrhs, double x0, double y0,
-    double k, AdLevels lv, int lmin, int lup, int parts, int chunk, cd* __restrict__ ys) {
+    double k, AdLevels lv, int lmin, int parts, int chunk, cd* __restrict__ ys) {
     extern __shared__ double smem[];
-    const int li = blockIdx.x;
+    const int li = blockIdx.x, lane = threadIdx.x;
     const AdBox b = boxes[leaves[li]];
     const bool l2p = b.level >= lmin;
-    const bool m2p = (parts & HFMM_PART_FAR_FREE) && w_beg[li] < w_beg[li + 1];
-    if (!l2p && !m2p) return;
-    const int pmax_here = lv.p[b.level];
+    const int nw = (parts & HFMM_PART_FAR_FREE) ? w_beg[li + 1] - w_beg[li] : 0;
+    if (!l2p && nw == 0) return;
     cd* B = (cd*)smem;
     for (int32_t c0 = b.lo; c0 < b.hi; c0 += chunk) {
         const int cnt = min(chunk, b.hi - c0);
-        const int items = nrhs * cnt;
-        // source 0: the leaf's own local expansion; sources 1..: its W list
-        const int nsrc = 1 + (m2p ? w_beg[li + 1] - w_beg[li] : 0);
-        for (int s = l2p ? 0 : 1; s < nsrc; ++s) {
-            int sl, sp;
+        const bool live = lane < cnt;
+        const double2 pt = live ? xs[c0 + lane] : make_double2(0.0, 0.0);
+        for (int s = l2p ? 0 : 1; s <= nw; ++s) {
+            int sl;
             double cx, cy;
             const cd* coef;
             if (s == 0) {
                 sl = b.level;
-                sp = pmax_here;
                 ad_centre(x0, y0, lv.h[sl], b.ix, b.iy, &cx, &cy);
-                coef = lv.loc[sl] + (int64_t)b.lidx * nrhs * (2 * sp + 1);
+                coef = lv.loc[sl] + (int64_t)b.lidx * nrhs * (2 * lv.p[sl] + 1);
             } else {
                 const AdBox D = boxes[w_src[w_beg[li] + s - 1]];
                 sl = D.level;
-                sp = lv.p[sl];
                 ad_centre(x0, y0, lv.h[sl], D.ix, D.iy, &cx, &cy);
-                coef = lv.mult[sl] + (int64_t)D.lidx * nrhs * (2 * sp + 1);
+                coef = lv.mult[sl] + (int64_t)D.lidx * nrhs * (2 * lv.p[sl] + 1);
             }
-            const int nc = 2 * sp + 1;
-            cd* scr = B + (size_t)chunk * nc;
-            __syncthreads();
-            for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-                const double2 pt = xs[c0 + t];
-                if (s == 0) ad_jbasis(pt.x - cx, pt.y - cy, k, sp, +1, (double*)(scr + (size_t)t * (sp + 1)),
-                                      B + (size_t)t * nc);
-                else ad_hbasis(pt.x - cx, pt.y - cy, k, sp, false, scr + (size_t)t * (sp + 1), B + (size_t)t * nc);
-            }
-            __syncthreads();
-            for (int it = threadIdx.x; it < items; it += blockDim.x) {
-                const int r = it / cnt, t = it % cnt;
-                cd acc = cmk(0.0, 0.0);
-                const cd* cr = coef + (int64_t)r * nc;
-                for (int m = 0; m < nc; ++m) cfma(acc, cr[m], B[(size_t)t * nc + m]);
-                cd* yy = ys + (int64_t)r * n + c0 + t;
-                *yy = cadd(*yy, cmuli(cscale(acc, 0.25)));
+            const int sp = lv.p[sl], nc = 2 * sp + 1;
+            cd* scr = B + (size_t)chunk * nc + (size_t)lane * (sp + 1);
+            __syncwarp();
+            if (live) {
+                if (s == 0) ad_jbasis(pt.x - cx, pt.y - cy, k, sp, +1, (double*)scr, B + lane, chunk);
+                else ad_hbasis(pt.x - cx, pt.y - cy, k, sp, false, scr, B + lane, chunk);
+                for (int r = 0; r < nrhs; ++r) {
+                    cd acc = cmk(0.0, 0.0);
+                    const cd* cr = coef + (int64_t)r * nc;
+                    for (int m = 0; m < nc; ++m) cfma(acc, cr[m], B[(size_t)m * chunk + lane]);
+                    cd* yy = ys + (int64_t)r * n + c0 + lane;
+                    *yy = cadd(*yy, cmuli(cscale(acc, 0.25)));
+                }
             }
         }
     }
 }
 
-// Near field of every leaf: (i/4) H0 over its U list (the self term skipped)
-// and the directly summed reaction blocks of its leaf pairs.
-constexpr int AD_PT = 32;
-__global__ void __launch_bounds__(AD_TB) ad_near_kernel(
-    const AdBox* __restrict__ boxes, const int32_t* __restrict__ leaves, const int32_t* __restrict__ u_beg,
-    const int32_t* __restrict__ u_src, const int32_t* __restrict__ d_beg, const int32_t* __restrict__ d_src,
-    const int64_t* __restrict__ d_blk, const cd* __restrict__ dvals, const double2* __restrict__ xs,
-    const cd* __restrict__ qs, int64_t n, int nrhs, double k, int parts, cd* __restrict__ ys) {
-    __shared__ cd G[AD_PT][AD_PT + 1];
+// Plan time: (i/4) H0(k r) of every U-list pair of every leaf, source-major
+// G[blk + j n_T + i] (0 where the source is the target itself).
+__global__ void ad_near_fill_kernel(const AdBox* __restrict__ boxes, const int32_t* __restrict__ leaves,
+                                    const int32_t* __restrict__ u_beg, const int32_t* __restrict__ u_src,
+                                    const int64_t* __restrict__ u_blk, const double2* __restrict__ xs, double k,
+                                    cd* __restrict__ G) {
     const int li = blockIdx.x;
     const AdBox b = boxes[leaves[li]];
-    const bool nf = (parts & HFMM_PART_NEAR_FREE) != 0, nr = (parts & HFMM_PART_NEAR_REACT) != 0;
-    for (int32_t t0 = b.lo; t0 < b.hi; t0 += AD_PT) {
-        const int tn = min(AD_PT, b.hi - t0);
-        if (nf)
-            for (int32_t e = u_beg[li]; e < u_beg[li + 1]; ++e) {
-                const AdBox S = boxes[u_src[e]];
-                for (int32_t s0 = S.lo; s0 < S.hi; s0 += AD_PT) {
-                    const int sn = min(AD_PT, S.hi - s0);
-                    __syncthreads();
-                    for (int idx = threadIdx.x; idx < tn * sn; idx += blockDim.x) {
-                        const int i = idx / sn, j = idx % sn;
-                        const int32_t ti = t0 + i, sj = s0 + j;
-                        cd g = cmk(0.0, 0.0);
-                        if (ti != sj) {
-                            const double2 a = xs[ti], c = xs[sj];
-                            g = cmuli(cscale(hankel0(k * hypot(a.x - c.x, a.y - c.y)), 0.25));
-                        }
-                        G[i][j] = g;
-                    }
-                    __syncthreads();
-                    for (int it = threadIdx.x; it < nrhs * tn; it += blockDim.x) {
-                        const int r = it / tn, i = it % tn;
-                        cd acc = cmk(0.0, 0.0);
-                        const cd* qr = qs + (int64_t)r * n + s0;
-                        for (int j = 0; j < sn; ++j) cfma(acc, G[i][j], qr[j]);
-                        cd* yy = ys + (int64_t)r * n + t0 + i;
-                        *yy = cadd(*yy, acc);
-                    }
-                }
+    const int tn = b.hi - b.lo;
+    for (int32_t e = u_beg[li]; e < u_beg[li + 1]; ++e) {
+        const AdBox S = boxes[u_src[e]];
+        const int sn = S.hi - S.lo;
+        for (int idx = threadIdx.x; idx < tn * sn; idx += blockDim.x) {
+            const int j = idx / tn, i = idx % tn;
+            cd g = cmk(0.0, 0.0);
+            if (b.lo + i != S.lo + j) {
+                const double2 a = xs[b.lo + i], c = xs[S.lo + j];
+                g = cmuli(cscale(hankel0(k * hypot(a.x - c.x, a.y - c.y)), 0.25));
             }
-        if (nr)
-            for (int32_t e = d_beg[li]; e < d_beg[li + 1]; ++e) {
-                const AdBox S = boxes[d_src[e]];
-                const int sn = S.hi - S.lo, btn = b.hi - b.lo;
-                (void)btn;
-                for (int it = threadIdx.x; it < nrhs * tn; it += blockDim.x) {
-                    const int r = it / tn, i = it % tn;
-                    const cd* Gr = dvals + d_blk[e] + (int64_t)(t0 - b.lo + i) * sn;
-                    const cd* qr = qs + (int64_t)r * n + S.lo;
-                    cd acc = cmk(0.0, 0.0);
-                    for (int j = 0; j < sn; ++j) cfma(acc, Gr[j], qr[j]);
-                    cd* yy = ys + (int64_t)r * n + t0 + i;
-                    *yy = cadd(*yy, acc);
-                }
-            }
+            G[u_blk[e] + (int64_t)j * tn + i] = g;
+        }
     }
 }
 
-int ad_chunk(int pmax) {
-    // (2p + 1) basis values + (p + 1) scratch values of 16 bytes per point in ~40 KB
+// Near field of every leaf, one warp per leaf (four per CTA), lane = target
+// point (passes of 32): (i/4) H0 over its U list, from the plan's blocks when
+// they exist (else evaluated here), and its directly summed reaction blocks.
+__global__ void __launch_bounds__(128) ad_near_kernel(
+    const AdBox* __restrict__ boxes, const int32_t* __restrict__ leaves, int64_t nleaf,
+    const int32_t* __restrict__ u_beg, const int32_t* __restrict__ u_src, const int64_t* __restrict__ u_blk,
+    const cd* __restrict__ G, const int32_t* __restrict__ d_beg, const int32_t* __restrict__ d_src,
+    const int64_t* __restrict__ d_blk, const cd* __restrict__ dvals, const double2* __restrict__ xs,
+    const cd* __restrict__ qs, int64_t n, int nrhs, double k, int parts, cd* __restrict__ ys) {
+    const int64_t li = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (li >= nleaf) return;
+    const int lane = threadIdx.x & 31;
+    const AdBox b = boxes[leaves[li]];
+    const int tn = b.hi - b.lo;
+    const bool nf = (parts & HFMM_PART_NEAR_FREE) != 0, nr = (parts & HFMM_PART_NEAR_REACT) != 0;
+    for (int r = 0; r < nrhs; ++r) {
+        const cd* qr = qs + (int64_t)r * n;
+        for (int i0 = 0; i0 < tn; i0 += 32) {
+            const int i = i0 + lane;
+            if (i >= tn) continue;
+            cd acc = cmk(0.0, 0.0);
+            if (nf)
+                for (int32_t e = u_beg[li]; e < u_beg[li + 1]; ++e) {
+                    const AdBox S = boxes[u_src[e]];
+                    if (G) {
+                        const cd* Ge = G + u_blk[e] + i;
+                        for (int32_t j = 0; j < S.hi - S.lo; ++j) cfma(acc, Ge[(int64_t)j * tn], qr[S.lo + j]);
+                    } else {
+                        const double2 a = xs[b.lo + i];
+                        for (int32_t j = S.lo; j < S.hi; ++j) {
+                            if (j == b.lo + i) continue;
+                            const double2 c = xs[j];
+                            cfma(acc, cmuli(cscale(hankel0(k * hypot(a.x - c.x, a.y - c.y)), 0.25)), qr[j]);
+                        }
+                    }
+                }
+            if (nr)
+                for (int32_t e = d_beg[li]; e < d_beg[li + 1]; ++e) {
+                    const AdBox S = boxes[d_src[e]];
+                    const int sn = S.hi - S.lo;
+                    const cd* Gr = dvals + d_blk[e] + (int64_t)i * sn;
+                    for (int j = 0; j < sn; ++j) cfma(acc, Gr[j], qr[S.lo + j]);
+                }
+            cd* yy = ys + (int64_t)r * n + b.lo + i;
+            *yy = cadd(*yy, acc);
+        }
+    }
+}
+
+int ad_chunk(int pmax, int cap) {
+    // (2p + 1) basis values + (p + 1) scratch values of 16 bytes per point in ~45 KB
     const int per = (2 * pmax + 1) * (int)sizeof(cd) + (pmax + 1) * (int)sizeof(cd);
-    return std::max(1, std::min(32, 40000 / per));
+    return std::max(1, std::min(cap, 45000 / per));
 }
 
 size_t ad_smem(int chunk, int pmax) {
@@ -389,7 +396,11 @@ struct AdaptiveTree {
     std::vector<int64_t> d_blk;
     std::vector<std::pair<int32_t, int32_t>> r_pairs_box, direct_pairs_box;   // (target, source) boxes
     int lup = 0;                              // coarsest level of the upward pass
-    int pmax = 0;
+    int pmax = 0;                             // largest order of any level
+    int pmax_leaf = 0;                        // largest order of a leaf's level or a W box's level
+    std::vector<int64_t> u_blk;               // offset of each U pair's H0 block
+    cd* near_G = nullptr;                     // plan-time H0 blocks (null above the budget)
+    int64_t* du_blk = nullptr;
     // device
     AdBox* d_boxes = nullptr;
     int32_t *dv_beg = nullptr, *dv_src = nullptr, *dv_off = nullptr, *dr_beg = nullptr, *dr_src = nullptr,
@@ -681,6 +692,8 @@ hfmm_status build_adaptive_lists(hfmm_plan_s* P, cudaStream_t st) {
         if (2.0 * P->y0 >= P->S / (double)(1 << l)) { lstar = l; break; }
     P->lstar = lstar;
     for (int l = 0; l <= L; ++l) T->pmax = std::max(T->pmax, P->lev[l].p);
+    for (int32_t b : T->leaves) T->pmax_leaf = std::max(T->pmax_leaf, P->lev[bx[b].level].p);
+    for (int32_t d : T->w_src) T->pmax_leaf = std::max(T->pmax_leaf, P->lev[bx[d].level].p);
     // leaves needing P2M: those of levels >= lup
     std::vector<int32_t> p2m;
     for (int32_t b : T->leaves)
@@ -696,6 +709,18 @@ hfmm_status build_adaptive_lists(hfmm_plan_s* P, cudaStream_t st) {
     }
     P->u_pairs = up;
     P->p2p_point_pairs = pp;
+    // offsets of the U pairs' H0 blocks (n_T x n_S each, source-major)
+    T->u_blk.assign(T->u_src.size(), 0);
+    {
+        int64_t o = 0;
+        for (int64_t li = 0; li < nl; ++li) {
+            const AdBox& B = bx[T->leaves[li]];
+            for (int32_t e = T->u_beg[li]; e < T->u_beg[li + 1]; ++e) {
+                T->u_blk[e] = o;
+                o += (int64_t)(B.hi - B.lo) * (bx[T->u_src[e]].hi - bx[T->u_src[e]].lo);
+            }
+        }
+    }
     P->nd = (int64_t)T->d_src.size();
     // every index the kernels follow stays inside its array (checked before any upload)
     {
@@ -741,6 +766,16 @@ hfmm_status build_adaptive_lists(hfmm_plan_s* P, cudaStream_t st) {
     HFMM_TRY(ad_upload(P, T->u_src, &T->du_src, st));
     HFMM_TRY(ad_upload(P, T->d_beg, &T->dd_beg, st));
     HFMM_TRY(ad_upload(P, T->d_src, &T->dd_src, st));
+    HFMM_TRY(ad_upload(P, T->u_blk, &T->du_blk, st));
+    // the near field's (i/4) H0 blocks, computed once (within the same budget as
+    // the uniform tree's FP64 blocks)
+    if (16.0 * (double)pp <= NEAR64_MAX_BYTES && pp > 0) {
+        HFMM_TRY(plan_alloc(P, (void**)&T->near_G, sizeof(cd) * (size_t)pp));
+        ad_near_fill_kernel<<<(unsigned)nl, 128, 0, st>>>(T->d_boxes, T->d_leaves, T->du_beg, T->du_src, T->du_blk,
+                                                          P->xy_sorted, P->k, T->near_G);
+        HFMM_CUDA_TRY(cudaGetLastError());
+        P->table_bytes += 16.0 * (double)pp;
+    }
     // the specs are kept for the table stage (direct blocks need the sorted points)
     T->d_blk.clear();
     if (!specs.empty()) {
@@ -768,16 +803,18 @@ hfmm_status apply_adaptive(hfmm_plan_s* P, int nrhs, int parts, cudaStream_t st)
         lv.p[l] = P->lev[l].p;
         lv.h[l] = P->lev[l].h;
     }
-    const int chunk = ad_chunk(T->pmax);
+    const int chunk = ad_chunk(T->pmax, 32);             // P2L passes in the downward kernel
     const size_t sm = ad_smem(chunk, T->pmax);
+    const int lchunk = ad_chunk(T->pmax_leaf, 32);       // the warp-per-leaf kernels
+    const size_t lsm = ad_smem(lchunk, T->pmax_leaf);
     const double MAC = 8.0 * nrhs;
     const bool far = (parts & (HFMM_PART_FAR_FREE | HFMM_PART_FAR_REACT)) != 0;
     const int lmin = T->lup;
     if (far) {
         tm.begin(HFMM_STAGE_P2M);
         if (T->n_p2m > 0) {
-            ad_p2m_kernel<<<(unsigned)T->n_p2m, AD_TB, sm, st>>>(T->d_boxes, T->d_p2m, P->xy_sorted, P->q_sorted, n,
-                                                                nrhs, P->x0, P->y0, P->k, lv, chunk);
+            ad_p2m_kernel<<<(unsigned)T->n_p2m, 32, lsm, st>>>(T->d_boxes, T->d_p2m, P->xy_sorted, P->q_sorted, n,
+                                                              nrhs, P->x0, P->y0, P->k, lv, lchunk);
             ++P->launches;
             HFMM_CUDA_TRY(cudaGetLastError());
         }
@@ -807,18 +844,19 @@ hfmm_status apply_adaptive(hfmm_plan_s* P, int nrhs, int parts, cudaStream_t st)
         }
         tm.end(HFMM_STAGE_DOWN);
         tm.begin(HFMM_STAGE_L2P);
-        ad_leaf_far_kernel<<<(unsigned)T->leaves.size(), AD_TB, sm, st>>>(
-            T->d_boxes, T->d_leaves, T->dw_beg, T->dw_src, P->xy_sorted, n, nrhs, P->x0, P->y0, P->k, lv, lmin, lmin,
-            parts, chunk, P->y_sorted);
+        ad_leaf_far_kernel<<<(unsigned)T->leaves.size(), 32, lsm, st>>>(
+            T->d_boxes, T->d_leaves, T->dw_beg, T->dw_src, P->xy_sorted, n, nrhs, P->x0, P->y0, P->k, lv, lmin, parts,
+            lchunk, P->y_sorted);
         ++P->launches;
         HFMM_CUDA_TRY(cudaGetLastError());
         tm.end(HFMM_STAGE_L2P);
     }
     if (parts & (HFMM_PART_NEAR_FREE | HFMM_PART_NEAR_REACT)) {
         tm.begin(HFMM_STAGE_P2P);
-        ad_near_kernel<<<(unsigned)T->leaves.size(), AD_TB, 0, st>>>(
-            T->d_boxes, T->d_leaves, T->du_beg, T->du_src, T->dd_beg, T->dd_src, T->dd_blk, P->d_vals, P->xy_sorted,
-            P->q_sorted, n, nrhs, P->k, parts, P->y_sorted);
+        const int64_t nleaf = (int64_t)T->leaves.size();
+        ad_near_kernel<<<(unsigned)ceil_div(nleaf, 4), 128, 0, st>>>(
+            T->d_boxes, T->d_leaves, nleaf, T->du_beg, T->du_src, T->du_blk, T->near_G, T->dd_beg, T->dd_src, T->dd_blk,
+            P->d_vals, P->xy_sorted, P->q_sorted, n, nrhs, P->k, parts, P->y_sorted);
         ++P->launches;
         HFMM_CUDA_TRY(cudaGetLastError());
         tm.end(HFMM_STAGE_P2P);

@@ -49,6 +49,9 @@ def _case(name):
     if name == "three-layer-near-interface":
         xy = _near_interface(700, 2)
         return CFG4_MED, xy, W.strengths(4, 700, 2, salt=42), 1e-6, 12
+    if name == "star-curve":
+        xy = W.points(8, 1500)
+        return W.WORKLOADS[8].medium, xy, W.strengths(8, 1500, 2, salt=45), 1e-6, 16
     raise KeyError(name)
 
 
@@ -68,7 +71,7 @@ def _plan(name, **kw):
     return Plan(xy, med, tol=tol, leaf_size=leaf, max_rhs=q.shape[0], adaptive=True, **kw)
 
 
-@pytest.mark.parametrize("name", ["cfg2-clusters", "three-layer-near-interface"])
+@pytest.mark.parametrize("name", ["cfg2-clusters", "three-layer-near-interface", "star-curve"])
 def test_adaptive_tree_and_lists_equal_the_oracle(name):
     F, _ = _oracle(name)
     med, xy, q, tol, leaf = _case(name)
@@ -104,7 +107,7 @@ def test_adaptive_tree_and_lists_equal_the_oracle(name):
 
 
 @pytest.mark.parametrize("part", [1, 2, 4, 8])
-@pytest.mark.parametrize("name", ["cfg2-clusters", "three-layer-near-interface"])
+@pytest.mark.parametrize("name", ["cfg2-clusters", "three-layer-near-interface", "star-curve"])
 def test_adaptive_terms_match_cpu_fmm(name, part):
     """Each term (1 U-list H0, 2 free far field with V, W and X, 4 reaction
     M2L, 8 directly summed reaction) against the oracle's adaptive FMM."""

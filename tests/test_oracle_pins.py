@@ -569,15 +569,18 @@ def test_adaptive_lists_cover_every_leaf_pair_once():
     assert all(cover.get((T.key, S.key), 0) == 1 for T in leaves for S in leaves)
 
 
-@pytest.mark.parametrize("case", ["impedance-clusters", "two-layer-clustered", "three-layer-clustered"])
+@pytest.mark.parametrize("case", ["impedance-clusters", "two-layer-clustered", "three-layer-clustered",
+                                  "impedance-star-curve"])
 def test_adaptive_cpu_fmm_matches_direct_sum(case):
     """The adaptive CPU H-FMM (U/V/W/X lists, reaction pairs down to leaves of
     any level) against the O(N^2) direct sum at tol 1e-6 and 1e-10: config 2's
     clusters (impedance) and a blob next to the interface (y >= 0.02) for the
-    two- and three-layer media."""
+    two- and three-layer media, and particles on a star-shaped curve."""
     from oracle import adaptive
     if case == "impedance-clusters":
         med, xy = W.WORKLOADS[2].medium, W.points(2, 1200)
+    elif case == "impedance-star-curve":
+        med, xy = W.WORKLOADS[8].medium, W.points(8, 1000)
     else:
         med = Medium(TWO, (60.0, 90.0)) if case == "two-layer-clustered" else CFG4
         xy = _clustered_near_interface(700, 1)

@@ -81,6 +81,11 @@ WORKLOADS = {
     7: Workload("impedance-unit-box-high-frequency", Medium(IMPEDANCE, (400.0,), alpha=200.0),
                 0, ((0.0, 1.0), (0.05, 1.05)), 1, 1e-6, 32, "uniform",
                 {"cases": ((400.0, 65536), (1500.0, 65536), (1500.0, 262144))}),
+    # particles on the surface of a scatterer (a five-lobed star curve in
+    # config 1's box): the setting the paper's adaptive tree is made for
+    8: Workload("impedance-star-curve-k40", Medium(IMPEDANCE, (40.0,), alpha=20.0),
+                65536, ((0.0, 1.0), (0.05, 1.05)), 1, 1e-6, 32, "curve",
+                {"centre": (0.5, 0.55), "R": 0.3, "a": 0.3, "lobes": 5, "bench_n": (65536, 262144)}),
 }
 
 
@@ -116,6 +121,17 @@ def _clusters(g, n, box):
     return xy[g.permutation(n)]
 
 
+def _curve(g, n, extra):
+    """Points on the closed star curve r(t) = R (1 + a cos(m t)) about c,
+    equally spaced in t with a uniform jitter of a quarter spacing: the
+    surface of a scatterer discretised into particles."""
+    cx, cy = extra["centre"]
+    R, a, m = extra["R"], extra["a"], extra["lobes"]
+    t = (np.arange(n) + 0.25 * g.uniform(-1.0, 1.0, n)) * (2.0 * math.pi / n)
+    r = R * (1.0 + a * np.cos(m * t))
+    return np.stack([cx + r * np.cos(t), cy + r * np.sin(t)], axis=1)
+
+
 def points(cfg: int, n: int | None = None, salt: int = 0) -> np.ndarray:
     """Point cloud [n, 2] (float64) of workload ``cfg``; ``n`` overrides the size."""
     w = WORKLOADS[cfg]
@@ -123,6 +139,8 @@ def points(cfg: int, n: int | None = None, salt: int = 0) -> np.ndarray:
     g = generator(cfg, 1, salt)
     if w.dist == "clusters":
         return _clusters(g, n, w.box)
+    if w.dist == "curve":
+        return _curve(g, n, w.extra)
     return _uniform(g, n, w.box)
 
 
