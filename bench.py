@@ -585,6 +585,35 @@ def run_diag(args):
     print(json.dumps(out), flush=True)
 
 
+def measure_adaptive(dev):
+    """Uniform against adaptive tree (FP64, 1 RHS, tol 1e-6) on config 2
+    itself (6400 clustered points) and on 65,536 particles of the star curve:
+    apply times, tree depths, and the two results' difference."""
+    import torch
+    import workloads as W
+    from paper_1703_09136_gb300 import Plan
+    out = {}
+    for cfg, n in ((2, 6400), (8, 65536)):
+        w = W.WORKLOADS[cfg]
+        xy = torch.from_numpy(W.points(cfg, n)).to(dev)
+        q = torch.from_numpy(W.strengths(cfg, n, 1)).to(dev)
+        row, ys = {"n": n}, {}
+        for ad in (False, True):
+            name = "adaptive" if ad else "uniform"
+            plan = Plan(xy, w.medium, tol=w.tol, leaf_size=w.leaf, max_rhs=1, adaptive=ad)
+            y = torch.empty_like(q)
+            row[name + "_ms"] = _events_ms(lambda: plan.apply(q, out=y), 5)
+            plan.apply(q, out=y)
+            inf = plan.info
+            row[name + "_levels"], row[name + "_leaves"] = inf["levels"], inf["nonempty_leaves"]
+            ys[ad] = y.clone()
+            plan.close()
+        row["rel_l2_adaptive_vs_uniform"] = float(torch.linalg.norm(ys[True] - ys[False]) / torch.linalg.norm(ys[False]))
+        row["speedup"] = row["uniform_ms"] / row["adaptive_ms"]
+        out[w.name] = row
+    return out
+
+
 def run_adaptive(args):
     """FP64 apply on the uniform tree against the adaptive tree (Sec. 3.1):
     config 2's clustered distribution (80% in two Gaussian blobs of sigma 0.1)
@@ -809,7 +838,8 @@ def run_ours(args):
     if not args.no_extra and cfg == 4 and n == w.n and nrhs == w.nrhs and not args.box:
         # the other full-size workloads, measured in the same run on the same GPU
         out["workloads"] = {"two-layer-262144-1rhs": measure_two_layer(dev, 20, cpu=rank == 0 and not args.no_cpu_baseline),
-                            "impedance-batch32-1rhs": measure_batch(dev, 20, cpu=rank == 0 and not args.no_cpu_baseline)}
+                            "impedance-batch32-1rhs": measure_batch(dev, 20, cpu=rank == 0 and not args.no_cpu_baseline),
+                            "adaptive-tree-fp64": measure_adaptive(dev)}
     if rank == 0 and not args.no_cpu_baseline:
         s = cpu_oracle_sample(cfg, nrhs, reps=2, n=args.cpu_sample_n)
         t_apply = s["apply_s"][-1]
