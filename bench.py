@@ -93,6 +93,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--adaptive", action="store_true",
                     help="FP64 uniform vs adaptive tree on config 2's clusters (N = 6400 .. 262144) and exit")
+    ap.add_argument("--cases", default="",
+                    help="--adaptive: workload:n pairs (e.g. 8:65536); --diag: k:n pairs (e.g. 1500:65536)")
     ap.add_argument("--diag", action="store_true",
                     help="FP64 diagonal vs dense translations at high frequency (k = 400, 1500) and exit")
     ap.add_argument("--sweep", action="store_true",
@@ -552,7 +554,10 @@ def run_diag(args):
     w = W.WORKLOADS[7]
     dev = torch.device("cuda", 0)
     rows = []
-    for k, n in w.extra["cases"]:
+    cases = w.extra["cases"]
+    if args.cases:
+        cases = [(float(c.split(":")[0]), int(c.split(":")[1])) for c in args.cases.split(",")]
+    for k, n in cases:
         med = W.Medium(W.IMPEDANCE, (k,), alpha=k / 2)
         xy = torch.from_numpy(W.points_in_box(7, n, w.box)).to(dev)
         q = torch.from_numpy(W.strengths(7, n, 1)).to(dev)
@@ -628,6 +633,8 @@ def run_adaptive(args):
     dev = torch.device("cuda", 0)
     rows = []
     cases = [(2, n) for n in (6400, 65536, 262144)] + [(8, n) for n in W.WORKLOADS[8].extra["bench_n"]]
+    if args.cases:
+        cases = [tuple(int(v) for v in c.split(":")) for c in args.cases.split(",")]
     for cfg, n in cases:
         w = W.WORKLOADS[cfg]
         xy = torch.from_numpy(W.points(cfg, n)).to(dev)

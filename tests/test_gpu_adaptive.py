@@ -162,3 +162,33 @@ def test_adaptive_adjoint_batch_and_refused_options():
         Plan(xy, med, tol=tol, leaf_size=leaf, precision=MIXED, adaptive=True)
     with pytest.raises(HfmmError):
         Plan(xy, med, tol=tol, leaf_size=leaf, autotune=True, adaptive=True)
+
+
+@pytest.mark.parametrize("case", ["n1", "n2", "n3", "n33", "collinear", "depth-cap"])
+def test_adaptive_edge_cases_match_direct_sum(case):
+    """Tiny and degenerate inputs on the adaptive tree against the direct
+    sum: 1, 2, 3 and 33 points; 400 points on one horizontal line (the root
+    square from the x extent); 60 points packed within 1e-9 of each other
+    beside 300 spread ones, so boxes reach the depth cap (level 16) still
+    holding more than leaf_size points and stay leaves."""
+    med = W.WORKLOADS[1].medium
+    g = np.random.Generator(np.random.PCG64(9100))
+    if case.startswith("n"):
+        n = int(case[1:])
+        xy = W.points(1, n, salt=9)
+    elif case == "collinear":
+        xy = np.stack([np.linspace(0.0, 1.0, 400) + 1e-4 * g.uniform(-1, 1, 400), np.full(400, 0.3)], axis=1)
+    else:
+        base = W.points(1, 300, salt=10)
+        tight = np.array([0.41, 0.57]) + 1e-9 * g.uniform(-1, 1, (60, 2))
+        xy = np.concatenate([base, tight])
+    q = W.strengths(1, xy.shape[0], 2, salt=11)
+    yd = direct.direct_apply(med, xy, q)
+    plan = Plan(xy, med, tol=1e-10, leaf_size=8, max_rhs=2, adaptive=True)
+    inf = plan.info
+    # host buffers (staged through the plan's device buffers)
+    y = plan.apply(q)
+    plan.close()
+    if case == "depth-cap":
+        assert inf["levels"] == 16
+    assert direct.rel_l2(y, yd) < 1e-9, (case, direct.rel_l2(y, yd))
