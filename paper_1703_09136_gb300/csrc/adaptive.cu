@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(AD_TB) ad_m2m_kernel(const AdBox* __restrict__
     const int pc = lv.p[l + 1], pp = lv.p[l];
     const int nc = 2 * pc + 1, np = 2 * pp + 1, nmax = pc + pp, w = 2 * nmax + 1;
     const int items = nrhs * np;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    for (int it = blockIdx.y * blockDim.x + threadIdx.x; it < items; it += gridDim.y * blockDim.x) {
         const int r = it / np, j = it % np - pp;
         cd acc = cmk(0.0, 0.0);
         for (int c = 0; c < 4; ++c) {
@@ -167,7 +167,9 @@ __global__ void __launch_bounds__(AD_TB) ad_down_kernel(
     const int items = nrhs * nc;
     cd* out = lv.loc[l] + (int64_t)b.lidx * nrhs * nc;
     const bool ff = (parts & HFMM_PART_FAR_FREE) != 0, fr = (parts & HFMM_PART_FAR_REACT) != 0;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    // blockIdx.y splits the box's outputs over several CTAs (coarse levels have few
+    // boxes); each thread keeps the same outputs in both phases
+    for (int it = blockIdx.y * blockDim.x + threadIdx.x; it < items; it += gridDim.y * blockDim.x) {
         const int r = it / nc, q = it % nc - p;
         cd acc = cmk(0.0, 0.0);
         if (l > lmin && b.parent >= 0) {
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(AD_TB) ad_down_kernel(
                 ad_hbasis(cx - pt.x, cy - pt.y, k, p, true, Ht + (size_t)t * (p + 1), B + (size_t)t * nc, 1);
             }
             __syncthreads();
-            for (int it = threadIdx.x; it < items; it += blockDim.x) {
+            for (int it = blockIdx.y * blockDim.x + threadIdx.x; it < items; it += gridDim.y * blockDim.x) {
                 const int r = it / nc, q = it % nc;
                 cd acc = out[it];
                 const cd* qr = qs + (int64_t)r * n + c0;
@@ -352,6 +354,15 @@ int ad_chunk(int pmax, int cap) {
     // (2p + 1) basis values + (p + 1) scratch values of 16 bytes per point in ~45 KB
     const int per = (2 * pmax + 1) * (int)sizeof(cd) + (pmax + 1) * (int)sizeof(cd);
     return std::max(1, std::min(cap, 45000 / per));
+}
+
+// CTAs per box for a level of nbox boxes with `items` outputs each (see the
+// uniform FP64 kernels): spread levels with few boxes over the GPU.
+unsigned ad_split(int64_t nbox, int items) {
+    if (nbox >= 2048) return 1;
+    const int64_t by_items = (items + AD_TB - 1) / AD_TB;
+    const int64_t by_grid = (2048 + nbox - 1) / nbox;
+    return (unsigned)std::max<int64_t>(1, std::min(by_items, by_grid));
 }
 
 size_t ad_smem(int chunk, int pmax) {
@@ -822,7 +833,8 @@ hfmm_status apply_adaptive(hfmm_plan_s* P, int nrhs, int parts, cudaStream_t st)
         tm.begin(HFMM_STAGE_M2M);
         for (int l = L - 1; l >= lmin; --l) {
             const LevelInfo& v = P->lev[l];
-            ad_m2m_kernel<<<(unsigned)v.nbox, AD_TB, 0, st>>>(T->d_boxes, T->lev_off[l], l, v.t_m2m, lv, nrhs);
+            ad_m2m_kernel<<<dim3((unsigned)v.nbox, ad_split(v.nbox, nrhs * v.ncoef)), AD_TB, 0, st>>>(
+                T->d_boxes, T->lev_off[l], l, v.t_m2m, lv, nrhs);
             ++P->launches;
             HFMM_CUDA_TRY(cudaGetLastError());
             P->st_flops[HFMM_STAGE_M2M] += MAC * 4.0 * v.nbox * v.ncoef * P->lev[l + 1].ncoef;
@@ -831,7 +843,7 @@ hfmm_status apply_adaptive(hfmm_plan_s* P, int nrhs, int parts, cudaStream_t st)
         tm.begin(HFMM_STAGE_DOWN);
         for (int l = lmin; l <= L; ++l) {
             const LevelInfo& v = P->lev[l];
-            ad_down_kernel<<<(unsigned)v.nbox, AD_TB, sm, st>>>(
+            ad_down_kernel<<<dim3((unsigned)v.nbox, ad_split(v.nbox, nrhs * v.ncoef)), AD_TB, sm, st>>>(
                 T->d_boxes, T->lev_off[l], l, lmin, nrhs, lv, l > lmin ? P->lev[l - 1].t_l2l : nullptr, T->dv_beg,
                 T->dv_src, T->dv_off, v.t_free, T->dr_beg, T->dr_src, T->dr_tab, v.t_react, T->dx_beg, T->dx_src,
                 P->xy_sorted, P->q_sorted, n, P->x0, P->y0, P->k, parts, chunk);

@@ -21,6 +21,16 @@ namespace {
 
 constexpr int TB = 128;
 
+// CTAs per box for the per-box translation kernels: enough to spread a level
+// with few boxes over the GPU (FP64 throughput is per SM), one where the
+// level alone fills it.
+inline unsigned box_split(int64_t nbox, int items) {
+    if (nbox >= 2048) return 1;
+    const int64_t by_items = (items + TB - 1) / TB;
+    const int64_t by_grid = (2048 + nbox - 1) / nbox;
+    return (unsigned)std::max<int64_t>(1, std::min(by_items, by_grid));
+}
+
 __global__ void gather_q(const cd* q, const int64_t* perm, int64_t n, int nrhs, bool conj_in,
                          cd* qs) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -100,7 +110,8 @@ __global__ void m2m_kernel(const cd* child, const cd* T, int pc, int pp, int nrh
     const int64_t b = blockIdx.x;
     const int nc = 2 * pc + 1, np = 2 * pp + 1, nmax = pc + pp, w = 2 * nmax + 1;
     const int items = nrhs * np;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    // blockIdx.y splits a box's outputs over several CTAs (coarse levels have few boxes)
+    for (int it = blockIdx.y * blockDim.x + threadIdx.x; it < items; it += gridDim.y * blockDim.x) {
         const int r = it / np, j = it % np - pp;
         cd acc = cmk(0.0, 0.0);
         for (int c = 0; c < 4; ++c) {
@@ -127,7 +138,7 @@ __global__ void downward_kernel(const int32_t* lb, int L, int l, int lmin, int n
     const int nc = 2 * p + 1;
     const int items = nrhs * nc;
     const int wf = 4 * p + 1;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    for (int it = blockIdx.y * blockDim.x + threadIdx.x; it < items; it += gridDim.y * blockDim.x) {
         const int r = it / nc, q = it % nc - p;
         cd acc = cmk(0.0, 0.0);
         if (l > lmin && ploc) {
@@ -370,7 +381,7 @@ int pick_chunk(int p) {
 // loc (used by the plan-time check of the diagonal form).
 hfmm_status down64_lists(hfmm_plan_s* P, int l, int nrhs, const cd* mult, cd* loc, cudaStream_t st) {
     LevelInfo& lv = P->lev[l];
-    downward_kernel<<<(unsigned)lv.nbox, TB, 0, st>>>(P->leaf_begin, P->L, l, l, nrhs, lv.p, 0, nullptr, nullptr, mult,
+    downward_kernel<<<dim3((unsigned)lv.nbox, box_split(lv.nbox, nrhs * lv.ncoef)), TB, 0, st>>>(P->leaf_begin, P->L, l, l, nrhs, lv.p, 0, nullptr, nullptr, mult,
                                                      lv.nv ? lv.v_begin : nullptr, lv.v_src, lv.v_off, lv.t_free,
                                                      lv.nr ? lv.r_begin : nullptr, lv.r_src, lv.r_tab, lv.t_react,
                                                      HFMM_PART_ALL, loc);
@@ -416,7 +427,7 @@ hfmm_status apply_fp64(hfmm_plan_s* P, int nrhs, const cd* q, cd* y, int parts, 
             tm.begin(HFMM_STAGE_M2M);
             for (int l = L - 1; l >= P->lmin; --l) {
                 LevelInfo& lv = P->lev[l];
-                m2m_kernel<<<(unsigned)lv.nbox, TB, 0, st>>>(P->lev[l + 1].mult, lv.t_m2m, P->lev[l + 1].p, lv.p,
+                m2m_kernel<<<dim3((unsigned)lv.nbox, box_split(lv.nbox, nrhs * lv.ncoef)), TB, 0, st>>>(P->lev[l + 1].mult, lv.t_m2m, P->lev[l + 1].p, lv.p,
                                                             nrhs, lv.mult);
                 ++P->launches;
                 HFMM_CUDA_TRY(cudaGetLastError());
@@ -431,7 +442,7 @@ hfmm_status apply_fp64(hfmm_plan_s* P, int nrhs, const cd* q, cd* y, int parts, 
                 LevelInfo& lv = P->lev[l];
                 const bool has_parent = l > P->lmin;
                 const bool dg = lv.diag_logq > 0;   // translations in diagonal form after the L2L
-                downward_kernel<<<(unsigned)lv.nbox, TB, 0, st>>>(
+                downward_kernel<<<dim3((unsigned)lv.nbox, box_split(lv.nbox, nrhs * lv.ncoef)), TB, 0, st>>>(
                     P->leaf_begin, L, l, P->lmin, nrhs, lv.p, has_parent ? P->lev[l - 1].p : 0,
                     has_parent ? P->lev[l - 1].loc : nullptr, has_parent ? P->lev[l - 1].t_l2l : nullptr,
                     lv.mult, lv.nv && !dg ? lv.v_begin : nullptr, lv.v_src, lv.v_off, lv.t_free,
@@ -787,7 +798,7 @@ hfmm_status field_grad_fp64(hfmm_plan_s* P, int nrhs, cd* fx, cd* fy, cudaStream
     }
     for (int l = L - 1; l >= P->lmin; --l) {
         LevelInfo& lv = P->lev[l];
-        m2m_kernel<<<(unsigned)lv.nbox, TB, 0, st>>>(P->lev[l + 1].mult, lv.t_m2m, P->lev[l + 1].p, lv.p, nrhs, lv.mult);
+        m2m_kernel<<<dim3((unsigned)lv.nbox, box_split(lv.nbox, nrhs * lv.ncoef)), TB, 0, st>>>(P->lev[l + 1].mult, lv.t_m2m, P->lev[l + 1].p, lv.p, nrhs, lv.mult);
         HFMM_CUDA_TRY(cudaGetLastError());
         if (lv.diag_logq) HFMM_TRY(diag_src(P, l, nrhs, st));
     }
@@ -795,7 +806,7 @@ hfmm_status field_grad_fp64(hfmm_plan_s* P, int nrhs, cd* fx, cd* fy, cudaStream
         LevelInfo& lv = P->lev[l];
         const bool has_parent = l > P->lmin;
         const bool dg = lv.diag_logq > 0;
-        downward_kernel<<<(unsigned)lv.nbox, TB, 0, st>>>(
+        downward_kernel<<<dim3((unsigned)lv.nbox, box_split(lv.nbox, nrhs * lv.ncoef)), TB, 0, st>>>(
             P->leaf_begin, L, l, P->lmin, nrhs, lv.p, has_parent ? P->lev[l - 1].p : 0,
             has_parent ? P->lev[l - 1].loc : nullptr, has_parent ? P->lev[l - 1].t_l2l : nullptr, lv.mult,
             lv.nv && !dg ? lv.v_begin : nullptr, lv.v_src, lv.v_off, lv.t_free, lv.nr && !dg ? lv.r_begin : nullptr,
