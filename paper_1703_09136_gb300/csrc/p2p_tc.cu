@@ -17,7 +17,10 @@
 // cp.async.bulk (prefetched into L2 a few chunks ahead); warps 0-3 build the
 // A rows of each chunk from the strengths, each right-hand side scaled by the
 // power of two that puts its largest |Re q|, |Im q| (reduced by the gather
-// kernel) in [2^14, 2^15), and split into f16 hi / lo; warp 5 issues three
+// kernel) in [2^14, 2^15), and split into f16 hi / lo, each thread writing
+// one 16-byte core-matrix row per part (4-byte stores in this layout conflict
+// on the shared-memory banks, and the build, not the tile stream or the MMAs,
+// paces the pass); warp 5 issues three
 // kind::f16 MMAs (hi*hi + hi*lo + lo*hi: 22 significant bits, like a TF32
 // pair) per run of adjacent target leaves into one 128-column TMEM
 // accumulator; warps 0-3 finally undo both scales and store y (point-major,
@@ -48,21 +51,6 @@ constexpr size_t NT_SMEM = (size_t)NT_STAGES * NT_STAGE + 1024;
 // half offset of (row, k) in a core-matrix tile (K = 16)
 __device__ __forceinline__ int core_off(int row, int k) {
     return ((row >> 3) * 2 + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
-}
-
-// A operand: the complex value v (already scaled) of (K pair j, right-hand
-// side r) into rows r (Re v, Im v) and 64 + r (Im v, -Re v), K columns 2j,
-// 2j + 1, f16 hi and lo parts (lo 2048 halves after hi).
-__device__ __forceinline__ void put_a(uint16_t* A, int j, int r, cf v) {
-    uint16_t rh, rl, ih, il, nrh, nrl;
-    split_f16(v.x, rh, rl);
-    split_f16(v.y, ih, il);
-    split_f16(-v.x, nrh, nrl);
-    const int o0 = core_off(r, 2 * j), o1 = core_off(64 + r, 2 * j);
-    *(uint32_t*)(A + o0) = (uint32_t)rh | ((uint32_t)ih << 16);
-    *(uint32_t*)(A + 2048 + o0) = (uint32_t)rl | ((uint32_t)il << 16);
-    *(uint32_t*)(A + o1) = (uint32_t)ih | ((uint32_t)nrh << 16);
-    *(uint32_t*)(A + 2048 + o1) = (uint32_t)il | ((uint32_t)nrl << 16);
 }
 
 struct NtSmall {
@@ -142,13 +130,16 @@ __global__ void __launch_bounds__(NT_THREADS, 4) p2p_tc_kernel(
         // the power of two of each right-hand side (rows r and 64 + r share it)
         const int rr_own = tid & 63;
         const int e_own = (r0 + rr_own < nrhs) ? f16_exp(__uint_as_float(qmax[r0 + rr_own])) : 0;
+        // thread tid builds row r = tid & 63 (and row 64 + r) for the chunk's
+        // sources 4 g .. 4 g + 3, g = tid >> 6: one 16-byte core-matrix row per part
+        const int g4 = 4 * (tid >> 6);
         auto fetch = [&](int i, cf* out) {
             const NtChunk& ch = S.ch[i];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int e = tid + 128 * u, j = e >> 6, r = e & 63;
+                const int j = g4 + u;
                 cf v = cfmk(0.f, 0.f);
-                if (r0 + r < nrhs && j < ch.cnt) v = qs[(int64_t)(ch.src + j) * nrhs + r0 + r];
+                if (r0 + rr_own < nrhs && j < ch.cnt) v = qs[(int64_t)(ch.src + j) * nrhs + r0 + rr_own];
                 out[u] = v;
             }
         };
@@ -165,10 +156,25 @@ __global__ void __launch_bounds__(NT_THREADS, 4) p2p_tc_kernel(
             if (!good) { s_abort = 1; break; }
             if (i + 2 < nch) fetch(i + 2, pn);
             uint16_t* A = (uint16_t*)(smem + stg * NT_STAGE);
+            {
+                // rows r: (Re q, Im q); rows 64 + r: (Im q, -Re q) (the split of -x is
+                // the negated split of x); K columns 2j, 2j + 1 of source j
+                uint16_t h0[8], l0[8], h1[8], l1[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int e = tid + 128 * u;
-                put_a(A, e >> 6, e & 63, cfmk(pa[u].x * qs_scale, pa[u].y * qs_scale));
+                for (int u = 0; u < 4; ++u) {
+                    uint16_t rh, rl, ih, il;
+                    split_f16(pa[u].x * qs_scale, rh, rl);
+                    split_f16(pa[u].y * qs_scale, ih, il);
+                    h0[2 * u] = rh; h0[2 * u + 1] = ih;
+                    l0[2 * u] = rl; l0[2 * u + 1] = il;
+                    h1[2 * u] = ih; h1[2 * u + 1] = (uint16_t)(rh ^ 0x8000u);
+                    l1[2 * u] = il; l1[2 * u + 1] = (uint16_t)(rl ^ 0x8000u);
+                }
+                const int o0 = core_off(rr_own, g4 * 2), o1 = core_off(64 + rr_own, g4 * 2);
+                *(uint4*)(A + o0) = pack8(h0);
+                *(uint4*)(A + 2048 + o0) = pack8(l0);
+                *(uint4*)(A + o1) = pack8(h1);
+                *(uint4*)(A + 2048 + o1) = pack8(l1);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(&afull[stg]);
