@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(NT_THREADS, 4) p2p_tc_kernel(
         }
         S.off[4] = o;
         for (int s = 0; s < NT_STAGES; ++s) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(&afull[s])), "r"(128));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(&afull[s])), "r"(4));   // a warp each
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(&bfull[s])), "r"(1));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(&empty[s])), "r"(1));
         }
@@ -177,7 +177,8 @@ __global__ void __launch_bounds__(NT_THREADS, 4) p2p_tc_kernel(
                 *(uint4*)(A + 2048 + o1) = pack8(l1);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(&afull[stg]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&afull[stg]);
 #pragma unroll
             for (int u = 0; u < 4; ++u) { pa[u] = pb[u]; pb[u] = pn[u]; }
         }
