@@ -78,12 +78,14 @@ struct TcCfg {
 constexpr int TC_MAX_NP = 128;         // widest column block (one 128-column TMEM buffer)
 
 // Shared memory of the leaf L2P in the downward epilogue, per drain warp: its
-// 32 rows of beta~ (stride NB + 1), the basis rows of 8 points and its rows of
-// y for them; used only where the four warps' regions fit the ring.
+// 32 rows of beta~ (stride NB + 1) and two buffers of the basis rows of 8
+// points and its rows of y for them (the next pass's data arrive while this
+// pass computes); used only where the four warps' regions fit the ring.
 template <int NB>
 struct TcL2p {
     static constexpr int pts = 8;
-    static constexpr int warp_bytes = 32 * (NB + 1) * 4 + pts * (NB / 2) * 8 + pts * 32 * 8;
+    static constexpr int buf = pts * (NB / 2) * 8 + pts * 32 * 8;
+    static constexpr int warp_bytes = 32 * (NB + 1) * 4 + 2 * buf;
     static constexpr bool fits = 4 * warp_bytes <= TcCfg<NB>::stages * TcCfg<NB>::stage_bytes;
 };
 
@@ -348,27 +350,40 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
                     if (TcL2p<NB>::fits && l2p_basis) {
                         // L2P of the leaf (Algorithm 1, step 4), one column block:
                         // y[t][r] += sum_m beta~[r][m] (i/4) conj(B[t][m]) over the leaf's
-                        // points t.  Per 8 points the warp brings the basis rows and its rows
-                        // of y into the ring (asynchronous copies, all in flight together);
-                        // the sum reads beta~ by row and the basis as broadcasts, eight points
-                        // per pass (each beta~ load feeds 32 FMAs).
+                        // points t, eight points per pass.  The basis rows and this
+                        // warp's rows of y of the next pass are copied (cp.async, second
+                        // buffer) while this pass computes; the sum reads beta~ by row and
+                        // the basis as broadcasts (each beta~ load feeds 32 FMAs).
                         constexpr int TCH = TcL2p<NB>::pts;
-                        cf* sbs = (cf*)(bet + 32 * (NB + 1));
-                        cf* sy = sbs + TCH * (NB / 2);
+                        unsigned char* bufs = (unsigned char*)(bet + 32 * (NB + 1));
                         const float* br = bet + lane * (NB + 1);   // Re beta~_m at m, Im at nc + m
                         const int r = rc * 64 + (row & 63);
                         const bool live = r < nrhs;
                         const int32_t t0 = lbeg[box], t1 = lbeg[box + 1];
-                        for (int32_t tc0 = t0; tc0 < t1; tc0 += TCH) {
+                        auto issue = [&](int32_t tc0, int k) {
+                            cf* sbs = (cf*)(bufs + (k & 1) * TcL2p<NB>::buf);
+                            cf* sy = sbs + TCH * (NB / 2);
                             const int tn = min(TCH, t1 - tc0);
-                            __syncwarp();
                             for (int e = lane; e < tn * nc; e += 32)
                                 cp_async8(sbs + e, l2p_basis + (int64_t)tc0 * nc + e);
                             if (live)
                                 for (int t = 0; t < tn; ++t)
                                     cp_async8(sy + t * 32 + lane, ys + (int64_t)(tc0 + t) * nrhs + r);
-                            cp_async_wait_all();
+                            asm volatile("cp.async.commit_group;" ::: "memory");
+                        };
+                        if (t0 < t1) issue(t0, 0);
+                        int kk = 0;
+                        for (int32_t tc0 = t0; tc0 < t1; tc0 += TCH, ++kk) {
+                            const int tn = min(TCH, t1 - tc0);
+                            if (tc0 + TCH < t1) {
+                                issue(tc0 + TCH, kk + 1);
+                                asm volatile("cp.async.wait_group 1;" ::: "memory");
+                            } else {
+                                asm volatile("cp.async.wait_group 0;" ::: "memory");
+                            }
                             __syncwarp();
+                            const cf* sbs = (const cf*)(bufs + (kk & 1) * TcL2p<NB>::buf);
+                            const cf* sy = sbs + TCH * (NB / 2);
                             float yr[TCH], yi[TCH];
 #pragma unroll
                             for (int u = 0; u < TCH; ++u) yr[u] = yi[u] = 0.0f;
@@ -376,9 +391,9 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
                                 const float are = br[m], aim = br[nc + m];
 #pragma unroll
                                 for (int u = 0; u < TCH; ++u) {
-                                    const cf b = sbs[(u < tn ? u : 0) * nc + m];
-                                    yr[u] = fmaf(are, b.y, fmaf(-aim, b.x, yr[u]));
-                                    yi[u] = fmaf(are, b.x, fmaf(aim, b.y, yi[u]));
+                                    const cf bv = sbs[(u < tn ? u : 0) * nc + m];
+                                    yr[u] = fmaf(are, bv.y, fmaf(-aim, bv.x, yr[u]));
+                                    yi[u] = fmaf(are, bv.x, fmaf(aim, bv.y, yi[u]));
                                 }
                             }
                             if (live) {
@@ -390,6 +405,7 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
                                             cfmk(y0.x + 0.25f * yr[u], y0.y + 0.25f * yi[u]);
                                     }
                             }
+                            __syncwarp();   // this buffer is the copy target two passes on
                         }
                     }
                     if (out) {
