@@ -62,9 +62,13 @@ using namespace tc;
 // SM's copy engine, not bandwidth, paces this pass.
 template <int NB>
 struct TcCfg {
-    static constexpr int tmem_cols = 2 * NB <= 128 ? 128 : 256;
-    static constexpr int buf_cols = tmem_cols / 2;
-    static constexpr int ctas = 512 / tmem_cols;
+    // TMEM accumulation buffers per CTA: two (the drain of one step overlaps the
+    // next step's MMAs), except at NB = 80, where one 128-column buffer lets a
+    // third CTA onto the SM (the CTAs then overlap each other's drains)
+    static constexpr int nbuf = NB == 80 ? 1 : 2;
+    static constexpr int tmem_cols = nbuf * NB <= 128 ? 128 : 256;
+    static constexpr int buf_cols = tmem_cols / nbuf;
+    static constexpr int ctas = nbuf == 1 ? 3 : 512 / tmem_cols;
     static constexpr int stage_bytes = 8192 + NB * 64;
     // 228 KB of shared memory per SM; per CTA 1 KB reserved by the system and
     // 256 B of barriers (the kernel has no static shared memory: its 1024-byte
@@ -303,10 +307,10 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
         };
         float f_next = nsteps > 0 ? factor(0) : 0.0f;
         for (int s = 0; s < nsteps && ok; ++s) {
-            const int b = s & 1;
+            const int b = s % CFG::nbuf;
             const float f = f_next;
             if (s + 1 < nsteps) f_next = factor(s + 1);   // one step ahead
-            bool good = !s_abort && mbar_wait(&dfull[b], (uint32_t)((s >> 1) & 1), spin);
+            bool good = !s_abort && mbar_wait(&dfull[b], (uint32_t)((s / CFG::nbuf) & 1), spin);
             good = __all_sync(0xffffffffu, good);
             if (!good) { ok = false; s_abort = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -481,8 +485,8 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
         for (int s = 0; s < nsteps && ok; ++s) {
             const int nk = nk_next;
             if (s + 1 < nsteps) nk_next = steps[sbeg + s + 1].c1 - steps[sbeg + s + 1].c0;
-            const int b = s & 1;
-            if (s_abort || !mbar_wait(&dfree[b], (uint32_t)(((s >> 1) & 1) ^ 1), spin)) { s_abort = 1; break; }
+            const int b = s % CFG::nbuf;
+            if (s_abort || !mbar_wait(&dfree[b], (uint32_t)(((s / CFG::nbuf) & 1) ^ 1), spin)) { s_abort = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t dt = taddr + (uint32_t)(b * CFG::buf_cols);
             for (int c = 0; c < nk; ++c, ++i) {
