@@ -65,7 +65,7 @@ struct TcCfg {
     // TMEM accumulation buffers per CTA: two (the drain of one step overlaps the
     // next step's MMAs), except at NB = 80, where one 128-column buffer lets a
     // third CTA onto the SM (the CTAs then overlap each other's drains)
-    static constexpr int nbuf = NB == 80 ? 1 : 2;
+    static constexpr int nbuf = (NB == 80 || NB == 96) ? 1 : 2;
     static constexpr int tmem_cols = nbuf * NB <= 128 ? 128 : 256;
     static constexpr int buf_cols = tmem_cols / nbuf;
     static constexpr int ctas = nbuf == 1 ? 3 : 512 / tmem_cols;
