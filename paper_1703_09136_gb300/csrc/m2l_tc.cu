@@ -65,10 +65,13 @@ struct TcCfg {
     // TMEM accumulation buffers per CTA: two (the drain of one step overlaps the
     // next step's MMAs), except at NB = 80, where one 128-column buffer lets a
     // third CTA onto the SM (the CTAs then overlap each other's drains)
-    static constexpr int nbuf = (NB == 80 || NB == 96) ? 1 : 2;
-    static constexpr int tmem_cols = nbuf * NB <= 128 ? 128 : 256;
+    static constexpr int nbuf = (NB == 48 || NB == 80 || NB == 96) ? 1 : 2;
+    // a power of two of at least 32 columns: one buffer takes the smallest that
+    // holds it, two buffers at least 128
+    static constexpr int tmem_cols = nbuf == 1 ? (NB <= 32 ? 32 : NB <= 64 ? 64 : 128) : (2 * NB <= 128 ? 128 : 256);
     static constexpr int buf_cols = tmem_cols / nbuf;
-    static constexpr int ctas = nbuf == 1 ? 3 : 512 / tmem_cols;
+    static constexpr int ctas = NB == 48 ? 5 : nbuf == 1 ? 3 : 512 / tmem_cols;
+    static_assert(ctas * tmem_cols <= 512, "the CTAs of an SM fit its tensor memory");
     static constexpr int stage_bytes = 8192 + NB * 64;
     // 228 KB of shared memory per SM; per CTA 1 KB reserved by the system and
     // 256 B of barriers (the kernel has no static shared memory: its 1024-byte
@@ -87,7 +90,7 @@ constexpr int TC_MAX_NP = 128;         // widest column block (one 128-column TM
 // pass computes); used only where the four warps' regions fit the ring.
 template <int NB>
 struct TcL2p {
-    static constexpr int pts = 8;
+    static constexpr int pts = NB == 48 ? 4 : 8;
     static constexpr int buf = pts * (NB / 2) * 8 + pts * 32 * 8;
     static constexpr int warp_bytes = 32 * (NB + 1) * 4 + 2 * buf;
     static constexpr bool fits = 4 * warp_bytes <= TcCfg<NB>::stages * TcCfg<NB>::stage_bytes;
