@@ -52,14 +52,17 @@ using namespace tc;
 
 // Occupancy of the tensor-core kernel.  Each CTA is one dependent chain (TMA
 // -> MMA -> drain per step), so the pass is latency-bound and wants as many
-// CTAs per SM as tensor memory, registers and shared memory allow: two TMEM
-// accumulation buffers of NB columns in a power-of-two allocation (128
-// columns for NB <= 64, i.e. four CTAs per SM; 256 beyond, where the drain
-// registers limit the SM to two CTAs anyway), and as many ring stages (one
-// 16-wide K chunk each: the two 4 KB A halves (hi and lo interleaved), B hi,
-// B lo) as fit the CTA's share of shared memory (at least two).  The stage
-// count matters less than the number of bulk copies per chunk (three): the
-// SM's copy engine, not bandwidth, paces this pass.
+// CTAs per SM as tensor memory, registers and shared memory allow.  Timing
+// builds that removed one part of the chain at a time (copies, MMAs, drain)
+// moved it by at most 11%, while each extra CTA per SM paid: the widths 48,
+// 80 and 96 therefore keep ONE TMEM accumulation buffer (the drain of a step
+// then holds back that CTA's next step, but the other CTAs fill the gap) and
+// run five (48: 64 columns) or three (80, 96: 128 columns) CTAs per SM; the
+// other widths keep two buffers (the drain overlaps the next step's MMAs) in a
+// power-of-two allocation (128 columns for NB <= 64, 256 beyond).  The ring
+// has as many stages (one 16-wide K chunk each: the two 4 KB A halves, hi and
+// lo interleaved, and the B block) as fit the CTA's share of shared memory
+// (at least two).
 template <int NB>
 struct TcCfg {
     // TMEM accumulation buffers per CTA: two (the drain of one step overlaps the
