@@ -350,6 +350,279 @@ __global__ void __launch_bounds__(128) ad_near_kernel(
     }
 }
 
+// ---------------------------------------------------------------------------
+// Mixed precision (HFMM_MIXED): expansions scaled per level as in the uniform
+// mixed path (a~_m = a_m / s(|m|), b~_p = b_p s(|p|), s(n) = min(1, (k R /
+// 2)^n / n!)) in FP32, the scaled FP32 translation matrices of the uniform
+// path, and plan-time FP32 copies of every point's basis, computed in FP64:
+//   P2M / L2P   B[m]  = J_m(k rho) e^{-i m theta} / s_l(|m|)   (L2P: conj(B))
+//   P2L (X)     P[q]  = s_l(|q|) H_{-q}(k r) e^{-i q theta},  (r, theta) of l - x_j
+//   M2P (W)     M[m]  = s_D(|m|) H_m(k r) e^{i m theta},      (r, theta) of x - c_D
+// all bounded by one (|J_m| <= s(m) over the box; |s H_m| ~ (R / r)^m / m with
+// r > R), so the apply is plain FP32 arithmetic on point-major strengths.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cfma_f(cf& acc, cf a, cf b) {
+    acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+    acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+}
+
+// Plan time: scaled P2M basis of every point of the listed leaves (one CTA
+// per leaf, a thread per point; Jt scratch of p + 1 doubles per thread in
+// dynamic shared memory).
+__global__ void ad32_basis_p2m_kernel(const AdBox* __restrict__ boxes, const int32_t* __restrict__ leaves,
+                                      const int64_t* __restrict__ boff, int lup, const double2* __restrict__ xs,
+                                      double x0, double y0, double k, AdLevels lv,
+                                      const double* const* __restrict__ log_s, cf* __restrict__ out) {
+    extern __shared__ double jt[];
+    const AdBox b = boxes[leaves[blockIdx.x]];
+    if (b.level < lup) return;   // no expansions at this level: no basis (and no range in out)
+    const int l = b.level, p = lv.p[l], nc = 2 * p + 1;
+    const double* ls = log_s[l];
+    double cx, cy;
+    ad_centre(x0, y0, lv.h[l], b.ix, b.iy, &cx, &cy);
+    double* Jt = jt + (size_t)threadIdx.x * (p + 1);
+    for (int32_t i = b.lo + threadIdx.x; i < b.hi; i += blockDim.x) {
+        const double dx = xs[i].x - cx, dy = xs[i].y - cy;
+        bessel_j_seq(k * hypot(dx, dy), p, Jt);
+        const cd e1 = cexpi(-atan2(dy, dx));
+        cf* B = out + boff[blockIdx.x] + (int64_t)(i - b.lo) * nc;
+        cd e = cmk(1.0, 0.0);
+        B[p] = cfmk((float)(Jt[0] * exp(-ls[0])), 0.0f);
+        for (int m = 1; m <= p; ++m) {
+            e = cmul(e, e1);
+            const double a = Jt[m] * exp(-ls[m]);
+            const double sg = (m & 1) ? -a : a;
+            B[p + m] = cfmk((float)(e.x * a), (float)(e.y * a));
+            B[p - m] = cfmk((float)(e.x * sg), (float)(-e.y * sg));
+        }
+    }
+}
+
+// Plan time: scaled M2P (m2p = true: pair = (leaf, W box), points of the
+// leaf) or P2L (pair = (box, X leaf), points of the leaf, about the box)
+// basis of every point of every pair.  One CTA per pair, a thread per point;
+// Ht scratch of p + 1 complex values per thread in dynamic shared memory.
+__global__ void ad32_basis_pair_kernel(const AdBox* __restrict__ boxes, const int32_t* __restrict__ tgt,
+                                       const int32_t* __restrict__ src, const int64_t* __restrict__ boff, bool m2p,
+                                       const double2* __restrict__ xs, double x0, double y0, double k, AdLevels lv,
+                                       const double* const* __restrict__ log_s, cf* __restrict__ out) {
+    extern __shared__ double hsm[];
+    const int64_t e = blockIdx.x;
+    const AdBox T = boxes[tgt[e]], S = boxes[src[e]];
+    // the expansion box (its centre, order and scaling) and the box holding the points
+    const AdBox& E = m2p ? S : T;
+    const AdBox& X = m2p ? T : S;
+    const int l = E.level, p = lv.p[l], nc = 2 * p + 1;
+    const double* ls = log_s[l];
+    double cx, cy;
+    ad_centre(x0, y0, lv.h[l], E.ix, E.iy, &cx, &cy);
+    cd* Ht = (cd*)hsm + (size_t)threadIdx.x * (p + 1);
+    for (int32_t i = X.lo + threadIdx.x; i < X.hi; i += blockDim.x) {
+        // M2P: (r, theta) of x - c; P2L: of c - x
+        const double dx = m2p ? xs[i].x - cx : cx - xs[i].x, dy = m2p ? xs[i].y - cy : cy - xs[i].y;
+        hankel_seq(k * hypot(dx, dy), p, Ht);
+        const cd e1 = cexpi(atan2(dy, dx));
+        cf* B = out + boff[e] + (int64_t)(i - X.lo) * nc;
+        cd ee = cmk(1.0, 0.0);
+        B[p] = cfmk((float)Ht[0].x, (float)Ht[0].y);
+        for (int m = 1; m <= p; ++m) {
+            ee = cmul(ee, e1);
+            const double sc = exp(ls[m]);
+            const double sg = (m & 1) ? -sc : sc;
+            const cd pos = cscale(cmul(Ht[m], ee), sc);          // s H_m e^{i m theta}
+            const cd neg = cscale(cmul(Ht[m], cconj(ee)), sg);   // s H_{-m} e^{-i m theta}
+            const cd hi = m2p ? pos : neg, lo = m2p ? neg : pos;
+            B[p + m] = cfmk((float)hi.x, (float)hi.y);
+            B[p - m] = cfmk((float)lo.x, (float)lo.y);
+        }
+    }
+}
+
+// Plan time: (i/4) H0 of every U pair in FP32 (source-major, as the FP64 blocks).
+__global__ void ad32_near_fill_kernel(const AdBox* __restrict__ boxes, const int32_t* __restrict__ leaves,
+                                      const int32_t* __restrict__ u_beg, const int32_t* __restrict__ u_src,
+                                      const int64_t* __restrict__ u_blk, const double2* __restrict__ xs, double k,
+                                      cf* __restrict__ G) {
+    const int li = blockIdx.x;
+    const AdBox b = boxes[leaves[li]];
+    const int tn = b.hi - b.lo;
+    for (int32_t e = u_beg[li]; e < u_beg[li + 1]; ++e) {
+        const AdBox S = boxes[u_src[e]];
+        const int sn = S.hi - S.lo;
+        for (int idx = threadIdx.x; idx < tn * sn; idx += blockDim.x) {
+            const int j = idx / tn, i = idx % tn;
+            cf g = cfmk(0.f, 0.f);
+            if (b.lo + i != S.lo + j) {
+                const double2 a = xs[b.lo + i], c = xs[S.lo + j];
+                const cd h = cmuli(cscale(hankel0(k * hypot(a.x - c.x, a.y - c.y)), 0.25));
+                g = cfmk((float)h.x, (float)h.y);
+            }
+            G[u_blk[e] + (int64_t)j * tn + i] = g;
+        }
+    }
+}
+
+// per-level FP32 expansion pointers
+struct AdLevels32 {
+    cf* mult[AD_MAX_LEVEL + 1];
+    cf* loc[AD_MAX_LEVEL + 1];
+    int p[AD_MAX_LEVEL + 1];
+};
+
+// P2M (scaled) at the listed leaves, one warp per leaf: lanes over (RHS, order).
+__global__ void __launch_bounds__(32) ad32_p2m_kernel(const AdBox* __restrict__ boxes, const int32_t* __restrict__ leaves,
+                                                      const int32_t* __restrict__ list, const int64_t* __restrict__ boff,
+                                                      const cf* __restrict__ basis, const cf* __restrict__ qs, int nrhs,
+                                                      AdLevels32 lv) {
+    const int li = list[blockIdx.x];
+    const AdBox b = boxes[leaves[li]];
+    const int l = b.level, nc = 2 * lv.p[l] + 1;
+    const cf* B = basis + boff[li];
+    cf* out = lv.mult[l] + (int64_t)b.lidx * nrhs * nc;
+    for (int it = threadIdx.x; it < nrhs * nc; it += 32) {
+        const int r = it / nc, m = it % nc;
+        cf acc = cfmk(0.f, 0.f);
+        for (int32_t j = b.lo; j < b.hi; ++j) cfma_f(acc, qs[(int64_t)j * nrhs + r], B[(int64_t)(j - b.lo) * nc + m]);
+        out[it] = acc;
+    }
+}
+
+// M2M (scaled) into the non-leaf boxes of level l: a~_j += sum_c sum_m T~[c][m][j] a~^c_m.
+__global__ void __launch_bounds__(AD_TB) ad32_m2m_kernel(const AdBox* __restrict__ boxes, int64_t off, int l,
+                                                         const cf* __restrict__ T, AdLevels32 lv, int nrhs) {
+    const AdBox b = boxes[off + blockIdx.x];
+    if (b.leaf) return;
+    const int nc = 2 * lv.p[l + 1] + 1, np = 2 * lv.p[l] + 1;
+    for (int it = blockIdx.y * blockDim.x + threadIdx.x; it < nrhs * np; it += gridDim.y * blockDim.x) {
+        const int r = it / np, j = it % np;
+        cf acc = cfmk(0.f, 0.f);
+        for (int c = 0; c < 4; ++c) {
+            if (b.child[c] < 0) continue;
+            const cf* a = lv.mult[l + 1] + ((int64_t)boxes[b.child[c]].lidx * nrhs + r) * nc;
+            const cf* Tc = T + (int64_t)c * nc * np + j;
+            for (int m = 0; m < nc; ++m) cfma_f(acc, a[m], Tc[(int64_t)m * np]);
+        }
+        lv.mult[l][((int64_t)b.lidx * nrhs + r) * np + j] = acc;
+    }
+}
+
+// Downward pass (scaled) at level l: L2L, V-list and reaction M2L, then P2L of
+// the X-list leaves' points with their plan-time bases.
+__global__ void __launch_bounds__(AD_TB) ad32_down_kernel(
+    const AdBox* __restrict__ boxes, int64_t off, int l, int lmin, int nrhs, AdLevels32 lv,
+    const cf* __restrict__ Tl2l, const int32_t* __restrict__ v_beg, const int32_t* __restrict__ v_src,
+    const int32_t* __restrict__ v_off, const cf* __restrict__ Tfree, const int32_t* __restrict__ r_beg,
+    const int32_t* __restrict__ r_src, const int32_t* __restrict__ r_tab, const cf* __restrict__ Treact,
+    const int32_t* __restrict__ x_beg, const int32_t* __restrict__ x_src, const int64_t* __restrict__ x_boff,
+    const cf* __restrict__ p2l, const cf* __restrict__ qs, int parts) {
+    const int64_t bi = off + blockIdx.x;
+    const AdBox b = boxes[bi];
+    const int nc = 2 * lv.p[l] + 1;
+    const bool ff = (parts & HFMM_PART_FAR_FREE) != 0, fr = (parts & HFMM_PART_FAR_REACT) != 0;
+    const bool l2l = l > lmin && b.parent >= 0;
+    const int c = (b.ix & 1) + 2 * (b.iy & 1);
+    for (int it = blockIdx.y * blockDim.x + threadIdx.x; it < nrhs * nc; it += gridDim.y * blockDim.x) {
+        const int r = it / nc, q = it % nc;
+        cf acc = cfmk(0.f, 0.f);
+        if (l2l) {
+            const int npp = 2 * lv.p[l - 1] + 1;
+            const cf* beta = lv.loc[l - 1] + ((int64_t)boxes[b.parent].lidx * nrhs + r) * npp;
+            const cf* Tc = Tl2l + (int64_t)c * npp * nc + q;
+            for (int n = 0; n < npp; ++n) cfma_f(acc, beta[n], Tc[(int64_t)n * nc]);
+        }
+        if (ff)
+            for (int32_t e = v_beg[bi]; e < v_beg[bi + 1]; ++e) {
+                const cf* a = lv.mult[l] + ((int64_t)v_src[e] * nrhs + r) * nc;
+                const cf* F = Tfree + (int64_t)v_off[e] * nc * nc + q;
+                for (int m = 0; m < nc; ++m) cfma_f(acc, a[m], F[(int64_t)m * nc]);
+            }
+        if (fr)
+            for (int32_t e = r_beg[bi]; e < r_beg[bi + 1]; ++e) {
+                const cf* a = lv.mult[l] + ((int64_t)r_src[e] * nrhs + r) * nc;
+                const cf* H = Treact + (int64_t)r_tab[e] * nc * nc + q;
+                for (int m = 0; m < nc; ++m) cfma_f(acc, a[m], H[(int64_t)m * nc]);
+            }
+        if (ff)
+            for (int32_t e = x_beg[bi]; e < x_beg[bi + 1]; ++e) {
+                const AdBox C = boxes[x_src[e]];
+                const cf* Pb = p2l + x_boff[e] + q;
+                for (int32_t j = C.lo; j < C.hi; ++j) cfma_f(acc, qs[(int64_t)j * nrhs + r], Pb[(int64_t)(j - C.lo) * nc]);
+            }
+        lv.loc[l][((int64_t)b.lidx * nrhs + r) * nc + q] = acc;
+    }
+}
+
+// Far field (scaled) at the points of every leaf, one warp per leaf, lane =
+// point: L2P (conj of the P2M basis) and M2P of the W list.
+__global__ void __launch_bounds__(32) ad32_leaf_far_kernel(
+    const AdBox* __restrict__ boxes, const int32_t* __restrict__ leaves, const int64_t* __restrict__ boff,
+    const cf* __restrict__ basis, const int32_t* __restrict__ w_beg, const int32_t* __restrict__ w_src,
+    const int64_t* __restrict__ w_boff, const cf* __restrict__ m2p, int nrhs, AdLevels32 lv, int lmin, int parts,
+    cf* __restrict__ ys) {
+    const int li = blockIdx.x, lane = threadIdx.x;
+    const AdBox b = boxes[leaves[li]];
+    const bool l2p = b.level >= lmin;
+    const int nw = (parts & HFMM_PART_FAR_FREE) ? w_beg[li + 1] - w_beg[li] : 0;
+    const int ncl = 2 * lv.p[b.level] + 1;
+    for (int32_t i = b.lo + lane; i < b.hi; i += 32) {
+        for (int r = 0; r < nrhs; ++r) {
+            cf acc = cfmk(0.f, 0.f);
+            if (l2p) {
+                const cf* beta = lv.loc[b.level] + ((int64_t)b.lidx * nrhs + r) * ncl;
+                const cf* B = basis + boff[li] + (int64_t)(i - b.lo) * ncl;
+                for (int m = 0; m < ncl; ++m) cfma_f(acc, beta[m], cfmk(B[m].x, -B[m].y));
+            }
+            for (int s = 0; s < nw; ++s) {
+                const int32_t e = w_beg[li] + s;
+                const AdBox D = boxes[w_src[e]];
+                const int ncd = 2 * lv.p[D.level] + 1;
+                const cf* a = lv.mult[D.level] + ((int64_t)D.lidx * nrhs + r) * ncd;
+                const cf* M = m2p + w_boff[e] + (int64_t)(i - b.lo) * ncd;
+                for (int m = 0; m < ncd; ++m) cfma_f(acc, a[m], M[m]);
+            }
+            cf* yy = ys + (int64_t)i * nrhs + r;
+            *yy = cfmk(yy->x - 0.25f * acc.y, yy->y + 0.25f * acc.x);
+        }
+    }
+}
+
+// Near field (FP32) of every leaf, one warp per leaf (four per CTA), lane =
+// target: plan-time (i/4) H0 blocks of the U list and the directly summed
+// reaction blocks.
+__global__ void __launch_bounds__(128) ad32_near_kernel(
+    const AdBox* __restrict__ boxes, const int32_t* __restrict__ leaves, int64_t nleaf,
+    const int32_t* __restrict__ u_beg, const int32_t* __restrict__ u_src, const int64_t* __restrict__ u_blk,
+    const cf* __restrict__ G, const int32_t* __restrict__ d_beg, const int32_t* __restrict__ d_src,
+    const int64_t* __restrict__ d_blk, const cf* __restrict__ dvals, const cf* __restrict__ qs, int nrhs, int parts,
+    cf* __restrict__ ys) {
+    const int64_t li = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (li >= nleaf) return;
+    const int lane = threadIdx.x & 31;
+    const AdBox b = boxes[leaves[li]];
+    const int tn = b.hi - b.lo;
+    const bool nf = (parts & HFMM_PART_NEAR_FREE) != 0, nr = (parts & HFMM_PART_NEAR_REACT) != 0;
+    for (int i = lane; i < tn; i += 32)
+        for (int r = 0; r < nrhs; ++r) {
+            cf acc = cfmk(0.f, 0.f);
+            if (nf)
+                for (int32_t e = u_beg[li]; e < u_beg[li + 1]; ++e) {
+                    const AdBox S = boxes[u_src[e]];
+                    const cf* Ge = G + u_blk[e] + i;
+                    for (int32_t j = 0; j < S.hi - S.lo; ++j)
+                        cfma_f(acc, Ge[(int64_t)j * tn], qs[(int64_t)(S.lo + j) * nrhs + r]);
+                }
+            if (nr)
+                for (int32_t e = d_beg[li]; e < d_beg[li + 1]; ++e) {
+                    const AdBox S = boxes[d_src[e]];
+                    const int sn = S.hi - S.lo;
+                    const cf* Gr = dvals + d_blk[e] + (int64_t)i * sn;
+                    for (int j = 0; j < sn; ++j) cfma_f(acc, Gr[j], qs[(int64_t)(S.lo + j) * nrhs + r]);
+                }
+            cf* yy = ys + (int64_t)(b.lo + i) * nrhs + r;
+            *yy = cfmk(yy->x + acc.x, yy->y + acc.y);
+        }
+}
+
 int ad_chunk(int pmax, int cap) {
     // (2p + 1) basis values + (p + 1) scratch values of 16 bytes per point in ~45 KB
     const int per = (2 * pmax + 1) * (int)sizeof(cd) + (pmax + 1) * (int)sizeof(cd);
@@ -412,6 +685,11 @@ struct AdaptiveTree {
     std::vector<int64_t> u_blk;               // offset of each U pair's H0 block
     cd* near_G = nullptr;                     // plan-time H0 blocks (null above the budget)
     int64_t* du_blk = nullptr;
+    // mixed precision: plan-time FP32 bases (P2M / L2P per leaf point, M2P per W
+    // pair and point, P2L per X pair and point) with their offsets, FP32 H0 blocks
+    cf *basis32 = nullptr, *m2p32 = nullptr, *p2l32 = nullptr, *near_G32 = nullptr;
+    int64_t *d_boff = nullptr, *d_wboff = nullptr, *d_xboff = nullptr;
+    int32_t* d_p2m_li = nullptr;              // leaf ordinals of the P2M list
     // device
     AdBox* d_boxes = nullptr;
     int32_t *dv_beg = nullptr, *dv_src = nullptr, *dv_off = nullptr, *dr_beg = nullptr, *dr_src = nullptr,
@@ -780,7 +1058,7 @@ hfmm_status build_adaptive_lists(hfmm_plan_s* P, cudaStream_t st) {
     HFMM_TRY(ad_upload(P, T->u_blk, &T->du_blk, st));
     // the near field's (i/4) H0 blocks, computed once (within the same budget as
     // the uniform tree's FP64 blocks)
-    if (16.0 * (double)pp <= NEAR64_MAX_BYTES && pp > 0) {
+    if (P->precision == HFMM_FP64 && 16.0 * (double)pp <= NEAR64_MAX_BYTES && pp > 0) {
         HFMM_TRY(plan_alloc(P, (void**)&T->near_G, sizeof(cd) * (size_t)pp));
         ad_near_fill_kernel<<<(unsigned)nl, 128, 0, st>>>(T->d_boxes, T->d_leaves, T->du_beg, T->du_src, T->du_blk,
                                                           P->xy_sorted, P->k, T->near_G);
@@ -869,6 +1147,182 @@ hfmm_status apply_adaptive(hfmm_plan_s* P, int nrhs, int parts, cudaStream_t st)
         ad_near_kernel<<<(unsigned)ceil_div(nleaf, 4), 128, 0, st>>>(
             T->d_boxes, T->d_leaves, nleaf, T->du_beg, T->du_src, T->du_blk, T->near_G, T->dd_beg, T->dd_src, T->dd_blk,
             P->d_vals, P->xy_sorted, P->q_sorted, n, nrhs, P->k, parts, P->y_sorted);
+        ++P->launches;
+        HFMM_CUDA_TRY(cudaGetLastError());
+        tm.end(HFMM_STAGE_P2P);
+        P->st_flops[HFMM_STAGE_P2P] = MAC * (double)P->p2p_point_pairs;
+        P->st_flops[HFMM_STAGE_DIRECT] = MAC * (double)P->nd_vals;
+    }
+    return HFMM_OK;
+}
+
+namespace {
+
+__global__ void ad_iperm_kernel(const int64_t* __restrict__ perm, int64_t n, int32_t* __restrict__ iperm) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) iperm[perm[i]] = (int32_t)i;
+}
+
+}  // namespace
+
+// Mixed-precision state of an adaptive plan (after build_tables32): the
+// inverse permutation, the plan-time FP32 bases and FP32 near-field blocks.
+hfmm_status build_adaptive32(hfmm_plan_s* P, cudaStream_t st) {
+    AdaptiveTree* T = P->ad;
+    const auto& bx = T->boxes;
+    const int64_t nl = (int64_t)T->leaves.size();
+    const int lup = T->lup;
+    HFMM_TRY(plan_alloc(P, (void**)&P->iperm32, sizeof(int32_t) * P->n));
+    ad_iperm_kernel<<<(unsigned)ceil_div(P->n, 256), 256, 0, st>>>(P->perm, P->n, P->iperm32);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    AdLevels lv{};
+    std::vector<const double*> lsp(AD_MAX_LEVEL + 1, nullptr);
+    for (int l = 0; l <= P->L; ++l) {
+        lv.p[l] = P->lev[l].p;
+        lv.h[l] = P->lev[l].h;
+        lsp[l] = P->lev[l].d_log_s;
+    }
+    const double** d_lsp = nullptr;
+    HFMM_TRY(ad_upload(P, lsp, &d_lsp, st));
+    auto nc = [&](int l) { return (int64_t)(2 * P->lev[l].p + 1); };
+    // P2M / L2P bases of the leaves at levels >= lup
+    std::vector<int64_t> boff(nl, 0), wboff(T->w_src.size(), 0), xboff(T->x_src.size(), 0);
+    std::vector<int32_t> p2m_li;
+    int64_t nb = 0;
+    for (int64_t li = 0; li < nl; ++li) {
+        const AdBox& B = bx[T->leaves[li]];
+        boff[li] = nb;
+        if (B.level >= lup) {
+            nb += (int64_t)(B.hi - B.lo) * nc(B.level);
+            p2m_li.push_back((int32_t)li);
+        }
+    }
+    std::vector<int32_t> w_tgt(T->w_src.size()), x_tgt(T->x_src.size());
+    int64_t nw = 0;
+    for (int64_t li = 0; li < nl; ++li) {
+        const AdBox& B = bx[T->leaves[li]];
+        for (int32_t e = T->w_beg[li]; e < T->w_beg[li + 1]; ++e) {
+            w_tgt[e] = T->leaves[li];
+            wboff[e] = nw;
+            nw += (int64_t)(B.hi - B.lo) * nc(bx[T->w_src[e]].level);
+        }
+    }
+    int64_t nx = 0;
+    for (size_t b = 0; b < bx.size(); ++b)
+        for (int32_t e = T->x_beg[b]; e < T->x_beg[b + 1]; ++e) {
+            x_tgt[e] = (int32_t)b;
+            xboff[e] = nx;
+            const AdBox& C = bx[T->x_src[e]];
+            nx += (int64_t)(C.hi - C.lo) * nc(bx[b].level);
+        }
+    HFMM_TRY(ad_upload(P, boff, &T->d_boff, st));
+    HFMM_TRY(ad_upload(P, wboff, &T->d_wboff, st));
+    HFMM_TRY(ad_upload(P, xboff, &T->d_xboff, st));
+    HFMM_TRY(ad_upload(P, p2m_li, &T->d_p2m_li, st));
+    int32_t *d_wt = nullptr, *d_xt = nullptr;
+    HFMM_TRY(ad_upload(P, w_tgt, &d_wt, st));
+    HFMM_TRY(ad_upload(P, x_tgt, &d_xt, st));
+    HFMM_TRY(plan_alloc(P, (void**)&T->basis32, sizeof(cf) * std::max<int64_t>(nb, 1)));
+    HFMM_TRY(plan_alloc(P, (void**)&T->m2p32, sizeof(cf) * std::max<int64_t>(nw, 1)));
+    HFMM_TRY(plan_alloc(P, (void**)&T->p2l32, sizeof(cf) * std::max<int64_t>(nx, 1)));
+    P->buffer_bytes += sizeof(cf) * (double)(nb + nw + nx);
+    const int pm = T->pmax;
+    const int thr = std::max(1, std::min(128, 6000 / (pm + 1)));
+    if (nl > 0) {
+        ad32_basis_p2m_kernel<<<(unsigned)nl, thr, (size_t)thr * (pm + 1) * sizeof(double), st>>>(
+            T->d_boxes, T->d_leaves, T->d_boff, lup, P->xy_sorted, P->x0, P->y0, P->k, lv, d_lsp, T->basis32);
+        HFMM_CUDA_TRY(cudaGetLastError());
+    }
+    const int thr2 = std::max(1, std::min(128, 3000 / (pm + 1)));
+    if (!T->w_src.empty()) {
+        ad32_basis_pair_kernel<<<(unsigned)T->w_src.size(), thr2, (size_t)thr2 * (pm + 1) * sizeof(cd), st>>>(
+            T->d_boxes, d_wt, T->dw_src, T->d_wboff, true, P->xy_sorted, P->x0, P->y0, P->k, lv, d_lsp, T->m2p32);
+        HFMM_CUDA_TRY(cudaGetLastError());
+    }
+    if (!T->x_src.empty()) {
+        ad32_basis_pair_kernel<<<(unsigned)T->x_src.size(), thr2, (size_t)thr2 * (pm + 1) * sizeof(cd), st>>>(
+            T->d_boxes, d_xt, T->dx_src, T->d_xboff, false, P->xy_sorted, P->x0, P->y0, P->k, lv, d_lsp, T->p2l32);
+        HFMM_CUDA_TRY(cudaGetLastError());
+    }
+    // FP32 near-field blocks
+    const double pp = (double)P->p2p_point_pairs;
+    if (pp > 0 && 8.0 * pp <= NEAR64_MAX_BYTES) {
+        HFMM_TRY(plan_alloc(P, (void**)&T->near_G32, sizeof(cf) * (size_t)P->p2p_point_pairs));
+        ad32_near_fill_kernel<<<(unsigned)nl, 128, 0, st>>>(T->d_boxes, T->d_leaves, T->du_beg, T->du_src, T->du_blk,
+                                                            P->xy_sorted, P->k, T->near_G32);
+        HFMM_CUDA_TRY(cudaGetLastError());
+        P->table_bytes += 8.0 * pp;
+    } else if (pp > 0) {
+        hfmm_set_error("adaptive mixed plan: near-field blocks of %.3g GB exceed the budget", 8.0 * pp / 1e9);
+        return HFMM_ERR_OOM;
+    }
+    HFMM_CUDA_TRY(cudaStreamSynchronize(st));
+    return HFMM_OK;
+}
+
+// The adaptive apply of a mixed plan between its gather and scatter (FP32
+// strengths and fields, point-major).
+hfmm_status apply_adaptive32(hfmm_plan_s* P, int nrhs, int parts, cudaStream_t st) {
+    AdaptiveTree* T = P->ad;
+    const int L = P->L;
+    StageTimer tm{P, st};
+    AdLevels32 lv{};
+    for (int l = 0; l <= L; ++l) {
+        lv.mult[l] = P->lev[l].mult32;
+        lv.loc[l] = P->lev[l].loc32;
+        lv.p[l] = P->lev[l].p;
+    }
+    const double MAC = 8.0 * nrhs;
+    const int lmin = T->lup;
+    const int64_t nl = (int64_t)T->leaves.size();
+    const bool far = (parts & (HFMM_PART_FAR_FREE | HFMM_PART_FAR_REACT)) != 0;
+    if (far) {
+        tm.begin(HFMM_STAGE_P2M);
+        if (T->n_p2m > 0) {
+            ad32_p2m_kernel<<<(unsigned)T->n_p2m, 32, 0, st>>>(T->d_boxes, T->d_leaves, T->d_p2m_li, T->d_boff,
+                                                               T->basis32, P->q32, nrhs, lv);
+            ++P->launches;
+            HFMM_CUDA_TRY(cudaGetLastError());
+        }
+        tm.end(HFMM_STAGE_P2M);
+        tm.begin(HFMM_STAGE_M2M);
+        for (int l = L - 1; l >= lmin; --l) {
+            const LevelInfo& v = P->lev[l];
+            ad32_m2m_kernel<<<dim3((unsigned)v.nbox, ad_split(v.nbox, nrhs * v.ncoef)), AD_TB, 0, st>>>(
+                T->d_boxes, T->lev_off[l], l, v.t_m2m32, lv, nrhs);
+            ++P->launches;
+            HFMM_CUDA_TRY(cudaGetLastError());
+            P->st_flops[HFMM_STAGE_M2M] += MAC * 4.0 * v.nbox * v.ncoef * P->lev[l + 1].ncoef;
+        }
+        tm.end(HFMM_STAGE_M2M);
+        tm.begin(HFMM_STAGE_DOWN);
+        for (int l = lmin; l <= L; ++l) {
+            const LevelInfo& v = P->lev[l];
+            ad32_down_kernel<<<dim3((unsigned)v.nbox, ad_split(v.nbox, nrhs * v.ncoef)), AD_TB, 0, st>>>(
+                T->d_boxes, T->lev_off[l], l, lmin, nrhs, lv, l > lmin ? P->lev[l - 1].t_l2l32 : nullptr, T->dv_beg,
+                T->dv_src, T->dv_off, v.t_free32, T->dr_beg, T->dr_src, T->dr_tab, v.t_react32, T->dx_beg, T->dx_src,
+                T->d_xboff, T->p2l32, P->q32, parts);
+            ++P->launches;
+            HFMM_CUDA_TRY(cudaGetLastError());
+            double pairs = 0.0;
+            if (parts & HFMM_PART_FAR_FREE) pairs += (double)v.nv;
+            if (parts & HFMM_PART_FAR_REACT) pairs += (double)v.nr;
+            P->st_flops[HFMM_STAGE_DOWN] += MAC * pairs * v.ncoef * v.ncoef;
+        }
+        tm.end(HFMM_STAGE_DOWN);
+        tm.begin(HFMM_STAGE_L2P);
+        ad32_leaf_far_kernel<<<(unsigned)nl, 32, 0, st>>>(T->d_boxes, T->d_leaves, T->d_boff, T->basis32, T->dw_beg,
+                                                          T->dw_src, T->d_wboff, T->m2p32, nrhs, lv, lmin, parts,
+                                                          P->y32);
+        ++P->launches;
+        HFMM_CUDA_TRY(cudaGetLastError());
+        tm.end(HFMM_STAGE_L2P);
+    }
+    if (parts & (HFMM_PART_NEAR_FREE | HFMM_PART_NEAR_REACT)) {
+        tm.begin(HFMM_STAGE_P2P);
+        ad32_near_kernel<<<(unsigned)ceil_div(nl, 4), 128, 0, st>>>(
+            T->d_boxes, T->d_leaves, nl, T->du_beg, T->du_src, T->du_blk, T->near_G32, T->dd_beg, T->dd_src, T->dd_blk,
+            P->d_vals32, P->q32, nrhs, parts, P->y32);
         ++P->launches;
         HFMM_CUDA_TRY(cudaGetLastError());
         tm.end(HFMM_STAGE_P2P);

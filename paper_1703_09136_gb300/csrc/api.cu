@@ -274,10 +274,6 @@ static hfmm_status plan_create_one(hfmm_plan_t* out, int64_t n, const double* xy
     if (o.levels < 0 || o.levels > 15) { hfmm_set_error("levels must be in [0, 15]"); return HFMM_ERR_INVALID_ARG; }
     if (o.spin_limit < 0) { hfmm_set_error("spin_limit must be >= 0"); return HFMM_ERR_INVALID_ARG; }
     if (o.small_rhs < -1) { hfmm_set_error("small_rhs must be >= -1"); return HFMM_ERR_INVALID_ARG; }
-    if ((o.flags & HFMM_FLAG_ADAPTIVE) && o.precision != HFMM_FP64) {
-        hfmm_set_error("adaptive trees run on the FP64 path only");
-        return HFMM_ERR_UNSUPPORTED;
-    }
     if (!(o.quad_scale >= 0.0) || !std::isfinite(o.quad_scale) || o.quad_scale > 64.0) {
         hfmm_set_error("quad_scale must be in [0, 64] (got %g)", o.quad_scale);
         return HFMM_ERR_INVALID_ARG;
@@ -347,7 +343,10 @@ static hfmm_status plan_create_one(hfmm_plan_t* out, int64_t n, const double* xy
         if ((s = build_tables(P, st)) != HFMM_OK) break;
         if (!mixed && !adaptive && (s = build_near64(P, st)) != HFMM_OK) break;
         if (!mixed && (s = build_diag(P, st)) != HFMM_OK) break;
-        if (mixed) {
+        if (mixed && adaptive) {
+            if ((s = build_tables32(P, st)) != HFMM_OK) break;
+            if ((s = build_adaptive32(P, st)) != HFMM_OK) break;
+        } else if (mixed) {
             if ((s = build_tables32(P, st)) != HFMM_OK) break;
             if ((s = init_h0_table(st)) != HFMM_OK) break;
             if ((s = init_small(P, st)) != HFMM_OK) break;

@@ -39,7 +39,7 @@ struct hfmm_batch_s {
 static bool batch_persistent(const hfmm_batch_s* B, int nrhs) {
     for (auto p : B->plans)
         if (!(p->flags & HFMM_FLAG_PERSISTENT) || p->precision != HFMM_MIXED || nrhs > p->small_rhs ||
-            (p->flags & HFMM_FLAG_SIMT_M2L))
+            (p->flags & HFMM_FLAG_SIMT_M2L) || p->ad)
             return false;
     return true;
 }

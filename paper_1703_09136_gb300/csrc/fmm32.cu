@@ -972,8 +972,9 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
         if (!l2p_fused && (near_free || far)) HFMM_TRY(near_section(near_free, far, st));
         return HFMM_OK;
     };
-    HFMM_TRY(small ? apply_small(P, nrhs, parts, st) : large_path());
-    if ((parts & HFMM_PART_NEAR_REACT) && P->nd > 0) {
+    if (P->ad) HFMM_TRY(apply_adaptive32(P, nrhs, parts, st));   // adaptive tree: its own FP32 passes
+    else HFMM_TRY(small ? apply_small(P, nrhs, parts, st) : large_path());
+    if ((parts & HFMM_PART_NEAR_REACT) && P->nd > 0 && !P->ad) {
         tm.begin(HFMM_STAGE_DIRECT);
         direct32_kernel<<<(unsigned)P->lev[L].nbox, 128, 0, st>>>(P->leaf_begin, P->d_begin, P->d_src, P->d_blk,
                                                                   P->d_vals32, P->q32, n, nrhs, P->y32);

@@ -284,6 +284,8 @@ hfmm_status build_diag(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status build_adaptive_tree(hfmm_plan_s* P, const double* d_xy, int leaf_size, cudaStream_t st);
 hfmm_status build_adaptive_lists(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status apply_adaptive(hfmm_plan_s* P, int nrhs, int parts, cudaStream_t st);
+hfmm_status build_adaptive32(hfmm_plan_s* P, cudaStream_t st);
+hfmm_status apply_adaptive32(hfmm_plan_s* P, int nrhs, int parts, cudaStream_t st);
 hfmm_status adaptive_boxes(const hfmm_plan_s* P, int64_t* count, int32_t* out);
 hfmm_status adaptive_pairs(const hfmm_plan_s* P, int kind, int64_t* count, int32_t* out);
 int64_t adaptive_count(const hfmm_plan_s* P, int kind);

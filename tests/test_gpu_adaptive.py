@@ -7,7 +7,9 @@ oracle's adaptive H-FMM (oracle/adaptive.py):
   the CPU FMM at equal p, on clustered clouds for the impedance and
   three-layer media;
 * the whole apply against the O(N^2) direct sum at tol 1e-6 and 1e-10;
-* adjoint, batches and the options that adaptive plans refuse.
+* adjoint, batches and the options that adaptive plans refuse;
+* mixed precision (FP32 passes over plan-time bases) against FP64 and the
+  oracle within 1e-5.
 """
 import numpy as np
 import pytest
@@ -159,8 +161,6 @@ def test_adaptive_adjoint_batch_and_refused_options():
         with Plan(x_, med, tol=tol, leaf_size=leaf, max_rhs=2, adaptive=True) as p1:
             assert np.array_equal(p1.apply(torch.from_numpy(q_).cuda()).cpu().numpy(), y_.cpu().numpy())
     with pytest.raises(HfmmError):
-        Plan(xy, med, tol=tol, leaf_size=leaf, precision=MIXED, adaptive=True)
-    with pytest.raises(HfmmError):
         Plan(xy, med, tol=tol, leaf_size=leaf, autotune=True, adaptive=True)
 
 
@@ -192,3 +192,53 @@ def test_adaptive_edge_cases_match_direct_sum(case):
     if case == "depth-cap":
         assert inf["levels"] == 16
     assert direct.rel_l2(y, yd) < 1e-9, (case, direct.rel_l2(y, yd))
+
+
+MIXED_TOL = 1e-5
+
+
+@pytest.mark.parametrize("part", [1, 2, 4, 8])
+@pytest.mark.parametrize("name", ["cfg2-clusters", "three-layer-near-interface", "star-curve"])
+def test_adaptive_mixed_terms_match_cpu_fmm(name, part):
+    """Mixed-precision adaptive plans (scaled FP32 expansions, plan-time FP32
+    bases for P2M / L2P, M2P and P2L, FP32 near-field blocks): each term
+    against the adaptive CPU FMM within 1e-5 of the full result."""
+    F, parts = _oracle(name)
+    med, xy, q, tol, leaf = _case(name)
+    plan = Plan(xy, med, tol=tol, leaf_size=leaf, max_rhs=q.shape[0], adaptive=True, precision=MIXED)
+    y = plan.apply(torch.from_numpy(q.astype(np.complex64)).cuda(), parts=part).cpu().numpy().astype(np.complex128)
+    plan.close()
+    full = sum(parts.values())
+    err = np.linalg.norm(y - parts[part]) / np.linalg.norm(full)
+    assert err < MIXED_TOL, (name, part, err)
+
+
+def test_adaptive_mixed_matches_fp64_many_rhs_and_batch():
+    """The star curve with 16 right-hand sides: mixed against FP64 adaptive
+    per right-hand side within 1e-5, host buffers, the adjoint identity, and a
+    batch of two mixed adaptive instances equal to their single plans."""
+    med = W.WORKLOADS[8].medium
+    xy = W.points(8, 3000)
+    q = W.strengths(8, 3000, 16, salt=46)
+    p64 = Plan(xy, med, tol=1e-6, leaf_size=16, max_rhs=16, adaptive=True)
+    y64 = p64.apply(torch.from_numpy(q).cuda()).cpu().numpy()
+    p64.close()
+    p32 = Plan(xy, med, tol=1e-6, leaf_size=16, max_rhs=16, adaptive=True, precision=MIXED)
+    q32 = q.astype(np.complex64)
+    y32 = p32.apply(q32).astype(np.complex128)          # host buffers
+    worst = max(direct.rel_l2(y32[r], y64[r]) for r in range(16))
+    assert worst < MIXED_TOL, worst
+    v = (W.strengths(8, 3000, 16, salt=47)).astype(np.complex64)
+    Gq = p32.apply(q32).astype(np.complex128)
+    GHv = p32.adjoint(v).astype(np.complex128)
+    lhs, rhs = np.vdot(v.astype(np.complex128), Gq), np.vdot(GHv, q32.astype(np.complex128))
+    assert abs(lhs - rhs) < 1e-5 * abs(lhs)
+    p32.close()
+    xy2 = W.points(8, 1200, salt=2)
+    q2 = W.strengths(8, 1200, 16, salt=48).astype(np.complex64)
+    b = Batch([xy, xy2], med, tol=1e-6, leaf_size=16, max_rhs=16, adaptive=True, precision=MIXED)
+    ys = b.apply([torch.from_numpy(q32).cuda(), torch.from_numpy(q2).cuda()])
+    b.close()
+    for x_, q_, y_ in ((xy, q32, ys[0]), (xy2, q2, ys[1])):
+        with Plan(x_, med, tol=1e-6, leaf_size=16, max_rhs=16, adaptive=True, precision=MIXED) as p1:
+            assert np.array_equal(p1.apply(torch.from_numpy(q_).cuda()).cpu().numpy(), y_.cpu().numpy())
