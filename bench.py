@@ -593,10 +593,11 @@ def run_diag(args):
 def measure_adaptive(dev):
     """Uniform against adaptive tree (FP64, 1 RHS, tol 1e-6) on config 2
     itself (6400 clustered points) and on 65,536 particles of the star curve:
-    apply times, tree depths, and the two results' difference."""
+    apply times, tree depths, and the two results' difference; the adaptive
+    tree also in mixed precision."""
     import torch
     import workloads as W
-    from paper_1703_09136_gb300 import Plan
+    from paper_1703_09136_gb300 import Plan, MIXED
     out = {}
     for cfg, n in ((2, 6400), (8, 65536)):
         w = W.WORKLOADS[cfg]
@@ -613,6 +614,15 @@ def measure_adaptive(dev):
             row[name + "_levels"], row[name + "_leaves"] = inf["levels"], inf["nonempty_leaves"]
             ys[ad] = y.clone()
             plan.close()
+        # the adaptive tree in mixed precision (FP32 passes)
+        q32 = q.to(torch.complex64)
+        plan = Plan(xy, w.medium, tol=w.tol, leaf_size=w.leaf, max_rhs=1, adaptive=True, precision=MIXED)
+        y32 = torch.empty_like(q32)
+        row["adaptive_mixed_ms"] = _events_ms(lambda: plan.apply(q32, out=y32), 5)
+        plan.apply(q32, out=y32)
+        plan.close()
+        row["rel_l2_adaptive_mixed_vs_fp64"] = float(torch.linalg.norm(y32.to(torch.complex128) - ys[True]) /
+                                                     torch.linalg.norm(ys[True]))
         row["rel_l2_adaptive_vs_uniform"] = float(torch.linalg.norm(ys[True] - ys[False]) / torch.linalg.norm(ys[False]))
         row["speedup"] = row["uniform_ms"] / row["adaptive_ms"]
         out[w.name] = row
@@ -624,10 +634,11 @@ def run_adaptive(args):
     config 2's clustered distribution (80% in two Gaussian blobs of sigma 0.1)
     at N = 6400 (config 2 itself), 65,536 and 262,144, and particles on a
     star-shaped curve (workload 8) at N = 65,536 and 262,144; impedance k = 40,
-    alpha = 20, tol 1e-6, leaf size 32, one right-hand side."""
+    alpha = 20, tol 1e-6, leaf size 32, one right-hand side; the adaptive tree
+    also in mixed precision."""
     import torch
     import workloads as W
-    from paper_1703_09136_gb300 import Plan
+    from paper_1703_09136_gb300 import Plan, MIXED
     from paper_1703_09136_gb300 import build as _build
     _build.build()
     dev = torch.device("cuda", 0)
@@ -659,6 +670,15 @@ def run_adaptive(args):
                 row["adaptive_w_pairs"], row["adaptive_x_pairs"] = inf["w_pairs"], inf["x_pairs"]
             ys[ad] = y.clone()
             plan.close()
+        q32 = q.to(torch.complex64)
+        plan = Plan(xy, w.medium, tol=w.tol, leaf_size=w.leaf, max_rhs=1, adaptive=True, precision=MIXED, profile=True)
+        y32 = torch.empty_like(q32)
+        row["adaptive_mixed_ms"] = _events_ms(lambda: plan.apply(q32, out=y32), 5)
+        plan.apply(q32, out=y32)
+        row["adaptive_mixed_stage_ms"] = {k: round(v, 4) for k, v in plan.stage_times().items()}
+        plan.close()
+        row["rel_l2_adaptive_mixed_vs_fp64"] = float(torch.linalg.norm(y32.to(torch.complex128) - ys[True]) /
+                                                     torch.linalg.norm(ys[True]))
         row["rel_l2_adaptive_vs_uniform"] = float(torch.linalg.norm(ys[True] - ys[False]) / torch.linalg.norm(ys[False]))
         row["speedup"] = row["uniform_ms"] / row["adaptive_ms"]
         rows.append(row)
