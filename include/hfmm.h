@@ -135,9 +135,11 @@ typedef struct {
                                    box's multipole evaluated at a leaf's points, X: a leaf's points
                                    into a small box's local expansion), and the reaction pairs of
                                    the uniform tree's recursion, summed directly below a leaf.  The
-                                   tree and lists are built on the host at plan time.  Not with
-                                   HFMM_MIXED or HFMM_FLAG_AUTOTUNE (HFMM_ERR_UNSUPPORTED); no
-                                   position gradients (hfmm_apply_grad returns UNSUPPORTED) */
+                                   tree and lists are built on the host at plan time.  FP64, or
+                                   HFMM_MIXED as FP32 passes over plan-time FP32 bases of the points
+                                   (no tensor cores, no persistent batches).  Not with
+                                   HFMM_FLAG_AUTOTUNE (HFMM_ERR_UNSUPPORTED); no position gradients
+                                   (hfmm_apply_grad returns UNSUPPORTED) */
 #define HFMM_FLAG_DENSE_M2L 16  /* HFMM_FP64: keep the dense (2p+1)^2 translations on every level.
                                    Without it the plan tries the diagonal form of the free and
                                    reaction translations (their matrices depend on m - p only,
