@@ -242,3 +242,36 @@ def test_adaptive_mixed_matches_fp64_many_rhs_and_batch():
     for x_, q_, y_ in ((xy, q32, ys[0]), (xy2, q2, ys[1])):
         with Plan(x_, med, tol=1e-6, leaf_size=16, max_rhs=16, adaptive=True, precision=MIXED) as p1:
             assert np.array_equal(p1.apply(torch.from_numpy(q_).cuda()).cpu().numpy(), y_.cpu().numpy())
+
+
+def test_adaptive_solve_and_layered_accuracy():
+    """hfmm_solve with an adaptive plan as the operator: GMRES on (10 I + A) x
+    = b for 1000 points of the star curve against numpy's dense solve of the
+    oracle's matrix (FP64 to 1e-8, mixed to 1e-4); and the FP64 adaptive
+    apply on a three-layer blob next to the interface against the direct sum
+    at tol 1e-10."""
+    med = W.WORKLOADS[8].medium
+    xy = W.points(8, 1000)
+    n = xy.shape[0]
+    G = np.empty((n, n), dtype=complex)
+    eye = np.eye(n, dtype=complex)
+    for c0 in range(0, n, 250):
+        G[:, c0:c0 + 250] = direct.direct_apply(med, xy, eye[c0:c0 + 250]).T
+    b = W.strengths(8, n, 1, salt=49)[0]
+    sigma = 10.0
+    x_ref = np.linalg.solve(sigma * np.eye(n) + G, b)
+    with Plan(xy, med, tol=1e-10, leaf_size=16, adaptive=True) as p64:
+        x, it, rr = p64.solve(torch.from_numpy(b).cuda(), sigma=sigma, tol=1e-10, restart=100, maxit=600)
+        assert rr <= 1e-10 and 0 < it <= 600
+        assert direct.rel_l2(x.cpu().numpy(), x_ref) < 1e-8, direct.rel_l2(x.cpu().numpy(), x_ref)
+    with Plan(xy, med, tol=1e-6, leaf_size=16, adaptive=True, precision=MIXED) as p32:
+        x32, it32, rr32 = p32.solve(torch.from_numpy(b.astype(np.complex64)).cuda(), sigma=sigma, tol=1e-5,
+                                    restart=100, maxit=600)
+        assert rr32 <= 1e-5
+        assert direct.rel_l2(x32.cpu().numpy().astype(np.complex128), x_ref) < 1e-4
+    xy3 = _near_interface(900, 5)
+    q3 = W.strengths(4, 900, 1, salt=50)
+    yd = direct.direct_apply(CFG4_MED, xy3, q3)
+    with Plan(xy3, CFG4_MED, tol=1e-10, leaf_size=12, adaptive=True) as p3:
+        y3 = p3.apply(torch.from_numpy(q3).cuda()).cpu().numpy()
+    assert direct.rel_l2(y3, yd) < 1e-10, direct.rel_l2(y3, yd)
