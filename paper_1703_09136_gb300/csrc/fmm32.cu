@@ -606,6 +606,95 @@ __global__ void __launch_bounds__(PC_THREADS) p2m32c_kernel(const int32_t* lb, c
     }
 }
 
+// P2M of the leaves with the MMA-ready output, one row per thread: a CTA of 64
+// threads per (leaf, block of 64 right-hand sides); thread r accumulates row r
+// of the leaf's scaled multipole (Eq. (multi_coeff)) in registers over the
+// leaf's points, which come into shared memory 32 at a time by asynchronous
+// copies (the strengths by the thread that uses them, the basis rows by all),
+// then writes its own row's f16 hi / lo K chunks and 2^-e factors (layout of
+// p2m32c_kernel) and, when write_mult, the FP32 row.  No CTA-wide pass follows
+// the accumulation, so the short per-leaf chain overlaps across the many CTAs
+// an SM holds.  The terms are added in the order of p2m32c_kernel (points in
+// ascending order), so both write the same bits.  nc <= NCM, NCM a multiple of 8.
+constexpr int PR_SRC = 32;
+template <int NCM>
+__global__ void __launch_bounds__(64) p2m_rows_kernel(const int32_t* lb, const cf* qs, const cf* basis, int nrhs,
+                                                      int nc, cf* mult, __half* amma, float* asc, int kc, int nrc,
+                                                      int nsb, int sblk, bool write_mult) {
+    static_assert(NCM % 8 == 0 && NCM <= 32, "row staging holds the padded K chunks");
+    __shared__ union {
+        cf q[PR_SRC][64];
+        float row[64][2 * NCM + 1];   // odd stride: one bank per thread
+    } S;
+    __shared__ __align__(16) cf g[PR_SRC][NCM];
+    const int r = threadIdx.x, rc = blockIdx.y, r0 = rc * 64;
+    const int64_t b = blockIdx.x;
+    const int32_t lo = lb[b], hi = lb[b + 1];
+    const bool live = r0 + r < nrhs;
+    cf acc[NCM];
+#pragma unroll
+    for (int m = 0; m < NCM; ++m) acc[m] = cfmk(0.f, 0.f);
+    for (int32_t s0 = lo; s0 < hi; s0 += PR_SRC) {
+        const int sn = min(PR_SRC, hi - s0);
+        __syncthreads();   // the previous chunk's basis rows are consumed
+        for (int j = 0; j < sn; ++j) {
+            if (live) tc::cp_async8(&S.q[j][r], qs + (int64_t)(s0 + j) * nrhs + r0 + r);
+            else S.q[j][r] = cfmk(0.f, 0.f);
+        }
+        const cf* gs = basis + (int64_t)s0 * nc;
+        for (int e = r; e < sn * nc; e += 64) {
+            const int j = e / nc;
+            tc::cp_async8(&g[j][e - j * nc], gs + e);
+        }
+        tc::cp_async_wait_all();
+        __syncthreads();   // every thread's basis copies have landed
+        for (int j = 0; j < sn; ++j) {
+            const cf qv = S.q[j][r];
+            const float4* gp = (const float4*)&g[j][0];
+#pragma unroll
+            for (int m = 0; m < NCM; m += 2)
+                if (m < nc) {
+                    const float4 g2 = gp[m >> 1];
+                    cfma32(acc[m], cfmk(g2.x, g2.y), qv);
+                    if (m + 1 < nc) cfma32(acc[m + 1], cfmk(g2.z, g2.w), qv);
+                }
+        }
+    }
+    __syncthreads();   // S.q becomes the row staging
+    float* row = S.row[r];
+#pragma unroll
+    for (int m = 0; m < NCM; ++m)
+        if (m < nc) {
+            row[m] = acc[m].x;
+            row[nc + m] = acc[m].y;
+        }
+    for (int k = 2 * nc; k < kc * 16; ++k) row[k] = 0.f;
+    const int64_t rb = b * nrc + rc;
+    for (int blk = 0; blk < nsb; ++blk) {
+        const int c0 = blk * sblk, c1 = min(kc, c0 + sblk);
+        float mx = 0.f;
+        for (int k = c0 * 16; k < c1 * 16; ++k) mx = fmaxf(mx, fabsf(row[k]));
+        const int ex = tc::f16_exp(mx);
+        asc[(rb * nsb + blk) * 64 + r] = tc::pow2f(-ex);
+        const float s = tc::pow2f(ex);
+        for (int c = c0; c < c1; ++c) {
+            uint16_t* d = (uint16_t*)amma + (rb * kc + c) * 2048 + (r >> 3) * 256 + (r & 7) * 8;
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf) {
+                uint16_t h[8], l[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) tc::split_f16(row[c * 16 + hf * 8 + u] * s, h[u], l[u]);
+                *(uint4*)(d + hf * 64) = tc::pack8(h);
+                *(uint4*)(d + hf * 64 + 128) = tc::pack8(l);
+            }
+        }
+    }
+    if (write_mult && live) {
+        cf* out = mult + ((int64_t)b * nrhs + r0 + r) * nc;
+        for (int m = 0; m < nc; ++m) out[m] = cfmk(row[m], row[nc + m]);
+    }
+}
+
 // Plan-time scaled P2M basis of every sorted point (FP64, stored in FP32).
 __global__ void basis32_kernel(const int32_t* lb, const double2* xs, int64_t nleaf, double x0, double y0, double h,
                                double k, int p, const double* log_s, cf* basis) {
@@ -896,9 +985,21 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
                 LevelInfo& lv = P->lev[L];
                 tf.begin(HFMM_STAGE_P2M);
                 const int nrc = (P->max_rhs + 63) / 64;
-                p2m32c_kernel<<<(unsigned)lv.nbox, PC_THREADS, 0, fs>>>(
-                    P->leaf_begin, P->q32, P->basis32, n, nrhs, lv.ncoef, lv.mult32, P->tc_on ? lv.tc_amma : nullptr,
-                    lv.tc_asc, lv.tc_kc, nrc, lv.tc_nb, lv.tc_nbw / 16, !tc_down);
+                const int nc = lv.ncoef;
+                if (P->tc_on && nc <= 32) {
+                    const dim3 grid((unsigned)lv.nbox, (unsigned)((nrhs + 63) / 64));
+#define HFMM_P2M_ROWS(NCM)                                                                                     \
+    p2m_rows_kernel<NCM><<<grid, 64, 0, fs>>>(P->leaf_begin, P->q32, P->basis32, nrhs, nc, lv.mult32, lv.tc_amma, \
+                                              lv.tc_asc, lv.tc_kc, nrc, lv.tc_nb, lv.tc_nbw / 16, !tc_down)
+                    if (nc <= 16) HFMM_P2M_ROWS(16);
+                    else if (nc <= 24) HFMM_P2M_ROWS(24);
+                    else HFMM_P2M_ROWS(32);
+#undef HFMM_P2M_ROWS
+                } else {
+                    p2m32c_kernel<<<(unsigned)lv.nbox, PC_THREADS, 0, fs>>>(
+                        P->leaf_begin, P->q32, P->basis32, n, nrhs, nc, lv.mult32, P->tc_on ? lv.tc_amma : nullptr,
+                        lv.tc_asc, lv.tc_kc, nrc, lv.tc_nb, lv.tc_nbw / 16, !tc_down);
+                }
                 ++P->launches;
                 HFMM_CUDA_TRY(cudaGetLastError());
                 tf.end(HFMM_STAGE_P2M);
