@@ -34,6 +34,8 @@ struct LevelInfo {
     int32_t* r_src = nullptr;     // [nr]
     int32_t* r_tab = nullptr;     // [nr] index of the A_n table entry
     int64_t nr = 0;
+    int32_t* r_tgt = nullptr;     // [n_rtgt] target boxes with a nonempty reaction list, increasing
+    int64_t n_rtgt = 0;
     // tables
     cd* t_free = nullptr;         // [49][4p + 1]  C_n(dx h, dy h), n = -2p .. 2p
     cd* t_m2m = nullptr;          // [4][2(p + p_child) + 1] J_n(parent - child_c)  (this level = parent)

@@ -133,9 +133,9 @@ __device__ __forceinline__ void translate_source(cf (&acc)[U][R], const cf* __re
 }
 
 // Adds the warps' partial sums in warp order and stores them (warp 0).
-template <int R, int U>
+template <int R, int U, int NW = SM_W>
 __device__ __forceinline__ void reduce_store(cf (&acc)[U][R], cf* red, cf* out, int64_t row0, int nrhs, int r0,
-                                             int ncout, int p0) {
+                                             int ncout, int p0, bool add = false) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     __syncthreads();
 #pragma unroll
@@ -149,13 +149,21 @@ __device__ __forceinline__ void reduce_store(cf (&acc)[U][R], cf* red, cf* out, 
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 cf s = red[(u * R + r) * 32 + lane];
-                for (int ww = 1; ww < SM_W; ++ww) {
+                for (int ww = 1; ww < NW; ++ww) {
                     const cf v = red[((ww * U + u) * R + r) * 32 + lane];
                     s.x += v.x;
                     s.y += v.y;
                 }
                 const int p = p0 + lane + 32 * u;
-                if (p < ncout && r0 + r < nrhs) out[(row0 + r0 + r) * ncout + p] = s;
+                if (p < ncout && r0 + r < nrhs) {
+                    cf* o = out + (row0 + r0 + r) * ncout + p;
+                    if (add) {
+                        const cf v = *o;
+                        s.x = v.x + s.x;
+                        s.y = v.y + s.y;
+                    }
+                    *o = s;
+                }
             }
     }
     __syncthreads();
@@ -199,18 +207,23 @@ __global__ void __launch_bounds__(SM_W * 32) m2m_small_kernel(const int32_t* __r
 // Downward pass of level l: L2L from the parent plus free-space and reaction
 // M2L over the box's lists (the parts mask selects the M2L terms).
 // ---------------------------------------------------------------------------
-template <int R, int U>
-__global__ void __launch_bounds__(SM_W * 32) down_small_kernel(
+template <int R, int U, int NW = SM_W>
+__global__ void __launch_bounds__(NW * 32) down_small_kernel(
     const int32_t* __restrict__ lb, int L, int l, int lmin, int nrhs, int p, int pp, const cf* __restrict__ ploc,
     const cf* __restrict__ Tl2l, const cf* __restrict__ mult, const int32_t* __restrict__ v_begin,
     const int32_t* __restrict__ v_src, const int32_t* __restrict__ v_off, const cf* __restrict__ Tfree,
     const int32_t* __restrict__ r_begin, const int32_t* __restrict__ r_src, const int32_t* __restrict__ r_tab,
-    const cf* __restrict__ Treact, int parts, int nchunk, int ncs_max, cf* __restrict__ loc) {
+    const cf* __restrict__ Treact, int parts, int nchunk, int ncs_max, cf* __restrict__ loc, bool react_add,
+    const int32_t* __restrict__ tgt_list) {
     extern __shared__ float4 sm_small[];
     const int w = threadIdx.x >> 5;
     cf* stage = (cf*)sm_small + (int64_t)w * R * ncs_max;
-    cf* red = (cf*)sm_small + (int64_t)SM_W * R * ncs_max;
-    const int64_t b = blockIdx.x / nchunk;
+    cf* red = (cf*)sm_small + (int64_t)NW * R * ncs_max;
+    if (react_add) {   // L2L and V list already in loc (vblock_kernel): add the reaction list only
+        ploc = nullptr;
+        v_begin = nullptr;
+    }
+    const int64_t b = tgt_list ? (int64_t)tgt_list[blockIdx.x / nchunk] : (int64_t)(blockIdx.x / nchunk);
     const int p0 = (blockIdx.x % nchunk) * 32 * U;
     int32_t lo, hi;
     box_range(lb, L, l, b, &lo, &hi);
@@ -224,6 +237,7 @@ __global__ void __launch_bounds__(SM_W * 32) down_small_kernel(
     const int nr0 = ((parts & HFMM_PART_FAR_REACT) && r_begin) ? r_begin[b] : 0;
     const int nr1 = ((parts & HFMM_PART_FAR_REACT) && r_begin) ? r_begin[b + 1] : 0;
     const int nsrc = (has_parent ? 1 : 0) + (nv1 - nv0) + (nr1 - nr0);
+    if (react_add && nsrc == 0) return;        // uniform over the CTA
     for (int r0 = 0; r0 < nrhs; r0 += R) {
         const int rows = min(R, nrhs - r0);
         cf acc[U][R];
@@ -231,7 +245,7 @@ __global__ void __launch_bounds__(SM_W * 32) down_small_kernel(
         for (int u = 0; u < U; ++u)
 #pragma unroll
             for (int r = 0; r < R; ++r) acc[u][r] = cfmk(0.f, 0.f);
-        for (int s = w; s < nsrc; s += SM_W) {
+        for (int s = w; s < nsrc; s += NW) {
             if (has_parent && s == 0) {
                 translate_source<R, U>(acc, ploc + (P * nrhs + r0) * (int64_t)npp, Tl2l + (int64_t)cchild * npp * nc,
                                        npp, nc, p0, rows, stage);
@@ -250,7 +264,189 @@ __global__ void __launch_bounds__(SM_W * 32) down_small_kernel(
             }
             translate_source<R, U>(acc, src, M, nc, nc, p0, rows, stage);
         }
-        reduce_store<R, U>(acc, red, loc, b * nrhs, nrhs, r0, nc, p0);
+        reduce_store<R, U, NW>(acc, red, loc, b * nrhs, nrhs, r0, nc, p0, react_add);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// L2L + free-space M2L of level l for blocks of 32 target boxes (32
+// consecutive Morton indices: 8 x 4 boxes, 4 x 2 parents), one right-hand
+// side per CTA.  The targets of one child position c share their L2L matrix,
+// and the targets of position c with a V-list source at offset o share that
+// M2L matrix, so one matrix row read from L2 feeds 4 targets (a per-box pass
+// reads it once per target).  The sources of the block (the 12 x 8 boxes of
+// level l around it, the 8 parents' local expansions) are staged in shared
+// memory once.  Warps 2 c and 2 c + 1 own the 8 targets of child position c,
+// each taking every other operator of the position's list; a lane owns 4
+// targets x CPT consecutive output coefficients.  The two warps' sums are
+// added in a fixed order, operators and k run in increasing order: the
+// result does not depend on scheduling.  The V-list entries give which
+// offsets a target uses: the source of offset index o = (dx + 3) * 7 + dy + 3
+// is the box (ix - dx, iy - dy) of level l, as the list builder enumerates
+// it.  Reaction lists are added afterwards by down_small_kernel (react_add).
+// ---------------------------------------------------------------------------
+constexpr int VB_T = 32;                       // target boxes per block
+constexpr int VB_WX = 12, VB_WY = 8;           // source window (boxes of level l)
+constexpr int VB_SLOTS = VB_WX * VB_WY;
+constexpr int VB_L2L = 49;                     // mask bit of the L2L of child position c: 49 + c
+constexpr uint64_t VB_LIVE = 1ull << 63;       // mask bit: nonempty target (written)
+
+__device__ __forceinline__ void cp_async8_vb(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;"
+                 :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+
+size_t vblock_smem(int cpt, int nc, int npp) {
+    const int kmax = std::max(nc, npp), ncw = nc | 1, npw = npp | 1;
+    const size_t red = (size_t)4 * 32 * 4 * cpt;   // half 1's sums, over the window
+    return sizeof(cf) * (std::max((size_t)VB_SLOTS * ncw, red) + kmax + 8 * (size_t)npw) +
+           sizeof(uint64_t) * VB_T;
+}
+
+template <int CPT>
+__global__ void __launch_bounds__(256, CPT == 2 ? 4 : 2) vblock_kernel(const int32_t* __restrict__ lb, int L, int l, int nrhs,
+                                                        int nc, int npp, const cf* __restrict__ ploc,
+                                                        const cf* __restrict__ Tl2l, const cf* __restrict__ mult,
+                                                        const int32_t* __restrict__ v_begin,
+                                                        const int32_t* __restrict__ v_off,
+                                                        const cf* __restrict__ Tfree, cf* __restrict__ loc) {
+    constexpr int VB_PF = CPT == 2 ? 3 : 4;        // matrix rows per lane per fetch (two fetches in flight)
+    extern __shared__ float4 sm_vb[];
+    const int kmax = max(nc, npp), ncw = nc | 1, npw = npp | 1;   // odd row strides
+    const int wsz = max(VB_SLOTS * ncw, 4 * 32 * 4 * CPT);
+    cf* W = (cf*)sm_vb;                            // source window [slot][ncw]; then half 1's sums
+    cf* Z = W + wsz;                               // kmax zeros (sources of lanes without the operator)
+    cf* Pw = Z + kmax;                             // parents' local expansions [8][npw]
+    uint64_t* mask = (uint64_t*)(Pw + 8 * npw);    // [32 targets]
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, c = w >> 1, h = w & 1;
+    const int r = blockIdx.y;
+    const int64_t b0 = (int64_t)blockIdx.x * VB_T;
+    const int bx0 = (int)morton_x((uint32_t)b0), by0 = (int)morton_y((uint32_t)b0);
+    const int m = 1 << l;
+    for (int e = tid; e < kmax; e += 256) Z[e] = cfmk(0.f, 0.f);
+    if (tid < VB_T) {
+        const int64_t b = b0 + tid;
+        int32_t lo, hi;
+        box_range(lb, L, l, b, &lo, &hi);
+        uint64_t mk = 0;
+        if (hi > lo) {
+            mk = VB_LIVE;
+            if (v_begin)
+                for (int32_t e = v_begin[b]; e < v_begin[b + 1]; ++e) mk |= 1ull << v_off[e];
+            if (ploc) mk |= 1ull << (VB_L2L + (tid & 3));
+        }
+        mask[tid] = mk;
+    }
+    // sources: slot (wx, wy) holds box (bx0 - 2 + wx, by0 - 2 + wy); boxes
+    // outside the domain are never a source
+    for (int s = w; s < VB_SLOTS; s += 8) {
+        const int sx = bx0 - 2 + s % VB_WX, sy = by0 - 2 + s / VB_WX;
+        const bool in = sx >= 0 && sy >= 0 && sx < m && sy < m;
+        const cf* src = in ? mult + ((int64_t)morton((uint32_t)sx, (uint32_t)sy) * nrhs + r) * nc : nullptr;
+        for (int k = lane; k < nc; k += 32) {
+            if (in) cp_async8_vb(W + s * ncw + k, src + k);
+            else W[s * ncw + k] = cfmk(0.f, 0.f);
+        }
+    }
+    if (ploc)
+        for (int j = w; j < 8; j += 8)
+            for (int k = lane; k < npp; k += 32)
+                cp_async8_vb(Pw + j * npw + k, ploc + ((b0 / 4 + j) * nrhs + r) * (int64_t)npp + k);
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    // this lane's targets: j = 4 tg + i of child position c (local index 4 j + c)
+    const int tg = lane >> 4, cg = lane & 15;
+    uint64_t tm[4], um = 0;
+    int tx[4], ty[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int li = 4 * (4 * tg + i) + c;
+        tm[i] = mask[li];
+        tx[i] = (li & 1) | ((li >> 1) & 2) | ((li >> 2) & 4);
+        ty[i] = ((li >> 1) & 1) | ((li >> 2) & 2);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) um |= mask[4 * j + c];   // operators of position c
+    um &= ~VB_LIVE;
+    cf acc[4][CPT];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int u = 0; u < CPT; ++u) acc[i][u] = cfmk(0.f, 0.f);
+    bool live_u[CPT];
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) live_u[u] = cg * CPT + u < nc;
+    // the position's L2L first, then the V offsets in increasing order; warp h
+    // takes the operators of even (h = 0) or odd (h = 1) rank
+    for (int rank = 0; um; ++rank) {
+        const uint64_t l2l = um & (0xFull << VB_L2L);
+        const int op = __ffsll((long long)(l2l ? l2l : um)) - 1;
+        um &= ~(1ull << op);
+        if ((rank & 1) != h) continue;
+        const bool isl2l = op >= VB_L2L;
+        const cf* sp[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const bool use = (tm[i] >> op) & 1;
+            if (!use) sp[i] = Z;
+            else if (isl2l) sp[i] = Pw + (4 * tg + i) * npw;
+            else {
+                const int dx = op / 7 - 3, dy = op % 7 - 3;
+                sp[i] = W + ((ty[i] - dy + 2) * VB_WX + (tx[i] - dx + 2)) * ncw;
+            }
+        }
+        const cf* M = (isl2l ? Tl2l + (int64_t)(op - VB_L2L) * npp * nc : Tfree + (int64_t)op * nc * nc) + cg * CPT;
+        const int K = isl2l ? npp : nc;
+        // rows k0 .. k0 + VB_PF - 1 in registers while the next VB_PF are in flight
+        cf mn[VB_PF][CPT];
+        auto fetch = [&](int k0) {
+#pragma unroll
+            for (int i = 0; i < VB_PF; ++i)
+#pragma unroll
+                for (int u = 0; u < CPT; ++u)
+                    mn[i][u] = (live_u[u] && k0 + i < K) ? __ldg(M + (int64_t)(k0 + i) * nc + u) : cfmk(0.f, 0.f);
+        };
+        fetch(0);
+        for (int k0 = 0; k0 < K; k0 += VB_PF) {
+            cf mv[VB_PF][CPT];
+#pragma unroll
+            for (int i = 0; i < VB_PF; ++i)
+#pragma unroll
+                for (int u = 0; u < CPT; ++u) mv[i][u] = mn[i][u];
+            if (k0 + VB_PF < K) fetch(k0 + VB_PF);
+#pragma unroll
+            for (int i = 0; i < VB_PF; ++i) {
+                if (k0 + i >= K) break;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const cf sv = sp[t][k0 + i];
+#pragma unroll
+                    for (int u = 0; u < CPT; ++u) cfma(acc[t][u], sv, mv[i][u]);
+                }
+            }
+        }
+    }
+    // warp 2 c + 1's sums go to shared memory (over the window), warp 2 c adds and stores
+    __syncthreads();
+    cf* red = W + (c * 32 + lane) * 4 * CPT;
+    if (h == 1) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int u = 0; u < CPT; ++u) red[t * CPT + u] = acc[t][u];
+    }
+    __syncthreads();
+    if (h == 1) return;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        if (!(tm[t] & VB_LIVE)) continue;
+        const int64_t b = b0 + 4 * (4 * tg + t) + c;
+#pragma unroll
+        for (int u = 0; u < CPT; ++u) {
+            if (!live_u[u]) continue;
+            const cf o = red[t * CPT + u];
+            loc[(b * nrhs + r) * nc + cg * CPT + u] = cfmk(acc[t][u].x + o.x, acc[t][u].y + o.y);
+        }
     }
 }
 
@@ -708,7 +904,8 @@ size_t smem_bytes(int R, int U, int ncs_max) {
 }
 
 template <int R, int U>
-hfmm_status launch_down_ru(hfmm_plan_s* P, int l, int nrhs, int parts, int nchunk, int ncs_max, cudaStream_t st) {
+hfmm_status launch_down_ru(hfmm_plan_s* P, int l, int nrhs, int parts, int nchunk, int ncs_max, bool react_add,
+                           cudaStream_t st) {
     LevelInfo& lv = P->lev[l];
     const bool has_parent = l > P->lmin;
     const size_t sm = smem_bytes(R, U, ncs_max);
@@ -718,7 +915,7 @@ hfmm_status launch_down_ru(hfmm_plan_s* P, int l, int nrhs, int parts, int nchun
         P->leaf_begin, P->L, l, P->lmin, nrhs, lv.p, has_parent ? P->lev[l - 1].p : 0,
         has_parent ? P->lev[l - 1].loc32 : nullptr, has_parent ? P->lev[l - 1].t_l2l32 : nullptr, lv.mult32,
         lv.nv ? lv.v_begin : nullptr, lv.v_src, lv.v_off, lv.t_free32, lv.nr ? lv.r_begin : nullptr, lv.r_src,
-        lv.r_tab, lv.t_react32, parts, nchunk, ncs_max, lv.loc32);
+        lv.r_tab, lv.t_react32, parts, nchunk, ncs_max, lv.loc32, react_add, nullptr);
     HFMM_CUDA_TRY(cudaGetLastError());
     return HFMM_OK;
 }
@@ -791,6 +988,35 @@ hfmm_status small_m2m(hfmm_plan_s* P, int l, int nrhs, cudaStream_t st) {
     return HFMM_ERR_UNSUPPORTED;
 }
 
+// Reaction lists only, added onto loc, over the boxes that have one: one
+// right-hand side per pass and 32 warps per target box.  The lists concentrate on the boxes of the two lowest
+// rows (up to 2^(l+1) sources each at level l, the other boxes none), so
+// these few CTAs carry the pass and need the width.
+template <int U>
+hfmm_status launch_react_u(hfmm_plan_s* P, int l, int nrhs, int parts, int nchunk, int ncs_max, cudaStream_t st) {
+    constexpr int NW = 32;
+    LevelInfo& lv = P->lev[l];
+    const size_t sm = sizeof(cf) * ((size_t)NW * ncs_max + (size_t)NW * U * 32);
+    auto kern = down_small_kernel<1, U, NW>;
+    HFMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (lv.n_rtgt == 0) return HFMM_OK;
+    kern<<<(unsigned)(lv.n_rtgt * nchunk), NW * 32, sm, st>>>(
+        P->leaf_begin, P->L, l, P->lmin, nrhs, lv.p, 0, nullptr, nullptr, lv.mult32, nullptr, lv.v_src, lv.v_off,
+        lv.t_free32, lv.r_begin, lv.r_src, lv.r_tab, lv.t_react32, parts, nchunk, ncs_max, lv.loc32, true, lv.r_tgt);
+    HFMM_CUDA_TRY(cudaGetLastError());
+    return HFMM_OK;
+}
+
+// Levels with at least 64 blocks of 32 boxes and at most 64 coefficients run
+// L2L + V lists on vblock_kernel, then the reaction lists on down_small_kernel.
+int vblock_cpt(const hfmm_plan_s* P, int l) {
+    const LevelInfo& lv = P->lev[l];
+    const int nc = lv.ncoef, npp = l > P->lmin ? P->lev[l - 1].ncoef : 0;
+    if (l < 3 || lv.nbox < 64 * VB_T || nc > 64) return 0;
+    const int cpt = nc <= 32 ? 2 : nc <= 48 ? 3 : 4;
+    return vblock_smem(cpt, nc, npp) <= 200 * 1024 ? cpt : 0;
+}
+
 hfmm_status small_down(hfmm_plan_s* P, int l, int nrhs, int parts, cudaStream_t st) {
     LevelInfo& lv = P->lev[l];
     const bool has_parent = l > P->lmin;
@@ -798,7 +1024,31 @@ hfmm_status small_down(hfmm_plan_s* P, int l, int nrhs, int parts, cudaStream_t 
     int U, nchunk;
     pick_u(lv.ncoef, lv.nbox, &U, &nchunk);
     const int R = pick_r(nrhs, ncs_max, U);
-    HFMM_SMALL_DISPATCH(launch_down_ru, P, l, nrhs, parts, nchunk, ncs_max, st)
+    if (const int cpt = vblock_cpt(P, l)) {
+        const int nc = lv.ncoef, npp = has_parent ? P->lev[l - 1].ncoef : 0;
+        const size_t sm = vblock_smem(cpt, nc, npp);
+        const dim3 grid((unsigned)(lv.nbox / VB_T), (unsigned)nrhs);
+        const cf* ploc = has_parent ? P->lev[l - 1].loc32 : nullptr;
+        const cf* tl2l = has_parent ? P->lev[l - 1].t_l2l32 : nullptr;
+        const int32_t* vb = ((parts & HFMM_PART_FAR_FREE) && lv.nv) ? lv.v_begin : nullptr;
+#define HFMM_VBLOCK(C)                                                                                              \
+    do {                                                                                                            \
+        HFMM_CUDA_TRY(cudaFuncSetAttribute(vblock_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
+        vblock_kernel<C><<<grid, 256, sm, st>>>(P->leaf_begin, P->L, l, nrhs, nc, npp, ploc, tl2l, lv.mult32, vb,    \
+                                                lv.v_off, lv.t_free32, lv.loc32);                                   \
+    } while (0)
+        if (cpt == 2) HFMM_VBLOCK(2);
+        else if (cpt == 3) HFMM_VBLOCK(3);
+        else HFMM_VBLOCK(4);
+#undef HFMM_VBLOCK
+        HFMM_CUDA_TRY(cudaGetLastError());
+        if (!((parts & HFMM_PART_FAR_REACT) && lv.nr)) return HFMM_OK;
+        ++P->launches;   // the caller counts the reaction launch below
+        // nc <= 64 here, so U is 1 or 2
+        if (U == 1) return launch_react_u<1>(P, l, nrhs, parts, nchunk, lv.ncoef, st);
+        return launch_react_u<2>(P, l, nrhs, parts, nchunk, lv.ncoef, st);
+    }
+    HFMM_SMALL_DISPATCH(launch_down_ru, P, l, nrhs, parts, nchunk, ncs_max, false, st)
     hfmm_set_error("small downward pass: no kernel for R=%d U=%d", R, U);
     return HFMM_ERR_UNSUPPORTED;
 }

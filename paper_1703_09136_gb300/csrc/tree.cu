@@ -383,6 +383,16 @@ hfmm_status build_lists(hfmm_plan_s* P, cudaStream_t st) {
             HFMM_TRY(plan_alloc(P, (void**)&lv.r_tab, sizeof(int32_t) * lv.nr));
             r_list_kernel<<<ceil_div(nbox, TB), TB, 0, st>>>(P->leaf_begin, L, l, lstar, P->y0, lv.h, lv.r_begin, nullptr, lv.r_src, lv.r_tab);
             HFMM_CUDA_TRY(cudaGetLastError());
+            // the boxes that have a reaction list (the few-RHS reaction pass runs over these only)
+            std::vector<int32_t> rb(nbox + 1), tg;
+            HFMM_CUDA_TRY(cudaMemcpyAsync(rb.data(), lv.r_begin, sizeof(int32_t) * (nbox + 1), cudaMemcpyDeviceToHost, st));
+            HFMM_CUDA_TRY(cudaStreamSynchronize(st));
+            for (int64_t b = 0; b < nbox; ++b)
+                if (rb[b + 1] > rb[b]) tg.push_back((int32_t)b);
+            lv.n_rtgt = (int64_t)tg.size();
+            HFMM_TRY(plan_alloc(P, (void**)&lv.r_tgt, sizeof(int32_t) * tg.size()));
+            HFMM_CUDA_TRY(cudaMemcpyAsync(lv.r_tgt, tg.data(), sizeof(int32_t) * tg.size(), cudaMemcpyHostToDevice, st));
+            HFMM_CUDA_TRY(cudaStreamSynchronize(st));
         }
     }
     // the coarsest level with work

@@ -746,6 +746,43 @@ def test_small_rhs_engine_matches_tensor_engine_and_fp64(nrhs):
         p.close()
 
 
+@pytest.mark.parametrize("p_fixed", [0, 18, 28])
+def test_blocked_few_rhs_downward_pass_matches_fp64_per_part(p_fixed):
+    """Few right-hand sides at a level of 4,096 boxes: L2L and the V lists run
+    on the blocked kernel (32 target boxes per CTA sharing each staged
+    matrix; 2, 3 and 4 output coefficients per lane for nc up to 32, 48, 64),
+    the reaction lists on the per-box kernel added on top.  Each far-field
+    part, the whole apply and the adjoint against the FP64 path at the same
+    p, right-hand side by right-hand side; two applies give the same bits."""
+    from paper_1703_09136_gb300 import MIXED
+    xy = W.points_in_box(4, 65536, ((0.0, 1.0), (0.02, 1.02)), salt=31)
+    nrhs = 2
+    q = W.strengths(4, 65536, nrhs, salt=32)
+    sm = Plan(xy, CFG4_MED, tol=1e-6, p=p_fixed, leaf_size=16, max_rhs=nrhs, precision=MIXED)
+    f64 = Plan(xy, CFG4_MED, tol=1e-6, p=p_fixed, leaf_size=16, max_rhs=nrhs)
+    info = sm.info
+    assert info["levels"] == 6
+    nc = 2 * info["p"][6] + 1
+    lo, hi = {0: (1, 32), 18: (33, 48), 28: (49, 64)}[p_fixed]
+    assert lo <= nc <= hi, nc
+    q32 = torch.from_numpy(q.astype(np.complex64)).cuda()
+    q64 = torch.from_numpy(q).cuda()
+    full = f64.apply(q64).cpu().numpy()
+    for part in (2, 4, 6, 15):
+        y = sm.apply(q32, parts=part).cpu().numpy().astype(np.complex128)
+        ref = f64.apply(q64, parts=part).cpu().numpy()
+        for r in range(nrhs):
+            err = np.linalg.norm(y[r] - ref[r]) / np.linalg.norm(full[r])
+            assert err < MIXED_TOL, (part, r, err)
+    ya = sm.adjoint(q32).cpu().numpy().astype(np.complex128)
+    ra = f64.adjoint(q64).cpu().numpy()
+    for r in range(nrhs):
+        assert direct.rel_l2(ya[r], ra[r]) < MIXED_TOL
+    assert torch.equal(sm.apply(q32), sm.apply(q32))
+    sm.close()
+    f64.close()
+
+
 def test_persistent_batch_forward_and_adjoint_match_single_plans():
     """Uneven mixed-precision instances (1 and 3 right-hand sides) through the
     persistent batch kernel: every stage of every instance from one device
