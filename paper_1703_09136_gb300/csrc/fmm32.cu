@@ -888,6 +888,24 @@ extern "C" hfmm_status hfmm_debug_green_f32(int32_t n, const double* z, float* g
     return HFMM_OK;
 }
 
+// The near field on a low-priority stream concurrently with the far-field
+// chain on a high-priority one (both created on first use), forked from st
+// after everything already queued there.
+hfmm_status fork_near_far(hfmm_plan_s* P, cudaStream_t st) {
+    if (!P->far_st) {
+        int least = 0, greatest = 0;
+        HFMM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        HFMM_CUDA_TRY(cudaStreamCreateWithPriority(&P->far_st, cudaStreamNonBlocking, greatest));
+        HFMM_CUDA_TRY(cudaStreamCreateWithPriority(&P->near_st, cudaStreamNonBlocking, least));
+        for (cudaEvent_t* e : {&P->ev_fork, &P->ev_near_done, &P->ev_far_done})
+            HFMM_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
+    HFMM_CUDA_TRY(cudaEventRecord(P->ev_fork, st));
+    HFMM_CUDA_TRY(cudaStreamWaitEvent(P->far_st, P->ev_fork, 0));
+    HFMM_CUDA_TRY(cudaStreamWaitEvent(P->near_st, P->ev_fork, 0));
+    return HFMM_OK;
+}
+
 hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts, bool adjoint,
                         cudaStream_t st) {
     const int64_t n = P->n;
@@ -964,17 +982,7 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
         const bool concurrent = l2p_fused && near_free;
         cudaStream_t fs = st;
         if (concurrent) {
-            if (!P->far_st) {
-                int least = 0, greatest = 0;
-                HFMM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-                HFMM_CUDA_TRY(cudaStreamCreateWithPriority(&P->far_st, cudaStreamNonBlocking, greatest));
-                HFMM_CUDA_TRY(cudaStreamCreateWithPriority(&P->near_st, cudaStreamNonBlocking, least));
-                for (cudaEvent_t* e : {&P->ev_fork, &P->ev_near_done, &P->ev_far_done})
-                    HFMM_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
-            }
-            HFMM_CUDA_TRY(cudaEventRecord(P->ev_fork, st));
-            HFMM_CUDA_TRY(cudaStreamWaitEvent(P->far_st, P->ev_fork, 0));
-            HFMM_CUDA_TRY(cudaStreamWaitEvent(P->near_st, P->ev_fork, 0));
+            HFMM_TRY(fork_near_far(P, st));
             HFMM_TRY(near_section(true, false, P->near_st));
             HFMM_CUDA_TRY(cudaEventRecord(P->ev_near_done, P->near_st));
             fs = P->far_st;

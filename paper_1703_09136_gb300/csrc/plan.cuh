@@ -350,6 +350,8 @@ void persist_destroy(PersistBatch* B);
 hfmm_status init_small(hfmm_plan_s* P, cudaStream_t st);
 // P2M, M2M, downward pass and near field + L2P of one apply on the sorted q32 / y32
 hfmm_status apply_small(hfmm_plan_s* P, int nrhs, int parts, cudaStream_t st);
+// forks P->near_st (low priority) and P->far_st (high priority) from st
+hfmm_status fork_near_far(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status build_local_coords(hfmm_plan_s* P, cudaStream_t st);
 hfmm_status fill_near_tiles(hfmm_plan_s* P, int64_t nchunks, int64_t total_rows, cudaStream_t st);
 // p2p_tc.cu

@@ -33,7 +33,7 @@ namespace {
 constexpr int SM_W = 8;                 // warps per CTA of the translation kernels
 constexpr int H0N = 64, H0D = 5;        // FP32 H0 table: 64 intervals on [0, 16], degree 5
 constexpr float H0_ZMAX = 16.0f, H0_INV_DZ = 4.0f;
-__constant__ float c_h0[2][H0N][H0D + 1];
+__device__ float g_h0[2][H0N][H0D + 1];    // global memory: the CTAs copy it to shared memory with coalesced loads
 
 __device__ __forceinline__ void cfma(cf& acc, cf a, cf b) {
     acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(256, CPT == 2 ? 4 : 2) vblock_kernel(const int
                                                         const int32_t* __restrict__ v_begin,
                                                         const int32_t* __restrict__ v_off,
                                                         const cf* __restrict__ Tfree, cf* __restrict__ loc) {
-    constexpr int VB_PF = CPT == 2 ? 3 : 4;        // matrix rows per lane per fetch (two fetches in flight)
+    constexpr int VB_PF = CPT == 2 ? 2 : 4;        // matrix rows per lane per fetch (two fetches in flight)
     extern __shared__ float4 sm_vb[];
     const int kmax = max(nc, npp), ncw = nc | 1, npw = npp | 1;   // odd row strides
     const int wsz = max(VB_SLOTS * ncw, 4 * 32 * 4 * CPT);
@@ -397,23 +397,16 @@ __global__ void __launch_bounds__(256, CPT == 2 ? 4 : 2) vblock_kernel(const int
         }
         const cf* M = (isl2l ? Tl2l + (int64_t)(op - VB_L2L) * npp * nc : Tfree + (int64_t)op * nc * nc) + cg * CPT;
         const int K = isl2l ? npp : nc;
-        // rows k0 .. k0 + VB_PF - 1 in registers while the next VB_PF are in flight
-        cf mn[VB_PF][CPT];
-        auto fetch = [&](int k0) {
+        // two register sets of VB_PF matrix rows: one is used while the other is in flight
+        cf ma[VB_PF][CPT], mb[VB_PF][CPT];
+        auto fetch = [&](cf (&mr)[VB_PF][CPT], int k0) {
 #pragma unroll
             for (int i = 0; i < VB_PF; ++i)
 #pragma unroll
                 for (int u = 0; u < CPT; ++u)
-                    mn[i][u] = (live_u[u] && k0 + i < K) ? __ldg(M + (int64_t)(k0 + i) * nc + u) : cfmk(0.f, 0.f);
+                    mr[i][u] = (live_u[u] && k0 + i < K) ? __ldg(M + (int64_t)(k0 + i) * nc + u) : cfmk(0.f, 0.f);
         };
-        fetch(0);
-        for (int k0 = 0; k0 < K; k0 += VB_PF) {
-            cf mv[VB_PF][CPT];
-#pragma unroll
-            for (int i = 0; i < VB_PF; ++i)
-#pragma unroll
-                for (int u = 0; u < CPT; ++u) mv[i][u] = mn[i][u];
-            if (k0 + VB_PF < K) fetch(k0 + VB_PF);
+        auto use = [&](const cf (&mr)[VB_PF][CPT], int k0) {
 #pragma unroll
             for (int i = 0; i < VB_PF; ++i) {
                 if (k0 + i >= K) break;
@@ -421,9 +414,17 @@ __global__ void __launch_bounds__(256, CPT == 2 ? 4 : 2) vblock_kernel(const int
                 for (int t = 0; t < 4; ++t) {
                     const cf sv = sp[t][k0 + i];
 #pragma unroll
-                    for (int u = 0; u < CPT; ++u) cfma(acc[t][u], sv, mv[i][u]);
+                    for (int u = 0; u < CPT; ++u) cfma(acc[t][u], sv, mr[i][u]);
                 }
             }
+        };
+        fetch(ma, 0);
+        for (int k0 = 0; k0 < K; k0 += 2 * VB_PF) {
+            if (k0 + VB_PF < K) fetch(mb, k0 + VB_PF);
+            use(ma, k0);
+            if (k0 + VB_PF >= K) break;
+            if (k0 + 2 * VB_PF < K) fetch(ma, k0 + 2 * VB_PF);
+            use(mb, k0 + VB_PF);
         }
     }
     // warp 2 c + 1's sums go to shared memory (over the window), warp 2 c adds and stores
@@ -461,10 +462,11 @@ __global__ void __launch_bounds__(128) near_small_kernel(const int32_t* __restri
                                                          const cf* __restrict__ loc, const cf* __restrict__ basis,
                                                          int nc, cf* __restrict__ ys) {
     __shared__ float tj[H0N][H0D + 1], tr[H0N][H0D + 1];
-    for (int e = threadIdx.x; e < H0N * (H0D + 1); e += blockDim.x) {
-        tj[e / (H0D + 1)][e % (H0D + 1)] = c_h0[0][e / (H0D + 1)][e % (H0D + 1)];
-        tr[e / (H0D + 1)][e % (H0D + 1)] = c_h0[1][e / (H0D + 1)][e % (H0D + 1)];
-    }
+    if (near)   // an L2P-only pass needs no table
+        for (int e = threadIdx.x; e < H0N * (H0D + 1); e += blockDim.x) {
+            tj[e / (H0D + 1)][e % (H0D + 1)] = g_h0[0][e / (H0D + 1)][e % (H0D + 1)];
+            tr[e / (H0D + 1)][e % (H0D + 1)] = g_h0[1][e / (H0D + 1)][e % (H0D + 1)];
+        }
     __syncthreads();
     const int64_t b = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
     if (b >= nleaf) return;
@@ -528,6 +530,7 @@ __global__ void __launch_bounds__(128) near_small_kernel(const int32_t* __restri
                 }
             if (loc) {
                 // L2P: (i/4) sum_m b~[r][m] conj(B[t][m])
+#pragma unroll 4
                 for (int m = half; m < nc; m += mstep) {
                     const cf B = live ? basis[(int64_t)t * nc + m] : cfmk(0.f, 0.f);
                     const cf g = cfmk(0.25f * B.y, 0.25f * B.x);
@@ -588,8 +591,8 @@ __global__ void __launch_bounds__(SM_W * 32, 3) persist_kernel(const PSeg* __res
     __shared__ float tj[H0N][H0D + 1], tr[H0N][H0D + 1];
     __shared__ int s_item, s_seg;
     for (int e = threadIdx.x; e < H0N * (H0D + 1); e += blockDim.x) {
-        tj[e / (H0D + 1)][e % (H0D + 1)] = c_h0[0][e / (H0D + 1)][e % (H0D + 1)];
-        tr[e / (H0D + 1)][e % (H0D + 1)] = c_h0[1][e / (H0D + 1)][e % (H0D + 1)];
+        tj[e / (H0D + 1)][e % (H0D + 1)] = g_h0[0][e / (H0D + 1)][e % (H0D + 1)];
+        tr[e / (H0D + 1)][e % (H0D + 1)] = g_h0[1][e / (H0D + 1)][e % (H0D + 1)];
     }
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
     cf* stage = (cf*)sm_small + (int64_t)w * R * ncs_max;
@@ -962,7 +965,7 @@ void pick_u(int ncout, int64_t nbox, int* U, int* nchunk) {
 
 hfmm_status init_small(hfmm_plan_s* P, cudaStream_t st) {
     (void)P;
-    HFMM_CUDA_TRY(cudaMemcpyToSymbolAsync(c_h0, h0_table_host(), sizeof(c_h0), 0, cudaMemcpyHostToDevice, st));
+    HFMM_CUDA_TRY(cudaMemcpyToSymbolAsync(g_h0, h0_table_host(), sizeof(g_h0), 0, cudaMemcpyHostToDevice, st));
     return HFMM_OK;
 }
 
@@ -1048,6 +1051,30 @@ hfmm_status small_down(hfmm_plan_s* P, int l, int nrhs, int parts, cudaStream_t 
         if (U == 1) return launch_react_u<1>(P, l, nrhs, parts, nchunk, lv.ncoef, st);
         return launch_react_u<2>(P, l, nrhs, parts, nchunk, lv.ncoef, st);
     }
+    // Levels with few (box, chunk) CTAs of plans with at least 2^17 points:
+    // wider CTAs (16 or 32 warps splitting the box's sources, one right-hand
+    // side per pass) keep more matrix rows in flight from L2 than 8-warp CTAs
+    // that leave most SMs idle.  Smaller plans keep 8 warps: they are the
+    // instances of batches, whose branches fill the SMs together and where wide
+    // CTAs only block co-residency (measured 2.7 -> 3.3 ms on 32 instances of
+    // 4k-120k points).  The choice depends on the plan alone, so a batch gives
+    // the bits of its single-plan applies.
+    const int64_t ncta = lv.nbox * nchunk;
+    if (U == 1 && ncta < 8 * 152 && P->n >= (1 << 17)) {
+        const int nw = ncta < 2 * 152 ? 32 : 16;
+        const size_t sm = sizeof(cf) * ((size_t)nw * ncs_max + (size_t)nw * 32);
+        if (sm <= 200 * 1024) {
+            auto kern = nw == 32 ? down_small_kernel<1, 1, 32> : down_small_kernel<1, 1, 16>;
+            HFMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            kern<<<(unsigned)ncta, nw * 32, sm, st>>>(
+                P->leaf_begin, P->L, l, P->lmin, nrhs, lv.p, has_parent ? P->lev[l - 1].p : 0,
+                has_parent ? P->lev[l - 1].loc32 : nullptr, has_parent ? P->lev[l - 1].t_l2l32 : nullptr, lv.mult32,
+                lv.nv ? lv.v_begin : nullptr, lv.v_src, lv.v_off, lv.t_free32, lv.nr ? lv.r_begin : nullptr,
+                lv.r_src, lv.r_tab, lv.t_react32, parts, nchunk, ncs_max, lv.loc32, false, nullptr);
+            HFMM_CUDA_TRY(cudaGetLastError());
+            return HFMM_OK;
+        }
+    }
     HFMM_SMALL_DISPATCH(launch_down_ru, P, l, nrhs, parts, nchunk, ncs_max, false, st)
     hfmm_set_error("small downward pass: no kernel for R=%d U=%d", R, U);
     return HFMM_ERR_UNSUPPORTED;
@@ -1072,14 +1099,30 @@ hfmm_status small_near(hfmm_plan_s* P, int nrhs, bool near, bool l2p, cudaStream
 hfmm_status apply_small(hfmm_plan_s* P, int nrhs, int parts, cudaStream_t st) {
     const int L = P->L;
     const int64_t n = P->n;
-    StageTimer tm{P, st};
     const double MAC = 8.0 * nrhs, C = 8.0 * nrhs;
     const bool far = (parts & (HFMM_PART_FAR_FREE | HFMM_PART_FAR_REACT)) != 0;
     const bool near = (parts & HFMM_PART_NEAR_FREE) != 0;
+    // Both fields: the near field (first writer of y32 after the memset) runs on
+    // a low-priority stream while the far-field chain runs on a high-priority
+    // one and fills the SMs that the coarse levels' few CTAs leave idle; the
+    // leaves' L2P then waits for it and adds into y32.
+    const bool concurrent = far && near;
+    cudaStream_t fs = st;
+    if (concurrent) {
+        HFMM_TRY(fork_near_far(P, st));
+        StageTimer tn{P, P->near_st};
+        tn.begin(HFMM_STAGE_P2P);
+        HFMM_TRY(small_near(P, nrhs, true, false, P->near_st));
+        ++P->launches;
+        tn.end(HFMM_STAGE_P2P);
+        HFMM_CUDA_TRY(cudaEventRecord(P->ev_near_done, P->near_st));
+        fs = P->far_st;
+    }
+    StageTimer tm{P, fs};
     if (far) {
         LevelInfo& leaf = P->lev[L];
         tm.begin(HFMM_STAGE_P2M);
-        HFMM_TRY(small_p2m(P, nrhs, st));
+        HFMM_TRY(small_p2m(P, nrhs, fs));
         ++P->launches;
         tm.end(HFMM_STAGE_P2M);
         P->st_flops[HFMM_STAGE_P2M] = MAC * n * leaf.ncoef;
@@ -1087,7 +1130,7 @@ hfmm_status apply_small(hfmm_plan_s* P, int nrhs, int parts, cudaStream_t st) {
         tm.begin(HFMM_STAGE_M2M);
         for (int l = L - 1; l >= P->lmin; --l) {
             LevelInfo& lv = P->lev[l];
-            HFMM_TRY(small_m2m(P, l, nrhs, st));
+            HFMM_TRY(small_m2m(P, l, nrhs, fs));
             ++P->launches;
             P->st_flops[HFMM_STAGE_M2M] += MAC * 4.0 * lv.nbox * lv.ncoef * P->lev[l + 1].ncoef;
             P->st_bytes[HFMM_STAGE_M2M] += C * (4.0 * lv.nbox * P->lev[l + 1].ncoef + lv.nbox * lv.ncoef);
@@ -1096,7 +1139,7 @@ hfmm_status apply_small(hfmm_plan_s* P, int nrhs, int parts, cudaStream_t st) {
         tm.begin(HFMM_STAGE_DOWN);
         for (int l = P->lmin; l <= L; ++l) {
             LevelInfo& lv = P->lev[l];
-            HFMM_TRY(small_down(P, l, nrhs, parts, st));
+            HFMM_TRY(small_down(P, l, nrhs, parts, fs));
             ++P->launches;
             double pairs = 0.0;
             if (parts & HFMM_PART_FAR_FREE) pairs += (double)lv.nv;
@@ -1110,10 +1153,19 @@ hfmm_status apply_small(hfmm_plan_s* P, int nrhs, int parts, cudaStream_t st) {
     }
     if (near || far) {
         LevelInfo& leaf = P->lev[L];
-        tm.begin(HFMM_STAGE_P2P);
-        HFMM_TRY(small_near(P, nrhs, near, far, st));
-        ++P->launches;
-        tm.end(HFMM_STAGE_P2P);
+        if (concurrent) {
+            // the leaves' L2P after the near field (both add into y32)
+            HFMM_CUDA_TRY(cudaStreamWaitEvent(fs, P->ev_near_done, 0));
+            HFMM_TRY(small_near(P, nrhs, false, true, fs));
+            ++P->launches;
+            HFMM_CUDA_TRY(cudaEventRecord(P->ev_far_done, fs));
+            HFMM_CUDA_TRY(cudaStreamWaitEvent(st, P->ev_far_done, 0));
+        } else {
+            tm.begin(HFMM_STAGE_P2P);
+            HFMM_TRY(small_near(P, nrhs, near, far, st));
+            ++P->launches;
+            tm.end(HFMM_STAGE_P2P);
+        }
         P->st_flops[HFMM_STAGE_P2P] = (near ? MAC * (double)P->p2p_point_pairs : 0.0) +
                                       (far ? MAC * n * leaf.ncoef : 0.0);
         P->st_bytes[HFMM_STAGE_P2P] = 3.0 * C * n + 16.0 * n + (far ? C * leaf.nbox * leaf.ncoef + 8.0 * n * leaf.ncoef : 0.0);
