@@ -620,7 +620,8 @@ constexpr int PR_SRC = 32;
 template <int NCM>
 __global__ void __launch_bounds__(64) p2m_rows_kernel(const int32_t* lb, const cf* qs, const cf* basis, int nrhs,
                                                       int nc, cf* mult, __half* amma, float* asc, int kc, int nrc,
-                                                      int nsb, int sblk, bool write_mult) {
+                                                      int nsb, int sblk, bool write_mult, const unsigned* qmax,
+                                                      float gain) {
     static_assert(NCM % 8 == 0 && NCM <= 32, "row staging holds the padded K chunks");
     __shared__ union {
         cf q[PR_SRC][64];
@@ -670,11 +671,16 @@ __global__ void __launch_bounds__(64) p2m_rows_kernel(const int32_t* lb, const c
         }
     for (int k = 2 * nc; k < kc * 16; ++k) row[k] = 0.f;
     const int64_t rb = b * nrc + rc;
+    // level-wide scale (qmax given): the exponent of the bound
+    // |a~_m| <= sum_j |q_j| |B[j][m]| <= sqrt(2) max(|Re q|, |Im q|) gain, with
+    // a factor 2 (sqrt(2) and the FP32 rounding of the sum), the same for every leaf
+    const int ex_all = qmax ? (live ? tc::f16_exp(2.0f * __uint_as_float(qmax[r0 + r]) * gain) : 0) : 0;
     for (int blk = 0; blk < nsb; ++blk) {
         const int c0 = blk * sblk, c1 = min(kc, c0 + sblk);
         float mx = 0.f;
-        for (int k = c0 * 16; k < c1 * 16; ++k) mx = fmaxf(mx, fabsf(row[k]));
-        const int ex = tc::f16_exp(mx);
+        if (!qmax)
+            for (int k = c0 * 16; k < c1 * 16; ++k) mx = fmaxf(mx, fabsf(row[k]));
+        const int ex = qmax ? ex_all : tc::f16_exp(mx);
         asc[(rb * nsb + blk) * 64 + r] = tc::pow2f(-ex);
         const float s = tc::pow2f(ex);
         for (int c = c0; c < c1; ++c) {
@@ -998,7 +1004,8 @@ hfmm_status apply_mixed(hfmm_plan_s* P, int nrhs, const cf* q, cf* y, int parts,
                     const dim3 grid((unsigned)lv.nbox, (unsigned)((nrhs + 63) / 64));
 #define HFMM_P2M_ROWS(NCM)                                                                                     \
     p2m_rows_kernel<NCM><<<grid, 64, 0, fs>>>(P->leaf_begin, P->q32, P->basis32, nrhs, nc, lv.mult32, lv.tc_amma, \
-                                              lv.tc_asc, lv.tc_kc, nrc, lv.tc_nb, lv.tc_nbw / 16, !tc_down)
+                                              lv.tc_asc, lv.tc_kc, nrc, lv.tc_nb, lv.tc_nbw / 16, !tc_down,    \
+                                              P->tc_leaf_runs ? P->qmax : nullptr, P->p2m_gain)
                     if (nc <= 16) HFMM_P2M_ROWS(16);
                     else if (nc <= 24) HFMM_P2M_ROWS(24);
                     else HFMM_P2M_ROWS(32);

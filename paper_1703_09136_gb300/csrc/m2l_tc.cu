@@ -40,6 +40,7 @@
 // result.  Every mbarrier wait is bounded; a timeout sets an error flag
 // instead of hanging.
 #include <algorithm>
+#include <cstring>
 #include <map>
 #include <vector>
 
@@ -116,7 +117,10 @@ bool tc_l2p_fits(int nbw) {
 struct TcTile { int32_t b0, b1, s0, s1; };          // boxes (-1: empty), step range
 // kind 0 free M2L, 1 reaction M2L, 2 secondary source (L2L parent or M2M child);
 // src -1: none; K chunks c0 .. c1 - 1 of the operator
-struct TcStep { int32_t kind, idx, src0, src1, c0, c1; };
+// cont = 1: the next step of the tile accumulates onto this one in TMEM (same
+// factor 2^-(ea + eb) for every row: the leaf level with level-wide scales),
+// so the result is drained once after the last step of the run.
+struct TcStep { int32_t kind, idx, src0, src1, c0, c1, cont; };
 
 // Largest |Re|, |Im| of each complex matrix M[i] (nin x nout) -> 2^-e, the
 // factor that undoes its f16 scaling.
@@ -136,6 +140,43 @@ __global__ void tc_bscale_kernel(const cf* M, int nin, int nout, float* sc) {
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
         sc[i] = pow2f(-f16_exp(m));
     }
+}
+
+// One factor for the matrices of two tables (the larger of all their factors,
+// i.e. the f16 scaling of the largest entry), written back to both.
+__global__ void tc_common_scale_kernel(float* sa, int na, float* sb, int nb) {
+    __shared__ float red[32];
+    float m = 0.0f;
+    for (int e = threadIdx.x; e < na + nb; e += blockDim.x) m = fmaxf(m, e < na ? sa[e] : sb[e - na]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    m = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+    for (int e = threadIdx.x; e < na + nb; e += blockDim.x) {
+        if (e < na) sa[e] = m;
+        else sb[e - na] = m;
+    }
+}
+
+// Largest over leaves and coefficients m of sum_j |B[j][m]| (the leaf's points
+// j): |a~_m| <= max_j |q_j| times this.  One warp per leaf; float bits max.
+__global__ void p2m_gain_kernel(const int32_t* lb, int64_t nleaf, const cf* basis, int nc, unsigned* gmax) {
+    const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= nleaf) return;
+    const int32_t lo = lb[b], hi = lb[b + 1];
+    float m = 0.0f;
+    for (int n = lane; n < nc; n += 32) {
+        float sum = 0.0f;
+        for (int32_t j = lo; j < hi; ++j) {
+            const cf v = basis[(int64_t)j * nc + n];
+            sum += sqrtf(v.x * v.x + v.y * v.y);
+        }
+        m = fmaxf(m, sum);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0 && m > 0.0f) atomicMax(gmax, __float_as_uint(m));
 }
 
 // Pre-split B chunks: for matrix index i, chunk c, part (0 hi, 1 lo):
@@ -311,12 +352,18 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
             const float fb = st.kind == 0 ? sfree[st.idx] : st.kind == 1 ? sreact[st.idx] : ssec[st.idx];
             return scs[(((int64_t)src * nrc + rc) * nsb + st.c0 / sbk) * 64 + rr] * fb;
         };
-        float f_next = nsteps > 0 ? factor(0) : 0.0f;
-        for (int s = 0; s < nsteps && ok; ++s) {
-            const int b = s % CFG::nbuf;
-            const float f = f_next;
-            if (s + 1 < nsteps) f_next = factor(s + 1);   // one step ahead
-            bool good = !s_abort && mbar_wait(&dfull[b], (uint32_t)((s / CFG::nbuf) & 1), spin);
+        // one drain per run of steps (a step, or the steps joined by cont); the
+        // run's factor is that of any of its steps with a source for this row
+        for (int s = 0, run = 0; s < nsteps && ok; ++run) {
+            int e = s;
+            float f = factor(s);
+            while (e + 1 < nsteps && steps[sbeg + e].cont) {
+                ++e;
+                if (f == 0.0f) f = factor(e);
+            }
+            s = e + 1;
+            const int b = run % CFG::nbuf;
+            bool good = !s_abort && mbar_wait(&dfull[b], (uint32_t)((run / CFG::nbuf) & 1), spin);
             good = __all_sync(0xffffffffu, good);
             if (!good) { ok = false; s_abort = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -483,17 +530,24 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
                 mbar_wait(&full[k % TC_STAGES], (uint32_t)((k / TC_STAGES) & 1));
         }
     } else if (warp == 5 && lane == 0) {
-        // ---------------- MMA issuer: one TMEM buffer per source step ----------------
+        // ---------------- MMA issuer: one TMEM buffer per run of source steps ----------------
         constexpr uint32_t idesc = idesc_f16(NB);
-        int i = 0;
-        bool ok = true;
+        int i = 0, run = 0;
+        bool ok = true, cont_prev = false;
         int nk_next = nsteps > 0 ? steps[sbeg].c1 - steps[sbeg].c0 : 0;
+        bool cont_next = nsteps > 0 && steps[sbeg].cont;
         for (int s = 0; s < nsteps && ok; ++s) {
             const int nk = nk_next;
-            if (s + 1 < nsteps) nk_next = steps[sbeg + s + 1].c1 - steps[sbeg + s + 1].c0;
-            const int b = s % CFG::nbuf;
-            if (s_abort || !mbar_wait(&dfree[b], (uint32_t)(((s / CFG::nbuf) & 1) ^ 1), spin)) { s_abort = 1; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const bool cont = cont_next && s + 1 < nsteps;   // a run ends with the segment
+            if (s + 1 < nsteps) {
+                nk_next = steps[sbeg + s + 1].c1 - steps[sbeg + s + 1].c0;
+                cont_next = steps[sbeg + s + 1].cont;
+            }
+            const int b = run % CFG::nbuf;
+            if (!cont_prev) {
+                if (s_abort || !mbar_wait(&dfree[b], (uint32_t)(((run / CFG::nbuf) & 1) ^ 1), spin)) { s_abort = 1; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            }
             const uint32_t dt = taddr + (uint32_t)(b * CFG::buf_cols);
             for (int c = 0; c < nk; ++c, ++i) {
                 const int stg = i % TC_STAGES;
@@ -503,12 +557,16 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
                 const uint32_t sb = su32(smem + stg * stage_bytes);
                 const uint64_t ah = sdesc(sb, 512), al = sdesc(sb + 256, 512);
                 const uint64_t bh = sdesc(sb + 8192, 256), bl = sdesc(sb + 8192 + NB * 32, 256);
-                mma_f16(dt, ah, bh, idesc, c > 0 ? 1u : 0u);
+                mma_f16(dt, ah, bh, idesc, (c > 0 || cont_prev) ? 1u : 0u);
                 mma_f16(dt, ah, bl, idesc, 1);
                 mma_f16(dt, al, bh, idesc, 1);
                 mma_commit(&empty[stg]);
             }
-            if (ok) mma_commit(&dfull[b]);
+            if (ok && !cont) {
+                mma_commit(&dfull[b]);
+                ++run;
+            }
+            cont_prev = cont;
         }
         // every MMA of this thread has completed before TMEM is released
         mma_commit(&mdone);
@@ -801,6 +859,30 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
         if (lv.nr > 0)
             HFMM_TRY(btable(P, lv.t_react32, lv.n_react_entries, lv.ncoef, lv.ncoef, Np, lv.tc_kc, &lv.tc_breact,
                             &lv.tc_sreact, st));
+        // leaf level: level-wide scales (one factor for the multipoles of a row,
+        // one for the free and reaction tables) when the leaf P2M is the row kernel
+        const bool runs = l == L && lv.ncoef <= 32 && lv.nv + lv.nr > 0;
+        if (runs) {
+            const int na = lv.nv > 0 ? 49 : 0, nr = lv.nr > 0 ? lv.n_react_entries : 0;
+            tc_common_scale_kernel<<<1, 256, 0, st>>>(lv.tc_sfree, na, lv.tc_sreact, nr);
+            HFMM_CUDA_TRY(cudaGetLastError());
+            if (na) tc_btable_kernel<<<4 * 152, 256, 0, st>>>(lv.t_free32, lv.tc_sfree, na, lv.ncoef, lv.ncoef, Np,
+                                                               lv.tc_kc, lv.tc_bfree);
+            if (nr) tc_btable_kernel<<<4 * 152, 256, 0, st>>>(lv.t_react32, lv.tc_sreact, nr, lv.ncoef, lv.ncoef, Np,
+                                                               lv.tc_kc, lv.tc_breact);
+            HFMM_CUDA_TRY(cudaGetLastError());
+            unsigned* dg = nullptr;
+            HFMM_TRY(plan_alloc(P, (void**)&dg, sizeof(unsigned)));
+            HFMM_CUDA_TRY(cudaMemsetAsync(dg, 0, sizeof(unsigned), st));
+            p2m_gain_kernel<<<(unsigned)ceil_div(lv.nbox, 4), 128, 0, st>>>(P->leaf_begin, lv.nbox, P->basis32,
+                                                                            lv.ncoef, dg);
+            HFMM_CUDA_TRY(cudaGetLastError());
+            unsigned hg = 0;
+            HFMM_CUDA_TRY(cudaMemcpyAsync(&hg, dg, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+            HFMM_CUDA_TRY(cudaStreamSynchronize(st));
+            std::memcpy(&P->p2m_gain, &hg, sizeof(float));
+            P->tc_leaf_runs = true;
+        }
         if (has_parent)
             HFMM_TRY(btable(P, P->lev[l - 1].t_l2l32, 4, npp, lv.ncoef, Np, lv.tc_kc2, &lv.tc_bl2l, &lv.tc_sl2l, st));
         const int sb_own = lv.tc_nbw / 16, sb_par = has_parent ? P->lev[l - 1].tc_nbw / 16 : 1;
@@ -831,6 +913,7 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
         pair_tiles(nbox, nonempty, [&](int32_t b0, int32_t b1) {
             const int c = (int)((b0 >= 0 ? b0 : b1) & 3);
             if (has_parent) push_step(steps, 2, c, b0 >= 0 ? b0 >> 2 : -1, b1 >= 0 ? b1 >> 2 : -1, lv.tc_kc2, sb_par);
+            const size_t first = steps.size();   // the tile's free and reaction steps start here
             if (lv.nv) {
                 int32_t s0[49], s1[49];
                 for (int o = 0; o < 49; ++o) s0[o] = s1[o] = -1;
@@ -851,6 +934,10 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
                 for (auto& kv : mm)
                     push_step(steps, 1, kv.first, kv.second.first, kv.second.second, lv.tc_kc, sb_own);
             }
+            // one run per K block: consecutive free / reaction steps over the same chunks
+            if (runs)
+                for (size_t j = first; j + 1 < steps.size(); ++j)
+                    steps[j].cont = steps[j].c0 == steps[j + 1].c0 ? 1 : 0;
         }, tiles, steps);
         HFMM_TRY(upload_tiles(P, tiles, steps, &lv.tc_tiles, &lv.tc_steps, &lv.tc_ntiles, &lv.tc_maxsteps));
     }
@@ -859,17 +946,30 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
         LevelInfo& lv = P->lev[l];
         const LevelInfo& ch = P->lev[l + 1];
         HFMM_TRY(btable(P, lv.t_m2m32, 4, ch.ncoef, lv.ncoef, lv.tc_np, ch.tc_kc, &lv.tc_bm2m, &lv.tc_sm2m, st));
+        // M2M from the leaves (their rows written with level-wide scales): one
+        // factor for the four shift matrices, so a tile's four children accumulate in TMEM
+        const bool mruns = P->tc_leaf_runs && l == L - 1;
+        if (mruns) {
+            tc_common_scale_kernel<<<1, 256, 0, st>>>(lv.tc_sm2m, 4, nullptr, 0);
+            tc_btable_kernel<<<4 * 152, 256, 0, st>>>(lv.t_m2m32, lv.tc_sm2m, 4, ch.ncoef, lv.ncoef, lv.tc_np,
+                                                      ch.tc_kc, lv.tc_bm2m);
+            HFMM_CUDA_TRY(cudaGetLastError());
+        }
         const int64_t span = (int64_t)1 << (2 * (L - l)), cspan = span >> 2;
         auto nonempty = [&](int64_t b) { return lb[(b + 1) * span] > lb[b * span]; };
         auto cnonempty = [&](int64_t b) { return lb[(b + 1) * cspan] > lb[b * cspan]; };
         std::vector<TcTile> tiles;
         std::vector<TcStep> steps;
         pair_tiles(lv.nbox, nonempty, [&](int32_t b0, int32_t b1) {
+            const size_t first = steps.size();
             for (int c = 0; c < 4; ++c) {
                 const int32_t s0 = (b0 >= 0 && cnonempty(4 * (int64_t)b0 + c)) ? 4 * b0 + c : -1;
                 const int32_t s1 = (b1 >= 0 && cnonempty(4 * (int64_t)b1 + c)) ? 4 * b1 + c : -1;
                 if (s0 >= 0 || s1 >= 0) push_step(steps, 2, c, s0, s1, ch.tc_kc, ch.tc_nbw / 16);
             }
+            if (mruns)
+                for (size_t j = first; j + 1 < steps.size(); ++j)
+                    steps[j].cont = steps[j].c0 == steps[j + 1].c0 ? 1 : 0;
         }, tiles, steps);
         HFMM_TRY(upload_tiles(P, tiles, steps, &lv.tc_mtiles, &lv.tc_msteps, &lv.tc_nmtiles, &lv.tc_mmaxsteps));
     }

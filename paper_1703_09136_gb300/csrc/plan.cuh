@@ -201,6 +201,12 @@ struct hfmm_plan_s {
     int64_t dj_njobs = 0;
     bool tc_on = false;             // every level lmin..L has tensor-core M2M / downward state
     bool tc_l2p = false;            // leaf L2P fused into the tensor-core downward epilogue
+    // leaf level with level-wide scales: every leaf multipole row r written with
+    // the exponent of the bound 2 qmax_r p2m_gain (p2m_gain = largest sum over a
+    // leaf's points of |basis|), one factor for all free and reaction tables, so
+    // the leaf-level V and reaction steps of a tile accumulate in TMEM (one drain)
+    bool tc_leaf_runs = false;
+    float p2m_gain = 0.0f;
     // concurrent near field: the far-field chain on a high-priority stream, the
     // near field on a low-priority one, both forked from and joined back into the
     // caller's stream (created on first use)
