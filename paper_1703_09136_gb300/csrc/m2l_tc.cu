@@ -179,6 +179,22 @@ __global__ void p2m_gain_kernel(const int32_t* lb, int64_t nleaf, const cf* basi
     if (lane == 0 && m > 0.0f) atomicMax(gmax, __float_as_uint(m));
 }
 
+// Largest over the matrices i and output columns p of sum_m |M[i][m][p]| (M
+// nin x nout complex, [m][p] layout): the factor of an infinity-norm bound.
+__global__ void tc_colsum_kernel(const cf* M, int nin, int nout, unsigned* gmax) {
+    const int i = blockIdx.x;
+    float mx = 0.0f;
+    for (int p = threadIdx.x; p < nout; p += blockDim.x) {
+        float sum = 0.0f;
+        for (int m = 0; m < nin; ++m) {
+            const cf z = M[((int64_t)i * nin + m) * nout + p];
+            sum += sqrtf(z.x * z.x + z.y * z.y);
+        }
+        mx = fmaxf(mx, sum);
+    }
+    if (mx > 0.0f) atomicMax(gmax, __float_as_uint(mx));
+}
+
 // Pre-split B chunks: for matrix index i, chunk c, part (0 hi, 1 lo):
 //   half offset ((i * kc + c) * 2 + part) * (Np * 16) + ((n / 8) * 2 + (k % 16) / 8) * 64 + (n % 8) * 8 + k % 8
 // of the entry scaled by 1 / sc[i].  M is a column-major complex matrix [m][p] (nin x nout).
@@ -231,7 +247,8 @@ constexpr int TC2_THREADS = 192;   // warps 0-3 drain, warp 4 TMA, warp 5 MMA
 template <int NB>
 __device__ __forceinline__ void tc_store_row(const float (&acc)[NB], int box, int row, int rc, int cb, int nbz,
                                              int n0, int nrhs, int nc, int nrc, cf* __restrict__ out,
-                                             __half* __restrict__ sdst, float* __restrict__ ssc, int kcd) {
+                                             __half* __restrict__ sdst, float* __restrict__ ssc, int kcd,
+                                             const unsigned* __restrict__ qmax, float qgain) {
     const int rr = row & 63, r = rc * 64 + rr;
     if (out && r < nrhs) {
         float* o = (float*)(out + ((int64_t)box * nrhs + r) * nc);
@@ -243,9 +260,12 @@ __device__ __forceinline__ void tc_store_row(const float (&acc)[NB], int box, in
         }
     }
     if (sdst) {
+        // level-wide scale (qmax given): the exponent of the bound 2 max|q_r| qgain
         float m = 0.0f;
+        if (qmax) m = r < nrhs ? 2.0f * __uint_as_float(qmax[r]) * qgain : 0.0f;
+        else
 #pragma unroll
-        for (int j = 0; j < NB; ++j) m = fmaxf(m, fabsf(acc[j]));
+            for (int j = 0; j < NB; ++j) m = fmaxf(m, fabsf(acc[j]));
         const int e = f16_exp(m);
         const float s = pow2f(e);
         ssc[(((int64_t)box * nrc + rc) * nbz + cb) * 64 + rr] = pow2f(-e);
@@ -284,7 +304,7 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
     const float* __restrict__ psc, int nsbp, int sbp, const __half* __restrict__ zero4k, cf* __restrict__ out,
     int nrhs, int nc, int kc, int kc2, int nrc, int Np, __half* __restrict__ sdst, float* __restrict__ ssc, int kcd,
     int nseg, float* __restrict__ part, const cf* __restrict__ l2p_basis, const int32_t* __restrict__ lbeg,
-    cf* __restrict__ ys, long spin, int* err) {
+    cf* __restrict__ ys, long spin, int* err, const unsigned* __restrict__ qmax, float qgain) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     using CFG = TcCfg<NB>;
@@ -393,7 +413,7 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
         } else {
             const int box = tgt ? tile.b1 : tile.b0;   // uniform over the warp
             if (box >= 0) {
-                tc_store_row<NB>(acc, box, row, rc, cb, nbz, n0, nrhs, nc, nrc, nullptr, sdst, ssc, kcd);
+                tc_store_row<NB>(acc, box, row, rc, cb, nbz, n0, nrhs, nc, nrc, nullptr, sdst, ssc, kcd, qmax, qgain);
                 if ((TcL2p<NB>::fits && l2p_basis) || out) {
                     // The warp's 32 rows of the result go to the ring once (every MMA of
                     // this CTA has completed; one region per warp); the leaf L2P and the
@@ -583,7 +603,8 @@ __global__ void __launch_bounds__(TC2_THREADS, TcCfg<NB>::ctas) m2l_tc_kernel(
 template <int NB>
 __global__ void tc_reduce_kernel(const TcTile* __restrict__ tiles, int ntiles, int nrcl, int nbz, int nseg,
                                  const float* __restrict__ part, cf* __restrict__ out, int nrhs, int nc, int nrc,
-                                 __half* __restrict__ sdst, float* __restrict__ ssc, int kcd) {
+                                 __half* __restrict__ sdst, float* __restrict__ ssc, int kcd,
+                                 const unsigned* __restrict__ qmax, float qgain) {
     constexpr int NQ = NB / 4;
     const int lane = threadIdx.x & 31;
     const int64_t nwarp = (int64_t)ntiles * nrcl * nbz * 128;
@@ -620,6 +641,7 @@ __global__ void tc_reduce_kernel(const TcTile* __restrict__ tiles, int ntiles, i
         if (sdst) {
             float m = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
             for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (qmax) m = r < nrhs ? 2.0f * __uint_as_float(qmax[r]) * qgain : 0.0f;   // level-wide scale
             const int e = f16_exp(m);
             if (lane == 0) ssc[(((int64_t)box * nrc + rc) * nbz + cb) * 64 + rr] = pow2f(-e);
             if (jq < NQ && (g0 >> 4) < kcd) {
@@ -731,6 +753,8 @@ struct TcLaunch {
     int kcd;
     int maxsteps;
     bool l2p;        // leaf level: L2P into y32 from the epilogue
+    const unsigned* qmax = nullptr;   // sdst with the level-wide scale 2 max|q_r| qgain
+    float qgain = 0.0f;
 };
 
 // Segments per tile for a launch of ntiles x nb CTAs (x nrc RHS blocks): split
@@ -758,13 +782,14 @@ hfmm_status launch_nb(hfmm_plan_s* P, const TcLaunch& a, int nrhs, cudaStream_t 
     m2l_tc_kernel<NB><<<grid, TC2_THREADS, smem, st>>>(
         (const TcTile*)a.tiles, (const TcStep*)a.steps, a.Bfree, a.Breact, a.Bsec, a.sfree, a.sreact, a.ssec, a.amma,
         a.asc, a.nsba, a.sba, a.pmma, a.psc, a.nsbp, a.sbp, P->tc_zero, a.out, nrhs, a.nc, a.kc, a.kc2, nrc, a.np,
-        a.sdst, a.ssc, a.kcd, nseg, part, a.l2p ? P->basis32 : nullptr, P->leaf_begin, P->y32, P->tc_spin, P->tc_err);
+        a.sdst, a.ssc, a.kcd, nseg, part, a.l2p ? P->basis32 : nullptr, P->leaf_begin, P->y32, P->tc_spin, P->tc_err,
+        a.qmax, a.qgain);
     HFMM_CUDA_TRY(cudaGetLastError());
     if (part) {
         const int64_t warps = a.ntiles * nrcl * a.nb * 128;
         const unsigned blocks = (unsigned)std::min<int64_t>((warps + 7) / 8, 8 * 152);
         tc_reduce_kernel<NB><<<blocks, 256, 0, st>>>((const TcTile*)a.tiles, (int)a.ntiles, nrcl, a.nb, nseg, part,
-                                                      a.out, nrhs, a.nc, nrc, a.sdst, a.ssc, a.kcd);
+                                                      a.out, nrhs, a.nc, nrc, a.sdst, a.ssc, a.kcd, a.qmax, a.qgain);
         HFMM_CUDA_TRY(cudaGetLastError());
         ++P->launches;
     }
@@ -817,10 +842,51 @@ hfmm_status tc_wait_probe(long spin, int arrive, int* timed_out) {
 
 // Plan-time preparation of the tensor-core upward (M2M) and downward
 // (L2L + M2L) passes of every level lmin .. L.
+// Largest float of a one-word device max (float bits), read back synchronously.
+hfmm_status read_fmax(hfmm_plan_s* P, unsigned* d, float* out, cudaStream_t st) {
+    unsigned h = 0;
+    HFMM_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    HFMM_CUDA_TRY(cudaStreamSynchronize(st));
+    std::memcpy(out, &h, sizeof(float));
+    return HFMM_OK;
+}
+
 hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
     const int L = P->L;
     const int nrc = (P->max_rhs + 63) / 64;
     const auto& lb = P->h_leaf_begin;
+    // Level-wide scales, so that the free and reaction steps of a tile (and the
+    // four children of an M2M tile) accumulate in TMEM with one drain: the leaves,
+    // when their P2M is the row kernel (bound 2 max|q_r| sum_j |B[j][m]|), and the
+    // level above, when its rows fit one column block (bound 4 max_c ||T_c|| times
+    // the leaves' bound, T_c the scaled M2M shifts).
+    {
+        LevelInfo& lf = P->lev[L];
+        if (lf.ncoef <= 32 && lf.nv + lf.nr > 0) {
+            unsigned* dg = nullptr;
+            HFMM_TRY(plan_alloc(P, (void**)&dg, 2 * sizeof(unsigned)));
+            HFMM_CUDA_TRY(cudaMemsetAsync(dg, 0, 2 * sizeof(unsigned), st));
+            p2m_gain_kernel<<<(unsigned)ceil_div(lf.nbox, 4), 128, 0, st>>>(P->leaf_begin, lf.nbox, P->basis32,
+                                                                            lf.ncoef, dg);
+            HFMM_CUDA_TRY(cudaGetLastError());
+            HFMM_TRY(read_fmax(P, dg, &P->p2m_gain, st));
+            lf.tc_runs = P->tc_leaf_runs = true;
+            lf.tc_gain = P->p2m_gain;
+            if (L - 1 >= P->lmin) {
+                LevelInfo& up = P->lev[L - 1];
+                int nb, nbw, np, kc;
+                tc_widths(up.ncoef, &nb, &nbw, &np, &kc);
+                if (nb == 1 && up.nv + up.nr > 0 && up.t_m2m32) {
+                    tc_colsum_kernel<<<4, 128, 0, st>>>(up.t_m2m32, lf.ncoef, up.ncoef, dg + 1);
+                    HFMM_CUDA_TRY(cudaGetLastError());
+                    float cs = 0.0f;
+                    HFMM_TRY(read_fmax(P, dg + 1, &cs, st));
+                    up.tc_runs = true;
+                    up.tc_gain = 4.0f * cs * lf.tc_gain;
+                }
+            }
+        }
+    }
     for (int l = P->lmin; l <= L; ++l) {
         LevelInfo& lv = P->lev[l];
         tc_widths(lv.ncoef, &lv.tc_nb, &lv.tc_nbw, &lv.tc_np, &lv.tc_kc);
@@ -859,9 +925,8 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
         if (lv.nr > 0)
             HFMM_TRY(btable(P, lv.t_react32, lv.n_react_entries, lv.ncoef, lv.ncoef, Np, lv.tc_kc, &lv.tc_breact,
                             &lv.tc_sreact, st));
-        // leaf level: level-wide scales (one factor for the multipoles of a row,
-        // one for the free and reaction tables) when the leaf P2M is the row kernel
-        const bool runs = l == L && lv.ncoef <= 32 && lv.nv + lv.nr > 0;
+        // level-wide scales: one factor for the free and reaction tables
+        const bool runs = lv.tc_runs;
         if (runs) {
             const int na = lv.nv > 0 ? 49 : 0, nr = lv.nr > 0 ? lv.n_react_entries : 0;
             tc_common_scale_kernel<<<1, 256, 0, st>>>(lv.tc_sfree, na, lv.tc_sreact, nr);
@@ -871,17 +936,6 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
             if (nr) tc_btable_kernel<<<4 * 152, 256, 0, st>>>(lv.t_react32, lv.tc_sreact, nr, lv.ncoef, lv.ncoef, Np,
                                                                lv.tc_kc, lv.tc_breact);
             HFMM_CUDA_TRY(cudaGetLastError());
-            unsigned* dg = nullptr;
-            HFMM_TRY(plan_alloc(P, (void**)&dg, sizeof(unsigned)));
-            HFMM_CUDA_TRY(cudaMemsetAsync(dg, 0, sizeof(unsigned), st));
-            p2m_gain_kernel<<<(unsigned)ceil_div(lv.nbox, 4), 128, 0, st>>>(P->leaf_begin, lv.nbox, P->basis32,
-                                                                            lv.ncoef, dg);
-            HFMM_CUDA_TRY(cudaGetLastError());
-            unsigned hg = 0;
-            HFMM_CUDA_TRY(cudaMemcpyAsync(&hg, dg, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-            HFMM_CUDA_TRY(cudaStreamSynchronize(st));
-            std::memcpy(&P->p2m_gain, &hg, sizeof(float));
-            P->tc_leaf_runs = true;
         }
         if (has_parent)
             HFMM_TRY(btable(P, P->lev[l - 1].t_l2l32, 4, npp, lv.ncoef, Np, lv.tc_kc2, &lv.tc_bl2l, &lv.tc_sl2l, st));
@@ -946,9 +1000,9 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
         LevelInfo& lv = P->lev[l];
         const LevelInfo& ch = P->lev[l + 1];
         HFMM_TRY(btable(P, lv.t_m2m32, 4, ch.ncoef, lv.ncoef, lv.tc_np, ch.tc_kc, &lv.tc_bm2m, &lv.tc_sm2m, st));
-        // M2M from the leaves (their rows written with level-wide scales): one
-        // factor for the four shift matrices, so a tile's four children accumulate in TMEM
-        const bool mruns = P->tc_leaf_runs && l == L - 1;
+        // M2M from a level with level-wide scales: one factor for the four shift
+        // matrices, so a tile's four children accumulate in TMEM
+        const bool mruns = ch.tc_runs;
         if (mruns) {
             tc_common_scale_kernel<<<1, 256, 0, st>>>(lv.tc_sm2m, 4, nullptr, 0);
             tc_btable_kernel<<<4 * 152, 256, 0, st>>>(lv.t_m2m32, lv.tc_sm2m, 4, ch.ncoef, lv.ncoef, lv.tc_np,
@@ -1013,6 +1067,10 @@ hfmm_status launch_m2m_tc(hfmm_plan_s* P, int l, int nrhs, bool fp32_out, cudaSt
                lv.tc_sm2m, nullptr, nullptr, 1, 1, ch.tc_amma, ch.tc_asc, ch.tc_nb, ch.tc_nbw / 16,
                fp32_out ? lv.mult32 : nullptr, lv.ncoef, 0, ch.tc_kc, lv.tc_np, lv.tc_nb, lv.tc_nbw, lv.tc_amma, lv.tc_asc, lv.tc_kc,
                lv.tc_mmaxsteps, false};
+    if (lv.tc_runs && l < P->L) {   // this level's multipoles with the level-wide scale
+        a.qmax = P->qmax;
+        a.qgain = lv.tc_gain;
+    }
     return launch_tc(P, a, nrhs, st);
 }
 

@@ -36,6 +36,11 @@ struct LevelInfo {
     int64_t nr = 0;
     int32_t* r_tgt = nullptr;     // [n_rtgt] target boxes with a nonempty reaction list, increasing
     int64_t n_rtgt = 0;
+    // tensor-core pass with level-wide scales: this level's multipole rows are
+    // written with the exponent of the bound 2 max|q_r| tc_gain, and its free and
+    // reaction tables share one factor (a tile's steps accumulate in TMEM)
+    bool tc_runs = false;
+    float tc_gain = 0.0f;
     // tables
     cd* t_free = nullptr;         // [49][4p + 1]  C_n(dx h, dy h), n = -2p .. 2p
     cd* t_m2m = nullptr;          // [4][2(p + p_child) + 1] J_n(parent - child_c)  (this level = parent)
