@@ -50,7 +50,7 @@ PROFILE_STEPS = 10           # applies of the profiling plan (stage and leaf-ker
 # by the leaf count to the 65536 leaves of the 1M-point workload (same order,
 # width and points per leaf: the traffic grows in proportion).  It belongs to
 # the kernel as captured; a changed kernel reports null until re-captured.
-LEAF48_TRAFFIC_BYTES = (110.809856e6 + 14.441984e6) * 16
+LEAF48_TRAFFIC_BYTES = (110.769408e6 + 13.832448e6) * 16
 
 
 def max_over_ranks(x):
