@@ -615,7 +615,9 @@ __global__ void __launch_bounds__(PC_THREADS) p2m32c_kernel(const int32_t* lb, c
 // p2m32c_kernel) and, when write_mult, the FP32 row.  No CTA-wide pass follows
 // the accumulation, so the short per-leaf chain overlaps across the many CTAs
 // an SM holds.  The terms are added in the order of p2m32c_kernel (points in
-// ascending order), so both write the same bits.  nc <= NCM, NCM a multiple of 8.
+// ascending order), so the FP32 rows are the same bits; with qmax given the
+// f16 split takes the level-wide exponent instead of the row's own.  nc <= NCM,
+// NCM a multiple of 8.
 constexpr int PR_SRC = 32;
 template <int NCM>
 __global__ void __launch_bounds__(64) p2m_rows_kernel(const int32_t* lb, const cf* qs, const cf* basis, int nrhs,
