@@ -465,6 +465,37 @@ def test_profile_plan_reports_stage_and_leaf_kernel_times():
     plan.close(); plain.close()
 
 
+def test_level_wide_scales_with_spread_and_spiked_right_hand_sides():
+    """The leaves and the level above them carry one f16 exponent per
+    right-hand side (from the bound 2 max|q_r| sum|B|) so that a tile's free
+    and reaction steps accumulate in TMEM: right-hand sides scaled from 1e-20
+    to 1e20, an all-zero one and ones with a single strength 1e6 times the
+    rest (a bound far above most leaves' multipoles) against the FP64 path,
+    right-hand side by right-hand side."""
+    from paper_1703_09136_gb300 import MIXED
+    n, nrhs = 16384, 64
+    xy = W.points_in_box(4, n, ((0.0, 1.0), (0.02, 1.02)), salt=41)
+    q = W.strengths(4, n, nrhs, salt=42)
+    q *= (10.0 ** np.linspace(-20, 20, nrhs))[:, None]
+    q[7] = 0.0
+    rng = np.random.default_rng(43)
+    for r in (11, 40):
+        q[r, rng.integers(n)] *= 1e6
+    mp = Plan(xy, CFG4_MED, tol=1e-6, leaf_size=16, max_rhs=nrhs, precision=MIXED)
+    f64 = Plan(xy, CFG4_MED, tol=1e-6, leaf_size=16, max_rhs=nrhs)
+    assert mp.info["tensor_levels"] > 0
+    y = mp.apply(torch.from_numpy(q.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
+    ref = f64.apply(torch.from_numpy(q).cuda()).cpu().numpy()
+    assert not np.any(y[7])
+    for r in range(nrhs):
+        if r == 7:
+            continue
+        assert np.all(np.isfinite(y[r])), r
+        assert direct.rel_l2(y[r], ref[r]) < MIXED_TOL, (r, direct.rel_l2(y[r], ref[r]))
+    mp.close()
+    f64.close()
+
+
 def test_tensor_core_ragged_rhs_blocks_and_changing_width():
     """Two 64-row right-hand-side blocks with a ragged second block (70 RHS),
     then a narrower apply (5 RHS) on the same plan: every column agrees with
