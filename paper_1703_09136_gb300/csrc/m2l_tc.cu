@@ -87,6 +87,7 @@ struct TcCfg {
     static constexpr size_t smem = (size_t)stages * stage_bytes + 256;
 };
 constexpr int TC_MAX_NP = 128;         // widest column block (one 128-column TMEM buffer)
+constexpr int TC_RUN_LEVELS = 2;       // finest levels with level-wide scales (the leaves and the level above)
 
 // Shared memory of the leaf L2P in the downward epilogue, per drain warp: its
 // 32 rows of beta~ (stride NB + 1) and two buffers of the basis rows of 8
@@ -857,33 +858,34 @@ hfmm_status build_tc(hfmm_plan_s* P, cudaStream_t st) {
     const auto& lb = P->h_leaf_begin;
     // Level-wide scales, so that the free and reaction steps of a tile (and the
     // four children of an M2M tile) accumulate in TMEM with one drain: the leaves,
-    // when their P2M is the row kernel (bound 2 max|q_r| sum_j |B[j][m]|), and the
-    // level above, when its rows fit one column block (bound 4 max_c ||T_c|| times
-    // the leaves' bound, T_c the scaled M2M shifts).
+    // when their P2M is the row kernel (bound 2 max|q_r| sum_j |B[j][m]|), and up
+    // to TC_RUN_LEVELS - 1 levels above, while their rows fit one column block
+    // (bound 4 max_c ||T_c|| times the bound of the level below, T_c the scaled
+    // M2M shifts).
     {
         LevelInfo& lf = P->lev[L];
         if (lf.ncoef <= 32 && lf.nv + lf.nr > 0) {
             unsigned* dg = nullptr;
-            HFMM_TRY(plan_alloc(P, (void**)&dg, 2 * sizeof(unsigned)));
-            HFMM_CUDA_TRY(cudaMemsetAsync(dg, 0, 2 * sizeof(unsigned), st));
+            HFMM_TRY(plan_alloc(P, (void**)&dg, (TC_RUN_LEVELS + 1) * sizeof(unsigned)));
+            HFMM_CUDA_TRY(cudaMemsetAsync(dg, 0, (TC_RUN_LEVELS + 1) * sizeof(unsigned), st));
             p2m_gain_kernel<<<(unsigned)ceil_div(lf.nbox, 4), 128, 0, st>>>(P->leaf_begin, lf.nbox, P->basis32,
                                                                             lf.ncoef, dg);
             HFMM_CUDA_TRY(cudaGetLastError());
             HFMM_TRY(read_fmax(P, dg, &P->p2m_gain, st));
             lf.tc_runs = P->tc_leaf_runs = true;
             lf.tc_gain = P->p2m_gain;
-            if (L - 1 >= P->lmin) {
-                LevelInfo& up = P->lev[L - 1];
+            for (int l = L - 1, i = 1; l >= P->lmin && i < TC_RUN_LEVELS; --l, ++i) {
+                LevelInfo& up = P->lev[l];
+                const LevelInfo& dn = P->lev[l + 1];
                 int nb, nbw, np, kc;
                 tc_widths(up.ncoef, &nb, &nbw, &np, &kc);
-                if (nb == 1 && up.nv + up.nr > 0 && up.t_m2m32) {
-                    tc_colsum_kernel<<<4, 128, 0, st>>>(up.t_m2m32, lf.ncoef, up.ncoef, dg + 1);
-                    HFMM_CUDA_TRY(cudaGetLastError());
-                    float cs = 0.0f;
-                    HFMM_TRY(read_fmax(P, dg + 1, &cs, st));
-                    up.tc_runs = true;
-                    up.tc_gain = 4.0f * cs * lf.tc_gain;
-                }
+                if (nb != 1 || up.nv + up.nr == 0 || !up.t_m2m32) break;
+                tc_colsum_kernel<<<4, 128, 0, st>>>(up.t_m2m32, dn.ncoef, up.ncoef, dg + i);
+                HFMM_CUDA_TRY(cudaGetLastError());
+                float cs = 0.0f;
+                HFMM_TRY(read_fmax(P, dg + i, &cs, st));
+                up.tc_runs = true;
+                up.tc_gain = 4.0f * cs * dn.tc_gain;
             }
         }
     }
