@@ -205,7 +205,9 @@ typedef struct {
     int32_t adaptive;           /* 1 for HFMM_FLAG_ADAPTIVE plans (levels = deepest level,
                                    nonempty_leaves = leaves, direct_leaf_pairs = leaf pairs of
                                    the directly summed reaction) */
-    int32_t reserved3;
+    int32_t tc_run_levels;      /* HFMM_MIXED, tensor-core pass: number of the finest levels with
+                                   level-wide f16 scales, whose free and reaction steps (and the
+                                   M2M from them) accumulate in tensor memory with one drain */
     int64_t w_pairs;            /* adaptive: (leaf, box) M2P pairs */
     int64_t x_pairs;            /* adaptive: (box, leaf) P2L pairs */
 } hfmm_plan_info;

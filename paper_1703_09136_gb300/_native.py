@@ -67,7 +67,7 @@ class hfmm_plan_info(ctypes.Structure):
                 ("near_tc_blocks", ctypes.c_int64), ("near_simt_leaves", ctypes.c_int64),
                 ("leaf_l2p_fused", ctypes.c_int32), ("leaf_tc_width", ctypes.c_int32),
                 ("table_check", ctypes.c_double), ("small_rhs", ctypes.c_int32), ("diag_levels", ctypes.c_int32),
-                ("diag_check", ctypes.c_double), ("adaptive", ctypes.c_int32), ("reserved3", ctypes.c_int32),
+                ("diag_check", ctypes.c_double), ("adaptive", ctypes.c_int32), ("tc_run_levels", ctypes.c_int32),
                 ("w_pairs", ctypes.c_int64), ("x_pairs", ctypes.c_int64)]
 
 

@@ -548,8 +548,10 @@ hfmm_status hfmm_plan_get_info(hfmm_plan_t P, hfmm_plan_info* info) {
         HFMM_CUDA_TRY(cudaMemcpy(&e, P->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
         info->device_error = e;
     }
-    for (int l = 0; l <= P->L; ++l)
+    for (int l = 0; l <= P->L; ++l) {
         info->tensor_levels += P->lev[l].tc_ntiles > 0 ? 1 : 0;
+        info->tc_run_levels += (P->tc_on && P->lev[l].tc_runs) ? 1 : 0;
+    }
     for (int s = 0; s < HFMM_NUM_STAGES; ++s) {
         info->flops_last_apply[s] = P->st_flops[s];
         info->bytes_last_apply[s] = P->st_bytes[s];

@@ -483,7 +483,7 @@ def test_level_wide_scales_with_spread_and_spiked_right_hand_sides():
         q[r, rng.integers(n)] *= 1e6
     mp = Plan(xy, CFG4_MED, tol=1e-6, leaf_size=16, max_rhs=nrhs, precision=MIXED)
     f64 = Plan(xy, CFG4_MED, tol=1e-6, leaf_size=16, max_rhs=nrhs)
-    assert mp.info["tensor_levels"] > 0
+    assert mp.info["tensor_levels"] > 0 and mp.info["tc_run_levels"] == 2
     y = mp.apply(torch.from_numpy(q.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
     ref = f64.apply(torch.from_numpy(q).cuda()).cpu().numpy()
     assert not np.any(y[7])
