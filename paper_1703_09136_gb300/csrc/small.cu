@@ -304,12 +304,10 @@ size_t vblock_smem(int cpt, int nc, int npp) {
 }
 
 template <int CPT>
-__global__ void __launch_bounds__(256, CPT == 2 ? 4 : 2) vblock_kernel(const int32_t* __restrict__ lb, int L, int l, int nrhs,
-                                                        int nc, int npp, const cf* __restrict__ ploc,
-                                                        const cf* __restrict__ Tl2l, const cf* __restrict__ mult,
-                                                        const int32_t* __restrict__ v_begin,
-                                                        const int32_t* __restrict__ v_off,
-                                                        const cf* __restrict__ Tfree, cf* __restrict__ loc) {
+__global__ void __launch_bounds__(256, CPT == 2 ? 4 : 2)
+    vblock_kernel(const int32_t* __restrict__ lb, int L, int l, int nrhs, int nc, int npp, const cf* __restrict__ ploc,
+                  const cf* __restrict__ Tl2l, const cf* __restrict__ mult, const int32_t* __restrict__ v_begin,
+                  const int32_t* __restrict__ v_off, const cf* __restrict__ Tfree, cf* __restrict__ loc) {
     constexpr int VB_PF = CPT == 2 ? 2 : 4;        // matrix rows per lane per fetch (two fetches in flight)
     extern __shared__ float4 sm_vb[];
     const int kmax = max(nc, npp), ncw = nc | 1, npw = npp | 1;   // odd row strides
