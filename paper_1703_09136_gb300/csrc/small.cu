@@ -276,10 +276,10 @@ __global__ void __launch_bounds__(NW * 32) down_small_kernel(
 // M2L matrix, so one matrix row read from L2 feeds 4 targets (a per-box pass
 // reads it once per target).  The sources of the block (the 12 x 8 boxes of
 // level l around it, the 8 parents' local expansions) are staged in shared
-// memory once.  Warps 2 c and 2 c + 1 own the 8 targets of child position c,
-// each taking every other operator of the position's list; a lane owns 4
-// targets x CPT consecutive output coefficients.  The two warps' sums are
-// added in a fixed order, operators and k run in increasing order: the
+// memory once.  NWC warps (2, or 4 for CPT > 2) own the 8 targets of child
+// position c, each taking every NWC-th operator of the position's list; a
+// lane owns 4 targets x CPT consecutive output coefficients.  The warps' sums
+// are added in a fixed order, operators and k run in increasing order: the
 // result does not depend on scheduling.  The V-list entries give which
 // offsets a target uses: the source of offset index o = (dx + 3) * 7 + dy + 3
 // is the box (ix - dx, iy - dy) of level l, as the list builder enumerates
@@ -296,32 +296,37 @@ __device__ __forceinline__ void cp_async8_vb(void* dst, const void* src) {
                  :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
 }
 
+// warps per child position: 2 with 2 coefficients per lane (levels of many
+// blocks), 4 otherwise (levels of few blocks, the wider lanes hold more registers)
+constexpr int vb_nwc(int cpt) { return cpt == 2 ? 2 : 4; }
+
 size_t vblock_smem(int cpt, int nc, int npp) {
     const int kmax = std::max(nc, npp), ncw = nc | 1, npw = npp | 1;
-    const size_t red = (size_t)4 * 32 * 4 * cpt;   // half 1's sums, over the window
+    const size_t red = (size_t)4 * (vb_nwc(cpt) - 1) * 32 * 4 * cpt;   // the other warps' sums, over the window
     return sizeof(cf) * (std::max((size_t)VB_SLOTS * ncw, red) + kmax + 8 * (size_t)npw) +
            sizeof(uint64_t) * VB_T;
 }
 
 template <int CPT>
-__global__ void __launch_bounds__(256, CPT == 2 ? 4 : 2)
+__global__ void __launch_bounds__(128 * vb_nwc(CPT), CPT == 2 ? 4 : 1)
     vblock_kernel(const int32_t* __restrict__ lb, int L, int l, int nrhs, int nc, int npp, const cf* __restrict__ ploc,
                   const cf* __restrict__ Tl2l, const cf* __restrict__ mult, const int32_t* __restrict__ v_begin,
                   const int32_t* __restrict__ v_off, const cf* __restrict__ Tfree, cf* __restrict__ loc) {
     constexpr int VB_PF = CPT == 2 ? 2 : 4;        // matrix rows per lane per fetch (two fetches in flight)
     extern __shared__ float4 sm_vb[];
     const int kmax = max(nc, npp), ncw = nc | 1, npw = npp | 1;   // odd row strides
-    const int wsz = max(VB_SLOTS * ncw, 4 * 32 * 4 * CPT);
+    constexpr int NWC = vb_nwc(CPT), NT = 128 * NWC;   // warps per child position, threads
+    const int wsz = max(VB_SLOTS * ncw, 4 * (NWC - 1) * 32 * 4 * CPT);
     cf* W = (cf*)sm_vb;                            // source window [slot][ncw]; then half 1's sums
     cf* Z = W + wsz;                               // kmax zeros (sources of lanes without the operator)
     cf* Pw = Z + kmax;                             // parents' local expansions [8][npw]
     uint64_t* mask = (uint64_t*)(Pw + 8 * npw);    // [32 targets]
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, c = w >> 1, h = w & 1;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, c = w / NWC, h = w % NWC;
     const int r = blockIdx.y;
     const int64_t b0 = (int64_t)blockIdx.x * VB_T;
     const int bx0 = (int)morton_x((uint32_t)b0), by0 = (int)morton_y((uint32_t)b0);
     const int m = 1 << l;
-    for (int e = tid; e < kmax; e += 256) Z[e] = cfmk(0.f, 0.f);
+    for (int e = tid; e < kmax; e += NT) Z[e] = cfmk(0.f, 0.f);
     if (tid < VB_T) {
         const int64_t b = b0 + tid;
         int32_t lo, hi;
@@ -337,7 +342,7 @@ __global__ void __launch_bounds__(256, CPT == 2 ? 4 : 2)
     }
     // sources: slot (wx, wy) holds box (bx0 - 2 + wx, by0 - 2 + wy); boxes
     // outside the domain are never a source
-    for (int s = w; s < VB_SLOTS; s += 8) {
+    for (int s = w; s < VB_SLOTS; s += NT / 32) {
         const int sx = bx0 - 2 + s % VB_WX, sy = by0 - 2 + s / VB_WX;
         const bool in = sx >= 0 && sy >= 0 && sx < m && sy < m;
         const cf* src = in ? mult + ((int64_t)morton((uint32_t)sx, (uint32_t)sy) * nrhs + r) * nc : nullptr;
@@ -347,7 +352,7 @@ __global__ void __launch_bounds__(256, CPT == 2 ? 4 : 2)
         }
     }
     if (ploc)
-        for (int j = w; j < 8; j += 8)
+        for (int j = w; j < 8; j += NT / 32)
             for (int k = lane; k < npp; k += 32)
                 cp_async8_vb(Pw + j * npw + k, ploc + ((b0 / 4 + j) * nrhs + r) * (int64_t)npp + k);
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
@@ -380,7 +385,7 @@ __global__ void __launch_bounds__(256, CPT == 2 ? 4 : 2)
         const uint64_t l2l = um & (0xFull << VB_L2L);
         const int op = __ffsll((long long)(l2l ? l2l : um)) - 1;
         um &= ~(1ull << op);
-        if ((rank & 1) != h) continue;
+        if (rank % NWC != h) continue;
         const bool isl2l = op >= VB_L2L;
         const cf* sp[4];
 #pragma unroll
@@ -425,17 +430,27 @@ __global__ void __launch_bounds__(256, CPT == 2 ? 4 : 2)
             use(mb, k0 + VB_PF);
         }
     }
-    // warp 2 c + 1's sums go to shared memory (over the window), warp 2 c adds and stores
+    // the sums of warps NWC c + 1 .. go to shared memory (over the window);
+    // warp NWC c adds them in warp order and stores
     __syncthreads();
-    cf* red = W + (c * 32 + lane) * 4 * CPT;
-    if (h == 1) {
+    cf* red = W + ((c * (NWC - 1)) * 32 + lane) * 4 * CPT;   // [c][h - 1][lane][4 CPT]
+    if (h > 0) {
 #pragma unroll
         for (int t = 0; t < 4; ++t)
 #pragma unroll
-            for (int u = 0; u < CPT; ++u) red[t * CPT + u] = acc[t][u];
+            for (int u = 0; u < CPT; ++u) red[((h - 1) * 32) * 4 * CPT + t * CPT + u] = acc[t][u];
     }
     __syncthreads();
-    if (h == 1) return;
+    if (h > 0) return;
+#pragma unroll
+    for (int hh = 1; hh < NWC; ++hh)
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int u = 0; u < CPT; ++u) {
+                const cf o = red[((hh - 1) * 32) * 4 * CPT + t * CPT + u];
+                acc[t][u] = cfmk(acc[t][u].x + o.x, acc[t][u].y + o.y);
+            }
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
         if (!(tm[t] & VB_LIVE)) continue;
@@ -443,8 +458,7 @@ __global__ void __launch_bounds__(256, CPT == 2 ? 4 : 2)
 #pragma unroll
         for (int u = 0; u < CPT; ++u) {
             if (!live_u[u]) continue;
-            const cf o = red[t * CPT + u];
-            loc[(b * nrhs + r) * nc + cg * CPT + u] = cfmk(acc[t][u].x + o.x, acc[t][u].y + o.y);
+            loc[(b * nrhs + r) * nc + cg * CPT + u] = acc[t][u];
         }
     }
 }
@@ -1035,7 +1049,7 @@ hfmm_status small_down(hfmm_plan_s* P, int l, int nrhs, int parts, cudaStream_t 
 #define HFMM_VBLOCK(C)                                                                                              \
     do {                                                                                                            \
         HFMM_CUDA_TRY(cudaFuncSetAttribute(vblock_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
-        vblock_kernel<C><<<grid, 256, sm, st>>>(P->leaf_begin, P->L, l, nrhs, nc, npp, ploc, tl2l, lv.mult32, vb,    \
+        vblock_kernel<C><<<grid, 128 * vb_nwc(C), sm, st>>>(P->leaf_begin, P->L, l, nrhs, nc, npp, ploc, tl2l, lv.mult32, vb,    \
                                                 lv.v_off, lv.t_free32, lv.loc32);                                   \
     } while (0)
         if (cpt == 2) HFMM_VBLOCK(2);
