@@ -428,7 +428,7 @@ hfmm_status hfmm_leaf_order_noalloc(int64_t n, const double* xy, int32_t levels,
  *            complex64 for HFMM_MIXED) in the caller's point order; x holds
  *            the initial guess on entry and the solution on return;
  *   tol      relative residual ||b - (sigma I + A) x|| / ||b|| to reach (the
- *            mixed path's apply carries ~1e-6 relative error: ask >= 1e-5);
+ *            mixed path's apply carries a few 1e-6 relative error: ask >= 1e-5);
  *   restart  Krylov dimension between restarts (1..1000), maxit the total
  *            number of applies; *iters, *relres report them (the true
  *            residual of the returned x).
